@@ -1,0 +1,134 @@
+/*
+ * sz3o.h -- serial CPU oracle of the SZ3-Interp hot path (TEST INFRASTRUCTURE).
+ *
+ * This library exists only to check the CUDA implementation.  It is called by
+ * the tests, by the smoke check and by the CPU-baseline leg of the benchmark;
+ * the product path never links, loads or calls it.  It shares no source, header,
+ * table or helper with the CUDA library: the only thing the two have in common
+ * is the written stream format and the parameter block layout.
+ *
+ * What it computes (SZ3 paper, arXiv 2111.02925):
+ *   - Alg. 1 (general compressor): per point, predict then quantize, save the
+ *     quantizer's unpredictable values, Huffman-encode the codes.  The
+ *     preprocessor and the lossless stage are bypassed (module bypass, Sec. 1).
+ *   - Sec. 6.2 "SZ3-Interp": multilevel linear / cubic interpolation predictor
+ *     with constant coefficients (no stored coefficients).
+ *   - Sec. 3.2 Quantizer: linear-scaling quantizer, bins of width 2*eb, the
+ *     prediction error mapped to the index of the bin holding it; errors out of
+ *     range are "unpredictable" and stored raw.  recover() reverses quantize().
+ *   - Sec. 3.2 Encoder: Huffman tree built greedily from the code frequencies,
+ *     codebook from the tree, codes encoded with it; save/load of the tree.
+ *
+ * The paper gives no formulas for the interpolation, no traversal order, no
+ * rounding rule and no Huffman tie-break; this oracle implements one written
+ * reading of each (listed in the design notes) and the CUDA path implements the
+ * same reading, so the two agree bit for bit.
+ *
+ * Floating point: every arithmetic step is one IEEE-754 round-to-nearest-even
+ * operation in the field's own type T (float or double), which is the type the
+ * paper's quantizer interface takes (quantize(T data, T pred), Appendix A.3).
+ * Compiled with -O2 -ffp-contract=off -fno-fast-math.
+ *
+ * All functions return 0 on success or a negative SZ3O_E_* code; none aborts.
+ * All pointers are host pointers owned by the caller.
+ */
+#ifndef SZ3O_H
+#define SZ3O_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SZ3O_OK = 0,
+  SZ3O_E_INVAL = -1,          /* bad dims / eb / radius / order / chunk size   */
+  SZ3O_E_NONFINITE = -2,      /* NaN or Inf in the input field                 */
+  SZ3O_E_ZERO_RANGE_REL = -3, /* REL bound on a field whose value range is 0   */
+  SZ3O_E_CAPACITY = -4,       /* output buffer too small                       */
+  SZ3O_E_CORRUPT = -5,        /* stream fails a magic/version/length check     */
+  SZ3O_E_NOMEM = -7           /* host allocation failed                        */
+};
+
+enum { SZ3O_F32 = 0, SZ3O_F64 = 1 };
+enum { SZ3O_EB_ABS = 0, SZ3O_EB_REL = 1 };
+enum { SZ3O_LINEAR = 0, SZ3O_CUBIC = 1 };
+
+#define SZ3O_MAX_LEVELS 32
+#define SZ3O_LMAX 24          /* longest Huffman code the format allows */
+#define SZ3O_HEADER_BYTES 288
+
+/* Parameter block.  Same byte layout as the CUDA library's sz3g_params. */
+typedef struct sz3o_params {
+  uint32_t dtype;          /* SZ3O_F32 / SZ3O_F64                          */
+  uint32_t ndim;           /* 1..4                                         */
+  uint64_t dims[4];        /* extents, slowest axis first; unused = 1      */
+  uint32_t eb_mode;        /* SZ3O_EB_ABS / SZ3O_EB_REL                    */
+  uint32_t interp;         /* SZ3O_LINEAR / SZ3O_CUBIC (all levels)        */
+  double eb;               /* > 0; REL: fraction of (max - min)            */
+  uint8_t dim_order[4];    /* permutation of 0..ndim-1 (all levels)        */
+  uint8_t per_level;       /* 1: level_interp / level_order override       */
+  uint8_t reserved[3];
+  uint32_t radius;         /* 2..32768; codes are uint16 in [0, 2*radius)  */
+  uint32_t chunk_codes;    /* Huffman chunk, multiple of 8 in [8, 65536]   */
+  uint8_t level_interp[SZ3O_MAX_LEVELS];   /* index = level l (1..L)     */
+  uint8_t level_order[SZ3O_MAX_LEVELS][4]; /* index = level l (1..L)     */
+} sz3o_params;
+
+/* Number of points N and number of levels L = ceil(log2(max extent)). */
+int sz3o_shape(const sz3o_params* p, uint64_t* n_points, uint32_t* n_levels);
+
+/* Error bound (REL: eb * (max - min) in double).  eb_T receives the bound
+ * rounded toward zero into T (4 or 8 bytes). */
+int sz3o_error_bound(const sz3o_params* p, const void* x, double* eb_abs, void* eb_T);
+
+/* Traversal order: spatial (row-major) index of the point behind each code. */
+int sz3o_traversal(const sz3o_params* p, uint64_t* spatial, uint64_t n);
+
+/* Quantizer on one (value, prediction) pair: code in [0, 2*radius), 0 means
+ * unpredictable; *recon receives the reconstructed value (x if unpredictable). */
+int sz3o_quantize1(uint32_t dtype, const void* x, const void* pred, const void* eb_T,
+                   uint32_t radius, uint32_t* code, void* recon);
+
+/* predict_quantize over the whole field (Alg. 1 lines 2-4).
+ * codes: N uint16 in traversal order; unpred: up to N values of T;
+ * recon: N values of T (the decompressed field); eb_T: T. */
+int sz3o_quantize(const sz3o_params* p, const void* x, uint16_t* codes, void* unpred,
+                  uint64_t* n_unpred, void* recon, void* eb_T);
+
+/* recover() over the whole field: inverse of sz3o_quantize given eb_T. */
+int sz3o_recover(const sz3o_params* p, const void* eb_T, const uint16_t* codes,
+                 const void* unpred, uint64_t n_unpred, void* out);
+
+/* Histogram of n codes into 65536 uint64 bins. */
+int sz3o_histogram(const uint16_t* codes, uint64_t n, uint64_t* hist);
+
+/* Huffman code lengths (0 = unused symbol) for nsym symbols, lengths <= lmax. */
+int sz3o_huffman_lengths(const uint64_t* freq, uint32_t nsym, uint32_t lmax, uint8_t* len);
+
+/* Canonical codes from lengths. */
+int sz3o_canonical_codes(const uint8_t* len, uint32_t nsym, uint32_t* code);
+
+/* Chunked encode: chunk j covers codes [chunk*j, chunk*(j+1)).  Writes the
+ * payload words and the word count of every chunk. */
+int sz3o_huffman_encode(const uint16_t* codes, uint64_t n, const uint8_t* len,
+                        const uint32_t* code, uint32_t chunk, uint32_t* words,
+                        uint64_t cap_words, uint32_t* chunk_words, uint64_t* n_words);
+
+/* Chunked decode of n codes. */
+int sz3o_huffman_decode(const uint32_t* words, uint64_t n_words, const uint32_t* chunk_words,
+                        uint32_t chunk, const uint8_t* len, uint32_t nsym, uint16_t* codes,
+                        uint64_t n);
+
+int sz3o_compress_bound(const sz3o_params* p, uint64_t* max_bytes);
+int sz3o_compress(const sz3o_params* p, const void* x, void* out, uint64_t capacity,
+                  uint64_t* out_bytes);
+int sz3o_read_header(const void* stream, uint64_t bytes, sz3o_params* p, uint64_t* n_points);
+int sz3o_decompress(const void* stream, uint64_t bytes, void* out, uint64_t capacity);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
