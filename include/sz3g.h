@@ -1,0 +1,215 @@
+/*
+ * sz3g.h -- C ABI of the GB300 (sm_103a) implementation of the SZ3-Interp
+ * compression hot path: multilevel interpolation prediction fused with the
+ * linear-scaling quantizer, the quantization-code histogram, and chunked
+ * canonical Huffman encode / decode (SZ3 paper, arXiv 2111.02925).
+ *
+ * Conventions for every function below:
+ *  - Return value: 0 (SZ3G_OK) or a negative SZ3G_E_* status.  No function
+ *    aborts, throws or exits; a CUDA failure is reported as SZ3G_E_CUDA.
+ *  - Buffers named d_* are device pointers, h_* host pointers, owned by the
+ *    caller, never freed or kept by the library after the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Kernels run on that stream; where a function returns a value
+ *    computed on the GPU (sizes, statuses) it synchronises that stream before
+ *    returning, and says so.
+ *  - Workspace: `d_workspace` may be NULL, in which case the library takes
+ *    the scratch it needs from the stream-ordered allocator
+ *    (cudaMallocAsync / cudaFreeAsync on `stream`) and returns it before
+ *    returning.  Otherwise it must be at least sz3g_workspace_size() bytes,
+ *    256-byte aligned, and is not read before it is written.
+ *  - Data layout: a field is a dense row-major (C order) array of N = prod(dims)
+ *    values of float (SZ3G_F32) or double (SZ3G_F64), slowest axis first.
+ */
+#ifndef SZ3G_H
+#define SZ3G_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SZ3G_OK = 0,
+  SZ3G_E_INVAL = -1,          /* bad dims / eb / radius / order / chunk / pointer alignment */
+  SZ3G_E_NONFINITE = -2,      /* NaN or Inf in the input field                 */
+  SZ3G_E_ZERO_RANGE_REL = -3, /* REL bound on a field whose value range is 0   */
+  SZ3G_E_CAPACITY = -4,       /* output buffer or workspace too small          */
+  SZ3G_E_CORRUPT = -5,        /* stream fails a magic/version/length/decode check */
+  SZ3G_E_CUDA = -6,           /* a CUDA runtime call failed                    */
+  SZ3G_E_NOMEM = -7,          /* device allocation failed                      */
+  SZ3G_E_TIMEOUT = -8         /* a bounded wait inside a kernel gave up        */
+};
+
+enum { SZ3G_F32 = 0, SZ3G_F64 = 1 };
+enum { SZ3G_EB_ABS = 0, SZ3G_EB_REL = 1 };
+enum { SZ3G_LINEAR = 0, SZ3G_CUBIC = 1 };
+
+#define SZ3G_MAX_LEVELS 32
+#define SZ3G_LMAX 24        /* longest Huffman code in a stream            */
+#define SZ3G_HEADER_BYTES 288
+
+/*
+ * Compression parameters (the paper's Config<T,N>, Appendix A.1 / Alg. 1
+ * input `conf`).  232 bytes, 8-byte aligned, no implicit padding.
+ *   dims        extents, slowest first, entries >= ndim ignored; every extent
+ *               >= 1 and N = prod(dims) <= 2^31.
+ *   eb_mode/eb  ABS: eb is the absolute bound.  REL: the bound is eb times the
+ *               value range max - min (Sec. 6.2, throughput figure caption).
+ *   interp      SZ3G_LINEAR or SZ3G_CUBIC (Sec. 6.2, SZ3-Interp).
+ *   dim_order   permutation of 0..ndim-1: the order in which a level refines
+ *               the axes.
+ *   per_level   1: level l (1..L, L = ceil(log2 max dim)) uses
+ *               level_interp[l] / level_order[l] instead.
+ *   radius      quantization radius r in [2, 32768]: codes are uint16 in
+ *               [0, 2r), 0 marks an unpredictable value (Sec. 3.2 Quantizer).
+ *   chunk_codes Huffman chunk length, a multiple of 8 in [8, 65536]; every
+ *               chunk starts on a fresh 32-bit word so chunks decode in parallel.
+ */
+typedef struct sz3g_params {
+  uint32_t dtype;
+  uint32_t ndim;
+  uint64_t dims[4];
+  uint32_t eb_mode;
+  uint32_t interp;
+  double eb;
+  uint8_t dim_order[4];
+  uint8_t per_level;
+  uint8_t reserved[3];
+  uint32_t radius;
+  uint32_t chunk_codes;
+  uint8_t level_interp[SZ3G_MAX_LEVELS];
+  uint8_t level_order[SZ3G_MAX_LEVELS][4];
+} sz3g_params;
+
+/* Human-readable text of a status code (static storage). */
+const char* sz3g_strerror(int status);
+
+/* Largest stream sz3g_compress can write for these parameters (header +
+ * every value unpredictable + longest codes).  No GPU work. */
+int sz3g_compress_bound(const sz3g_params* p, size_t* max_bytes);
+
+/* Scratch bytes sz3g_compress (for_decompress = 0) or sz3g_decompress
+ * (for_decompress = 1) needs for these parameters.  No GPU work. */
+int sz3g_workspace_size(const sz3g_params* p, int for_decompress, size_t* bytes);
+
+/*
+ * Compress one field: Alg. 1 of the paper without its preprocessor and
+ * lossless stages -- predict (multilevel interpolation, Sec. 6.2) and quantize
+ * (linear-scaling quantizer, Sec. 3.2) every point, save the unpredictable
+ * values, histogram the codes, build a Huffman code from the histogram and
+ * encode the codes (Sec. 3.2 Encoder), chunk by chunk.
+ *   d_in         N values of T (device, 8-byte aligned), not modified.
+ *   d_out        device buffer of out_capacity bytes (>= sz3g_compress_bound
+ *                is always enough), 8-byte aligned.  Receives the stream.
+ *   out_bytes    host; receives the stream length.  This needs the result of
+ *                the GPU work, so the call synchronises `stream` before return.
+ * Errors: SZ3G_E_INVAL, SZ3G_E_NONFINITE, SZ3G_E_ZERO_RANGE_REL,
+ * SZ3G_E_CAPACITY (the stream did not fit; d_out contents undefined),
+ * SZ3G_E_TIMEOUT, SZ3G_E_CUDA, SZ3G_E_NOMEM.
+ */
+int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t out_capacity,
+                  size_t* out_bytes, void* d_workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Parse and validate a stream header.  `stream` is a host pointer
+ * (stream_on_device = 0) or a device pointer (1: the 288 header bytes are
+ * copied to the host with a synchronous cudaMemcpy).  Fills *p and the point
+ * count.  Errors: SZ3G_E_CORRUPT, SZ3G_E_INVAL (NULL pointers), SZ3G_E_CUDA.
+ */
+int sz3g_read_header(const void* stream, size_t bytes, int stream_on_device, sz3g_params* p,
+                     uint64_t* n_points);
+
+/*
+ * Decompress one stream: decode the chunks, then recover every point in the
+ * traversal order of the compressor (recover(), Sec. 3.2; decode(), Sec. 3.2
+ * Encoder).
+ *   d_stream     device, `bytes` long, 8-byte aligned.
+ *   d_out        device, out_capacity >= N * sizeof(T) bytes, 8-byte aligned.
+ * Reads the header to the host first (synchronous) and synchronises `stream`
+ * at the end to report decode errors.
+ * Errors: SZ3G_E_CORRUPT, SZ3G_E_CAPACITY, SZ3G_E_INVAL, SZ3G_E_TIMEOUT,
+ * SZ3G_E_CUDA, SZ3G_E_NOMEM.
+ */
+int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_capacity,
+                    void* d_workspace, size_t ws_bytes, void* stream);
+
+/*
+ * End-to-end forms on HOST buffers: copy h_in to the device, compress, copy
+ * the stream back (and the reverse for decompress), all on `stream`, with
+ * device memory from the stream-ordered allocator.  h_* may be pageable or
+ * pinned; pinned memory makes the copies asynchronous and faster.
+ * Same errors as the device forms.
+ */
+int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size_t out_capacity,
+                       size_t* out_bytes, void* stream);
+int sz3g_decompress_host(const void* h_stream, size_t bytes, void* h_out, size_t out_capacity,
+                         void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Stage entry points: the steps of the hot path one at a time, with their
+ * intermediate results exposed (used to check each step on its own).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * predict_quantize (Appendix A.7, Alg. 1 lines 2-4) over the whole field.
+ *   d_codes   N uint16 codes in traversal order (0 = unpredictable).
+ *   d_unpred  up to N values of T: the unpredictable values in traversal
+ *             order (Sec. 3.2 Quantizer save()).
+ *   d_hist    65536 uint32 bins: histogram of d_codes.
+ *   h_n_unpred, h_ebT (host, 8 bytes: the bound rounded into T, as its T
+ *             bits) are written after a stream synchronisation.
+ */
+int sz3g_predict_quantize(const sz3g_params* p, const void* d_in, uint16_t* d_codes, void* d_unpred,
+                          uint32_t* d_hist, uint64_t* h_n_unpred, void* h_ebT, void* d_workspace,
+                          size_t ws_bytes, void* stream);
+
+/*
+ * recover() (Sec. 3.2) over the whole field: inverse of sz3g_predict_quantize.
+ *   h_ebT     host, the T value of the bound.  d_codes / d_unpred as above.
+ *   d_out     N values of T.
+ * Errors: SZ3G_E_CORRUPT when a code is outside [0, 2r) or the number of zero
+ * codes differs from n_unpred (after a stream synchronisation).
+ */
+int sz3g_recover(const sz3g_params* p, const void* h_ebT, const uint16_t* d_codes,
+                 const void* d_unpred, uint64_t n_unpred, void* d_out, void* d_workspace,
+                 size_t ws_bytes, void* stream);
+
+/*
+ * Huffman code lengths from a histogram (Sec. 3.2 Encoder: tree built
+ * greedily from frequencies): d_hist 65536 uint32 bins -> d_len 65536 uint8
+ * (0 = unused), every length <= SZ3G_LMAX.  d_code receives the canonical
+ * codewords (uint32, right-aligned).  One CTA; synchronises `stream` to
+ * report errors.
+ */
+int sz3g_huffman_build(const uint32_t* d_hist, uint32_t nsym, uint8_t* d_len, uint32_t* d_code,
+                       void* stream);
+
+/*
+ * Chunked Huffman encode of n codes with the lengths / codewords above.
+ * Chunk j covers codes [chunk*j, chunk*(j+1)); it starts on a fresh word,
+ * bits most significant first, tail zero.
+ *   d_words        payload capacity cap_words uint32.
+ *   d_chunk_words  ceil(n/chunk) uint32: words of every chunk.
+ *   h_n_words      host, total words (after a stream synchronisation).
+ */
+int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_len,
+                        const uint32_t* d_code, uint32_t nsym, uint32_t chunk, uint32_t* d_words,
+                        uint64_t cap_words, uint32_t* d_chunk_words, uint64_t* h_n_words,
+                        void* stream);
+
+/*
+ * Chunked Huffman decode of n codes (Sec. 3.2 Encoder decode()).  d_len are
+ * the code lengths of nsym symbols.  SZ3G_E_CORRUPT when a chunk runs out of
+ * bits or holds a bit pattern that is no codeword (after a synchronisation).
+ */
+int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_t* d_chunk_words,
+                        uint32_t chunk, const uint8_t* d_len, uint32_t nsym, uint16_t* d_codes,
+                        uint64_t n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

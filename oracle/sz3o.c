@@ -73,7 +73,7 @@ static int geom_of(const sz3o_params* p, walk_geom* g) {
     if (p->dims[d] < 1 || p->dims[d] > ((uint64_t)1 << 31)) return SZ3O_E_INVAL;
     g->n[d] = p->dims[d];
     if (g->n[d] > maxn) maxn = g->n[d];
-    if (g->N > (((uint64_t)1 << 40) / g->n[d])) return SZ3O_E_INVAL;
+    if (g->N > (((uint64_t)1 << 31) / g->n[d])) return SZ3O_E_INVAL; /* N <= 2^31 */
     g->N *= g->n[d];
   }
   for (d = p->ndim; d < 4; ++d) g->n[d] = 1;

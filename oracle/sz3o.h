@@ -64,7 +64,8 @@ enum { SZ3O_LINEAR = 0, SZ3O_CUBIC = 1 };
 typedef struct sz3o_params {
   uint32_t dtype;          /* SZ3O_F32 / SZ3O_F64                          */
   uint32_t ndim;           /* 1..4                                         */
-  uint64_t dims[4];        /* extents, slowest axis first; unused = 1      */
+  uint64_t dims[4];        /* extents, slowest axis first; unused = 1;
+                              the product N must be in [1, 2^31]           */
   uint32_t eb_mode;        /* SZ3O_EB_ABS / SZ3O_EB_REL                    */
   uint32_t interp;         /* SZ3O_LINEAR / SZ3O_CUBIC (all levels)        */
   double eb;               /* > 0; REL: fraction of (max - min)            */

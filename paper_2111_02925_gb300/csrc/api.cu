@@ -1,0 +1,518 @@
+// api.cu -- the extern "C" entry points declared in include/sz3g.h: argument
+// checks, workspace layout, the launch sequence of compress / decompress and
+// the stage entry points, and the mapping of device status bits to statuses.
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace sz3g {
+
+// Launchers defined in k_huffman.cu that are used only here.
+int launch_encode(const Plan& pl, const uint16_t* codes, const uint32_t* table, const void* d_in,
+                  const PassMap* map, unsigned long long* wstat, unsigned long long* zstat, DevState* st,
+                  unsigned char* d_out, unsigned long long out_capacity, int mode, uint32_t* words_out,
+                  uint32_t* chunk_words_out, unsigned long long cap_words, cudaStream_t s);
+int launch_compact_unpred(const Plan& pl, const uint16_t* codes, const void* d_in, const PassMap* map,
+                          unsigned long long* wstat, unsigned long long* zstat, const uint32_t* table,
+                          void* d_unpred, DevState* st, cudaStream_t s);
+int launch_decode_tables(const unsigned char* tab, uint32_t n_used, const uint8_t* len, uint32_t nsym,
+                         void* tables, DevState* st, cudaStream_t s);
+int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, const uint32_t* chunk_words,
+                         unsigned long long n_chunks, uint32_t chunk, unsigned long long n, const void* tables,
+                         unsigned long long* woff, uint16_t* codes, uint32_t* zchunk, uint32_t* zsub,
+                         uint32_t nsub, DevState* st, cudaStream_t s);
+int launch_zero_counts(const uint16_t* codes, unsigned long long n, uint32_t chunk, uint32_t nsub,
+                       unsigned long long n_chunks, uint32_t* zchunk, uint32_t* zsub, cudaStream_t s);
+int launch_scan_u32(const uint32_t* in, unsigned long long n, unsigned long long* out, unsigned long long* total,
+                    unsigned long long expect, int check_expect, DevState* st, cudaStream_t s);
+int launch_pack_table(const uint8_t* len, const uint32_t* code, uint32_t nsym, uint32_t* table, cudaStream_t s);
+size_t dec_tables_bytes();
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+inline size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// Bump layout of a workspace.
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += up(bytes);
+    return o;
+  }
+};
+
+struct CompressWs {
+  size_t st, hist, table, range, cb, wstat, zstat, codes, R[34], total;
+};
+
+CompressWs compress_layout(const Plan& pl) {
+  CompressWs w{};
+  Layout l;
+  w.st = l.take(sizeof(DevState));
+  w.hist = l.take(kSyms * 4);
+  w.table = l.take(kSyms * 4);
+  w.range = l.take(range_scratch_bytes(pl));
+  w.cb = l.take(codebook_scratch_bytes());
+  w.wstat = l.take(pl.n_chunks * 8);
+  w.zstat = l.take(pl.n_chunks * 8);
+  w.codes = l.take(pl.N * 2);
+  for (int k = 0; k <= pl.L; ++k) w.R[k] = l.take(pl.gsize[k] * pl.esz);
+  w.total = l.off;
+  return w;
+}
+
+struct DecompressWs {
+  size_t st, tables, woff, zchunk, zsub, zbase, codes, R[34], total;
+};
+
+DecompressWs decompress_layout(const Plan& pl) {
+  DecompressWs w{};
+  Layout l;
+  w.st = l.take(sizeof(DevState));
+  w.tables = l.take(dec_tables_bytes());
+  w.woff = l.take(pl.n_chunks * 8);
+  w.zchunk = l.take(pl.n_chunks * 4);
+  w.zsub = l.take(pl.n_chunks * pl.nsub * 4);
+  w.zbase = l.take(pl.n_chunks * 8);
+  w.codes = l.take(pl.N * 2);
+  for (int k = 1; k <= pl.L; ++k) w.R[k] = l.take(pl.gsize[k] * pl.esz);
+  w.R[0] = 0;
+  w.total = l.off;
+  return w;
+}
+
+// Workspace owned for the duration of one call when the caller passes none.
+struct Scratch {
+  void* ptr = nullptr;
+  cudaStream_t s = nullptr;
+  ~Scratch() {
+    if (ptr) cudaFreeAsync(ptr, s);
+  }
+};
+
+int get_ws(void* user, size_t user_bytes, size_t need, cudaStream_t s, Scratch& own, unsigned char** base) {
+  if (user) {
+    if (user_bytes < need) return SZ3G_E_CAPACITY;
+    if ((uintptr_t)user % kAlign) return SZ3G_E_INVAL;
+    *base = (unsigned char*)user;
+    return SZ3G_OK;
+  }
+  own.s = s;
+  if (cudaMallocAsync(&own.ptr, need ? need : kAlign, s) != cudaSuccess) {
+    cudaGetLastError();
+    own.ptr = nullptr;
+    return SZ3G_E_NOMEM;
+  }
+  *base = (unsigned char*)own.ptr;
+  return SZ3G_OK;
+}
+
+int status_of(uint32_t f) {
+  if (f & kFlagBadBound) return SZ3G_E_INVAL;
+  if (f & kFlagNonFinite) return SZ3G_E_NONFINITE;
+  if (f & kFlagZeroRange) return SZ3G_E_ZERO_RANGE_REL;
+  if (f & kFlagCapacity) return SZ3G_E_CAPACITY;
+  if (f & kFlagTimeout) return SZ3G_E_TIMEOUT;
+  if (f & kFlagCorrupt) return SZ3G_E_CORRUPT;
+  return SZ3G_OK;
+}
+
+int read_state(const DevState* d, DevState* h, cudaStream_t s) {
+  if (cudaMemcpyAsync(h, d, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SZ3G_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SZ3G_E_CUDA;
+  return SZ3G_OK;
+}
+
+#define SZ3G_TRY(x)                 \
+  do {                              \
+    int _rc = (x);                  \
+    if (_rc != SZ3G_OK) return _rc; \
+  } while (0)
+#define SZ3G_CUDA(x)                              \
+  do {                                            \
+    if ((x) != cudaSuccess) {                     \
+      cudaGetLastError();                         \
+      return SZ3G_E_CUDA;                         \
+    }                                             \
+  } while (0)
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// ---- stream header parse (host) -------------------------------------------
+uint64_t get_le(const unsigned char* b, int n) {
+  uint64_t v = 0;
+  for (int i = n - 1; i >= 0; --i) v = (v << 8) | b[i];
+  return v;
+}
+
+struct Header {
+  sz3g_params p;
+  Plan plan;
+  unsigned long long n_unpred, n_words, ebT_bits;
+  uint32_t n_used;
+  unsigned long long off_table, off_chunks, off_payload, end;
+};
+
+int parse_header(const unsigned char* s, size_t bytes, Header* h) {
+  std::memset(h, 0, sizeof(*h));
+  if (bytes < SZ3G_HEADER_BYTES) return SZ3G_E_CORRUPT;
+  if (s[0] != 'S' || s[1] != 'Z' || s[2] != '3' || s[3] != 'G') return SZ3G_E_CORRUPT;
+  if (get_le(s + 4, 2) != 1) return SZ3G_E_CORRUPT;
+  sz3g_params& p = h->p;
+  p.dtype = s[6];
+  p.ndim = s[7];
+  if (p.ndim < 1 || p.ndim > 4) return SZ3G_E_CORRUPT;
+  for (int i = 0; i < 4; ++i) p.dims[i] = get_le(s + 8 + 8 * i, 8);
+  p.eb_mode = s[40];
+  p.interp = s[41];
+  p.per_level = s[42];
+  p.radius = (uint32_t)get_le(s + 44, 4);
+  uint64_t ebb = get_le(s + 48, 8);
+  std::memcpy(&p.eb, &ebb, 8);
+  p.chunk_codes = (uint32_t)get_le(s + 72, 4);
+  for (int l = 0; l < SZ3G_MAX_LEVELS; ++l) {
+    p.level_interp[l] = s[112 + l];
+    for (int i = 0; i < 4; ++i) p.level_order[l][i] = s[144 + 4 * l + i];
+  }
+  for (int i = 0; i < 4; ++i) p.dim_order[i] = s[272 + i];
+  if (make_plan(&p, &h->plan) != SZ3G_OK) return SZ3G_E_CORRUPT;
+  const Plan& pl = h->plan;
+  if ((int)s[43] != pl.L) return SZ3G_E_CORRUPT;
+  h->ebT_bits = get_le(s + 64, 8);
+  if (pl.esz == 4) {
+    if (h->ebT_bits >> 32) return SZ3G_E_CORRUPT;
+    float e;
+    uint32_t u = (uint32_t)h->ebT_bits;
+    std::memcpy(&e, &u, 4);
+    if (!std::isnormal(e) || !(e > 0) || !std::isnormal(1.0f / e)) return SZ3G_E_CORRUPT;
+  } else {
+    double e;
+    std::memcpy(&e, &h->ebT_bits, 8);
+    if (!std::isnormal(e) || !(e > 0) || !std::isnormal(1.0 / e)) return SZ3G_E_CORRUPT;
+  }
+  h->n_used = (uint32_t)get_le(s + 76, 4);
+  if (get_le(s + 80, 8) != pl.N) return SZ3G_E_CORRUPT;
+  h->n_unpred = get_le(s + 88, 8);
+  const unsigned long long nch = get_le(s + 96, 8);
+  h->n_words = get_le(s + 104, 8);
+  if (h->n_unpred > pl.N || nch != pl.n_chunks) return SZ3G_E_CORRUPT;
+  if (h->n_used < 1 || h->n_used > 2 * pl.radius) return SZ3G_E_CORRUPT;
+  if (h->n_words > pl.n_chunks * (((unsigned long long)pl.chunk * SZ3G_LMAX + 31) / 32)) return SZ3G_E_CORRUPT;
+  h->off_table = SZ3G_HEADER_BYTES + pad8(h->n_unpred * pl.esz);
+  h->off_chunks = h->off_table + pad8(3ull * h->n_used);
+  h->off_payload = h->off_chunks + pad8(pl.n_chunks * 4);
+  h->end = h->off_payload + pad8(h->n_words * 4);
+  if (h->end > bytes) return SZ3G_E_CORRUPT;
+  return SZ3G_OK;
+}
+
+}  // namespace
+}  // namespace sz3g
+
+using namespace sz3g;
+
+extern "C" {
+
+const char* sz3g_strerror(int status) {
+  switch (status) {
+    case SZ3G_OK: return "ok";
+    case SZ3G_E_INVAL: return "invalid argument (dims, error bound, radius, order, chunk or alignment)";
+    case SZ3G_E_NONFINITE: return "input field holds NaN or Inf";
+    case SZ3G_E_ZERO_RANGE_REL: return "relative error bound on a field whose value range is zero";
+    case SZ3G_E_CAPACITY: return "output buffer or workspace too small";
+    case SZ3G_E_CORRUPT: return "stream is corrupt or truncated";
+    case SZ3G_E_CUDA: return "a CUDA runtime call failed";
+    case SZ3G_E_NOMEM: return "device allocation failed";
+    case SZ3G_E_TIMEOUT: return "a bounded wait inside a kernel gave up";
+    default: return "unknown status";
+  }
+}
+
+int sz3g_compress_bound(const sz3g_params* p, size_t* max_bytes) {
+  Plan pl;
+  SZ3G_TRY(make_plan(p, &pl));
+  if (!max_bytes) return SZ3G_E_INVAL;
+  const unsigned long long maxw = ((unsigned long long)pl.chunk * SZ3G_LMAX + 31) / 32;
+  *max_bytes = SZ3G_HEADER_BYTES + pad8(pl.N * pl.esz) + pad8(2ull * pl.radius * 3) + pad8(pl.n_chunks * 4) +
+               pad8(pl.n_chunks * maxw * 4);
+  return SZ3G_OK;
+}
+
+int sz3g_workspace_size(const sz3g_params* p, int for_decompress, size_t* bytes) {
+  Plan pl;
+  SZ3G_TRY(make_plan(p, &pl));
+  if (!bytes) return SZ3G_E_INVAL;
+  *bytes = for_decompress ? decompress_layout(pl).total : compress_layout(pl).total;
+  return SZ3G_OK;
+}
+
+int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t out_capacity, size_t* out_bytes,
+                  void* d_workspace, size_t ws_bytes, void* stream) {
+  Plan pl;
+  SZ3G_TRY(make_plan(p, &pl));
+  if (!d_in || !d_out || !out_bytes || !aligned(d_in, 16) || !aligned(d_out, 16)) return SZ3G_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const CompressWs L = compress_layout(pl);
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
+  DevState* st = (DevState*)(ws + L.st);
+  SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.codes, s));  // state, histogram, tables, look-back status
+  SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s));
+  void* R[34];
+  for (int k = 0; k <= pl.L; ++k) R[k] = ws + L.R[k];
+  uint16_t* codes = (uint16_t*)(ws + L.codes);
+  uint32_t* hist = (uint32_t*)(ws + L.hist);
+  uint32_t* table = (uint32_t*)(ws + L.table);
+  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, s));
+  SZ3G_TRY(launch_codebook(hist, 2 * pl.radius, table, nullptr, nullptr, st, ws + L.cb, (unsigned char*)d_out,
+                           out_capacity, pl.esz, s));
+  PassMap map;  // kernel parameter, copied at launch
+  make_pass_map(pl, &map);
+  SZ3G_TRY(launch_encode(pl, codes, table, d_in, &map, (unsigned long long*)(ws + L.wstat),
+                         (unsigned long long*)(ws + L.zstat), st, (unsigned char*)d_out, out_capacity,
+                         kEncodeStream, nullptr, nullptr, 0, s));
+  SZ3G_TRY(launch_finalize(pl, p, st, (unsigned char*)d_out, out_capacity, s));
+  DevState h;
+  SZ3G_TRY(read_state(st, &h, s));
+  SZ3G_TRY(status_of(h.flags));
+  *out_bytes = (size_t)h.out_bytes;
+  return SZ3G_OK;
+}
+
+int sz3g_read_header(const void* stream, size_t bytes, int stream_on_device, sz3g_params* p, uint64_t* n_points) {
+  if (!stream || !p) return SZ3G_E_INVAL;
+  unsigned char hb[SZ3G_HEADER_BYTES];
+  if (bytes < SZ3G_HEADER_BYTES) return SZ3G_E_CORRUPT;
+  if (stream_on_device) {
+    SZ3G_CUDA(cudaMemcpy(hb, stream, SZ3G_HEADER_BYTES, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(hb, stream, SZ3G_HEADER_BYTES);
+  }
+  Header h;
+  SZ3G_TRY(parse_header(hb, bytes, &h));
+  *p = h.p;
+  if (n_points) *n_points = h.plan.N;
+  return SZ3G_OK;
+}
+
+int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_capacity, void* d_workspace,
+                    size_t ws_bytes, void* stream) {
+  if (!d_stream || !d_out || !aligned(d_stream, 16) || !aligned(d_out, 16)) return SZ3G_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char hb[SZ3G_HEADER_BYTES];
+  if (bytes < SZ3G_HEADER_BYTES) return SZ3G_E_CORRUPT;
+  SZ3G_CUDA(cudaMemcpyAsync(hb, d_stream, SZ3G_HEADER_BYTES, cudaMemcpyDeviceToHost, s));
+  SZ3G_CUDA(cudaStreamSynchronize(s));
+  Header h;
+  SZ3G_TRY(parse_header(hb, bytes, &h));
+  const Plan& pl = h.plan;
+  if (out_capacity < pl.N * pl.esz) return SZ3G_E_CAPACITY;
+  const DecompressWs L = decompress_layout(pl);
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
+  DevState* st = (DevState*)(ws + L.st);
+  SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+  const unsigned char* base = (const unsigned char*)d_stream;
+  SZ3G_TRY(launch_decode_tables(base + h.off_table, h.n_used, nullptr, 2 * pl.radius, ws + L.tables, st, s));
+  uint16_t* codes = (uint16_t*)(ws + L.codes);
+  SZ3G_TRY(launch_decode_chunks((const uint32_t*)(base + h.off_payload), h.n_words,
+                                (const uint32_t*)(base + h.off_chunks), pl.n_chunks, pl.chunk, pl.N, ws + L.tables,
+                                (unsigned long long*)(ws + L.woff), codes, (uint32_t*)(ws + L.zchunk),
+                                (uint32_t*)(ws + L.zsub), pl.nsub, st, s));
+  SZ3G_TRY(launch_scan_u32((uint32_t*)(ws + L.zchunk), pl.n_chunks, (unsigned long long*)(ws + L.zbase), nullptr,
+                           h.n_unpred, 1, st, s));
+  void* R[34];
+  for (int k = 0; k <= pl.L; ++k) R[k] = k == 0 ? d_out : ws + L.R[k];
+  SZ3G_TRY(launch_recover_levels(pl, codes, base + SZ3G_HEADER_BYTES, h.n_unpred,
+                                 (unsigned long long*)(ws + L.zbase), (uint32_t*)(ws + L.zsub), R, d_out, st,
+                                 h.ebT_bits, s));
+  DevState hs;
+  SZ3G_TRY(read_state(st, &hs, s));
+  return status_of(hs.flags);
+}
+
+int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size_t out_capacity, size_t* out_bytes,
+                       void* stream) {
+  Plan pl;
+  SZ3G_TRY(make_plan(p, &pl));
+  if (!h_in || !h_out || !out_bytes) return SZ3G_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t bound;
+  SZ3G_TRY(sz3g_compress_bound(p, &bound));
+  Scratch din, dout;
+  din.s = dout.s = s;
+  if (cudaMallocAsync(&din.ptr, pl.N * pl.esz, s) != cudaSuccess ||
+      cudaMallocAsync(&dout.ptr, bound, s) != cudaSuccess) {
+    cudaGetLastError();
+    return SZ3G_E_NOMEM;
+  }
+  SZ3G_CUDA(cudaMemcpyAsync(din.ptr, h_in, pl.N * pl.esz, cudaMemcpyHostToDevice, s));
+  size_t nb = 0;
+  SZ3G_TRY(sz3g_compress(p, din.ptr, dout.ptr, bound, &nb, nullptr, 0, stream));
+  if (nb > out_capacity) return SZ3G_E_CAPACITY;
+  SZ3G_CUDA(cudaMemcpyAsync(h_out, dout.ptr, nb, cudaMemcpyDeviceToHost, s));
+  SZ3G_CUDA(cudaStreamSynchronize(s));
+  *out_bytes = nb;
+  return SZ3G_OK;
+}
+
+int sz3g_decompress_host(const void* h_stream, size_t bytes, void* h_out, size_t out_capacity, void* stream) {
+  if (!h_stream || !h_out) return SZ3G_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  sz3g_params p;
+  uint64_t n;
+  SZ3G_TRY(sz3g_read_header(h_stream, bytes, 0, &p, &n));
+  const size_t esz = p.dtype == SZ3G_F32 ? 4 : 8;
+  if (out_capacity < n * esz) return SZ3G_E_CAPACITY;
+  Scratch dst, dout;
+  dst.s = dout.s = s;
+  if (cudaMallocAsync(&dst.ptr, bytes, s) != cudaSuccess || cudaMallocAsync(&dout.ptr, n * esz, s) != cudaSuccess) {
+    cudaGetLastError();
+    return SZ3G_E_NOMEM;
+  }
+  SZ3G_CUDA(cudaMemcpyAsync(dst.ptr, h_stream, bytes, cudaMemcpyHostToDevice, s));
+  SZ3G_TRY(sz3g_decompress(dst.ptr, bytes, dout.ptr, n * esz, nullptr, 0, stream));
+  SZ3G_CUDA(cudaMemcpyAsync(h_out, dout.ptr, n * esz, cudaMemcpyDeviceToHost, s));
+  SZ3G_CUDA(cudaStreamSynchronize(s));
+  return SZ3G_OK;
+}
+
+int sz3g_predict_quantize(const sz3g_params* p, const void* d_in, uint16_t* d_codes, void* d_unpred,
+                          uint32_t* d_hist, uint64_t* h_n_unpred, void* h_ebT, void* d_workspace, size_t ws_bytes,
+                          void* stream) {
+  Plan pl;
+  SZ3G_TRY(make_plan(p, &pl));
+  if (!d_in || !d_codes || !d_unpred || !d_hist || !aligned(d_in, 16) || !aligned(d_codes, 16)) return SZ3G_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const CompressWs L = compress_layout(pl);
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
+  DevState* st = (DevState*)(ws + L.st);
+  SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.codes, s));
+  SZ3G_CUDA(cudaMemsetAsync(d_hist, 0, kSyms * 4, s));
+  SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s));
+  void* R[34];
+  for (int k = 0; k <= pl.L; ++k) R[k] = ws + L.R[k];
+  SZ3G_TRY(launch_quantize_levels(pl, d_in, d_codes, R, d_hist, st, s));
+  PassMap map;
+  make_pass_map(pl, &map);
+  SZ3G_TRY(launch_compact_unpred(pl, d_codes, d_in, &map, (unsigned long long*)(ws + L.wstat),
+                                 (unsigned long long*)(ws + L.zstat), (uint32_t*)(ws + L.table), d_unpred, st, s));
+  DevState h;
+  SZ3G_TRY(read_state(st, &h, s));
+  SZ3G_TRY(status_of(h.flags));
+  if (h_n_unpred) *h_n_unpred = h.n_unpred;
+  if (h_ebT) std::memcpy(h_ebT, &h.ebT_bits, 8);
+  return SZ3G_OK;
+}
+
+int sz3g_recover(const sz3g_params* p, const void* h_ebT, const uint16_t* d_codes, const void* d_unpred,
+                 uint64_t n_unpred, void* d_out, void* d_workspace, size_t ws_bytes, void* stream) {
+  Plan pl;
+  SZ3G_TRY(make_plan(p, &pl));
+  if (!h_ebT || !d_codes || !d_out || (n_unpred && !d_unpred) || !aligned(d_codes, 16)) return SZ3G_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const DecompressWs L = decompress_layout(pl);
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
+  DevState* st = (DevState*)(ws + L.st);
+  SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+  SZ3G_TRY(launch_zero_counts(d_codes, pl.N, pl.chunk, pl.nsub, pl.n_chunks, (uint32_t*)(ws + L.zchunk),
+                              (uint32_t*)(ws + L.zsub), s));
+  SZ3G_TRY(launch_scan_u32((uint32_t*)(ws + L.zchunk), pl.n_chunks, (unsigned long long*)(ws + L.zbase), nullptr,
+                           n_unpred, 1, st, s));
+  unsigned long long eb_bits = 0;
+  std::memcpy(&eb_bits, h_ebT, pl.esz);
+  void* R[34];
+  for (int k = 0; k <= pl.L; ++k) R[k] = k == 0 ? d_out : ws + L.R[k];
+  SZ3G_TRY(launch_recover_levels(pl, d_codes, d_unpred, n_unpred, (unsigned long long*)(ws + L.zbase),
+                                 (uint32_t*)(ws + L.zsub), R, d_out, st, eb_bits, s));
+  DevState h;
+  SZ3G_TRY(read_state(st, &h, s));
+  return status_of(h.flags);
+}
+
+int sz3g_huffman_build(const uint32_t* d_hist, uint32_t nsym, uint8_t* d_len, uint32_t* d_code, void* stream) {
+  if (!d_hist || !d_len || !d_code || nsym < 1 || nsym > (uint32_t)kSyms) return SZ3G_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Layout l;
+  const size_t o_st = l.take(sizeof(DevState)), o_tab = l.take(kSyms * 4), o_cb = l.take(codebook_scratch_bytes());
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(nullptr, 0, l.off, s, own, &ws));
+  DevState* st = (DevState*)(ws + o_st);
+  SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+  SZ3G_TRY(launch_codebook(d_hist, nsym, (uint32_t*)(ws + o_tab), d_len, d_code, st, ws + o_cb, nullptr, 0, 4, s));
+  DevState h;
+  SZ3G_TRY(read_state(st, &h, s));
+  return status_of(h.flags);
+}
+
+int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_len, const uint32_t* d_code,
+                        uint32_t nsym, uint32_t chunk, uint32_t* d_words, uint64_t cap_words,
+                        uint32_t* d_chunk_words, uint64_t* h_n_words, void* stream) {
+  if (!d_codes || !d_len || !d_code || !d_words || !d_chunk_words || n < 1 || nsym < 1 || nsym > (uint32_t)kSyms ||
+      chunk < 8 || chunk > 65536 || chunk % 8 || !aligned(d_codes, 16))
+    return SZ3G_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Plan pl;
+  std::memset(&pl, 0, sizeof(pl));
+  pl.N = n;
+  pl.chunk = chunk;
+  pl.n_chunks = (n + chunk - 1) / chunk;
+  pl.esz = 4;
+  Layout l;
+  const size_t o_st = l.take(sizeof(DevState)), o_tab = l.take(kSyms * 4), o_w = l.take(pl.n_chunks * 8),
+               o_z = l.take(pl.n_chunks * 8);
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(nullptr, 0, l.off, s, own, &ws));
+  DevState* st = (DevState*)(ws + o_st);
+  SZ3G_CUDA(cudaMemsetAsync(ws, 0, l.off, s));
+  SZ3G_TRY(launch_pack_table(d_len, d_code, nsym, (uint32_t*)(ws + o_tab), s));
+  PassMap map;  // unused in this mode
+  std::memset(&map, 0, sizeof(map));
+  map.n = 1;
+  for (int d = 0; d < 4; ++d) map.e[0].E[d] = 1;
+  SZ3G_TRY(launch_encode(pl, d_codes, (uint32_t*)(ws + o_tab), nullptr, &map, (unsigned long long*)(ws + o_w),
+                         (unsigned long long*)(ws + o_z), st, nullptr, 0, kEncodeRaw, d_words, d_chunk_words,
+                         cap_words, s));
+  DevState h;
+  SZ3G_TRY(read_state(st, &h, s));
+  SZ3G_TRY(status_of(h.flags));
+  if (h_n_words) *h_n_words = h.n_words;
+  return SZ3G_OK;
+}
+
+int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_t* d_chunk_words, uint32_t chunk,
+                        const uint8_t* d_len, uint32_t nsym, uint16_t* d_codes, uint64_t n, void* stream) {
+  if (!d_words || !d_chunk_words || !d_len || !d_codes || n < 1 || nsym < 1 || nsym > (uint32_t)kSyms || chunk < 8 ||
+      chunk > 65536 || chunk % 8 || !aligned(d_codes, 16))
+    return SZ3G_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned long long nch = (n + chunk - 1) / chunk, nsub = (chunk + 255) / 256;
+  Layout l;
+  const size_t o_st = l.take(sizeof(DevState)), o_t = l.take(dec_tables_bytes()), o_wo = l.take(nch * 8),
+               o_zc = l.take(nch * 4), o_zs = l.take(nch * nsub * 4);
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(nullptr, 0, l.off, s, own, &ws));
+  DevState* st = (DevState*)(ws + o_st);
+  SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+  SZ3G_TRY(launch_decode_tables(nullptr, 0, d_len, nsym, ws + o_t, st, s));
+  SZ3G_TRY(launch_decode_chunks(d_words, n_words, d_chunk_words, nch, chunk, n, ws + o_t,
+                                (unsigned long long*)(ws + o_wo), d_codes, (uint32_t*)(ws + o_zc),
+                                (uint32_t*)(ws + o_zs), (uint32_t)nsub, st, s));
+  DevState h;
+  SZ3G_TRY(read_state(st, &h, s));
+  return status_of(h.flags);
+}
+
+}  // extern "C"

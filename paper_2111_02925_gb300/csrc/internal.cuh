@@ -1,0 +1,221 @@
+// internal.cuh -- shared definitions of the sm_103a implementation (not part of
+// the public ABI).  Every floating-point step of the prediction and of the
+// quantizer is one IEEE round-to-nearest-even operation in the field type T;
+// the library is compiled with -fmad=false so no multiply-add is contracted.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sz3g.h"
+
+namespace sz3g {
+
+constexpr int kMaxPasses = 1 + 4 * 31;  // anchor + up to 4 passes on each of 31 levels
+constexpr int kSyms = 65536;            // alphabet of uint16 codes
+constexpr int kLutBits = 12;            // direct decode table: first 12 bits of a codeword
+
+// Status bits raised on the device and read back once per call.
+enum : uint32_t {
+  kFlagNonFinite = 1u << 0,
+  kFlagZeroRange = 1u << 1,
+  kFlagBadBound = 1u << 2,
+  kFlagCapacity = 1u << 3,
+  kFlagCorrupt = 1u << 4,
+  kFlagTimeout = 1u << 5,
+};
+
+// Small block of device state at the start of every workspace.
+struct DevState {
+  uint32_t flags;        // kFlag* bits
+  uint32_t n_used;       // symbols with a code
+  uint32_t ticket;       // dynamic chunk counter of the encoder
+  uint32_t pad0;
+  unsigned long long n_unpred;     // unpredictable values
+  unsigned long long n_words;      // payload words
+  unsigned long long out_bytes;    // stream length
+  double eb_abs;         // absolute bound (double)
+  double ebT_bits_d;     // unused padding slot
+  unsigned long long ebT_bits;     // bound rounded into T, as T bits
+  unsigned long long ebr_bits;     // fl_T(1 / eb_T), as T bits
+  unsigned long long zeros_total;  // decompress: zero codes seen by the decoder
+  unsigned long long pad[6];
+};
+static_assert(sizeof(DevState) <= 256, "DevState must fit its 256-byte slot");
+
+// One pass of the interpolation schedule on the compact grid G_k (level
+// l = k + 1): the sub-lattice of points whose coordinate on the pass axis is
+// odd, on axes refined earlier in this level any, on later axes even.
+// Coordinates are padded to 4 axes (leading unit axes).
+struct PassDesc {
+  unsigned long long off;      // code index of the pass's first point
+  unsigned long long count;    // points in the pass
+  uint32_t E[4];               // lattice extents
+  uint32_t start[4], step[4];  // grid coordinate = start + step * lattice coordinate
+  uint32_t m[4];               // extents of the grid G_k
+  unsigned long long gstride[4];  // element strides of G_k (compact, row-major)
+  unsigned long long xstride[4];  // strides in the full-resolution input for one G_k step
+  int axis;                    // pass axis 0..3
+  int interp;                  // SZ3G_LINEAR / SZ3G_CUBIC
+  int grid;                    // k
+  int pad;
+};
+
+// Inverse map code index -> input index for every pass (used by the encoder
+// to fetch unpredictable values).  Entry 0 is the anchor.
+struct PassMapEntry {
+  unsigned long long off;
+  uint32_t E[4];
+  unsigned long long xstart;      // input index of lattice coordinate 0
+  unsigned long long xls[4];      // input stride of one lattice step per axis
+};
+struct PassMap {
+  int n;
+  int pad;
+  PassMapEntry e[kMaxPasses];
+};
+
+// Host-side plan of one field.
+struct Plan {
+  int dtype;                 // SZ3G_F32 / SZ3G_F64
+  int esz;                   // 4 / 8
+  int ndim;                  // as given
+  int L;                     // levels
+  uint32_t radius, chunk;
+  unsigned long long N;
+  unsigned long long n[4];   // padded to 4 axes
+  unsigned long long fstride[4];
+  unsigned long long gm[33][4];   // extents of G_k, k = 0..L
+  unsigned long long gsize[33];   // points of G_k
+  int n_pass;                // passes excluding the anchor
+  PassDesc pass[kMaxPasses]; // in traversal order (level L first)
+  unsigned long long n_chunks;
+  uint32_t nsub;             // 256-code sub-blocks per chunk (decoder)
+};
+
+// Builds the plan; returns SZ3G_OK or SZ3G_E_INVAL.  Shared by all entry points.
+int make_plan(const sz3g_params* p, Plan* plan);
+void make_pass_map(const Plan& plan, PassMap* map);
+
+// ---------------------------------------------------------------------------
+// Device arithmetic of the method.
+// ---------------------------------------------------------------------------
+
+// Interpolation predictor (Sec. 6.2): a, b at -1 / +1 and c, d at -3 / +3 on
+// the pass axis of the compact grid; has_* say which of b, c, d exist.
+template <typename T>
+__device__ __forceinline__ T interp_predict(T a, T b, T c, T d, bool has_b, bool has_c, bool has_d,
+                                            int interp) {
+  if (interp == SZ3G_CUBIC) {
+    if (has_c && has_d) {
+      T ab = a + b;
+      T nine = T(9) * ab;
+      T cd = c + d;
+      T num = nine - cd;
+      return num * T(0.0625);
+    }
+    if (!has_c && has_d) {
+      T a3 = T(3) * a;
+      T b6 = T(6) * b;
+      T sum = a3 + b6;
+      T num = sum - d;
+      return num * T(0.125);
+    }
+    if (has_c && has_b) {
+      T a6 = T(6) * a;
+      T b3 = T(3) * b;
+      T sum = a6 + b3;
+      T num = sum - c;
+      return num * T(0.125);
+    }
+  }
+  if (has_b) {
+    T ab = a + b;
+    return ab * T(0.5);
+  }
+  if (has_c) {
+    T a15 = T(1.5) * a;
+    T c05 = T(0.5) * c;
+    return a15 - c05;
+  }
+  return a;
+}
+
+// Linear-scaling quantizer (Sec. 3.2): code radius + q with q the index of the
+// width-2*eb bin holding x - pred (half-up), or 0 when |q| would reach the
+// radius or the reconstruction misses the bound.
+template <typename T>
+__device__ __forceinline__ uint32_t quantize_point(T x, T pred, T ebT, T ebr, int radius, T& recon) {
+  T d = x - pred;
+  T ad = d < T(0) ? -d : d;
+  T t = ad * ebr;
+  T lim = T(2 * radius - 1);
+  if (!(t < lim)) {
+    recon = x;
+    return 0u;
+  }
+  int m = (int)t;
+  int h = (m + 1) >> 1;
+  int q = (d < T(0)) ? -h : h;
+  T q2 = T(2 * q);
+  T step = q2 * ebT;
+  T r = pred + step;
+  T diff = r - x;
+  T err = diff < T(0) ? -diff : diff;
+  if (!(err <= ebT)) {
+    recon = x;
+    return 0u;
+  }
+  recon = r;
+  return (uint32_t)(radius + q);
+}
+
+// recover() (Sec. 3.2): pred + 2 (code - radius) eb.
+template <typename T>
+__device__ __forceinline__ T recover_point(T pred, uint32_t code, int radius, T ebT) {
+  int q = (int)code - radius;
+  T q2 = T(2 * q);
+  T step = q2 * ebT;
+  return pred + step;
+}
+
+template <typename T>
+__device__ __forceinline__ T bits_to(unsigned long long b);
+template <>
+__device__ __forceinline__ float bits_to<float>(unsigned long long b) {
+  return __uint_as_float((uint32_t)b);
+}
+template <>
+__device__ __forceinline__ double bits_to<double>(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (host functions, defined in the .cu files).
+// ---------------------------------------------------------------------------
+// k_interp.cu
+size_t range_scratch_bytes(const Plan& pl);
+int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratch, size_t scratch_bytes,
+                    int eb_mode, double eb, cudaStream_t s);
+int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R,
+                           uint32_t* hist, DevState* st, cudaStream_t s);
+int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred,
+                          unsigned long long n_unpred, const unsigned long long* zbase, const uint32_t* zsub,
+                          void* const* R, void* d_out, DevState* st, unsigned long long ebT_bits,
+                          cudaStream_t s);
+
+// k_huffman.cu
+size_t codebook_scratch_bytes();
+int launch_codebook(const uint32_t* hist, uint32_t nsym, uint32_t* table, uint8_t* len_out,
+                    uint32_t* code_out, DevState* st, void* scratch, unsigned char* d_out,
+                    unsigned long long out_capacity, int esz, cudaStream_t s);
+int launch_finalize(const Plan& pl, const sz3g_params* p, DevState* st, unsigned char* d_out,
+                    unsigned long long out_capacity, cudaStream_t s);
+
+// Encoder modes.
+enum { kEncodeStream = 0, kEncodeRaw = 1 };
+
+__host__ __device__ __forceinline__ unsigned long long pad8(unsigned long long x) { return (x + 7) & ~7ull; }
+
+}  // namespace sz3g

@@ -1,0 +1,949 @@
+// k_huffman.cu -- the encoder module of the pipeline (SZ3 paper Sec. 3.2
+// Encoder): Huffman code lengths built greedily from the code histogram,
+// canonical codewords, chunk-parallel encode and decode, and the stream
+// sections that go with them.
+//
+//  * codebook_kernel  one CTA: used symbols sorted by (frequency, symbol),
+//    two-queue merge (leaf first on equal weight), depths by a bounded walk to
+//    the root, frequency halving while a code is longer than 24 bits, then
+//    canonical codewords ordered by (length, symbol).
+//  * encode_kernel    one warp per chunk of the code stream: chunk bit count,
+//    decoupled look-back over the chunks for the payload word offset and the
+//    unpredictable-value offset, then packing through a shared-memory word
+//    ring (MSB first) and the gather of the chunk's unpredictable values.
+//  * decode_kernel    one thread per chunk: 12-bit direct table, canonical
+//    comparison for longer codes; counts zero codes for the recover step.
+#include "internal.cuh"
+
+namespace sz3g {
+
+constexpr int kCbThreads = 1024;
+constexpr int kSmemLeaves = 8192;  // leaf count handled in shared memory
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagInc = 2ull << 62, kValMask = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 22;
+
+// ---------------------------------------------------------------------------
+// Block primitives (1024 threads).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v,
+                                                                   unsigned long long* s_warp,
+                                                                   unsigned long long* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long t = lane < nw ? s_warp[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) s_warp[lane] = t;  // inclusive warp totals
+  }
+  __syncthreads();
+  const unsigned long long before = (w ? s_warp[w - 1] : 0) + x - v;
+  if (total) *total = s_warp[nw - 1];
+  __syncthreads();
+  return before;
+}
+
+// Ascending bitonic sort of P (a power of two) keys, whole block.
+__device__ void block_bitonic_sort(unsigned long long* a, int P) {
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const unsigned long long x = a[i], y = a[ixj];
+          if ((x > y) == up) {
+            a[i] = y;
+            a[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ int pow2_at_least(int k) {
+  int p = 1;
+  while (p < k) p <<= 1;
+  return p;
+}
+
+// Two-queue Huffman merge over K leaves sorted by (weight, symbol); node ids:
+// leaves 0..K-1, internal K..2K-2 in creation order.  Single thread.
+__device__ void two_queue_merge(const unsigned long long* keys, int K, uint32_t* nf, uint32_t* parent) {
+  int li = 0, ni = 0, nn = 0;
+  uint32_t lf = K > 0 ? (uint32_t)(keys[0] >> 16) : 0u;
+  while (nn < K - 1) {
+    uint32_t pick[2], w[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (li < K && (ni >= nn || lf <= nf[ni])) {
+        pick[t] = (uint32_t)li;
+        w[t] = lf;
+        ++li;
+        lf = li < K ? (uint32_t)(keys[li] >> 16) : 0u;
+      } else {
+        pick[t] = (uint32_t)(K + ni);
+        w[t] = nf[ni];
+        ++ni;
+      }
+    }
+    nf[nn] = w[0] + w[1];
+    parent[pick[0]] = (uint32_t)(K + nn);
+    parent[pick[1]] = (uint32_t)(K + nn);
+    ++nn;
+  }
+}
+
+struct CbGlobal {  // global scratch of the codebook kernel
+  unsigned long long keys[kSyms];
+  uint32_t nf[kSyms];
+  uint32_t parent[2 * kSyms];
+  uint32_t sym[kSyms];   // used symbols in symbol order
+  uint32_t freq[kSyms];  // their current weights
+  uint32_t len[kSyms];   // length per sorted leaf
+};
+
+size_t codebook_scratch_bytes() { return sizeof(CbGlobal); }
+
+constexpr size_t kCbSmem = kSmemLeaves * 8 + kSmemLeaves * 4 + 2 * kSmemLeaves * 4;
+
+// table[sym] = len << 24 | code (0 for unused symbols).
+__global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __restrict__ hist, uint32_t nsym,
+                                                              uint32_t* table, uint8_t* len_out, uint32_t* code_out,
+                                                              DevState* st, CbGlobal* g, unsigned char* d_out,
+                                                              unsigned long long out_capacity, int esz) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_warp[32];
+  __shared__ uint32_t s_cnt[SZ3G_LMAX + 2], s_start[SZ3G_LMAX + 2], s_fc[SZ3G_LMAX + 2];
+  __shared__ int s_deep;
+  const int tid = threadIdx.x;
+
+  // 1. used symbols in symbol order (each thread a contiguous 64-symbol run)
+  const int per = kSyms / kCbThreads;
+  uint32_t mine = 0;
+  for (int s = tid * per; s < tid * per + per; ++s) {
+    const uint32_t f = s < (int)nsym ? hist[s] : 0u;
+    if (s >= (int)nsym && hist[s]) atomicOr(&st->flags, kFlagCorrupt);
+    table[s] = 0u;
+    if (len_out) len_out[s] = 0;
+    if (code_out) code_out[s] = 0;
+    mine += f != 0;
+  }
+  unsigned long long Ktot;
+  unsigned long long pos = block_exclusive_scan(mine, s_warp, &Ktot);
+  for (int s = tid * per; s < tid * per + per && s < (int)nsym; ++s) {
+    const uint32_t f = hist[s];
+    if (f) {
+      g->sym[pos] = (uint32_t)s;
+      g->freq[pos] = f;
+      ++pos;
+    }
+  }
+  __syncthreads();
+  const int K = (int)Ktot;
+  if (K == 0) {
+    if (tid == 0) atomicOr(&st->flags, kFlagCorrupt);
+    return;
+  }
+  const bool in_smem = K <= kSmemLeaves;
+  unsigned long long* keys = in_smem ? (unsigned long long*)smem : g->keys;
+  uint32_t* nf = in_smem ? (uint32_t*)(smem + kSmemLeaves * 8) : g->nf;
+  uint32_t* parent = in_smem ? (uint32_t*)(smem + kSmemLeaves * 12) : g->parent;
+  const int P = pow2_at_least(K);
+
+  // 2. lengths, halving the weights while some code is longer than LMAX
+  if (K == 1) {
+    if (tid == 0) g->len[0] = 1, keys[0] = ((unsigned long long)g->freq[0] << 16) | g->sym[0];
+    __syncthreads();
+  } else {
+    for (int iter = 0; iter < 40; ++iter) {
+      for (int i = tid; i < P; i += kCbThreads)
+        keys[i] = i < K ? (((unsigned long long)g->freq[i] << 16) | g->sym[i]) : ~0ull;
+      __syncthreads();
+      block_bitonic_sort(keys, P);
+      if (tid == 0) {
+        two_queue_merge(keys, K, nf, parent);
+        s_deep = 0;
+      }
+      __syncthreads();
+      const uint32_t root = (uint32_t)(2 * K - 2);
+      for (int i = tid; i < K; i += kCbThreads) {
+        uint32_t v = (uint32_t)i, d = 0;
+        while (v != root && d <= SZ3G_LMAX) {
+          v = parent[v];
+          ++d;
+        }
+        if (v != root || d > SZ3G_LMAX) s_deep = 1;
+        g->len[i] = d;
+      }
+      __syncthreads();
+      if (!s_deep) break;
+      for (int i = tid; i < K; i += kCbThreads) {
+        const uint32_t f = g->freq[i] >> 1;
+        g->freq[i] = f ? f : 1u;
+      }
+      __syncthreads();
+    }
+  }
+  // 3. canonical codewords: sort leaves by (length, symbol)
+  if (tid <= SZ3G_LMAX + 1) s_cnt[tid] = 0;
+  __syncthreads();
+  for (int i = tid; i < P; i += kCbThreads) {
+    if (i < K) {
+      const uint32_t L = g->len[i];
+      const uint32_t s = (uint32_t)(keys[i] & 0xffffu);
+      atomicAdd(&s_cnt[L], 1u);
+      keys[i] = ((unsigned long long)L << 16) | s;
+    } else {
+      keys[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  block_bitonic_sort(keys, P);
+  if (tid == 0) {
+    uint32_t start = 0, fc = 0;
+    for (int L = 1; L <= SZ3G_LMAX; ++L) {
+      if (L > 1) fc = (fc + s_cnt[L - 1]) << 1;
+      s_fc[L] = fc;
+      s_start[L] = start;
+      start += s_cnt[L];
+    }
+    st->n_used = (uint32_t)K;
+  }
+  __syncthreads();
+  for (int i = tid; i < K; i += kCbThreads) {
+    const uint32_t L = (uint32_t)(keys[i] >> 16), s = (uint32_t)(keys[i] & 0xffffu);
+    const uint32_t code = s_fc[L] + ((uint32_t)i - s_start[L]);
+    table[s] = (L << 24) | code;
+    if (len_out) len_out[s] = (uint8_t)L;
+    if (code_out) code_out[s] = code;
+  }
+  __syncthreads();
+  // 4. code-length section of the stream: (u16 symbol, u8 length) by symbol
+  if (d_out) {
+    const unsigned long long off = SZ3G_HEADER_BYTES + pad8(st->n_unpred * (unsigned long long)esz);
+    const unsigned long long end = pad8(off + 3ull * K);
+    if (end > out_capacity) {
+      if (tid == 0) atomicOr(&st->flags, kFlagCapacity);
+      return;
+    }
+    for (int i = tid; i < K; i += kCbThreads) {
+      const uint32_t s = g->sym[i];
+      unsigned char* q = d_out + off + 3ull * i;
+      q[0] = (unsigned char)(s & 0xff);
+      q[1] = (unsigned char)(s >> 8);
+      q[2] = (unsigned char)(table[s] >> 24);
+    }
+    for (unsigned long long b = off + 3ull * K + tid; b < end; b += kCbThreads) d_out[b] = 0;
+  }
+}
+
+int launch_codebook(const uint32_t* hist, uint32_t nsym, uint32_t* table, uint8_t* len_out, uint32_t* code_out,
+                    DevState* st, void* scratch, unsigned char* d_out, unsigned long long out_capacity, int esz,
+                    cudaStream_t s) {
+  if (cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) !=
+      cudaSuccess)
+    return SZ3G_E_CUDA;
+  codebook_kernel<<<1, kCbThreads, kCbSmem, s>>>(hist, nsym, table, len_out, code_out, st, (CbGlobal*)scratch, d_out,
+                                                 out_capacity, esz);
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Encoder.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Decoupled look-back: exclusive prefix of chunk j's value, whole warp.
+__device__ unsigned long long lookback(unsigned long long* stat, long long j, DevState* st) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long excl = 0;
+  long long base = j - 1;
+  int spins = 0;
+  while (base >= 0) {
+    const long long idx = base - lane;
+    unsigned long long v = idx >= 0 ? ld_acquire(stat + idx) : kFlagInc;
+    const unsigned not_ready = __ballot_sync(0xffffffffu, (v >> 62) == 0);
+    if (not_ready) {
+      if (++spins > kSpinLimit) {
+        if (lane == 0) atomicOr(&st->flags, kFlagTimeout);
+        return excl;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    const unsigned inc = __ballot_sync(0xffffffffu, (v >> 62) == 2);
+    const int stop = inc ? __ffs(inc) - 1 : 31;  // nearest inclusive predecessor
+    unsigned long long part = lane <= stop ? (v & kValMask) : 0ull;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    excl += part;
+    if (inc) break;
+    base -= 32;
+  }
+  return excl;
+}
+
+struct EncArgs {
+  const uint16_t* codes;
+  const uint32_t* table;
+  const void* x;                // input field (unpredictable values), stream mode
+  unsigned long long n, n_chunks;
+  uint32_t chunk;
+  int esz;
+  unsigned long long* wstat;
+  unsigned long long* zstat;
+  DevState* st;
+  unsigned char* d_out;         // stream mode: the output stream
+  unsigned long long out_capacity;
+  uint32_t* words_out;          // raw mode: payload
+  uint32_t* chunk_words_out;    // raw mode: words per chunk
+  unsigned long long cap_words; // raw mode
+  void* unpred_out;             // raw mode: unpredictable values (or null)
+  int mode;                     // kEncodeStream / kEncodeRaw
+  int emit_payload;             // 0: only gather unpredictable values
+};
+
+constexpr int kEncWarps = 8;
+constexpr int kRingWords = 200;
+
+__device__ __forceinline__ unsigned long long map_code_to_input(const PassMap& map, unsigned long long i) {
+  int lo = 0, hi = map.n - 1;
+  while (lo < hi) {  // largest p with off <= i
+    const int mid = (lo + hi + 1) >> 1;
+    if (map.e[mid].off <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const PassMapEntry& e = map.e[lo];
+  unsigned long long j = i - e.off;
+  const unsigned long long c3 = j % e.E[3];
+  j /= e.E[3];
+  const unsigned long long c2 = j % e.E[2];
+  j /= e.E[2];
+  const unsigned long long c1 = j % e.E[1];
+  j /= e.E[1];
+  return e.xstart + j * e.xls[0] + c1 * e.xls[1] + c2 * e.xls[2] + c3 * e.xls[3];
+}
+
+template <typename U>
+__global__ void __launch_bounds__(kEncWarps * 32) encode_kernel(const EncArgs a, const __grid_constant__ PassMap map) {
+  __shared__ uint32_t ring[kEncWarps][kRingWords];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* buf = ring[w];
+  for (int k = lane; k < kRingWords; k += 32) buf[k] = 0;
+  __syncwarp();
+  DevState* st = a.st;
+  for (;;) {
+    unsigned long long j = 0;
+    if (lane == 0) j = atomicAdd(&st->ticket, 1u);
+    j = __shfl_sync(0xffffffffu, j, 0);
+    if (j >= a.n_chunks) break;
+    const unsigned long long i0 = j * a.chunk;
+    const uint32_t cnt = (uint32_t)min((unsigned long long)a.chunk, a.n - i0);
+    const uint16_t* cp = a.codes + i0;
+    // pass 1: bits and zeros of the chunk
+    unsigned long long bits = 0;
+    uint32_t zeros = 0;
+    for (uint32_t t = lane * 8; t < cnt; t += 256) {
+      if (t + 8 <= cnt) {
+        const uint4 v = *reinterpret_cast<const uint4*>(cp + t);
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t c0 = wv[q] & 0xffffu, c1 = wv[q] >> 16;
+          bits += (a.table[c0] >> 24) + (a.table[c1] >> 24);
+          zeros += (c0 == 0) + (c1 == 0);
+        }
+      } else {
+        for (uint32_t u = t; u < cnt; ++u) {
+          const uint32_t c = cp[u];
+          bits += a.table[c] >> 24;
+          zeros += c == 0;
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      bits += __shfl_xor_sync(0xffffffffu, bits, o);
+      zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
+    }
+    const unsigned long long words = (bits + 31) >> 5;
+    if (lane == 0) {
+      st_release(a.wstat + j, (j == 0 ? kFlagInc : kFlagAgg) | words);
+      st_release(a.zstat + j, (j == 0 ? kFlagInc : kFlagAgg) | zeros);
+    }
+    const unsigned long long wexcl = lookback(a.wstat, (long long)j, st);
+    const unsigned long long zexcl = lookback(a.zstat, (long long)j, st);
+    if (lane == 0 && j > 0) {
+      st_release(a.wstat + j, kFlagInc | (wexcl + words));
+      st_release(a.zstat + j, kFlagInc | (zexcl + zeros));
+    }
+    if (lane == 0 && j == a.n_chunks - 1) st->n_words = wexcl + words;
+    // destinations
+    uint32_t* pay;
+    U* unp;
+    bool ok = true;
+    if (a.mode == kEncodeStream) {
+      const unsigned long long nu = st->n_unpred;
+      const unsigned long long off_table = SZ3G_HEADER_BYTES + pad8(nu * a.esz);
+      const unsigned long long off_chunks = off_table + pad8(3ull * st->n_used);
+      const unsigned long long off_payload = off_chunks + pad8(a.n_chunks * 4);
+      unp = reinterpret_cast<U*>(a.d_out + SZ3G_HEADER_BYTES);
+      pay = reinterpret_cast<uint32_t*>(a.d_out + off_payload);
+      if (off_payload + 4 * (wexcl + words) > a.out_capacity || zexcl + zeros > nu) {
+        ok = false;
+        if (lane == 0) atomicOr(&st->flags, kFlagCapacity);
+      } else if (lane == 0) {
+        *reinterpret_cast<uint32_t*>(a.d_out + off_chunks + 4 * j) = (uint32_t)words;
+      }
+    } else {
+      unp = reinterpret_cast<U*>(a.unpred_out);
+      pay = a.words_out;
+      if (a.emit_payload) {
+        if (wexcl + words > a.cap_words) {
+          ok = false;
+          if (lane == 0) atomicOr(&st->flags, kFlagCapacity);
+        } else if (lane == 0) {
+          a.chunk_words_out[j] = (uint32_t)words;
+        }
+      }
+    }
+    if (!ok) continue;
+    // pass 2: emit the bits, gather the unpredictable values
+    const bool emit = a.emit_payload != 0;
+    unsigned long long wpos = wexcl;  // next word to write
+    uint32_t carry = 0;               // bits pending in buf[0]
+    unsigned long long zpos = zexcl;
+    for (uint32_t r0 = 0; r0 < cnt; r0 += 256) {
+      const uint32_t t = r0 + lane * 8;
+      uint32_t c8[8];
+      uint32_t nb = 0, nzl = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) c8[q] = 0xffffffffu;
+      if (t + 8 <= cnt) {
+        const uint4 v = *reinterpret_cast<const uint4*>(cp + t);
+        c8[0] = v.x & 0xffffu; c8[1] = v.x >> 16; c8[2] = v.y & 0xffffu; c8[3] = v.y >> 16;
+        c8[4] = v.z & 0xffffu; c8[5] = v.z >> 16; c8[6] = v.w & 0xffffu; c8[7] = v.w >> 16;
+      } else {
+        for (uint32_t u = t; u < cnt; ++u) c8[u - t] = cp[u];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (c8[q] != 0xffffffffu) {
+          nb += a.table[c8[q]] >> 24;
+          nzl += c8[q] == 0;
+        }
+      }
+      uint32_t incl = nb, zincl = nzl;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        const uint32_t yz = __shfl_up_sync(0xffffffffu, zincl, o);
+        if (lane >= o) {
+          incl += y;
+          zincl += yz;
+        }
+      }
+      const uint32_t round_bits = __shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t round_zeros = __shfl_sync(0xffffffffu, zincl, 31);
+      if (emit) {
+        uint32_t o = carry + incl - nb;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (c8[q] == 0xffffffffu) continue;
+          const uint32_t e = a.table[c8[q]];
+          const uint32_t L = e >> 24, val = e & 0xffffffu;
+          const uint32_t wi = o >> 5, sh = o & 31;
+          if (sh + L <= 32) {
+            atomicOr(&buf[wi], val << (32 - sh - L));
+          } else {
+            atomicOr(&buf[wi], val >> (sh + L - 32));
+            atomicOr(&buf[wi + 1], val << (64 - sh - L));
+          }
+          o += L;
+        }
+        __syncwarp();
+        const uint32_t total = carry + round_bits;
+        const uint32_t full = total >> 5;
+        for (uint32_t k = lane; k < full; k += 32) pay[wpos + k] = buf[k];
+        wpos += full;
+        const uint32_t rest = buf[full];
+        __syncwarp();
+        for (uint32_t k = lane; k <= full; k += 32) buf[k] = 0;
+        __syncwarp();
+        carry = total & 31;
+        if (lane == 0) buf[0] = carry ? rest : 0u;
+        __syncwarp();
+      }
+      if (nzl && unp) {
+        unsigned long long zr = zpos + zincl - nzl;
+        for (int q = 0; q < 8; ++q) {
+          if (c8[q] == 0) {
+            const unsigned long long xi = map_code_to_input(map, i0 + t + q);
+            unp[zr++] = reinterpret_cast<const U*>(a.x)[xi];
+          }
+        }
+      }
+      zpos += round_zeros;
+    }
+    if (emit) {
+      if (carry && lane == 0) pay[wpos] = buf[0];
+      __syncwarp();
+      if (lane == 0) buf[0] = 0;
+      __syncwarp();
+    }
+  }
+}
+
+int launch_encode_impl(const EncArgs& a, const PassMap* map, cudaStream_t s) {
+  int nb = (int)((a.n_chunks + kEncWarps - 1) / kEncWarps);
+  if (nb > 152 * 8) nb = 152 * 8;
+  if (nb < 1) nb = 1;
+  if (a.esz == 4)
+    encode_kernel<uint32_t><<<nb, kEncWarps * 32, 0, s>>>(a, *map);
+  else
+    encode_kernel<unsigned long long><<<nb, kEncWarps * 32, 0, s>>>(a, *map);
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+int launch_encode(const Plan& pl, const uint16_t* codes, const uint32_t* table, const void* d_in, const PassMap* map,
+                  unsigned long long* wstat, unsigned long long* zstat, DevState* st, unsigned char* d_out,
+                  unsigned long long out_capacity, int mode, uint32_t* words_out, uint32_t* chunk_words_out,
+                  unsigned long long cap_words, cudaStream_t s) {
+  EncArgs a{};
+  a.codes = codes;
+  a.table = table;
+  a.x = d_in;
+  a.n = pl.N;
+  a.n_chunks = pl.n_chunks;
+  a.chunk = pl.chunk;
+  a.esz = pl.esz;
+  a.wstat = wstat;
+  a.zstat = zstat;
+  a.st = st;
+  a.d_out = d_out;
+  a.out_capacity = out_capacity;
+  a.words_out = words_out;
+  a.chunk_words_out = chunk_words_out;
+  a.cap_words = cap_words;
+  a.unpred_out = nullptr;
+  a.mode = mode;
+  a.emit_payload = 1;
+  return launch_encode_impl(a, map, s);
+}
+
+// Unpredictable values in traversal order, without encoding (stage API).
+int launch_compact_unpred(const Plan& pl, const uint16_t* codes, const void* d_in, const PassMap* map,
+                          unsigned long long* wstat, unsigned long long* zstat, const uint32_t* table,
+                          void* d_unpred, DevState* st, cudaStream_t s) {
+  EncArgs a{};
+  a.codes = codes;
+  a.table = table;
+  a.x = d_in;
+  a.n = pl.N;
+  a.n_chunks = pl.n_chunks;
+  a.chunk = pl.chunk;
+  a.esz = pl.esz;
+  a.wstat = wstat;
+  a.zstat = zstat;
+  a.st = st;
+  a.mode = kEncodeRaw;
+  a.emit_payload = 0;
+  a.unpred_out = d_unpred;
+  return launch_encode_impl(a, map, s);
+}
+
+// ---------------------------------------------------------------------------
+// Stream header (written last, once every count is known).
+// ---------------------------------------------------------------------------
+struct HeaderArgs {
+  unsigned char bytes[SZ3G_HEADER_BYTES];  // static fields, counts filled on device
+  unsigned long long n_chunks;
+  int esz;
+};
+
+__global__ void finalize_kernel(const HeaderArgs h, DevState* st, unsigned char* d_out,
+                                unsigned long long out_capacity) {
+  const int tid = threadIdx.x;
+  if (st->flags & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound | kFlagCapacity | kFlagTimeout)) return;
+  const unsigned long long nu = st->n_unpred, nw = st->n_words;
+  const uint32_t nused = st->n_used;
+  const unsigned long long off_table = SZ3G_HEADER_BYTES + pad8(nu * h.esz);
+  const unsigned long long off_chunks = off_table + pad8(3ull * nused);
+  const unsigned long long off_payload = off_chunks + pad8(h.n_chunks * 4);
+  const unsigned long long end = off_payload + pad8(nw * 4);
+  if (end > out_capacity) {
+    if (tid == 0) atomicOr(&st->flags, kFlagCapacity);
+    return;
+  }
+  for (int b = tid; b < SZ3G_HEADER_BYTES; b += blockDim.x) {
+    unsigned char v = h.bytes[b];
+    if (b >= 56 && b < 64) v = (unsigned char)(__double_as_longlong(st->eb_abs) >> (8 * (b - 56)));
+    if (b >= 64 && b < 72) v = (unsigned char)(st->ebT_bits >> (8 * (b - 64)));
+    if (b >= 76 && b < 80) v = (unsigned char)(nused >> (8 * (b - 76)));
+    if (b >= 88 && b < 96) v = (unsigned char)(nu >> (8 * (b - 88)));
+    if (b >= 104 && b < 112) v = (unsigned char)(nw >> (8 * (b - 104)));
+    d_out[b] = v;
+  }
+  // zero padding after the unpredictable values, the chunk table and the payload
+  if (tid < 8) {
+    const unsigned long long u_end = SZ3G_HEADER_BYTES + nu * h.esz;
+    if (u_end + tid < off_table) d_out[u_end + tid] = 0;
+    const unsigned long long c_end = off_chunks + h.n_chunks * 4;
+    if (c_end + tid < off_payload) d_out[c_end + tid] = 0;
+    const unsigned long long p_end = off_payload + nw * 4;
+    if (p_end + tid < end) d_out[p_end + tid] = 0;
+  }
+  if (tid == 0) st->out_bytes = end;
+}
+
+int launch_finalize(const Plan& pl, const sz3g_params* p, DevState* st, unsigned char* d_out,
+                    unsigned long long out_capacity, cudaStream_t s) {
+  HeaderArgs h;
+  memset(&h, 0, sizeof(h));
+  unsigned char* b = h.bytes;
+  auto put = [&](int off, unsigned long long v, int n) {
+    for (int i = 0; i < n; ++i) b[off + i] = (unsigned char)(v >> (8 * i));
+  };
+  b[0] = 'S';
+  b[1] = 'Z';
+  b[2] = '3';
+  b[3] = 'G';
+  put(4, 1, 2);
+  b[6] = (unsigned char)p->dtype;
+  b[7] = (unsigned char)p->ndim;
+  for (int i = 0; i < 4; ++i) put(8 + 8 * i, i < (int)p->ndim ? p->dims[i] : 1, 8);
+  b[40] = (unsigned char)p->eb_mode;
+  b[41] = (unsigned char)p->interp;
+  b[42] = p->per_level;
+  b[43] = (unsigned char)pl.L;
+  put(44, p->radius, 4);
+  unsigned long long ebb;
+  memcpy(&ebb, &p->eb, 8);
+  put(48, ebb, 8);
+  put(72, p->chunk_codes, 4);
+  put(80, pl.N, 8);
+  put(96, pl.n_chunks, 8);
+  if (p->per_level) {
+    for (int l = 1; l <= pl.L; ++l) {
+      b[112 + l] = p->level_interp[l];
+      for (int i = 0; i < 4; ++i) b[144 + 4 * l + i] = i < (int)p->ndim ? p->level_order[l][i] : 0;
+    }
+  }
+  for (int i = 0; i < 4; ++i) b[272 + i] = i < (int)p->ndim ? p->dim_order[i] : 0;
+  h.n_chunks = pl.n_chunks;
+  h.esz = pl.esz;
+  finalize_kernel<<<1, 64, 0, s>>>(h, st, d_out, out_capacity);
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Decoder.
+// ---------------------------------------------------------------------------
+struct DecTables {
+  uint32_t lut[1 << kLutBits];  // len << 16 | sym, 0 = longer than 12 bits / no codeword
+  uint32_t fc[SZ3G_LMAX + 2], cnt[SZ3G_LMAX + 2], start[SZ3G_LMAX + 2];
+  uint32_t n_used;
+  uint32_t pad;
+  unsigned long long keys[kSyms];  // sort scratch
+  uint16_t sorted[kSyms];          // symbols by (length, symbol)
+};
+
+// Decode tables from a (symbol, length) list: either the stream's 3-byte
+// records (tab != null, n_used entries) or a length per symbol (len != null).
+__global__ void __launch_bounds__(kCbThreads) decode_tables_kernel(const unsigned char* tab, uint32_t n_used,
+                                                                   const uint8_t* len, uint32_t nsym, DecTables* T,
+                                                                   DevState* st) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_warp[32];
+  __shared__ uint32_t s_cnt[SZ3G_LMAX + 2];
+  __shared__ int s_bad;
+  __shared__ unsigned long long s_kraft;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_bad = 0;
+    s_kraft = 0;
+  }
+  if (tid <= SZ3G_LMAX + 1) s_cnt[tid] = 0;
+  for (int i = tid; i < (1 << kLutBits); i += kCbThreads) T->lut[i] = 0;
+  __syncthreads();
+  unsigned long long* keys;
+  int K;
+  if (tab) {
+    K = (int)n_used;
+    keys = K <= kSmemLeaves ? (unsigned long long*)smem : T->keys;
+    for (int i = tid; i < K; i += kCbThreads) {
+      const uint32_t s = tab[3 * i] | ((uint32_t)tab[3 * i + 1] << 8);
+      const uint32_t L = tab[3 * i + 2];
+      if (s >= nsym || L < 1 || L > SZ3G_LMAX) s_bad = 1;
+      if (i > 0) {
+        const uint32_t sp = tab[3 * (i - 1)] | ((uint32_t)tab[3 * (i - 1) + 1] << 8);
+        if (sp >= s) s_bad = 1;
+      }
+      keys[i] = ((unsigned long long)(L & 31) << 16) | (s & 0xffffu);
+    }
+  } else {
+    // compact the used symbols (symbol order), 64 per thread
+    const int per = kSyms / kCbThreads;
+    uint32_t mine = 0;
+    for (int s = tid * per; s < tid * per + per; ++s) mine += (s < (int)nsym && len[s]) ? 1u : 0u;
+    unsigned long long tot;
+    unsigned long long pos = block_exclusive_scan(mine, s_warp, &tot);
+    K = (int)tot;
+    keys = K <= kSmemLeaves ? (unsigned long long*)smem : T->keys;
+    for (int s = tid * per; s < tid * per + per && s < (int)nsym; ++s) {
+      if (len[s]) {
+        if (len[s] > SZ3G_LMAX) s_bad = 1;
+        keys[pos++] = ((unsigned long long)(len[s] & 31) << 16) | (uint32_t)s;
+      }
+    }
+  }
+  __syncthreads();
+  if (K < 1) {
+    if (tid == 0) atomicOr(&st->flags, kFlagCorrupt);
+    return;
+  }
+  // Kraft sum in units of 2^-LMAX
+  for (int i = tid; i < K; i += kCbThreads) {
+    const uint32_t L = (uint32_t)(keys[i] >> 16);
+    if (L >= 1 && L <= SZ3G_LMAX) atomicAdd(&s_kraft, 1ull << (SZ3G_LMAX - L));
+    if (L >= 1 && L <= SZ3G_LMAX) atomicAdd(&s_cnt[L], 1u);
+  }
+  const int P = pow2_at_least(K);
+  for (int i = K + tid; i < P; i += kCbThreads) keys[i] = ~0ull;
+  __syncthreads();
+  const bool kraft_ok = K == 1 ? s_kraft == (1ull << (SZ3G_LMAX - 1)) : s_kraft == (1ull << SZ3G_LMAX);
+  if (s_bad || !kraft_ok) {
+    if (tid == 0) atomicOr(&st->flags, kFlagCorrupt);
+    return;
+  }
+  block_bitonic_sort(keys, P);
+  if (tid == 0) {
+    uint32_t start = 0, fc = 0;
+    for (int L = 1; L <= SZ3G_LMAX; ++L) {
+      if (L > 1) fc = (fc + s_cnt[L - 1]) << 1;
+      T->fc[L] = fc;
+      T->cnt[L] = s_cnt[L];
+      T->start[L] = start;
+      start += s_cnt[L];
+    }
+    T->n_used = (uint32_t)K;
+  }
+  __syncthreads();
+  for (int i = tid; i < K; i += kCbThreads) {
+    const uint32_t L = (uint32_t)(keys[i] >> 16), s = (uint32_t)(keys[i] & 0xffffu);
+    T->sorted[i] = (uint16_t)s;
+    if (L <= kLutBits) {
+      uint32_t fc = 0, start = 0, c = 0;
+      // recompute this length's first code and start (tables written by thread 0)
+      fc = T->fc[L];
+      start = T->start[L];
+      c = fc + ((uint32_t)i - start);
+      const uint32_t lo = c << (kLutBits - L), nfill = 1u << (kLutBits - L);
+      for (uint32_t k = 0; k < nfill; ++k) T->lut[lo + k] = (L << 16) | s;
+    }
+  }
+}
+
+struct DecArgs {
+  const uint32_t* words;
+  const unsigned long long* woff;  // word offset of every chunk
+  const uint32_t* chunk_words;
+  unsigned long long n_chunks, n;
+  uint32_t chunk, nsub;
+  const DecTables* T;
+  uint16_t* codes;
+  uint32_t* zchunk;  // zero codes per chunk
+  uint32_t* zsub;    // zero codes before each 256-code block of a chunk
+  DevState* st;
+};
+
+__global__ void __launch_bounds__(128) decode_kernel(const DecArgs a) {
+  if (a.st->flags & kFlagCorrupt) return;  // tables or chunk table rejected
+  __shared__ uint32_t lut[1 << kLutBits];
+  __shared__ uint32_t fc[SZ3G_LMAX + 2], cnt[SZ3G_LMAX + 2], start[SZ3G_LMAX + 2];
+  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) lut[i] = a.T->lut[i];
+  if (threadIdx.x <= SZ3G_LMAX + 1) {
+    fc[threadIdx.x] = a.T->fc[threadIdx.x];
+    cnt[threadIdx.x] = a.T->cnt[threadIdx.x];
+    start[threadIdx.x] = a.T->start[threadIdx.x];
+  }
+  __syncthreads();
+  const unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.n_chunks) return;
+  const unsigned long long i0 = j * a.chunk;
+  const uint32_t n = (uint32_t)min((unsigned long long)a.chunk, a.n - i0);
+  const uint32_t* wp = a.words + a.woff[j];
+  const uint32_t nw = a.chunk_words[j];
+  uint32_t wi = 0;
+  unsigned long long buf = 0;
+  int nb = 0;
+  uint32_t zeros = 0;
+  bool bad = false;
+  uint32_t pack[4] = {0, 0, 0, 0};
+  uint16_t* out = a.codes + i0;
+  for (uint32_t i = 0; i < n; ++i) {
+    if ((i & 255) == 0) a.zsub[j * a.nsub + (i >> 8)] = zeros;
+    while (nb <= 32 && wi < nw) {
+      buf |= (unsigned long long)wp[wi++] << (32 - nb);
+      nb += 32;
+    }
+    uint32_t e = lut[buf >> (64 - kLutBits)];
+    uint32_t L = e >> 16, sym = e & 0xffffu;
+    if (L == 0) {
+      for (uint32_t l = kLutBits + 1; l <= SZ3G_LMAX; ++l) {
+        const uint32_t v = (uint32_t)(buf >> (64 - l));
+        if (v - fc[l] < cnt[l]) {
+          const uint32_t k = start[l] + (v - fc[l]);
+          if (k < a.T->n_used) {
+            L = l;
+            sym = a.T->sorted[k];
+          }
+          break;
+        }
+      }
+    }
+    if (L == 0 || (int)L > nb) {
+      bad = true;
+      break;
+    }
+    buf <<= L;
+    nb -= (int)L;
+    zeros += sym == 0;
+    const uint32_t q = i & 7;
+    pack[q >> 1] |= sym << (16 * (q & 1));
+    if (q == 7) {
+      *reinterpret_cast<uint4*>(out + (i - 7)) = make_uint4(pack[0], pack[1], pack[2], pack[3]);
+      pack[0] = pack[1] = pack[2] = pack[3] = 0;
+    }
+  }
+  if (!bad) {
+    const uint32_t rem = n & 7;
+    for (uint32_t q = 0; q < rem; ++q) out[n - rem + q] = (uint16_t)(pack[q >> 1] >> (16 * (q & 1)));
+    a.zchunk[j] = zeros;
+  } else {
+    atomicOr(&a.st->flags, kFlagCorrupt);
+    a.zchunk[j] = 0;
+  }
+}
+
+// Exclusive prefix of n values (u32 in, u64 out) in one CTA; total -> *total.
+// If limit != 0, every value must be <= limit.
+__global__ void __launch_bounds__(kCbThreads) scan_u32_kernel(const uint32_t* in, unsigned long long n,
+                                                              unsigned long long* out, unsigned long long* total,
+                                                              uint32_t limit, unsigned long long expect,
+                                                              int check_expect, DevState* st) {
+  __shared__ unsigned long long s_warp[32];
+  const unsigned long long per = (n + kCbThreads - 1) / kCbThreads;
+  const unsigned long long b = threadIdx.x * per, e = min(n, b + per);
+  unsigned long long sum = 0;
+  bool bad = false;
+  for (unsigned long long i = b; i < e; ++i) {
+    const uint32_t v = in[i];
+    if (limit && v > limit) bad = true;
+    sum += v;
+  }
+  unsigned long long tot;
+  unsigned long long run = block_exclusive_scan(sum, s_warp, &tot);
+  for (unsigned long long i = b; i < e; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  if (bad) atomicOr(&st->flags, kFlagCorrupt);
+  if (threadIdx.x == 0) {
+    if (total) *total = tot;
+    if (check_expect && tot != expect) atomicOr(&st->flags, kFlagCorrupt);
+  }
+}
+
+size_t dec_tables_bytes() { return sizeof(DecTables); }
+
+constexpr size_t kDecSmem = kSmemLeaves * 8;
+
+int launch_decode_tables(const unsigned char* tab, uint32_t n_used, const uint8_t* len, uint32_t nsym, void* tables,
+                         DevState* st, cudaStream_t s) {
+  if (cudaFuncSetAttribute(decode_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem) !=
+      cudaSuccess)
+    return SZ3G_E_CUDA;
+  decode_tables_kernel<<<1, kCbThreads, kDecSmem, s>>>(tab, n_used, len, nsym, (DecTables*)tables, st);
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+// words: payload; chunk_words: per-chunk word counts (validated here).
+int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, const uint32_t* chunk_words,
+                         unsigned long long n_chunks, uint32_t chunk, unsigned long long n, const void* tables,
+                         unsigned long long* woff, uint16_t* codes, uint32_t* zchunk, uint32_t* zsub, uint32_t nsub,
+                         DevState* st, cudaStream_t s) {
+  const uint32_t maxw = (uint32_t)(((unsigned long long)chunk * SZ3G_LMAX + 31) / 32);
+  scan_u32_kernel<<<1, kCbThreads, 0, s>>>(chunk_words, n_chunks, woff, nullptr, maxw, n_words, 1, st);
+  DecArgs a{};
+  a.words = words;
+  a.woff = woff;
+  a.chunk_words = chunk_words;
+  a.n_chunks = n_chunks;
+  a.n = n;
+  a.chunk = chunk;
+  a.nsub = nsub;
+  a.T = (const DecTables*)tables;
+  a.codes = codes;
+  a.zchunk = zchunk;
+  a.zsub = zsub;
+  a.st = st;
+  decode_kernel<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+// Zero-code counts per chunk and per 256-code block from a code array (used
+// when codes come from the caller instead of the decoder).
+__global__ void zero_count_kernel(const uint16_t* codes, unsigned long long n, uint32_t chunk, uint32_t nsub,
+                                  unsigned long long n_chunks, uint32_t* zchunk, uint32_t* zsub) {
+  const unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_chunks) return;
+  const unsigned long long i0 = j * chunk;
+  const uint32_t cnt = (uint32_t)min((unsigned long long)chunk, n - i0);
+  uint32_t z = 0;
+  for (uint32_t i = 0; i < cnt; ++i) {
+    if ((i & 255) == 0) zsub[j * nsub + (i >> 8)] = z;
+    z += codes[i0 + i] == 0;
+  }
+  zchunk[j] = z;
+}
+
+int launch_zero_counts(const uint16_t* codes, unsigned long long n, uint32_t chunk, uint32_t nsub,
+                       unsigned long long n_chunks, uint32_t* zchunk, uint32_t* zsub, cudaStream_t s) {
+  zero_count_kernel<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(codes, n, chunk, nsub, n_chunks, zchunk, zsub);
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+int launch_scan_u32(const uint32_t* in, unsigned long long n, unsigned long long* out, unsigned long long* total,
+                    unsigned long long expect, int check_expect, DevState* st, cudaStream_t s) {
+  scan_u32_kernel<<<1, kCbThreads, 0, s>>>(in, n, out, total, 0, expect, check_expect, st);
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+// table[sym] = len << 24 | code from separate arrays (stage API).
+__global__ void pack_table_kernel(const uint8_t* len, const uint32_t* code, uint32_t nsym, uint32_t* table) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < (uint32_t)kSyms) table[s] = s < nsym ? (((uint32_t)len[s] << 24) | (code[s] & 0xffffffu)) : 0u;
+}
+
+int launch_pack_table(const uint8_t* len, const uint32_t* code, uint32_t nsym, uint32_t* table, cudaStream_t s) {
+  pack_table_kernel<<<kSyms / 256, 256, 0, s>>>(len, code, nsym, table);
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+}  // namespace sz3g

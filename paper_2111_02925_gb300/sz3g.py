@@ -1,0 +1,270 @@
+"""Python binding of libsz3g.so (the C ABI in include/sz3g.h).
+
+Argument marshalling only: every step of compression and decompression runs
+in the library's CUDA kernels.  PyTorch supplies device memory and the
+stream.  If the library has not been built, every call raises -- there is no
+CPU fallback.
+
+Functions named ``sz3g_*`` mirror the C entry points one to one and take raw
+pointers (ints); the lower-case helpers below them take torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+F32, F64 = 0, 1
+ABS, REL = 0, 1
+LINEAR, CUBIC = 0, 1
+MAX_LEVELS = 32
+LMAX = 24
+HEADER_BYTES = 288
+
+OK = 0
+E_INVAL = -1
+E_NONFINITE = -2
+E_ZERO_RANGE_REL = -3
+E_CAPACITY = -4
+E_CORRUPT = -5
+E_CUDA = -6
+E_NOMEM = -7
+E_TIMEOUT = -8
+
+
+class SZ3GError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {code} ({strerror(code) if _lib else 'library not loaded'})")
+        self.code = code
+
+
+class Params(C.Structure):
+    """sz3g_params (232 bytes)."""
+
+    _fields_ = [
+        ("dtype", C.c_uint32),
+        ("ndim", C.c_uint32),
+        ("dims", C.c_uint64 * 4),
+        ("eb_mode", C.c_uint32),
+        ("interp", C.c_uint32),
+        ("eb", C.c_double),
+        ("dim_order", C.c_uint8 * 4),
+        ("per_level", C.c_uint8),
+        ("reserved", C.c_uint8 * 3),
+        ("radius", C.c_uint32),
+        ("chunk_codes", C.c_uint32),
+        ("level_interp", C.c_uint8 * MAX_LEVELS),
+        ("level_order", (C.c_uint8 * 4) * MAX_LEVELS),
+    ]
+
+
+assert C.sizeof(Params) == 232
+
+_lib = None
+
+# name -> argtypes (restype int unless noted)
+_P = C.POINTER(Params)
+_vp, _sz, _u64, _u32 = C.c_void_p, C.c_size_t, C.c_uint64, C.c_uint32
+_SIGS = {
+    "sz3g_compress_bound": [_P, C.POINTER(_sz)],
+    "sz3g_workspace_size": [_P, C.c_int, C.POINTER(_sz)],
+    "sz3g_compress": [_P, _vp, _vp, _sz, C.POINTER(_sz), _vp, _sz, _vp],
+    "sz3g_read_header": [_vp, _sz, C.c_int, _P, C.POINTER(_u64)],
+    "sz3g_decompress": [_vp, _sz, _vp, _sz, _vp, _sz, _vp],
+    "sz3g_compress_host": [_P, _vp, _vp, _sz, C.POINTER(_sz), _vp],
+    "sz3g_decompress_host": [_vp, _sz, _vp, _sz, _vp],
+    "sz3g_predict_quantize": [_P, _vp, _vp, _vp, _vp, C.POINTER(_u64), _vp, _vp, _sz, _vp],
+    "sz3g_recover": [_P, _vp, _vp, _vp, _u64, _vp, _vp, _sz, _vp],
+    "sz3g_huffman_build": [_vp, _u32, _vp, _vp, _vp],
+    "sz3g_huffman_encode": [_vp, _u64, _vp, _vp, _u32, _u32, _vp, _u64, _vp, C.POINTER(_u64), _vp],
+    "sz3g_huffman_decode": [_vp, _u64, _vp, _u32, _vp, _u32, _vp, _u64, _vp],
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load the built library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (paper_2111_02925_gb300.build)")
+    L = C.CDLL(path)
+    for name, args in _SIGS.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.sz3g_strerror.argtypes = [C.c_int]
+    L.sz3g_strerror.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return load().sz3g_strerror(code).decode()
+
+
+def _chk(rc: int, where: str):
+    if rc != OK:
+        raise SZ3GError(rc, where)
+
+
+def make_params(dims, eb, *, dtype=F32, eb_mode=ABS, interp=LINEAR, order=None, radius=32768, chunk=4096,
+                level_interp=None, level_order=None) -> Params:
+    p = Params()
+    dims = [int(d) for d in dims]
+    p.dtype, p.ndim = dtype, len(dims)
+    for i in range(4):
+        p.dims[i] = dims[i] if i < len(dims) else 1
+    p.eb_mode, p.interp, p.eb = eb_mode, interp, float(eb)
+    order = list(range(len(dims))) if order is None else list(order)
+    for i in range(4):
+        p.dim_order[i] = order[i] if i < len(order) else 0
+    p.radius, p.chunk_codes = radius, chunk
+    if level_interp is not None or level_order is not None:
+        p.per_level = 1
+        for l in range(1, MAX_LEVELS):
+            li = (level_interp or {}).get(l, interp)
+            lo = (level_order or {}).get(l, order)
+            p.level_interp[l] = li
+            for i in range(4):
+                p.level_order[l][i] = lo[i] if i < len(lo) else 0
+    return p
+
+
+# ---- raw C entry points ----------------------------------------------------
+def sz3g_compress_bound(p: Params) -> int:
+    n = _sz()
+    _chk(load().sz3g_compress_bound(C.byref(p), C.byref(n)), "sz3g_compress_bound")
+    return n.value
+
+
+def sz3g_workspace_size(p: Params, for_decompress: int) -> int:
+    n = _sz()
+    _chk(load().sz3g_workspace_size(C.byref(p), int(for_decompress), C.byref(n)), "sz3g_workspace_size")
+    return n.value
+
+
+def sz3g_compress(p: Params, d_in: int, d_out: int, out_capacity: int, d_ws: int = 0, ws_bytes: int = 0,
+                  stream: int = 0):
+    """Returns (status, out_bytes)."""
+    nb = _sz(0)
+    rc = load().sz3g_compress(C.byref(p), d_in, d_out, out_capacity, C.byref(nb), d_ws or None, ws_bytes,
+                              stream or None)
+    return rc, nb.value
+
+
+def sz3g_read_header(stream_ptr: int, nbytes: int, on_device: int):
+    p, n = Params(), _u64()
+    rc = load().sz3g_read_header(stream_ptr, nbytes, on_device, C.byref(p), C.byref(n))
+    return rc, p, n.value
+
+
+def sz3g_decompress(d_stream: int, nbytes: int, d_out: int, out_capacity: int, d_ws: int = 0, ws_bytes: int = 0,
+                    stream: int = 0) -> int:
+    return load().sz3g_decompress(d_stream, nbytes, d_out, out_capacity, d_ws or None, ws_bytes, stream or None)
+
+
+def sz3g_compress_host(p: Params, h_in: int, h_out: int, out_capacity: int, stream: int = 0):
+    nb = _sz(0)
+    rc = load().sz3g_compress_host(C.byref(p), h_in, h_out, out_capacity, C.byref(nb), stream or None)
+    return rc, nb.value
+
+
+def sz3g_decompress_host(h_stream: int, nbytes: int, h_out: int, out_capacity: int, stream: int = 0) -> int:
+    return load().sz3g_decompress_host(h_stream, nbytes, h_out, out_capacity, stream or None)
+
+
+def sz3g_predict_quantize(p: Params, d_in: int, d_codes: int, d_unpred: int, d_hist: int, d_ws: int = 0,
+                          ws_bytes: int = 0, stream: int = 0):
+    nu = _u64()
+    eb = (C.c_uint8 * 8)()
+    rc = load().sz3g_predict_quantize(C.byref(p), d_in, d_codes, d_unpred, d_hist, C.byref(nu), eb, d_ws or None,
+                                      ws_bytes, stream or None)
+    return rc, nu.value, bytes(eb)
+
+
+def sz3g_recover(p: Params, ebT_bytes: bytes, d_codes: int, d_unpred: int, n_unpred: int, d_out: int,
+                 d_ws: int = 0, ws_bytes: int = 0, stream: int = 0) -> int:
+    eb = (C.c_uint8 * 8)(*ebT_bytes[:8].ljust(8, b"\0"))
+    return load().sz3g_recover(C.byref(p), eb, d_codes, d_unpred or None, n_unpred, d_out, d_ws or None, ws_bytes,
+                               stream or None)
+
+
+def sz3g_huffman_build(d_hist: int, nsym: int, d_len: int, d_code: int, stream: int = 0) -> int:
+    return load().sz3g_huffman_build(d_hist, nsym, d_len, d_code, stream or None)
+
+
+def sz3g_huffman_encode(d_codes: int, n: int, d_len: int, d_code: int, nsym: int, chunk: int, d_words: int,
+                        cap_words: int, d_chunk_words: int, stream: int = 0):
+    nw = _u64()
+    rc = load().sz3g_huffman_encode(d_codes, n, d_len, d_code, nsym, chunk, d_words, cap_words, d_chunk_words,
+                                    C.byref(nw), stream or None)
+    return rc, nw.value
+
+
+def sz3g_huffman_decode(d_words: int, n_words: int, d_chunk_words: int, chunk: int, d_len: int, nsym: int,
+                        d_codes: int, n: int, stream: int = 0) -> int:
+    return load().sz3g_huffman_decode(d_words, n_words, d_chunk_words, chunk, d_len, nsym, d_codes, n,
+                                      stream or None)
+
+
+# ---- torch-tensor helpers ----------------------------------------------------
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def params_for(x, eb, **kw) -> Params:
+    torch = _torch()
+    dtype = F32 if x.dtype == torch.float32 else F64
+    return make_params(tuple(x.shape), eb, dtype=dtype, **kw)
+
+
+def compress(x, p: Params, workspace=None, out=None, stream=None):
+    """Compress a contiguous CUDA tensor; returns a uint8 CUDA tensor (a view of `out`)."""
+    torch = _torch()
+    assert x.is_cuda and x.is_contiguous()
+    cap = sz3g_compress_bound(p)
+    if out is None:
+        out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+    ws, wsb = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) if workspace is not None else (0, 0)
+    rc, nb = sz3g_compress(p, x.data_ptr(), out.data_ptr(), out.numel(), ws, wsb, _stream_handle(stream))
+    _chk(rc, "sz3g_compress")
+    return out[:nb]
+
+
+def decompress(stream_bytes, out=None, workspace=None, stream=None):
+    """Decompress a uint8 CUDA tensor holding a stream; returns a flat tensor."""
+    torch = _torch()
+    assert stream_bytes.is_cuda and stream_bytes.dtype == torch.uint8
+    head = stream_bytes[:HEADER_BYTES].cpu().numpy().tobytes()
+    buf = C.create_string_buffer(head, len(head))
+    rc, p, n = sz3g_read_header(C.addressof(buf), stream_bytes.numel(), 0)
+    _chk(rc, "sz3g_read_header")
+    dt = torch.float32 if p.dtype == F32 else torch.float64
+    if out is None:
+        out = torch.empty(n, dtype=dt, device=stream_bytes.device)
+    ws, wsb = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) if workspace is not None else (0, 0)
+    rc = sz3g_decompress(stream_bytes.data_ptr(), stream_bytes.numel(), out.data_ptr(),
+                         out.numel() * out.element_size(), ws, wsb, _stream_handle(stream))
+    _chk(rc, "sz3g_decompress")
+    return out
+
+
+def workspace(p: Params, for_decompress: bool, device="cuda"):
+    torch = _torch()
+    n = sz3g_workspace_size(p, int(for_decompress))
+    return torch.empty(n, dtype=torch.uint8, device=device)
