@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Throughput of the SZ3-Interp hot path (multilevel interpolation + linear-
+scaling quantizer + histogram + chunked Huffman) on GB300.
+
+Workload: one 512^3 FP32 Gaussian random field with power spectrum ~ k^-3
+(unit variance, seed 2; a synthetic stand-in for NYX 512^3), REL error bound
+1e-3 (the bound of the paper's throughput figure), cubic interpolation, axis
+order (0,1,2), radius 32768, 4096-code Huffman chunks.  One step = compress
+the field and decompress the stream, i.e. every step of the hot path once.
+The 512 MiB input is larger than L2 (129 MB), so no flush is needed between
+steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sz3g|reference]
+
+--impl reference times the serial CPU oracle on the host cores, on a bounded
+sample (a 128^3 corner of the same field) per step.  N > 1 (torchrun) runs
+independent replicas, one per GPU: a single field does not shard without
+changing its result, so there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compress/decompress GB/s (input bytes) on 1 GB300 and % of HBM roofline, at stated eb"
+SIZE = 512
+EB = 1e-3
+SEED = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="sz3g", choices=["sz3g", "reference"])
+    ap.add_argument("--size", type=int, default=SIZE)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(n):
+    return {
+        "workload": f"{n}^3 FP32 k^-3 Gaussian random field (seed {SEED}), REL eb {EB:g}, cubic, order (0,1,2), "
+                    "radius 32768, 4096-code chunks; step = compress + decompress",
+        "dims": [n, n, n],
+        "dtype": "f32",
+        "eb_mode": "REL",
+        "eb": EB,
+        "interp": "cubic",
+        "radius": 32768,
+        "chunk_codes": 4096,
+        "l2": "inputs larger than L2 (512 MiB field vs 129 MB L2), no flush",
+    }
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(kernel: str, info: dict) -> float:
+    """Bytes a kernel must move per step, counting each input read and each
+    output written once (the figure the roofline fraction divides)."""
+    N, esz = info["N"], info["esz"]
+    coarse = info["coarse_points"]  # points of G_1 and coarser (recon pyramid)
+    payload = info["payload_bytes"]
+    unpred = info["n_unpred"] * esz
+    return {
+        "range": N * esz,
+        "pass_quantize": N * (esz + 2) + coarse * esz,
+        "level_quantize": info["level_quantize_bytes"],
+        "pass_recover": N * (2 + esz) + coarse * esz,
+        "level_recover": info["level_recover_bytes"],
+        "decode": payload + 2 * N,
+        "encode": 2 * N + payload + 2 * unpred,
+        "codebook": 65536 * 4 * 2,
+        "lift": 2 * coarse * esz,
+    }.get(kernel, float("nan"))
+
+
+def traffic_for(kernel: str):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json for the
+    current kernel sources, else None."""
+    try:
+        from paper_2111_02925_gb300 import build as B
+
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            d = json.load(fh)
+        e = d.get(kernel)
+        if e and e.get("source_stamp") == B._stamp():
+            return e.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle as O
+    from paper_2111_02925_gb300 import synthetic as S
+
+    O.build()
+    x = S.grf((args.size,) * 3, SEED)
+    m = min(128, args.size)
+    sample = np.ascontiguousarray(x[:m, :m, :m])
+    p = O.make_params(sample.shape, EB, eb_mode=O.REL, interp=O.CUBIC)
+    for _ in range(args.warmup):
+        O.decompress(O.compress(p, sample))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = O.compress(p, sample)
+        O.decompress(s)
+    dt = (time.perf_counter() - t0) / args.steps
+    gbs = sample.nbytes / dt / 1e9
+    cfg = workload_config(args.size)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{m}^3 corner of the {args.size}^3 field, compress + decompress per step"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(x):
+    import numpy as np
+
+    import oracle as O
+
+    O.build()
+    m = min(256, x.shape[0])
+    sample = np.ascontiguousarray(x[:m, :m, :m])
+    p = O.make_params(sample.shape, EB, eb_mode=O.REL, interp=O.CUBIC)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        O.decompress(O.compress(p, sample))
+        reps += 1
+        if time.perf_counter() - t0 > 8.0 or reps >= 3:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": sample.nbytes / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{m}^3 corner of the field, compress + decompress, {reps} run(s), one thread"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    from paper_2111_02925_gb300 import build as B
+    from paper_2111_02925_gb300 import synthetic as S
+    from paper_2111_02925_gb300 import sz3g as G
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B.build()
+    G.load()
+    n = args.size
+    x = S.grf((n, n, n), SEED)
+    xd = torch.from_numpy(x).to(dev)
+    p = G.make_params(x.shape, EB, eb_mode=G.REL, interp=G.CUBIC)
+    wsc, wsd = G.workspace(p, False, dev), G.workspace(p, True, dev)
+    out = torch.empty(G.sz3g_compress_bound(p), dtype=torch.uint8, device=dev)
+    y = torch.empty(x.size, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+
+    def step():
+        rc, nb = G.sz3g_compress(p, xd.data_ptr(), out.data_ptr(), out.numel(), wsc.data_ptr(), wsc.numel(), sh)
+        if rc:
+            raise G.SZ3GError(rc, "compress")
+        rc = G.sz3g_decompress(out.data_ptr(), nb, y.data_ptr(), y.numel() * 4, wsd.data_ptr(), wsd.numel(), sh)
+        if rc:
+            raise G.SZ3GError(rc, "decompress")
+        return nb
+
+    nb = 0
+    for _ in range(max(args.warmup, 3)):
+        nb = step()
+    torch.cuda.synchronize()
+    maxerr = float((y - xd.reshape(-1)).abs().max().item())
+    # timed region
+    clocks = Clocks(torch.cuda.current_device())
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.1)
+    G.sz3g_profile_enable(True)
+    launches0 = G.sz3g_launch_count()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    e[0].record(stream)
+    for k in range(args.steps):
+        rc, nbk = G.sz3g_compress(p, xd.data_ptr(), out.data_ptr(), out.numel(), wsc.data_ptr(), wsc.numel(), sh)
+        e[2 * k + 1].record(stream)
+        rc2 = G.sz3g_decompress(out.data_ptr(), nbk, y.data_ptr(), y.numel() * 4, wsd.data_ptr(), wsd.numel(), sh)
+        e[2 * k + 2].record(stream)
+        if rc or rc2:
+            raise RuntimeError(f"status {rc} {rc2}")
+    torch.cuda.synchronize()
+    launches = G.sz3g_launch_count() - launches0
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = e[0].elapsed_time(e[-1])
+    comp_ms = sum(e[2 * k].elapsed_time(e[2 * k + 1]) for k in range(args.steps)) / args.steps
+    dec_ms = sum(e[2 * k + 1].elapsed_time(e[2 * k + 2]) for k in range(args.steps)) / args.steps
+    step_ms = total_ms / args.steps
+    kern = {}
+    for name in G.sz3g_profile_kernel_names():
+        t, c = G.sz3g_profile_read(name)
+        if c:
+            kern[name] = (t / args.steps, c / args.steps)
+    G.sz3g_profile_enable(False)
+    if ws > 1:
+        t = torch.tensor([step_ms, comp_ms, dec_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms, comp_ms, dec_ms = [float(v) for v in t.tolist()]
+    in_bytes = x.nbytes
+    value = ws * in_bytes / (step_ms * 1e-3) / 1e9
+    # roofline of the dominant kernel
+    import struct
+
+    head = out[:288].cpu().numpy().tobytes()
+    n_unpred = struct.unpack_from("<Q", head, 88)[0]
+    n_words = struct.unpack_from("<Q", head, 104)[0]
+    coarse = sum(int(np.prod([-(-n // (1 << k))] * 3)) for k in range(1, 10))
+    g1 = int(np.prod([-(-n // 2)] * 3))
+    info = {"N": x.size, "esz": 4, "coarse_points": coarse, "payload_bytes": n_words * 4, "n_unpred": n_unpred,
+            "level_quantize_bytes": x.size * (4 + 2) + coarse * 4,
+            "level_recover_bytes": x.size * (2 + 4) + coarse * 4}
+    del g1
+    peak, peak_kind = peaks()
+    dom = max(kern.items(), key=lambda kv: kv[1][0]) if kern else None
+    roof = None
+    if dom:
+        name, (ms_per_step, l_per_step) = dom
+        byts = algorithmic_bytes(name, info)
+        ach = byts / (ms_per_step * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_kind": peak_kind, "traffic": traffic_for(name),
+                "launches_per_step": l_per_step, "ms_per_step": ms_per_step,
+                "algorithmic_bytes_per_step": byts}
+    # end to end through the host-buffer entry points (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.from_numpy(x).reshape(-1).pin_memory()
+        hs = torch.empty(out.numel(), dtype=torch.uint8).pin_memory()
+        hy = torch.empty(x.size, dtype=torch.float32).pin_memory()
+        ke = min(args.steps, 5)
+        nbh = 0
+        for _ in range(2):
+            rc, nbh = G.sz3g_compress_host(p, hx.data_ptr(), hs.data_ptr(), hs.numel(), sh)
+            G.sz3g_decompress_host(hs.data_ptr(), nbh, hy.data_ptr(), hy.numel() * 4, sh)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            rc, nbh = G.sz3g_compress_host(p, hx.data_ptr(), hs.data_ptr(), hs.numel(), sh)
+            rc2 = G.sz3g_decompress_host(hs.data_ptr(), nbh, hy.data_ptr(), hy.numel() * 4, sh)
+            if rc or rc2:
+                raise RuntimeError(f"host status {rc} {rc2}")
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / ke
+        e2e = {"value": ws * in_bytes / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": in_bytes + nbh,
+               "d2h_bytes_per_step": nbh + in_bytes, "ms_per_step": dt * 1e3}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(x)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(n),
+            "compress": {"ms": comp_ms, "GB/s": in_bytes / (comp_ms * 1e-3) / 1e9,
+                         "frac_of_hbm_algorithmic": (in_bytes * 2 + nb) / (comp_ms * 1e-3) / 1e9 / peak},
+            "decompress": {"ms": dec_ms, "GB/s": in_bytes / (dec_ms * 1e-3) / 1e9,
+                           "frac_of_hbm_algorithmic": (in_bytes + nb) / (dec_ms * 1e-3) / 1e9 / peak},
+            "compression_ratio": in_bytes / nb, "max_abs_error": maxerr, "stream_bytes": nb,
+            "roofline": roof, "kernels_ms_per_step": {k: v[0] for k, v in sorted(kern.items())},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -101,9 +101,9 @@ int sz3g_workspace_size(const sz3g_params* p, int for_decompress, size_t* bytes)
  * (linear-scaling quantizer, Sec. 3.2) every point, save the unpredictable
  * values, histogram the codes, build a Huffman code from the histogram and
  * encode the codes (Sec. 3.2 Encoder), chunk by chunk.
- *   d_in         N values of T (device, 8-byte aligned), not modified.
+ *   d_in         N values of T (device, 16-byte aligned), not modified.
  *   d_out        device buffer of out_capacity bytes (>= sz3g_compress_bound
- *                is always enough), 8-byte aligned.  Receives the stream.
+ *                is always enough), 16-byte aligned.  Receives the stream.
  *   out_bytes    host; receives the stream length.  This needs the result of
  *                the GPU work, so the call synchronises `stream` before return.
  * Errors: SZ3G_E_INVAL, SZ3G_E_NONFINITE, SZ3G_E_ZERO_RANGE_REL,
@@ -126,8 +126,8 @@ int sz3g_read_header(const void* stream, size_t bytes, int stream_on_device, sz3
  * Decompress one stream: decode the chunks, then recover every point in the
  * traversal order of the compressor (recover(), Sec. 3.2; decode(), Sec. 3.2
  * Encoder).
- *   d_stream     device, `bytes` long, 8-byte aligned.
- *   d_out        device, out_capacity >= N * sizeof(T) bytes, 8-byte aligned.
+ *   d_stream     device, `bytes` long, 16-byte aligned.
+ *   d_out        device, out_capacity >= N * sizeof(T) bytes, 16-byte aligned.
  * Reads the header to the host first (synchronous) and synchronises `stream`
  * at the end to report decode errors.
  * Errors: SZ3G_E_CORRUPT, SZ3G_E_CAPACITY, SZ3G_E_INVAL, SZ3G_E_TIMEOUT,
@@ -208,6 +208,26 @@ int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_le
 int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_t* d_chunk_words,
                         uint32_t chunk, const uint8_t* d_len, uint32_t nsym, uint16_t* d_codes,
                         uint64_t n, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics (no counterpart in the paper): launch accounting and per-kernel
+ * timing with CUDA events, used by the benchmark to attribute time to kernels.
+ * ------------------------------------------------------------------------- */
+
+/* Total kernel launches issued by the library since it was loaded. */
+int sz3g_launch_count(uint64_t* launches);
+
+/* on != 0: from now on bracket every launch with CUDA events on its stream
+ * (and drop earlier records); on == 0: stop recording.  Host-side only. */
+int sz3g_profile_enable(int on);
+
+/* Sum of the recorded durations of one kernel (name from
+ * sz3g_profile_kernel_name) and the number of recorded launches.  Waits for
+ * the recorded events.  SZ3G_E_INVAL for an unknown name. */
+int sz3g_profile_read(const char* kernel, double* total_ms, uint64_t* launches);
+
+/* Name of kernel `index` (0, 1, ...), or NULL past the last one. */
+const char* sz3g_profile_kernel_name(int index);
 
 #ifdef __cplusplus
 }

@@ -59,7 +59,8 @@ CompressWs compress_layout(const Plan& pl) {
   w.wstat = l.take(pl.n_chunks * 8);
   w.zstat = l.take(pl.n_chunks * 8);
   w.codes = l.take(pl.N * 2);
-  for (int k = 0; k <= pl.L; ++k) w.R[k] = l.take(pl.gsize[k] * pl.esz);
+  // the fused level path never stores the finest grid's reconstruction
+  for (int k = level_path_ok(pl) ? 1 : 0; k <= pl.L; ++k) w.R[k] = l.take(pl.gsize[k] * pl.esz);
   w.total = l.off;
   return w;
 }
@@ -263,7 +264,7 @@ int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t ou
   SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.codes, s));  // state, histogram, tables, look-back status
   SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s));
   void* R[34];
-  for (int k = 0; k <= pl.L; ++k) R[k] = ws + L.R[k];
+  for (int k = 0; k <= pl.L; ++k) R[k] = (k == 0 && level_path_ok(pl)) ? nullptr : ws + L.R[k];
   uint16_t* codes = (uint16_t*)(ws + L.codes);
   uint32_t* hist = (uint32_t*)(ws + L.hist);
   uint32_t* table = (uint32_t*)(ws + L.table);
@@ -398,7 +399,7 @@ int sz3g_predict_quantize(const sz3g_params* p, const void* d_in, uint16_t* d_co
   SZ3G_CUDA(cudaMemsetAsync(d_hist, 0, kSyms * 4, s));
   SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s));
   void* R[34];
-  for (int k = 0; k <= pl.L; ++k) R[k] = ws + L.R[k];
+  for (int k = 0; k <= pl.L; ++k) R[k] = (k == 0 && level_path_ok(pl)) ? nullptr : ws + L.R[k];
   SZ3G_TRY(launch_quantize_levels(pl, d_in, d_codes, R, d_hist, st, s));
   PassMap map;
   make_pass_map(pl, &map);

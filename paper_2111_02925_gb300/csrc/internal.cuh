@@ -94,6 +94,32 @@ struct Plan {
   uint32_t nsub;             // 256-code sub-blocks per chunk (decoder)
 };
 
+// Kernels known to the launch accounting (names in prof.cu).
+enum KernelId {
+  kKRange, kKEb, kKAnchor, kKLift, kKPassQuantize, kKPassRecover, kKCodebook, kKEncode, kKFinalize,
+  kKDecodeTables, kKDecode, kKScan, kKZeroCount, kKPackTable, kKLevelQuantize, kKLevelRecover,
+  kKCoarseQuantize, kKCoarseRecover, kKernelCount
+};
+
+// Counts a launch and, while profiling is on, brackets it with CUDA events.
+class LaunchScope {
+ public:
+  LaunchScope(int kid, cudaStream_t s);
+  ~LaunchScope();
+  LaunchScope(const LaunchScope&) = delete;
+  LaunchScope& operator=(const LaunchScope&) = delete;
+
+ private:
+  int kid_;
+  cudaStream_t s_;
+  void* a_;
+};
+#define SZ3G_LAUNCH(kid, s, ...)                    \
+  do {                                              \
+    ::sz3g::LaunchScope sz3g_launch_scope_((kid), (s)); \
+    __VA_ARGS__;                                    \
+  } while (0)
+
 // Builds the plan; returns SZ3G_OK or SZ3G_E_INVAL.  Shared by all entry points.
 int make_plan(const sz3g_params* p, Plan* plan);
 void make_pass_map(const Plan& plan, PassMap* map);
@@ -204,6 +230,14 @@ int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unp
                           unsigned long long n_unpred, const unsigned long long* zbase, const uint32_t* zsub,
                           void* const* R, void* d_out, DevState* st, unsigned long long ebT_bits,
                           cudaStream_t s);
+
+// k_level.cu (fields of rank <= 3)
+bool level_path_ok(const Plan& pl);
+int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
+                          DevState* st, cudaStream_t s);
+int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
+                         const unsigned long long* zbase, const uint32_t* zsub, void* const* R, void* d_out,
+                         DevState* st, unsigned long long ebT_bits, cudaStream_t s);
 
 // k_huffman.cu
 size_t codebook_scratch_bytes();

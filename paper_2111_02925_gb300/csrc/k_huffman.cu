@@ -254,8 +254,8 @@ int launch_codebook(const uint32_t* hist, uint32_t nsym, uint32_t* table, uint8_
   if (cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) !=
       cudaSuccess)
     return SZ3G_E_CUDA;
-  codebook_kernel<<<1, kCbThreads, kCbSmem, s>>>(hist, nsym, table, len_out, code_out, st, (CbGlobal*)scratch, d_out,
-                                                 out_capacity, esz);
+  SZ3G_LAUNCH(kKCodebook, s, codebook_kernel<<<1, kCbThreads, kCbSmem, s>>>(hist, nsym, table, len_out, code_out, st, (CbGlobal*)scratch, d_out,
+                                                 out_capacity, esz));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
@@ -514,9 +514,9 @@ int launch_encode_impl(const EncArgs& a, const PassMap* map, cudaStream_t s) {
   if (nb > 152 * 8) nb = 152 * 8;
   if (nb < 1) nb = 1;
   if (a.esz == 4)
-    encode_kernel<uint32_t><<<nb, kEncWarps * 32, 0, s>>>(a, *map);
+    SZ3G_LAUNCH(kKEncode, s, encode_kernel<uint32_t><<<nb, kEncWarps * 32, 0, s>>>(a, *map));
   else
-    encode_kernel<unsigned long long><<<nb, kEncWarps * 32, 0, s>>>(a, *map);
+    SZ3G_LAUNCH(kKEncode, s, encode_kernel<unsigned long long><<<nb, kEncWarps * 32, 0, s>>>(a, *map));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
@@ -647,7 +647,7 @@ int launch_finalize(const Plan& pl, const sz3g_params* p, DevState* st, unsigned
   for (int i = 0; i < 4; ++i) b[272 + i] = i < (int)p->ndim ? p->dim_order[i] : 0;
   h.n_chunks = pl.n_chunks;
   h.esz = pl.esz;
-  finalize_kernel<<<1, 64, 0, s>>>(h, st, d_out, out_capacity);
+  SZ3G_LAUNCH(kKFinalize, s, finalize_kernel<<<1, 64, 0, s>>>(h, st, d_out, out_capacity));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
@@ -879,7 +879,7 @@ int launch_decode_tables(const unsigned char* tab, uint32_t n_used, const uint8_
   if (cudaFuncSetAttribute(decode_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem) !=
       cudaSuccess)
     return SZ3G_E_CUDA;
-  decode_tables_kernel<<<1, kCbThreads, kDecSmem, s>>>(tab, n_used, len, nsym, (DecTables*)tables, st);
+  SZ3G_LAUNCH(kKDecodeTables, s, decode_tables_kernel<<<1, kCbThreads, kDecSmem, s>>>(tab, n_used, len, nsym, (DecTables*)tables, st));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
@@ -889,7 +889,7 @@ int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, cons
                          unsigned long long* woff, uint16_t* codes, uint32_t* zchunk, uint32_t* zsub, uint32_t nsub,
                          DevState* st, cudaStream_t s) {
   const uint32_t maxw = (uint32_t)(((unsigned long long)chunk * SZ3G_LMAX + 31) / 32);
-  scan_u32_kernel<<<1, kCbThreads, 0, s>>>(chunk_words, n_chunks, woff, nullptr, maxw, n_words, 1, st);
+  SZ3G_LAUNCH(kKScan, s, scan_u32_kernel<<<1, kCbThreads, 0, s>>>(chunk_words, n_chunks, woff, nullptr, maxw, n_words, 1, st));
   DecArgs a{};
   a.words = words;
   a.woff = woff;
@@ -903,7 +903,7 @@ int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, cons
   a.zchunk = zchunk;
   a.zsub = zsub;
   a.st = st;
-  decode_kernel<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(a);
+  SZ3G_LAUNCH(kKDecode, s, decode_kernel<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(a));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
@@ -925,13 +925,13 @@ __global__ void zero_count_kernel(const uint16_t* codes, unsigned long long n, u
 
 int launch_zero_counts(const uint16_t* codes, unsigned long long n, uint32_t chunk, uint32_t nsub,
                        unsigned long long n_chunks, uint32_t* zchunk, uint32_t* zsub, cudaStream_t s) {
-  zero_count_kernel<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(codes, n, chunk, nsub, n_chunks, zchunk, zsub);
+  SZ3G_LAUNCH(kKZeroCount, s, zero_count_kernel<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(codes, n, chunk, nsub, n_chunks, zchunk, zsub));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
 int launch_scan_u32(const uint32_t* in, unsigned long long n, unsigned long long* out, unsigned long long* total,
                     unsigned long long expect, int check_expect, DevState* st, cudaStream_t s) {
-  scan_u32_kernel<<<1, kCbThreads, 0, s>>>(in, n, out, total, 0, expect, check_expect, st);
+  SZ3G_LAUNCH(kKScan, s, scan_u32_kernel<<<1, kCbThreads, 0, s>>>(in, n, out, total, 0, expect, check_expect, st));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
@@ -942,7 +942,7 @@ __global__ void pack_table_kernel(const uint8_t* len, const uint32_t* code, uint
 }
 
 int launch_pack_table(const uint8_t* len, const uint32_t* code, uint32_t nsym, uint32_t* table, cudaStream_t s) {
-  pack_table_kernel<<<kSyms / 256, 256, 0, s>>>(len, code, nsym, table);
+  SZ3G_LAUNCH(kKPackTable, s, pack_table_kernel<<<kSyms / 256, 256, 0, s>>>(len, code, nsym, table));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 

@@ -129,15 +129,15 @@ int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratc
     unsigned long long want = (pl.N + kRangeThreads * 8 - 1) / (kRangeThreads * 8);
     nparts = (int)(want < kRangeBlocks ? (want ? want : 1) : kRangeBlocks);
     if (pl.dtype == SZ3G_F32)
-      range_partial_kernel<float><<<nparts, kRangeThreads, 0, s>>>((const float*)d_in, pl.N, (float*)scratch, st);
+      SZ3G_LAUNCH(kKRange, s, range_partial_kernel<float><<<nparts, kRangeThreads, 0, s>>>((const float*)d_in, pl.N, (float*)scratch, st));
     else
-      range_partial_kernel<double><<<nparts, kRangeThreads, 0, s>>>((const double*)d_in, pl.N, (double*)scratch,
-                                                                     st);
+      SZ3G_LAUNCH(kKRange, s, range_partial_kernel<double><<<nparts, kRangeThreads, 0, s>>>((const double*)d_in, pl.N, (double*)scratch,
+                                                                     st));
   }
   if (pl.dtype == SZ3G_F32)
-    eb_kernel<float><<<1, 32, 0, s>>>((const float*)scratch, nparts, eb_mode, eb, st);
+    SZ3G_LAUNCH(kKEb, s, eb_kernel<float><<<1, 32, 0, s>>>((const float*)scratch, nparts, eb_mode, eb, st));
   else
-    eb_kernel<double><<<1, 32, 0, s>>>((const double*)scratch, nparts, eb_mode, eb, st);
+    SZ3G_LAUNCH(kKEb, s, eb_kernel<double><<<1, 32, 0, s>>>((const double*)scratch, nparts, eb_mode, eb, st));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
@@ -342,22 +342,22 @@ static void lift(const Plan& pl, int k, const T* Rc, T* Rf, cudaStream_t s) {
   const unsigned long long* mf = pl.gm[k];
   const unsigned long long fs2 = mf[3], fs1 = fs2 * mf[2], fs0 = fs1 * mf[1];
   const unsigned long long nc = pl.gsize[k + 1];
-  lift_kernel<T><<<grid_for(nc, 256), 256, 0, s>>>(Rc, Rf, nc, (uint32_t)mc[1], (uint32_t)mc[2], (uint32_t)mc[3], fs0,
-                                                   fs1, fs2);
+  SZ3G_LAUNCH(kKLift, s, lift_kernel<T><<<grid_for(nc, 256), 256, 0, s>>>(Rc, Rf, nc, (uint32_t)mc[1], (uint32_t)mc[2], (uint32_t)mc[3], fs0,
+                                                   fs1, fs2));
 }
 
 template <typename T>
 static int quantize_levels_t(const Plan& pl, const T* x, uint16_t* codes, void* const* R, uint32_t* hist,
                              DevState* st, cudaStream_t s) {
-  anchor_quantize_kernel<T><<<1, 32, 0, s>>>(x, codes, (T*)R[pl.L], hist, st, (int)pl.radius);
+  SZ3G_LAUNCH(kKAnchor, s, anchor_quantize_kernel<T><<<1, 32, 0, s>>>(x, codes, (T*)R[pl.L], hist, st, (int)pl.radius));
   int pi = 0;
   for (int l = pl.L; l >= 1; --l) {
     const int k = l - 1;
     lift<T>(pl, k, (const T*)R[k + 1], (T*)R[k], s);
     for (; pi < pl.n_pass && pl.pass[pi].grid == k; ++pi) {
       const PassDesc& pd = pl.pass[pi];
-      pass_quantize_kernel<T><<<grid_for(pd.count, 256), 256, 0, s>>>(pd, x, (T*)R[k], codes, hist, st,
-                                                                      (int)pl.radius);
+      SZ3G_LAUNCH(kKPassQuantize, s, pass_quantize_kernel<T><<<grid_for(pd.count, 256), 256, 0, s>>>(pd, x, (T*)R[k], codes, hist, st,
+                                                                      (int)pl.radius));
     }
   }
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
@@ -365,6 +365,7 @@ static int quantize_levels_t(const Plan& pl, const T* x, uint16_t* codes, void* 
 
 int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
                            DevState* st, cudaStream_t s) {
+  if (level_path_ok(pl)) return launch_quantize_fused(pl, d_in, codes, R, hist, st, s);
   if (pl.dtype == SZ3G_F32) return quantize_levels_t<float>(pl, (const float*)d_in, codes, R, hist, st, s);
   return quantize_levels_t<double>(pl, (const double*)d_in, codes, R, hist, st, s);
 }
@@ -374,7 +375,7 @@ static int recover_levels_t(const Plan& pl, const uint16_t* codes, const T* unpr
                             const unsigned long long* zbase, const uint32_t* zsub, void* const* R, T* out,
                             DevState* st, T ebT, cudaStream_t s) {
   T* top = pl.L == 0 ? out : (T*)R[pl.L];
-  anchor_recover_kernel<T><<<1, 32, 0, s>>>(codes, unpred, n_unpred, top, st, (int)pl.radius, ebT);
+  SZ3G_LAUNCH(kKAnchor, s, anchor_recover_kernel<T><<<1, 32, 0, s>>>(codes, unpred, n_unpred, top, st, (int)pl.radius, ebT));
   int pi = 0;
   for (int l = pl.L; l >= 1; --l) {
     const int k = l - 1;
@@ -382,9 +383,9 @@ static int recover_levels_t(const Plan& pl, const uint16_t* codes, const T* unpr
     lift<T>(pl, k, (const T*)R[k + 1], Rf, s);
     for (; pi < pl.n_pass && pl.pass[pi].grid == k; ++pi) {
       const PassDesc& pd = pl.pass[pi];
-      pass_recover_kernel<T><<<grid_for(pd.count, 256), 256, 0, s>>>(pd, codes, unpred, n_unpred, zbase, zsub,
+      SZ3G_LAUNCH(kKPassRecover, s, pass_recover_kernel<T><<<grid_for(pd.count, 256), 256, 0, s>>>(pd, codes, unpred, n_unpred, zbase, zsub,
                                                                      pl.chunk, pl.nsub, Rf, st, (int)pl.radius,
-                                                                     ebT);
+                                                                     ebT));
     }
   }
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
@@ -393,6 +394,7 @@ static int recover_levels_t(const Plan& pl, const uint16_t* codes, const T* unpr
 int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
                           const unsigned long long* zbase, const uint32_t* zsub, void* const* R, void* d_out,
                           DevState* st, unsigned long long ebT_bits, cudaStream_t s) {
+  if (level_path_ok(pl)) return launch_recover_fused(pl, codes, unpred, n_unpred, zbase, zsub, R, d_out, st, ebT_bits, s);
   if (pl.dtype == SZ3G_F32) {
     float e;
     uint32_t b = (uint32_t)ebT_bits;

@@ -1,0 +1,855 @@
+// k_level.cu -- fused level kernels for fields of rank <= 3 (coordinates
+// padded to 3 axes).
+//
+// level_kernel: one launch per grid G_k that is larger than the coarse group.
+// A persistent CTA walks the tiles of G_k; for each tile it stages in shared
+// memory a box V holding the input values (compress) and the coarse
+// reconstruction R_{k+1} (all-even points), runs every pass of the level on the
+// box (the tile plus the halo points whose reconstruction later passes read),
+// writes the codes of the tile's own points in traversal order, and writes the
+// tile of R_k that the next finer level reads.  Decompress is the same walk
+// with codes read instead of computed.
+//
+// Halos: the last pass reads neighbours at +-1 and +-3 along its axis; those
+// points belong to earlier passes, so a pass p is evaluated on the tile
+// extended by 2 (low) / 3 (high) along the axes of the passes after p, and the
+// first pass reads coarse points up to 3 away along its own axis, so the box
+// spans the tile plus that halo on every refined axis.  It is staged with
+// cp.async copies (all in flight at once), only at the points some pass reads.
+// Halo points are evaluated redundantly with the same arithmetic and never
+// written.
+//
+// coarse_kernel: one CTA evaluates every level whose grid has at most
+// kCoarseMax points, in traversal order, on a shared-memory copy of the
+// coarsest such grid G_kc (strided in place), then writes R_kc.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "internal.cuh"
+
+namespace sz3g {
+
+constexpr int kLevelThreads = 256;
+constexpr int kHistWin = 2048;  // shared-memory histogram window around the radius
+constexpr uint32_t kNone = 0xffffffffu;
+
+struct LevelDesc {
+  int k, P, interp, write_out;
+  int ax[3];      // axis of pass p
+  int pos[3];     // order position of axis d, -1 for a unit axis
+  int m[3];       // extents of G_k
+  int B[3];       // tile extents
+  int nt[3];      // tiles per axis
+  int vext[3], vlo[3];  // box extent and low halo per axis
+  uint32_t ntiles;
+  uint32_t off[3];      // first code of each pass
+  uint32_t E[3][3];     // pass lattice extents
+  uint32_t xs[3];       // input stride of one G_k step
+  uint32_t rs[3];       // strides of the output grid (R_k or the field)
+  uint32_t rcs[3];      // strides of R_{k+1} (rcs[2] == 1)
+  uint32_t chunk, nsub;
+  // tensor-copy staging
+  int xb0_tile;         // input box spans only the tile along axis 0
+  int cw[3];            // coarse box extents (compact), cw[2] a multiple of 16 bytes
+  int calign;           // coarse box start alignment along axis 2 (elements)
+  uint32_t smem_c, smem_h, smem_bar;  // byte offsets of the coarse box, histogram, barrier
+};
+
+template <typename T>
+struct LevelArgs {
+  const T* x;          // compress: input field
+  const T* Rc;         // R_{k+1}
+  T* Rout;             // R_k, or the field on decompress at k = 0
+  uint16_t* codes;
+  uint32_t* hist;
+  DevState* st;
+  const T* unpred;     // decompress
+  unsigned long long n_unpred;
+  const unsigned long long* zbase;
+  const uint32_t* zsub;
+  int radius;
+  T ebT;               // decompress (compress reads the device state)
+};
+
+// Asynchronous 4- or 8-byte global -> shared copy.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst_smem, const T* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// ---- tensor copies (TMA) ----------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          (uint32_t)__cvta_generic_to_shared(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"((uint32_t)__cvta_generic_to_shared(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+constexpr int kWaitLimit = 1 << 22;  // bounded wait on a tensor copy
+
+__device__ __forceinline__ unsigned long long rank_of_zero(const uint16_t* codes, unsigned long long i, uint32_t chunk,
+                                                           uint32_t nsub, const unsigned long long* zbase,
+                                                           const uint32_t* zsub) {
+  const unsigned long long c = i / chunk;
+  const unsigned long long r = i - c * chunk;
+  const unsigned long long b = r >> 8;
+  unsigned long long rank = zbase[c] + zsub[c * nsub + b];
+  for (unsigned long long q = c * chunk + (b << 8); q < i; ++q) rank += codes[q] == 0;
+  return rank;
+}
+
+__device__ __forceinline__ int floor_to(int v, int a) {  // a power of two
+  return v & ~(a - 1);
+}
+
+// Work on a box region is distributed as (row, 32-wide segment) items over the
+// warps of the CTA: lanes run along axis 2, the contiguous axis.  A pass
+// handles kUnroll items per warp at a time: all their loads are issued before
+// any result is stored (the points a pass writes are never its own inputs).
+constexpr int kUnroll = 4;
+
+template <typename T, bool COMP, bool TMA, int INTERP>
+__global__ void __launch_bounds__(kLevelThreads) level_kernel(const LevelDesc d, const LevelArgs<T> a,
+                                                              const __grid_constant__ CUtensorMap tmx,
+                                                              const __grid_constant__ CUtensorMap tmc) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int vsize = d.vext[0] * d.vext[1] * d.vext[2];
+  T* V = reinterpret_cast<T*>(sm);
+  T* C = reinterpret_cast<T*>(sm + d.smem_c);
+  uint32_t* hwin = reinterpret_cast<uint32_t*>(sm + d.smem_h);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + d.smem_bar);
+  __shared__ unsigned long long s_nz;
+  __shared__ int s_bad, s_timeout;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kLevelThreads / 32;
+  DevState* st = a.st;
+  if (COMP && (st->flags & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound))) return;
+  if (!COMP && (st->flags & kFlagCorrupt)) return;
+  const T ebT = COMP ? bits_to<T>(st->ebT_bits) : a.ebT;
+  const T ebr = COMP ? bits_to<T>(st->ebr_bits) : T(0);
+  const int radius = a.radius;
+  const int hlo = radius - kHistWin / 2;
+  if (COMP)
+    for (int i = tid; i < kHistWin; i += kLevelThreads) hwin[i] = 0;
+  if (tid == 0) {
+    s_nz = 0;
+    s_bad = 0;
+    s_timeout = 0;
+    if (TMA) {
+      mbar_init(bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  unsigned int my_nz = 0;
+  bool my_bad = false;
+  const int ve1 = d.vext[1], ve2 = d.vext[2];
+  const int vs0 = ve1 * ve2;
+  const int m0 = d.m[0], m1 = d.m[1], m2 = d.m[2];
+  const int pos0 = d.pos[0], pos1 = d.pos[1], pos2 = d.pos[2];
+  uint32_t phase = 0;
+  (void)vsize;
+  __syncthreads();
+
+  for (uint32_t tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
+    const int t2 = (int)(tile % (uint32_t)d.nt[2]);
+    const int t1 = (int)((tile / (uint32_t)d.nt[2]) % (uint32_t)d.nt[1]);
+    const int t0 = (int)(tile / ((uint32_t)d.nt[2] * (uint32_t)d.nt[1]));
+    const int A0 = t0 * d.B[0], A1 = t1 * d.B[1], A2 = t2 * d.B[2];
+    const int E0 = min(A0 + d.B[0], m0), E1 = min(A1 + d.B[1], m1), E2 = min(A2 + d.B[2], m2);
+    const int lo0 = A0 - d.vlo[0], lo1 = A1 - d.vlo[1], lo2 = A2 - d.vlo[2];
+
+    if (TMA) {
+      // ---- stage with two tensor copies: the input box (compress) and the
+      //      coarse box of R_{k+1}; then spread the coarse values over V
+      const int cs0 = lo0 >> 1, cs1 = lo1 >> 1, cs2 = floor_to(lo2 >> 1, d.calign);
+      if (tid == 0) {
+        fence_proxy_async_smem();  // earlier generic writes to V / C precede the copies
+        const uint32_t cbytes = (uint32_t)(d.cw[0] * d.cw[1] * d.cw[2] * (int)sizeof(T));
+        const int xb0 = d.xb0_tile ? d.B[0] : d.vext[0];
+        const uint32_t xbytes = COMP ? (uint32_t)(xb0 * vs0 * (int)sizeof(T)) : 0u;
+        mbar_expect_tx(bar, cbytes + xbytes);
+        if (COMP) tma_load_3d(V + (d.xb0_tile ? d.vlo[0] * vs0 : 0), &tmx, lo2, lo1, d.xb0_tile ? A0 : lo0, bar);
+        tma_load_3d(C, &tmc, cs2, cs1, cs0, bar);
+      }
+      int spins = 0;
+      while (!mbar_try_wait(bar, phase)) {
+        if (++spins > kWaitLimit) {
+          s_timeout = 1;
+          break;
+        }
+      }
+      phase ^= 1u;
+      __syncthreads();
+      if (s_timeout) break;
+      // coarse values to the all-even positions of V
+      const int i0a = (max(lo0, 0) + 1) >> 1, i0b = min(lo0 + d.vext[0] - 1, m0 - 1) >> 1;
+      const int i1a = (max(lo1, 0) + 1) >> 1, i1b = min(lo1 + ve1 - 1, m1 - 1) >> 1;
+      const int i2a = (max(lo2, 0) + 1) >> 1, i2b = min(lo2 + ve2 - 1, m2 - 1) >> 1;
+      const int n2 = i2b - i2a + 1, n1 = i1b - i1a + 1, n0 = i0b - i0a + 1;
+      const int cst1 = d.cw[2], cst0 = d.cw[1] * d.cw[2];
+      if (n0 > 0 && n1 > 0 && n2 > 0) {
+        const int nseg = (n2 + 31) >> 5;
+        const int items = n0 * n1 * nseg;
+        for (int it = warp; it < items; it += kWarps) {
+          const int r = it / nseg, seg = it - r * nseg;
+          const int q0 = r / n1, q1 = r - q0 * n1;
+          const int q2 = seg * 32 + lane;
+          if (q2 >= n2) continue;
+          const int i0 = i0a + q0, i1 = i1a + q1, i2 = i2a + q2;
+          V[(2 * i0 - lo0) * vs0 + (2 * i1 - lo1) * ve2 + (2 * i2 - lo2)] =
+              C[(i0 - cs0) * cst0 + (i1 - cs1) * cst1 + (i2 - cs2)];
+        }
+      }
+      __syncthreads();
+    } else {
+      // ---- stage with element copies, only the points some pass reads
+      const int nseg = (ve2 + 31) >> 5;
+      const int items = d.vext[0] * ve1 * nseg;
+      for (int it = warp; it < items; it += kWarps) {
+        const int r = it / nseg, seg = it - r * nseg;
+        const int b0 = r / ve1, b1 = r - b0 * ve1;
+        const int c0 = lo0 + b0, c1 = lo1 + b1;
+        if (c0 < 0 || c1 < 0 || c0 >= m0 || c1 >= m1) continue;
+        const int b2 = seg * 32 + lane;
+        const int c2 = lo2 + b2;
+        if (b2 >= ve2 || c2 < 0 || c2 >= m2) continue;
+        T* vp = V + r * ve2 + b2;
+        const bool odd01 = ((c0 | c1) & 1) != 0;
+        if (!odd01 && !(c2 & 1)) {
+          cp_async_elem(vp, a.Rc + ((uint32_t)(c0 >> 1) * d.rcs[0] + (uint32_t)(c1 >> 1) * d.rcs[1] +
+                                    (uint32_t)(c2 >> 1)));
+        } else if (COMP) {
+          // evaluated by pass p = the latest axis (in order) with an odd
+          // coordinate, on the tile range of the axes up to p
+          int p = -1;
+          if ((c0 & 1) && pos0 > p) p = pos0;
+          if ((c1 & 1) && pos1 > p) p = pos1;
+          if ((c2 & 1) && pos2 > p) p = pos2;
+          bool need = true;
+          if (pos0 >= 0 && pos0 <= p && (c0 < A0 || c0 >= E0)) need = false;
+          if (pos1 >= 0 && pos1 <= p && (c1 < A1 || c1 >= E1)) need = false;
+          if (pos2 >= 0 && pos2 <= p && (c2 < A2 || c2 >= E2)) need = false;
+          if (need) cp_async_elem(vp, a.x + ((uint32_t)c0 * d.xs[0] + (uint32_t)c1 * d.xs[1] + (uint32_t)c2 * d.xs[2]));
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
+
+    // ---- the passes of the level
+    for (int p = 0; p < d.P; ++p) {
+      const int ax = d.ax[p];
+      int s0[3], sp[3], cnt[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int pq = q == 0 ? pos0 : (q == 1 ? pos1 : pos2);
+        const int Aq = q == 0 ? A0 : (q == 1 ? A1 : A2);
+        const int Eq = q == 0 ? E0 : (q == 1 ? E1 : E2);
+        const bool ext = pq > p;  // axis refined by a later pass: halo of 2 below, 3 above
+        const int rlo = ext ? max(Aq - 2, 0) : Aq;
+        const int rhi = ext ? min(Aq + d.B[q] + 3, d.m[q]) : Eq;
+        int st0 = rlo, stp = 1;
+        if (q == ax) {
+          st0 = rlo | 1;
+          stp = 2;
+        } else if (ext || pq < 0) {
+          st0 = (rlo + 1) & ~1;
+          stp = 2;
+        }
+        s0[q] = st0;
+        sp[q] = stp;
+        cnt[q] = rhi > st0 ? (rhi - st0 + stp - 1) / stp : 0;
+      }
+      const int vst = ax == 2 ? 1 : (ax == 1 ? ve2 : vs0);
+      const int n_ax = d.m[ax];
+      // lattice coordinate per axis: c >> 1 on the pass axis and on later /
+      // unit axes, c on axes refined earlier in this level
+      const int sh0 = (pos0 >= 0 && pos0 < p) ? 0 : 1, sh1 = (pos1 >= 0 && pos1 < p) ? 0 : 1,
+                sh2 = (pos2 >= 0 && pos2 < p) ? 0 : 1;
+      const uint32_t PE1 = d.E[p][1], PE2 = d.E[p][2];
+      const uint32_t poff = d.off[p];
+      const int rows = cnt[0] * cnt[1];
+      const int c2first = s0[2], c2step = sp[2], n2 = cnt[2];
+      // row r of the region -> (j0, j1); warps take rows warp, warp + kWarps, ...
+      int j0 = cnt[1] ? warp / cnt[1] : 0, j1 = cnt[1] ? warp - j0 * cnt[1] : 0;
+      for (int r0 = warp; r0 < rows; r0 += kWarps * kUnroll) {
+        T pred[kUnroll], xv[kUnroll];
+        int vv[kUnroll];
+        uint32_t ci[kUnroll];
+        bool own[kUnroll], ok[kUnroll];
+        int rj0[kUnroll], rj1[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {  // rows r0 + u * kWarps
+          rj0[u] = j0;
+          rj1[u] = j1;
+          j1 += kWarps;
+          while (j1 >= cnt[1] && cnt[1] > 0) {
+            j1 -= cnt[1];
+            ++j0;
+          }
+        }
+        for (int j2b = 0; j2b < n2; j2b += 32) {
+          // phase 1: indices and loads
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            ok[u] = false;
+            own[u] = false;
+            vv[u] = 0;
+            ci[u] = 0;
+            pred[u] = T(0);
+            xv[u] = T(0);
+            const int j2 = j2b + lane;
+            if (r0 + u * kWarps < rows && j2 < n2) {
+              const int c0 = s0[0] + sp[0] * rj0[u], c1 = s0[1] + sp[1] * rj1[u];
+              const int c2 = c2first + c2step * j2;
+              const int v = (c0 - lo0) * vs0 + (c1 - lo1) * ve2 + (c2 - lo2);
+              const int i = ax == 0 ? c0 : (ax == 1 ? c1 : c2);
+              const bool hb = i + 1 < n_ax, hc = i >= 3, hd = i + 3 < n_ax;
+              const T va = V[v - vst];
+              const T vb = hb ? V[v + vst] : T(0);
+              const T vc = hc ? V[v - 3 * vst] : T(0);
+              const T vd = hd ? V[v + 3 * vst] : T(0);
+              pred[u] = interp_predict<T>(va, vb, vc, vd, hb, hc, hd, INTERP);
+              if (COMP) xv[u] = V[v];
+              ci[u] = poff + (((uint32_t)c0 >> sh0) * PE1 + ((uint32_t)c1 >> sh1)) * PE2 + ((uint32_t)c2 >> sh2);
+              own[u] = c0 >= A0 && c0 < E0 && c1 >= A1 && c1 < E1 && c2 >= A2 && c2 < E2;
+              vv[u] = v;
+              ok[u] = true;
+            }
+          }
+          // phase 2: quantize / recover, stores
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            if (!ok[u]) continue;
+            if (COMP) {
+              T rr;
+              const uint32_t code = quantize_point<T>(xv[u], pred[u], ebT, ebr, radius, rr);
+              V[vv[u]] = rr;
+              if (own[u]) {
+                a.codes[ci[u]] = (uint16_t)code;
+                my_nz += code == 0;
+                my_bad |= !isfinite(xv[u]);
+                const int b = (int)code - hlo;
+                if (b >= 0 && b < kHistWin) atomicAdd(&hwin[b], 1u);
+                else atomicAdd(&a.hist[code], 1u);
+              }
+            } else {
+              const uint32_t code = a.codes[ci[u]];
+              T rr;
+              if (code == 0) {
+                const unsigned long long rk = rank_of_zero(a.codes, ci[u], d.chunk, d.nsub, a.zbase, a.zsub);
+                if (rk < a.n_unpred) {
+                  rr = a.unpred[rk];
+                } else {
+                  rr = T(0);
+                  my_bad = true;
+                }
+              } else if (code >= 2u * (uint32_t)radius) {
+                rr = T(0);
+                my_bad = true;
+              } else {
+                rr = recover_point<T>(pred[u], code, radius, ebT);
+              }
+              V[vv[u]] = rr;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- write the tile of the output grid
+    if (d.write_out) {
+      const int w1 = E1 - A1, w2 = E2 - A2;
+      const int rows = (E0 - A0) * w1;
+      int q0 = warp / w1, q1 = warp - (warp / w1) * w1;
+      for (int r = warp; r < rows; r += kWarps) {
+        const int c0 = A0 + q0, c1 = A1 + q1;
+        T* dst = a.Rout + ((uint32_t)c0 * d.rs[0] + (uint32_t)c1 * d.rs[1] + (uint32_t)A2 * d.rs[2]);
+        const T* src = V + ((c0 - lo0) * vs0 + (c1 - lo1) * ve2 + (A2 - lo2));
+        for (int q2 = lane; q2 < w2; q2 += 32) dst[(uint32_t)q2 * d.rs[2]] = src[q2];
+        q1 += kWarps;
+        while (q1 >= w1) {
+          q1 -= w1;
+          ++q0;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- flush the per-CTA counters
+  if (my_nz) atomicAdd(&s_nz, (unsigned long long)my_nz);
+  if (my_bad) s_bad = 1;
+  __syncthreads();
+  if (TMA && s_timeout) {
+    // give an outstanding copy a last bounded chance to land before exiting
+    int spins = 0;
+    while (!mbar_try_wait(bar, phase ^ 1u) && ++spins < kWaitLimit) {
+    }
+    if (tid == 0) atomicOr(&st->flags, kFlagTimeout);
+  }
+  if (COMP) {
+    for (int i = tid; i < kHistWin; i += kLevelThreads)
+      if (hwin[i]) atomicAdd(&a.hist[hlo + i], hwin[i]);
+    if (tid == 0) {
+      if (s_nz) atomicAdd(&st->n_unpred, s_nz);
+      if (s_bad) atomicOr(&st->flags, kFlagNonFinite);
+    }
+  } else if (tid == 0 && s_bad) {
+    atomicOr(&st->flags, kFlagCorrupt);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coarse group: every level whose grid is small, one CTA.
+// ---------------------------------------------------------------------------
+constexpr int kCoarseThreads = 1024;
+constexpr int kCoarseMaxPasses = 96;
+
+struct CoarsePass {
+  unsigned long long off;
+  uint32_t count;
+  uint32_t E[3];
+  uint32_t start[3], step[3];
+  uint32_t m_ax;        // extent of the pass axis in G_grid
+  int ax, interp, scale_log;  // scale_log = grid - kc
+  unsigned long long xs[3];   // input strides of one G_grid step
+};
+
+struct CoarseDesc {
+  int n_pass, kc;
+  uint32_t mk[3];              // extents of G_kc
+  uint32_t gs[3];              // strides of G_kc (compact)
+  unsigned long long rs[3];    // strides of the output grid (R_kc or the field)
+  CoarsePass pass[kCoarseMaxPasses];
+  uint32_t chunk, nsub;
+};
+
+template <typename T, bool COMP>
+__global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc d, const LevelArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  T* R = reinterpret_cast<T*>(sm);
+  const int tid = threadIdx.x;
+  DevState* st = a.st;
+  if (COMP && (st->flags & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound))) return;
+  if (!COMP && (st->flags & kFlagCorrupt)) return;
+  const T ebT = COMP ? bits_to<T>(st->ebT_bits) : a.ebT;
+  const T ebr = COMP ? bits_to<T>(st->ebr_bits) : T(0);
+  const int radius = a.radius;
+  __shared__ unsigned int s_nz;
+  __shared__ int s_bad;
+  if (tid == 0) {
+    s_nz = 0;
+    s_bad = 0;
+    // anchor: point 0, prediction 0
+    T r;
+    if (COMP) {
+      const T xv = a.x[0];
+      const uint32_t code = quantize_point<T>(xv, T(0), ebT, ebr, radius, r);
+      a.codes[0] = (uint16_t)code;
+      atomicAdd(&a.hist[code], 1u);
+      if (code == 0) s_nz = 1;
+      if (!isfinite(xv)) s_bad = 1;
+    } else {
+      const uint32_t code = a.codes[0];
+      if (code == 0) {
+        if (a.n_unpred) {
+          r = a.unpred[0];
+        } else {
+          r = T(0);
+          s_bad = 1;
+        }
+      } else if (code >= 2u * (uint32_t)radius) {
+        r = T(0);
+        s_bad = 1;
+      } else {
+        r = recover_point<T>(T(0), code, radius, ebT);
+      }
+    }
+    R[0] = r;
+  }
+  __syncthreads();
+  for (int q = 0; q < d.n_pass; ++q) {
+    const CoarsePass& P = d.pass[q];
+    const uint32_t sc = 1u << P.scale_log;
+    const uint32_t vst = sc * d.gs[P.ax];
+    for (uint32_t j = tid; j < P.count; j += kCoarseThreads) {
+      const uint32_t j2 = j % P.E[2], j1 = (j / P.E[2]) % P.E[1], j0 = j / (P.E[2] * P.E[1]);
+      const uint32_t g0 = P.start[0] + P.step[0] * j0, g1 = P.start[1] + P.step[1] * j1,
+                     g2 = P.start[2] + P.step[2] * j2;
+      const uint32_t v = sc * (g0 * d.gs[0] + g1 * d.gs[1] + g2 * d.gs[2]);
+      const uint32_t i = P.ax == 0 ? g0 : (P.ax == 1 ? g1 : g2);
+      const bool hb = i + 1 < P.m_ax, hc = i >= 3, hd = i + 3 < P.m_ax;
+      const T va = R[v - vst];
+      const T vb = hb ? R[v + vst] : T(0);
+      const T vc = hc ? R[v - 3 * vst] : T(0);
+      const T vd = hd ? R[v + 3 * vst] : T(0);
+      const T pred = interp_predict<T>(va, vb, vc, vd, hb, hc, hd, P.interp);
+      const unsigned long long ci = P.off + j;
+      T r;
+      if (COMP) {
+        const T xv = a.x[(unsigned long long)g0 * P.xs[0] + (unsigned long long)g1 * P.xs[1] +
+                         (unsigned long long)g2 * P.xs[2]];
+        const uint32_t code = quantize_point<T>(xv, pred, ebT, ebr, radius, r);
+        a.codes[ci] = (uint16_t)code;
+        atomicAdd(&a.hist[code], 1u);
+        if (code == 0) atomicAdd(&s_nz, 1u);
+        if (!isfinite(xv)) s_bad = 1;
+      } else {
+        const uint32_t code = a.codes[ci];
+        if (code == 0) {
+          const unsigned long long rk = rank_of_zero(a.codes, ci, d.chunk, d.nsub, a.zbase, a.zsub);
+          if (rk < a.n_unpred) {
+            r = a.unpred[rk];
+          } else {
+            r = T(0);
+            s_bad = 1;
+          }
+        } else if (code >= 2u * (uint32_t)radius) {
+          r = T(0);
+          s_bad = 1;
+        } else {
+          r = recover_point<T>(pred, code, radius, ebT);
+        }
+      }
+      R[v] = r;
+    }
+    __syncthreads();
+  }
+  // write G_kc
+  const uint32_t tot = a.Rout ? d.mk[0] * d.mk[1] * d.mk[2] : 0u;
+  for (uint32_t f = tid; f < tot; f += kCoarseThreads) {
+    const uint32_t c2 = f % d.mk[2], c1 = (f / d.mk[2]) % d.mk[1], c0 = f / (d.mk[2] * d.mk[1]);
+    a.Rout[(unsigned long long)c0 * d.rs[0] + (unsigned long long)c1 * d.rs[1] + (unsigned long long)c2 * d.rs[2]] =
+        R[c0 * d.gs[0] + c1 * d.gs[1] + c2 * d.gs[2]];
+  }
+  if (tid == 0) {
+    if (COMP) {
+      if (s_nz) atomicAdd(&st->n_unpred, (unsigned long long)s_nz);
+      if (s_bad) atomicOr(&st->flags, kFlagNonFinite);
+    } else if (s_bad) {
+      atomicOr(&st->flags, kFlagCorrupt);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kCoarseMax = 4096;  // points of the largest coarse-group grid
+
+bool level_path_ok(const Plan& pl) { return pl.n[0] == 1; }  // rank <= 3
+
+int coarse_grid(const Plan& pl) {
+  int kc = pl.L;
+  while (kc > 0 && pl.gsize[kc - 1] <= kCoarseMax) --kc;
+  return kc;
+}
+
+static void tile_shape(const Plan& pl, int k, const int* pos, int* B) {
+  const unsigned long long* m = pl.gm[k];  // padded 4 axes; 3-D axes are 1..3
+  uint32_t want[3];
+  const int rank3 = (m[1] > 1) + (m[2] > 1) + (m[3] > 1);
+  // even extents (a tile starts on an even coordinate); along axis 2 the
+  // evaluated rows hold B/2 or B/2 + 3 points, close to a 32-lane multiple
+  if (rank3 <= 1) {
+    want[0] = want[1] = 1;
+    want[2] = 2048;
+  } else if (m[1] == 1) {
+    want[0] = 1;
+    want[1] = 32;
+    want[2] = 120;
+  } else {
+    want[0] = 4;
+    want[1] = 16;
+    want[2] = 56;
+  }
+  for (int q = 0; q < 3; ++q) {
+    const unsigned long long e = m[q + 1];
+    B[q] = e <= want[q] ? (int)e : (int)want[q];
+    (void)pos;
+  }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 3-D tensor map over a dense row-major grid (extents m0, m1, m2; axis 2
+// contiguous) with a box of b0 x b1 x b2 elements.
+template <typename T>
+static bool encode_map(CUtensorMap* map, const T* base, int m0, int m1, int m2, int b0, int b1, int b2) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)m2, (cuuint64_t)m1, (cuuint64_t)m0};
+  const cuuint64_t strides[2] = {(cuuint64_t)m2 * sizeof(T), (cuuint64_t)m1 * m2 * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)b2, (cuuint32_t)b1, (cuuint32_t)b0};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  return enc(map, dt, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static size_t up128(size_t x) { return (x + 127) & ~(size_t)127; }
+
+template <typename T, bool COMP>
+static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t s) {
+  LevelDesc d;
+  memset(&d, 0, sizeof(d));
+  d.k = k;
+  d.write_out = a.Rout != nullptr;
+  for (int q = 0; q < 3; ++q) {
+    d.m[q] = (int)pl.gm[k][q + 1];
+    d.pos[q] = -1;
+  }
+  int P = 0;
+  for (int i = 0; i < pl.n_pass; ++i) {
+    const PassDesc& pd = pl.pass[i];
+    if (pd.grid != k) continue;
+    d.ax[P] = pd.axis - 1;
+    d.pos[pd.axis - 1] = P;
+    d.off[P] = (uint32_t)pd.off;
+    for (int q = 0; q < 3; ++q) d.E[P][q] = pd.E[q + 1];
+    d.interp = pd.interp;
+    ++P;
+  }
+  d.P = P;
+  if (P == 0) return SZ3G_OK;
+  tile_shape(pl, k, d.pos, d.B);
+  const unsigned long long* mc = pl.gm[k + 1];
+  const int mc0 = (int)mc[1], mc1 = (int)mc[2], mc2 = (int)mc[3];
+  const int esz = (int)sizeof(T), al = 16 / esz;
+  // tensor copies: the coarse grid rows (and, on compress, the input rows of a
+  // finest-level grid) must be 16-byte multiples, the box start along axis 2
+  // a 16-byte boundary (tile starts are multiples of `al`)
+  bool tma = (size_t)mc2 * esz % 16 == 0 && (size_t)mc1 * mc2 * esz % 16 == 0 && d.B[2] % al == 0 &&
+             ((uintptr_t)a.Rc % 16) == 0 && tensor_map_encoder() != nullptr;
+  if (COMP)
+    tma = tma && k == 0 && (size_t)d.m[2] * esz % 16 == 0 && (size_t)d.m[1] * d.m[2] * esz % 16 == 0 &&
+          ((uintptr_t)a.x % 16) == 0;
+  // a tensor-copy box has at most 256 elements per dimension
+  for (int q = 0; q < 3; ++q) tma = tma && d.B[q] + 8 <= 256;
+  d.ntiles = 1;
+  for (int q = 0; q < 3; ++q) {
+    d.nt[q] = (d.m[q] + d.B[q] - 1) / d.B[q];
+    d.ntiles *= (uint32_t)d.nt[q];
+    const bool refined = d.pos[q] >= 0;
+    if (q == 2 && refined && tma) {
+      d.vlo[q] = 4;  // box start on a 16-byte boundary
+      d.vext[q] = d.B[q] + 8;
+    } else {
+      d.vlo[q] = refined ? 2 : 0;
+      d.vext[q] = d.B[q] + (refined ? 5 : 0);
+    }
+    d.xs[q] = (uint32_t)(pl.fstride[q + 1] << k);
+  }
+  d.rcs[2] = 1;
+  d.rcs[1] = (uint32_t)mc2;
+  d.rcs[0] = (uint32_t)mc2 * (uint32_t)mc1;
+  if (k == 0 && !COMP) {
+    for (int q = 0; q < 3; ++q) d.rs[q] = (uint32_t)pl.fstride[q + 1];
+  } else {
+    d.rs[2] = 1;
+    d.rs[1] = (uint32_t)pl.gm[k][3];
+    d.rs[0] = (uint32_t)(pl.gm[k][3] * pl.gm[k][2]);
+  }
+  d.chunk = pl.chunk;
+  d.nsub = pl.nsub;
+  const size_t vbytes = (size_t)d.vext[0] * d.vext[1] * d.vext[2] * esz;
+  CUtensorMap tmx, tmc;
+  memset(&tmx, 0, sizeof(tmx));
+  memset(&tmc, 0, sizeof(tmc));
+  size_t cbytes = 0;
+  if (tma) {
+    d.calign = al;
+    for (int q = 0; q < 2; ++q) d.cw[q] = ((d.vext[q] - 1) >> 1) + 1;
+    d.cw[2] = (((d.vext[2] - 1) >> 1) + 1 + al - 1 + al - 1) / al * al;
+    cbytes = (size_t)d.cw[0] * d.cw[1] * d.cw[2] * esz;
+    const size_t plane = (size_t)d.vext[1] * d.vext[2] * esz;
+    d.xb0_tile = d.pos[0] == 0 && (plane * d.vlo[0]) % 128 == 0;
+    const int xb0 = d.xb0_tile ? d.B[0] : d.vext[0];
+    bool okm = encode_map<T>(&tmc, a.Rc, mc0, mc1, mc2, d.cw[0], d.cw[1], d.cw[2]);
+    if (COMP) okm = okm && encode_map<T>(&tmx, a.x, d.m[0], d.m[1], d.m[2], xb0, d.vext[1], d.vext[2]);
+    if (!okm) return SZ3G_E_CUDA;
+  }
+  d.smem_c = (uint32_t)up128(vbytes);
+  d.smem_h = (uint32_t)up128(d.smem_c + cbytes);
+  d.smem_bar = (uint32_t)(d.smem_h + (COMP ? kHistWin * 4 : 0));
+  const size_t smem = d.smem_bar + 16;
+  auto kern = tma ? (d.interp == SZ3G_CUBIC ? level_kernel<T, COMP, true, SZ3G_CUBIC>
+                                            : level_kernel<T, COMP, true, SZ3G_LINEAR>)
+                  : (d.interp == SZ3G_CUBIC ? level_kernel<T, COMP, false, SZ3G_CUBIC>
+                                            : level_kernel<T, COMP, false, SZ3G_LINEAR>);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return SZ3G_E_CUDA;
+  int dev = 0, nsm = 152, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kLevelThreads, smem);
+  if (per < 1) per = 1;
+  unsigned long long grid = (unsigned long long)nsm * per;
+  if (grid > d.ntiles) grid = d.ntiles;
+  SZ3G_LAUNCH(COMP ? kKLevelQuantize : kKLevelRecover, s,
+              kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(d, a, tmx, tmc));
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+template <typename T, bool COMP>
+static int run_coarse(const Plan& pl, int kc, const LevelArgs<T>& a, cudaStream_t s) {
+  CoarseDesc d;
+  memset(&d, 0, sizeof(d));
+  d.kc = kc;
+  for (int q = 0; q < 3; ++q) d.mk[q] = (uint32_t)pl.gm[kc][q + 1];
+  d.gs[2] = 1;
+  d.gs[1] = d.mk[2];
+  d.gs[0] = d.mk[2] * d.mk[1];
+  if (kc == 0 && !COMP) {
+    for (int q = 0; q < 3; ++q) d.rs[q] = pl.fstride[q + 1];
+  } else {
+    for (int q = 0; q < 3; ++q) d.rs[q] = d.gs[q];
+  }
+  int n = 0;
+  for (int i = 0; i < pl.n_pass; ++i) {
+    const PassDesc& pd = pl.pass[i];
+    if (pd.grid < kc) continue;
+    if (n >= kCoarseMaxPasses) return SZ3G_E_INVAL;
+    CoarsePass& c = d.pass[n++];
+    c.off = pd.off;
+    c.count = (uint32_t)pd.count;
+    for (int q = 0; q < 3; ++q) {
+      c.E[q] = pd.E[q + 1];
+      c.start[q] = pd.start[q + 1];
+      c.step[q] = pd.step[q + 1];
+      c.xs[q] = pd.xstride[q + 1];
+    }
+    c.ax = pd.axis - 1;
+    c.m_ax = pd.m[pd.axis];
+    c.interp = pd.interp;
+    c.scale_log = pd.grid - kc;
+  }
+  d.n_pass = n;
+  d.chunk = pl.chunk;
+  d.nsub = pl.nsub;
+  const size_t smem = (size_t)pl.gsize[kc] * sizeof(T);
+  if (cudaFuncSetAttribute(coarse_kernel<T, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return SZ3G_E_CUDA;
+  SZ3G_LAUNCH(COMP ? kKCoarseQuantize : kKCoarseRecover, s,
+              coarse_kernel<T, COMP><<<1, kCoarseThreads, smem, s>>>(d, a));
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+template <typename T>
+static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* const* R, uint32_t* hist, DevState* st,
+                          cudaStream_t s) {
+  const int kc = coarse_grid(pl);
+  LevelArgs<T> a{};
+  a.x = x;
+  a.codes = codes;
+  a.hist = hist;
+  a.st = st;
+  a.radius = (int)pl.radius;
+  a.Rout = kc == 0 ? nullptr : (T*)R[kc];  // the finest grid's reconstruction is not kept
+  int rc = run_coarse<T, true>(pl, kc, a, s);
+  if (rc) return rc;
+  for (int k = kc - 1; k >= 0; --k) {
+    a.Rc = (const T*)R[k + 1];
+    a.Rout = k == 0 ? nullptr : (T*)R[k];
+    rc = run_level<T, true>(pl, k, a, s);
+    if (rc) return rc;
+  }
+  return SZ3G_OK;
+}
+
+template <typename T>
+static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred, unsigned long long n_unpred,
+                         const unsigned long long* zbase, const uint32_t* zsub, void* const* R, T* out, DevState* st,
+                         T ebT, cudaStream_t s) {
+  const int kc = coarse_grid(pl);
+  LevelArgs<T> a{};
+  a.codes = const_cast<uint16_t*>(codes);
+  a.st = st;
+  a.radius = (int)pl.radius;
+  a.unpred = unpred;
+  a.n_unpred = n_unpred;
+  a.zbase = zbase;
+  a.zsub = zsub;
+  a.ebT = ebT;
+  a.Rout = kc == 0 ? out : (T*)R[kc];
+  int rc = run_coarse<T, false>(pl, kc, a, s);
+  if (rc) return rc;
+  for (int k = kc - 1; k >= 0; --k) {
+    a.Rc = (const T*)R[k + 1];
+    a.Rout = k == 0 ? out : (T*)R[k];
+    rc = run_level<T, false>(pl, k, a, s);
+    if (rc) return rc;
+  }
+  return SZ3G_OK;
+}
+
+int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
+                          DevState* st, cudaStream_t s) {
+  if (pl.dtype == SZ3G_F32) return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, s);
+  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, s);
+}
+
+int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
+                         const unsigned long long* zbase, const uint32_t* zsub, void* const* R, void* d_out,
+                         DevState* st, unsigned long long ebT_bits, cudaStream_t s) {
+  if (pl.dtype == SZ3G_F32) {
+    float e;
+    uint32_t b = (uint32_t)ebT_bits;
+    memcpy(&e, &b, 4);
+    return recover_fused<float>(pl, codes, (const float*)unpred, n_unpred, zbase, zsub, R, (float*)d_out, st, e, s);
+  }
+  double e;
+  memcpy(&e, &ebT_bits, 8);
+  return recover_fused<double>(pl, codes, (const double*)unpred, n_unpred, zbase, zsub, R, (double*)d_out, st, e, s);
+}
+
+}  // namespace sz3g

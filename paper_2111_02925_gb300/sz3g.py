@@ -99,6 +99,14 @@ def load(path: str | None = None):
         f = getattr(L, name)
         f.argtypes = args
         f.restype = C.c_int
+    L.sz3g_launch_count.argtypes = [C.POINTER(_u64)]
+    L.sz3g_launch_count.restype = C.c_int
+    L.sz3g_profile_enable.argtypes = [C.c_int]
+    L.sz3g_profile_enable.restype = C.c_int
+    L.sz3g_profile_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(_u64)]
+    L.sz3g_profile_read.restype = C.c_int
+    L.sz3g_profile_kernel_name.argtypes = [C.c_int]
+    L.sz3g_profile_kernel_name.restype = C.c_char_p
     L.sz3g_strerror.argtypes = [C.c_int]
     L.sz3g_strerror.restype = C.c_char_p
     _lib = L
@@ -212,6 +220,32 @@ def sz3g_huffman_decode(d_words: int, n_words: int, d_chunk_words: int, chunk: i
                         d_codes: int, n: int, stream: int = 0) -> int:
     return load().sz3g_huffman_decode(d_words, n_words, d_chunk_words, chunk, d_len, nsym, d_codes, n,
                                       stream or None)
+
+
+def sz3g_launch_count() -> int:
+    n = _u64()
+    _chk(load().sz3g_launch_count(C.byref(n)), "sz3g_launch_count")
+    return n.value
+
+
+def sz3g_profile_enable(on: bool) -> None:
+    _chk(load().sz3g_profile_enable(int(on)), "sz3g_profile_enable")
+
+
+def sz3g_profile_read(kernel: str):
+    t, n = C.c_double(), _u64()
+    _chk(load().sz3g_profile_read(kernel.encode(), C.byref(t), C.byref(n)), "sz3g_profile_read")
+    return t.value, n.value
+
+
+def sz3g_profile_kernel_names():
+    out, i = [], 0
+    while True:
+        nm = load().sz3g_profile_kernel_name(i)
+        if nm is None:
+            return out
+        out.append(nm.decode())
+        i += 1
 
 
 # ---- torch-tensor helpers ----------------------------------------------------

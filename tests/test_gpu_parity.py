@@ -236,3 +236,72 @@ def test_corrupt_streams_are_rejected():
         i = int(rng.integers(off_payload, len(s)))
         b[i] ^= 1 << int(rng.integers(8))
         assert gpu_decompress(bytes(b), x.size, O.F32)[0] in (G.OK, G.E_CORRUPT)
+
+
+# ---- full-size workloads (the benchmark's launch configuration) -------------------
+def test_full_64cube_bumps_abs_linear():
+    x = S.gaussian_bumps(64, 1)
+    eb = 1e-3 * float(x.max() - x.min())
+    op, gp = both_params(x.shape, eb, interp=O.LINEAR)
+    rc, s = gpu_compress(gp, x)
+    assert rc == G.OK and s == O.compress(op, x)
+
+
+@pytest.mark.parametrize("interp", [O.LINEAR, O.CUBIC])
+def test_full_latlon_fp64(interp):
+    x = S.latlon(1800, 3600, 3)
+    eb = 1e-6 * float(x.max() - x.min())
+    op, gp = both_params(x.shape, eb, dtype=O.F64, interp=interp)
+    rc, s = gpu_compress(gp, x)
+    assert rc == G.OK
+    ref = O.compress(op, x)
+    assert s == ref
+    rc, y = gpu_decompress(s, x.size, O.F64)
+    assert rc == G.OK
+    assert np.array_equal(y, O.decompress(ref))
+    assert np.max(np.abs(y - x.ravel())) <= eb
+
+
+_GRF512 = {}
+
+
+def _grf512():
+    if "x" not in _GRF512:
+        _GRF512["x"] = S.grf((512, 512, 512), 2)
+    return _GRF512["x"]
+
+
+@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
+def test_full_512cube_rel_cubic(eb):
+    x = _grf512()
+    op, gp = both_params(x.shape, eb, eb_mode=O.REL, interp=O.CUBIC)
+    rc, s = gpu_compress(gp, x)
+    assert rc == G.OK
+    if eb == 1e-3:  # the whole stream against the oracle
+        assert s == O.compress(op, x)
+    rc, y = gpu_decompress(s, x.size, O.F32)
+    assert rc == G.OK
+    eb_abs = eb * (float(x.max()) - float(x.min()))
+    assert float(np.max(np.abs(y.astype(np.float64) - x.ravel()))) <= eb_abs
+    # sampled points: each code and reconstruction re-derived by the oracle's
+    # quantizer from the GPU's reconstruction of the point's neighbours
+    import struct
+    ebT = np.frombuffer(struct.pack("<Q", struct.unpack_from("<Q", s, 64)[0])[:4], np.float32)[0]
+    yr = y.reshape(x.shape)
+    rng = np.random.default_rng(int(eb * 1e6))
+    for _ in range(300):
+        i, j, k = (int(v) for v in rng.integers(0, 512, 3))
+        if k % 2 == 1:  # a last-pass point: neighbours along axis 2 at +-1, +-3
+            nb = [yr[i, j, k + dd] if 0 <= k + dd < 512 else None for dd in (-1, 1, -3, 3)]
+            a, b, c, d = [np.float32(v) if v is not None else np.float32(0) for v in nb]
+            hb, hc, hd = k + 1 < 512, k >= 3, k + 3 < 512
+            if hc and hd:
+                pred = np.float32(np.float32(np.float32(9) * np.float32(a + b)) - np.float32(c + d)) * np.float32(0.0625)
+            elif not hc and hd:
+                pred = np.float32(np.float32(np.float32(3) * a + np.float32(6) * b) - d) * np.float32(0.125)
+            elif hc and hb:
+                pred = np.float32(np.float32(np.float32(6) * a + np.float32(3) * b) - c) * np.float32(0.125)
+            else:
+                continue
+            code, recon = O.quantize1(x[i, j, k], np.float32(pred), ebT)
+            assert (recon == yr[i, j, k]) or code == 0
