@@ -36,6 +36,7 @@ LINEAR, CUBIC = 0, 1
 MAX_LEVELS = 32
 LMAX = 24
 HEADER_BYTES = 288
+SUBBLOCK = 512
 
 OK = 0
 E_INVAL = -1
@@ -102,8 +103,8 @@ def lib():
             "sz3o_histogram": [vp, C.c_uint64, vp],
             "sz3o_huffman_lengths": [vp, C.c_uint32, C.c_uint32, vp],
             "sz3o_canonical_codes": [vp, C.c_uint32, vp],
-            "sz3o_huffman_encode": [vp, C.c_uint64, vp, vp, C.c_uint32, vp, C.c_uint64, vp, u64p],
-            "sz3o_huffman_decode": [vp, C.c_uint64, vp, C.c_uint32, vp, C.c_uint32, vp, C.c_uint64],
+            "sz3o_huffman_encode": [vp, C.c_uint64, vp, vp, C.c_uint32, vp, C.c_uint64, vp, vp, u64p],
+            "sz3o_huffman_decode": [vp, C.c_uint64, vp, vp, C.c_uint32, vp, C.c_uint32, vp, C.c_uint64],
             "sz3o_compress_bound": [P, u64p],
             "sz3o_compress": [P, vp, vp, C.c_uint64, u64p],
             "sz3o_read_header": [vp, C.c_uint64, P, u64p],
@@ -238,7 +239,13 @@ def canonical_codes(lengths) -> np.ndarray:
     return c
 
 
-def huffman_encode(codes, lengths, canon, chunk=4096):
+def sub_blocks(chunk: int) -> int:
+    """Sub-block entries recorded per chunk."""
+    return (chunk + SUBBLOCK - 1) // SUBBLOCK - 1
+
+
+def huffman_encode(codes, lengths, canon, chunk=4096, with_sub=False):
+    """Returns (payload words, words per chunk[, sub-block bit lengths])."""
     codes = np.ascontiguousarray(codes, np.uint16)
     ln = np.ascontiguousarray(lengths, np.uint8)
     cc = np.ascontiguousarray(canon, np.uint32)
@@ -246,18 +253,24 @@ def huffman_encode(codes, lengths, canon, chunk=4096):
     cap = nch * ((chunk * LMAX + 31) // 32)
     words = np.zeros(max(cap, 1), np.uint32)
     cw = np.zeros(max(nch, 1), np.uint32)
+    sub = np.zeros(max(nch * sub_blocks(chunk), 1), np.uint16)
     nw = C.c_uint64()
     _check(lib().sz3o_huffman_encode(_ptr(codes), codes.size, _ptr(ln), _ptr(cc), chunk, _ptr(words), cap,
-                                     _ptr(cw), C.byref(nw)), "huffman_encode")
-    return words[: nw.value].copy(), cw[:nch].copy()
+                                     _ptr(cw), _ptr(sub), C.byref(nw)), "huffman_encode")
+    out = (words[: nw.value].copy(), cw[:nch].copy())
+    if with_sub:
+        out = out + (sub[: nch * sub_blocks(chunk)].copy(),)
+    return out
 
 
-def huffman_decode(words, chunk_words, lengths, n, chunk=4096) -> np.ndarray:
+def huffman_decode(words, chunk_words, lengths, n, chunk=4096, sub_bits=None) -> np.ndarray:
     w = np.ascontiguousarray(words, np.uint32)
     cw = np.ascontiguousarray(chunk_words, np.uint32)
     ln = np.ascontiguousarray(lengths, np.uint8)
+    sb = None if sub_bits is None else np.ascontiguousarray(sub_bits, np.uint16)
     out = np.zeros(n, np.uint16)
-    _check(lib().sz3o_huffman_decode(_ptr(w) if w.size else None, w.size, _ptr(cw), chunk, _ptr(ln), ln.size,
+    _check(lib().sz3o_huffman_decode(_ptr(w) if w.size else None, w.size, _ptr(cw),
+                                     _ptr(sb) if sb is not None and sb.size else None, chunk, _ptr(ln), ln.size,
                                      _ptr(out), n), "huffman_decode")
     return out
 

@@ -369,17 +369,24 @@ int sz3o_canonical_codes(const uint8_t* len, uint32_t nsym, uint32_t* code) {
 }
 
 /* Chunked encode: every chunk starts on a fresh 32-bit word; bits are packed
- * most significant first; the tail of a chunk's last word is zero. */
+ * most significant first; the tail of a chunk's last word is zero.  For every
+ * chunk the bit lengths of its first ceil(chunk/512) - 1 sub-blocks of 512
+ * codes are recorded as well (sub_bits, may be NULL): they let a decoder
+ * start inside a chunk. */
 int sz3o_huffman_encode(const uint16_t* codes, uint64_t n, const uint8_t* len,
                         const uint32_t* code, uint32_t chunk, uint32_t* words,
-                        uint64_t cap_words, uint32_t* chunk_words, uint64_t* n_words) {
+                        uint64_t cap_words, uint32_t* chunk_words, uint16_t* sub_bits,
+                        uint64_t* n_words) {
   uint64_t nchunks, j, w = 0;
+  uint32_t nsb;
   if (chunk == 0) return SZ3O_E_INVAL;
   nchunks = (n + chunk - 1) / chunk;
+  nsb = (chunk + SZ3O_SUBBLOCK - 1) / SZ3O_SUBBLOCK;
   for (j = 0; j < nchunks; ++j) {
     uint64_t i0 = j * chunk, i1 = i0 + chunk < n ? i0 + chunk : n, i;
     uint64_t w0 = w;
     uint32_t acc = 0, nacc = 0; /* bits held in acc (MSB-aligned count) */
+    uint32_t sb_bits = 0;
     for (i = i0; i < i1; ++i) {
       uint32_t L = len[codes[i]], b;
       uint32_t v = code[codes[i]];
@@ -393,6 +400,22 @@ int sz3o_huffman_encode(const uint16_t* codes, uint64_t n, const uint8_t* len,
           nacc = 0;
         }
       }
+      sb_bits += L;
+      if ((i - i0 + 1) % SZ3O_SUBBLOCK == 0) {
+        uint64_t sb = (i - i0) / SZ3O_SUBBLOCK;
+        if (sub_bits && sb + 1 < nsb) sub_bits[j * (nsb - 1) + sb] = (uint16_t)sb_bits;
+        sb_bits = 0;
+      }
+    }
+    if (sub_bits) { /* sub-blocks past the end of a short last chunk are empty */
+      uint64_t sb;
+      for (sb = (i1 - i0 + SZ3O_SUBBLOCK - 1) / SZ3O_SUBBLOCK; sb + 1 < nsb; ++sb) {
+        if (sb * SZ3O_SUBBLOCK >= i1 - i0) sub_bits[j * (nsb - 1) + sb] = 0;
+      }
+      if ((i1 - i0) % SZ3O_SUBBLOCK != 0) {
+        uint64_t sb = (i1 - i0) / SZ3O_SUBBLOCK;
+        if (sb + 1 < nsb) sub_bits[j * (nsb - 1) + sb] = (uint16_t)sb_bits;
+      }
     }
     if (nacc) {
       if (w >= cap_words) return SZ3O_E_CAPACITY;
@@ -405,18 +428,20 @@ int sz3o_huffman_encode(const uint16_t* codes, uint64_t n, const uint8_t* len,
 }
 
 /* Chunked decode with the canonical code: read one bit at a time until the
- * prefix read so far is a code of its length. */
+ * prefix read so far is a code of its length.  With sub_bits, every sub-block
+ * boundary must fall where the recorded lengths put it. */
 int sz3o_huffman_decode(const uint32_t* words, uint64_t n_words, const uint32_t* chunk_words,
-                        uint32_t chunk, const uint8_t* len, uint32_t nsym, uint16_t* codes,
-                        uint64_t n) {
+                        const uint16_t* sub_bits, uint32_t chunk, const uint8_t* len,
+                        uint32_t nsym, uint16_t* codes, uint64_t n) {
   uint64_t first[33], count[33], offs[33];
   uint32_t* sorted;
   uint64_t nchunks, j, w = 0;
-  uint32_t L, s, k = 0;
+  uint32_t L, s, k = 0, nsb;
   uint64_t c = 0;
   int have = 0;
   uint32_t prev_len = 0;
   if (chunk == 0) return SZ3O_E_INVAL;
+  nsb = (chunk + SZ3O_SUBBLOCK - 1) / SZ3O_SUBBLOCK;
   sorted = (uint32_t*)malloc(sizeof(uint32_t) * (nsym ? nsym : 1));
   if (!sorted) return SZ3O_E_NOMEM;
   for (L = 0; L <= 32; ++L) {
@@ -439,7 +464,7 @@ int sz3o_huffman_decode(const uint32_t* words, uint64_t n_words, const uint32_t*
   nchunks = (n + chunk - 1) / chunk;
   for (j = 0; j < nchunks; ++j) {
     uint64_t i0 = j * chunk, i1 = i0 + chunk < n ? i0 + chunk : n, i;
-    uint64_t wend = w + chunk_words[j], bit = 0;
+    uint64_t wend = w + chunk_words[j], bit = 0, expect = 0;
     if (wend > n_words) {
       free(sorted);
       return SZ3O_E_CORRUPT;
@@ -447,6 +472,13 @@ int sz3o_huffman_decode(const uint32_t* words, uint64_t n_words, const uint32_t*
     for (i = i0; i < i1; ++i) {
       uint64_t v = 0;
       int found = 0;
+      if (sub_bits && i > i0 && (i - i0) % SZ3O_SUBBLOCK == 0) {
+        expect += sub_bits[j * (nsb - 1) + (i - i0) / SZ3O_SUBBLOCK - 1];
+        if (bit != expect) {
+          free(sorted);
+          return SZ3O_E_CORRUPT;
+        }
+      }
       for (L = 1; L <= 32 && !found; ++L) {
         uint64_t wi = w + bit / 32;
         if (wi >= wend) break;
@@ -461,6 +493,14 @@ int sz3o_huffman_decode(const uint32_t* words, uint64_t n_words, const uint32_t*
         free(sorted);
         return SZ3O_E_CORRUPT;
       }
+    }
+    if (sub_bits) { /* recorded lengths of empty sub-blocks must be zero */
+      uint64_t sb;
+      for (sb = (i1 - i0 + SZ3O_SUBBLOCK - 1) / SZ3O_SUBBLOCK; sb + 1 < nsb; ++sb)
+        if (sub_bits[j * (nsb - 1) + sb] != 0) {
+          free(sorted);
+          return SZ3O_E_CORRUPT;
+        }
     }
     w = wend;
   }
@@ -492,9 +532,14 @@ int sz3o_huffman_decode(const uint32_t* words, uint64_t n_words, const uint32_t*
  *              unpredictable values  T[n_unpred]
  *              code-length table     n_used x (u16 symbol, u8 length), by symbol
  *              chunk table           u32[n_chunks] (words per chunk)
+ *              sub-block table       u16[n_chunks x (ceil(chunk/512) - 1)]: bit
+ *                                    lengths of each chunk's 512-code sub-blocks
+ *                                    but the last (0 past a short chunk's end)
  *              payload               u32[payload words]
  * ------------------------------------------------------------------------- */
 static uint64_t pad8(uint64_t x) { return (x + 7) & ~(uint64_t)7; }
+
+static uint64_t nsb_of(uint32_t chunk) { return (chunk + SZ3O_SUBBLOCK - 1) / SZ3O_SUBBLOCK; }
 
 static void put_le(uint8_t* b, uint64_t v, int nbytes) {
   int i;
@@ -529,7 +574,8 @@ int sz3o_compress_bound(const sz3o_params* p, uint64_t* max_bytes) {
   nchunks = (g.N + p->chunk_codes - 1) / p->chunk_codes;
   maxbits_chunk = (uint64_t)p->chunk_codes * SZ3O_LMAX;
   *max_bytes = SZ3O_HEADER_BYTES + pad8(g.N * esz) + pad8((uint64_t)2 * p->radius * 3) +
-               pad8(nchunks * 4) + pad8(nchunks * ((maxbits_chunk + 31) / 32) * 4);
+               pad8(nchunks * 4) + pad8(nchunks * (nsb_of(p->chunk_codes) - 1) * 2) +
+               pad8(nchunks * ((maxbits_chunk + 31) / 32) * 4);
   return SZ3O_OK;
 }
 
@@ -544,8 +590,10 @@ int sz3o_compress(const sz3o_params* p, const void* x, void* out, uint64_t capac
   uint8_t* len = NULL;
   uint32_t* code = NULL;
   uint32_t* chunk_words = NULL;
+  uint16_t* sub_bits = NULL;
   uint32_t* words = NULL;
   uint32_t nsym, n_used = 0, l;
+  uint64_t nsub_entries;
   double eb_abs = 0;
   uint8_t ebT[8];
   uint8_t* o = (uint8_t*)out;
@@ -562,8 +610,10 @@ int sz3o_compress(const sz3o_params* p, const void* x, void* out, uint64_t capac
   len = (uint8_t*)malloc(nsym);
   code = (uint32_t*)malloc(nsym * 4);
   chunk_words = (uint32_t*)malloc(nchunks * 4);
+  nsub_entries = nchunks * (nsb_of(p->chunk_codes) - 1);
+  sub_bits = (uint16_t*)malloc(nsub_entries ? nsub_entries * 2 : 2);
   words = (uint32_t*)malloc(cap_words * 4);
-  if (!codes || !unpred || !recon || !hist || !len || !code || !chunk_words || !words) {
+  if (!codes || !unpred || !recon || !hist || !len || !code || !chunk_words || !sub_bits || !words) {
     rc = SZ3O_E_NOMEM;
     goto done;
   }
@@ -581,12 +631,12 @@ int sz3o_compress(const sz3o_params* p, const void* x, void* out, uint64_t capac
   rc = sz3o_canonical_codes(len, nsym, code);
   if (rc) goto done;
   rc = sz3o_huffman_encode(codes, g.N, len, code, p->chunk_codes, words, cap_words, chunk_words,
-                           &n_words);
+                           sub_bits, &n_words);
   if (rc) goto done;
   for (i = 0; i < nsym; ++i)
     if (len[i]) ++n_used;
   off = SZ3O_HEADER_BYTES + pad8(n_unpred * esz) + pad8((uint64_t)n_used * 3) + pad8(nchunks * 4) +
-        pad8(n_words * 4);
+        pad8(nsub_entries * 2) + pad8(n_words * 4);
   if (off > capacity) {
     rc = SZ3O_E_CAPACITY;
     goto done;
@@ -640,6 +690,8 @@ int sz3o_compress(const sz3o_params* p, const void* x, void* out, uint64_t capac
   off += pad8((uint64_t)n_used * 3);
   for (i = 0; i < nchunks; ++i) put_le(o + off + 4 * i, chunk_words[i], 4);
   off += pad8(nchunks * 4);
+  for (i = 0; i < nsub_entries; ++i) put_le(o + off + 2 * i, sub_bits[i], 2);
+  off += pad8(nsub_entries * 2);
   for (i = 0; i < n_words; ++i) put_le(o + off + 4 * i, words[i], 4);
   off += pad8(n_words * 4);
   *out_bytes = off;
@@ -652,6 +704,7 @@ done:
   free(len);
   free(code);
   free(chunk_words);
+  free(sub_bits);
   free(words);
   return rc;
 }
@@ -661,7 +714,7 @@ typedef struct {
   uint64_t N, n_unpred, n_chunks, n_words;
   uint32_t n_used, L;
   uint8_t ebT[8];
-  uint64_t off_unpred, off_table, off_chunks, off_payload, end;
+  uint64_t off_unpred, off_table, off_chunks, off_sub, off_payload, end;
 } parsed_t;
 
 static int parse(const uint8_t* s, uint64_t bytes, parsed_t* h) {
@@ -719,7 +772,8 @@ static int parse(const uint8_t* s, uint64_t bytes, parsed_t* h) {
   h->off_unpred = SZ3O_HEADER_BYTES;
   h->off_table = h->off_unpred + pad8(h->n_unpred * esz);
   h->off_chunks = h->off_table + pad8((uint64_t)h->n_used * 3);
-  h->off_payload = h->off_chunks + pad8(h->n_chunks * 4);
+  h->off_sub = h->off_chunks + pad8(h->n_chunks * 4);
+  h->off_payload = h->off_sub + pad8(h->n_chunks * (nsb_of(h->p.chunk_codes) - 1) * 2);
   h->end = h->off_payload + pad8(h->n_words * 4);
   if (h->end > bytes) return SZ3O_E_CORRUPT;
   return SZ3O_OK;
@@ -741,10 +795,12 @@ int sz3o_decompress(const void* stream, uint64_t bytes, void* out, uint64_t capa
   uint32_t nsym;
   uint8_t* len = NULL;
   uint32_t* chunk_words = NULL;
+  uint16_t* sub_bits = NULL;
   uint32_t* words = NULL;
   uint16_t* codes = NULL;
   uint8_t* unpred = NULL;
   double kraft = 0;
+  uint64_t nsub_entries;
   int rc = parse(s, bytes, &h);
   if (rc) return rc;
   esz = h.p.dtype == SZ3O_F32 ? 4 : 8;
@@ -752,10 +808,12 @@ int sz3o_decompress(const void* stream, uint64_t bytes, void* out, uint64_t capa
   nsym = 2 * h.p.radius;
   len = (uint8_t*)calloc(nsym, 1);
   chunk_words = (uint32_t*)malloc(h.n_chunks * 4);
+  nsub_entries = h.n_chunks * (nsb_of(h.p.chunk_codes) - 1);
+  sub_bits = (uint16_t*)malloc(nsub_entries ? nsub_entries * 2 : 2);
   words = (uint32_t*)malloc((h.n_words ? h.n_words : 1) * 4);
   codes = (uint16_t*)malloc(h.N * 2);
   unpred = (uint8_t*)malloc((h.n_unpred ? h.n_unpred : 1) * esz);
-  if (!len || !chunk_words || !words || !codes || !unpred) {
+  if (!len || !chunk_words || !sub_bits || !words || !codes || !unpred) {
     rc = SZ3O_E_NOMEM;
     goto done;
   }
@@ -792,8 +850,10 @@ int sz3o_decompress(const void* stream, uint64_t bytes, void* out, uint64_t capa
     rc = SZ3O_E_CORRUPT;
     goto done;
   }
+  for (i = 0; i < nsub_entries; ++i) sub_bits[i] = (uint16_t)get_le(s + h.off_sub + 2 * i, 2);
   for (i = 0; i < h.n_words; ++i) words[i] = (uint32_t)get_le(s + h.off_payload + 4 * i, 4);
-  rc = sz3o_huffman_decode(words, h.n_words, chunk_words, h.p.chunk_codes, len, nsym, codes, h.N);
+  rc = sz3o_huffman_decode(words, h.n_words, chunk_words, sub_bits, h.p.chunk_codes, len, nsym, codes,
+                           h.N);
   if (rc) goto done;
   for (i = 0; i < h.n_unpred; ++i) {
     uint64_t v = get_le(s + h.off_unpred + i * esz, (int)esz);
@@ -815,6 +875,7 @@ int sz3o_decompress(const void* stream, uint64_t bytes, void* out, uint64_t capa
 done:
   free(len);
   free(chunk_words);
+  free(sub_bits);
   free(words);
   free(codes);
   free(unpred);

@@ -59,6 +59,7 @@ enum { SZ3O_LINEAR = 0, SZ3O_CUBIC = 1 };
 #define SZ3O_MAX_LEVELS 32
 #define SZ3O_LMAX 24          /* longest Huffman code the format allows */
 #define SZ3O_HEADER_BYTES 288
+#define SZ3O_SUBBLOCK 512     /* codes per decode sub-block inside a chunk */
 
 /* Parameter block.  Same byte layout as the CUDA library's sz3g_params. */
 typedef struct sz3o_params {
@@ -113,15 +114,19 @@ int sz3o_huffman_lengths(const uint64_t* freq, uint32_t nsym, uint32_t lmax, uin
 int sz3o_canonical_codes(const uint8_t* len, uint32_t nsym, uint32_t* code);
 
 /* Chunked encode: chunk j covers codes [chunk*j, chunk*(j+1)).  Writes the
- * payload words and the word count of every chunk. */
+ * payload words, the word count of every chunk and (sub_bits, may be NULL)
+ * the bit lengths of each chunk's 512-code sub-blocks but the last,
+ * ceil(chunk/512) - 1 per chunk. */
 int sz3o_huffman_encode(const uint16_t* codes, uint64_t n, const uint8_t* len,
                         const uint32_t* code, uint32_t chunk, uint32_t* words,
-                        uint64_t cap_words, uint32_t* chunk_words, uint64_t* n_words);
+                        uint64_t cap_words, uint32_t* chunk_words, uint16_t* sub_bits,
+                        uint64_t* n_words);
 
-/* Chunked decode of n codes. */
+/* Chunked decode of n codes; sub_bits (may be NULL) is checked against the
+ * decoded sub-block boundaries. */
 int sz3o_huffman_decode(const uint32_t* words, uint64_t n_words, const uint32_t* chunk_words,
-                        uint32_t chunk, const uint8_t* len, uint32_t nsym, uint16_t* codes,
-                        uint64_t n);
+                        const uint16_t* sub_bits, uint32_t chunk, const uint8_t* len,
+                        uint32_t nsym, uint16_t* codes, uint64_t n);
 
 int sz3o_compress_bound(const sz3o_params* p, uint64_t* max_bytes);
 int sz3o_compress(const sz3o_params* p, const void* x, void* out, uint64_t capacity,

@@ -156,7 +156,7 @@ def test_canonical_code_properties():
         assert int(cc[s1]) == (int(cc[s0]) + 1) << int(ln[s1] - ln[s0])
 
 
-@pytest.mark.parametrize("chunk", [8, 16, 4096, 1000 * 8])
+@pytest.mark.parametrize("chunk", [8, 16, 4096, 1000 * 8, 520])
 def test_encode_decode_round_trip(chunk):
     rng = np.random.default_rng(chunk)
     n = 50_000 + 13
@@ -166,13 +166,24 @@ def test_encode_decode_round_trip(chunk):
     assert int(hist.sum()) == n and hist[32768] == np.sum(codes == 32768)
     ln = O.huffman_lengths(hist)
     cc = O.canonical_codes(ln)
-    words, cw = O.huffman_encode(codes, ln, cc, chunk)
+    words, cw, sub = O.huffman_encode(codes, ln, cc, chunk, with_sub=True)
     nch = (n + chunk - 1) // chunk
     assert cw.size == nch
+    nsb = O.sub_blocks(chunk)
+    assert sub.size == nch * nsb
+    for j in range(0, nch, max(1, nch // 7)):
+        for b in range(nsb):
+            blk = codes[j * chunk + b * 512: min(j * chunk + min((b + 1) * 512, chunk), n)]
+            assert sub[j * nsb + b] == int(np.sum(ln[blk].astype(np.int64)))
     # per-chunk word counts from the lengths alone
     for j in range(nch):
         bits = int(np.sum(ln[codes[j * chunk:(j + 1) * chunk]].astype(np.int64)))
         assert cw[j] == (bits + 31) // 32
     assert words.size == int(cw.sum())
-    back = O.huffman_decode(words, cw, ln, n, chunk)
+    back = O.huffman_decode(words, cw, ln, n, chunk, sub_bits=sub)
     assert np.array_equal(back, codes)
+    if sub.size:
+        bad = sub.copy()
+        bad[0] ^= 1
+        with pytest.raises(O.OracleError):
+            O.huffman_decode(words, cw, ln, n, chunk, sub_bits=bad)

@@ -39,6 +39,9 @@ def parse(stream: bytes):
     off += _pad8(h["n_used"] * 3)
     h["off_chunks"] = off
     off += _pad8(h["n_chunks"] * 4)
+    h["n_sub"] = h["n_chunks"] * ((h["chunk"] + 511) // 512 - 1)
+    h["off_sub"] = off
+    off += _pad8(h["n_sub"] * 2)
     h["off_payload"] = off
     off += _pad8(h["n_words"] * 4)
     h["end"] = off
@@ -50,18 +53,18 @@ def test_header_and_sections(dtype):
     t = np.float32 if dtype == O.F32 else np.float64
     x = S.grf((30, 20, 17), 1).astype(t)
     x[3, 4, 5] = 50.0  # beyond radius * 2 eb: a certain unpredictable
-    p = O.make_params(x.shape, 1e-3, dtype=dtype, eb_mode=O.REL, interp=O.CUBIC, order=(2, 0, 1), chunk=512,
+    p = O.make_params(x.shape, 1e-3, dtype=dtype, eb_mode=O.REL, interp=O.CUBIC, order=(2, 0, 1), chunk=2048,
                       radius=64)
     s = O.compress(p, x)
     h = parse(s)
     assert h["version"] == 1 and h["dtype"] == dtype and h["ndim"] == 3
     assert h["dims"] == [30, 20, 17, 1]
     assert (h["eb_mode"], h["interp"], h["per_level"], h["L"]) == (O.REL, O.CUBIC, 0, 5)
-    assert h["radius"] == 64 and h["chunk"] == 512 and h["eb"] == 1e-3
+    assert h["radius"] == 64 and h["chunk"] == 2048 and h["eb"] == 1e-3
     assert list(s[272:275]) == [2, 0, 1]
     codes, unpred, recon, ebT = O.quantize(p, x)
     assert h["n_codes"] == x.size and h["n_unpred"] == unpred.size and unpred.size >= 1
-    assert h["n_chunks"] == (x.size + 511) // 512
+    assert h["n_chunks"] == (x.size + 2047) // 2048
     assert h["end"] == len(s)
     ebT_bits = np.array([ebT], t).view(np.uint32 if dtype == O.F32 else np.uint64)[0]
     assert h["ebT_bits"] == int(ebT_bits)
@@ -77,7 +80,13 @@ def test_header_and_sections(dtype):
     cw = np.frombuffer(s, np.uint32, count=h["n_chunks"], offset=h["off_chunks"])
     words = np.frombuffer(s, np.uint32, count=h["n_words"], offset=h["off_payload"])
     assert int(cw.sum()) == h["n_words"]
-    assert np.array_equal(O.huffman_decode(words, cw, ln, x.size, 512), codes)
+    assert np.array_equal(O.huffman_decode(words, cw, ln, x.size, 2048), codes)
+    # sub-block table: bit lengths of 512-code sub-blocks 0..2 of every chunk
+    sub = np.frombuffer(s, np.uint16, count=h["n_sub"], offset=h["off_sub"]).reshape(h["n_chunks"], 3)
+    for j in range(h["n_chunks"]):
+        for b in range(3):
+            blk = codes[j * 2048 + b * 512: min(j * 2048 + (b + 1) * 512, x.size)]
+            assert sub[j, b] == int(np.sum(ln[blk].astype(np.int64)))
     # padding bytes are zero
     assert s[275:288] == bytes(13)
     rp, n = O.read_header(s)
@@ -100,7 +109,7 @@ def test_per_level_fields():
 
 def test_corrupt_and_truncated_streams_are_rejected():
     x = S.grf((20, 20, 20), 5)
-    p = O.make_params(x.shape, 1e-3, eb_mode=O.REL, chunk=256)
+    p = O.make_params(x.shape, 1e-3, eb_mode=O.REL, chunk=1024)
     s = bytearray(O.compress(p, x))
     out = np.zeros(x.size, np.float32)
     assert O.decompress_status(bytes(s), out) == O.OK
@@ -124,6 +133,9 @@ def test_corrupt_and_truncated_streams_are_rejected():
     b = bytearray(s)
     b[h["off_table"] + 2] = 30  # a length above the limit
     assert O.decompress_status(bytes(b), out) == O.E_CORRUPT
+    b = bytearray(s)
+    struct.pack_into("<H", b, h["off_sub"], struct.unpack_from("<H", s, h["off_sub"])[0] + 1)
+    assert O.decompress_status(bytes(b), out) == O.E_CORRUPT  # sub-block boundary moved
     b = bytearray(s)
     struct.pack_into("<Q", b, 64, 0)  # eb_T = 0
     assert O.decompress_status(bytes(b), out) == O.E_CORRUPT
