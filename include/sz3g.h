@@ -193,21 +193,28 @@ int sz3g_huffman_build(const uint32_t* d_hist, uint32_t nsym, uint8_t* d_len, ui
  * bits most significant first, tail zero.
  *   d_words        payload capacity cap_words uint32.
  *   d_chunk_words  ceil(n/chunk) uint32: words of every chunk.
+ *   d_sub_bits     NULL, or ceil(n/chunk) * (ceil(chunk/512) - 1) uint16: bit
+ *                  lengths of each chunk's 512-code sub-blocks but the last
+ *                  (0 past the end of a short last chunk).
  *   h_n_words      host, total words (after a stream synchronisation).
  */
 int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_len,
                         const uint32_t* d_code, uint32_t nsym, uint32_t chunk, uint32_t* d_words,
-                        uint64_t cap_words, uint32_t* d_chunk_words, uint64_t* h_n_words,
-                        void* stream);
+                        uint64_t cap_words, uint32_t* d_chunk_words, uint16_t* d_sub_bits,
+                        uint64_t* h_n_words, void* stream);
 
 /*
  * Chunked Huffman decode of n codes (Sec. 3.2 Encoder decode()).  d_len are
- * the code lengths of nsym symbols.  SZ3G_E_CORRUPT when a chunk runs out of
- * bits or holds a bit pattern that is no codeword (after a synchronisation).
+ * the code lengths of nsym symbols.  With d_sub_bits (as written by
+ * sz3g_huffman_encode) every 512-code sub-block decodes on its own thread and
+ * must end exactly where the table says; with NULL one thread decodes a
+ * chunk.  SZ3G_E_CORRUPT when a chunk runs out of bits, holds a bit pattern
+ * that is no codeword or contradicts the sub-block table (after a
+ * synchronisation).
  */
 int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_t* d_chunk_words,
-                        uint32_t chunk, const uint8_t* d_len, uint32_t nsym, uint16_t* d_codes,
-                        uint64_t n, void* stream);
+                        const uint16_t* d_sub_bits, uint32_t chunk, const uint8_t* d_len,
+                        uint32_t nsym, uint16_t* d_codes, uint64_t n, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Diagnostics (no counterpart in the paper): launch accounting and per-kernel

@@ -8,23 +8,24 @@
 namespace sz3g {
 
 // Launchers defined in k_huffman.cu that are used only here.
-int launch_encode(const Plan& pl, const uint16_t* codes, const uint32_t* table, const void* d_in,
-                  const PassMap* map, unsigned long long* wstat, unsigned long long* zstat, DevState* st,
-                  unsigned char* d_out, unsigned long long out_capacity, int mode, uint32_t* words_out,
-                  uint32_t* chunk_words_out, unsigned long long cap_words, cudaStream_t s);
-int launch_compact_unpred(const Plan& pl, const uint16_t* codes, const void* d_in, const PassMap* map,
-                          unsigned long long* wstat, unsigned long long* zstat, const uint32_t* table,
-                          void* d_unpred, DevState* st, cudaStream_t s);
+int launch_encode(const Plan& pl, const uint16_t* codes, const uint32_t* table, const void* d_in, const PassMap* map,
+                  void* scratch, DevState* st, unsigned char* d_out, unsigned long long out_capacity, int mode,
+                  uint32_t* words_out, uint32_t* chunk_words_out, uint16_t* sub_out, unsigned long long cap_words,
+                  cudaStream_t s);
+int launch_compact_unpred(const Plan& pl, const uint16_t* codes, const void* d_in, const PassMap* map, void* scratch,
+                          const uint32_t* table, void* d_unpred, DevState* st, cudaStream_t s);
+size_t encode_scratch_bytes(unsigned long long n_chunks);
 int launch_decode_tables(const unsigned char* tab, uint32_t n_used, const uint8_t* len, uint32_t nsym,
                          void* tables, DevState* st, cudaStream_t s);
 int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, const uint32_t* chunk_words,
-                         unsigned long long n_chunks, uint32_t chunk, unsigned long long n, const void* tables,
-                         unsigned long long* woff, uint16_t* codes, uint32_t* zchunk, uint32_t* zsub,
-                         uint32_t nsub, DevState* st, cudaStream_t s);
-int launch_zero_counts(const uint16_t* codes, unsigned long long n, uint32_t chunk, uint32_t nsub,
-                       unsigned long long n_chunks, uint32_t* zchunk, uint32_t* zsub, cudaStream_t s);
-int launch_scan_u32(const uint32_t* in, unsigned long long n, unsigned long long* out, unsigned long long* total,
-                    unsigned long long expect, int check_expect, DevState* st, cudaStream_t s);
+                         const uint16_t* sub_bits, unsigned long long n_chunks, uint32_t chunk, unsigned long long n,
+                         const void* tables, unsigned long long* woff, uint16_t* codes, uint32_t* zcnt,
+                         void* scan_state, DevState* st, cudaStream_t s);
+int launch_zero_counts(const uint16_t* codes, unsigned long long n, uint32_t chunk, unsigned long long n_chunks,
+                       uint32_t* zcnt, cudaStream_t s);
+int launch_scan(const uint32_t* in, unsigned long long n, unsigned long long* out, uint32_t limit,
+                unsigned long long expect, int check_expect, void* state, DevState* st, cudaStream_t s);
+size_t scan_state_bytes(unsigned long long n);
 int launch_pack_table(const uint8_t* len, const uint32_t* code, uint32_t nsym, uint32_t* table, cudaStream_t s);
 size_t dec_tables_bytes();
 
@@ -45,7 +46,7 @@ struct Layout {
 };
 
 struct CompressWs {
-  size_t st, hist, table, range, cb, wstat, zstat, codes, R[34], total;
+  size_t st, hist, table, range, cb, enc, codes, R[34], total;
 };
 
 CompressWs compress_layout(const Plan& pl) {
@@ -56,8 +57,7 @@ CompressWs compress_layout(const Plan& pl) {
   w.table = l.take(kSyms * 4);
   w.range = l.take(range_scratch_bytes(pl));
   w.cb = l.take(codebook_scratch_bytes());
-  w.wstat = l.take(pl.n_chunks * 8);
-  w.zstat = l.take(pl.n_chunks * 8);
+  w.enc = l.take(encode_scratch_bytes(pl.n_chunks));
   w.codes = l.take(pl.N * 2);
   // the fused level path never stores the finest grid's reconstruction
   for (int k = level_path_ok(pl) ? 1 : 0; k <= pl.L; ++k) w.R[k] = l.take(pl.gsize[k] * pl.esz);
@@ -66,7 +66,7 @@ CompressWs compress_layout(const Plan& pl) {
 }
 
 struct DecompressWs {
-  size_t st, tables, woff, zchunk, zsub, zbase, codes, R[34], total;
+  size_t st, tables, woff, zcnt, zunit, scan1, scan2, codes, R[34], total;
 };
 
 DecompressWs decompress_layout(const Plan& pl) {
@@ -75,9 +75,10 @@ DecompressWs decompress_layout(const Plan& pl) {
   w.st = l.take(sizeof(DevState));
   w.tables = l.take(dec_tables_bytes());
   w.woff = l.take(pl.n_chunks * 8);
-  w.zchunk = l.take(pl.n_chunks * 4);
-  w.zsub = l.take(pl.n_chunks * pl.nsub * 4);
-  w.zbase = l.take(pl.n_chunks * 8);
+  w.zcnt = l.take(pl.n_chunks * pl.nsub * 4);
+  w.zunit = l.take(pl.n_chunks * pl.nsub * 8);
+  w.scan1 = l.take(scan_state_bytes(pl.n_chunks));
+  w.scan2 = l.take(scan_state_bytes(pl.n_chunks * pl.nsub));
   w.codes = l.take(pl.N * 2);
   for (int k = 1; k <= pl.L; ++k) w.R[k] = l.take(pl.gsize[k] * pl.esz);
   w.R[0] = 0;
@@ -154,7 +155,7 @@ struct Header {
   Plan plan;
   unsigned long long n_unpred, n_words, ebT_bits;
   uint32_t n_used;
-  unsigned long long off_table, off_chunks, off_payload, end;
+  unsigned long long off_table, off_chunks, off_sub, off_payload, end;
 };
 
 int parse_header(const unsigned char* s, size_t bytes, Header* h) {
@@ -204,7 +205,8 @@ int parse_header(const unsigned char* s, size_t bytes, Header* h) {
   if (h->n_words > pl.n_chunks * (((unsigned long long)pl.chunk * SZ3G_LMAX + 31) / 32)) return SZ3G_E_CORRUPT;
   h->off_table = SZ3G_HEADER_BYTES + pad8(h->n_unpred * pl.esz);
   h->off_chunks = h->off_table + pad8(3ull * h->n_used);
-  h->off_payload = h->off_chunks + pad8(pl.n_chunks * 4);
+  h->off_sub = h->off_chunks + pad8(pl.n_chunks * 4);
+  h->off_payload = h->off_sub + pad8(pl.n_chunks * (pl.nsub - 1) * 2);
   h->end = h->off_payload + pad8(h->n_words * 4);
   if (h->end > bytes) return SZ3G_E_CORRUPT;
   return SZ3G_OK;
@@ -238,7 +240,7 @@ int sz3g_compress_bound(const sz3g_params* p, size_t* max_bytes) {
   if (!max_bytes) return SZ3G_E_INVAL;
   const unsigned long long maxw = ((unsigned long long)pl.chunk * SZ3G_LMAX + 31) / 32;
   *max_bytes = SZ3G_HEADER_BYTES + pad8(pl.N * pl.esz) + pad8(2ull * pl.radius * 3) + pad8(pl.n_chunks * 4) +
-               pad8(pl.n_chunks * maxw * 4);
+               pad8(pl.n_chunks * (pl.nsub - 1) * 2) + pad8(pl.n_chunks * maxw * 4);
   return SZ3G_OK;
 }
 
@@ -273,9 +275,8 @@ int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t ou
                            out_capacity, pl.esz, s));
   PassMap map;  // kernel parameter, copied at launch
   make_pass_map(pl, &map);
-  SZ3G_TRY(launch_encode(pl, codes, table, d_in, &map, (unsigned long long*)(ws + L.wstat),
-                         (unsigned long long*)(ws + L.zstat), st, (unsigned char*)d_out, out_capacity,
-                         kEncodeStream, nullptr, nullptr, 0, s));
+  SZ3G_TRY(launch_encode(pl, codes, table, d_in, &map, ws + L.enc, st, (unsigned char*)d_out, out_capacity,
+                         kEncodeStream, nullptr, nullptr, nullptr, 0, s));
   SZ3G_TRY(launch_finalize(pl, p, st, (unsigned char*)d_out, out_capacity, s));
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
@@ -322,16 +323,16 @@ int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_
   SZ3G_TRY(launch_decode_tables(base + h.off_table, h.n_used, nullptr, 2 * pl.radius, ws + L.tables, st, s));
   uint16_t* codes = (uint16_t*)(ws + L.codes);
   SZ3G_TRY(launch_decode_chunks((const uint32_t*)(base + h.off_payload), h.n_words,
-                                (const uint32_t*)(base + h.off_chunks), pl.n_chunks, pl.chunk, pl.N, ws + L.tables,
-                                (unsigned long long*)(ws + L.woff), codes, (uint32_t*)(ws + L.zchunk),
-                                (uint32_t*)(ws + L.zsub), pl.nsub, st, s));
-  SZ3G_TRY(launch_scan_u32((uint32_t*)(ws + L.zchunk), pl.n_chunks, (unsigned long long*)(ws + L.zbase), nullptr,
-                           h.n_unpred, 1, st, s));
+                                (const uint32_t*)(base + h.off_chunks),
+                                pl.nsub > 1 ? (const uint16_t*)(base + h.off_sub) : nullptr, pl.n_chunks, pl.chunk,
+                                pl.N, ws + L.tables, (unsigned long long*)(ws + L.woff), codes,
+                                (uint32_t*)(ws + L.zcnt), ws + L.scan1, st, s));
+  SZ3G_TRY(launch_scan((uint32_t*)(ws + L.zcnt), pl.n_chunks * pl.nsub, (unsigned long long*)(ws + L.zunit), 0,
+                       h.n_unpred, 1, ws + L.scan2, st, s));
   void* R[34];
   for (int k = 0; k <= pl.L; ++k) R[k] = k == 0 ? d_out : ws + L.R[k];
-  SZ3G_TRY(launch_recover_levels(pl, codes, base + SZ3G_HEADER_BYTES, h.n_unpred,
-                                 (unsigned long long*)(ws + L.zbase), (uint32_t*)(ws + L.zsub), R, d_out, st,
-                                 h.ebT_bits, s));
+  SZ3G_TRY(launch_recover_levels(pl, codes, base + SZ3G_HEADER_BYTES, h.n_unpred, (unsigned long long*)(ws + L.zunit),
+                                 R, d_out, st, h.ebT_bits, s));
   DevState hs;
   SZ3G_TRY(read_state(st, &hs, s));
   return status_of(hs.flags);
@@ -403,8 +404,7 @@ int sz3g_predict_quantize(const sz3g_params* p, const void* d_in, uint16_t* d_co
   SZ3G_TRY(launch_quantize_levels(pl, d_in, d_codes, R, d_hist, st, s));
   PassMap map;
   make_pass_map(pl, &map);
-  SZ3G_TRY(launch_compact_unpred(pl, d_codes, d_in, &map, (unsigned long long*)(ws + L.wstat),
-                                 (unsigned long long*)(ws + L.zstat), (uint32_t*)(ws + L.table), d_unpred, st, s));
+  SZ3G_TRY(launch_compact_unpred(pl, d_codes, d_in, &map, ws + L.enc, (uint32_t*)(ws + L.table), d_unpred, st, s));
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
   SZ3G_TRY(status_of(h.flags));
@@ -425,16 +425,15 @@ int sz3g_recover(const sz3g_params* p, const void* h_ebT, const uint16_t* d_code
   SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
   DevState* st = (DevState*)(ws + L.st);
   SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
-  SZ3G_TRY(launch_zero_counts(d_codes, pl.N, pl.chunk, pl.nsub, pl.n_chunks, (uint32_t*)(ws + L.zchunk),
-                              (uint32_t*)(ws + L.zsub), s));
-  SZ3G_TRY(launch_scan_u32((uint32_t*)(ws + L.zchunk), pl.n_chunks, (unsigned long long*)(ws + L.zbase), nullptr,
-                           n_unpred, 1, st, s));
+  SZ3G_TRY(launch_zero_counts(d_codes, pl.N, pl.chunk, pl.n_chunks, (uint32_t*)(ws + L.zcnt), s));
+  SZ3G_TRY(launch_scan((uint32_t*)(ws + L.zcnt), pl.n_chunks * pl.nsub, (unsigned long long*)(ws + L.zunit), 0,
+                       n_unpred, 1, ws + L.scan2, st, s));
   unsigned long long eb_bits = 0;
   std::memcpy(&eb_bits, h_ebT, pl.esz);
   void* R[34];
   for (int k = 0; k <= pl.L; ++k) R[k] = k == 0 ? d_out : ws + L.R[k];
-  SZ3G_TRY(launch_recover_levels(pl, d_codes, d_unpred, n_unpred, (unsigned long long*)(ws + L.zbase),
-                                 (uint32_t*)(ws + L.zsub), R, d_out, st, eb_bits, s));
+  SZ3G_TRY(launch_recover_levels(pl, d_codes, d_unpred, n_unpred, (unsigned long long*)(ws + L.zunit), R, d_out,
+                                 st, eb_bits, s));
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
   return status_of(h.flags);
@@ -458,7 +457,7 @@ int sz3g_huffman_build(const uint32_t* d_hist, uint32_t nsym, uint8_t* d_len, ui
 
 int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_len, const uint32_t* d_code,
                         uint32_t nsym, uint32_t chunk, uint32_t* d_words, uint64_t cap_words,
-                        uint32_t* d_chunk_words, uint64_t* h_n_words, void* stream) {
+                        uint32_t* d_chunk_words, uint16_t* d_sub_bits, uint64_t* h_n_words, void* stream) {
   if (!d_codes || !d_len || !d_code || !d_words || !d_chunk_words || n < 1 || nsym < 1 || nsym > (uint32_t)kSyms ||
       chunk < 8 || chunk > 65536 || chunk % 8 || !aligned(d_codes, 16))
     return SZ3G_E_INVAL;
@@ -468,10 +467,11 @@ int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_le
   pl.N = n;
   pl.chunk = chunk;
   pl.n_chunks = (n + chunk - 1) / chunk;
+  pl.nsub = (chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
   pl.esz = 4;
   Layout l;
-  const size_t o_st = l.take(sizeof(DevState)), o_tab = l.take(kSyms * 4), o_w = l.take(pl.n_chunks * 8),
-               o_z = l.take(pl.n_chunks * 8);
+  const size_t o_st = l.take(sizeof(DevState)), o_tab = l.take(kSyms * 4),
+               o_enc = l.take(encode_scratch_bytes(pl.n_chunks));
   Scratch own;
   unsigned char* ws;
   SZ3G_TRY(get_ws(nullptr, 0, l.off, s, own, &ws));
@@ -482,9 +482,8 @@ int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_le
   std::memset(&map, 0, sizeof(map));
   map.n = 1;
   for (int d = 0; d < 4; ++d) map.e[0].E[d] = 1;
-  SZ3G_TRY(launch_encode(pl, d_codes, (uint32_t*)(ws + o_tab), nullptr, &map, (unsigned long long*)(ws + o_w),
-                         (unsigned long long*)(ws + o_z), st, nullptr, 0, kEncodeRaw, d_words, d_chunk_words,
-                         cap_words, s));
+  SZ3G_TRY(launch_encode(pl, d_codes, (uint32_t*)(ws + o_tab), nullptr, &map, ws + o_enc, st, nullptr, 0, kEncodeRaw,
+                         d_words, d_chunk_words, d_sub_bits, cap_words, s));
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
   SZ3G_TRY(status_of(h.flags));
@@ -492,25 +491,25 @@ int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_le
   return SZ3G_OK;
 }
 
-int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_t* d_chunk_words, uint32_t chunk,
-                        const uint8_t* d_len, uint32_t nsym, uint16_t* d_codes, uint64_t n, void* stream) {
+int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_t* d_chunk_words,
+                        const uint16_t* d_sub_bits, uint32_t chunk, const uint8_t* d_len, uint32_t nsym,
+                        uint16_t* d_codes, uint64_t n, void* stream) {
   if (!d_words || !d_chunk_words || !d_len || !d_codes || n < 1 || nsym < 1 || nsym > (uint32_t)kSyms || chunk < 8 ||
       chunk > 65536 || chunk % 8 || !aligned(d_codes, 16))
     return SZ3G_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  const unsigned long long nch = (n + chunk - 1) / chunk, nsub = (chunk + 255) / 256;
+  const unsigned long long nch = (n + chunk - 1) / chunk, nsb = (chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
   Layout l;
   const size_t o_st = l.take(sizeof(DevState)), o_t = l.take(dec_tables_bytes()), o_wo = l.take(nch * 8),
-               o_zc = l.take(nch * 4), o_zs = l.take(nch * nsub * 4);
+               o_zc = l.take(nch * nsb * 4), o_sc = l.take(scan_state_bytes(nch));
   Scratch own;
   unsigned char* ws;
   SZ3G_TRY(get_ws(nullptr, 0, l.off, s, own, &ws));
   DevState* st = (DevState*)(ws + o_st);
   SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
   SZ3G_TRY(launch_decode_tables(nullptr, 0, d_len, nsym, ws + o_t, st, s));
-  SZ3G_TRY(launch_decode_chunks(d_words, n_words, d_chunk_words, nch, chunk, n, ws + o_t,
-                                (unsigned long long*)(ws + o_wo), d_codes, (uint32_t*)(ws + o_zc),
-                                (uint32_t*)(ws + o_zs), (uint32_t)nsub, st, s));
+  SZ3G_TRY(launch_decode_chunks(d_words, n_words, d_chunk_words, d_sub_bits, nch, chunk, n, ws + o_t,
+                                (unsigned long long*)(ws + o_wo), d_codes, (uint32_t*)(ws + o_zc), ws + o_sc, st, s));
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
   return status_of(h.flags);

@@ -15,6 +15,7 @@ namespace sz3g {
 constexpr int kMaxPasses = 1 + 4 * 31;  // anchor + up to 4 passes on each of 31 levels
 constexpr int kSyms = 65536;            // alphabet of uint16 codes
 constexpr int kLutBits = 12;            // direct decode table: first 12 bits of a codeword
+#define SZ3G_SUBBLOCK 512               // codes per decode sub-block inside a chunk
 
 // Status bits raised on the device and read back once per call.
 enum : uint32_t {
@@ -91,7 +92,7 @@ struct Plan {
   int n_pass;                // passes excluding the anchor
   PassDesc pass[kMaxPasses]; // in traversal order (level L first)
   unsigned long long n_chunks;
-  uint32_t nsub;             // 256-code sub-blocks per chunk (decoder)
+  uint32_t nsub;             // 512-code sub-blocks per chunk
 };
 
 // Kernels known to the launch accounting (names in prof.cu).
@@ -227,7 +228,7 @@ int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratc
 int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R,
                            uint32_t* hist, DevState* st, cudaStream_t s);
 int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred,
-                          unsigned long long n_unpred, const unsigned long long* zbase, const uint32_t* zsub,
+                          unsigned long long n_unpred, const unsigned long long* zunit,
                           void* const* R, void* d_out, DevState* st, unsigned long long ebT_bits,
                           cudaStream_t s);
 
@@ -236,7 +237,7 @@ bool level_path_ok(const Plan& pl);
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
                           DevState* st, cudaStream_t s);
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
-                         const unsigned long long* zbase, const uint32_t* zsub, void* const* R, void* d_out,
+                         const unsigned long long* zunit, void* const* R, void* d_out,
                          DevState* st, unsigned long long ebT_bits, cudaStream_t s);
 
 // k_huffman.cu

@@ -78,28 +78,45 @@ __device__ __forceinline__ int pow2_at_least(int k) {
 }
 
 // Two-queue Huffman merge over K leaves sorted by (weight, symbol); node ids:
-// leaves 0..K-1, internal K..2K-2 in creation order.  Single thread.
+// leaves 0..K-1, internal K..2K-2 in creation order.  Single thread.  The
+// next weight of each queue is kept in a register, so a step waits on at most
+// one shared-memory load.
 __device__ void two_queue_merge(const unsigned long long* keys, int K, uint32_t* nf, uint32_t* parent) {
   int li = 0, ni = 0, nn = 0;
-  uint32_t lf = K > 0 ? (uint32_t)(keys[0] >> 16) : 0u;
+  uint32_t lf = (uint32_t)(keys[0] >> 16);  // weight of the next leaf
+  uint32_t lf_next = K > 1 ? (uint32_t)(keys[1] >> 16) : 0u;
+  uint32_t nfront = 0;                      // weight of the next internal node (valid if ni < nn)
   while (nn < K - 1) {
-    uint32_t pick[2], w[2];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      if (li < K && (ni >= nn || lf <= nf[ni])) {
-        pick[t] = (uint32_t)li;
-        w[t] = lf;
-        ++li;
-        lf = li < K ? (uint32_t)(keys[li] >> 16) : 0u;
-      } else {
-        pick[t] = (uint32_t)(K + ni);
-        w[t] = nf[ni];
-        ++ni;
-      }
+    uint32_t pick0, pick1, w0, w1;
+    if (li < K && (ni >= nn || lf <= nfront)) {
+      pick0 = (uint32_t)li;
+      w0 = lf;
+      ++li;
+      lf = lf_next;
+      lf_next = li + 1 < K ? (uint32_t)(keys[li + 1] >> 16) : 0u;
+    } else {
+      pick0 = (uint32_t)(K + ni);
+      w0 = nfront;
+      ++ni;
+      nfront = ni < nn ? nf[ni] : 0u;
     }
-    nf[nn] = w[0] + w[1];
-    parent[pick[0]] = (uint32_t)(K + nn);
-    parent[pick[1]] = (uint32_t)(K + nn);
+    if (li < K && (ni >= nn || lf <= nfront)) {
+      pick1 = (uint32_t)li;
+      w1 = lf;
+      ++li;
+      lf = lf_next;
+      lf_next = li + 1 < K ? (uint32_t)(keys[li + 1] >> 16) : 0u;
+    } else {
+      pick1 = (uint32_t)(K + ni);
+      w1 = nfront;
+      ++ni;
+      nfront = ni < nn ? nf[ni] : 0u;
+    }
+    const uint32_t w = w0 + w1;
+    nf[nn] = w;
+    if (ni == nn) nfront = w;  // the queue was empty: the new node is its front
+    parent[pick0] = (uint32_t)(K + nn);
+    parent[pick1] = (uint32_t)(K + nn);
     ++nn;
   }
 }
@@ -124,33 +141,51 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
                                                               unsigned long long out_capacity, int esz) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_warp[32];
+  __shared__ uint32_t s_wcount[32];
   __shared__ uint32_t s_cnt[SZ3G_LMAX + 2], s_start[SZ3G_LMAX + 2], s_fc[SZ3G_LMAX + 2];
   __shared__ int s_deep;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kPerWarp = kSyms / (kCbThreads / 32);  // 2048 symbols per warp, 64 rounds of 32
 
-  // 1. used symbols in symbol order (each thread a contiguous 64-symbol run)
-  const int per = kSyms / kCbThreads;
-  uint32_t mine = 0;
-  for (int s = tid * per; s < tid * per + per; ++s) {
-    const uint32_t f = s < (int)nsym ? hist[s] : 0u;
-    if (s >= (int)nsym && hist[s]) atomicOr(&st->flags, kFlagCorrupt);
-    table[s] = 0u;
-    if (len_out) len_out[s] = 0;
-    if (code_out) code_out[s] = 0;
-    mine += f != 0;
+  // 1. used symbols in symbol order: each warp owns a contiguous run of
+  //    2048 symbols, read 32 at a time (coalesced), ranked with ballots
+  uint32_t wcount = 0;
+  for (int r = 0; r < kPerWarp; r += 32) {
+    const int sy = warp * kPerWarp + r + lane;
+    const uint32_t f = hist[sy];
+    if (sy >= (int)nsym && f) atomicOr(&st->flags, kFlagCorrupt);
+    wcount += __popc(__ballot_sync(0xffffffffu, f != 0 && sy < (int)nsym));
   }
-  unsigned long long Ktot;
-  unsigned long long pos = block_exclusive_scan(mine, s_warp, &Ktot);
-  for (int s = tid * per; s < tid * per + per && s < (int)nsym; ++s) {
-    const uint32_t f = hist[s];
-    if (f) {
-      g->sym[pos] = (uint32_t)s;
-      g->freq[pos] = f;
-      ++pos;
+  if (lane == 0) s_wcount[warp] = wcount;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < kCbThreads / 32 ? s_wcount[lane] : 0u, x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
+    if (lane < kCbThreads / 32) s_wcount[lane] = x - v;  // exclusive
+    if (lane == 31) s_warp[0] = x;
   }
   __syncthreads();
-  const int K = (int)Ktot;
+  const int K = (int)s_warp[0];
+  uint32_t pos = s_wcount[warp];
+  for (int r = 0; r < kPerWarp; r += 32) {
+    const int sy = warp * kPerWarp + r + lane;
+    const uint32_t f = hist[sy];
+    const bool used = f != 0 && sy < (int)nsym;
+    const unsigned m = __ballot_sync(0xffffffffu, used);
+    if (used) {
+      const uint32_t q = pos + __popc(m & ((1u << lane) - 1u));
+      g->sym[q] = (uint32_t)sy;
+      g->freq[q] = f;
+    }
+    pos += __popc(m);
+    table[sy] = 0u;
+    if (len_out && sy < (int)nsym) len_out[sy] = 0;
+    if (code_out && sy < (int)nsym) code_out[sy] = 0;
+  }
+  __syncthreads();
   if (K == 0) {
     if (tid == 0) atomicOr(&st->flags, kFlagCorrupt);
     return;
@@ -303,17 +338,20 @@ __device__ unsigned long long lookback(unsigned long long* stat, long long j, De
 struct EncArgs {
   const uint16_t* codes;
   const uint32_t* table;
-  const void* x;                // input field (unpredictable values), stream mode
+  const void* x;                // input field (unpredictable values)
   unsigned long long n, n_chunks;
   uint32_t chunk;
   int esz;
-  unsigned long long* wstat;
-  unsigned long long* zstat;
+  const uint32_t* cwords;       // words of every chunk (from count_kernel)
+  const unsigned long long* wexcl;  // exclusive prefix of cwords
+  const unsigned long long* zexcl;  // exclusive prefix of the zero codes per chunk
   DevState* st;
   unsigned char* d_out;         // stream mode: the output stream
   unsigned long long out_capacity;
   uint32_t* words_out;          // raw mode: payload
   uint32_t* chunk_words_out;    // raw mode: words per chunk
+  uint16_t* sub_out;            // raw mode: sub-block bit lengths (nsb - 1 per chunk), or null
+  uint32_t nsb;                 // 512-code sub-blocks per chunk
   unsigned long long cap_words; // raw mode
   void* unpred_out;             // raw mode: unpredictable values (or null)
   int mode;                     // kEncodeStream / kEncodeRaw
@@ -341,25 +379,19 @@ __device__ __forceinline__ unsigned long long map_code_to_input(const PassMap& m
   return e.xstart + j * e.xls[0] + c1 * e.xls[1] + c2 * e.xls[2] + c3 * e.xls[3];
 }
 
-template <typename U>
-__global__ void __launch_bounds__(kEncWarps * 32) encode_kernel(const EncArgs a, const __grid_constant__ PassMap map) {
-  __shared__ uint32_t ring[kEncWarps][kRingWords];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t* buf = ring[w];
-  for (int k = lane; k < kRingWords; k += 32) buf[k] = 0;
-  __syncwarp();
-  DevState* st = a.st;
-  for (;;) {
-    unsigned long long j = 0;
-    if (lane == 0) j = atomicAdd(&st->ticket, 1u);
-    j = __shfl_sync(0xffffffffu, j, 0);
-    if (j >= a.n_chunks) break;
-    const unsigned long long i0 = j * a.chunk;
-    const uint32_t cnt = (uint32_t)min((unsigned long long)a.chunk, a.n - i0);
-    const uint16_t* cp = a.codes + i0;
-    // pass 1: bits and zeros of the chunk
-    unsigned long long bits = 0;
-    uint32_t zeros = 0;
+// Pass 1 of the encoder: bits (as 32-bit words) and zero codes of every chunk.
+__global__ void __launch_bounds__(kEncWarps * 32) count_kernel(const uint16_t* __restrict__ codes,
+                                                               const uint32_t* __restrict__ table, unsigned long long n,
+                                                               unsigned long long n_chunks, uint32_t chunk,
+                                                               uint32_t* cwords, uint32_t* czeros) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * kEncWarps;
+  for (unsigned long long j = (unsigned long long)blockIdx.x * kEncWarps + (threadIdx.x >> 5); j < n_chunks;
+       j += nwarps) {
+    const unsigned long long i0 = j * chunk;
+    const uint32_t cnt = (uint32_t)min((unsigned long long)chunk, n - i0);
+    const uint16_t* cp = codes + i0;
+    uint32_t bits = 0, zeros = 0;
     for (uint32_t t = lane * 8; t < cnt; t += 256) {
       if (t + 8 <= cnt) {
         const uint4 v = *reinterpret_cast<const uint4*>(cp + t);
@@ -367,13 +399,13 @@ __global__ void __launch_bounds__(kEncWarps * 32) encode_kernel(const EncArgs a,
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t c0 = wv[q] & 0xffffu, c1 = wv[q] >> 16;
-          bits += (a.table[c0] >> 24) + (a.table[c1] >> 24);
+          bits += (table[c0] >> 24) + (table[c1] >> 24);
           zeros += (c0 == 0) + (c1 == 0);
         }
       } else {
         for (uint32_t u = t; u < cnt; ++u) {
           const uint32_t c = cp[u];
-          bits += a.table[c] >> 24;
+          bits += table[c] >> 24;
           zeros += c == 0;
         }
       }
@@ -382,30 +414,47 @@ __global__ void __launch_bounds__(kEncWarps * 32) encode_kernel(const EncArgs a,
       bits += __shfl_xor_sync(0xffffffffu, bits, o);
       zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
     }
-    const unsigned long long words = (bits + 31) >> 5;
     if (lane == 0) {
-      st_release(a.wstat + j, (j == 0 ? kFlagInc : kFlagAgg) | words);
-      st_release(a.zstat + j, (j == 0 ? kFlagInc : kFlagAgg) | zeros);
+      cwords[j] = (bits + 31) >> 5;
+      czeros[j] = zeros;
     }
-    const unsigned long long wexcl = lookback(a.wstat, (long long)j, st);
-    const unsigned long long zexcl = lookback(a.zstat, (long long)j, st);
-    if (lane == 0 && j > 0) {
-      st_release(a.wstat + j, kFlagInc | (wexcl + words));
-      st_release(a.zstat + j, kFlagInc | (zexcl + zeros));
-    }
+  }
+}
+
+// Pass 2: one warp per chunk writes the chunk's bits (MSB first, through a
+// shared-memory word ring), its table entries, and gathers its unpredictable
+// values from the input.
+template <typename U>
+__global__ void __launch_bounds__(kEncWarps * 32) emit_kernel(const EncArgs a, const __grid_constant__ PassMap map) {
+  __shared__ uint32_t ring[kEncWarps][kRingWords];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* buf = ring[w];
+  for (int k = lane; k < kRingWords; k += 32) buf[k] = 0;
+  __syncwarp();
+  DevState* st = a.st;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * kEncWarps;
+  for (unsigned long long j = (unsigned long long)blockIdx.x * kEncWarps + w; j < a.n_chunks; j += nwarps) {
+    const unsigned long long i0 = j * a.chunk;
+    const uint32_t cnt = (uint32_t)min((unsigned long long)a.chunk, a.n - i0);
+    const uint16_t* cp = a.codes + i0;
+    const unsigned long long words = a.cwords[j];
+    const unsigned long long wexcl = a.wexcl[j], zexcl = a.zexcl[j];
     if (lane == 0 && j == a.n_chunks - 1) st->n_words = wexcl + words;
     // destinations
     uint32_t* pay;
+    uint16_t* sub = nullptr;
     U* unp;
     bool ok = true;
     if (a.mode == kEncodeStream) {
       const unsigned long long nu = st->n_unpred;
       const unsigned long long off_table = SZ3G_HEADER_BYTES + pad8(nu * a.esz);
       const unsigned long long off_chunks = off_table + pad8(3ull * st->n_used);
-      const unsigned long long off_payload = off_chunks + pad8(a.n_chunks * 4);
+      const unsigned long long off_sub = off_chunks + pad8(a.n_chunks * 4);
+      const unsigned long long off_payload = off_sub + pad8(a.n_chunks * (a.nsb - 1) * 2);
       unp = reinterpret_cast<U*>(a.d_out + SZ3G_HEADER_BYTES);
       pay = reinterpret_cast<uint32_t*>(a.d_out + off_payload);
-      if (off_payload + 4 * (wexcl + words) > a.out_capacity || zexcl + zeros > nu) {
+      if (a.nsb > 1) sub = reinterpret_cast<uint16_t*>(a.d_out + off_sub) + j * (a.nsb - 1);
+      if (off_payload + 4 * (wexcl + words) > a.out_capacity) {
         ok = false;
         if (lane == 0) atomicOr(&st->flags, kFlagCapacity);
       } else if (lane == 0) {
@@ -414,6 +463,7 @@ __global__ void __launch_bounds__(kEncWarps * 32) encode_kernel(const EncArgs a,
     } else {
       unp = reinterpret_cast<U*>(a.unpred_out);
       pay = a.words_out;
+      if (a.sub_out && a.nsb > 1) sub = a.sub_out + j * (a.nsb - 1);
       if (a.emit_payload) {
         if (wexcl + words > a.cap_words) {
           ok = false;
@@ -424,11 +474,13 @@ __global__ void __launch_bounds__(kEncWarps * 32) encode_kernel(const EncArgs a,
       }
     }
     if (!ok) continue;
-    // pass 2: emit the bits, gather the unpredictable values
     const bool emit = a.emit_payload != 0;
     unsigned long long wpos = wexcl;  // next word to write
     uint32_t carry = 0;               // bits pending in buf[0]
     unsigned long long zpos = zexcl;
+    uint32_t sbits = 0;               // bits of the current 512-code sub-block
+    if (emit && sub && lane == 0)     // sub-blocks past the end of a short chunk are empty
+      for (uint32_t b = (cnt + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK; b + 1 < a.nsb; ++b) sub[b] = 0;
     for (uint32_t r0 = 0; r0 < cnt; r0 += 256) {
       const uint32_t t = r0 + lane * 8;
       uint32_t c8[8];
@@ -440,14 +492,16 @@ __global__ void __launch_bounds__(kEncWarps * 32) encode_kernel(const EncArgs a,
         c8[0] = v.x & 0xffffu; c8[1] = v.x >> 16; c8[2] = v.y & 0xffffu; c8[3] = v.y >> 16;
         c8[4] = v.z & 0xffffu; c8[5] = v.z >> 16; c8[6] = v.w & 0xffffu; c8[7] = v.w >> 16;
       } else {
-        for (uint32_t u = t; u < cnt; ++u) c8[u - t] = cp[u];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (t + q < cnt) c8[q] = cp[t + q];
       }
+      uint32_t e8[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        if (c8[q] != 0xffffffffu) {
-          nb += a.table[c8[q]] >> 24;
-          nzl += c8[q] == 0;
-        }
+        e8[q] = c8[q] != 0xffffffffu ? a.table[c8[q]] : 0u;
+        nb += e8[q] >> 24;
+        nzl += c8[q] == 0;
       }
       uint32_t incl = nb, zincl = nzl;
       for (int o = 1; o < 32; o <<= 1) {
@@ -460,13 +514,18 @@ __global__ void __launch_bounds__(kEncWarps * 32) encode_kernel(const EncArgs a,
       }
       const uint32_t round_bits = __shfl_sync(0xffffffffu, incl, 31);
       const uint32_t round_zeros = __shfl_sync(0xffffffffu, zincl, 31);
+      sbits += round_bits;
+      if ((r0 & 256) || r0 + 256 >= cnt) {  // a sub-block ends with this round
+        const uint32_t b = r0 >> 9;
+        if (emit && sub && lane == 0 && b + 1 < a.nsb) sub[b] = (uint16_t)sbits;
+        sbits = 0;
+      }
       if (emit) {
         uint32_t o = carry + incl - nb;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          if (c8[q] == 0xffffffffu) continue;
-          const uint32_t e = a.table[c8[q]];
-          const uint32_t L = e >> 24, val = e & 0xffffffu;
+          const uint32_t L = e8[q] >> 24, val = e8[q] & 0xffffffu;
+          if (L == 0) continue;
           const uint32_t wi = o >> 5, sh = o & 31;
           if (sh + L <= 32) {
             atomicOr(&buf[wi], val << (32 - sh - L));
@@ -509,21 +568,110 @@ __global__ void __launch_bounds__(kEncWarps * 32) encode_kernel(const EncArgs a,
   }
 }
 
-int launch_encode_impl(const EncArgs& a, const PassMap* map, cudaStream_t s) {
-  int nb = (int)((a.n_chunks + kEncWarps - 1) / kEncWarps);
+// ---------------------------------------------------------------------------
+// Device-wide exclusive prefix sum of n uint32 values into uint64, one pass:
+// each CTA scans a tile of kScanTile values and finds the total of the tiles
+// before it by decoupled look-back.  Optionally checks that every value is
+// <= limit and that the grand total equals `expect` (else: corrupt flag).
+// `state` is scan_state_bytes(n) of scratch, zeroed by the launcher.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256, kScanPer = 16, kScanTile = kScanThreads * kScanPer;
+
+size_t scan_state_bytes(unsigned long long n) { return 256 + 8 * ((n + kScanTile - 1) / kScanTile + 1); }
+
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* in, unsigned long long n,
+                                                            unsigned long long* out, uint32_t limit,
+                                                            unsigned long long expect, int check_expect,
+                                                            unsigned char* state, DevState* st) {
+  __shared__ unsigned long long s_warp[32];
+  __shared__ unsigned long long s_excl;
+  __shared__ unsigned long long s_tile;
+  uint32_t* ticket = reinterpret_cast<uint32_t*>(state);
+  unsigned long long* stat = reinterpret_cast<unsigned long long*>(state + 256);
+  const unsigned long long ntiles = (n + kScanTile - 1) / kScanTile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const unsigned long long t = s_tile;
+  if (t >= ntiles) return;
+  const unsigned long long b = t * kScanTile + (unsigned long long)threadIdx.x * kScanPer;
+  uint32_t v[kScanPer];
+  unsigned long long sum = 0;
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = b + k < n ? in[b + k] : 0u;
+    if (limit && v[k] > limit) bad = true;
+    sum += v[k];
+  }
+  unsigned long long agg;
+  unsigned long long run = block_exclusive_scan(sum, s_warp, &agg);
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) st_release(stat + t, (t == 0 ? kFlagInc : kFlagAgg) | agg);
+    const unsigned long long ex = lookback(stat, (long long)t, st);
+    if (threadIdx.x == 0) {
+      if (t > 0) st_release(stat + t, kFlagInc | (ex + agg));
+      s_excl = ex;
+      if (check_expect && t == ntiles - 1 && ex + agg != expect) atomicOr(&st->flags, kFlagCorrupt);
+    }
+  }
+  __syncthreads();
+  run += s_excl;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (b + k < n) out[b + k] = run;
+    run += v[k];
+  }
+  if (bad) atomicOr(&st->flags, kFlagCorrupt);
+}
+
+int launch_scan(const uint32_t* in, unsigned long long n, unsigned long long* out, uint32_t limit,
+                unsigned long long expect, int check_expect, void* state, DevState* st, cudaStream_t s) {
+  if (cudaMemsetAsync(state, 0, scan_state_bytes(n), s) != cudaSuccess) return SZ3G_E_CUDA;
+  const unsigned long long ntiles = (n + kScanTile - 1) / kScanTile;
+  SZ3G_LAUNCH(kKScan, s,
+              scan_kernel<<<(unsigned)(ntiles ? ntiles : 1), kScanThreads, 0, s>>>(
+                  in, n, out, limit, expect, check_expect, (unsigned char*)state, st));
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+size_t encode_scratch_bytes(unsigned long long n_chunks) {
+  return 2 * ((n_chunks * 4 + 255) & ~255ull) + 2 * ((n_chunks * 8 + 255) & ~255ull) +
+         2 * ((scan_state_bytes(n_chunks) + 255) & ~255ull);
+}
+
+// count -> two scans -> emit.  scratch: encode_scratch_bytes(n_chunks).
+static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch, cudaStream_t s) {
+  const unsigned long long nch = a.n_chunks;
+  const size_t a4 = (nch * 4 + 255) & ~255ull, a8 = (nch * 8 + 255) & ~255ull,
+               as = (scan_state_bytes(nch) + 255) & ~255ull;
+  uint32_t* cw = (uint32_t*)scratch;
+  uint32_t* cz = (uint32_t*)(scratch + a4);
+  unsigned long long* we = (unsigned long long*)(scratch + 2 * a4);
+  unsigned long long* ze = (unsigned long long*)(scratch + 2 * a4 + a8);
+  unsigned char* s1 = scratch + 2 * a4 + 2 * a8;
+  unsigned char* s2 = s1 + as;
+  int nb = (int)((nch + kEncWarps - 1) / kEncWarps);
   if (nb > 152 * 8) nb = 152 * 8;
   if (nb < 1) nb = 1;
+  SZ3G_LAUNCH(kKEncode, s, count_kernel<<<nb, kEncWarps * 32, 0, s>>>(a.codes, a.table, a.n, nch, a.chunk, cw, cz));
+  int rc = launch_scan(cw, nch, we, 0, 0, 0, s1, a.st, s);
+  if (rc) return rc;
+  rc = launch_scan(cz, nch, ze, 0, 0, 0, s2, a.st, s);
+  if (rc) return rc;
+  a.cwords = cw;
+  a.wexcl = we;
+  a.zexcl = ze;
   if (a.esz == 4)
-    SZ3G_LAUNCH(kKEncode, s, encode_kernel<uint32_t><<<nb, kEncWarps * 32, 0, s>>>(a, *map));
+    SZ3G_LAUNCH(kKEncode, s, emit_kernel<uint32_t><<<nb, kEncWarps * 32, 0, s>>>(a, *map));
   else
-    SZ3G_LAUNCH(kKEncode, s, encode_kernel<unsigned long long><<<nb, kEncWarps * 32, 0, s>>>(a, *map));
+    SZ3G_LAUNCH(kKEncode, s, emit_kernel<unsigned long long><<<nb, kEncWarps * 32, 0, s>>>(a, *map));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
 int launch_encode(const Plan& pl, const uint16_t* codes, const uint32_t* table, const void* d_in, const PassMap* map,
-                  unsigned long long* wstat, unsigned long long* zstat, DevState* st, unsigned char* d_out,
-                  unsigned long long out_capacity, int mode, uint32_t* words_out, uint32_t* chunk_words_out,
-                  unsigned long long cap_words, cudaStream_t s) {
+                  void* scratch, DevState* st, unsigned char* d_out, unsigned long long out_capacity, int mode,
+                  uint32_t* words_out, uint32_t* chunk_words_out, uint16_t* sub_out, unsigned long long cap_words,
+                  cudaStream_t s) {
   EncArgs a{};
   a.codes = codes;
   a.table = table;
@@ -532,24 +680,23 @@ int launch_encode(const Plan& pl, const uint16_t* codes, const uint32_t* table, 
   a.n_chunks = pl.n_chunks;
   a.chunk = pl.chunk;
   a.esz = pl.esz;
-  a.wstat = wstat;
-  a.zstat = zstat;
   a.st = st;
   a.d_out = d_out;
   a.out_capacity = out_capacity;
   a.words_out = words_out;
   a.chunk_words_out = chunk_words_out;
+  a.sub_out = sub_out;
+  a.nsb = (pl.chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
   a.cap_words = cap_words;
   a.unpred_out = nullptr;
   a.mode = mode;
   a.emit_payload = 1;
-  return launch_encode_impl(a, map, s);
+  return encode_pipeline(a, map, (unsigned char*)scratch, s);
 }
 
 // Unpredictable values in traversal order, without encoding (stage API).
-int launch_compact_unpred(const Plan& pl, const uint16_t* codes, const void* d_in, const PassMap* map,
-                          unsigned long long* wstat, unsigned long long* zstat, const uint32_t* table,
-                          void* d_unpred, DevState* st, cudaStream_t s) {
+int launch_compact_unpred(const Plan& pl, const uint16_t* codes, const void* d_in, const PassMap* map, void* scratch,
+                          const uint32_t* table, void* d_unpred, DevState* st, cudaStream_t s) {
   EncArgs a{};
   a.codes = codes;
   a.table = table;
@@ -558,13 +705,12 @@ int launch_compact_unpred(const Plan& pl, const uint16_t* codes, const void* d_i
   a.n_chunks = pl.n_chunks;
   a.chunk = pl.chunk;
   a.esz = pl.esz;
-  a.wstat = wstat;
-  a.zstat = zstat;
   a.st = st;
   a.mode = kEncodeRaw;
   a.emit_payload = 0;
+  a.nsb = (pl.chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
   a.unpred_out = d_unpred;
-  return launch_encode_impl(a, map, s);
+  return encode_pipeline(a, map, (unsigned char*)scratch, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -574,6 +720,7 @@ struct HeaderArgs {
   unsigned char bytes[SZ3G_HEADER_BYTES];  // static fields, counts filled on device
   unsigned long long n_chunks;
   int esz;
+  uint32_t nsb;  // 512-code sub-blocks per chunk
 };
 
 __global__ void finalize_kernel(const HeaderArgs h, DevState* st, unsigned char* d_out,
@@ -584,7 +731,9 @@ __global__ void finalize_kernel(const HeaderArgs h, DevState* st, unsigned char*
   const uint32_t nused = st->n_used;
   const unsigned long long off_table = SZ3G_HEADER_BYTES + pad8(nu * h.esz);
   const unsigned long long off_chunks = off_table + pad8(3ull * nused);
-  const unsigned long long off_payload = off_chunks + pad8(h.n_chunks * 4);
+  const unsigned long long off_sub = off_chunks + pad8(h.n_chunks * 4);
+  const unsigned long long n_sub = h.n_chunks * (h.nsb - 1);
+  const unsigned long long off_payload = off_sub + pad8(n_sub * 2);
   const unsigned long long end = off_payload + pad8(nw * 4);
   if (end > out_capacity) {
     if (tid == 0) atomicOr(&st->flags, kFlagCapacity);
@@ -604,7 +753,9 @@ __global__ void finalize_kernel(const HeaderArgs h, DevState* st, unsigned char*
     const unsigned long long u_end = SZ3G_HEADER_BYTES + nu * h.esz;
     if (u_end + tid < off_table) d_out[u_end + tid] = 0;
     const unsigned long long c_end = off_chunks + h.n_chunks * 4;
-    if (c_end + tid < off_payload) d_out[c_end + tid] = 0;
+    if (c_end + tid < off_sub) d_out[c_end + tid] = 0;
+    const unsigned long long s_end = off_sub + n_sub * 2;
+    if (s_end + tid < off_payload) d_out[s_end + tid] = 0;
     const unsigned long long p_end = off_payload + nw * 4;
     if (p_end + tid < end) d_out[p_end + tid] = 0;
   }
@@ -647,6 +798,7 @@ int launch_finalize(const Plan& pl, const sz3g_params* p, DevState* st, unsigned
   for (int i = 0; i < 4; ++i) b[272 + i] = i < (int)p->ndim ? p->dim_order[i] : 0;
   h.n_chunks = pl.n_chunks;
   h.esz = pl.esz;
+  h.nsb = pl.nsub;
   SZ3G_LAUNCH(kKFinalize, s, finalize_kernel<<<1, 64, 0, s>>>(h, st, d_out, out_capacity));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
@@ -763,16 +915,23 @@ struct DecArgs {
   const uint32_t* words;
   const unsigned long long* woff;  // word offset of every chunk
   const uint32_t* chunk_words;
+  const uint16_t* sub_bits;        // bit lengths of 512-code sub-blocks (nsb - 1 per chunk), or null
   unsigned long long n_chunks, n;
-  uint32_t chunk, nsub;
+  uint32_t chunk, nsb;             // nsb = 512-code sub-blocks per chunk
+  uint32_t unit, upc;              // codes per decoding thread, threads per chunk
   const DecTables* T;
   uint16_t* codes;
-  uint32_t* zchunk;  // zero codes per chunk
-  uint32_t* zsub;    // zero codes before each 256-code block of a chunk
+  uint32_t* zcnt;                  // zero codes per 512-code sub-block
   DevState* st;
 };
 
-__global__ void __launch_bounds__(128) decode_kernel(const DecArgs a) {
+// One thread decodes one unit: a 512-code sub-block when the stream carries
+// sub-block lengths (its start bit is their sum), else a whole chunk.
+// Large CTAs: the shared-memory lookup table is then held once per many warps,
+// leaving L1 for the per-thread payload streams.
+constexpr int kDecThreads = 512;
+
+__global__ void __launch_bounds__(kDecThreads) decode_kernel(const DecArgs a) {
   if (a.st->flags & kFlagCorrupt) return;  // tables or chunk table rejected
   __shared__ uint32_t lut[1 << kLutBits];
   __shared__ uint32_t fc[SZ3G_LMAX + 2], cnt[SZ3G_LMAX + 2], start[SZ3G_LMAX + 2];
@@ -783,21 +942,49 @@ __global__ void __launch_bounds__(128) decode_kernel(const DecArgs a) {
     start[threadIdx.x] = a.T->start[threadIdx.x];
   }
   __syncthreads();
-  const unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.n_chunks) return;
-  const unsigned long long i0 = j * a.chunk;
-  const uint32_t n = (uint32_t)min((unsigned long long)a.chunk, a.n - i0);
-  const uint32_t* wp = a.words + a.woff[j];
+  const unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= a.n_chunks * a.upc) return;
+  const unsigned long long j = u / a.upc;
+  const uint32_t b = (uint32_t)(u - j * a.upc);
+  const uint32_t n_chunk = (uint32_t)min((unsigned long long)a.chunk, a.n - j * a.chunk);
+  const uint32_t c0 = b * a.unit;
   const uint32_t nw = a.chunk_words[j];
-  uint32_t wi = 0;
+  const uint16_t* sb = a.sub_bits ? a.sub_bits + j * (a.nsb - 1) : nullptr;
+  bool bad = false;
+  unsigned long long bit0 = 0;  // start bit of the unit inside the chunk
+  if (sb)
+    for (uint32_t q = 0; q < b; ++q) bit0 += sb[q];
+  if (c0 >= n_chunk) {  // past the end of a short last chunk
+    if (sb && b + 1 < a.nsb && sb[b] != 0) bad = true;
+    if (a.unit == SZ3G_SUBBLOCK) a.zcnt[j * a.nsb + b] = 0;
+    if (bad) atomicOr(&a.st->flags, kFlagCorrupt);
+    return;
+  }
+  const uint32_t c1 = min(c0 + a.unit, n_chunk);
+  if (bit0 > 32ull * nw) {
+    atomicOr(&a.st->flags, kFlagCorrupt);
+    return;
+  }
+  const uint32_t* wp = a.words + a.woff[j];
+  uint32_t wi = (uint32_t)(bit0 >> 5);
   unsigned long long buf = 0;
   int nb = 0;
+  if (wi < nw) {
+    buf = (unsigned long long)wp[wi++] << 32;
+    nb = 32;
+    const int skip = (int)(bit0 & 31);
+    buf <<= skip;
+    nb -= skip;
+  }
+  unsigned long long used = bit0;
   uint32_t zeros = 0;
-  bool bad = false;
   uint32_t pack[4] = {0, 0, 0, 0};
-  uint16_t* out = a.codes + i0;
-  for (uint32_t i = 0; i < n; ++i) {
-    if ((i & 255) == 0) a.zsub[j * a.nsub + (i >> 8)] = zeros;
+  uint16_t* out = a.codes + j * a.chunk;
+  for (uint32_t i = c0; i < c1; ++i) {
+    if (i != c0 && (i & (SZ3G_SUBBLOCK - 1)) == 0) {  // whole-chunk units count per sub-block
+      a.zcnt[j * a.nsb + ((i >> 9) - 1)] = zeros;
+      zeros = 0;
+    }
     while (nb <= 32 && wi < nw) {
       buf |= (unsigned long long)wp[wi++] << (32 - nb);
       nb += 32;
@@ -823,6 +1010,7 @@ __global__ void __launch_bounds__(128) decode_kernel(const DecArgs a) {
     }
     buf <<= L;
     nb -= (int)L;
+    used += L;
     zeros += sym == 0;
     const uint32_t q = i & 7;
     pack[q >> 1] |= sym << (16 * (q & 1));
@@ -832,42 +1020,14 @@ __global__ void __launch_bounds__(128) decode_kernel(const DecArgs a) {
     }
   }
   if (!bad) {
-    const uint32_t rem = n & 7;
-    for (uint32_t q = 0; q < rem; ++q) out[n - rem + q] = (uint16_t)(pack[q >> 1] >> (16 * (q & 1)));
-    a.zchunk[j] = zeros;
-  } else {
-    atomicOr(&a.st->flags, kFlagCorrupt);
-    a.zchunk[j] = 0;
+    const uint32_t rem = c1 & 7;  // c0 is a multiple of 8
+    for (uint32_t q = 0; q < rem; ++q) out[c1 - rem + q] = (uint16_t)(pack[q >> 1] >> (16 * (q & 1)));
+    a.zcnt[j * a.nsb + ((c1 - 1) >> 9)] = zeros;
+    // the recorded sub-block boundary must be exactly where decoding ended
+    if (sb && a.unit == SZ3G_SUBBLOCK && b + 1 < a.nsb && used != bit0 + sb[b]) bad = true;
+    if (used > 32ull * nw) bad = true;
   }
-}
-
-// Exclusive prefix of n values (u32 in, u64 out) in one CTA; total -> *total.
-// If limit != 0, every value must be <= limit.
-__global__ void __launch_bounds__(kCbThreads) scan_u32_kernel(const uint32_t* in, unsigned long long n,
-                                                              unsigned long long* out, unsigned long long* total,
-                                                              uint32_t limit, unsigned long long expect,
-                                                              int check_expect, DevState* st) {
-  __shared__ unsigned long long s_warp[32];
-  const unsigned long long per = (n + kCbThreads - 1) / kCbThreads;
-  const unsigned long long b = threadIdx.x * per, e = min(n, b + per);
-  unsigned long long sum = 0;
-  bool bad = false;
-  for (unsigned long long i = b; i < e; ++i) {
-    const uint32_t v = in[i];
-    if (limit && v > limit) bad = true;
-    sum += v;
-  }
-  unsigned long long tot;
-  unsigned long long run = block_exclusive_scan(sum, s_warp, &tot);
-  for (unsigned long long i = b; i < e; ++i) {
-    out[i] = run;
-    run += in[i];
-  }
-  if (bad) atomicOr(&st->flags, kFlagCorrupt);
-  if (threadIdx.x == 0) {
-    if (total) *total = tot;
-    if (check_expect && tot != expect) atomicOr(&st->flags, kFlagCorrupt);
-  }
+  if (bad) atomicOr(&a.st->flags, kFlagCorrupt);
 }
 
 size_t dec_tables_bytes() { return sizeof(DecTables); }
@@ -883,57 +1043,60 @@ int launch_decode_tables(const unsigned char* tab, uint32_t n_used, const uint8_
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
-// words: payload; chunk_words: per-chunk word counts (validated here).
+// words: payload; chunk_words: per-chunk word counts (validated here);
+// sub_bits: sub-block lengths or null.  zcnt: zero codes per 512-code block.
 int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, const uint32_t* chunk_words,
-                         unsigned long long n_chunks, uint32_t chunk, unsigned long long n, const void* tables,
-                         unsigned long long* woff, uint16_t* codes, uint32_t* zchunk, uint32_t* zsub, uint32_t nsub,
-                         DevState* st, cudaStream_t s) {
+                         const uint16_t* sub_bits, unsigned long long n_chunks, uint32_t chunk, unsigned long long n,
+                         const void* tables, unsigned long long* woff, uint16_t* codes, uint32_t* zcnt,
+                         void* scan_state, DevState* st, cudaStream_t s) {
   const uint32_t maxw = (uint32_t)(((unsigned long long)chunk * SZ3G_LMAX + 31) / 32);
-  SZ3G_LAUNCH(kKScan, s, scan_u32_kernel<<<1, kCbThreads, 0, s>>>(chunk_words, n_chunks, woff, nullptr, maxw, n_words, 1, st));
+  const int rc = launch_scan(chunk_words, n_chunks, woff, maxw, n_words, 1, scan_state, st, s);
+  if (rc) return rc;
   DecArgs a{};
   a.words = words;
   a.woff = woff;
   a.chunk_words = chunk_words;
+  a.sub_bits = sub_bits;
   a.n_chunks = n_chunks;
   a.n = n;
   a.chunk = chunk;
-  a.nsub = nsub;
+  a.nsb = (chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
+  a.unit = (sub_bits && a.nsb > 1) ? (uint32_t)SZ3G_SUBBLOCK : chunk;
+  a.upc = (chunk + a.unit - 1) / a.unit;
   a.T = (const DecTables*)tables;
   a.codes = codes;
-  a.zchunk = zchunk;
-  a.zsub = zsub;
+  a.zcnt = zcnt;
   a.st = st;
-  SZ3G_LAUNCH(kKDecode, s, decode_kernel<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(a));
+  const unsigned long long threads = n_chunks * a.upc;
+  SZ3G_LAUNCH(kKDecode, s, decode_kernel<<<(unsigned)((threads + kDecThreads - 1) / kDecThreads), kDecThreads, 0, s>>>(a));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
-// Zero-code counts per chunk and per 256-code block from a code array (used
-// when codes come from the caller instead of the decoder).
-__global__ void zero_count_kernel(const uint16_t* codes, unsigned long long n, uint32_t chunk, uint32_t nsub,
-                                  unsigned long long n_chunks, uint32_t* zchunk, uint32_t* zsub) {
-  const unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n_chunks) return;
-  const unsigned long long i0 = j * chunk;
-  const uint32_t cnt = (uint32_t)min((unsigned long long)chunk, n - i0);
+// Zero-code counts per 512-code sub-block of every chunk, from a code array
+// (used when codes come from the caller instead of the decoder).
+__global__ void zero_count_kernel(const uint16_t* codes, unsigned long long n, uint32_t chunk, uint32_t nsb,
+                                  unsigned long long n_chunks, uint32_t* zcnt) {
+  const unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n_chunks * nsb) return;
+  const unsigned long long j = u / nsb;
+  const uint32_t b = (uint32_t)(u - j * nsb);
+  const unsigned long long n_chunk = min((unsigned long long)chunk, n - j * chunk);
+  const unsigned long long i0 = j * chunk + (unsigned long long)b * SZ3G_SUBBLOCK;
+  const unsigned long long i1 = j * chunk + min((unsigned long long)(b + 1) * SZ3G_SUBBLOCK, n_chunk);
   uint32_t z = 0;
-  for (uint32_t i = 0; i < cnt; ++i) {
-    if ((i & 255) == 0) zsub[j * nsub + (i >> 8)] = z;
-    z += codes[i0 + i] == 0;
-  }
-  zchunk[j] = z;
+  for (unsigned long long i = i0; i < i1; ++i) z += codes[i] == 0;
+  zcnt[u] = z;
 }
 
-int launch_zero_counts(const uint16_t* codes, unsigned long long n, uint32_t chunk, uint32_t nsub,
-                       unsigned long long n_chunks, uint32_t* zchunk, uint32_t* zsub, cudaStream_t s) {
-  SZ3G_LAUNCH(kKZeroCount, s, zero_count_kernel<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(codes, n, chunk, nsub, n_chunks, zchunk, zsub));
+int launch_zero_counts(const uint16_t* codes, unsigned long long n, uint32_t chunk, unsigned long long n_chunks,
+                       uint32_t* zcnt, cudaStream_t s) {
+  const uint32_t nsb = (chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
+  const unsigned long long units = n_chunks * nsb;
+  SZ3G_LAUNCH(kKZeroCount, s,
+              zero_count_kernel<<<(unsigned)((units + 127) / 128), 128, 0, s>>>(codes, n, chunk, nsb, n_chunks, zcnt));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
-int launch_scan_u32(const uint32_t* in, unsigned long long n, unsigned long long* out, unsigned long long* total,
-                    unsigned long long expect, int check_expect, DevState* st, cudaStream_t s) {
-  SZ3G_LAUNCH(kKScan, s, scan_u32_kernel<<<1, kCbThreads, 0, s>>>(in, n, out, total, 0, expect, check_expect, st));
-  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
-}
 
 // table[sym] = len << 24 | code from separate arrays (stage API).
 __global__ void pack_table_kernel(const uint8_t* len, const uint32_t* code, uint32_t nsym, uint32_t* table) {

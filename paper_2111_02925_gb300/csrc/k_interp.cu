@@ -155,17 +155,15 @@ __device__ __forceinline__ void warp_hist_add(uint32_t* hist, uint32_t code) {
 }
 
 // Rank of the unpredictable value at code index i: zeros before it.
-// zbase[c]: zeros in chunks < c; zsub[c*nsub + b]: zeros in chunk c before
-// its 256-code block b.
+// zunit[c*nsub + b]: zeros before 512-code sub-block b of chunk c.
 __device__ __forceinline__ unsigned long long unpred_rank(const uint16_t* codes, unsigned long long i,
                                                           uint32_t chunk, uint32_t nsub,
-                                                          const unsigned long long* zbase,
-                                                          const uint32_t* zsub) {
+                                                          const unsigned long long* zunit) {
   const unsigned long long c = i / chunk;
   const unsigned long long r = i - c * chunk;
-  const unsigned long long b = r >> 8;
-  unsigned long long rank = zbase[c] + zsub[c * nsub + b];
-  for (unsigned long long k = c * chunk + (b << 8); k < i; ++k) rank += codes[k] == 0;
+  const unsigned long long b = r >> 9;
+  unsigned long long rank = zunit[c * nsub + b];
+  for (unsigned long long k = c * chunk + (b << 9); k < i; ++k) rank += codes[k] == 0;
   return rank;
 }
 
@@ -302,7 +300,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) pass_recover_kernel(const PassDesc pd, const uint16_t* __restrict__ codes,
                                                            const T* __restrict__ unpred,
                                                            unsigned long long n_unpred,
-                                                           const unsigned long long* zbase, const uint32_t* zsub,
+                                                           const unsigned long long* zunit,
                                                            uint32_t chunk, uint32_t nsub, T* R, DevState* st,
                                                            int radius, T ebT) {
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -311,7 +309,7 @@ __global__ void __launch_bounds__(256) pass_recover_kernel(const PassDesc pd, co
     const uint32_t c = codes[pd.off + j];
     T v;
     if (c == 0) {
-      const unsigned long long rk = unpred_rank(codes, pd.off + j, chunk, nsub, zbase, zsub);
+      const unsigned long long rk = unpred_rank(codes, pd.off + j, chunk, nsub, zunit);
       if (rk < n_unpred) {
         v = unpred[rk];
       } else {
@@ -372,7 +370,7 @@ int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, vo
 
 template <typename T>
 static int recover_levels_t(const Plan& pl, const uint16_t* codes, const T* unpred, unsigned long long n_unpred,
-                            const unsigned long long* zbase, const uint32_t* zsub, void* const* R, T* out,
+                            const unsigned long long* zunit, void* const* R, T* out,
                             DevState* st, T ebT, cudaStream_t s) {
   T* top = pl.L == 0 ? out : (T*)R[pl.L];
   SZ3G_LAUNCH(kKAnchor, s, anchor_recover_kernel<T><<<1, 32, 0, s>>>(codes, unpred, n_unpred, top, st, (int)pl.radius, ebT));
@@ -383,7 +381,7 @@ static int recover_levels_t(const Plan& pl, const uint16_t* codes, const T* unpr
     lift<T>(pl, k, (const T*)R[k + 1], Rf, s);
     for (; pi < pl.n_pass && pl.pass[pi].grid == k; ++pi) {
       const PassDesc& pd = pl.pass[pi];
-      SZ3G_LAUNCH(kKPassRecover, s, pass_recover_kernel<T><<<grid_for(pd.count, 256), 256, 0, s>>>(pd, codes, unpred, n_unpred, zbase, zsub,
+      SZ3G_LAUNCH(kKPassRecover, s, pass_recover_kernel<T><<<grid_for(pd.count, 256), 256, 0, s>>>(pd, codes, unpred, n_unpred, zunit,
                                                                      pl.chunk, pl.nsub, Rf, st, (int)pl.radius,
                                                                      ebT));
     }
@@ -392,19 +390,19 @@ static int recover_levels_t(const Plan& pl, const uint16_t* codes, const T* unpr
 }
 
 int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
-                          const unsigned long long* zbase, const uint32_t* zsub, void* const* R, void* d_out,
+                          const unsigned long long* zunit, void* const* R, void* d_out,
                           DevState* st, unsigned long long ebT_bits, cudaStream_t s) {
-  if (level_path_ok(pl)) return launch_recover_fused(pl, codes, unpred, n_unpred, zbase, zsub, R, d_out, st, ebT_bits, s);
+  if (level_path_ok(pl)) return launch_recover_fused(pl, codes, unpred, n_unpred, zunit, R, d_out, st, ebT_bits, s);
   if (pl.dtype == SZ3G_F32) {
     float e;
     uint32_t b = (uint32_t)ebT_bits;
     memcpy(&e, &b, 4);
-    return recover_levels_t<float>(pl, codes, (const float*)unpred, n_unpred, zbase, zsub, R, (float*)d_out, st, e,
+    return recover_levels_t<float>(pl, codes, (const float*)unpred, n_unpred, zunit, R, (float*)d_out, st, e,
                                    s);
   }
   double e;
   memcpy(&e, &ebT_bits, 8);
-  return recover_levels_t<double>(pl, codes, (const double*)unpred, n_unpred, zbase, zsub, R, (double*)d_out, st, e,
+  return recover_levels_t<double>(pl, codes, (const double*)unpred, n_unpred, zunit, R, (double*)d_out, st, e,
                                   s);
 }
 

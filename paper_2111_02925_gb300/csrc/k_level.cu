@@ -65,8 +65,7 @@ struct LevelArgs {
   DevState* st;
   const T* unpred;     // decompress
   unsigned long long n_unpred;
-  const unsigned long long* zbase;
-  const uint32_t* zsub;
+  const unsigned long long* zunit;  // zeros before each 512-code sub-block
   int radius;
   T ebT;               // decompress (compress reads the device state)
 };
@@ -118,13 +117,12 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 constexpr int kWaitLimit = 1 << 22;  // bounded wait on a tensor copy
 
 __device__ __forceinline__ unsigned long long rank_of_zero(const uint16_t* codes, unsigned long long i, uint32_t chunk,
-                                                           uint32_t nsub, const unsigned long long* zbase,
-                                                           const uint32_t* zsub) {
+                                                           uint32_t nsub, const unsigned long long* zunit) {
   const unsigned long long c = i / chunk;
   const unsigned long long r = i - c * chunk;
-  const unsigned long long b = r >> 8;
-  unsigned long long rank = zbase[c] + zsub[c * nsub + b];
-  for (unsigned long long q = c * chunk + (b << 8); q < i; ++q) rank += codes[q] == 0;
+  const unsigned long long b = r >> 9;
+  unsigned long long rank = zunit[c * nsub + b];
+  for (unsigned long long q = c * chunk + (b << 9); q < i; ++q) rank += codes[q] == 0;
   return rank;
 }
 
@@ -368,7 +366,7 @@ __global__ void __launch_bounds__(kLevelThreads) level_kernel(const LevelDesc d,
               const uint32_t code = a.codes[ci[u]];
               T rr;
               if (code == 0) {
-                const unsigned long long rk = rank_of_zero(a.codes, ci[u], d.chunk, d.nsub, a.zbase, a.zsub);
+                const unsigned long long rk = rank_of_zero(a.codes, ci[u], d.chunk, d.nsub, a.zunit);
                 if (rk < a.n_unpred) {
                   rr = a.unpred[rk];
                 } else {
@@ -530,7 +528,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
       } else {
         const uint32_t code = a.codes[ci];
         if (code == 0) {
-          const unsigned long long rk = rank_of_zero(a.codes, ci, d.chunk, d.nsub, a.zbase, a.zsub);
+          const unsigned long long rk = rank_of_zero(a.codes, ci, d.chunk, d.nsub, a.zunit);
           if (rk < a.n_unpred) {
             r = a.unpred[rk];
           } else {
@@ -808,7 +806,7 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
 
 template <typename T>
 static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred, unsigned long long n_unpred,
-                         const unsigned long long* zbase, const uint32_t* zsub, void* const* R, T* out, DevState* st,
+                         const unsigned long long* zunit, void* const* R, T* out, DevState* st,
                          T ebT, cudaStream_t s) {
   const int kc = coarse_grid(pl);
   LevelArgs<T> a{};
@@ -817,8 +815,7 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
   a.radius = (int)pl.radius;
   a.unpred = unpred;
   a.n_unpred = n_unpred;
-  a.zbase = zbase;
-  a.zsub = zsub;
+  a.zunit = zunit;
   a.ebT = ebT;
   a.Rout = kc == 0 ? out : (T*)R[kc];
   int rc = run_coarse<T, false>(pl, kc, a, s);
@@ -839,17 +836,17 @@ int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, voi
 }
 
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
-                         const unsigned long long* zbase, const uint32_t* zsub, void* const* R, void* d_out,
+                         const unsigned long long* zunit, void* const* R, void* d_out,
                          DevState* st, unsigned long long ebT_bits, cudaStream_t s) {
   if (pl.dtype == SZ3G_F32) {
     float e;
     uint32_t b = (uint32_t)ebT_bits;
     memcpy(&e, &b, 4);
-    return recover_fused<float>(pl, codes, (const float*)unpred, n_unpred, zbase, zsub, R, (float*)d_out, st, e, s);
+    return recover_fused<float>(pl, codes, (const float*)unpred, n_unpred, zunit, R, (float*)d_out, st, e, s);
   }
   double e;
   memcpy(&e, &ebT_bits, 8);
-  return recover_fused<double>(pl, codes, (const double*)unpred, n_unpred, zbase, zsub, R, (double*)d_out, st, e, s);
+  return recover_fused<double>(pl, codes, (const double*)unpred, n_unpred, zunit, R, (double*)d_out, st, e, s);
 }
 
 }  // namespace sz3g

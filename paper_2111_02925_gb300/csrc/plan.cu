@@ -124,7 +124,7 @@ int make_plan(const sz3g_params* p, Plan* pl) {
   if (pos != N) return SZ3G_E_INVAL;  // cannot happen for a valid shape
   pl->n_pass = np;
   pl->n_chunks = (N + pl->chunk - 1) / pl->chunk;
-  pl->nsub = (pl->chunk + 255) / 256;
+  pl->nsub = (pl->chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
   return SZ3G_OK;
 }
 

@@ -77,8 +77,8 @@ _SIGS = {
     "sz3g_predict_quantize": [_P, _vp, _vp, _vp, _vp, C.POINTER(_u64), _vp, _vp, _sz, _vp],
     "sz3g_recover": [_P, _vp, _vp, _vp, _u64, _vp, _vp, _sz, _vp],
     "sz3g_huffman_build": [_vp, _u32, _vp, _vp, _vp],
-    "sz3g_huffman_encode": [_vp, _u64, _vp, _vp, _u32, _u32, _vp, _u64, _vp, C.POINTER(_u64), _vp],
-    "sz3g_huffman_decode": [_vp, _u64, _vp, _u32, _vp, _u32, _vp, _u64, _vp],
+    "sz3g_huffman_encode": [_vp, _u64, _vp, _vp, _u32, _u32, _vp, _u64, _vp, _vp, C.POINTER(_u64), _vp],
+    "sz3g_huffman_decode": [_vp, _u64, _vp, _vp, _u32, _vp, _u32, _vp, _u64, _vp],
 }
 
 
@@ -209,17 +209,17 @@ def sz3g_huffman_build(d_hist: int, nsym: int, d_len: int, d_code: int, stream: 
 
 
 def sz3g_huffman_encode(d_codes: int, n: int, d_len: int, d_code: int, nsym: int, chunk: int, d_words: int,
-                        cap_words: int, d_chunk_words: int, stream: int = 0):
+                        cap_words: int, d_chunk_words: int, d_sub_bits: int = 0, stream: int = 0):
     nw = _u64()
     rc = load().sz3g_huffman_encode(d_codes, n, d_len, d_code, nsym, chunk, d_words, cap_words, d_chunk_words,
-                                    C.byref(nw), stream or None)
+                                    d_sub_bits or None, C.byref(nw), stream or None)
     return rc, nw.value
 
 
-def sz3g_huffman_decode(d_words: int, n_words: int, d_chunk_words: int, chunk: int, d_len: int, nsym: int,
-                        d_codes: int, n: int, stream: int = 0) -> int:
-    return load().sz3g_huffman_decode(d_words, n_words, d_chunk_words, chunk, d_len, nsym, d_codes, n,
-                                      stream or None)
+def sz3g_huffman_decode(d_words: int, n_words: int, d_chunk_words: int, d_sub_bits: int, chunk: int, d_len: int,
+                        nsym: int, d_codes: int, n: int, stream: int = 0) -> int:
+    return load().sz3g_huffman_decode(d_words, n_words, d_chunk_words, d_sub_bits or None, chunk, d_len, nsym,
+                                      d_codes, n, stream or None)
 
 
 def sz3g_launch_count() -> int:

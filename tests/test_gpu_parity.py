@@ -150,23 +150,34 @@ def test_huffman_build_encode_decode(seed, nsym, spread):
     assert G.sz3g_huffman_build(hd.data_ptr(), nsym, glen.data_ptr(), gcode.data_ptr(), G._stream_handle()) == G.OK
     assert np.array_equal(glen.cpu().numpy(), ln)
     assert np.array_equal(gcode.cpu().numpy().view(np.uint32), cc)
-    for chunk in (8, 1000 * 8, 4096):
-        words, cw = O.huffman_encode(codes, ln, cc, chunk)
+    for chunk in (8, 1000 * 8, 4096, 520):
+        words, cw, sub = O.huffman_encode(codes, ln, cc, chunk, with_sub=True)
         cd = dev(codes.view(np.int16))
         nch = (n + chunk - 1) // chunk
+        nsb = O.sub_blocks(chunk)
         cap = nch * ((chunk * 24 + 31) // 32)
         gw = torch.zeros(cap, dtype=torch.int32, device=DEV)
         gcw = torch.zeros(nch, dtype=torch.int32, device=DEV)
+        gsub = torch.zeros(max(nch * nsb, 1), dtype=torch.int16, device=DEV)
         rc, nw = G.sz3g_huffman_encode(cd.data_ptr(), n, glen.data_ptr(), gcode.data_ptr(), nsym, chunk, gw.data_ptr(),
-                                       cap, gcw.data_ptr(), G._stream_handle())
+                                       cap, gcw.data_ptr(), gsub.data_ptr(), G._stream_handle())
         assert rc == G.OK and nw == words.size
         assert np.array_equal(gcw.cpu().numpy().view(np.uint32), cw)
         assert np.array_equal(gw[:nw].cpu().numpy().view(np.uint32), words)
-        back = torch.empty(n, dtype=torch.int16, device=DEV)
-        rc = G.sz3g_huffman_decode(gw.data_ptr(), nw, gcw.data_ptr(), chunk, glen.data_ptr(), nsym, back.data_ptr(), n,
-                                   G._stream_handle())
-        assert rc == G.OK
-        assert np.array_equal(back.cpu().numpy().view(np.uint16), codes)
+        assert np.array_equal(gsub[:nch * nsb].cpu().numpy().view(np.uint16), sub)
+        for use_sub in (True, False):
+            back = torch.empty(n, dtype=torch.int16, device=DEV)
+            rc = G.sz3g_huffman_decode(gw.data_ptr(), nw, gcw.data_ptr(), gsub.data_ptr() if use_sub else 0, chunk,
+                                       glen.data_ptr(), nsym, back.data_ptr(), n, G._stream_handle())
+            assert rc == G.OK
+            assert np.array_equal(back.cpu().numpy().view(np.uint16), codes)
+        if nsb:  # a moved sub-block boundary is reported
+            bad = gsub.clone()
+            bad[0] += 1
+            back = torch.empty(n, dtype=torch.int16, device=DEV)
+            rc = G.sz3g_huffman_decode(gw.data_ptr(), nw, gcw.data_ptr(), bad.data_ptr(), chunk, glen.data_ptr(), nsym,
+                                       back.data_ptr(), n, G._stream_handle())
+            assert rc == G.E_CORRUPT
 
 
 def test_length_limit_matches_oracle():
@@ -230,7 +241,7 @@ def test_corrupt_streams_are_rejected():
     assert gpu_decompress(bytes(b), x.size, O.F32)[0] == G.E_CORRUPT
     rng = np.random.default_rng(1)
     nch = struct.unpack_from("<Q", s, 96)[0]
-    off_payload = off_chunks + ((nch * 4 + 7) & ~7)
+    off_payload = off_chunks + ((nch * 4 + 7) & ~7)  # chunk 256: no sub-block table
     for _ in range(20):  # random payload bit flips: decode or report, never crash
         b = bytearray(s)
         i = int(rng.integers(off_payload, len(s)))
