@@ -31,7 +31,6 @@ namespace sz3g {
 
 constexpr int kLevelThreads = 256;
 constexpr int kHistWin = 2048;  // shared-memory histogram window around the radius
-constexpr uint32_t kNone = 0xffffffffu;
 
 struct LevelDesc {
   int k, P, interp, write_out;
@@ -52,6 +51,7 @@ struct LevelDesc {
   int xb0_tile;         // input box spans only the tile along axis 0
   int cw[3];            // coarse box extents (compact), cw[2] a multiple of 16 bytes
   int calign;           // coarse box start alignment along axis 2 (elements)
+  int fast012;          // the specialised 4 x 16 x 56 interior tile applies
   uint32_t smem_c, smem_h, smem_bar;  // byte offsets of the coarse box, histogram, barrier
 };
 
@@ -130,14 +130,438 @@ __device__ __forceinline__ int floor_to(int v, int a) {  // a power of two
   return v & ~(a - 1);
 }
 
+constexpr int kUnroll = 4;  // rows a warp works on at once
+
+struct TileGeo {
+  int A0, A1, A2, E0, E1, E2, lo0, lo1, lo2;
+};
+
+// One pass of a level on the staged box V.  Warps take the rows of the pass
+// region (tile on the axes refined so far, tile + halo on later ones); lanes
+// run along axis 2.  INTERIOR: every neighbour at +-1 and +-3 exists, so the
+// prediction needs no boundary cases.
+template <typename T, bool COMP, int INTERP, bool INTERIOR>
+__device__ __forceinline__ void level_pass(const LevelDesc& d, const LevelArgs<T>& a, T* V, uint32_t* hwin,
+                                           const TileGeo& g, int p, T ebT, T ebr, int hlo, unsigned int& my_nz,
+                                           bool& my_bad) {
+  constexpr int kWarps = kLevelThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ve2 = d.vext[2], vs0 = d.vext[1] * d.vext[2];
+  const int pos0 = d.pos[0], pos1 = d.pos[1], pos2 = d.pos[2];
+  const int radius = a.radius;
+  const int ax = d.ax[p];
+  int s0[3], sp[3], cnt[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int pq = q == 0 ? pos0 : (q == 1 ? pos1 : pos2);
+    const int Aq = q == 0 ? g.A0 : (q == 1 ? g.A1 : g.A2);
+    const int Eq = q == 0 ? g.E0 : (q == 1 ? g.E1 : g.E2);
+    const bool ext = pq > p;  // axis refined by a later pass: halo of 2 below, 3 above
+    const int rlo = ext ? max(Aq - 2, 0) : Aq;
+    const int rhi = ext ? min(Aq + d.B[q] + 3, d.m[q]) : Eq;
+    int st0 = rlo, stp = 1;
+    if (q == ax) {
+      st0 = rlo | 1;
+      stp = 2;
+    } else if (ext || pq < 0) {
+      st0 = (rlo + 1) & ~1;
+      stp = 2;
+    }
+    s0[q] = st0;
+    sp[q] = stp;
+    cnt[q] = rhi > st0 ? (rhi - st0 + stp - 1) / stp : 0;
+  }
+  const int vst = ax == 2 ? 1 : (ax == 1 ? ve2 : vs0);
+  const int n_ax = d.m[ax];
+  // lattice coordinate per axis: c >> 1 on the pass axis and on later /
+  // unit axes, c on axes refined earlier in this level
+  const int sh0 = (pos0 >= 0 && pos0 < p) ? 0 : 1, sh1 = (pos1 >= 0 && pos1 < p) ? 0 : 1,
+            sh2 = (pos2 >= 0 && pos2 < p) ? 0 : 1;
+  const uint32_t PE1 = d.E[p][1], PE2 = d.E[p][2];
+  const uint32_t poff = d.off[p];
+  const int rows = cnt[0] * cnt[1];
+  const int c2first = s0[2], c2step = sp[2], n2 = cnt[2];
+  int j0 = cnt[1] ? warp / cnt[1] : 0, j1 = cnt[1] ? warp - j0 * cnt[1] : 0;
+  for (int r0 = warp; r0 < rows; r0 += kWarps * kUnroll) {
+    int vrow[kUnroll];
+    uint32_t crow[kUnroll];
+    bool orow[kUnroll], rok[kUnroll];
+    int irow[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {  // rows r0 + u * kWarps
+      const int c0 = s0[0] + sp[0] * j0, c1 = s0[1] + sp[1] * j1;
+      rok[u] = r0 + u * kWarps < rows;
+      vrow[u] = (c0 - g.lo0) * vs0 + (c1 - g.lo1) * ve2 - g.lo2;
+      crow[u] = poff + (((uint32_t)c0 >> sh0) * PE1 + ((uint32_t)c1 >> sh1)) * PE2;
+      orow[u] = c0 >= g.A0 && c0 < g.E0 && c1 >= g.A1 && c1 < g.E1;
+      irow[u] = ax == 0 ? c0 : c1;
+      j1 += kWarps;
+      while (j1 >= cnt[1] && cnt[1] > 0) {
+        j1 -= cnt[1];
+        ++j0;
+      }
+    }
+    for (int j2b = 0; j2b < n2; j2b += 32) {
+      const int j2 = j2b + lane;
+      const int c2 = c2first + c2step * j2;
+      const bool own2 = c2 >= g.A2 && c2 < g.E2;
+      T pred[kUnroll], xv[kUnroll];
+      // phase 1: loads and predictions
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        pred[u] = T(0);
+        xv[u] = T(0);
+        if (rok[u] && j2 < n2) {
+          const int v = vrow[u] + c2;
+          if (INTERIOR) {
+            const T va = V[v - vst], vb = V[v + vst], vc = V[v - 3 * vst], vd = V[v + 3 * vst];
+            pred[u] = interp_predict<T>(va, vb, vc, vd, true, true, true, INTERP);
+          } else {
+            const int i = ax == 2 ? c2 : irow[u];
+            const bool hb = i + 1 < n_ax, hc = i >= 3, hd = i + 3 < n_ax;
+            const T va = V[v - vst];
+            const T vb = hb ? V[v + vst] : T(0);
+            const T vc = hc ? V[v - 3 * vst] : T(0);
+            const T vd = hd ? V[v + 3 * vst] : T(0);
+            pred[u] = interp_predict<T>(va, vb, vc, vd, hb, hc, hd, INTERP);
+          }
+          if (COMP) xv[u] = V[v];
+        }
+      }
+      // phase 2: quantize / recover, stores
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (!(rok[u] && j2 < n2)) continue;
+        const int v = vrow[u] + c2;
+        const uint32_t ci = crow[u] + ((uint32_t)c2 >> sh2);
+        if (COMP) {
+          T rr;
+          const uint32_t code = quantize_point<T>(xv[u], pred[u], ebT, ebr, radius, rr);
+          V[v] = rr;
+          if (orow[u] && own2) {
+            a.codes[ci] = (uint16_t)code;
+            if (code == 0) {  // unpredictable: also where a non-finite input ends up
+              ++my_nz;
+              my_bad |= !isfinite(xv[u]);
+            }
+            const int b = (int)code - hlo;
+            if (b >= 0 && b < kHistWin) atomicAdd(&hwin[b], 1u);
+            else atomicAdd(&a.hist[code], 1u);
+          }
+        } else {
+          const uint32_t code = a.codes[ci];
+          T rr;
+          if (code == 0) {
+            const unsigned long long rk = rank_of_zero(a.codes, ci, d.chunk, d.nsub, a.zunit);
+            if (rk < a.n_unpred) {
+              rr = a.unpred[rk];
+            } else {
+              rr = T(0);
+              my_bad = true;
+            }
+          } else if (code >= 2u * (uint32_t)radius) {
+            rr = T(0);
+            my_bad = true;
+          } else {
+            rr = recover_point<T>(pred[u], code, radius, ebT);
+          }
+          V[v] = rr;
+        }
+      }
+    }
+  }
+}
+
+// Region of one pass inside the box for a tile away from every grid face, in
+// box coordinates (the same for all such tiles): first, step and count per
+// axis; the shift that maps a coordinate to its lattice coordinate; the
+// ownership window; the box stride along the pass axis.
+struct PassRegion {
+  int f[3], s[3], n[3];
+  int sh[3];
+  int olo[3], ohi[3];  // owned box coordinates [olo, ohi)
+  int vst;
+  uint32_t E1, E2, off;
+};
+
+__device__ void make_regions(const LevelDesc& d, PassRegion* R) {
+  for (int p = 0; p < d.P; ++p) {
+    PassRegion& g = R[p];
+    const int ax = d.ax[p];
+    for (int q = 0; q < 3; ++q) {
+      const int pq = d.pos[q];
+      const bool ext = pq > p;
+      const int rlo = ext ? -2 : 0, rhi = ext ? d.B[q] + 3 : d.B[q];  // relative to the tile start (even)
+      int st0 = rlo, stp = 1;
+      if (q == ax) {
+        st0 = rlo | 1;
+        stp = 2;
+      } else if (ext || pq < 0) {
+        st0 = (rlo + 1) & ~1;
+        stp = 2;
+      }
+      g.f[q] = st0 + d.vlo[q];
+      g.s[q] = stp;
+      g.n[q] = rhi > st0 ? (rhi - st0 + stp - 1) / stp : 0;
+      g.sh[q] = (pq >= 0 && pq < p) ? 0 : 1;
+      g.olo[q] = d.vlo[q];
+      g.ohi[q] = d.vlo[q] + d.B[q];
+    }
+    g.vst = ax == 2 ? 1 : (ax == 1 ? d.vext[2] : d.vext[1] * d.vext[2]);
+    g.E1 = d.E[p][1];
+    g.E2 = d.E[p][2];
+    g.off = d.off[p];
+  }
+}
+
+// One pass on a tile away from every grid face: every neighbour at +-1 and
+// +-3 exists.  Each warp takes a contiguous run of rows of the region, each
+// lane a fixed column; two rows are loaded before either is stored.
+template <typename T, bool COMP, int INTERP>
+__device__ __forceinline__ void level_pass_interior(const LevelDesc& d, const LevelArgs<T>& a, T* V, uint32_t* hwin,
+                                                    const PassRegion& g, int A0, int A1, int A2, T ebT, T ebr,
+                                                    int hlo, unsigned int& my_nz, bool& my_bad) {
+  constexpr int kWarps = kLevelThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ve2 = d.vext[2], vs0 = d.vext[1] * ve2;
+  const int radius = a.radius;
+  const int vst = g.vst;
+  const uint32_t tilebase =
+      g.off + (((uint32_t)A0 >> g.sh[0]) * g.E1 + ((uint32_t)A1 >> g.sh[1])) * g.E2 + ((uint32_t)A2 >> g.sh[2]);
+  const int rows = g.n[0] * g.n[1];
+  const int rb = (rows * warp) / kWarps, re = (rows * (warp + 1)) / kWarps;
+  if (rb >= re) return;
+  for (int seg = 0; seg < g.n[2]; seg += 32) {
+    const int j2 = seg + lane;
+    const bool col = j2 < g.n[2];
+    const int b2 = g.f[2] + g.s[2] * j2;
+    const int rel2 = b2 - d.vlo[2];
+    const uint32_t cl2 = (uint32_t)(rel2 >> g.sh[2]);
+    const bool own2 = b2 >= g.olo[2] && b2 < g.ohi[2];
+    int j0 = rb / g.n[1], j1 = rb - j0 * g.n[1];
+    for (int r = rb; r < re; r += 2) {
+      const bool two = r + 1 < re;
+      int v[2];
+      uint32_t ci[2];
+      bool own[2];
+      T pred[2], xv[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int b0 = g.f[0] + g.s[0] * j0, b1 = g.f[1] + g.s[1] * j1;
+        const int rel0 = b0 - d.vlo[0], rel1 = b1 - d.vlo[1];
+        v[u] = b0 * vs0 + b1 * ve2 + b2;
+        ci[u] = tilebase + ((uint32_t)(rel0 >> g.sh[0]) * g.E1 + (uint32_t)(rel1 >> g.sh[1])) * g.E2 + cl2;
+        own[u] = own2 && b0 >= g.olo[0] && b0 < g.ohi[0] && b1 >= g.olo[1] && b1 < g.ohi[1];
+        if (++j1 == g.n[1]) {
+          j1 = 0;
+          ++j0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        pred[u] = T(0);
+        xv[u] = T(0);
+        if (col && (u == 0 || two)) {
+          const T* w = V + v[u];
+          pred[u] = interp_predict<T>(w[-vst], w[vst], w[-3 * vst], w[3 * vst], true, true, true, INTERP);
+          if (COMP) xv[u] = w[0];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (!col || !(u == 0 || two)) continue;
+        if (COMP) {
+          T rr;
+          const uint32_t code = quantize_point<T>(xv[u], pred[u], ebT, ebr, radius, rr);
+          V[v[u]] = rr;
+          if (own[u]) {
+            a.codes[ci[u]] = (uint16_t)code;
+            if (code == 0) {  // unpredictable: also where a non-finite input ends up
+              ++my_nz;
+              my_bad |= !isfinite(xv[u]);
+            }
+            const int bn = (int)code - hlo;
+            if (bn >= 0 && bn < kHistWin) atomicAdd(&hwin[bn], 1u);
+            else atomicAdd(&a.hist[code], 1u);
+          }
+        } else {
+          const uint32_t code = a.codes[ci[u]];
+          T rr;
+          if (code == 0) {
+            const unsigned long long rk = rank_of_zero(a.codes, ci[u], d.chunk, d.nsub, a.zunit);
+            if (rk < a.n_unpred) {
+              rr = a.unpred[rk];
+            } else {
+              rr = T(0);
+              my_bad = true;
+            }
+          } else if (code >= 2u * (uint32_t)radius) {
+            rr = T(0);
+            my_bad = true;
+          } else {
+            rr = recover_point<T>(pred[u], code, radius, ebT);
+          }
+          V[v[u]] = rr;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Specialised interior tile for 3-D grids refined in axis order (0, 1, 2) with
+// 4 x 16 x 56 tiles: the box (9 x 21 x 64, low halos 2, 2, 4), the pass
+// regions, strides and lattice shifts are compile-time constants, so each
+// point costs its loads, the predictor, the quantizer and its stores.
+// ---------------------------------------------------------------------------
+constexpr int kT0 = 4, kT1 = 16, kT2 = 56;                 // tile
+constexpr int kX0 = kT0 + 5, kX1 = kT1 + 5, kX2 = kT2 + 8;  // box
+constexpr int kXS1 = kX2, kXS0 = kX1 * kX2;                 // box strides
+constexpr int kH0 = 2, kH1 = 2, kH2 = 4;                    // low halos
+
+template <typename T, bool COMP, int INTERP, int PASS, bool EDGE2>
+__device__ __forceinline__ void pass012(const LevelDesc& d, const LevelArgs<T>& a, T* V, uint32_t* hwin, int A0,
+                                        int A1, int A2, int E2, T ebT, T ebr, int hlo, unsigned int& my_nz,
+                                        bool& my_bad) {
+  // region of the pass in box coordinates: first, step, count per axis
+  constexpr int F0 = PASS == 0 ? kH0 + 1 : kH0, S0 = PASS == 0 ? 2 : 1, N0 = PASS == 0 ? kT0 / 2 : kT0;
+  constexpr int F1 = PASS == 0 ? 0 : (PASS == 1 ? kH1 + 1 : kH1), S1 = PASS == 2 ? 1 : 2;
+  constexpr int N1 = PASS == 0 ? (kT1 + 6) / 2 : (PASS == 1 ? kT1 / 2 : kT1);
+  constexpr int F2 = PASS == 2 ? kH2 + 1 : kH2 - 2, S2 = 2, N2 = PASS == 2 ? kT2 / 2 : (kT2 + 6) / 2;
+  constexpr int VST = PASS == 0 ? kXS0 : (PASS == 1 ? kXS1 : 1);
+  constexpr int SH0 = PASS == 0 ? 1 : 0, SH1 = PASS == 2 ? 0 : 1;  // lattice shifts (axis 2: 1)
+  constexpr int ROWS = N0 * N1;
+  constexpr int kWarps = kLevelThreads / 32;
+  constexpr int KMAX = (ROWS + kWarps - 1) / kWarps;
+  static_assert(N2 <= 32, "one lane per column");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int radius = a.radius;
+  const uint32_t E1 = d.E[PASS][1], E2L = d.E[PASS][2];
+  const uint32_t tilebase =
+      d.off[PASS] + (((uint32_t)A0 >> SH0) * E1 + ((uint32_t)A1 >> SH1)) * E2L + ((uint32_t)A2 >> 1);
+  const int b2 = F2 + S2 * lane;
+  const int c2 = A2 - kH2 + b2;  // grid coordinate of the column
+  const uint32_t cl2 = (uint32_t)((b2 - kH2) >> 1);
+  const bool own2 = b2 >= kH2 && c2 < E2;
+  // EDGE2: the tile touches a face along axis 2: columns past the grid drop
+  // out, and the axis-2 pass needs its boundary cases
+  const int m2 = d.m[2];
+  bool col = lane < N2;
+  if (EDGE2) col = col && c2 >= 0 && (PASS == 2 ? c2 < E2 : c2 < m2);
+  const bool hb = !EDGE2 || PASS != 2 || c2 + 1 < m2, hc = !EDGE2 || PASS != 2 || c2 >= 3,
+             hd = !EDGE2 || PASS != 2 || c2 + 3 < m2;
+  if (!col) return;
+#pragma unroll
+  for (int k = 0; k < KMAX; k += 2) {
+    int v[2];
+    uint32_t ci[2];
+    bool own[2], ok[2];
+    T pred[2], xv[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int r = warp + kWarps * (k + u);
+      ok[u] = k + u < KMAX && r < ROWS;
+      const int j0 = r / N1, j1 = r - (r / N1) * N1;
+      const int b0 = F0 + S0 * j0, b1 = F1 + S1 * j1;
+      v[u] = b0 * kXS0 + b1 * kXS1 + b2;
+      ci[u] = tilebase + ((uint32_t)((b0 - kH0) >> SH0) * E1 + (uint32_t)((b1 - kH1) >> SH1)) * E2L + cl2;
+      own[u] = own2 && b0 >= kH0 && b0 < kH0 + kT0 && b1 >= kH1 && b1 < kH1 + kT1;
+      pred[u] = T(0);
+      xv[u] = T(0);
+      if (ok[u]) {
+        const T* w = V + v[u];
+        if (EDGE2 && PASS == 2) {
+          const T vb = hb ? w[VST] : T(0), vc = hc ? w[-3 * VST] : T(0), vd = hd ? w[3 * VST] : T(0);
+          pred[u] = interp_predict<T>(w[-VST], vb, vc, vd, hb, hc, hd, INTERP);
+        } else {
+          pred[u] = interp_predict<T>(w[-VST], w[VST], w[-3 * VST], w[3 * VST], true, true, true, INTERP);
+        }
+        if (COMP) xv[u] = w[0];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!ok[u]) continue;
+      if (COMP) {
+        T rr;
+        const uint32_t code = quantize_point<T>(xv[u], pred[u], ebT, ebr, radius, rr);
+        V[v[u]] = rr;
+        if (own[u]) {
+          a.codes[ci[u]] = (uint16_t)code;
+          if (code == 0) {
+            ++my_nz;
+            my_bad |= !isfinite(xv[u]);
+          }
+          const int bn = (int)code - hlo;
+          if (bn >= 0 && bn < kHistWin) atomicAdd(&hwin[bn], 1u);
+          else atomicAdd(&a.hist[code], 1u);
+        }
+      } else {
+        const uint32_t code = a.codes[ci[u]];
+        T rr;
+        if (code == 0) {
+          const unsigned long long rk = rank_of_zero(a.codes, ci[u], d.chunk, d.nsub, a.zunit);
+          if (rk < a.n_unpred) {
+            rr = a.unpred[rk];
+          } else {
+            rr = T(0);
+            my_bad = true;
+          }
+        } else if (code >= 2u * (uint32_t)radius) {
+          rr = T(0);
+          my_bad = true;
+        } else {
+          rr = recover_point<T>(pred[u], code, radius, ebT);
+        }
+        V[v[u]] = rr;
+      }
+    }
+  }
+}
+
+// Coarse values of a specialised interior tile from the coarse box C to the
+// all-even positions of V (every one lies inside the grid).
+template <typename T>
+__device__ __forceinline__ void scatter012(const LevelDesc& d, T* V, const T* C, int coff2) {
+  constexpr int NI0 = (kX0 + 1) / 2, NI1 = (kX1 + 1) / 2, NI2 = kX2 / 2;  // 5, 11, 32
+  constexpr int TOT = NI0 * NI1 * NI2;
+  const int cw2 = d.cw[2], cst0 = d.cw[1] * d.cw[2];
+#pragma unroll
+  for (int k = 0; k < (TOT + kLevelThreads - 1) / kLevelThreads; ++k) {
+    const int e = threadIdx.x + kLevelThreads * k;
+    if (e < TOT) {
+      const int i2 = e % NI2, i1 = (e / NI2) % NI1, i0 = e / (NI2 * NI1);
+      V[2 * i0 * kXS0 + 2 * i1 * kXS1 + 2 * i2] = C[i0 * cst0 + i1 * cw2 + i2 + coff2];
+    }
+  }
+}
+
+// The owned 4 x 16 x (E2 - A2) tile of V to the output grid.
+template <typename T>
+__device__ __forceinline__ void write012(const LevelDesc& d, const LevelArgs<T>& a, const T* V, int A0, int A1,
+                                         int A2, int E2) {
+  constexpr int kWarps = kLevelThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w2 = E2 - A2;
+#pragma unroll
+  for (int k = 0; k < kT0 * kT1 / kWarps; ++k) {
+    const int r = warp + kWarps * k;
+    const int q0 = r / kT1, q1 = r % kT1;
+    T* dst = a.Rout + ((uint32_t)(A0 + q0) * d.rs[0] + (uint32_t)(A1 + q1) * d.rs[1] + (uint32_t)A2);
+    const T* src = V + (q0 + kH0) * kXS0 + (q1 + kH1) * kXS1 + kH2;
+#pragma unroll
+    for (int q2 = lane; q2 < kT2; q2 += 32)
+      if (q2 < w2) dst[q2] = src[q2];
+  }
+}
+
 // Work on a box region is distributed as (row, 32-wide segment) items over the
 // warps of the CTA: lanes run along axis 2, the contiguous axis.  A pass
 // handles kUnroll items per warp at a time: all their loads are issued before
 // any result is stored (the points a pass writes are never its own inputs).
-constexpr int kUnroll = 4;
 
 template <typename T, bool COMP, bool TMA, int INTERP>
-__global__ void __launch_bounds__(kLevelThreads) level_kernel(const LevelDesc d, const LevelArgs<T> a,
+__global__ void __launch_bounds__(kLevelThreads, 3) level_kernel(const LevelDesc d, const LevelArgs<T> a,
                                                               const __grid_constant__ CUtensorMap tmx,
                                                               const __grid_constant__ CUtensorMap tmc) {
   extern __shared__ __align__(128) unsigned char sm[];
@@ -177,6 +601,8 @@ __global__ void __launch_bounds__(kLevelThreads) level_kernel(const LevelDesc d,
   const int pos0 = d.pos[0], pos1 = d.pos[1], pos2 = d.pos[2];
   uint32_t phase = 0;
   (void)vsize;
+  __shared__ PassRegion s_reg[3];
+  if (tid == 0) make_regions(d, s_reg);
   __syncthreads();
 
   for (uint32_t tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
@@ -210,6 +636,11 @@ __global__ void __launch_bounds__(kLevelThreads) level_kernel(const LevelDesc d,
       phase ^= 1u;
       __syncthreads();
       if (s_timeout) break;
+      const bool fast = d.fast012 && (A0 >= 6 && A0 + kT0 + 6 <= m0) && (A1 >= 6 && A1 + kT1 + 6 <= m1);
+      if (fast) {
+        scatter012<T>(d, V, C, (lo2 >> 1) - cs2);
+        __syncthreads();
+      } else {
       // coarse values to the all-even positions of V
       const int i0a = (max(lo0, 0) + 1) >> 1, i0b = min(lo0 + d.vext[0] - 1, m0 - 1) >> 1;
       const int i1a = (max(lo1, 0) + 1) >> 1, i1b = min(lo1 + ve1 - 1, m1 - 1) >> 1;
@@ -230,6 +661,7 @@ __global__ void __launch_bounds__(kLevelThreads) level_kernel(const LevelDesc d,
         }
       }
       __syncthreads();
+      }
     } else {
       // ---- stage with element copies, only the points some pass reads
       const int nseg = (ve2 + 31) >> 5;
@@ -265,130 +697,44 @@ __global__ void __launch_bounds__(kLevelThreads) level_kernel(const LevelDesc d,
       __syncthreads();
     }
 
-    // ---- the passes of the level
-    for (int p = 0; p < d.P; ++p) {
-      const int ax = d.ax[p];
-      int s0[3], sp[3], cnt[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int pq = q == 0 ? pos0 : (q == 1 ? pos1 : pos2);
-        const int Aq = q == 0 ? A0 : (q == 1 ? A1 : A2);
-        const int Eq = q == 0 ? E0 : (q == 1 ? E1 : E2);
-        const bool ext = pq > p;  // axis refined by a later pass: halo of 2 below, 3 above
-        const int rlo = ext ? max(Aq - 2, 0) : Aq;
-        const int rhi = ext ? min(Aq + d.B[q] + 3, d.m[q]) : Eq;
-        int st0 = rlo, stp = 1;
-        if (q == ax) {
-          st0 = rlo | 1;
-          stp = 2;
-        } else if (ext || pq < 0) {
-          st0 = (rlo + 1) & ~1;
-          stp = 2;
-        }
-        s0[q] = st0;
-        sp[q] = stp;
-        cnt[q] = rhi > st0 ? (rhi - st0 + stp - 1) / stp : 0;
-      }
-      const int vst = ax == 2 ? 1 : (ax == 1 ? ve2 : vs0);
-      const int n_ax = d.m[ax];
-      // lattice coordinate per axis: c >> 1 on the pass axis and on later /
-      // unit axes, c on axes refined earlier in this level
-      const int sh0 = (pos0 >= 0 && pos0 < p) ? 0 : 1, sh1 = (pos1 >= 0 && pos1 < p) ? 0 : 1,
-                sh2 = (pos2 >= 0 && pos2 < p) ? 0 : 1;
-      const uint32_t PE1 = d.E[p][1], PE2 = d.E[p][2];
-      const uint32_t poff = d.off[p];
-      const int rows = cnt[0] * cnt[1];
-      const int c2first = s0[2], c2step = sp[2], n2 = cnt[2];
-      // row r of the region -> (j0, j1); warps take rows warp, warp + kWarps, ...
-      int j0 = cnt[1] ? warp / cnt[1] : 0, j1 = cnt[1] ? warp - j0 * cnt[1] : 0;
-      for (int r0 = warp; r0 < rows; r0 += kWarps * kUnroll) {
-        T pred[kUnroll], xv[kUnroll];
-        int vv[kUnroll];
-        uint32_t ci[kUnroll];
-        bool own[kUnroll], ok[kUnroll];
-        int rj0[kUnroll], rj1[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {  // rows r0 + u * kWarps
-          rj0[u] = j0;
-          rj1[u] = j1;
-          j1 += kWarps;
-          while (j1 >= cnt[1] && cnt[1] > 0) {
-            j1 -= cnt[1];
-            ++j0;
-          }
-        }
-        for (int j2b = 0; j2b < n2; j2b += 32) {
-          // phase 1: indices and loads
-#pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            ok[u] = false;
-            own[u] = false;
-            vv[u] = 0;
-            ci[u] = 0;
-            pred[u] = T(0);
-            xv[u] = T(0);
-            const int j2 = j2b + lane;
-            if (r0 + u * kWarps < rows && j2 < n2) {
-              const int c0 = s0[0] + sp[0] * rj0[u], c1 = s0[1] + sp[1] * rj1[u];
-              const int c2 = c2first + c2step * j2;
-              const int v = (c0 - lo0) * vs0 + (c1 - lo1) * ve2 + (c2 - lo2);
-              const int i = ax == 0 ? c0 : (ax == 1 ? c1 : c2);
-              const bool hb = i + 1 < n_ax, hc = i >= 3, hd = i + 3 < n_ax;
-              const T va = V[v - vst];
-              const T vb = hb ? V[v + vst] : T(0);
-              const T vc = hc ? V[v - 3 * vst] : T(0);
-              const T vd = hd ? V[v + 3 * vst] : T(0);
-              pred[u] = interp_predict<T>(va, vb, vc, vd, hb, hc, hd, INTERP);
-              if (COMP) xv[u] = V[v];
-              ci[u] = poff + (((uint32_t)c0 >> sh0) * PE1 + ((uint32_t)c1 >> sh1)) * PE2 + ((uint32_t)c2 >> sh2);
-              own[u] = c0 >= A0 && c0 < E0 && c1 >= A1 && c1 < E1 && c2 >= A2 && c2 < E2;
-              vv[u] = v;
-              ok[u] = true;
-            }
-          }
-          // phase 2: quantize / recover, stores
-#pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            if (!ok[u]) continue;
-            if (COMP) {
-              T rr;
-              const uint32_t code = quantize_point<T>(xv[u], pred[u], ebT, ebr, radius, rr);
-              V[vv[u]] = rr;
-              if (own[u]) {
-                a.codes[ci[u]] = (uint16_t)code;
-                my_nz += code == 0;
-                my_bad |= !isfinite(xv[u]);
-                const int b = (int)code - hlo;
-                if (b >= 0 && b < kHistWin) atomicAdd(&hwin[b], 1u);
-                else atomicAdd(&a.hist[code], 1u);
-              }
-            } else {
-              const uint32_t code = a.codes[ci[u]];
-              T rr;
-              if (code == 0) {
-                const unsigned long long rk = rank_of_zero(a.codes, ci[u], d.chunk, d.nsub, a.zunit);
-                if (rk < a.n_unpred) {
-                  rr = a.unpred[rk];
-                } else {
-                  rr = T(0);
-                  my_bad = true;
-                }
-              } else if (code >= 2u * (uint32_t)radius) {
-                rr = T(0);
-                my_bad = true;
-              } else {
-                rr = recover_point<T>(pred[u], code, radius, ebT);
-              }
-              V[vv[u]] = rr;
-            }
-          }
-        }
-      }
+    // ---- the passes of the level (tiles away from every grid face take the
+    //      branch-free interior form)
+    const bool interior = (pos0 < 0 || (A0 >= 6 && A0 + d.B[0] + 6 <= m0)) &&
+                          (pos1 < 0 || (A1 >= 6 && A1 + d.B[1] + 6 <= m1)) &&
+                          (pos2 < 0 || (A2 >= 6 && A2 + d.B[2] + 6 <= m2));
+    // the specialised tile: interior along axes 0 and 1; a face along axis 2
+    // only changes the columns and the axis-2 pass
+    const bool fast = d.fast012 && (A0 >= 6 && A0 + kT0 + 6 <= m0) && (A1 >= 6 && A1 + kT1 + 6 <= m1);
+    const bool edge2 = !(A2 >= 6 && A2 + kT2 + 6 <= m2);
+    if (fast && !edge2) {
+      pass012<T, COMP, INTERP, 0, false>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
       __syncthreads();
+      pass012<T, COMP, INTERP, 1, false>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
+      __syncthreads();
+      pass012<T, COMP, INTERP, 2, false>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
+      __syncthreads();
+    } else if (fast) {
+      pass012<T, COMP, INTERP, 0, true>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
+      __syncthreads();
+      pass012<T, COMP, INTERP, 1, true>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
+      __syncthreads();
+      pass012<T, COMP, INTERP, 2, true>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
+      __syncthreads();
+    } else {
+      for (int p = 0; p < d.P; ++p) {
+        const TileGeo g{A0, A1, A2, E0, E1, E2, lo0, lo1, lo2};
+        if (interior)
+          level_pass_interior<T, COMP, INTERP>(d, a, V, hwin, s_reg[p], A0, A1, A2, ebT, ebr, hlo, my_nz, my_bad);
+        else
+          level_pass<T, COMP, INTERP, false>(d, a, V, hwin, g, p, ebT, ebr, hlo, my_nz, my_bad);
+        __syncthreads();
+      }
     }
 
     // ---- write the tile of the output grid
-    if (d.write_out) {
+    if (d.write_out && fast) {
+      write012<T>(d, a, V, A0, A1, A2, E2);
+    } else if (d.write_out) {
       const int w1 = E1 - A1, w2 = E2 - A2;
       const int rows = (E0 - A0) * w1;
       int q0 = warp / w1, q1 = warp - (warp / w1) * w1;
@@ -677,8 +1023,8 @@ static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t 
     d.nt[q] = (d.m[q] + d.B[q] - 1) / d.B[q];
     d.ntiles *= (uint32_t)d.nt[q];
     const bool refined = d.pos[q] >= 0;
-    if (q == 2 && refined && tma) {
-      d.vlo[q] = 4;  // box start on a 16-byte boundary
+    if (q == 2 && refined) {
+      d.vlo[q] = 4;  // box start on a 16-byte boundary (tensor copies)
       d.vext[q] = d.B[q] + 8;
     } else {
       d.vlo[q] = refined ? 2 : 0;
@@ -698,6 +1044,9 @@ static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t 
   }
   d.chunk = pl.chunk;
   d.nsub = pl.nsub;
+  d.fast012 = d.P == 3 && d.pos[0] == 0 && d.pos[1] == 1 && d.pos[2] == 2 && d.B[0] == kT0 && d.B[1] == kT1 &&
+              d.B[2] == kT2 && d.vext[0] == kX0 && d.vext[1] == kX1 && d.vext[2] == kX2 && d.vlo[0] == kH0 &&
+              d.vlo[1] == kH1 && d.vlo[2] == kH2 && d.rs[2] == 1;
   const size_t vbytes = (size_t)d.vext[0] * d.vext[1] * d.vext[2] * esz;
   CUtensorMap tmx, tmc;
   memset(&tmx, 0, sizeof(tmx));
