@@ -216,6 +216,30 @@ int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_
                         const uint16_t* d_sub_bits, uint32_t chunk, const uint8_t* d_len,
                         uint32_t nsym, uint16_t* d_codes, uint64_t n, void* stream);
 
+/*
+ * sz3g_huffman_decode without any device allocation (the paper has no
+ * counterpart: this serves callers that must not allocate device memory,
+ * such as a process whose device memory is owned by another allocator's pool,
+ * or a latency-sensitive path where an allocation may block or fail).  Same
+ * arguments and results as sz3g_huffman_decode; its scratch is a fixed 4 MiB
+ * array built into the library (held on every GPU that loads the library
+ * until the process exits).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the array and each call resets the parts that must start
+ *    at zero; calls whose GPU work overlaps race on it, so do not run two at
+ *    once.
+ *  - SZ3G_E_CAPACITY when the stream needs more scratch than the array holds
+ *    (about 40 bytes per 4096-code chunk plus 0.7 MiB of decode tables,
+ *    i.e. n up to roughly 3.5e8 codes at 4096-code chunks); nothing is
+ *    launched then.
+ *  - Synchronises `stream` before returning.
+ */
+int sz3g_huffman_decode_static(const uint32_t* d_words, uint64_t n_words, const uint32_t* d_chunk_words,
+                               const uint16_t* d_sub_bits, uint32_t chunk, const uint8_t* d_len,
+                               uint32_t nsym, uint16_t* d_codes, uint64_t n, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Diagnostics (no counterpart in the paper): launch accounting and per-kernel
  * timing with CUDA events, used by the benchmark to attribute time to kernels.

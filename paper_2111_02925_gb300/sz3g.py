@@ -79,6 +79,7 @@ _SIGS = {
     "sz3g_huffman_build": [_vp, _u32, _vp, _vp, _vp],
     "sz3g_huffman_encode": [_vp, _u64, _vp, _vp, _u32, _u32, _vp, _u64, _vp, _vp, C.POINTER(_u64), _vp],
     "sz3g_huffman_decode": [_vp, _u64, _vp, _vp, _u32, _vp, _u32, _vp, _u64, _vp],
+    "sz3g_huffman_decode_static": [_vp, _u64, _vp, _vp, _u32, _vp, _u32, _vp, _u64, _vp],
 }
 
 
@@ -220,6 +221,13 @@ def sz3g_huffman_decode(d_words: int, n_words: int, d_chunk_words: int, d_sub_bi
                         nsym: int, d_codes: int, n: int, stream: int = 0) -> int:
     return load().sz3g_huffman_decode(d_words, n_words, d_chunk_words, d_sub_bits or None, chunk, d_len, nsym,
                                       d_codes, n, stream or None)
+
+
+def sz3g_huffman_decode_static(d_words: int, n_words: int, d_chunk_words: int, d_sub_bits: int, chunk: int,
+                               d_len: int, nsym: int, d_codes: int, n: int, stream: int = 0) -> int:
+    """sz3g_huffman_decode with its scratch in the library's fixed device array (allocates nothing)."""
+    return load().sz3g_huffman_decode_static(d_words, n_words, d_chunk_words, d_sub_bits or None, chunk, d_len, nsym,
+                                             d_codes, n, stream or None)
 
 
 def sz3g_launch_count() -> int:
