@@ -150,8 +150,9 @@ def algorithmic_bytes(kernel: str, info: dict) -> float:
 
 
 def traffic_for(kernel: str):
-    """ncu DRAM bytes per launch recorded in profiles/traffic.json for the
-    current kernel sources, else None."""
+    """ncu DRAM bytes (read + write) of one step's launches of `kernel`,
+    recorded in profiles/traffic.json for the current kernel sources, else
+    None (the kernels changed since the counters were taken)."""
     try:
         from paper_2111_02925_gb300 import build as B
 
@@ -159,7 +160,7 @@ def traffic_for(kernel: str):
             d = json.load(fh)
         e = d.get(kernel)
         if e and e.get("source_stamp") == B._stamp():
-            return e.get("bytes_per_launch")
+            return e.get("bytes_per_step")
     except Exception:
         pass
     return None

@@ -40,12 +40,15 @@ def _sources():
 
 
 def _stamp() -> str:
+    """Hash of the sources, the public header and the compile flags, keyed by
+    names relative to the package so that a copy of the tree elsewhere gives
+    the same stamp."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)) + [os.path.join(INCLUDE, "sz3g.h")]:
-        p = f if os.path.isabs(f) else os.path.join(CSRC, f)
+    files = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))] + [os.path.join(INCLUDE, "sz3g.h")]
+    for p in files:
         with open(p, "rb") as fh:
-            h.update(p.encode() + fh.read())
-    h.update(" ".join(NVCC_FLAGS).encode())
+            h.update(os.path.relpath(p, os.path.dirname(HERE)).encode() + fh.read())
+    h.update(" ".join(f for f in NVCC_FLAGS if not f.startswith("-I")).encode())
     return h.hexdigest()
 
 
