@@ -32,7 +32,7 @@ struct DevState {
   uint32_t flags;        // kFlag* bits
   uint32_t n_used;       // symbols with a code
   uint32_t ticket;       // dynamic chunk counter of the encoder
-  uint32_t pad0;
+  uint32_t range_ticket;  // blocks of the range kernel that have finished
   unsigned long long n_unpred;     // unpredictable values
   unsigned long long n_words;      // payload words
   unsigned long long out_bytes;    // stream length

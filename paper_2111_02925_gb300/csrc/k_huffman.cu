@@ -78,173 +78,261 @@ __device__ __forceinline__ int pow2_at_least(int k) {
 }
 
 // Two-queue Huffman merge over K leaves sorted by (weight, symbol); node ids:
-// leaves 0..K-1, internal K..2K-2 in creation order.  Single thread.  The
-// next weight of each queue is kept in a register, so a step waits on at most
-// one shared-memory load.
-__device__ void two_queue_merge(const unsigned long long* keys, int K, uint32_t* nf, uint32_t* parent) {
-  int li = 0, ni = 0, nn = 0;
-  uint32_t lf = (uint32_t)(keys[0] >> 16);  // weight of the next leaf
-  uint32_t lf_next = K > 1 ? (uint32_t)(keys[1] >> 16) : 0u;
-  uint32_t nfront = 0;                      // weight of the next internal node (valid if ni < nn)
-  while (nn < K - 1) {
-    uint32_t pick0, pick1, w0, w1;
-    if (li < K && (ni >= nn || lf <= nfront)) {
-      pick0 = (uint32_t)li;
-      w0 = lf;
-      ++li;
-      lf = lf_next;
-      lf_next = li + 1 < K ? (uint32_t)(keys[li + 1] >> 16) : 0u;
-    } else {
-      pick0 = (uint32_t)(K + ni);
-      w0 = nfront;
-      ++ni;
-      nfront = ni < nn ? nf[ni] : 0u;
+// leaves 0..K-1, internal K..2K-2 in creation order.  Each step takes the two
+// lightest fronts, the leaf first on equal weight, and appends their parent
+// to the internal queue.  Single thread, branch-free: lw = sorted leaf
+// weights followed by two kInf sentinels, nf = internal weights pre-filled
+// with kInf up to K + 2 (so loads past the created nodes read kInf).  Three
+// weights of each queue are held in registers; every load is used two picks
+// after it was issued.
+template <typename PT>
+__device__ __forceinline__ void two_queue_merge_fast(const uint32_t* lw, int K, uint32_t* nf, PT* parent) {
+  constexpr uint32_t kInf = 0xffffffffu;
+  uint32_t li = 0, ni = 0;
+  uint32_t L0 = lw[0], L1 = lw[1], L2 = lw[2];
+  uint32_t I0 = kInf, I1 = kInf, I2 = kInf;
+  for (uint32_t nn = 0; nn + 1 < (uint32_t)K; ++nn) {
+    uint32_t id[2], w[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const bool tl = L0 <= I0;  // the leaf first on equal weight
+      id[t] = tl ? li : (uint32_t)K + ni;
+      w[t] = tl ? L0 : I0;
+      const uint32_t nl = lw[min(li + 3, (uint32_t)K + 1)], ninl = nf[ni + 3];
+      li += tl;
+      ni += !tl;
+      L0 = tl ? L1 : L0;
+      L1 = tl ? L2 : L1;
+      L2 = tl ? nl : L2;
+      I0 = tl ? I0 : I1;
+      I1 = tl ? I1 : I2;
+      I2 = tl ? I2 : ninl;
     }
-    if (li < K && (ni >= nn || lf <= nfront)) {
-      pick1 = (uint32_t)li;
-      w1 = lf;
-      ++li;
-      lf = lf_next;
-      lf_next = li + 1 < K ? (uint32_t)(keys[li + 1] >> 16) : 0u;
-    } else {
-      pick1 = (uint32_t)(K + ni);
-      w1 = nfront;
-      ++ni;
-      nfront = ni < nn ? nf[ni] : 0u;
-    }
-    const uint32_t w = w0 + w1;
-    nf[nn] = w;
-    if (ni == nn) nfront = w;  // the queue was empty: the new node is its front
-    parent[pick0] = (uint32_t)(K + nn);
-    parent[pick1] = (uint32_t)(K + nn);
-    ++nn;
+    const uint32_t wn = w[0] + w[1];
+    nf[nn] = wn;
+    // a node created while the queue is short is one of its three fronts
+    I0 = nn == ni ? wn : I0;
+    I1 = nn == ni + 1 ? wn : I1;
+    I2 = nn == ni + 2 ? wn : I2;
+    parent[id[0]] = (PT)(K + nn);
+    parent[id[1]] = (PT)(K + nn);
   }
 }
 
-struct CbGlobal {  // global scratch of the codebook kernel
+// Rank sort of K distinct keys (K <= kRankSortMax): out[rank(k)] = k.
+constexpr int kRankSortMax = 2048;
+__device__ void block_rank_sort(const unsigned long long* in, unsigned long long* out, int K) {
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const unsigned long long k = in[i];
+    int r = 0, j = 0;
+    for (; j + 1 < K; j += 2) {
+      const ulonglong2 p = *reinterpret_cast<const ulonglong2*>(in + j);
+      r += (p.x < k) + (p.y < k);
+    }
+    if (j < K) r += in[j] < k;
+    out[r] = k;
+  }
+}
+
+struct CbGlobal {  // global scratch of the codebook kernel (more than kSmemLeaves used symbols)
   unsigned long long keys[kSyms];
-  uint32_t nf[kSyms];
+  unsigned long long keys2[kSyms];
+  uint32_t nf[kSyms + 16];
   uint32_t parent[2 * kSyms];
-  uint32_t sym[kSyms];   // used symbols in symbol order
-  uint32_t freq[kSyms];  // their current weights
-  uint32_t len[kSyms];   // length per sorted leaf
+  uint16_t symord[kSyms];
 };
 
 size_t codebook_scratch_bytes() { return sizeof(CbGlobal); }
 
-constexpr size_t kCbSmem = kSmemLeaves * 8 + kSmemLeaves * 4 + 2 * kSmemLeaves * 4;
+// shared memory: two key arrays, internal weights / lengths, 16-bit parents,
+// used symbols in symbol order
+constexpr size_t kCbOffNf = (size_t)kSmemLeaves * 16;
+constexpr size_t kCbOffPar = kCbOffNf + (size_t)(kSmemLeaves + 16) * 4;
+constexpr size_t kCbOffSym = kCbOffPar + (size_t)kSmemLeaves * 4;
+constexpr size_t kCbSmem = kCbOffSym + (size_t)kSmemLeaves * 2;
 
-// table[sym] = len << 24 | code (0 for unused symbols).
+// Depth of every leaf by walking its parents (stops past SZ3G_LMAX); returns,
+// block-wide, whether some code is longer than SZ3G_LMAX.
+template <typename PT>
+__device__ bool leaf_depths(const PT* parent, int K, uint32_t* len) {
+  const uint32_t root = (uint32_t)(2 * K - 2);
+  bool deep = false;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    uint32_t v = (uint32_t)i, d = 0;
+    while (v != root && d <= SZ3G_LMAX) {
+      v = parent[v];
+      ++d;
+    }
+    deep |= v != root || d > SZ3G_LMAX;
+    len[i] = d;
+  }
+  return __syncthreads_or(deep) != 0;
+}
+
+// Code lengths of K leaves whose keys (weight << 16 | symbol) are in `cur`,
+// halving the weights while some code is longer than SZ3G_LMAX.  `other` is
+// a second key array; on return `srt` holds the leaves sorted by the
+// (weight, symbol) of the last round and len[i] the length of leaf srt[i].
+template <typename PT>
+__device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* cur, unsigned long long* other,
+                                                            uint32_t* nf, PT* parent, int K) {
+  const bool rank = K <= kRankSortMax;
+  const int P = pow2_at_least(K);
+  const int tid = threadIdx.x;
+  unsigned long long* srt = cur;
+  if (K == 1) {
+    if (tid == 0) nf[0] = 1;
+    __syncthreads();
+    return srt;
+  }
+  for (int iter = 0; iter < 40; ++iter) {
+    if (rank) {
+      block_rank_sort(cur, other, K);  // out of place
+      srt = other;
+    } else {
+      srt = cur;  // in place, padded to a power of two
+      for (int i = K + tid; i < P; i += kCbThreads) srt[i] = ~0ull;
+      __syncthreads();
+      block_bitonic_sort(srt, P);
+    }
+    __syncthreads();
+    // leaf weights (in the free key array) and the empty internal queue
+    uint32_t* lw = reinterpret_cast<uint32_t*>(srt == cur ? other : cur);
+    for (int i = tid; i < K + 2; i += kCbThreads) lw[i] = i < K ? (uint32_t)(srt[i] >> 16) : 0xffffffffu;
+    for (int i = tid; i < K + 4; i += kCbThreads) nf[i] = 0xffffffffu;
+    __syncthreads();
+    if (tid == 0) two_queue_merge_fast(lw, K, nf, parent);
+    __syncthreads();
+    if (!leaf_depths(parent, K, nf)) break;
+    for (int i = tid; i < K; i += kCbThreads) {
+      const unsigned long long k = srt[i];
+      const uint32_t f = (uint32_t)(k >> 16) >> 1;
+      srt[i] = ((unsigned long long)(f ? f : 1u) << 16) | (k & 0xffffu);
+    }
+    __syncthreads();
+    // the halved keys are the input of the next sort; the other array is
+    // free again
+    if (rank) {
+      unsigned long long* t = cur;
+      cur = srt;
+      other = t;
+    }
+  }
+  return srt;
+}
+
+// table[sym] = len << 24 | code for every used symbol.  VEC: the histogram is
+// 16-byte aligned and read with vector loads.
+template <bool VEC>
 __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __restrict__ hist, uint32_t nsym,
                                                               uint32_t* table, uint8_t* len_out, uint32_t* code_out,
                                                               DevState* st, CbGlobal* g, unsigned char* d_out,
                                                               unsigned long long out_capacity, int esz) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_warp[32];
-  __shared__ uint32_t s_wcount[32];
   __shared__ uint32_t s_cnt[SZ3G_LMAX + 2], s_start[SZ3G_LMAX + 2], s_fc[SZ3G_LMAX + 2];
-  __shared__ int s_deep;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kPerWarp = kSyms / (kCbThreads / 32);  // 2048 symbols per warp, 64 rounds of 32
+  const int tid = threadIdx.x;
+  static_assert(kSyms == kCbThreads * 64, "64 symbols per thread");
 
-  // 1. used symbols in symbol order: each warp owns a contiguous run of
-  //    2048 symbols, read 32 at a time (coalesced), ranked with ballots
-  uint32_t wcount = 0;
-  for (int r = 0; r < kPerWarp; r += 32) {
-    const int sy = warp * kPerWarp + r + lane;
-    const uint32_t f = hist[sy];
-    if (sy >= (int)nsym && f) atomicOr(&st->flags, kFlagCorrupt);
-    wcount += __popc(__ballot_sync(0xffffffffu, f != 0 && sy < (int)nsym));
-  }
-  if (lane == 0) s_wcount[warp] = wcount;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t v = lane < kCbThreads / 32 ? s_wcount[lane] : 0u, x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+  // 1. used symbols in symbol order: thread t owns symbols [64 t, 64 t + 64),
+  //    read in two halves of 32 with every load of a half in flight at once
+  const int s0 = tid * 64;
+  auto load8 = [&](int h, uint4* v) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int sy = s0 + 32 * h + 4 * r;
+      if (VEC) {
+        v[r] = __ldcg(reinterpret_cast<const uint4*>(hist + sy));
+      } else {
+        v[r] = make_uint4(hist[sy], hist[sy + 1], hist[sy + 2], hist[sy + 3]);
+      }
     }
-    if (lane < kCbThreads / 32) s_wcount[lane] = x - v;  // exclusive
-    if (lane == 31) s_warp[0] = x;
+  };
+  auto comp = [](const uint4& v, int e) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); };
+  unsigned long long used = 0;
+  bool bad = false;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint4 v[8];
+    load8(h, v);
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int b = 32 * h + 4 * r + e;
+        if (comp(v[r], e)) {
+          if (s0 + b < (int)nsym) used |= 1ull << b;
+          else bad = true;
+        }
+      }
   }
-  __syncthreads();
-  const int K = (int)s_warp[0];
-  uint32_t pos = s_wcount[warp];
-  for (int r = 0; r < kPerWarp; r += 32) {
-    const int sy = warp * kPerWarp + r + lane;
-    const uint32_t f = hist[sy];
-    const bool used = f != 0 && sy < (int)nsym;
-    const unsigned m = __ballot_sync(0xffffffffu, used);
-    if (used) {
-      const uint32_t q = pos + __popc(m & ((1u << lane) - 1u));
-      g->sym[q] = (uint32_t)sy;
-      g->freq[q] = f;
-    }
-    pos += __popc(m);
-    table[sy] = 0u;
-    if (len_out && sy < (int)nsym) len_out[sy] = 0;
-    if (code_out && sy < (int)nsym) code_out[sy] = 0;
-  }
-  __syncthreads();
+  if (bad) atomicOr(&st->flags, kFlagCorrupt);
+  unsigned long long tot;
+  uint32_t pos = (uint32_t)block_exclusive_scan((unsigned long long)__popcll(used), s_warp, &tot);
+  const int K = (int)tot;
   if (K == 0) {
     if (tid == 0) atomicOr(&st->flags, kFlagCorrupt);
     return;
   }
   const bool in_smem = K <= kSmemLeaves;
-  unsigned long long* keys = in_smem ? (unsigned long long*)smem : g->keys;
-  uint32_t* nf = in_smem ? (uint32_t*)(smem + kSmemLeaves * 8) : g->nf;
-  uint32_t* parent = in_smem ? (uint32_t*)(smem + kSmemLeaves * 12) : g->parent;
-  const int P = pow2_at_least(K);
-
-  // 2. lengths, halving the weights while some code is longer than LMAX
-  if (K == 1) {
-    if (tid == 0) g->len[0] = 1, keys[0] = ((unsigned long long)g->freq[0] << 16) | g->sym[0];
-    __syncthreads();
-  } else {
-    for (int iter = 0; iter < 40; ++iter) {
-      for (int i = tid; i < P; i += kCbThreads)
-        keys[i] = i < K ? (((unsigned long long)g->freq[i] << 16) | g->sym[i]) : ~0ull;
-      __syncthreads();
-      block_bitonic_sort(keys, P);
-      if (tid == 0) {
-        two_queue_merge(keys, K, nf, parent);
-        s_deep = 0;
-      }
-      __syncthreads();
-      const uint32_t root = (uint32_t)(2 * K - 2);
-      for (int i = tid; i < K; i += kCbThreads) {
-        uint32_t v = (uint32_t)i, d = 0;
-        while (v != root && d <= SZ3G_LMAX) {
-          v = parent[v];
-          ++d;
+  unsigned long long* ka = in_smem ? (unsigned long long*)smem : g->keys;
+  unsigned long long* kb = in_smem ? (unsigned long long*)(smem + kSmemLeaves * 8) : g->keys2;
+  uint32_t* nf = in_smem ? (uint32_t*)(smem + kCbOffNf) : g->nf;
+  uint16_t* symord = in_smem ? (uint16_t*)(smem + kCbOffSym) : g->symord;
+  if (used) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint4 v[8];
+      load8(h, v);
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int b = 32 * h + 4 * r + e;
+          if ((used >> b) & 1ull) {
+            ka[pos] = ((unsigned long long)comp(v[r], e) << 16) | (uint32_t)(s0 + b);
+            symord[pos] = (uint16_t)(s0 + b);
+            ++pos;
+          }
         }
-        if (v != root || d > SZ3G_LMAX) s_deep = 1;
-        g->len[i] = d;
-      }
-      __syncthreads();
-      if (!s_deep) break;
-      for (int i = tid; i < K; i += kCbThreads) {
-        const uint32_t f = g->freq[i] >> 1;
-        g->freq[i] = f ? f : 1u;
-      }
-      __syncthreads();
     }
   }
-  // 3. canonical codewords: sort leaves by (length, symbol)
+  if (len_out || code_out)
+    for (int sy = tid; sy < (int)nsym; sy += kCbThreads) {
+      if (len_out) len_out[sy] = 0;
+      if (code_out) code_out[sy] = 0;
+    }
+  __syncthreads();
+
+  // 2. lengths (shared-memory arrays are addressed through pointers derived
+  //    from the shared array itself in their own branch)
+  const bool rank = K <= kRankSortMax;
+  const int P = pow2_at_least(K);
+  unsigned long long* srt;
+  if (in_smem) {
+    srt = code_lengths((unsigned long long*)smem, (unsigned long long*)(smem + kSmemLeaves * 8),
+                       (uint32_t*)(smem + kCbOffNf), (uint16_t*)(smem + kCbOffPar), K);
+  } else {
+    srt = code_lengths(g->keys, g->keys2, g->nf, g->parent, K);
+  }
+  // 3. canonical codewords: leaves ordered by (length, symbol)
   if (tid <= SZ3G_LMAX + 1) s_cnt[tid] = 0;
   __syncthreads();
-  for (int i = tid; i < P; i += kCbThreads) {
-    if (i < K) {
-      const uint32_t L = g->len[i];
-      const uint32_t s = (uint32_t)(keys[i] & 0xffffu);
-      atomicAdd(&s_cnt[L], 1u);
-      keys[i] = ((unsigned long long)L << 16) | s;
-    } else {
-      keys[i] = ~0ull;
-    }
+  unsigned long long* c_in = srt;
+  unsigned long long* c_out = rank ? (srt == ka ? kb : ka) : srt;
+  for (int i = tid; i < K; i += kCbThreads) {
+    const uint32_t L = nf[i];
+    atomicAdd(&s_cnt[L], 1u);
+    c_in[i] = ((unsigned long long)L << 16) | (c_in[i] & 0xffffu);
   }
   __syncthreads();
-  block_bitonic_sort(keys, P);
+  if (rank) {
+    block_rank_sort(c_in, c_out, K);
+  } else {
+    for (int i = K + tid; i < P; i += kCbThreads) c_out[i] = ~0ull;
+    __syncthreads();
+    block_bitonic_sort(c_out, P);
+  }
   if (tid == 0) {
     uint32_t start = 0, fc = 0;
     for (int L = 1; L <= SZ3G_LMAX; ++L) {
@@ -257,7 +345,7 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   }
   __syncthreads();
   for (int i = tid; i < K; i += kCbThreads) {
-    const uint32_t L = (uint32_t)(keys[i] >> 16), s = (uint32_t)(keys[i] & 0xffffu);
+    const uint32_t L = (uint32_t)(c_out[i] >> 16), s = (uint32_t)(c_out[i] & 0xffffu);
     const uint32_t code = s_fc[L] + ((uint32_t)i - s_start[L]);
     table[s] = (L << 24) | code;
     if (len_out) len_out[s] = (uint8_t)L;
@@ -273,7 +361,7 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
       return;
     }
     for (int i = tid; i < K; i += kCbThreads) {
-      const uint32_t s = g->sym[i];
+      const uint32_t s = symord[i];
       unsigned char* q = d_out + off + 3ull * i;
       q[0] = (unsigned char)(s & 0xff);
       q[1] = (unsigned char)(s >> 8);
@@ -286,11 +374,13 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
 int launch_codebook(const uint32_t* hist, uint32_t nsym, uint32_t* table, uint8_t* len_out, uint32_t* code_out,
                     DevState* st, void* scratch, unsigned char* d_out, unsigned long long out_capacity, int esz,
                     cudaStream_t s) {
-  if (cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) !=
-      cudaSuccess)
+  const bool vec = ((uintptr_t)hist % 16) == 0;
+  auto kern = vec ? codebook_kernel<true> : codebook_kernel<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) != cudaSuccess)
     return SZ3G_E_CUDA;
-  SZ3G_LAUNCH(kKCodebook, s, codebook_kernel<<<1, kCbThreads, kCbSmem, s>>>(hist, nsym, table, len_out, code_out, st, (CbGlobal*)scratch, d_out,
-                                                 out_capacity, esz));
+  SZ3G_LAUNCH(kKCodebook, s,
+              kern<<<1, kCbThreads, kCbSmem, s>>>(hist, nsym, table, len_out, code_out, st, (CbGlobal*)scratch, d_out,
+                                                  out_capacity, esz));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
@@ -522,18 +612,38 @@ __global__ void __launch_bounds__(kEncWarps * 32) emit_kernel(const EncArgs a, c
       }
       if (emit) {
         uint32_t o = carry + incl - nb;
+        if (nb <= 64) {
+          // the lane's codes concatenated in one register, then OR-ed into
+          // the (at most three) ring words they cover
+          unsigned long long acc = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint32_t L = e8[q] >> 24, val = e8[q] & 0xffffffu;
-          if (L == 0) continue;
-          const uint32_t wi = o >> 5, sh = o & 31;
-          if (sh + L <= 32) {
-            atomicOr(&buf[wi], val << (32 - sh - L));
-          } else {
-            atomicOr(&buf[wi], val >> (sh + L - 32));
-            atomicOr(&buf[wi + 1], val << (64 - sh - L));
+          for (int q = 0; q < 8; ++q) {
+            const uint32_t L = e8[q] >> 24;
+            acc = L ? (acc << L) | (e8[q] & 0xffffffu) : acc;
           }
-          o += L;
+          if (nb) {
+            const unsigned long long x = acc << (64 - nb);  // left-aligned
+            const uint32_t wi = o >> 5, sh = o & 31;
+            const uint32_t v0 = (uint32_t)(x >> (32 + sh)), v1 = (uint32_t)(x >> sh),
+                           v2 = (uint32_t)(x << (32 - sh));
+            if (v0) atomicOr(&buf[wi], v0);
+            if (v1) atomicOr(&buf[wi + 1], v1);
+            if (v2) atomicOr(&buf[wi + 2], v2);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const uint32_t L = e8[q] >> 24, val = e8[q] & 0xffffffu;
+            if (L == 0) continue;
+            const uint32_t wi = o >> 5, sh = o & 31;
+            if (sh + L <= 32) {
+              atomicOr(&buf[wi], val << (32 - sh - L));
+            } else {
+              atomicOr(&buf[wi], val >> (sh + L - 32));
+              atomicOr(&buf[wi + 1], val << (64 - sh - L));
+            }
+            o += L;
+          }
         }
         __syncwarp();
         const uint32_t total = carry + round_bits;
@@ -931,7 +1041,7 @@ struct DecArgs {
 // leaving L1 for the per-thread payload streams.
 constexpr int kDecThreads = 512;
 
-__global__ void __launch_bounds__(kDecThreads) decode_kernel(const DecArgs a) {
+__global__ void __launch_bounds__(kDecThreads, 3) decode_kernel(const DecArgs a) {
   if (a.st->flags & kFlagCorrupt) return;  // tables or chunk table rejected
   __shared__ uint32_t lut[1 << kLutBits];
   __shared__ uint32_t fc[SZ3G_LMAX + 2], cnt[SZ3G_LMAX + 2], start[SZ3G_LMAX + 2];
@@ -966,62 +1076,74 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(const DecArgs a) {
     return;
   }
   const uint32_t* wp = a.words + a.woff[j];
-  uint32_t wi = (uint32_t)(bit0 >> 5);
+  // bit buffer: `buf` holds nb valid bits at the top; the next two payload
+  // words are loaded ahead (w1 is shifted in at the next refill), so a load
+  // is consumed about 64 bits (some ten codes) after it was issued
+  uint32_t wi = (uint32_t)(bit0 >> 5);  // next word to shift into buf
   unsigned long long buf = 0;
   int nb = 0;
+  uint32_t w1 = wi < nw ? __ldg(wp + wi) : 0u, w2 = wi + 1 < nw ? __ldg(wp + wi + 1) : 0u;
   if (wi < nw) {
-    buf = (unsigned long long)wp[wi++] << 32;
-    nb = 32;
-    const int skip = (int)(bit0 & 31);
-    buf <<= skip;
-    nb -= skip;
+    buf = (unsigned long long)w1 << (32 + (int)(bit0 & 31));
+    nb = 32 - (int)(bit0 & 31);
+    ++wi;
+    w1 = w2;
+    w2 = wi + 1 < nw ? __ldg(wp + wi + 1) : 0u;
   }
-  unsigned long long used = bit0;
   uint32_t zeros = 0;
-  uint32_t pack[4] = {0, 0, 0, 0};
   uint16_t* out = a.codes + j * a.chunk;
-  for (uint32_t i = c0; i < c1; ++i) {
+  const uint32_t n_used = a.T->n_used;
+  for (uint32_t i = c0; i < c1; i += 8) {  // c0 is a multiple of 8
     if (i != c0 && (i & (SZ3G_SUBBLOCK - 1)) == 0) {  // whole-chunk units count per sub-block
       a.zcnt[j * a.nsb + ((i >> 9) - 1)] = zeros;
       zeros = 0;
     }
-    while (nb <= 32 && wi < nw) {
-      buf |= (unsigned long long)wp[wi++] << (32 - nb);
-      nb += 32;
-    }
-    uint32_t e = lut[buf >> (64 - kLutBits)];
-    uint32_t L = e >> 16, sym = e & 0xffffu;
-    if (L == 0) {
-      for (uint32_t l = kLutBits + 1; l <= SZ3G_LMAX; ++l) {
-        const uint32_t v = (uint32_t)(buf >> (64 - l));
-        if (v - fc[l] < cnt[l]) {
-          const uint32_t k = start[l] + (v - fc[l]);
-          if (k < a.T->n_used) {
-            L = l;
-            sym = a.T->sorted[k];
+    const uint32_t m = min(8u, c1 - i);
+    uint32_t pk[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (uint32_t q = 0; q < 8; ++q) {
+      if (q < m) {
+        if (nb <= 32 && wi < nw) {
+          buf |= (unsigned long long)w1 << (32 - nb);
+          nb += 32;
+          ++wi;
+          w1 = w2;
+          w2 = wi + 1 < nw ? __ldg(wp + wi + 1) : 0u;
+        }
+        const uint32_t e = lut[(uint32_t)(buf >> (64 - kLutBits))];
+        uint32_t L = e >> 16, sym = e & 0xffffu;
+        if (L == 0) {  // longer than kLutBits: canonical first-code comparison
+          for (uint32_t l = kLutBits + 1; l <= SZ3G_LMAX; ++l) {
+            const uint32_t v = (uint32_t)(buf >> (64 - l));
+            if (v - fc[l] < cnt[l]) {
+              const uint32_t k = start[l] + (v - fc[l]);
+              if (k < n_used) {
+                L = l;
+                sym = a.T->sorted[k];
+              }
+              break;
+            }
           }
+        }
+        if (L == 0 || (int)L > nb) {
+          bad = true;
           break;
         }
+        buf <<= L;
+        nb -= (int)L;
+        zeros += sym == 0;
+        pk[q >> 1] |= sym << (16 * (q & 1));
       }
     }
-    if (L == 0 || (int)L > nb) {
-      bad = true;
-      break;
-    }
-    buf <<= L;
-    nb -= (int)L;
-    used += L;
-    zeros += sym == 0;
-    const uint32_t q = i & 7;
-    pack[q >> 1] |= sym << (16 * (q & 1));
-    if (q == 7) {
-      *reinterpret_cast<uint4*>(out + (i - 7)) = make_uint4(pack[0], pack[1], pack[2], pack[3]);
-      pack[0] = pack[1] = pack[2] = pack[3] = 0;
+    if (bad) break;
+    if (m == 8) {
+      *reinterpret_cast<uint4*>(out + i) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    } else {
+      for (uint32_t q = 0; q < m; ++q) out[i + q] = (uint16_t)(pk[q >> 1] >> (16 * (q & 1)));
     }
   }
   if (!bad) {
-    const uint32_t rem = c1 & 7;  // c0 is a multiple of 8
-    for (uint32_t q = 0; q < rem; ++q) out[c1 - rem + q] = (uint16_t)(pack[q >> 1] >> (16 * (q & 1)));
+    const unsigned long long used = 32ull * wi - (unsigned long long)nb;  // bits consumed from the chunk start
     a.zcnt[j * a.nsb + ((c1 - 1) >> 9)] = zeros;
     // the recorded sub-block boundary must be exactly where decoding ended
     if (sb && a.unit == SZ3G_SUBBLOCK && b + 1 < a.nsb && used != bit0 + sb[b]) bad = true;

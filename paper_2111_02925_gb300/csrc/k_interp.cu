@@ -5,6 +5,7 @@
 // the pass, reading the compact recon grid R_k of the level.  Coordinates are
 // padded to 4 axes, so this form handles every rank 1..4.
 #include <cstdio>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -20,48 +21,6 @@ constexpr int kRangeBlocks = 152 * 4;
 template <typename T>
 __device__ __forceinline__ bool finite_val(T v) {
   return isfinite(v);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kRangeThreads) range_partial_kernel(const T* __restrict__ x,
-                                                                       unsigned long long n, T* part,
-                                                                       DevState* st) {
-  T mn = x[0], mx = x[0];
-  bool bad = false;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  // 4 independent loads in flight per thread
-  for (; i + 3 * stride < n; i += 4 * stride) {
-    T v0 = x[i], v1 = x[i + stride], v2 = x[i + 2 * stride], v3 = x[i + 3 * stride];
-    bad |= !finite_val(v0) | !finite_val(v1) | !finite_val(v2) | !finite_val(v3);
-    mn = fmin(fmin(mn, v0), fmin(fmin(v1, v2), v3));
-    mx = fmax(fmax(mx, v0), fmax(fmax(v1, v2), v3));
-  }
-  for (; i < n; i += stride) {
-    T v = x[i];
-    bad |= !finite_val(v);
-    mn = fmin(mn, v);
-    mx = fmax(mx, v);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  }
-  __shared__ T smn[kRangeThreads / 32], smx[kRangeThreads / 32];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    smn[w] = mn;
-    smx[w] = mx;
-  }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->flags, kFlagNonFinite);
-  if (threadIdx.x == 0) {
-    for (int k = 1; k < kRangeThreads / 32; ++k) {
-      mn = fmin(mn, smn[k]);
-      mx = fmax(mx, smx[k]);
-    }
-    part[2 * blockIdx.x] = fmin(smn[0], mn);
-    part[2 * blockIdx.x + 1] = fmax(smx[0], mx);
-  }
 }
 
 __device__ __forceinline__ bool is_normal_f(float v) {
@@ -94,18 +53,13 @@ __device__ bool bound_into(double*, double e, DevState* st) {
   return true;
 }
 
+// The bound from the (REL) value range or the absolute eb.
 template <typename T>
-__global__ void eb_kernel(const T* part, int nparts, int eb_mode, double eb, DevState* st) {
-  if (threadIdx.x != 0) return;
+__device__ void set_bound(int eb_mode, double eb, T mn, T mx, DevState* st) {
   double e = eb;
   if (eb_mode == SZ3G_EB_REL) {
     if (st->flags & kFlagNonFinite) return;
-    T mn = part[0], mx = part[1];
-    for (int k = 1; k < nparts; ++k) {
-      mn = fmin(mn, part[2 * k]);
-      mx = fmax(mx, part[2 * k + 1]);
-    }
-    double range = (double)mx - (double)mn;
+    const double range = (double)mx - (double)mn;
     if (range == 0.0) {
       atomicOr(&st->flags, kFlagZeroRange);
       return;
@@ -119,6 +73,94 @@ __global__ void eb_kernel(const T* part, int nparts, int eb_mode, double eb, Dev
   st->eb_abs = e;
 }
 
+template <typename T>
+__device__ __forceinline__ void block_minmax(T& mn, T& mx, T* smn, T* smx) {
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    smn[w] = mn;
+    smx[w] = mx;
+  }
+  __syncthreads();
+  if (w == 0) {
+    mn = lane < kRangeThreads / 32 ? smn[lane] : smn[0];
+    mx = lane < kRangeThreads / 32 ? smx[lane] : smx[0];
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+  }
+}
+
+// Min / max / finiteness of the field with 16-byte loads (the field is 16-byte
+// aligned), four in flight per thread; each block writes its partial result
+// and the last block to finish reduces them and sets the bound.
+template <typename T>
+__global__ void __launch_bounds__(kRangeThreads) range_partial_kernel(const T* __restrict__ x,
+                                                                       unsigned long long n, T* part,
+                                                                       DevState* st, int eb_mode, double eb) {
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int kPer = 16 / sizeof(T);
+  T mn = x[0], mx = x[0];
+  bool bad = false;
+  auto take = [&](T v) {
+    bad |= !finite_val(v);
+    mn = fmin(mn, v);
+    mx = fmax(mx, v);
+  };
+  auto take_v = [&](const V& v) {
+    if constexpr (sizeof(T) == 4) {
+      take(v.x); take(v.y); take(v.z); take(v.w);
+    } else {
+      take(v.x); take(v.y);
+    }
+  };
+  const V* xv = reinterpret_cast<const V*>(x);
+  const unsigned long long nv = n / kPer;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < nv; i += 4 * stride) {
+    const V v0 = __ldcs(xv + i), v1 = __ldcs(xv + i + stride), v2 = __ldcs(xv + i + 2 * stride),
+            v3 = __ldcs(xv + i + 3 * stride);
+    take_v(v0); take_v(v1); take_v(v2); take_v(v3);
+  }
+  for (; i < nv; i += stride) take_v(__ldcs(xv + i));
+  for (unsigned long long t = nv * kPer + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride)
+    take(x[t]);
+  __shared__ T smn[kRangeThreads / 32], smx[kRangeThreads / 32];
+  __shared__ bool s_last;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->flags, kFlagNonFinite);
+  block_minmax(mn, mx, smn, smx);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = mn;
+    part[2 * blockIdx.x + 1] = mx;
+    __threadfence();
+    s_last = atomicAdd(&st->range_ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // last block: reduce the partial results
+  __threadfence();
+  mn = __ldcg(part);
+  mx = __ldcg(part + 1);
+  for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+    mn = fmin(mn, __ldcg(part + 2 * k));
+    mx = fmax(mx, __ldcg(part + 2 * k + 1));
+  }
+  __syncthreads();
+  block_minmax(mn, mx, smn, smx);
+  if (threadIdx.x == 0) set_bound<T>(eb_mode, eb, mn, mx, st);
+}
+
+// Absolute bound only (no range needed).
+template <typename T>
+__global__ void eb_kernel(int eb_mode, double eb, DevState* st) {
+  if (threadIdx.x == 0) set_bound<T>(eb_mode, eb, T(0), T(0), st);
+}
+
 size_t range_scratch_bytes(const Plan&) { return (size_t)kRangeBlocks * 2 * 8; }
 
 int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratch, size_t scratch_bytes,
@@ -126,18 +168,22 @@ int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratc
   if (scratch_bytes < range_scratch_bytes(pl)) return SZ3G_E_CAPACITY;
   int nparts = 1;
   if (eb_mode == SZ3G_EB_REL) {
-    unsigned long long want = (pl.N + kRangeThreads * 8 - 1) / (kRangeThreads * 8);
+    const int per = 16 / pl.esz;
+    unsigned long long want = (pl.N / per + kRangeThreads * 4 - 1) / (kRangeThreads * 4);
     nparts = (int)(want < kRangeBlocks ? (want ? want : 1) : kRangeBlocks);
     if (pl.dtype == SZ3G_F32)
-      SZ3G_LAUNCH(kKRange, s, range_partial_kernel<float><<<nparts, kRangeThreads, 0, s>>>((const float*)d_in, pl.N, (float*)scratch, st));
+      SZ3G_LAUNCH(kKRange, s,
+                  range_partial_kernel<float><<<nparts, kRangeThreads, 0, s>>>((const float*)d_in, pl.N,
+                                                                                (float*)scratch, st, eb_mode, eb));
     else
-      SZ3G_LAUNCH(kKRange, s, range_partial_kernel<double><<<nparts, kRangeThreads, 0, s>>>((const double*)d_in, pl.N, (double*)scratch,
-                                                                     st));
+      SZ3G_LAUNCH(kKRange, s,
+                  range_partial_kernel<double><<<nparts, kRangeThreads, 0, s>>>((const double*)d_in, pl.N,
+                                                                                 (double*)scratch, st, eb_mode, eb));
+  } else if (pl.dtype == SZ3G_F32) {
+    SZ3G_LAUNCH(kKEb, s, eb_kernel<float><<<1, 32, 0, s>>>(eb_mode, eb, st));
+  } else {
+    SZ3G_LAUNCH(kKEb, s, eb_kernel<double><<<1, 32, 0, s>>>(eb_mode, eb, st));
   }
-  if (pl.dtype == SZ3G_F32)
-    SZ3G_LAUNCH(kKEb, s, eb_kernel<float><<<1, 32, 0, s>>>((const float*)scratch, nparts, eb_mode, eb, st));
-  else
-    SZ3G_LAUNCH(kKEb, s, eb_kernel<double><<<1, 32, 0, s>>>((const double*)scratch, nparts, eb_mode, eb, st));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
