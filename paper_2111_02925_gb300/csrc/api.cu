@@ -79,7 +79,7 @@ DecompressWs decompress_layout(const Plan& pl) {
   w.zunit = l.take(pl.n_chunks * pl.nsub * 8);
   w.scan1 = l.take(scan_state_bytes(pl.n_chunks));
   w.scan2 = l.take(scan_state_bytes(pl.n_chunks * pl.nsub));
-  w.codes = l.take(pl.N * 2);
+  w.codes = l.take(pl.N * 2 + 256);  // the level kernels copy whole 16-byte blocks of codes
   for (int k = 1; k <= pl.L; ++k) w.R[k] = l.take(pl.gsize[k] * pl.esz);
   w.R[0] = 0;
   w.total = l.off;
@@ -332,7 +332,7 @@ int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_
   void* R[34];
   for (int k = 0; k <= pl.L; ++k) R[k] = k == 0 ? d_out : ws + L.R[k];
   SZ3G_TRY(launch_recover_levels(pl, codes, base + SZ3G_HEADER_BYTES, h.n_unpred, (unsigned long long*)(ws + L.zunit),
-                                 R, d_out, st, h.ebT_bits, s));
+                                 R, d_out, st, h.ebT_bits, true, s));
   DevState hs;
   SZ3G_TRY(read_state(st, &hs, s));
   return status_of(hs.flags);
@@ -433,7 +433,7 @@ int sz3g_recover(const sz3g_params* p, const void* h_ebT, const uint16_t* d_code
   void* R[34];
   for (int k = 0; k <= pl.L; ++k) R[k] = k == 0 ? d_out : ws + L.R[k];
   SZ3G_TRY(launch_recover_levels(pl, d_codes, d_unpred, n_unpred, (unsigned long long*)(ws + L.zunit), R, d_out,
-                                 st, eb_bits, s));
+                                 st, eb_bits, false, s));
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
   return status_of(h.flags);

@@ -169,33 +169,33 @@ __device__ __forceinline__ T interp_predict(T a, T b, T c, T d, bool has_b, bool
   return a;
 }
 
+// Truncation toward zero, saturating (NaN -> 0): only used where the result is
+// discarded unless the value is in range.
+__device__ __forceinline__ int to_int_rz(float v) { return __float2int_rz(v); }
+__device__ __forceinline__ int to_int_rz(double v) { return __double2int_rz(v); }
+
 // Linear-scaling quantizer (Sec. 3.2): code radius + q with q the index of the
 // width-2*eb bin holding x - pred (half-up), or 0 when |q| would reach the
-// radius or the reconstruction misses the bound.
+// radius or the reconstruction misses the bound.  Evaluated without branches:
+// every candidate value is computed and the result selected, so the rounding
+// of each step is the same as in the sequential form
+//   d = x - pred; t = |d| * ebr; if !(t < 2r - 1) -> 0;
+//   h = (trunc(t) + 1) >> 1; q = sign(d) h; r = pred + (2q) * eb;
+//   if !(|r - x| <= eb) -> 0; else radius + q.
 template <typename T>
 __device__ __forceinline__ uint32_t quantize_point(T x, T pred, T ebT, T ebr, int radius, T& recon) {
-  T d = x - pred;
-  T ad = d < T(0) ? -d : d;
-  T t = ad * ebr;
-  T lim = T(2 * radius - 1);
-  if (!(t < lim)) {
-    recon = x;
-    return 0u;
-  }
-  int m = (int)t;
-  int h = (m + 1) >> 1;
-  int q = (d < T(0)) ? -h : h;
-  T q2 = T(2 * q);
-  T step = q2 * ebT;
-  T r = pred + step;
-  T diff = r - x;
-  T err = diff < T(0) ? -diff : diff;
-  if (!(err <= ebT)) {
-    recon = x;
-    return 0u;
-  }
-  recon = r;
-  return (uint32_t)(radius + q);
+  const T d = x - pred;
+  const T t = fabs(d) * ebr;
+  const bool in = t < T(2 * radius - 1);  // false for NaN
+  const int m = to_int_rz(t);
+  const int h = (int)(((unsigned)m + 1u) >> 1);
+  const int q = d < T(0) ? -h : h;
+  const T q2 = T((int)((unsigned)q << 1));
+  const T step = q2 * ebT;
+  const T r = pred + step;
+  const bool ok = in && fabs(r - x) <= ebT;
+  recon = ok ? r : x;
+  return ok ? (uint32_t)(radius + q) : 0u;
 }
 
 // recover() (Sec. 3.2): pred + 2 (code - radius) eb.
@@ -230,7 +230,7 @@ int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, vo
 int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred,
                           unsigned long long n_unpred, const unsigned long long* zunit,
                           void* const* R, void* d_out, DevState* st, unsigned long long ebT_bits,
-                          cudaStream_t s);
+                          bool codes_padded, cudaStream_t s);
 
 // k_level.cu (fields of rank <= 3)
 bool level_path_ok(const Plan& pl);
@@ -238,7 +238,7 @@ int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, voi
                           DevState* st, cudaStream_t s);
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
                          const unsigned long long* zunit, void* const* R, void* d_out,
-                         DevState* st, unsigned long long ebT_bits, cudaStream_t s);
+                         DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s);
 
 // k_huffman.cu
 size_t codebook_scratch_bytes();

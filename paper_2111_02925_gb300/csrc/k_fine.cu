@@ -1,0 +1,614 @@
+// k_fine.cu -- register-blocked level kernel for grids refined in axis order
+// (0, 1, 2) (3-D) or (1, 2) (2-D: axis 0 is a unit axis).
+//
+// One launch per grid G_k.  The level's passes (Sec. 6.2, multilevel
+// interpolation: refine axis 0, then 1, then 2 at the finest stride of G_k)
+// split the points of G_k by the parity of their coordinates: pass 0 takes
+// (odd i, even j, even k), pass 1 (any i, odd j, even k), pass 2 (any i, any j,
+// odd k).  Passes 0 and 1 read and write only even-k points, so a tile keeps
+// the even-k points of its rows in a separate shared-memory plane E (the
+// coarse points R_{k+1} copied in, then the pass-0 and pass-1 results); pass 2
+// then reads, for a run of four odd points along k, the seven even values
+// around them with two 16-byte loads.
+//
+// Tile: T0 x T1 x 64 points (i, j, k); 4 x 16 x 64 in 3-D, 1 x 64 x 64 in 2-D.
+// Staged per tile, double-buffered, on one mbarrier per buffer:
+//   x box   (compress) input rows i in [A0, A0+T0), j in [A1-2, A1+T1+3),
+//           k in [A2-4, A2+68)                      -- tensor copy
+//   C box   R_{k+1} points (i/2, j/2, k/2) around the tile    -- tensor copy
+//   codes   (recover) every row of codes the tile's passes read -- bulk copies
+// The next tile's copies are issued before the current tile is computed.
+// Halo points (pass-0/1 points just outside the tile that pass 1/2 read) are
+// evaluated redundantly and never written; points outside the grid are
+// skipped.  Tiles on a face of the grid take the one-sided predictors through
+// per-row (passes 0, 1) and per-point (pass 2) boundary flags.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "internal.cuh"
+#include "level_common.cuh"
+
+namespace sz3g {
+
+// threads per CTA: compress keeps twice the x box in shared memory, so it runs
+// fewer, larger CTAs
+template <bool COMP>
+struct FineThreads {
+  static constexpr int kN = COMP ? 512 : 256, kMinBlocks = COMP ? 2 : 4;
+};
+
+template <int T0>
+struct FineShape {
+  static constexpr bool kHas0 = T0 > 1;                   // axis 0 refined
+  static constexpr int kT0 = T0, kT1 = T0 > 1 ? 16 : 64, kW = 64;
+  static constexpr int kXJ = kT1 + 5;                     // x box / E rows: j = A1 - 2 + j21
+  static constexpr int kXK = kW + 8;                      // x box columns: k = A2 - 4 + c
+  static constexpr int kEK = kXK / 2;                     // even-k values per row: k = A2 - 4 + 2 ke
+  static constexpr int kPairs = kEK / 2;                  // tasks of two even-k points per row
+  static constexpr int kCI = T0 > 1 ? 5 : 1;              // coarse box: i/2 = A0/2 - 1 + ci (3-D)
+  static constexpr int kCJ = kT1 / 2 + 3;                 //             j/2 = A1/2 - 1 + cj
+  static constexpr int kCK = 40;                          //             k/2 = A2/2 - 4 + ck
+  static constexpr int kEvenI = T0 > 1 ? 2 : 1;           // tile rows along i that are even
+  static constexpr int kCopyTasks = kEvenI * kCJ * kPairs;
+  static constexpr int kP0Tasks = T0 > 1 ? 2 * kCJ * kPairs : 0;
+  static constexpr int kP1Tasks = kT0 * (kT1 / 2) * kPairs;
+  static constexpr int kP2Tasks = kT0 * kT1 * (kW / 8);   // runs of four odd points
+  // code rows (recover): pass 2 rows of 32 codes, pass 1 / pass 0 rows of 36
+  static constexpr int kR2 = kT0 * kT1, kR1 = kT0 * (kT1 / 2), kR0 = T0 > 1 ? 2 * kCJ : 0;
+  static constexpr int kL2 = 40, kL01 = 48;               // u16 slots per staged row (80 / 96 bytes)
+  static constexpr int kCodeSlots = kR2 * kL2 + (kR1 + kR0) * kL01;
+};
+
+// Shared-memory layout: tensor-copy destinations on 128-byte boundaries,
+// buffers padded so that the second buffer stays aligned.
+template <typename T, bool COMP, int T0>
+struct FineLayout {
+  using S = FineShape<T0>;
+  static constexpr size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+  static constexpr int kXB = COMP ? (int)(up(S::kT0 * S::kXJ * S::kXK * sizeof(T), 128) / sizeof(T)) : 0;
+  static constexpr int kCB = (int)(up(S::kCI * S::kCJ * S::kCK * sizeof(T), 128) / sizeof(T));
+  static constexpr int kKB = COMP ? 0 : (int)up(S::kCodeSlots, 64);
+  static constexpr size_t kOffX = 0;
+  static constexpr size_t kOffC = kOffX + 2 * (size_t)kXB * sizeof(T);
+  static constexpr size_t kOffE = kOffC + 2 * (size_t)kCB * sizeof(T);
+  static constexpr size_t kOffK = up(kOffE + (size_t)S::kT0 * S::kXJ * S::kEK * sizeof(T), 128);
+  static constexpr size_t kOffH = kOffK + 2 * (size_t)kKB * 2;
+  static constexpr size_t kOffBar = up(kOffH + (COMP ? kHistWin * 4 : 0), 16);
+  static constexpr size_t kBytes = kOffBar + 16;
+};
+
+struct FineDesc {
+  int m0, m1, m2;              // extents of G_k (m0 = 1 in 2-D)
+  int nt1, nt2;                // tiles along j, k
+  uint32_t ntiles;
+  uint32_t off[3];             // first code of passes 0, 1, 2 (pass 0 unused in 2-D)
+  uint32_t E1[3], E2[3];       // lattice extents of each pass along j and k
+  uint32_t rs0, rs1;           // output row strides (elements) along i, j; contiguous along k
+  uint32_t chunk, nsub;
+  int write_out;
+  uint32_t tensor_bytes;       // bytes of the x and coarse boxes of one tile
+};
+
+// ---- vector helpers -----------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T* v) {  // 4 consecutive, 16-byte aligned
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+  } else {
+    const double2 q0 = *reinterpret_cast<const double2*>(p), q1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = q0.x, v[1] = q0.y, v[2] = q1.x, v[3] = q1.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void ld2(const T* p, T* v) {  // 2 consecutive, 2 * sizeof(T)-aligned
+  if constexpr (sizeof(T) == 4) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x, v[1] = q.y;
+  } else {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x, v[1] = q.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st2(T* p, T a, T b) {
+  if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  else *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, T a, T b, T c, T d) {  // 16-byte aligned
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+  }
+}
+
+// Per-thread results of the tile passes, flushed once per CTA.
+struct FineAcc {
+  unsigned int nz;
+  bool bad;
+};
+
+// Quantize (compress) or recover (decompress) one point whose prediction is
+// p; returns its reconstruction.  `code_in` is the stored code (recover).
+template <typename T, bool COMP>
+__device__ __forceinline__ T fine_point(const LevelArgs<T>& a, const FineDesc& d, uint32_t* hwin, int hlo, T x, T p,
+                                        T ebT, T ebr, bool own, uint32_t ci, uint32_t code_in, FineAcc& acc) {
+  if (COMP) {
+    T r;
+    const uint32_t code = quantize_point<T>(x, p, ebT, ebr, a.radius, r);
+    if (own) {
+      a.codes[ci] = (uint16_t)code;
+      // unpredictable: also where a non-finite input ends up
+      acc.nz += code == 0;
+      acc.bad |= (code == 0) & !isfinite(x);
+      const uint32_t bn = code - (uint32_t)hlo;
+      if (bn < (uint32_t)kHistWin) atomicAdd(&hwin[bn], 1u);
+      else atomicAdd(&a.hist[code], 1u);
+    }
+    return r;
+  } else {
+    if (code_in == 0) {
+      const unsigned long long rk = rank_of_zero(a.codes, ci, d.chunk, d.nsub, a.zunit);
+      if (rk < a.n_unpred) return a.unpred[rk];
+      acc.bad = true;
+      return T(0);
+    }
+    if (code_in >= 2u * (uint32_t)a.radius) {
+      acc.bad = true;
+      return T(0);
+    }
+    return recover_point<T>(p, code_in, a.radius, ebT);
+  }
+}
+
+// First code of a staged row and where its aligned 16-byte copy starts
+// (codes before the array start, only at rows whose leading points lie
+// outside the grid, are never read).
+__device__ __forceinline__ void code_row(long long c0, long long* a16, int* o) {
+  long long al = c0 >= 0 ? (c0 & ~7ll) : 0;
+  *a16 = al;
+  *o = (int)(c0 - al);
+}
+
+template <typename T, bool COMP, int INTERP, int T0>
+__global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMinBlocks)
+    fine_kernel(const FineDesc d, const LevelArgs<T> a, const __grid_constant__ CUtensorMap tmx,
+                const __grid_constant__ CUtensorMap tmc) {
+  using S = FineShape<T0>;
+  using L = FineLayout<T, COMP, T0>;
+  constexpr int kFineThreads = FineThreads<COMP>::kN;
+  constexpr int XB = L::kXB, CB = L::kCB, KB = L::kKB;  // elements per buffer
+  extern __shared__ __align__(128) unsigned char sm[];
+  T* Xs = reinterpret_cast<T*>(sm + L::kOffX);              // [2][XB] (compress)
+  T* Cs = reinterpret_cast<T*>(sm + L::kOffC);              // [2][CB]
+  T* E = reinterpret_cast<T*>(sm + L::kOffE);               // even-k plane
+  uint16_t* Ks = reinterpret_cast<uint16_t*>(sm + L::kOffK);  // [2][KB] (recover)
+  uint32_t* hwin = reinterpret_cast<uint32_t*>(sm + L::kOffH);  // [kHistWin] (compress)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::kOffBar);  // [2]
+  __shared__ unsigned long long s_nz;
+  __shared__ int s_bad, s_timeout;
+  __shared__ uint32_t s_bytes[2];
+  const int tid = threadIdx.x;
+  DevState* st = a.st;
+  if (COMP && (st->flags & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound))) return;
+  if (!COMP && (st->flags & kFlagCorrupt)) return;
+  const T ebT = COMP ? bits_to<T>(st->ebT_bits) : a.ebT;
+  const T ebr = COMP ? bits_to<T>(st->ebr_bits) : T(0);
+  const int hlo = a.radius - kHistWin / 2;
+  const int m0 = d.m0, m1 = d.m1, m2 = d.m2;
+  if (COMP)
+    for (int i = tid; i < kHistWin; i += kFineThreads) hwin[i] = 0;
+  if (tid == 0) {
+    s_nz = 0;
+    s_bad = 0;
+    s_timeout = 0;
+    s_bytes[0] = s_bytes[1] = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  FineAcc acc{0u, false};
+
+  auto tile_origin = [&](uint32_t tile, int& A0, int& A1, int& A2) {
+    const uint32_t t2 = tile % (uint32_t)d.nt2, r = tile / (uint32_t)d.nt2;
+    const uint32_t t1 = r % (uint32_t)d.nt1, t0 = r / (uint32_t)d.nt1;
+    A0 = (int)t0 * S::kT0;
+    A1 = (int)t1 * S::kT1;
+    A2 = (int)t2 * S::kW;
+  };
+  // code rows of a tile: first code of each staged row
+  auto row_c0 = [&](int A0, int A1, int A2, int r, int& which, int& slot, bool& valid) -> long long {
+    if (r < S::kR2) {  // pass 2 row (i, j) of the tile
+      const int i = A0 + r / S::kT1, j = A1 + r % S::kT1;
+      which = 2;
+      slot = r * S::kL2;
+      valid = i < m0 && j < m1;
+      return (long long)d.off[2] + ((long long)i * d.E1[2] + j) * d.E2[2] + A2 / 2;
+    }
+    r -= S::kR2;
+    if (r < S::kR1) {  // pass 1 row (i, odd j)
+      const int i = A0 + r / (S::kT1 / 2), j = A1 + 2 * (r % (S::kT1 / 2)) + 1;
+      which = 1;
+      slot = S::kR2 * S::kL2 + r * S::kL01;
+      valid = i < m0 && j < m1;
+      return (long long)d.off[1] + ((long long)i * d.E1[1] + (j - 1) / 2) * d.E2[1] + (A2 / 2 - 2);
+    }
+    r -= S::kR1;  // pass 0 row (odd i, even j)
+    const int i = A0 + 2 * (r / S::kCJ) + 1, j = A1 - 2 + 2 * (r % S::kCJ);
+    which = 0;
+    slot = S::kR2 * S::kL2 + (S::kR1 + r) * S::kL01;
+    valid = i < m0 && j >= 0 && j < m1;
+    return (long long)d.off[0] + ((long long)(i - 1) / 2 * d.E1[0] + j / 2) * d.E2[0] + (A2 / 2 - 2);
+  };
+  // issue the copies of `tile` into buffer b (compress: tensor copies and the
+  // arrival; recover: also the code rows, whose bytes are summed in
+  // s_bytes[b] and announced by finish_issue after a barrier)
+  auto issue = [&](uint32_t tile, int b) {
+    int A0, A1, A2;
+    tile_origin(tile, A0, A1, A2);
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      if (COMP) {
+        mbar_expect_tx(&bar[b], d.tensor_bytes);
+        tma_load_3d(Xs + b * XB, &tmx, A2 - 4, A1 - 2, A0, &bar[b]);
+      }
+      tma_load_3d(Cs + b * CB, &tmc, A2 / 2 - 4, A1 / 2 - 1, S::kHas0 ? A0 / 2 - 1 : 0, &bar[b]);
+    }
+    if (!COMP && tid < S::kR2 + S::kR1 + S::kR0) {
+      int which, slot;
+      bool valid;
+      const long long c0 = row_c0(A0, A1, A2, tid, which, slot, valid);
+      if (valid) {
+        long long al;
+        int o;
+        code_row(c0, &al, &o);
+        const uint32_t bytes = which == 2 ? S::kL2 * 2 : S::kL01 * 2;
+        fence_proxy_async_smem();
+        bulk_load(Ks + b * KB + slot, a.codes + al, bytes, &bar[b]);
+        atomicAdd(&s_bytes[b], bytes);
+      }
+    }
+  };
+  auto finish_issue = [&](int b) {  // after a barrier that follows issue(b)
+    if (!COMP && tid == 0) {
+      mbar_expect_tx(&bar[b], d.tensor_bytes + s_bytes[b]);
+      s_bytes[b] = 0;
+    }
+  };
+
+  uint32_t phase[2] = {0u, 0u};
+  uint32_t tile = blockIdx.x;
+  if (tile < d.ntiles) issue(tile, 0);
+  __syncthreads();
+  if (tile < d.ntiles) finish_issue(0);
+  int b = 0;
+  for (; tile < d.ntiles; tile += gridDim.x, b ^= 1) {
+    const uint32_t next = tile + gridDim.x;
+    const bool has_next = next < d.ntiles;
+    if (has_next) issue(next, b ^ 1);
+    // wait for this tile's copies
+    {
+      int spins = 0;
+      bool done = true;
+      while (!mbar_try_wait(&bar[b], phase[b])) {
+        if (++spins > kWaitLimit) {
+          s_timeout = 1;
+          done = false;
+          break;
+        }
+      }
+      if (done) phase[b] ^= 1u;
+    }
+    __syncthreads();
+    if (s_timeout) {
+      if (has_next) finish_issue(b ^ 1);  // so that the copies in flight can be waited for
+      break;
+    }
+    if (has_next) finish_issue(b ^ 1);
+    int A0, A1, A2;
+    tile_origin(tile, A0, A1, A2);
+    const T* X = Xs + b * XB;
+    const T* C = Cs + b * CB;
+    const uint16_t* K = Ks + b * KB;
+    const bool edgek = !(A2 >= 4 && A2 + S::kW + 4 <= m2);
+
+    // ---- coarse points into E, and pass 0 (odd i, even j) ------------------
+    for (int t = tid; t < S::kCopyTasks + S::kP0Tasks; t += kFineThreads) {
+      if (t < S::kCopyTasks) {
+        const int pr = t % S::kPairs, row = t / S::kPairs;
+        const int e = row / S::kCJ, cj = row % S::kCJ;
+        T v[2];
+        ld2(C + ((e + (S::kHas0 ? 1 : 0)) * S::kCJ + cj) * S::kCK + 2 * pr + 2, v);
+        st2(E + ((2 * e) * S::kXJ + 2 * cj) * S::kEK + 2 * pr, v[0], v[1]);
+        continue;
+      }
+      if constexpr (S::kHas0) {
+        const int u = t - S::kCopyTasks;
+        const int pr = u % S::kPairs, row = u / S::kPairs;
+        const int eo = row / S::kCJ, cj = row % S::kCJ;
+        const int i = A0 + 2 * eo + 1, j = A1 - 2 + 2 * cj;
+        if (i >= m0 || j < 0 || j >= m1) continue;
+        const int ke = 2 * pr, k = A2 - 4 + 2 * ke;
+        const bool hb = i + 1 < m0, hc = i >= 3, hd = i + 3 < m0;
+        T va[2], vb[2], vc[2], vd[2];
+        ld2(C + ((eo + 1) * S::kCJ + cj) * S::kCK + ke + 2, va);
+        ld2(C + ((eo + 2) * S::kCJ + cj) * S::kCK + ke + 2, vb);
+        ld2(C + ((eo + 0) * S::kCJ + cj) * S::kCK + ke + 2, vc);
+        ld2(C + ((eo + 3) * S::kCJ + cj) * S::kCK + ke + 2, vd);
+        T xv[4] = {T(0), T(0), T(0), T(0)};
+        if (COMP) ld4(X + ((2 * eo + 1) * S::kXJ + 2 * cj) * S::kXK + 2 * ke, xv);
+        const long long c0 = (long long)d.off[0] + ((long long)(i - 1) / 2 * d.E1[0] + j / 2) * d.E2[0] + (A2 / 2 - 2);
+        const bool ownj = j >= A1 && j < A1 + S::kT1;
+        int o = 0;
+        const uint16_t* kr = nullptr;
+        if (!COMP) {
+          long long al;
+          code_row(c0, &al, &o);
+          kr = K + S::kR2 * S::kL2 + (S::kR1 + row) * S::kL01 + o;
+        }
+        T r[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int kq = k + 2 * q;
+          r[q] = T(0);
+          if (kq < 0 || kq >= m2) continue;
+          const T p = interp_predict<T>(va[q], vb[q], vc[q], vd[q], hb, hc, hd, INTERP);
+          const bool own = ownj && ke + q >= 2 && ke + q < 2 + S::kW / 2;
+          r[q] = fine_point<T, COMP>(a, d, hwin, hlo, xv[2 * q], p, ebT, ebr, own, (uint32_t)(c0 + ke + q),
+                                     COMP ? 0u : (uint32_t)kr[ke + q], acc);
+        }
+        st2(E + ((2 * eo + 1) * S::kXJ + 2 * cj) * S::kEK + ke, r[0], r[1]);
+      }
+    }
+    __syncthreads();
+
+    // ---- pass 1 (any i, odd j) ----------------------------------------------
+    for (int t = tid; t < S::kP1Tasks; t += kFineThreads) {
+      const int pr = t % S::kPairs, row = t / S::kPairs;
+      const int i4 = row / (S::kT1 / 2), jo = row % (S::kT1 / 2);
+      const int i = A0 + i4, j = A1 + 2 * jo + 1;
+      if (i >= m0 || j >= m1) continue;
+      const int ke = 2 * pr, k = A2 - 4 + 2 * ke;
+      const int j21 = 2 * jo + 3;
+      const bool hb = j + 1 < m1, hc = j >= 3, hd = j + 3 < m1;
+      const T* Er = E + (i4 * S::kXJ + j21) * S::kEK + ke;
+      T va[2], vb[2], vc[2], vd[2];
+      ld2(Er - S::kEK, va);
+      ld2(Er + S::kEK, vb);
+      ld2(Er - 3 * S::kEK, vc);
+      ld2(Er + 3 * S::kEK, vd);
+      T xv[4] = {T(0), T(0), T(0), T(0)};
+      if (COMP) ld4(X + (i4 * S::kXJ + j21) * S::kXK + 2 * ke, xv);
+      const long long c0 = (long long)d.off[1] + ((long long)i * d.E1[1] + (j - 1) / 2) * d.E2[1] + (A2 / 2 - 2);
+      int o = 0;
+      const uint16_t* kr = nullptr;
+      if (!COMP) {
+        long long al;
+        code_row(c0, &al, &o);
+        kr = K + S::kR2 * S::kL2 + row * S::kL01 + o;
+      }
+      T r[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int kq = k + 2 * q;
+        r[q] = T(0);
+        if (kq < 0 || kq >= m2) continue;
+        const T p = interp_predict<T>(va[q], vb[q], vc[q], vd[q], hb, hc, hd, INTERP);
+        const bool own = ke + q >= 2 && ke + q < 2 + S::kW / 2;
+        r[q] = fine_point<T, COMP>(a, d, hwin, hlo, xv[2 * q], p, ebT, ebr, own, (uint32_t)(c0 + ke + q),
+                                   COMP ? 0u : (uint32_t)kr[ke + q], acc);
+      }
+      st2(E + (i4 * S::kXJ + j21) * S::kEK + ke, r[0], r[1]);
+    }
+    __syncthreads();
+
+    // ---- pass 2 (any i, any j, odd k): runs of four ------------------------
+    for (int t = tid; t < S::kP2Tasks; t += kFineThreads) {
+      const int q4 = t & 7, row = t >> 3;
+      const int i4 = row / S::kT1, j16 = row % S::kT1;
+      const int i = A0 + i4, j = A1 + j16;
+      if (i >= m0 || j >= m1) continue;
+      const int j21 = j16 + 2;
+      const T* Er = E + (i4 * S::kXJ + j21) * S::kEK + 4 * q4;
+      T e[8];
+      ld4(Er, e);
+      ld4(Er + 4, e + 4);
+      T xo[4] = {T(0), T(0), T(0), T(0)};
+      if (COMP) {
+        T xv[8];
+        const T* xr = X + (i4 * S::kXJ + j21) * S::kXK + 8 * q4 + 4;
+        ld4(xr, xv);
+        ld4(xr + 4, xv + 4);
+        xo[0] = xv[1], xo[1] = xv[3], xo[2] = xv[5], xo[3] = xv[7];
+      }
+      const long long c0 = (long long)d.off[2] + ((long long)i * d.E1[2] + j) * d.E2[2] + A2 / 2;
+      const uint32_t ci = (uint32_t)(c0 + 4 * q4);
+      const uint16_t* kr = nullptr;
+      if (!COMP) {
+        long long al;
+        int o;
+        code_row(c0, &al, &o);
+        kr = K + row * S::kL2 + o + 4 * q4;
+      }
+      const int k0 = A2 + 8 * q4;  // first (even) k of the run's eight points
+      T r[4];
+      if (!edgek) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const T p = interp_predict<T>(e[u + 2], e[u + 3], e[u + 1], e[u + 4], true, true, true, INTERP);
+          r[u] = fine_point<T, COMP>(a, d, hwin, hlo, xo[u], p, ebT, ebr, true, ci + u, COMP ? 0u : (uint32_t)kr[u],
+                                     acc);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int kk = k0 + 2 * u + 1;
+          r[u] = T(0);
+          if (kk >= m2) continue;
+          const bool hb = kk + 1 < m2, hc = kk >= 3, hd = kk + 3 < m2;
+          const T p = interp_predict<T>(e[u + 2], hb ? e[u + 3] : T(0), hc ? e[u + 1] : T(0), hd ? e[u + 4] : T(0),
+                                        hb, hc, hd, INTERP);
+          r[u] = fine_point<T, COMP>(a, d, hwin, hlo, xo[u], p, ebT, ebr, true, ci + u, COMP ? 0u : (uint32_t)kr[u],
+                                     acc);
+        }
+      }
+      if (d.write_out) {
+        T* dst = a.Rout + ((unsigned long long)i * d.rs0 + (unsigned long long)j * d.rs1 + (unsigned long long)k0);
+        if (k0 + 8 <= m2) {
+          st4(dst, e[2], r[0], e[3], r[1]);
+          st4(dst + 4, e[4], r[2], e[5], r[3]);
+        } else {
+          const T v8[8] = {e[2], r[0], e[3], r[1], e[4], r[2], e[5], r[3]};
+#pragma unroll
+          for (int s = 0; s < 8; ++s)
+            if (k0 + s < m2) dst[s] = v8[s];
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- flush the per-CTA counters
+  if (acc.nz) atomicAdd(&s_nz, (unsigned long long)acc.nz);
+  if (acc.bad) s_bad = 1;
+  __syncthreads();
+  if (s_timeout) {
+    // give copies still in flight a last bounded chance to land
+    for (int q = 0; q < 2; ++q) {
+      int spins = 0;
+      while (!mbar_try_wait(&bar[q], phase[q]) && ++spins < kWaitLimit) {
+      }
+    }
+    if (tid == 0) atomicOr(&st->flags, kFlagTimeout);
+  }
+  if (COMP) {
+    for (int i = tid; i < kHistWin; i += kFineThreads)
+      if (hwin[i]) atomicAdd(&a.hist[hlo + i], hwin[i]);
+    if (tid == 0) {
+      if (s_nz) atomicAdd(&st->n_unpred, s_nz);
+      if (s_bad) atomicOr(&st->flags, kFlagNonFinite);
+    }
+  } else if (tid == 0 && s_bad) {
+    atomicOr(&st->flags, kFlagCorrupt);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
+template <typename T>
+static bool fine_map(CUtensorMap* map, const T* base, int m0, int m1, int m2, int b0, int b1, int b2) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)m2, (cuuint64_t)m1, (cuuint64_t)m0};
+  const cuuint64_t strides[2] = {(cuuint64_t)m2 * sizeof(T), (cuuint64_t)m1 * m2 * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)b2, (cuuint32_t)b1, (cuuint32_t)b0};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  return enc(map, dt, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Whether the register-blocked kernel takes level k (the passes of G_k in
+// plan order): 3-D grids refined in axis order (0, 1, 2) or 2-D grids in
+// (1, 2), with 16-byte aligned rows for the tensor copies.
+bool fine_eligible(const Plan& pl, int k, bool comp, const void* x, const void* Rc, const void* Rout, bool to_field) {
+  if (pl.ndim < 2 || pl.n[0] != 1) return false;
+  int ax[4], P = 0;
+  for (int i = 0; i < pl.n_pass; ++i)
+    if (pl.pass[i].grid == k) {
+      if (P == 4) return false;
+      ax[P++] = pl.pass[i].axis;
+    }
+  const unsigned long long* m = pl.gm[k];
+  const bool three = m[1] > 1;
+  if (three ? !(P == 3 && ax[0] == 1 && ax[1] == 2 && ax[2] == 3) : !(P == 2 && ax[0] == 2 && ax[1] == 3))
+    return false;
+  const size_t esz = (size_t)pl.esz;
+  const unsigned long long* mc = pl.gm[k + 1];
+  auto rows16 = [&](unsigned long long e2) { return (e2 * esz) % 16 == 0; };
+  if (!rows16(mc[3]) || ((uintptr_t)Rc % 16) != 0) return false;
+  if (comp && (k != 0 || !rows16(m[3]) || ((uintptr_t)x % 16) != 0)) return false;
+  if (!comp && Rout && (!rows16(to_field ? pl.n[3] : m[3]) || ((uintptr_t)Rout % 16) != 0)) return false;
+  return m[2] >= 2 && m[3] >= 2 && pl.gsize[k] <= 0xffffffffull;
+}
+
+template <typename T, bool COMP, int T0>
+static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_field, cudaStream_t s) {
+  using S = FineShape<T0>;
+  FineDesc d;
+  memset(&d, 0, sizeof(d));
+  const unsigned long long* m = pl.gm[k];
+  d.m0 = (int)m[1];
+  d.m1 = (int)m[2];
+  d.m2 = (int)m[3];
+  d.nt1 = (d.m1 + S::kT1 - 1) / S::kT1;
+  d.nt2 = (d.m2 + S::kW - 1) / S::kW;
+  const int nt0 = (d.m0 + S::kT0 - 1) / S::kT0;
+  d.ntiles = (uint32_t)nt0 * (uint32_t)d.nt1 * (uint32_t)d.nt2;
+  int p = S::kHas0 ? 0 : 1;
+  int interp = SZ3G_LINEAR;
+  for (int i = 0; i < pl.n_pass; ++i) {
+    const PassDesc& pd = pl.pass[i];
+    if (pd.grid != k) continue;
+    d.off[p] = (uint32_t)pd.off;
+    d.E1[p] = pd.E[2];
+    d.E2[p] = pd.E[3];
+    interp = pd.interp;
+    ++p;
+  }
+  d.write_out = a.Rout != nullptr;
+  if (to_field) {
+    d.rs1 = (uint32_t)pl.fstride[2];
+    d.rs0 = (uint32_t)pl.fstride[1];
+  } else {
+    d.rs1 = (uint32_t)m[3];
+    d.rs0 = (uint32_t)(m[3] * m[2]);
+  }
+  d.chunk = pl.chunk;
+  d.nsub = pl.nsub;
+  const unsigned long long* mc = pl.gm[k + 1];
+  CUtensorMap tmx, tmc;
+  memset(&tmx, 0, sizeof(tmx));
+  memset(&tmc, 0, sizeof(tmc));
+  bool ok = fine_map<T>(&tmc, a.Rc, (int)mc[1], (int)mc[2], (int)mc[3], S::kCI, S::kCJ, S::kCK);
+  d.tensor_bytes = (uint32_t)(S::kCI * S::kCJ * S::kCK * sizeof(T));
+  if (COMP) {
+    ok = ok && fine_map<T>(&tmx, a.x, d.m0, d.m1, d.m2, S::kT0, S::kXJ, S::kXK);
+    d.tensor_bytes += (uint32_t)(S::kT0 * S::kXJ * S::kXK * sizeof(T));
+  }
+  if (!ok) return SZ3G_E_CUDA;
+  const size_t smem = FineLayout<T, COMP, T0>::kBytes;
+  auto kern = interp == SZ3G_CUBIC ? fine_kernel<T, COMP, SZ3G_CUBIC, T0> : fine_kernel<T, COMP, SZ3G_LINEAR, T0>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return SZ3G_E_CUDA;
+  int dev = 0, nsm = 152, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, FineThreads<COMP>::kN, smem);
+  if (per < 1) per = 1;
+  unsigned long long grid = (unsigned long long)nsm * per;
+  if (grid > d.ntiles) grid = d.ntiles;
+  SZ3G_LAUNCH(COMP ? kKLevelQuantize : kKLevelRecover, s,
+              kern<<<(unsigned)grid, FineThreads<COMP>::kN, smem, s>>>(d, a, tmx, tmc));
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+template <typename T, bool COMP>
+int launch_fine(const Plan& pl, int k, const LevelArgs<T>& a, bool to_field, cudaStream_t s) {
+  return pl.gm[k][1] > 1 ? launch_fine_t<T, COMP, 4>(pl, k, a, to_field, s)
+                         : launch_fine_t<T, COMP, 1>(pl, k, a, to_field, s);
+}
+
+template int launch_fine<float, true>(const Plan&, int, const LevelArgs<float>&, bool, cudaStream_t);
+template int launch_fine<float, false>(const Plan&, int, const LevelArgs<float>&, bool, cudaStream_t);
+template int launch_fine<double, true>(const Plan&, int, const LevelArgs<double>&, bool, cudaStream_t);
+template int launch_fine<double, false>(const Plan&, int, const LevelArgs<double>&, bool, cudaStream_t);
+
+}  // namespace sz3g

@@ -437,8 +437,9 @@ static int recover_levels_t(const Plan& pl, const uint16_t* codes, const T* unpr
 
 int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
                           const unsigned long long* zunit, void* const* R, void* d_out,
-                          DevState* st, unsigned long long ebT_bits, cudaStream_t s) {
-  if (level_path_ok(pl)) return launch_recover_fused(pl, codes, unpred, n_unpred, zunit, R, d_out, st, ebT_bits, s);
+                          DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s) {
+  if (level_path_ok(pl))
+    return launch_recover_fused(pl, codes, unpred, n_unpred, zunit, R, d_out, st, ebT_bits, codes_padded, s);
   if (pl.dtype == SZ3G_F32) {
     float e;
     uint32_t b = (uint32_t)ebT_bits;

@@ -26,11 +26,11 @@
 #include <cudaTypedefs.h>
 
 #include "internal.cuh"
+#include "level_common.cuh"
 
 namespace sz3g {
 
 constexpr int kLevelThreads = 256;
-constexpr int kHistWin = 2048;  // shared-memory histogram window around the radius
 
 struct LevelDesc {
   int k, P, interp, write_out;
@@ -55,76 +55,6 @@ struct LevelDesc {
   uint32_t smem_c, smem_h, smem_bar;  // byte offsets of the coarse box, histogram, barrier
 };
 
-template <typename T>
-struct LevelArgs {
-  const T* x;          // compress: input field
-  const T* Rc;         // R_{k+1}
-  T* Rout;             // R_k, or the field on decompress at k = 0
-  uint16_t* codes;
-  uint32_t* hist;
-  DevState* st;
-  const T* unpred;     // decompress
-  unsigned long long n_unpred;
-  const unsigned long long* zunit;  // zeros before each 512-code sub-block
-  int radius;
-  T ebT;               // decompress (compress reads the device state)
-};
-
-// Asynchronous 4- or 8-byte global -> shared copy.
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* dst_smem, const T* src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
-  if (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
-// ---- tensor copies (TMA) ----------------------------------------------------
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-          (uint32_t)__cvta_generic_to_shared(dst)),
-      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"((uint32_t)__cvta_generic_to_shared(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-constexpr int kWaitLimit = 1 << 22;  // bounded wait on a tensor copy
-
-__device__ __forceinline__ unsigned long long rank_of_zero(const uint16_t* codes, unsigned long long i, uint32_t chunk,
-                                                           uint32_t nsub, const unsigned long long* zunit) {
-  const unsigned long long c = i / chunk;
-  const unsigned long long r = i - c * chunk;
-  const unsigned long long b = r >> 9;
-  unsigned long long rank = zunit[c * nsub + b];
-  for (unsigned long long q = c * chunk + (b << 9); q < i; ++q) rank += codes[q] == 0;
-  return rank;
-}
 
 __device__ __forceinline__ int floor_to(int v, int a) {  // a power of two
   return v & ~(a - 1);
@@ -916,6 +846,11 @@ constexpr unsigned long long kCoarseMax = 4096;  // points of the largest coarse
 
 bool level_path_ok(const Plan& pl) { return pl.n[0] == 1; }  // rank <= 3
 
+// k_fine.cu
+bool fine_eligible(const Plan& pl, int k, bool comp, const void* x, const void* Rc, const void* Rout, bool to_field);
+template <typename T, bool COMP>
+int launch_fine(const Plan& pl, int k, const LevelArgs<T>& a, bool to_field, cudaStream_t s);
+
 int coarse_grid(const Plan& pl) {
   int kc = pl.L;
   while (kc > 0 && pl.gsize[kc - 1] <= kCoarseMax) --kc;
@@ -947,7 +882,7 @@ static void tile_shape(const Plan& pl, int k, const int* pos, int* B) {
   }
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static bool tried = false;
   if (!tried) {
@@ -983,6 +918,8 @@ static size_t up128(size_t x) { return (x + 127) & ~(size_t)127; }
 
 template <typename T, bool COMP>
 static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t s) {
+  if ((COMP || a.codes_padded) && fine_eligible(pl, k, COMP, a.x, a.Rc, a.Rout, !COMP && k == 0))
+    return launch_fine<T, COMP>(pl, k, a, !COMP && k == 0, s);
   LevelDesc d;
   memset(&d, 0, sizeof(d));
   d.k = k;
@@ -1156,7 +1093,7 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
 template <typename T>
 static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred, unsigned long long n_unpred,
                          const unsigned long long* zunit, void* const* R, T* out, DevState* st,
-                         T ebT, cudaStream_t s) {
+                         T ebT, bool codes_padded, cudaStream_t s) {
   const int kc = coarse_grid(pl);
   LevelArgs<T> a{};
   a.codes = const_cast<uint16_t*>(codes);
@@ -1166,6 +1103,7 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
   a.n_unpred = n_unpred;
   a.zunit = zunit;
   a.ebT = ebT;
+  a.codes_padded = codes_padded;
   a.Rout = kc == 0 ? out : (T*)R[kc];
   int rc = run_coarse<T, false>(pl, kc, a, s);
   if (rc) return rc;
@@ -1186,16 +1124,18 @@ int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, voi
 
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
                          const unsigned long long* zunit, void* const* R, void* d_out,
-                         DevState* st, unsigned long long ebT_bits, cudaStream_t s) {
+                         DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s) {
   if (pl.dtype == SZ3G_F32) {
     float e;
     uint32_t b = (uint32_t)ebT_bits;
     memcpy(&e, &b, 4);
-    return recover_fused<float>(pl, codes, (const float*)unpred, n_unpred, zunit, R, (float*)d_out, st, e, s);
+    return recover_fused<float>(pl, codes, (const float*)unpred, n_unpred, zunit, R, (float*)d_out, st, e,
+                                codes_padded, s);
   }
   double e;
   memcpy(&e, &ebT_bits, 8);
-  return recover_fused<double>(pl, codes, (const double*)unpred, n_unpred, zunit, R, (double*)d_out, st, e, s);
+  return recover_fused<double>(pl, codes, (const double*)unpred, n_unpred, zunit, R, (double*)d_out, st, e,
+                               codes_padded, s);
 }
 
 }  // namespace sz3g
