@@ -99,7 +99,7 @@ struct Plan {
 enum KernelId {
   kKRange, kKEb, kKAnchor, kKLift, kKPassQuantize, kKPassRecover, kKCodebook, kKEncode, kKFinalize,
   kKDecodeTables, kKDecode, kKScan, kKZeroCount, kKPackTable, kKLevelQuantize, kKLevelRecover,
-  kKCoarseQuantize, kKCoarseRecover, kKernelCount
+  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKernelCount
 };
 
 // Counts a launch and, while profiling is on, brackets it with CUDA events.
@@ -226,7 +226,7 @@ size_t range_scratch_bytes(const Plan& pl);
 int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratch, size_t scratch_bytes,
                     int eb_mode, double eb, cudaStream_t s);
 int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R,
-                           uint32_t* hist, DevState* st, cudaStream_t s);
+                           uint32_t* hist, DevState* st, void* X1, cudaStream_t s);
 int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred,
                           unsigned long long n_unpred, const unsigned long long* zunit,
                           void* const* R, void* d_out, DevState* st, unsigned long long ebT_bits,
@@ -235,7 +235,17 @@ int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unp
 // k_level.cu (fields of rank <= 3)
 bool level_path_ok(const Plan& pl);
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                          DevState* st, cudaStream_t s);
+                          DevState* st, void* X1, cudaStream_t s);
+// Decimated copy of the field over G_1 (rows pitched to 16 bytes), the input
+// of the coarser levels; x1_bytes is 0 when the level path does not use it.
+inline unsigned long long x1_pitch(const Plan& pl) {
+  const unsigned long long al = 16 / pl.esz;
+  return (pl.gm[1][3] + al - 1) / al * al;
+}
+inline unsigned long long x1_bytes(const Plan& pl) {
+  if (pl.n[0] != 1 || pl.L < 1) return 0;
+  return x1_pitch(pl) * pl.gm[1][2] * pl.gm[1][1] * pl.esz;
+}
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
                          const unsigned long long* zunit, void* const* R, void* d_out,
                          DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s);

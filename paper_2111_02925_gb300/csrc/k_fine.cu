@@ -502,12 +502,15 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
 // ---------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
+// 3-D tensor map over rows of m2 elements (row stride s1, plane stride s0
+// elements) with a box of b0 x b1 x b2 elements.
 template <typename T>
-static bool fine_map(CUtensorMap* map, const T* base, int m0, int m1, int m2, int b0, int b1, int b2) {
+static bool fine_map(CUtensorMap* map, const T* base, int m0, int m1, int m2, unsigned long long s0,
+                     unsigned long long s1, int b0, int b1, int b2) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)m2, (cuuint64_t)m1, (cuuint64_t)m0};
-  const cuuint64_t strides[2] = {(cuuint64_t)m2 * sizeof(T), (cuuint64_t)m1 * m2 * sizeof(T)};
+  const cuuint64_t strides[2] = {(cuuint64_t)s1 * sizeof(T), (cuuint64_t)s0 * sizeof(T)};
   const cuuint32_t box[3] = {(cuuint32_t)b2, (cuuint32_t)b1, (cuuint32_t)b0};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
@@ -518,7 +521,8 @@ static bool fine_map(CUtensorMap* map, const T* base, int m0, int m1, int m2, in
 // Whether the register-blocked kernel takes level k (the passes of G_k in
 // plan order): 3-D grids refined in axis order (0, 1, 2) or 2-D grids in
 // (1, 2), with 16-byte aligned rows for the tensor copies.
-bool fine_eligible(const Plan& pl, int k, bool comp, const void* x, const void* Rc, const void* Rout, bool to_field) {
+bool fine_eligible(const Plan& pl, int k, bool comp, const void* x, const unsigned long long* xs, const void* Rc,
+                   const void* Rout, bool to_field) {
   if (pl.ndim < 2 || pl.n[0] != 1) return false;
   int ax[4], P = 0;
   for (int i = 0; i < pl.n_pass; ++i)
@@ -534,8 +538,9 @@ bool fine_eligible(const Plan& pl, int k, bool comp, const void* x, const void* 
   const unsigned long long* mc = pl.gm[k + 1];
   auto rows16 = [&](unsigned long long e2) { return (e2 * esz) % 16 == 0; };
   if (!rows16(mc[3]) || ((uintptr_t)Rc % 16) != 0) return false;
-  if (comp && (k != 0 || !rows16(m[3]) || ((uintptr_t)x % 16) != 0)) return false;
-  if (!comp && Rout && (!rows16(to_field ? pl.n[3] : m[3]) || ((uintptr_t)Rout % 16) != 0)) return false;
+  // compress reads x by tensor copies: contiguous rows, 16-byte strides
+  if (comp && (xs[2] != 1 || !rows16(xs[1]) || !rows16(xs[0]) || ((uintptr_t)x % 16) != 0)) return false;
+  if (Rout && (!rows16(to_field ? pl.n[3] : m[3]) || ((uintptr_t)Rout % 16) != 0)) return false;
   return m[2] >= 2 && m[3] >= 2 && pl.gsize[k] <= 0xffffffffull;
 }
 
@@ -577,10 +582,10 @@ static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_f
   CUtensorMap tmx, tmc;
   memset(&tmx, 0, sizeof(tmx));
   memset(&tmc, 0, sizeof(tmc));
-  bool ok = fine_map<T>(&tmc, a.Rc, (int)mc[1], (int)mc[2], (int)mc[3], S::kCI, S::kCJ, S::kCK);
+  bool ok = fine_map<T>(&tmc, a.Rc, (int)mc[1], (int)mc[2], (int)mc[3], mc[3] * mc[2], mc[3], S::kCI, S::kCJ, S::kCK);
   d.tensor_bytes = (uint32_t)(S::kCI * S::kCJ * S::kCK * sizeof(T));
   if (COMP) {
-    ok = ok && fine_map<T>(&tmx, a.x, d.m0, d.m1, d.m2, S::kT0, S::kXJ, S::kXK);
+    ok = ok && fine_map<T>(&tmx, a.x, d.m0, d.m1, d.m2, a.xs[0], a.xs[1], S::kT0, S::kXJ, S::kXK);
     d.tensor_bytes += (uint32_t)(S::kT0 * S::kXJ * S::kXK * sizeof(T));
   }
   if (!ok) return SZ3G_E_CUDA;

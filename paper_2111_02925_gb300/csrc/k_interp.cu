@@ -408,8 +408,8 @@ static int quantize_levels_t(const Plan& pl, const T* x, uint16_t* codes, void* 
 }
 
 int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                           DevState* st, cudaStream_t s) {
-  if (level_path_ok(pl)) return launch_quantize_fused(pl, d_in, codes, R, hist, st, s);
+                           DevState* st, void* X1, cudaStream_t s) {
+  if (level_path_ok(pl)) return launch_quantize_fused(pl, d_in, codes, R, hist, st, X1, s);
   if (pl.dtype == SZ3G_F32) return quantize_levels_t<float>(pl, (const float*)d_in, codes, R, hist, st, s);
   return quantize_levels_t<double>(pl, (const double*)d_in, codes, R, hist, st, s);
 }

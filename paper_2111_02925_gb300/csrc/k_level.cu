@@ -847,7 +847,8 @@ constexpr unsigned long long kCoarseMax = 4096;  // points of the largest coarse
 bool level_path_ok(const Plan& pl) { return pl.n[0] == 1; }  // rank <= 3
 
 // k_fine.cu
-bool fine_eligible(const Plan& pl, int k, bool comp, const void* x, const void* Rc, const void* Rout, bool to_field);
+bool fine_eligible(const Plan& pl, int k, bool comp, const void* x, const unsigned long long* xs, const void* Rc,
+                   const void* Rout, bool to_field);
 template <typename T, bool COMP>
 int launch_fine(const Plan& pl, int k, const LevelArgs<T>& a, bool to_field, cudaStream_t s);
 
@@ -918,7 +919,7 @@ static size_t up128(size_t x) { return (x + 127) & ~(size_t)127; }
 
 template <typename T, bool COMP>
 static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t s) {
-  if ((COMP || a.codes_padded) && fine_eligible(pl, k, COMP, a.x, a.Rc, a.Rout, !COMP && k == 0))
+  if ((COMP || a.codes_padded) && fine_eligible(pl, k, COMP, a.x, a.xs, a.Rc, a.Rout, !COMP && k == 0))
     return launch_fine<T, COMP>(pl, k, a, !COMP && k == 0, s);
   LevelDesc d;
   memset(&d, 0, sizeof(d));
@@ -967,7 +968,7 @@ static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t 
       d.vlo[q] = refined ? 2 : 0;
       d.vext[q] = d.B[q] + (refined ? 5 : 0);
     }
-    d.xs[q] = (uint32_t)(pl.fstride[q + 1] << k);
+    d.xs[q] = (uint32_t)a.xs[q];
   }
   d.rcs[2] = 1;
   d.rcs[1] = (uint32_t)mc2;
@@ -1068,12 +1069,48 @@ static int run_coarse(const Plan& pl, int kc, const LevelArgs<T>& a, cudaStream_
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
+// X1[i][j][k] = x[2i][2j][2k] over G_1, rows pitched to 16 bytes: the input of
+// every level but the finest, read contiguously (and by tensor copies)
+// instead of at stride 2^k from the field.  One warp per output row.
+template <typename T>
+__global__ void decimate_kernel(const T* __restrict__ x, unsigned long long s0, unsigned long long s1, int n2,
+                                T* __restrict__ X1, int m0, int m1, int m2, unsigned long long p0,
+                                unsigned long long p1) {
+  const unsigned long long row = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= (unsigned long long)m0 * m1) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long i = row / (unsigned)m1, j = row % (unsigned)m1;
+  const T* src = x + 2 * i * s0 + 2 * j * s1;
+  T* dst = X1 + i * p0 + j * p1;
+  for (int c = lane; c < m2; c += 32) dst[c] = __ldcs(src + 2 * c);
+  (void)n2;
+}
+
+int launch_decimate(const Plan& pl, const void* x, void* X1, cudaStream_t s) {
+  const unsigned long long* m = pl.gm[1];
+  const unsigned long long p1 = x1_pitch(pl), p0 = p1 * m[2];
+  const unsigned long long rows = m[1] * m[2];
+  const unsigned blocks = (unsigned)((rows + 7) / 8);
+  if (pl.dtype == SZ3G_F32)
+    SZ3G_LAUNCH(kKDecimate, s,
+                decimate_kernel<float><<<blocks, 256, 0, s>>>((const float*)x, pl.fstride[1], pl.fstride[2],
+                                                              (int)pl.n[3], (float*)X1, (int)m[1], (int)m[2],
+                                                              (int)m[3], p0, p1));
+  else
+    SZ3G_LAUNCH(kKDecimate, s,
+                decimate_kernel<double><<<blocks, 256, 0, s>>>((const double*)x, pl.fstride[1], pl.fstride[2],
+                                                               (int)pl.n[3], (double*)X1, (int)m[1], (int)m[2],
+                                                               (int)m[3], p0, p1));
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
 template <typename T>
 static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* const* R, uint32_t* hist, DevState* st,
-                          cudaStream_t s) {
+                          void* X1, cudaStream_t s) {
   const int kc = coarse_grid(pl);
   LevelArgs<T> a{};
   a.x = x;
+  for (int q = 0; q < 3; ++q) a.xs[q] = pl.fstride[q + 1];
   a.codes = codes;
   a.hist = hist;
   a.st = st;
@@ -1081,9 +1118,25 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
   a.Rout = kc == 0 ? nullptr : (T*)R[kc];  // the finest grid's reconstruction is not kept
   int rc = run_coarse<T, true>(pl, kc, a, s);
   if (rc) return rc;
+  // levels on G_1 and coarser read the decimated copy
+  const bool dec = X1 && kc >= 2;
+  if (dec) {
+    rc = launch_decimate(pl, x, X1, s);
+    if (rc) return rc;
+  }
+  const unsigned long long p1 = x1_pitch(pl), p0 = p1 * pl.gm[1][2];
   for (int k = kc - 1; k >= 0; --k) {
     a.Rc = (const T*)R[k + 1];
     a.Rout = k == 0 ? nullptr : (T*)R[k];
+    if (dec && k >= 1) {
+      a.x = (const T*)X1;
+      a.xs[0] = p0 << (k - 1);
+      a.xs[1] = p1 << (k - 1);
+      a.xs[2] = 1ull << (k - 1);
+    } else {
+      a.x = x;
+      for (int q = 0; q < 3; ++q) a.xs[q] = pl.fstride[q + 1] << k;
+    }
     rc = run_level<T, true>(pl, k, a, s);
     if (rc) return rc;
   }
@@ -1117,9 +1170,9 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
 }
 
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                          DevState* st, cudaStream_t s) {
-  if (pl.dtype == SZ3G_F32) return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, s);
-  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, s);
+                          DevState* st, void* X1, cudaStream_t s) {
+  if (pl.dtype == SZ3G_F32) return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, X1, s);
+  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, X1, s);
 }
 
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,

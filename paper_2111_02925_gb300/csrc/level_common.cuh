@@ -14,7 +14,8 @@ constexpr int kHistWin = 2048;  // shared-memory histogram window around the rad
 
 template <typename T>
 struct LevelArgs {
-  const T* x;          // compress: input field
+  const T* x;          // compress: input of the level (the field, or its decimated copy)
+  unsigned long long xs[3];  // compress: element strides in x of one G_k step along axes 0..2
   const T* Rc;         // R_{k+1}
   T* Rout;             // R_k, or the field on decompress at k = 0
   uint16_t* codes;
