@@ -25,6 +25,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 #include "level_common.cuh"
 
@@ -127,8 +129,7 @@ __device__ __forceinline__ void st4(T* p, T a, T b, T c, T d) {  // 16-byte alig
 
 // Per-thread results of the tile passes, flushed once per CTA.
 struct FineAcc {
-  unsigned int nz;
-  bool bad;
+  bool bad;  // recover: a code outside [0, 2r) or an unpredictable value past the list
 };
 
 // Quantize (compress) or recover (decompress) one point whose prediction is
@@ -140,10 +141,10 @@ __device__ __forceinline__ T fine_point(const LevelArgs<T>& a, const FineDesc& d
     T r;
     const uint32_t code = quantize_point<T>(x, p, ebT, ebr, a.radius, r);
     if (own) {
+      // (unpredictable values -- also every non-finite input -- are counted by
+      // histogram bin 0 and checked for finiteness where the encoder gathers
+      // them)
       a.codes[ci] = (uint16_t)code;
-      // unpredictable: also where a non-finite input ends up
-      acc.nz += code == 0;
-      acc.bad |= (code == 0) & !isfinite(x);
       const uint32_t bn = code - (uint32_t)hlo;
       if (bn < (uint32_t)kHistWin) atomicAdd(&hwin[bn], 1u);
       else atomicAdd(&a.hist[code], 1u);
@@ -188,7 +189,6 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
   uint16_t* Ks = reinterpret_cast<uint16_t*>(sm + L::kOffK);  // [2][KB] (recover)
   uint32_t* hwin = reinterpret_cast<uint32_t*>(sm + L::kOffH);  // [kHistWin] (compress)
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::kOffBar);  // [2]
-  __shared__ unsigned long long s_nz;
   __shared__ int s_bad, s_timeout;
   __shared__ uint32_t s_bytes[2];
   const int tid = threadIdx.x;
@@ -202,7 +202,6 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
   if (COMP)
     for (int i = tid; i < kHistWin; i += kFineThreads) hwin[i] = 0;
   if (tid == 0) {
-    s_nz = 0;
     s_bad = 0;
     s_timeout = 0;
     s_bytes[0] = s_bytes[1] = 0;
@@ -211,7 +210,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  FineAcc acc{0u, false};
+  FineAcc acc{false};
 
   auto tile_origin = [&](uint32_t tile, int& A0, int& A1, int& A2) {
     const uint32_t t2 = tile % (uint32_t)d.nt2, r = tile / (uint32_t)d.nt2;
@@ -314,166 +313,174 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
     const T* X = Xs + b * XB;
     const T* C = Cs + b * CB;
     const uint16_t* K = Ks + b * KB;
+    // tiles away from every face: all points in the grid, every neighbour of
+    // every pass present (compile-time predictor, no per-point checks)
     const bool edgek = !(A2 >= 4 && A2 + S::kW + 4 <= m2);
-
-    // ---- coarse points into E, and pass 0 (odd i, even j) ------------------
-    for (int t = tid; t < S::kCopyTasks + S::kP0Tasks; t += kFineThreads) {
-      if (t < S::kCopyTasks) {
-        const int pr = t % S::kPairs, row = t / S::kPairs;
-        const int e = row / S::kCJ, cj = row % S::kCJ;
-        T v[2];
-        ld2(C + ((e + (S::kHas0 ? 1 : 0)) * S::kCJ + cj) * S::kCK + 2 * pr + 2, v);
-        st2(E + ((2 * e) * S::kXJ + 2 * cj) * S::kEK + 2 * pr, v[0], v[1]);
-        continue;
+    const bool in0 = !S::kHas0 || (A0 >= 4 && A0 + S::kT0 + 4 <= m0);
+    const bool in1 = A1 >= 4 && A1 + S::kT1 + 4 <= m1;
+    auto passes = [&](auto interior_tag) {
+      constexpr bool IN = decltype(interior_tag)::value;
+      // ---- coarse points into E, and pass 0 (odd i, even j) ----------------
+      for (int t = tid; t < S::kCopyTasks + S::kP0Tasks; t += kFineThreads) {
+        if (t < S::kCopyTasks) {
+          const int pr = t % S::kPairs, row = t / S::kPairs;
+          const int e = row / S::kCJ, cj = row % S::kCJ;
+          T v[2];
+          ld2(C + ((e + (S::kHas0 ? 1 : 0)) * S::kCJ + cj) * S::kCK + 2 * pr + 2, v);
+          st2(E + ((2 * e) * S::kXJ + 2 * cj) * S::kEK + 2 * pr, v[0], v[1]);
+          continue;
+        }
+        if constexpr (S::kHas0) {
+          const int u = t - S::kCopyTasks;
+          const int pr = u % S::kPairs, row = u / S::kPairs;
+          const int eo = row / S::kCJ, cj = row % S::kCJ;
+          const int i = A0 + 2 * eo + 1, j = A1 - 2 + 2 * cj;
+          if (!IN && (i >= m0 || j < 0 || j >= m1)) continue;
+          const int ke = 2 * pr, k = A2 - 4 + 2 * ke;
+          const bool hb = IN || i + 1 < m0, hc = IN || i >= 3, hd = IN || i + 3 < m0;
+          T va[2], vb[2], vc[2], vd[2];
+          const T* Cr = C + cj * S::kCK + ke + 2;
+          ld2(Cr + (eo + 1) * S::kCJ * S::kCK, va);
+          ld2(Cr + (eo + 2) * S::kCJ * S::kCK, vb);
+          ld2(Cr + (eo + 0) * S::kCJ * S::kCK, vc);
+          ld2(Cr + (eo + 3) * S::kCJ * S::kCK, vd);
+          T xv[4] = {T(0), T(0), T(0), T(0)};
+          if (COMP) ld4(X + ((2 * eo + 1) * S::kXJ + 2 * cj) * S::kXK + 2 * ke, xv);
+          const int c0 = (int)d.off[0] + ((i - 1) / 2 * (int)d.E1[0] + j / 2) * (int)d.E2[0] + (A2 / 2 - 2);
+          const bool ownj = j >= A1 && j < A1 + S::kT1;
+          const uint16_t* kr = nullptr;
+          if (!COMP) {
+            long long al;
+            int o;
+            code_row(c0, &al, &o);
+            kr = K + S::kR2 * S::kL2 + (S::kR1 + row) * S::kL01 + o + ke;
+          }
+          T r[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int kq = k + 2 * q;
+            r[q] = T(0);
+            if (!IN && (kq < 0 || kq >= m2)) continue;
+            const T p = interp_predict<T>(va[q], vb[q], vc[q], vd[q], hb, hc, hd, INTERP);
+            const bool own = ownj && ke + q >= 2 && ke + q < 2 + S::kW / 2;
+            r[q] = fine_point<T, COMP>(a, d, hwin, hlo, xv[2 * q], p, ebT, ebr, own, (uint32_t)(c0 + ke + q),
+                                       COMP ? 0u : (uint32_t)kr[q], acc);
+          }
+          st2(E + ((2 * eo + 1) * S::kXJ + 2 * cj) * S::kEK + ke, r[0], r[1]);
+        }
       }
-      if constexpr (S::kHas0) {
-        const int u = t - S::kCopyTasks;
-        const int pr = u % S::kPairs, row = u / S::kPairs;
-        const int eo = row / S::kCJ, cj = row % S::kCJ;
-        const int i = A0 + 2 * eo + 1, j = A1 - 2 + 2 * cj;
-        if (i >= m0 || j < 0 || j >= m1) continue;
+      __syncthreads();
+
+      // ---- pass 1 (any i, odd j) --------------------------------------------
+      for (int t = tid; t < S::kP1Tasks; t += kFineThreads) {
+        const int pr = t % S::kPairs, row = t / S::kPairs;
+        const int i4 = row / (S::kT1 / 2), jo = row % (S::kT1 / 2);
+        const int i = A0 + i4, j = A1 + 2 * jo + 1;
+        if (!IN && (i >= m0 || j >= m1)) continue;
         const int ke = 2 * pr, k = A2 - 4 + 2 * ke;
-        const bool hb = i + 1 < m0, hc = i >= 3, hd = i + 3 < m0;
+        const int j21 = 2 * jo + 3;
+        const bool hb = IN || j + 1 < m1, hc = IN || j >= 3, hd = IN || j + 3 < m1;
+        const T* Er = E + (i4 * S::kXJ + j21) * S::kEK + ke;
         T va[2], vb[2], vc[2], vd[2];
-        ld2(C + ((eo + 1) * S::kCJ + cj) * S::kCK + ke + 2, va);
-        ld2(C + ((eo + 2) * S::kCJ + cj) * S::kCK + ke + 2, vb);
-        ld2(C + ((eo + 0) * S::kCJ + cj) * S::kCK + ke + 2, vc);
-        ld2(C + ((eo + 3) * S::kCJ + cj) * S::kCK + ke + 2, vd);
+        ld2(Er - S::kEK, va);
+        ld2(Er + S::kEK, vb);
+        ld2(Er - 3 * S::kEK, vc);
+        ld2(Er + 3 * S::kEK, vd);
         T xv[4] = {T(0), T(0), T(0), T(0)};
-        if (COMP) ld4(X + ((2 * eo + 1) * S::kXJ + 2 * cj) * S::kXK + 2 * ke, xv);
-        const long long c0 = (long long)d.off[0] + ((long long)(i - 1) / 2 * d.E1[0] + j / 2) * d.E2[0] + (A2 / 2 - 2);
-        const bool ownj = j >= A1 && j < A1 + S::kT1;
-        int o = 0;
+        if (COMP) ld4(X + (i4 * S::kXJ + j21) * S::kXK + 2 * ke, xv);
+        const int c0 = (int)d.off[1] + (i * (int)d.E1[1] + (j - 1) / 2) * (int)d.E2[1] + (A2 / 2 - 2);
         const uint16_t* kr = nullptr;
         if (!COMP) {
           long long al;
+          int o;
           code_row(c0, &al, &o);
-          kr = K + S::kR2 * S::kL2 + (S::kR1 + row) * S::kL01 + o;
+          kr = K + S::kR2 * S::kL2 + row * S::kL01 + o + ke;
         }
         T r[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int kq = k + 2 * q;
           r[q] = T(0);
-          if (kq < 0 || kq >= m2) continue;
+          if (!IN && (kq < 0 || kq >= m2)) continue;
           const T p = interp_predict<T>(va[q], vb[q], vc[q], vd[q], hb, hc, hd, INTERP);
-          const bool own = ownj && ke + q >= 2 && ke + q < 2 + S::kW / 2;
+          const bool own = ke + q >= 2 && ke + q < 2 + S::kW / 2;
           r[q] = fine_point<T, COMP>(a, d, hwin, hlo, xv[2 * q], p, ebT, ebr, own, (uint32_t)(c0 + ke + q),
-                                     COMP ? 0u : (uint32_t)kr[ke + q], acc);
+                                     COMP ? 0u : (uint32_t)kr[q], acc);
         }
-        st2(E + ((2 * eo + 1) * S::kXJ + 2 * cj) * S::kEK + ke, r[0], r[1]);
+        st2(E + (i4 * S::kXJ + j21) * S::kEK + ke, r[0], r[1]);
       }
-    }
-    __syncthreads();
+      __syncthreads();
 
-    // ---- pass 1 (any i, odd j) ----------------------------------------------
-    for (int t = tid; t < S::kP1Tasks; t += kFineThreads) {
-      const int pr = t % S::kPairs, row = t / S::kPairs;
-      const int i4 = row / (S::kT1 / 2), jo = row % (S::kT1 / 2);
-      const int i = A0 + i4, j = A1 + 2 * jo + 1;
-      if (i >= m0 || j >= m1) continue;
-      const int ke = 2 * pr, k = A2 - 4 + 2 * ke;
-      const int j21 = 2 * jo + 3;
-      const bool hb = j + 1 < m1, hc = j >= 3, hd = j + 3 < m1;
-      const T* Er = E + (i4 * S::kXJ + j21) * S::kEK + ke;
-      T va[2], vb[2], vc[2], vd[2];
-      ld2(Er - S::kEK, va);
-      ld2(Er + S::kEK, vb);
-      ld2(Er - 3 * S::kEK, vc);
-      ld2(Er + 3 * S::kEK, vd);
-      T xv[4] = {T(0), T(0), T(0), T(0)};
-      if (COMP) ld4(X + (i4 * S::kXJ + j21) * S::kXK + 2 * ke, xv);
-      const long long c0 = (long long)d.off[1] + ((long long)i * d.E1[1] + (j - 1) / 2) * d.E2[1] + (A2 / 2 - 2);
-      int o = 0;
-      const uint16_t* kr = nullptr;
-      if (!COMP) {
-        long long al;
-        code_row(c0, &al, &o);
-        kr = K + S::kR2 * S::kL2 + row * S::kL01 + o;
-      }
-      T r[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int kq = k + 2 * q;
-        r[q] = T(0);
-        if (kq < 0 || kq >= m2) continue;
-        const T p = interp_predict<T>(va[q], vb[q], vc[q], vd[q], hb, hc, hd, INTERP);
-        const bool own = ke + q >= 2 && ke + q < 2 + S::kW / 2;
-        r[q] = fine_point<T, COMP>(a, d, hwin, hlo, xv[2 * q], p, ebT, ebr, own, (uint32_t)(c0 + ke + q),
-                                   COMP ? 0u : (uint32_t)kr[ke + q], acc);
-      }
-      st2(E + (i4 * S::kXJ + j21) * S::kEK + ke, r[0], r[1]);
-    }
-    __syncthreads();
-
-    // ---- pass 2 (any i, any j, odd k): runs of four ------------------------
-    for (int t = tid; t < S::kP2Tasks; t += kFineThreads) {
-      const int q4 = t & 7, row = t >> 3;
-      const int i4 = row / S::kT1, j16 = row % S::kT1;
-      const int i = A0 + i4, j = A1 + j16;
-      if (i >= m0 || j >= m1) continue;
-      const int j21 = j16 + 2;
-      const T* Er = E + (i4 * S::kXJ + j21) * S::kEK + 4 * q4;
-      T e[8];
-      ld4(Er, e);
-      ld4(Er + 4, e + 4);
-      T xo[4] = {T(0), T(0), T(0), T(0)};
-      if (COMP) {
-        T xv[8];
-        const T* xr = X + (i4 * S::kXJ + j21) * S::kXK + 8 * q4 + 4;
-        ld4(xr, xv);
-        ld4(xr + 4, xv + 4);
-        xo[0] = xv[1], xo[1] = xv[3], xo[2] = xv[5], xo[3] = xv[7];
-      }
-      const long long c0 = (long long)d.off[2] + ((long long)i * d.E1[2] + j) * d.E2[2] + A2 / 2;
-      const uint32_t ci = (uint32_t)(c0 + 4 * q4);
-      const uint16_t* kr = nullptr;
-      if (!COMP) {
-        long long al;
-        int o;
-        code_row(c0, &al, &o);
-        kr = K + row * S::kL2 + o + 4 * q4;
-      }
-      const int k0 = A2 + 8 * q4;  // first (even) k of the run's eight points
-      T r[4];
-      if (!edgek) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const T p = interp_predict<T>(e[u + 2], e[u + 3], e[u + 1], e[u + 4], true, true, true, INTERP);
-          r[u] = fine_point<T, COMP>(a, d, hwin, hlo, xo[u], p, ebT, ebr, true, ci + u, COMP ? 0u : (uint32_t)kr[u],
-                                     acc);
+      // ---- pass 2 (any i, any j, odd k): runs of four ------------------------
+      for (int t = tid; t < S::kP2Tasks; t += kFineThreads) {
+        const int q4 = t & 7, row = t >> 3;
+        const int i4 = row / S::kT1, j16 = row % S::kT1;
+        const int i = A0 + i4, j = A1 + j16;
+        if (!IN && (i >= m0 || j >= m1)) continue;
+        const int j21 = j16 + 2;
+        const T* Er = E + (i4 * S::kXJ + j21) * S::kEK + 4 * q4;
+        T e[8];
+        ld4(Er, e);
+        ld4(Er + 4, e + 4);
+        T xo[4] = {T(0), T(0), T(0), T(0)};
+        if (COMP) {
+          T xv[8];
+          const T* xr = X + (i4 * S::kXJ + j21) * S::kXK + 8 * q4 + 4;
+          ld4(xr, xv);
+          ld4(xr + 4, xv + 4);
+          xo[0] = xv[1], xo[1] = xv[3], xo[2] = xv[5], xo[3] = xv[7];
         }
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int kk = k0 + 2 * u + 1;
-          r[u] = T(0);
-          if (kk >= m2) continue;
-          const bool hb = kk + 1 < m2, hc = kk >= 3, hd = kk + 3 < m2;
-          const T p = interp_predict<T>(e[u + 2], hb ? e[u + 3] : T(0), hc ? e[u + 1] : T(0), hd ? e[u + 4] : T(0),
-                                        hb, hc, hd, INTERP);
-          r[u] = fine_point<T, COMP>(a, d, hwin, hlo, xo[u], p, ebT, ebr, true, ci + u, COMP ? 0u : (uint32_t)kr[u],
-                                     acc);
+        const int c0 = (int)d.off[2] + (i * (int)d.E1[2] + j) * (int)d.E2[2] + A2 / 2;
+        const uint32_t ci = (uint32_t)(c0 + 4 * q4);
+        const uint16_t* kr = nullptr;
+        if (!COMP) {
+          long long al;
+          int o;
+          code_row(c0, &al, &o);
+          kr = K + row * S::kL2 + o + 4 * q4;
         }
-      }
-      if (d.write_out) {
-        T* dst = a.Rout + ((unsigned long long)i * d.rs0 + (unsigned long long)j * d.rs1 + (unsigned long long)k0);
-        if (k0 + 8 <= m2) {
-          st4(dst, e[2], r[0], e[3], r[1]);
-          st4(dst + 4, e[4], r[2], e[5], r[3]);
+        const int k0 = A2 + 8 * q4;  // first (even) k of the run's eight points
+        T r[4];
+        if (IN || !edgek) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const T p = interp_predict<T>(e[u + 2], e[u + 3], e[u + 1], e[u + 4], true, true, true, INTERP);
+            r[u] = fine_point<T, COMP>(a, d, hwin, hlo, xo[u], p, ebT, ebr, true, ci + u,
+                                       COMP ? 0u : (uint32_t)kr[u], acc);
+          }
         } else {
-          const T v8[8] = {e[2], r[0], e[3], r[1], e[4], r[2], e[5], r[3]};
 #pragma unroll
-          for (int s = 0; s < 8; ++s)
-            if (k0 + s < m2) dst[s] = v8[s];
+          for (int u = 0; u < 4; ++u) {
+            const int kk = k0 + 2 * u + 1;
+            r[u] = T(0);
+            if (kk >= m2) continue;
+            const bool hb = kk + 1 < m2, hc = kk >= 3, hd = kk + 3 < m2;
+            const T p = interp_predict<T>(e[u + 2], hb ? e[u + 3] : T(0), hc ? e[u + 1] : T(0),
+                                          hd ? e[u + 4] : T(0), hb, hc, hd, INTERP);
+            r[u] = fine_point<T, COMP>(a, d, hwin, hlo, xo[u], p, ebT, ebr, true, ci + u,
+                                       COMP ? 0u : (uint32_t)kr[u], acc);
+          }
+        }
+        if (d.write_out) {
+          T* dst = a.Rout + ((unsigned long long)i * d.rs0 + (unsigned long long)j * d.rs1 + (unsigned long long)k0);
+          if (IN || k0 + 8 <= m2) {
+            st4(dst, e[2], r[0], e[3], r[1]);
+            st4(dst + 4, e[4], r[2], e[5], r[3]);
+          } else {
+            const T v8[8] = {e[2], r[0], e[3], r[1], e[4], r[2], e[5], r[3]};
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8)
+              if (k0 + s8 < m2) dst[s8] = v8[s8];
+          }
         }
       }
-    }
-    __syncthreads();
+      __syncthreads();
+    };
+    if (in0 && in1 && !edgek) passes(std::true_type{});
+    else passes(std::false_type{});
   }
 
   // ---- flush the per-CTA counters
-  if (acc.nz) atomicAdd(&s_nz, (unsigned long long)acc.nz);
   if (acc.bad) s_bad = 1;
   __syncthreads();
   if (s_timeout) {
@@ -488,10 +495,6 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
   if (COMP) {
     for (int i = tid; i < kHistWin; i += kFineThreads)
       if (hwin[i]) atomicAdd(&a.hist[hlo + i], hwin[i]);
-    if (tid == 0) {
-      if (s_nz) atomicAdd(&st->n_unpred, s_nz);
-      if (s_bad) atomicOr(&st->flags, kFlagNonFinite);
-    }
   } else if (tid == 0 && s_bad) {
     atomicOr(&st->flags, kFlagCorrupt);
   }

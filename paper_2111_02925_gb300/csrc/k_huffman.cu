@@ -267,6 +267,7 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
       }
   }
   if (bad) atomicOr(&st->flags, kFlagCorrupt);
+  if (tid == 0) st->n_unpred = hist[0];  // code 0 marks an unpredictable value
   unsigned long long tot;
   uint32_t pos = (uint32_t)block_exclusive_scan((unsigned long long)__popcll(used), s_warp, &tot);
   const int K = (int)tot;
@@ -660,15 +661,23 @@ __global__ void __launch_bounds__(kEncWarps * 32) emit_kernel(const EncArgs a, c
       }
       if (nzl && unp) {
         unsigned long long zr = zpos + zincl - nzl;
+        bool nonfinite = false;
         for (int q = 0; q < 8; ++q) {
           if (c8[q] == 0) {
             const unsigned long long xi = map_code_to_input(map, i0 + t + q);
-            unp[zr++] = reinterpret_cast<const U*>(a.x)[xi];
+            const U v = reinterpret_cast<const U*>(a.x)[xi];
+            unp[zr++] = v;
+            // the quantizer sends every NaN / Inf to the unpredictable list
+            nonfinite |= sizeof(U) == 4 ? ((v & 0x7f800000u) == 0x7f800000u)
+                                        : ((v & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
           }
         }
+        if (nonfinite) atomicOr(&st->flags, kFlagNonFinite);
       }
       zpos += round_zeros;
     }
+    // raw mode: the number of unpredictable values is known at the last chunk
+    if (a.mode == kEncodeRaw && lane == 0 && j == a.n_chunks - 1) st->n_unpred = zpos;
     if (emit) {
       if (carry && lane == 0) pay[wpos] = buf[0];
       __syncwarp();
@@ -1041,7 +1050,7 @@ struct DecArgs {
 // leaving L1 for the per-thread payload streams.
 constexpr int kDecThreads = 512;
 
-__global__ void __launch_bounds__(kDecThreads, 3) decode_kernel(const DecArgs a) {
+__global__ void __launch_bounds__(kDecThreads) decode_kernel(const DecArgs a) {
   if (a.st->flags & kFlagCorrupt) return;  // tables or chunk table rejected
   __shared__ uint32_t lut[1 << kLutBits];
   __shared__ uint32_t fc[SZ3G_LMAX + 2], cnt[SZ3G_LMAX + 2], start[SZ3G_LMAX + 2];
@@ -1071,25 +1080,27 @@ __global__ void __launch_bounds__(kDecThreads, 3) decode_kernel(const DecArgs a)
     return;
   }
   const uint32_t c1 = min(c0 + a.unit, n_chunk);
-  if (bit0 > 32ull * nw) {
+  if (nw == 0 || bit0 > 32ull * nw) {  // a chunk with codes has at least one word
     atomicOr(&a.st->flags, kFlagCorrupt);
     return;
   }
   const uint32_t* wp = a.words + a.woff[j];
-  // bit buffer: `buf` holds nb valid bits at the top; the next two payload
-  // words are loaded ahead (w1 is shifted in at the next refill), so a load
-  // is consumed about 64 bits (some ten codes) after it was issued
-  uint32_t wi = (uint32_t)(bit0 >> 5);  // next word to shift into buf
-  unsigned long long buf = 0;
-  int nb = 0;
-  uint32_t w1 = wi < nw ? __ldg(wp + wi) : 0u, w2 = wi + 1 < nw ? __ldg(wp + wi + 1) : 0u;
-  if (wi < nw) {
-    buf = (unsigned long long)w1 << (32 + (int)(bit0 & 31));
-    nb = 32 - (int)(bit0 & 31);
-    ++wi;
-    w1 = w2;
-    w2 = wi + 1 < nw ? __ldg(wp + wi + 1) : 0u;
-  }
+  // bit buffer: `buf` holds nb valid bits at the top.  The next three payload
+  // words are held in w1..w3; a refill shifts w1 in and loads the word after
+  // w3 into a register that is only read three refills later, so a load is
+  // consumed some fifteen codes after it was issued.  Loads past the chunk
+  // read its last word again: a correct code never depends on bits after its
+  // own (canonical codes are prefix-free), and a decode that runs past the
+  // chunk is caught by the bit count at the end.
+  const uint32_t last = nw ? nw - 1 : 0;
+  uint32_t wi = (uint32_t)(bit0 >> 5);  // index of the word held in w1
+  uint32_t w1 = __ldg(wp + min(wi, last)), w2 = __ldg(wp + min(wi + 1, last)), w3 = __ldg(wp + min(wi + 2, last));
+  unsigned long long buf = (unsigned long long)w1 << (32 + (int)(bit0 & 31));
+  int nb = 32 - (int)(bit0 & 31);
+  ++wi;
+  w1 = w2;
+  w2 = w3;
+  w3 = __ldg(wp + min(wi + 2, last));
   uint32_t zeros = 0;
   uint16_t* out = a.codes + j * a.chunk;
   const uint32_t n_used = a.T->n_used;
@@ -1103,12 +1114,13 @@ __global__ void __launch_bounds__(kDecThreads, 3) decode_kernel(const DecArgs a)
 #pragma unroll
     for (uint32_t q = 0; q < 8; ++q) {
       if (q < m) {
-        if (nb <= 32 && wi < nw) {
+        if (nb <= 32) {
           buf |= (unsigned long long)w1 << (32 - nb);
           nb += 32;
           ++wi;
           w1 = w2;
-          w2 = wi + 1 < nw ? __ldg(wp + wi + 1) : 0u;
+          w2 = w3;
+          w3 = __ldg(wp + min(wi + 2, last));
         }
         const uint32_t e = lut[(uint32_t)(buf >> (64 - kLutBits))];
         uint32_t L = e >> 16, sym = e & 0xffffu;
@@ -1125,7 +1137,7 @@ __global__ void __launch_bounds__(kDecThreads, 3) decode_kernel(const DecArgs a)
             }
           }
         }
-        if (L == 0 || (int)L > nb) {
+        if (L == 0) {
           bad = true;
           break;
         }
