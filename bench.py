@@ -11,6 +11,7 @@ The 512 MiB input is larger than L2 (129 MB), so no flush is needed between
 steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sz3g|reference]
+  python bench.py --workload batch   # the uneven 256-field batch, batched vs one call per field
 
 --impl reference times the serial CPU oracle on the host cores, on a bounded
 sample (a 128^3 corner of the same field) per step.  N > 1 (torchrun) runs
@@ -46,6 +47,8 @@ def parse():
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="field", choices=["field", "batch"])
+    ap.add_argument("--fields", type=int, default=256)
     return ap.parse_args()
 
 
@@ -222,10 +225,123 @@ def cpu_baseline(x):
             "sample": f"{m}^3 corner of the field, compress + decompress, {reps} run(s), one thread"}
 
 
+def grf_gpu(shape, seed, dev):
+    """k^-3 Gaussian random field generated on the GPU (seeded white noise
+    shaped by |k|^-3/2, unit variance); the batch inputs."""
+    import torch
+
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    w = torch.randn(shape, generator=g, device=dev, dtype=torch.float32)
+    f = torch.fft.rfftn(w)
+    ks = [torch.fft.fftfreq(n, device=dev) for n in shape[:-1]] + [torch.fft.rfftfreq(shape[-1], device=dev)]
+    k2 = sum(torch.meshgrid(*[k * k for k in ks], indexing="ij"))
+    k2[(0,) * len(shape)] = 1.0
+    f = f * k2.pow(-0.75)
+    f[(0,) * len(shape)] = 0
+    x = torch.fft.irfftn(f, s=shape)
+    x = (x - x.mean()) / x.std()
+    return x.contiguous()
+
+
+def run_batch(args):
+    """The uneven batch: `--fields` FP32 fields, each axis log-uniform in
+    [32, 256], k^-3 random fields, REL bounds log-uniform in [1e-5, 1e-2],
+    linear / cubic at random.  One step = compress every field, then
+    decompress every stream.  Timed (a) batched: one graph launch per
+    direction, branches and CTA cap picked by the autotuner; (b) one
+    sz3g_compress / sz3g_decompress call per field on one stream."""
+    import torch
+
+    from paper_2111_02925_gb300 import build as B
+    from paper_2111_02925_gb300 import synthetic as S
+    from paper_2111_02925_gb300 import sz3g as G
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local if ws > 1 else 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B.build()
+    G.load()
+    mix = S.batch_shapes(args.fields, 4)
+    xs = [grf_gpu(d, 4000 + i, dev).reshape(-1) for i, (d, _, _) in enumerate(mix)]
+    params = [G.make_params(d, eb, eb_mode=G.REL, interp=it) for d, eb, it in mix]
+    caps = [G.sz3g_compress_bound(p) for p in params]
+    streams = [torch.empty(c, dtype=torch.uint8, device=dev) for c in caps]
+    outs = [torch.empty_like(x) for x in xs]
+    in_bytes = sum(x.numel() * 4 for x in xs)
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    # (b) one call per field (workspace allocated once per field, outside the timing)
+    wsc = [G.workspace(p, False, dev) for p in params]
+    wsd = [G.workspace(p, True, dev) for p in params]
+
+    def per_field():
+        nbs = []
+        for p, x, s, w in zip(params, xs, streams, wsc):
+            rc, nb = G.sz3g_compress(p, x.data_ptr(), s.data_ptr(), s.numel(), w.data_ptr(), w.numel(), sh)
+            assert rc == 0
+            nbs.append(nb)
+        for s, nb, o, w in zip(streams, nbs, outs, wsd):
+            rc = G.sz3g_decompress(s.data_ptr(), nb, o.data_ptr(), o.numel() * 4, w.data_ptr(), w.numel(), sh)
+            assert rc == 0
+        return nbs
+
+    nbs = per_field()
+    # (a) batched
+    bc = G.Batch(params, [x.data_ptr() for x in xs], [s.data_ptr() for s in streams], caps)
+    bd = G.Batch(None, [s.data_ptr() for s in streams], [o.data_ptr() for o in outs], [o.numel() * 4 for o in outs],
+                 in_bytes=nbs, decompress=True)
+    tc = bc.tune(sh)
+    td = bd.tune(sh)
+
+    def batched():
+        bc.run(sh)
+        bd.run(sh)
+
+    def timeit(fn, k):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    k = max(1, min(args.steps, 20))
+    t_batch = timeit(batched, k)
+    rc, nb2, st = bc.results()
+    assert rc == 0 and list(nb2) == list(nbs)
+    rc, _, st = bd.results()
+    assert rc == 0
+    t_single = timeit(per_field, max(1, min(k, 3)))
+    line = {
+        "metric": "batch compress+decompress GB/s (input bytes), uneven fields, 1 GB300",
+        "value": in_bytes / (t_batch * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": k,
+        "warmup": max(args.warmup, 3), "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.fields} FP32 3-D k^-3 random fields, axes log-uniform in [32, 256], "
+                               "REL eb log-uniform in [1e-5, 1e-2], linear/cubic at random (seed 4); "
+                               "step = compress all + decompress all",
+                   "fields": args.fields, "input_bytes": in_bytes, "stream_bytes": int(sum(nbs))},
+        "per_field_calls": {"ms_per_step": t_single, "GB/s": in_bytes / (t_single * 1e-3) / 1e9},
+        "speedup_vs_per_field_calls": t_single / t_batch,
+        "tuned": {"compress": {"branches": tc[0], "cta_cap": tc[1], "graph_nodes": bc.info()[2]},
+                  "decompress": {"branches": td[0], "cta_cap": td[1], "graph_nodes": bd.info()[2]}},
+    }
+    print(json.dumps(line), flush=True)
+    bc.close()
+    bd.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     import numpy as np
     import torch
 

@@ -241,6 +241,63 @@ int sz3g_huffman_decode_static(const uint32_t* d_words, uint64_t n_words, const 
                                uint32_t nsym, uint16_t* d_codes, uint64_t n, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batches (no counterpart in the paper: its compressor handles one field per
+ * call).  Many fields of uneven shape and error bound are compressed, or
+ * decompressed, by one graph launch.  A batch is planned once for a fixed set
+ * of buffers: its fields are spread over parallel branches, each branch runs
+ * its fields' pipelines one after another in a workspace the batch owns, and
+ * every launch of every field is captured once into a CUDA graph that each
+ * run replays.  The results are bit-identical to one sz3g_compress /
+ * sz3g_decompress call per field.
+ * ------------------------------------------------------------------------- */
+typedef struct sz3g_batch sz3g_batch;
+
+/*
+ * Plans a batch of n fields and captures its graph (8 branches, no CTA cap).
+ *   decompress = 0: params[i] and d_in[i] (device, 16-byte aligned) describe
+ *     field i, d_out[i] receives its stream (out_capacity[i] >= its
+ *     sz3g_compress_bound); in_bytes may be NULL.
+ *   decompress = 1: d_in[i] holds a stream of in_bytes[i] bytes, d_out[i]
+ *     (out_capacity[i] bytes) receives the field; params may be NULL.  The
+ *     stream headers are read here (synchronises).
+ * Buffers stay owned by the caller and must outlive the batch; the batch
+ * allocates its workspaces and a result array.  Errors as for the single-
+ * field calls (the first failing field decides).
+ */
+int sz3g_batch_create(int n, int decompress, const sz3g_params* params, const void* const* d_in,
+                      const size_t* in_bytes, void* const* d_out, const size_t* out_capacity,
+                      sz3g_batch** batch);
+
+/* Replays the batch's graph on `stream` (asynchronous). */
+int sz3g_batch_run(sz3g_batch* batch, void* stream);
+
+/*
+ * Synchronises the device and reads the results of the last run: h_bytes[i]
+ * the stream length of field i (compress), h_status[i] its status (either may
+ * be NULL).  Returns the first non-OK status, else SZ3G_OK.
+ */
+int sz3g_batch_results(sz3g_batch* batch, uint64_t* h_bytes, int* h_status);
+
+/*
+ * Rebuilds the graph with `branches` parallel branches (clamped to [1, n])
+ * and at most `cta_cap` CTAs per level-kernel launch (0: a full wave).
+ */
+int sz3g_batch_configure(sz3g_batch* batch, int branches, int cta_cap);
+
+/*
+ * Autotuner: runs the batch (twice after a warm-up) under every combination
+ * of 1..256 branches and CTA caps of none, 1, 1/2 and 1/4 of the SMs, keeps
+ * the fastest and reports it.  Overwrites the batch's outputs; synchronises.
+ */
+int sz3g_batch_tune(sz3g_batch* batch, void* stream, int* h_branches, int* h_cta_cap);
+
+/* Current configuration and the number of nodes of the captured graph. */
+int sz3g_batch_info(const sz3g_batch* batch, int* branches, int* cta_cap, uint64_t* graph_nodes);
+
+/* Frees the batch's graph, workspaces and result array (NULL is accepted). */
+int sz3g_batch_destroy(sz3g_batch* batch);
+
+/* ---------------------------------------------------------------------------
  * Diagnostics (no counterpart in the paper): launch accounting and per-kernel
  * timing with CUDA events, used by the benchmark to attribute time to kernels.
  * ------------------------------------------------------------------------- */

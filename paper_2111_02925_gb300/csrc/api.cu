@@ -151,13 +151,6 @@ uint64_t get_le(const unsigned char* b, int n) {
   return v;
 }
 
-struct Header {
-  sz3g_params p;
-  Plan plan;
-  unsigned long long n_unpred, n_words, ebT_bits;
-  uint32_t n_used;
-  unsigned long long off_table, off_chunks, off_sub, off_payload, end;
-};
 
 int parse_header(const unsigned char* s, size_t bytes, Header* h) {
   std::memset(h, 0, sizeof(*h));
@@ -214,6 +207,62 @@ int parse_header(const unsigned char* s, size_t bytes, Header* h) {
 }
 
 }  // namespace
+
+size_t compress_ws_bytes(const Plan& pl) { return compress_layout(pl).total; }
+size_t decompress_ws_bytes(const Plan& pl) { return decompress_layout(pl).total; }
+int stream_status(uint32_t flags) { return status_of(flags); }
+int parse_stream_header(const unsigned char* hb, size_t bytes, Header* h) { return parse_header(hb, bytes, h); }
+
+// The compress pipeline on stream s, without synchronising: on completion the
+// status block *st holds the flags and the stream length.
+int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
+                     unsigned char* ws, cudaStream_t s, DevState** st_out) {
+  const CompressWs L = compress_layout(pl);
+  DevState* st = (DevState*)(ws + L.st);
+  *st_out = st;
+  SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.codes, s));  // state, histogram, tables, look-back status
+  SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s));
+  void* R[34];
+  for (int k = 0; k <= pl.L; ++k) R[k] = (k == 0 && level_path_ok(pl)) ? nullptr : ws + L.R[k];
+  uint16_t* codes = (uint16_t*)(ws + L.codes);
+  uint32_t* hist = (uint32_t*)(ws + L.hist);
+  uint32_t* table = (uint32_t*)(ws + L.table);
+  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, x1_bytes(pl) ? ws + L.x1 : nullptr, s));
+  SZ3G_TRY(launch_codebook(hist, 2 * pl.radius, table, nullptr, nullptr, st, ws + L.cb, (unsigned char*)d_out,
+                           out_capacity, pl.esz, s));
+  PassMap map;  // kernel parameter, copied at launch
+  make_pass_map(pl, &map);
+  SZ3G_TRY(launch_encode(pl, codes, table, d_in, &map, ws + L.enc, st, (unsigned char*)d_out, out_capacity,
+                         kEncodeStream, nullptr, nullptr, nullptr, 0, s));
+  SZ3G_TRY(launch_finalize(pl, p, st, (unsigned char*)d_out, out_capacity, s));
+  return SZ3G_OK;
+}
+
+// The decompress pipeline of a parsed stream on s, without synchronising.
+int decompress_enqueue(const Header& h, const void* d_stream, void* d_out, unsigned char* ws, cudaStream_t s,
+                       DevState** st_out) {
+  const Plan& pl = h.plan;
+  const DecompressWs L = decompress_layout(pl);
+  DevState* st = (DevState*)(ws + L.st);
+  *st_out = st;
+  SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+  const unsigned char* base = (const unsigned char*)d_stream;
+  SZ3G_TRY(launch_decode_tables(base + h.off_table, h.n_used, nullptr, 2 * pl.radius, ws + L.tables, st, s));
+  uint16_t* codes = (uint16_t*)(ws + L.codes);
+  SZ3G_TRY(launch_decode_chunks((const uint32_t*)(base + h.off_payload), h.n_words,
+                                (const uint32_t*)(base + h.off_chunks),
+                                pl.nsub > 1 ? (const uint16_t*)(base + h.off_sub) : nullptr, pl.n_chunks, pl.chunk,
+                                pl.N, ws + L.tables, (unsigned long long*)(ws + L.woff), codes,
+                                (uint32_t*)(ws + L.zcnt), ws + L.scan1, st, s));
+  SZ3G_TRY(launch_scan((uint32_t*)(ws + L.zcnt), pl.n_chunks * pl.nsub, (unsigned long long*)(ws + L.zunit), 0,
+                       h.n_unpred, 1, ws + L.scan2, st, s));
+  void* R[34];
+  for (int k = 0; k <= pl.L; ++k) R[k] = k == 0 ? d_out : ws + L.R[k];
+  SZ3G_TRY(launch_recover_levels(pl, codes, base + SZ3G_HEADER_BYTES, h.n_unpred, (unsigned long long*)(ws + L.zunit),
+                                 R, d_out, st, h.ebT_bits, true, s));
+  return SZ3G_OK;
+}
+
 }  // namespace sz3g
 
 using namespace sz3g;
@@ -263,22 +312,8 @@ int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t ou
   Scratch own;
   unsigned char* ws;
   SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
-  DevState* st = (DevState*)(ws + L.st);
-  SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.codes, s));  // state, histogram, tables, look-back status
-  SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s));
-  void* R[34];
-  for (int k = 0; k <= pl.L; ++k) R[k] = (k == 0 && level_path_ok(pl)) ? nullptr : ws + L.R[k];
-  uint16_t* codes = (uint16_t*)(ws + L.codes);
-  uint32_t* hist = (uint32_t*)(ws + L.hist);
-  uint32_t* table = (uint32_t*)(ws + L.table);
-  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, x1_bytes(pl) ? ws + L.x1 : nullptr, s));
-  SZ3G_TRY(launch_codebook(hist, 2 * pl.radius, table, nullptr, nullptr, st, ws + L.cb, (unsigned char*)d_out,
-                           out_capacity, pl.esz, s));
-  PassMap map;  // kernel parameter, copied at launch
-  make_pass_map(pl, &map);
-  SZ3G_TRY(launch_encode(pl, codes, table, d_in, &map, ws + L.enc, st, (unsigned char*)d_out, out_capacity,
-                         kEncodeStream, nullptr, nullptr, nullptr, 0, s));
-  SZ3G_TRY(launch_finalize(pl, p, st, (unsigned char*)d_out, out_capacity, s));
+  DevState* st = nullptr;
+  SZ3G_TRY(compress_enqueue(p, pl, d_in, d_out, out_capacity, ws, s, &st));
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
   SZ3G_TRY(status_of(h.flags));
@@ -318,22 +353,8 @@ int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_
   Scratch own;
   unsigned char* ws;
   SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
-  DevState* st = (DevState*)(ws + L.st);
-  SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
-  const unsigned char* base = (const unsigned char*)d_stream;
-  SZ3G_TRY(launch_decode_tables(base + h.off_table, h.n_used, nullptr, 2 * pl.radius, ws + L.tables, st, s));
-  uint16_t* codes = (uint16_t*)(ws + L.codes);
-  SZ3G_TRY(launch_decode_chunks((const uint32_t*)(base + h.off_payload), h.n_words,
-                                (const uint32_t*)(base + h.off_chunks),
-                                pl.nsub > 1 ? (const uint16_t*)(base + h.off_sub) : nullptr, pl.n_chunks, pl.chunk,
-                                pl.N, ws + L.tables, (unsigned long long*)(ws + L.woff), codes,
-                                (uint32_t*)(ws + L.zcnt), ws + L.scan1, st, s));
-  SZ3G_TRY(launch_scan((uint32_t*)(ws + L.zcnt), pl.n_chunks * pl.nsub, (unsigned long long*)(ws + L.zunit), 0,
-                       h.n_unpred, 1, ws + L.scan2, st, s));
-  void* R[34];
-  for (int k = 0; k <= pl.L; ++k) R[k] = k == 0 ? d_out : ws + L.R[k];
-  SZ3G_TRY(launch_recover_levels(pl, codes, base + SZ3G_HEADER_BYTES, h.n_unpred, (unsigned long long*)(ws + L.zunit),
-                                 R, d_out, st, h.ebT_bits, true, s));
+  DevState* st = nullptr;
+  SZ3G_TRY(decompress_enqueue(h, d_stream, d_out, ws, s, &st));
   DevState hs;
   SZ3G_TRY(read_state(st, &hs, s));
   return status_of(hs.flags);

@@ -99,7 +99,7 @@ struct Plan {
 enum KernelId {
   kKRange, kKEb, kKAnchor, kKLift, kKPassQuantize, kKPassRecover, kKCodebook, kKEncode, kKFinalize,
   kKDecodeTables, kKDecode, kKScan, kKZeroCount, kKPackTable, kKLevelQuantize, kKLevelRecover,
-  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKernelCount
+  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKPublish, kKernelCount
 };
 
 // Counts a launch and, while profiling is on, brackets it with CUDA events.
@@ -233,6 +233,10 @@ int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unp
                           bool codes_padded, cudaStream_t s);
 
 // k_level.cu (fields of rank <= 3)
+// Upper bound on the CTAs of one level-kernel launch (0: one wave of the whole
+// GPU).  Set while a batch graph is built, so that concurrent fields share the
+// SMs; read on the host at launch time.
+extern int g_level_cta_cap;
 bool level_path_ok(const Plan& pl);
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
                           DevState* st, void* X1, cudaStream_t s);
@@ -249,6 +253,23 @@ inline unsigned long long x1_bytes(const Plan& pl) {
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
                          const unsigned long long* zunit, void* const* R, void* d_out,
                          DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s);
+
+// api.cu: the pipelines without synchronisation (also used by the batch).
+struct Header {  // a parsed stream header
+  sz3g_params p;
+  Plan plan;
+  unsigned long long n_unpred, n_words, ebT_bits;
+  uint32_t n_used;
+  unsigned long long off_table, off_chunks, off_sub, off_payload, end;
+};
+size_t compress_ws_bytes(const Plan& pl);
+size_t decompress_ws_bytes(const Plan& pl);
+int stream_status(uint32_t flags);
+int parse_stream_header(const unsigned char* hb, size_t bytes, Header* h);
+int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
+                     unsigned char* ws, cudaStream_t s, DevState** st);
+int decompress_enqueue(const Header& h, const void* d_stream, void* d_out, unsigned char* ws, cudaStream_t s,
+                       DevState** st);
 
 // k_huffman.cu
 size_t codebook_scratch_bytes();

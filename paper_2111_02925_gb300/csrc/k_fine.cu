@@ -602,6 +602,7 @@ static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_f
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, FineThreads<COMP>::kN, smem);
   if (per < 1) per = 1;
   unsigned long long grid = (unsigned long long)nsm * per;
+  if (g_level_cta_cap > 0 && grid > (unsigned long long)g_level_cta_cap) grid = (unsigned long long)g_level_cta_cap;
   if (grid > d.ntiles) grid = d.ntiles;
   SZ3G_LAUNCH(COMP ? kKLevelQuantize : kKLevelRecover, s,
               kern<<<(unsigned)grid, FineThreads<COMP>::kN, smem, s>>>(d, a, tmx, tmc));

@@ -844,6 +844,8 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kCoarseMax = 4096;  // points of the largest coarse-group grid
 
+int g_level_cta_cap = 0;
+
 bool level_path_ok(const Plan& pl) { return pl.n[0] == 1; }  // rank <= 3
 
 // k_fine.cu
@@ -1018,6 +1020,7 @@ static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t 
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kLevelThreads, smem);
   if (per < 1) per = 1;
   unsigned long long grid = (unsigned long long)nsm * per;
+  if (g_level_cta_cap > 0 && grid > (unsigned long long)g_level_cta_cap) grid = (unsigned long long)g_level_cta_cap;
   if (grid > d.ntiles) grid = d.ntiles;
   SZ3G_LAUNCH(COMP ? kKLevelQuantize : kKLevelRecover, s,
               kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(d, a, tmx, tmc));

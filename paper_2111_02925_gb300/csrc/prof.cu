@@ -15,7 +15,7 @@ namespace sz3g {
 static const char* kKernelNames[kKernelCount] = {
     "range", "eb", "anchor", "lift", "pass_quantize", "pass_recover", "codebook", "encode", "finalize",
     "decode_tables", "decode", "scan", "zero_count", "pack_table", "level_quantize", "level_recover",
-    "coarse_quantize", "coarse_recover", "decimate",
+    "coarse_quantize", "coarse_recover", "decimate", "publish",
 };
 
 namespace {
@@ -48,6 +48,11 @@ LaunchScope::LaunchScope(int kid, cudaStream_t s) : kid_(kid), s_(s), a_(nullptr
   g_launches.fetch_add(1, std::memory_order_relaxed);
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;  // launches captured into a graph are not timed one by one
+  }
   a_ = take_event();
   if (a_) cudaEventRecord((cudaEvent_t)a_, s);
 }

@@ -80,6 +80,14 @@ _SIGS = {
     "sz3g_huffman_encode": [_vp, _u64, _vp, _vp, _u32, _u32, _vp, _u64, _vp, _vp, C.POINTER(_u64), _vp],
     "sz3g_huffman_decode": [_vp, _u64, _vp, _vp, _u32, _vp, _u32, _vp, _u64, _vp],
     "sz3g_huffman_decode_static": [_vp, _u64, _vp, _vp, _u32, _vp, _u32, _vp, _u64, _vp],
+    "sz3g_batch_create": [C.c_int, C.c_int, _P, C.POINTER(_vp), C.POINTER(_sz), C.POINTER(_vp), C.POINTER(_sz),
+                          C.POINTER(_vp)],
+    "sz3g_batch_run": [_vp, _vp],
+    "sz3g_batch_results": [_vp, C.POINTER(_u64), C.POINTER(C.c_int)],
+    "sz3g_batch_configure": [_vp, C.c_int, C.c_int],
+    "sz3g_batch_tune": [_vp, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "sz3g_batch_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_u64)],
+    "sz3g_batch_destroy": [_vp],
 }
 
 
@@ -228,6 +236,60 @@ def sz3g_huffman_decode_static(d_words: int, n_words: int, d_chunk_words: int, d
     """sz3g_huffman_decode with its scratch in the library's fixed device array (allocates nothing)."""
     return load().sz3g_huffman_decode_static(d_words, n_words, d_chunk_words, d_sub_bits or None, chunk, d_len, nsym,
                                              d_codes, n, stream or None)
+
+
+class Batch:
+    """sz3g_batch_* over device pointers: many fields (or streams) per call.
+
+    compress:   Batch(params_list, in_ptrs, out_ptrs, out_caps)
+    decompress: Batch(None, stream_ptrs, out_ptrs, out_caps, in_bytes=stream_lengths, decompress=True)
+    """
+
+    def __init__(self, params, d_in, d_out, out_capacity, in_bytes=None, decompress=False):
+        n = len(d_in)
+        L = load()
+        pa = (Params * n)(*params) if params is not None else None
+        ins = (_vp * n)(*[int(v) for v in d_in])
+        outs = (_vp * n)(*[int(v) for v in d_out])
+        caps = (_sz * n)(*[int(v) for v in out_capacity])
+        ib = (_sz * n)(*[int(v) for v in in_bytes]) if in_bytes is not None else None
+        h = _vp()
+        _chk(L.sz3g_batch_create(n, int(decompress), pa, ins, ib, outs, caps, C.byref(h)), "sz3g_batch_create")
+        self.n, self.h = n, h
+
+    def run(self, stream: int = 0) -> None:
+        _chk(load().sz3g_batch_run(self.h, _vp(stream)), "sz3g_batch_run")
+
+    def results(self):
+        """(rc, stream lengths, per-field statuses) of the last run (synchronises)."""
+        b = (_u64 * self.n)()
+        st = (C.c_int * self.n)()
+        rc = load().sz3g_batch_results(self.h, b, st)
+        return rc, list(b), list(st)
+
+    def configure(self, branches: int, cta_cap: int = 0) -> None:
+        _chk(load().sz3g_batch_configure(self.h, branches, cta_cap), "sz3g_batch_configure")
+
+    def tune(self, stream: int = 0):
+        br, cap = C.c_int(), C.c_int()
+        _chk(load().sz3g_batch_tune(self.h, _vp(stream), C.byref(br), C.byref(cap)), "sz3g_batch_tune")
+        return br.value, cap.value
+
+    def info(self):
+        br, cap, nodes = C.c_int(), C.c_int(), _u64()
+        _chk(load().sz3g_batch_info(self.h, C.byref(br), C.byref(cap), C.byref(nodes)), "sz3g_batch_info")
+        return br.value, cap.value, nodes.value
+
+    def close(self) -> None:
+        if self.h:
+            load().sz3g_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sz3g_launch_count() -> int:
