@@ -298,6 +298,69 @@ int sz3g_batch_info(const sz3g_batch* batch, int* branches, int* cta_cap, uint64
 int sz3g_batch_destroy(sz3g_batch* batch);
 
 /* ---------------------------------------------------------------------------
+ * Per-level choice of interpolation and axis order (the paper's best-fit /
+ * composite predictor idea, Sec. 3.1, and the per-level interpolation of
+ * SZ3-Interp, Sec. 6.2; fields of rank <= 3).  Candidate c = 2 o + interp
+ * over the axis orders (0,1,2), (1,2,0), (2,0,1), (2,1,0) (2-D: (0,1), (1,0),
+ * then the same two again, never chosen on a tie; 1-D: (0)).  For level l the
+ * estimate predicts every point of the level from the original values along
+ * its pass axis (the last axis of the order on which its coordinate at
+ * stride 2^(l-1) is odd), quantizes it with p's bound and radius, and costs
+ * the codes by their Shannon bits plus 8 sizeof(T) bits per unpredictable
+ * value -- over all points of the level (nblocks = 0) or those inside
+ * nblocks seeded sample blocks of up to 16 grid points per axis (block b of
+ * level l starts on axis d at SplitMix64(seed ^ l << 48 ^ b << 8 ^ d) mod
+ * (m_d - span_d + 1); a point in several blocks counts once).  p's interp /
+ * dim_order are not used.  All of these synchronise `stream`.
+ * ------------------------------------------------------------------------- */
+
+/* h_cost[(l - 1) * 8 + c]: estimated bits of level l (1..L) under candidate c. */
+int sz3g_select_costs(const sz3g_params* p, const void* d_x, uint32_t nblocks, uint64_t seed, double* h_cost,
+                      void* stream);
+
+/*
+ * h_feat[(l - 1) * 16 + k]: 16 features of level l from the same sample
+ * blocks: per axis d = 0..2 (0 for missing axes) log2(1 + mean |linear
+ * error| / eb), log2(1 + mean |cubic error| / eb) and the log2 ratio of mean
+ * squared lag-2 to lag-1 differences; l / L; l - 1; log10(eb / (max - min));
+ * the fraction of points whose differences to their +1 neighbours are all
+ * within eb; the fractions of the level's points (order (0,1,2)) whose linear
+ * and cubic errors exceed 64 eb; log2 of the last over the first extent.
+ */
+int sz3g_select_features(const sz3g_params* p, const void* d_x, uint32_t nblocks, uint64_t seed, double* h_feat,
+                         void* stream);
+
+/* Sampling selector: h_choice[l] = the candidate of least estimated bits for
+ * level l = 1..L (ties: the lower index); h_choice[0] = 0. */
+int sz3g_select_sampled(const sz3g_params* p, const void* d_x, uint32_t nblocks, uint64_t seed, uint8_t* h_choice,
+                        void* stream);
+
+/* Learned selector: h_choice[l] = argmax of the network's logits on level l's
+ * features (d_w: SZ3G_MLP_WEIGHTS floats on the device). */
+int sz3g_select_learned(const sz3g_params* p, const void* d_x, const float* d_w, uint32_t nblocks, uint64_t seed,
+                        uint8_t* h_choice, void* stream);
+
+/*
+ * The selector's network: 16 features, standardised by (f - mu) / sd, -> 64
+ * hidden units (ReLU) -> 8 logits; masked softmax cross-entropy.  Weights, as
+ * SZ3G_MLP_WEIGHTS floats: mu[16], sd[16], W1[64][16], b1[64], W2[8][64],
+ * b2[8].  d_feat: n x 16 floats; d_mask: n x 8 bytes (1: candidate allowed);
+ * d_label: n int32 (an allowed candidate).
+ */
+#define SZ3G_MLP_WEIGHTS 1640
+/* d_logits: n x 8 (masked: -inf). */
+int sz3g_mlp_forward(const float* d_w, const float* d_feat, const uint8_t* d_mask, uint32_t n, float* d_logits,
+                     void* stream);
+/* d_grad: SZ3G_MLP_WEIGHTS floats, the gradient of the mean loss (zero for
+ * mu / sd); h_loss: the mean loss.  Synchronises. */
+int sz3g_mlp_gradient(const float* d_w, const float* d_feat, const uint8_t* d_mask, const int32_t* d_label,
+                      uint32_t n, float* d_grad, float* h_loss, void* stream);
+/* `steps` full-batch gradient steps of size lr on d_w; h_loss: the mean loss
+ * before the last step.  Synchronises. */
+int sz3g_mlp_train(float* d_w, const float* d_feat, const uint8_t* d_mask, const int32_t* d_label, uint32_t n,
+                   float lr, uint32_t steps, float* h_loss, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Diagnostics (no counterpart in the paper): launch accounting and per-kernel
  * timing with CUDA events, used by the benchmark to attribute time to kernels.
  * ------------------------------------------------------------------------- */

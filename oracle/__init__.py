@@ -109,6 +109,8 @@ def lib():
             "sz3o_compress": [P, vp, vp, C.c_uint64, u64p],
             "sz3o_read_header": [vp, C.c_uint64, P, u64p],
             "sz3o_decompress": [vp, C.c_uint64, vp, C.c_uint64],
+            "sz3o_select_costs": [P, vp, C.c_uint32, C.c_uint32, C.c_uint64, vp],
+            "sz3o_select_features": [P, vp, C.c_uint32, C.c_uint32, C.c_uint64, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -321,3 +323,50 @@ def decompress(stream: bytes) -> np.ndarray:
     out = np.zeros(n, np_dtype(p))
     _check(decompress_status(stream, out), "decompress")
     return out
+
+
+# ---------------------------------------------------------------------------
+# Per-level selection of interpolation and axis order (rank <= 3).
+# ---------------------------------------------------------------------------
+SEL_CANDIDATES = 8
+SEL_FEATURES = 16
+_SEL_ORDERS = {3: [(0, 1, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)], 2: [(0, 1), (1, 0), (0, 1), (1, 0)], 1: [(0,)] * 4}
+
+
+def candidate(ndim: int, c: int):
+    """(interp, axis order) of candidate c = 2 o + interp."""
+    return c % 2, _SEL_ORDERS[ndim][c // 2]
+
+
+def select_costs(p: Params, x: np.ndarray, level: int, nblocks: int = 0, seed: int = 0) -> np.ndarray:
+    """Estimated bits of level `level` under the 8 candidates (all points of
+    the level when nblocks == 0, else those in the seeded sample blocks)."""
+    x = np.ascontiguousarray(x, dtype=np_dtype(p)).reshape(-1)
+    out = np.zeros(SEL_CANDIDATES, np.float64)
+    _check(lib().sz3o_select_costs(C.byref(p), _ptr(x), level, nblocks, seed, _ptr(out)), "select_costs")
+    return out
+
+
+def select_features(p: Params, x: np.ndarray, level: int, nblocks: int = 0, seed: int = 0) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np_dtype(p)).reshape(-1)
+    out = np.zeros(SEL_FEATURES, np.float64)
+    _check(lib().sz3o_select_features(C.byref(p), _ptr(x), level, nblocks, seed, _ptr(out)), "select_features")
+    return out
+
+
+def select_levels(p: Params, x: np.ndarray, nblocks: int = 0, seed: int = 0):
+    """{level: candidate} minimising the estimated bits of every level
+    (ties: the lower candidate)."""
+    _, L = shape(p)
+    return {l: int(np.argmin(select_costs(p, x, l, nblocks, seed))) for l in range(1, L + 1)}
+
+
+def params_for_choices(p: Params, dims, choices) -> Params:
+    """Copy of p with the per-level interpolation / order of `choices`."""
+    nd = len(dims)
+    li = {l: candidate(nd, c)[0] for l, c in choices.items()}
+    lo = {l: list(candidate(nd, c)[1]) for l, c in choices.items()}
+    q = make_params(dims, p.eb, dtype=p.dtype, eb_mode=p.eb_mode, interp=p.interp,
+                    order=[p.dim_order[i] for i in range(nd)], radius=p.radius, chunk=p.chunk_codes,
+                    level_interp=li, level_order=lo)
+    return q

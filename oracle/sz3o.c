@@ -103,6 +103,65 @@ int sz3o_shape(const sz3o_params* p, uint64_t* n_points, uint32_t* n_levels) {
 }
 
 /* ---------------------------------------------------------------------------
+ * Selection helpers (type independent): candidates, sample blocks.
+ * Candidate c = 2 o + interp: interp 0 linear / 1 cubic, o an axis order of
+ * the list below (3-D: (0,1,2), (1,2,0), (2,0,1), (2,1,0); 2-D: (0,1), (1,0)
+ * listed twice, so the later copies never win a tie; 1-D: (0)).
+ * Sample blocks of level l: up to 16 points per axis of G_{l-1} (the grid of
+ * stride 2^(l-1)); block b starts on axis d at splitmix64(key) mod
+ * (m_d - span_d + 1), key = seed ^ (l << 48) ^ (b << 8) ^ d, with splitmix64
+ * the published SplitMix64 output function applied to key.
+ * ------------------------------------------------------------------------- */
+#define SZ3O_SEL_MAX_BLOCKS 1024
+
+typedef struct {
+  uint32_t n;  /* 0: the whole grid */
+  uint64_t lo[SZ3O_SEL_MAX_BLOCKS][4], hi[SZ3O_SEL_MAX_BLOCKS][4];
+} sel_blocks;
+
+static const uint8_t* sel_order(uint32_t ndim, uint32_t o) {
+  static const uint8_t o3[4][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  static const uint8_t o2[4][2] = {{0, 1}, {1, 0}, {0, 1}, {1, 0}};
+  static const uint8_t o1[1] = {0};
+  if (ndim == 3) return o3[o];
+  if (ndim == 2) return o2[o];
+  return o1;
+}
+
+static uint64_t splitmix64(uint64_t key) {
+  uint64_t z = key + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static void sel_make_blocks(const walk_geom* g, uint32_t l, uint32_t nblocks, uint64_t seed, sel_blocks* blk) {
+  const uint64_t s = (uint64_t)1 << (l - 1);
+  uint32_t b, d;
+  blk->n = nblocks > SZ3O_SEL_MAX_BLOCKS ? SZ3O_SEL_MAX_BLOCKS : nblocks;
+  for (b = 0; b < blk->n; ++b)
+    for (d = 0; d < g->ndim; ++d) {
+      const uint64_t m = (g->n[d] + s - 1) / s;
+      const uint64_t span = m < 16 ? m : 16;
+      const uint64_t key = seed ^ ((uint64_t)l << 48) ^ ((uint64_t)b << 8) ^ (uint64_t)d;
+      const uint64_t o = splitmix64(key) % (m - span + 1);
+      blk->lo[b][d] = o;
+      blk->hi[b][d] = o + span;
+    }
+}
+
+/* Is grid point gc inside one of blocks 0..b-1? */
+static int sel_in_earlier(const sel_blocks* blk, uint32_t b, const uint64_t* gc, uint32_t ndim) {
+  uint32_t e, d;
+  for (e = 0; e < b; ++e) {
+    int in = 1;
+    for (d = 0; d < ndim && in; ++d) in = gc[d] >= blk->lo[e][d] && gc[d] < blk->hi[e][d];
+    if (in) return 1;
+  }
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------
  * The two type instantiations.
  * ------------------------------------------------------------------------- */
 #define T float
@@ -880,4 +939,34 @@ done:
   free(codes);
   free(unpred);
   return rc;
+}
+
+/* ---------------------------------------------------------------------------
+ * Per-level selection (see sel_hist in sz3o_typed.inc).
+ * ------------------------------------------------------------------------- */
+static int sel_geom(const sz3o_params* p, uint32_t level, walk_geom* g) {
+  int rc = geom_of(p, g);
+  if (rc) return rc;
+  if (p->ndim > 3 || level < 1 || level > g->L) return SZ3O_E_INVAL;
+  return SZ3O_OK;
+}
+
+int sz3o_select_costs(const sz3o_params* p, const void* x, uint32_t level, uint32_t nblocks, uint64_t seed,
+                      double* cost) {
+  walk_geom g;
+  int rc = sel_geom(p, level, &g);
+  if (rc) return rc;
+  if (!x || !cost) return SZ3O_E_INVAL;
+  return p->dtype == SZ3O_F32 ? select_costs_f32(p, &g, (const float*)x, level, nblocks, seed, cost)
+                              : select_costs_f64(p, &g, (const double*)x, level, nblocks, seed, cost);
+}
+
+int sz3o_select_features(const sz3o_params* p, const void* x, uint32_t level, uint32_t nblocks, uint64_t seed,
+                         double* feat) {
+  walk_geom g;
+  int rc = sel_geom(p, level, &g);
+  if (rc) return rc;
+  if (!x || !feat) return SZ3O_E_INVAL;
+  return p->dtype == SZ3O_F32 ? select_features_f32(p, &g, (const float*)x, level, nblocks, seed, feat)
+                              : select_features_f64(p, &g, (const double*)x, level, nblocks, seed, feat);
 }

@@ -134,6 +134,18 @@ int sz3o_compress(const sz3o_params* p, const void* x, void* out, uint64_t capac
 int sz3o_read_header(const void* stream, uint64_t bytes, sz3o_params* p, uint64_t* n_points);
 int sz3o_decompress(const void* stream, uint64_t bytes, void* out, uint64_t capacity);
 
+/* Per-level selection of interpolation and axis order (rank <= 3).
+ * Candidate c = 2 o + interp over the axis orders (0,1,2), (1,2,0), (2,0,1),
+ * (2,1,0) (2-D: (0,1), (1,0), (0,1), (1,0); 1-D: (0)).  cost[8]: estimated
+ * bits of level `level` (1..L) under each candidate, from all points of the
+ * level (nblocks = 0) or those inside nblocks seeded 16-point sample blocks.
+ * feat[16]: the level's features.  p's interp / order are not used. */
+#define SZ3O_SEL_CANDIDATES 8
+int sz3o_select_costs(const sz3o_params* p, const void* x, uint32_t level, uint32_t nblocks, uint64_t seed,
+                      double* cost);
+int sz3o_select_features(const sz3o_params* p, const void* x, uint32_t level, uint32_t nblocks, uint64_t seed,
+                         double* feat);
+
 #ifdef __cplusplus
 }
 #endif

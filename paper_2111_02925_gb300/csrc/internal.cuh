@@ -99,7 +99,7 @@ struct Plan {
 enum KernelId {
   kKRange, kKEb, kKAnchor, kKLift, kKPassQuantize, kKPassRecover, kKCodebook, kKEncode, kKFinalize,
   kKDecodeTables, kKDecode, kKScan, kKZeroCount, kKPackTable, kKLevelQuantize, kKLevelRecover,
-  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKPublish, kKernelCount
+  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKPublish, kKSelect, kKMlp, kKernelCount
 };
 
 // Counts a launch and, while profiling is on, brackets it with CUDA events.

@@ -136,3 +136,23 @@ def batch_shapes(count: int = 256, seed: int = 4):
         interp = int(rng.random() < 0.5)
         out.append((dims, eb, interp))
     return out
+
+
+def grf_fronts(shape, seed: int, n_fronts: int = 16) -> np.ndarray:
+    """k^-3 Gaussian random field plus n_fronts sharp fronts
+    A tanh((n . p - c) / w): n uniform on the sphere, c uniform over the
+    projection of the box on n, w ~ U[1, 8] cells, A ~ U[0.5, 2] (float32)."""
+    x = grf(shape, seed).astype(np.float64)
+    rng = np.random.default_rng(seed + 7919)
+    grids = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij")
+    for _ in range(n_fronts):
+        nv = rng.normal(size=len(shape))
+        nv /= np.linalg.norm(nv)
+        corners = np.array(np.meshgrid(*[[0, n - 1] for n in shape], indexing="ij")).reshape(len(shape), -1)
+        proj = nv @ corners
+        c = rng.uniform(proj.min(), proj.max())
+        w = rng.uniform(1.0, 8.0)
+        a = rng.uniform(0.5, 2.0)
+        t = sum(nv[i] * grids[i] for i in range(len(shape)))
+        x += a * np.tanh((t - c) / w)
+    return x.astype(np.float32)

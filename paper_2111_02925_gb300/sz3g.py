@@ -88,7 +88,17 @@ _SIGS = {
     "sz3g_batch_tune": [_vp, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "sz3g_batch_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_u64)],
     "sz3g_batch_destroy": [_vp],
+    "sz3g_select_costs": [_P, _vp, _u32, _u64, _vp, _vp],
+    "sz3g_select_features": [_P, _vp, _u32, _u64, _vp, _vp],
+    "sz3g_select_sampled": [_P, _vp, _u32, _u64, _vp, _vp],
+    "sz3g_select_learned": [_P, _vp, _vp, _u32, _u64, _vp, _vp],
+    "sz3g_mlp_forward": [_vp, _vp, _vp, _u32, _vp, _vp],
+    "sz3g_mlp_gradient": [_vp, _vp, _vp, _vp, _u32, _vp, C.POINTER(C.c_float), _vp],
+    "sz3g_mlp_train": [_vp, _vp, _vp, _vp, _u32, C.c_float, _u32, C.POINTER(C.c_float), _vp],
 }
+MLP_WEIGHTS = 1640
+SEL_CANDIDATES = 8
+SEL_FEATURES = 16
 
 
 def lib_path() -> str:
@@ -290,6 +300,81 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _levels(p: Params) -> int:
+    m = max(p.dims[i] for i in range(p.ndim))
+    L = 0
+    while (1 << L) < m:
+        L += 1
+    return L
+
+
+def sz3g_select_costs(p: Params, d_x: int, nblocks: int = 0, seed: int = 0, stream: int = 0):
+    """(L x 8) estimated bits per level and candidate."""
+    import numpy as np
+
+    L = _levels(p)
+    out = np.zeros((max(L, 1), SEL_CANDIDATES), np.float64)
+    _chk(load().sz3g_select_costs(C.byref(p), d_x, nblocks, seed, out.ctypes.data, stream), "sz3g_select_costs")
+    return out[:L]
+
+
+def sz3g_select_features(p: Params, d_x: int, nblocks: int = 0, seed: int = 0, stream: int = 0):
+    import numpy as np
+
+    L = _levels(p)
+    out = np.zeros((max(L, 1), SEL_FEATURES), np.float64)
+    _chk(load().sz3g_select_features(C.byref(p), d_x, nblocks, seed, out.ctypes.data, stream),
+         "sz3g_select_features")
+    return out[:L]
+
+
+def sz3g_select_sampled(p: Params, d_x: int, nblocks: int, seed: int = 0, stream: int = 0):
+    """{level: candidate} of least estimated bits."""
+    L = _levels(p)
+    ch = (C.c_uint8 * (L + 1))()
+    _chk(load().sz3g_select_sampled(C.byref(p), d_x, nblocks, seed, ch, stream), "sz3g_select_sampled")
+    return {l: int(ch[l]) for l in range(1, L + 1)}
+
+
+def sz3g_select_learned(p: Params, d_x: int, d_w: int, nblocks: int, seed: int = 0, stream: int = 0):
+    L = _levels(p)
+    ch = (C.c_uint8 * (L + 1))()
+    _chk(load().sz3g_select_learned(C.byref(p), d_x, d_w, nblocks, seed, ch, stream), "sz3g_select_learned")
+    return {l: int(ch[l]) for l in range(1, L + 1)}
+
+
+def sz3g_mlp_forward(d_w: int, d_feat: int, d_mask: int, n: int, d_logits: int, stream: int = 0) -> None:
+    _chk(load().sz3g_mlp_forward(d_w, d_feat, d_mask, n, d_logits, stream), "sz3g_mlp_forward")
+
+
+def sz3g_mlp_gradient(d_w: int, d_feat: int, d_mask: int, d_label: int, n: int, d_grad: int, stream: int = 0):
+    loss = C.c_float()
+    _chk(load().sz3g_mlp_gradient(d_w, d_feat, d_mask, d_label, n, d_grad, C.byref(loss), stream),
+         "sz3g_mlp_gradient")
+    return loss.value
+
+
+def sz3g_mlp_train(d_w: int, d_feat: int, d_mask: int, d_label: int, n: int, lr: float, steps: int,
+                   stream: int = 0) -> float:
+    loss = C.c_float()
+    _chk(load().sz3g_mlp_train(d_w, d_feat, d_mask, d_label, n, lr, steps, C.byref(loss), stream),
+         "sz3g_mlp_train")
+    return loss.value
+
+
+_ORDERS = {3: [(0, 1, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)], 2: [(0, 1), (1, 0), (0, 1), (1, 0)], 1: [(0,)] * 4}
+
+
+def params_for_choices(p: Params, choices) -> Params:
+    """Copy of p with per-level interpolation / axis order from {level: candidate}."""
+    nd = p.ndim
+    li = {l: c % 2 for l, c in choices.items()}
+    lo = {l: list(_ORDERS[nd][c // 2]) for l, c in choices.items()}
+    return make_params([p.dims[i] for i in range(nd)], p.eb, dtype=p.dtype, eb_mode=p.eb_mode, interp=p.interp,
+                       order=[p.dim_order[i] for i in range(nd)], radius=p.radius, chunk=p.chunk_codes,
+                       level_interp=li, level_order=lo)
 
 
 def sz3g_launch_count() -> int:
