@@ -12,6 +12,7 @@ steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sz3g|reference]
   python bench.py --workload batch   # the uneven 256-field batch, batched vs one call per field
+  python bench.py --workload selector  # per-level selection on a 1024^3 field with fronts
 
 --impl reference times the serial CPU oracle on the host cores, on a bounded
 sample (a 128^3 corner of the same field) per step.  N > 1 (torchrun) runs
@@ -47,7 +48,8 @@ def parse():
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="field", choices=["field", "batch"])
+    ap.add_argument("--workload", default="field", choices=["field", "batch", "selector"])
+    ap.add_argument("--train-fields", type=int, default=400)
     ap.add_argument("--fields", type=int, default=256)
     return ap.parse_args()
 
@@ -336,8 +338,156 @@ def run_batch(args):
     return 0
 
 
+def _label_field(job):
+    """Oracle labels of one training field (runs in a spawned worker)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2111_02925_gb300 import synthetic as S
+
+    shape, seed, fronts, eb = job
+    x = S.grf_fronts(shape, seed, fronts)
+    op = O.make_params(shape, eb, eb_mode=O.REL)
+    _, L = O.shape(op)
+    return [int(np.argmin(O.select_costs(op, x, l))) for l in range(1, L + 1)]
+
+
+def fronts_gpu(shape, seed, n_fronts, dev):
+    """k^-3 random field plus n_fronts tanh fronts (as synthetic.grf_fronts,
+    generated on the GPU for fields too large for the host FFT)."""
+    import numpy as np
+    import torch
+
+    x = grf_gpu(shape, seed, dev)
+    rng = np.random.default_rng(seed + 7919)
+    coords = [torch.arange(n, device=dev, dtype=torch.float32) for n in shape]
+    for _ in range(n_fronts):
+        nv = rng.normal(size=3)
+        nv /= np.linalg.norm(nv)
+        corners = np.array(np.meshgrid(*[[0, n - 1] for n in shape], indexing="ij")).reshape(3, -1)
+        proj = nv @ corners
+        c = rng.uniform(proj.min(), proj.max())
+        w = rng.uniform(1.0, 8.0)
+        a = rng.uniform(0.5, 2.0)
+        t = (nv[0] * coords[0])[:, None, None] + (nv[1] * coords[1])[None, :, None] + (nv[2] * coords[2])[None, None, :]
+        x += a * torch.tanh((t - c) / w)
+    return x.contiguous()
+
+
+def run_selector(args):
+    """Per-level selection of interpolation and axis order on one 1024^3 FP32
+    field (k^-3 random field + 16 tanh fronts, REL 1e-4).  The network is
+    trained on the GPU (own kernels) on small fields labelled by the oracle's
+    exhaustive trial; reported: stream size / compression ratio under a fixed
+    choice, the exhaustive, sampling and learned selections, and the time of
+    each selection."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    rng = np.random.default_rng(31)
+    jobs = []
+    for i in range(args.train_fields):
+        shape = tuple(int(v) for v in rng.integers(32, 65, 3))
+        eb = float(np.exp(rng.uniform(np.log(1e-5), np.log(1e-2))))
+        jobs.append((shape, 20000 + i, int(rng.integers(0, 17)), eb))
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:  # before any GPU call
+        labels = pool.map(_label_field, jobs)
+    import torch
+
+    from oracle import mlp as M
+    from paper_2111_02925_gb300 import build as B
+    from paper_2111_02925_gb300 import synthetic as S
+    from paper_2111_02925_gb300 import sz3g as G
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    B.build()
+    G.load()
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    feats, ys = [], []
+    for (shape, seed, fr, eb), lab in zip(jobs, labels):
+        x = torch.from_numpy(S.grf_fronts(shape, seed, fr).reshape(-1)).to(dev)
+        f = G.sz3g_select_features(G.make_params(shape, eb, eb_mode=G.REL), x.data_ptr(), 8, seed, sh)
+        feats.extend(f)
+        ys.extend(lab)
+    feats = np.array(feats)
+    ys = np.array(ys, np.int32)
+    w = torch.from_numpy(M.init(feats, 5).astype(np.float32)).to(dev)
+    fd = torch.from_numpy(feats.astype(np.float32).reshape(-1)).to(dev)
+    yd = torch.from_numpy(ys).to(dev)
+    md = torch.ones(len(ys) * 8, dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    loss = G.sz3g_mlp_train(w.data_ptr(), fd.data_ptr(), md.data_ptr(), yd.data_ptr(), len(ys), 0.3, 3000, sh)
+    train_s = time.perf_counter() - t0
+    n = 1024
+    x = fronts_gpu((n, n, n), 5, 16, dev).reshape(-1)
+    p = G.make_params((n, n, n), 1e-4, eb_mode=G.REL, interp=G.LINEAR)
+    cap = G.sz3g_compress_bound(p)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    wsc = G.workspace(p, False, dev)
+
+    def size(q):
+        rc, nb = G.sz3g_compress(q, x.data_ptr(), out.data_ptr(), cap, wsc.data_ptr(), wsc.numel(), sh)
+        assert rc == 0
+        return nb
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, (time.perf_counter() - t) * 1e3
+
+    def kernel_ms(fn):
+        """Time of the selection's own kernels (not the range pass it shares
+        with the compressor), from the library's CUDA-event profile."""
+        G.sz3g_profile_enable(True)
+        fn()
+        torch.cuda.synchronize()
+        t = G.sz3g_profile_read("select")[0] + G.sz3g_profile_read("mlp")[0]
+        G.sz3g_profile_enable(False)
+        return t
+
+    sel_s = lambda: G.sz3g_select_sampled(p, x.data_ptr(), 64, 1, sh)  # noqa: E731
+    sel_l = lambda: G.sz3g_select_learned(p, x.data_ptr(), w.data_ptr(), 16, 1, sh)  # noqa: E731
+    sel_e = lambda: G.sz3g_select_sampled(p, x.data_ptr(), 0, 1, sh)  # noqa: E731
+    ch_s, ms_s = timed(sel_s)
+    ch_l, ms_l = timed(sel_l)
+    ch_e, ms_e = timed(sel_e)
+    ks_s, ks_l, ks_e = kernel_ms(sel_s), kernel_ms(sel_l), kernel_ms(sel_e)
+    raw = x.numel() * 4
+    res = {
+        "fixed_linear_012": size(p),
+        "fixed_cubic_012": size(G.make_params((n, n, n), 1e-4, eb_mode=G.REL, interp=G.CUBIC)),
+        "exhaustive": size(G.params_for_choices(p, ch_e)),
+        "sampled": size(G.params_for_choices(p, ch_s)),
+        "learned": size(G.params_for_choices(p, ch_l)),
+    }
+    line = {
+        "metric": "compression ratio with the learned per-level selector (1024^3 FP32, REL 1e-4)",
+        "value": raw / res["learned"], "unit": "ratio", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "1024^3 FP32 k^-3 random field + 16 tanh fronts (seed 5), REL eb 1e-4; network "
+                               f"trained on {args.train_fields} oracle-labelled fields of 32..64 per axis",
+                   "sample_blocks": {"sampled": 64, "learned_features": 16}},
+        "ratio": {k: raw / v for k, v in res.items()},
+        "learned_vs_sampled": res["sampled"] / res["learned"],
+        "selection_ms": {"sampled": ms_s, "learned": ms_l, "exhaustive": ms_e,
+                         "note": "wall time of the call, including one pass over the field for its value range"},
+        "selection_kernel_ms": {"sampled": ks_s, "learned": ks_l, "exhaustive": ks_e},
+        "choices": {"sampled": ch_s, "learned": ch_l, "exhaustive": ch_e},
+        "training": {"examples": int(len(ys)), "steps": 3000, "final_loss": loss, "seconds": train_s},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "selector":
+        return run_selector(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

@@ -332,9 +332,48 @@ int launch_select(const Plan& pl, const sz3g_params* p, const void* d_x, int nbl
   SelAcc* acc = (SelAcc*)take((size_t)L * sizeof(SelAcc));
   double* cost = (double*)take((size_t)L * kSelCand * 8);
   double* feat = (double*)take((size_t)L * kSelFeat * 8);
-  if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return SZ3G_E_CUDA;
-  int rc = launch_range_eb(pl, d_x, st, rsc, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s);
+  // one pass over the field: its value range (the REL bound of eb = 1 is
+  // exactly max - min), then the bound rounded into T as the compressor does
+  if (cudaMemsetAsync(st2, 0, sizeof(DevState), s) != cudaSuccess) return SZ3G_E_CUDA;
+  int rc = launch_range_eb(pl, d_x, st2, rsc, range_scratch_bytes(pl), SZ3G_EB_REL, 1.0, s);
   if (rc) return rc;
+  double range = 0.0;
+  {
+    DevState hs;
+    if (cudaMemcpyAsync(&hs, st2, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return SZ3G_E_CUDA;
+    if (hs.flags & kFlagNonFinite) return SZ3G_E_NONFINITE;
+    if (hs.flags & kFlagZeroRange) {
+      if (p->eb_mode == SZ3G_EB_REL) return SZ3G_E_ZERO_RANGE_REL;
+    } else {
+      range = hs.eb_abs;
+    }
+    DevState b;
+    std::memset(&b, 0, sizeof(b));
+    const double e = p->eb_mode == SZ3G_EB_REL ? p->eb * range : p->eb;
+    if (!(e > 0.0) || !std::isfinite(e)) return SZ3G_E_INVAL;
+    if (pl.esz == 4) {
+      float t = (float)e;
+      if ((double)t > e) t = std::nextafter(t, 0.0f);
+      if (!std::isnormal(t) || !std::isnormal(1.0f / t)) return SZ3G_E_INVAL;
+      const float r = 1.0f / t;
+      uint32_t tb, rb;
+      std::memcpy(&tb, &t, 4);
+      std::memcpy(&rb, &r, 4);
+      b.ebT_bits = tb;
+      b.ebr_bits = rb;
+    } else {
+      const double t = e, r = 1.0 / t;
+      if (!std::isnormal(t) || !std::isnormal(r)) return SZ3G_E_INVAL;
+      std::memcpy(&b.ebT_bits, &t, 8);
+      std::memcpy(&b.ebr_bits, &r, 8);
+    }
+    b.eb_abs = e;
+    if (cudaMemcpyAsync(st, &b, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return SZ3G_E_CUDA;
+  }
   std::vector<SelLevel> hg(L);
   for (int l = 1; l <= L; ++l) sel_level(pl, l, nblocks, seed, &hg[l - 1]);
   if (cudaMemcpyAsync(gl, hg.data(), (size_t)L * sizeof(SelLevel), cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -376,18 +415,6 @@ int launch_select(const Plan& pl, const sz3g_params* p, const void* d_x, int nbl
         SZ3G_LAUNCH(kKSelect, s,
                     sel_acc_kernel<double><<<blocks, kSelThreads, 0, s>>>(gl + (l - 1), (const double*)d_x, st,
                                                                           acc + (l - 1)));
-    }
-    // value range max - min of the field: the REL bound of eb = 1 is exactly it
-    double range = 0.0;
-    {
-      if (cudaMemsetAsync(st2, 0, sizeof(DevState), s) != cudaSuccess) return SZ3G_E_CUDA;
-      rc = launch_range_eb(pl, d_x, st2, rsc, range_scratch_bytes(pl), SZ3G_EB_REL, 1.0, s);
-      if (rc) return rc;
-      DevState hs;
-      if (cudaMemcpyAsync(&hs, st2, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess)
-        return SZ3G_E_CUDA;
-      if (!(hs.flags & (kFlagZeroRange | kFlagNonFinite))) range = hs.eb_abs;
     }
     SZ3G_LAUNCH(kKSelect, s,
                 sel_features_kernel<<<1, 32, 0, s>>>(acc, gl, L, st, pl.esz, range, feat, d_feat_f));
