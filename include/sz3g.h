@@ -14,9 +14,10 @@
  *    computed on the GPU (sizes, statuses) it synchronises that stream before
  *    returning, and says so.
  *  - Workspace: `d_workspace` may be NULL, in which case the library takes
- *    the scratch it needs from the stream-ordered allocator
- *    (cudaMallocAsync / cudaFreeAsync on `stream`) and returns it before
- *    returning.  Otherwise it must be at least sz3g_workspace_size() bytes,
+ *    the scratch it needs from its own stream-ordered memory pool
+ *    (cudaMallocFromPoolAsync / cudaFreeAsync on `stream`) and returns it to
+ *    the pool before returning; the pool keeps freed memory reserved for the
+ *    process, so repeated calls reuse it without mapping it again.  Otherwise it must be at least sz3g_workspace_size() bytes,
  *    256-byte aligned, and is not read before it is written.
  *  - Data layout: a field is a dense row-major (C order) array of N = prod(dims)
  *    values of float (SZ3G_F32) or double (SZ3G_F64), slowest axis first.
@@ -139,7 +140,7 @@ int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_
 /*
  * End-to-end forms on HOST buffers: copy h_in to the device, compress, copy
  * the stream back (and the reverse for decompress), all on `stream`, with
- * device memory from the stream-ordered allocator.  h_* may be pageable or
+ * device memory from the library's stream-ordered pool (see Workspace).  h_* may be pageable or
  * pinned; pinned memory makes the copies asynchronous and faster.
  * Same errors as the device forms.
  */

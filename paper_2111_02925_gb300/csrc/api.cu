@@ -2,6 +2,7 @@
 // checks, workspace layout, the launch sequence of compress / decompress and
 // the stage entry points, and the mapping of device status bits to statuses.
 #include <cstring>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -87,6 +88,42 @@ DecompressWs decompress_layout(const Plan& pl) {
   return w;
 }
 
+// The library's stream-ordered memory pool on the current device: memory
+// freed into it stays reserved for the process (release threshold: never),
+// so the scratch of repeated calls is not mapped and unmapped every time.
+cudaMemPool_t lib_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pl = nullptr;
+    if (cudaMemPoolCreate(&pl, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    unsigned long long keep = ~0ull;
+    cudaMemPoolSetAttribute(pl, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaGetLastError();
+    pools[dev] = pl;
+  }
+  return pools[dev];
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pl = lib_pool();
+  return pl ? cudaMallocFromPoolAsync(p, bytes, pl, s) : cudaMallocAsync(p, bytes, s);
+}
+
 // Workspace owned for the duration of one call when the caller passes none.
 struct Scratch {
   void* ptr = nullptr;
@@ -104,7 +141,7 @@ int get_ws(void* user, size_t user_bytes, size_t need, cudaStream_t s, Scratch& 
     return SZ3G_OK;
   }
   own.s = s;
-  if (cudaMallocAsync(&own.ptr, need ? need : kAlign, s) != cudaSuccess) {
+  if (pool_alloc(&own.ptr, need ? need : kAlign, s) != cudaSuccess) {
     cudaGetLastError();
     own.ptr = nullptr;
     return SZ3G_E_NOMEM;
@@ -370,8 +407,7 @@ int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size
   SZ3G_TRY(sz3g_compress_bound(p, &bound));
   Scratch din, dout;
   din.s = dout.s = s;
-  if (cudaMallocAsync(&din.ptr, pl.N * pl.esz, s) != cudaSuccess ||
-      cudaMallocAsync(&dout.ptr, bound, s) != cudaSuccess) {
+  if (pool_alloc(&din.ptr, pl.N * pl.esz, s) != cudaSuccess || pool_alloc(&dout.ptr, bound, s) != cudaSuccess) {
     cudaGetLastError();
     return SZ3G_E_NOMEM;
   }
@@ -395,7 +431,7 @@ int sz3g_decompress_host(const void* h_stream, size_t bytes, void* h_out, size_t
   if (out_capacity < n * esz) return SZ3G_E_CAPACITY;
   Scratch dst, dout;
   dst.s = dout.s = s;
-  if (cudaMallocAsync(&dst.ptr, bytes, s) != cudaSuccess || cudaMallocAsync(&dout.ptr, n * esz, s) != cudaSuccess) {
+  if (pool_alloc(&dst.ptr, bytes, s) != cudaSuccess || pool_alloc(&dout.ptr, n * esz, s) != cudaSuccess) {
     cudaGetLastError();
     return SZ3G_E_NOMEM;
   }
