@@ -221,6 +221,88 @@ __device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* 
   return srt;
 }
 
+// Speculative halving rounds for small alphabets.  Round i of the length
+// limit uses the weights max(1, f >> i) (halving max(1, f >> 1) i times), so
+// rounds 0..3 are independent: each is sorted (block-wide), the four merges
+// run at once on four threads of different warps, and the first round whose
+// codes fit SZ3G_LMAX is the answer, as if the rounds had run one after
+// another.  `ka` holds the leaves in symbol order on entry.  On success the
+// chosen round's leaves sorted by (weight, symbol) are left in ka and their
+// lengths in nf; otherwise ka holds the weights of round 4 for the
+// sequential rounds.  Round scratch lives in [region, region + 4 * kSpecRound).
+constexpr int kSpecMax = 512, kSpecRounds = 4;
+constexpr int kSpecRound = 2 * kSpecMax * 8 + (kSpecMax + 4) * 4 * 2 + 2 * kSpecMax * 2;
+__device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsigned char* region, int K) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int s_deep[kSpecRounds];
+  auto uk = [&](int i) { return reinterpret_cast<unsigned long long*>(region + i * kSpecRound); };
+  auto sk = [&](int i) { return reinterpret_cast<unsigned long long*>(region + i * kSpecRound + kSpecMax * 8); };
+  auto lw = [&](int i) { return reinterpret_cast<uint32_t*>(region + i * kSpecRound + 2 * kSpecMax * 8); };
+  auto nfi = [&](int i) {
+    return reinterpret_cast<uint32_t*>(region + i * kSpecRound + 2 * kSpecMax * 8 + (kSpecMax + 4) * 4);
+  };
+  auto par = [&](int i) {
+    return reinterpret_cast<uint16_t*>(region + i * kSpecRound + 2 * kSpecMax * 8 + (kSpecMax + 4) * 8);
+  };
+  auto key_of = [&](int i, int j) {
+    const unsigned long long k = ka[j];
+    const uint32_t f = (uint32_t)(k >> 16) >> i;
+    return ((unsigned long long)(f ? f : 1u) << 16) | (k & 0xffffu);
+  };
+  if (tid < kSpecRounds) s_deep[tid] = 0;
+  for (int it = tid; it < kSpecRounds * K; it += blockDim.x) {
+    const int i = it / K, j = it - i * K;
+    uk(i)[j] = key_of(i, j);
+  }
+  __syncthreads();
+  // 1. every round sorted by (weight, symbol)
+  for (int i = 0; i < kSpecRounds; ++i) block_rank_sort(uk(i), sk(i), K);
+  __syncthreads();
+  for (int it = tid; it < kSpecRounds * (K + 4); it += blockDim.x) {
+    const int i = it / (K + 4), t = it - i * (K + 4);
+    if (t < K + 2) lw(i)[t] = t < K ? (uint32_t)(sk(i)[t] >> 16) : 0xffffffffu;
+    nfi(i)[t] = 0xffffffffu;
+  }
+  __syncthreads();
+  // 2. the merges at once (warps 0, 8, 16, 24: one per scheduler quarter)
+  if (lane == 0 && (warp & 7) == 0 && warp / 8 < kSpecRounds) {
+    const int i = warp / 8;
+    two_queue_merge_fast(lw(i), K, nfi(i), par(i));
+  }
+  __syncthreads();
+  // 3. depths (into nf of the round), deep rounds flagged
+  const uint32_t root = (uint32_t)(2 * K - 2);
+  for (int it = tid; it < kSpecRounds * K; it += blockDim.x) {
+    const int i = it / K, j = it - i * K;
+    uint32_t v = (uint32_t)j, d = 0;
+    while (v != root && d <= SZ3G_LMAX) {
+      v = par(i)[v];
+      ++d;
+    }
+    if (v != root || d > SZ3G_LMAX) s_deep[i] = 1;
+    nfi(i)[j] = d;
+  }
+  __syncthreads();
+  int pick = -1;
+  for (int i = 0; i < kSpecRounds && pick < 0; ++i)
+    if (!s_deep[i]) pick = i;
+  // 4. the answer (or round 4's weights) into ka / nf (K <= kSpecMax <
+  //    blockDim: one leaf per thread)
+  unsigned long long kk = 0;
+  uint32_t ll = 0;
+  if (tid < K) {
+    kk = pick >= 0 ? sk(pick)[tid] : key_of(kSpecRounds, tid);
+    ll = pick >= 0 ? nfi(pick)[tid] : 0u;
+  }
+  __syncthreads();
+  if (tid < K) {
+    ka[tid] = kk;
+    if (pick >= 0) nf[tid] = ll;
+  }
+  __syncthreads();
+  return pick >= 0;
+}
+
 // table[sym] = len << 24 | code for every used symbol.  VEC: the histogram is
 // 16-byte aligned and read with vector loads.
 template <bool VEC>
@@ -311,8 +393,16 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   const int P = pow2_at_least(K);
   unsigned long long* srt;
   if (in_smem) {
-    srt = code_lengths((unsigned long long*)smem, (unsigned long long*)(smem + kSmemLeaves * 8),
-                       (uint32_t*)(smem + kCbOffNf), (uint16_t*)(smem + kCbOffPar), K);
+    // the rounds' scratch spans the second key array and the nf / parent
+    // areas, all free until the lengths are known
+    static_assert(kSpecRounds * kSpecRound <= kCbOffSym - kSmemLeaves * 8, "speculative rounds fit");
+    if (K > 1 && K <= kSpecMax &&
+        speculative_lengths((unsigned long long*)smem, (uint32_t*)(smem + kCbOffNf), smem + kSmemLeaves * 8, K)) {
+      srt = (unsigned long long*)smem;
+    } else {
+      srt = code_lengths((unsigned long long*)smem, (unsigned long long*)(smem + kSmemLeaves * 8),
+                         (uint32_t*)(smem + kCbOffNf), (uint16_t*)(smem + kCbOffPar), K);
+    }
   } else {
     srt = code_lengths(g->keys, g->keys2, g->nf, g->parent, K);
   }

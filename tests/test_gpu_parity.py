@@ -195,6 +195,41 @@ def test_length_limit_matches_oracle():
     assert glen.cpu().numpy().max() <= 24
 
 
+@pytest.mark.parametrize("nfib", [26, 30, 36, 44])
+def test_length_limit_rounds_match_oracle(nfib):
+    # Fibonacci weights: one halving round after another is needed, up to
+    # beyond the rounds the codebook kernel tries at once
+    fib = [1, 1]
+    while len(fib) < nfib:
+        fib.append(fib[-1] + fib[-2])
+    hist = np.zeros(65536, np.uint64)
+    hist[1000:1000 + nfib] = fib
+    ln = O.huffman_lengths(hist)
+    hd = dev(hist.astype(np.uint32).view(np.int32))
+    glen = torch.empty(65536, dtype=torch.uint8, device=DEV)
+    gcode = torch.empty(65536, dtype=torch.int32, device=DEV)
+    assert G.sz3g_huffman_build(hd.data_ptr(), 65536, glen.data_ptr(), gcode.data_ptr(), G._stream_handle()) == G.OK
+    assert np.array_equal(glen.cpu().numpy(), ln)
+    assert np.array_equal(gcode.cpu().numpy().view(np.uint32), O.canonical_codes(ln))
+
+
+@pytest.mark.parametrize("k", [2, 3, 511, 512, 513, 900])
+def test_codebook_alphabet_sizes_match_oracle(k):
+    # steeply falling weights over k symbols (deep trees, several rounds)
+    rng = np.random.default_rng(k)
+    w = np.floor(2.0 ** (30.0 * (1.0 - np.arange(k) / k))).astype(np.uint64) // max(1, k // 16) + 1
+    assert w.sum() < 2 ** 31  # totals of a field of at most 2^31 points
+    hist = np.zeros(65536, np.uint64)
+    hist[rng.permutation(65536)[:k]] = w
+    ln = O.huffman_lengths(hist)
+    hd = dev(hist.astype(np.uint32).view(np.int32))
+    glen = torch.empty(65536, dtype=torch.uint8, device=DEV)
+    gcode = torch.empty(65536, dtype=torch.int32, device=DEV)
+    assert G.sz3g_huffman_build(hd.data_ptr(), 65536, glen.data_ptr(), gcode.data_ptr(), G._stream_handle()) == G.OK
+    assert np.array_equal(glen.cpu().numpy(), ln)
+    assert np.array_equal(gcode.cpu().numpy().view(np.uint32), O.canonical_codes(ln))
+
+
 def test_error_statuses_match_oracle():
     x = np.zeros((8, 8, 8), np.float32)
     op, gp = both_params(x.shape, 1e-3, eb_mode=O.REL)
