@@ -60,7 +60,7 @@ CompressWs compress_layout(const Plan& pl) {
   w.cb = l.take(codebook_scratch_bytes());
   w.enc = l.take(encode_scratch_bytes(pl.n_chunks));
   w.codes = l.take(pl.N * 2);
-  w.x1 = l.take(x1_bytes(pl));
+  w.x1 = l.take(xpyr_bytes(pl));
   // the fused level path never stores the finest grid's reconstruction
   for (int k = level_path_ok(pl) ? 1 : 0; k <= pl.L; ++k) w.R[k] = l.take(pl.gsize[k] * pl.esz);
   w.total = l.off;
@@ -264,7 +264,7 @@ int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, voi
   uint16_t* codes = (uint16_t*)(ws + L.codes);
   uint32_t* hist = (uint32_t*)(ws + L.hist);
   uint32_t* table = (uint32_t*)(ws + L.table);
-  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, x1_bytes(pl) ? ws + L.x1 : nullptr, s));
+  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, xpyr_bytes(pl) ? ws + L.x1 : nullptr, s));
   SZ3G_TRY(launch_codebook(hist, 2 * pl.radius, table, nullptr, nullptr, st, ws + L.cb, (unsigned char*)d_out,
                            out_capacity, pl.esz, s));
   PassMap map;  // kernel parameter, copied at launch
@@ -459,7 +459,7 @@ int sz3g_predict_quantize(const sz3g_params* p, const void* d_in, uint16_t* d_co
   SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s));
   void* R[34];
   for (int k = 0; k <= pl.L; ++k) R[k] = (k == 0 && level_path_ok(pl)) ? nullptr : ws + L.R[k];
-  SZ3G_TRY(launch_quantize_levels(pl, d_in, d_codes, R, d_hist, st, x1_bytes(pl) ? ws + L.x1 : nullptr, s));
+  SZ3G_TRY(launch_quantize_levels(pl, d_in, d_codes, R, d_hist, st, xpyr_bytes(pl) ? ws + L.x1 : nullptr, s));
   PassMap map;
   make_pass_map(pl, &map);
   SZ3G_TRY(launch_compact_unpred(pl, d_codes, d_in, &map, ws + L.enc, (uint32_t*)(ws + L.table), d_unpred, st, s));

@@ -240,15 +240,24 @@ extern int g_level_cta_cap;
 bool level_path_ok(const Plan& pl);
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
                           DevState* st, void* X1, cudaStream_t s);
-// Decimated copy of the field over G_1 (rows pitched to 16 bytes), the input
-// of the coarser levels; x1_bytes is 0 when the level path does not use it.
-inline unsigned long long x1_pitch(const Plan& pl) {
+// Decimated copies of the field X_k = x[::2^k, ::2^k, ::2^k] over G_k, k >= 1
+// (rows pitched to 16 bytes, one after another): the inputs of the coarser
+// levels; xpyr_bytes is 0 when the level path does not use them.
+inline unsigned long long xk_pitch(const Plan& pl, int k) {
   const unsigned long long al = 16 / pl.esz;
-  return (pl.gm[1][3] + al - 1) / al * al;
+  return (pl.gm[k][3] + al - 1) / al * al;
 }
-inline unsigned long long x1_bytes(const Plan& pl) {
+inline unsigned long long xk_bytes(const Plan& pl, int k) {
+  return ((xk_pitch(pl, k) * pl.gm[k][2] * pl.gm[k][1] * pl.esz) + 255) & ~255ull;
+}
+inline unsigned long long xpyr_offset(const Plan& pl, int k) {  // byte offset of X_k
+  unsigned long long o = 0;
+  for (int q = 1; q < k; ++q) o += xk_bytes(pl, q);
+  return o;
+}
+inline unsigned long long xpyr_bytes(const Plan& pl) {
   if (pl.n[0] != 1 || pl.L < 1) return 0;
-  return x1_pitch(pl) * pl.gm[1][2] * pl.gm[1][1] * pl.esz;
+  return xpyr_offset(pl, pl.L + 1);
 }
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
                          const unsigned long long* zunit, void* const* R, void* d_out,

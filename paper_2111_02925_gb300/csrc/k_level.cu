@@ -1072,44 +1072,58 @@ static int run_coarse(const Plan& pl, int kc, const LevelArgs<T>& a, cudaStream_
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
-// X1[i][j][k] = x[2i][2j][2k] over G_1, rows pitched to 16 bytes: the input of
-// every level but the finest, read contiguously (and by tensor copies)
-// instead of at stride 2^k from the field.  One warp per output row.
+// X_k[i][j][c] = src[2i][2j][2c] (src = the field for k = 1, else X_{k-1}):
+// the decimated pyramid that the levels on G_1 and coarser read contiguously
+// (and by tensor copies) instead of the field at stride 2^k.  One warp per
+// output row; rows of X_k pitched to 16 bytes.
 template <typename T>
-__global__ void decimate_kernel(const T* __restrict__ x, unsigned long long s0, unsigned long long s1, int n2,
-                                T* __restrict__ X1, int m0, int m1, int m2, unsigned long long p0,
+__global__ void decimate_kernel(const T* __restrict__ src, unsigned long long s0, unsigned long long s1,
+                                T* __restrict__ dst, int m0, int m1, int m2, unsigned long long p0,
                                 unsigned long long p1) {
   const unsigned long long row = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= (unsigned long long)m0 * m1) return;
   const int lane = threadIdx.x & 31;
   const unsigned long long i = row / (unsigned)m1, j = row % (unsigned)m1;
-  const T* src = x + 2 * i * s0 + 2 * j * s1;
-  T* dst = X1 + i * p0 + j * p1;
-  for (int c = lane; c < m2; c += 32) dst[c] = __ldcs(src + 2 * c);
-  (void)n2;
+  const T* sp = src + 2 * i * s0 + 2 * j * s1;
+  T* dp = dst + i * p0 + j * p1;
+  for (int c = lane; c < m2; c += 32) dp[c] = __ldcs(sp + 2 * c);
 }
 
-int launch_decimate(const Plan& pl, const void* x, void* X1, cudaStream_t s) {
-  const unsigned long long* m = pl.gm[1];
-  const unsigned long long p1 = x1_pitch(pl), p0 = p1 * m[2];
-  const unsigned long long rows = m[1] * m[2];
-  const unsigned blocks = (unsigned)((rows + 7) / 8);
-  if (pl.dtype == SZ3G_F32)
-    SZ3G_LAUNCH(kKDecimate, s,
-                decimate_kernel<float><<<blocks, 256, 0, s>>>((const float*)x, pl.fstride[1], pl.fstride[2],
-                                                              (int)pl.n[3], (float*)X1, (int)m[1], (int)m[2],
-                                                              (int)m[3], p0, p1));
-  else
-    SZ3G_LAUNCH(kKDecimate, s,
-                decimate_kernel<double><<<blocks, 256, 0, s>>>((const double*)x, pl.fstride[1], pl.fstride[2],
-                                                               (int)pl.n[3], (double*)X1, (int)m[1], (int)m[2],
-                                                               (int)m[3], p0, p1));
-  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+// X_k for k = 1..kmax into the pyramid at X (byte offsets xpyr_offset).
+static int launch_decimate(const Plan& pl, const void* x, unsigned char* X, int kmax, cudaStream_t s) {
+  for (int k = 1; k <= kmax; ++k) {
+    const unsigned long long* m = pl.gm[k];
+    const unsigned long long p1 = xk_pitch(pl, k), p0 = p1 * m[2];
+    unsigned long long s0, s1;
+    const void* src;
+    if (k == 1) {
+      src = x;
+      s0 = pl.fstride[1];
+      s1 = pl.fstride[2];
+    } else {
+      src = X + xpyr_offset(pl, k - 1);
+      s1 = xk_pitch(pl, k - 1);
+      s0 = s1 * pl.gm[k - 1][2];
+    }
+    void* dst = X + xpyr_offset(pl, k);
+    const unsigned long long rows = m[1] * m[2];
+    const unsigned blocks = (unsigned)((rows + 7) / 8);
+    if (pl.dtype == SZ3G_F32)
+      SZ3G_LAUNCH(kKDecimate, s,
+                  decimate_kernel<float><<<blocks, 256, 0, s>>>((const float*)src, s0, s1, (float*)dst, (int)m[1],
+                                                                (int)m[2], (int)m[3], p0, p1));
+    else
+      SZ3G_LAUNCH(kKDecimate, s,
+                  decimate_kernel<double><<<blocks, 256, 0, s>>>((const double*)src, s0, s1, (double*)dst, (int)m[1],
+                                                                 (int)m[2], (int)m[3], p0, p1));
+    if (cudaGetLastError() != cudaSuccess) return SZ3G_E_CUDA;
+  }
+  return SZ3G_OK;
 }
 
 template <typename T>
 static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* const* R, uint32_t* hist, DevState* st,
-                          void* X1, cudaStream_t s) {
+                          void* X, cudaStream_t s) {
   const int kc = coarse_grid(pl);
   LevelArgs<T> a{};
   a.x = x;
@@ -1121,21 +1135,20 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
   a.Rout = kc == 0 ? nullptr : (T*)R[kc];  // the finest grid's reconstruction is not kept
   int rc = run_coarse<T, true>(pl, kc, a, s);
   if (rc) return rc;
-  // levels on G_1 and coarser read the decimated copy
-  const bool dec = X1 && kc >= 2;
+  // levels on G_1 and coarser read the decimated pyramid
+  const bool dec = X && kc >= 2;
   if (dec) {
-    rc = launch_decimate(pl, x, X1, s);
+    rc = launch_decimate(pl, x, (unsigned char*)X, kc - 1, s);
     if (rc) return rc;
   }
-  const unsigned long long p1 = x1_pitch(pl), p0 = p1 * pl.gm[1][2];
   for (int k = kc - 1; k >= 0; --k) {
     a.Rc = (const T*)R[k + 1];
     a.Rout = k == 0 ? nullptr : (T*)R[k];
     if (dec && k >= 1) {
-      a.x = (const T*)X1;
-      a.xs[0] = p0 << (k - 1);
-      a.xs[1] = p1 << (k - 1);
-      a.xs[2] = 1ull << (k - 1);
+      a.x = (const T*)((unsigned char*)X + xpyr_offset(pl, k));
+      a.xs[1] = xk_pitch(pl, k);
+      a.xs[0] = a.xs[1] * pl.gm[k][2];
+      a.xs[2] = 1;
     } else {
       a.x = x;
       for (int q = 0; q < 3; ++q) a.xs[q] = pl.fstride[q + 1] << k;
@@ -1173,9 +1186,9 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
 }
 
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                          DevState* st, void* X1, cudaStream_t s) {
-  if (pl.dtype == SZ3G_F32) return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, X1, s);
-  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, X1, s);
+                          DevState* st, void* X, cudaStream_t s) {
+  if (pl.dtype == SZ3G_F32) return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, X, s);
+  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, X, s);
 }
 
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
