@@ -258,13 +258,16 @@ int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, voi
   DevState* st = (DevState*)(ws + L.st);
   *st_out = st;
   SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.codes, s));  // state, histogram, tables, look-back status
-  SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s));
+  void* X = xpyr_bytes(pl) ? ws + L.x1 : nullptr;
+  bool x1_ready = false;
+  SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s, X,
+                           &x1_ready));
   void* R[34];
   for (int k = 0; k <= pl.L; ++k) R[k] = (k == 0 && level_path_ok(pl)) ? nullptr : ws + L.R[k];
   uint16_t* codes = (uint16_t*)(ws + L.codes);
   uint32_t* hist = (uint32_t*)(ws + L.hist);
   uint32_t* table = (uint32_t*)(ws + L.table);
-  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, xpyr_bytes(pl) ? ws + L.x1 : nullptr, s));
+  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, X, x1_ready, s));
   SZ3G_TRY(launch_codebook(hist, 2 * pl.radius, table, nullptr, nullptr, st, ws + L.cb, (unsigned char*)d_out,
                            out_capacity, pl.esz, s));
   PassMap map;  // kernel parameter, copied at launch
@@ -459,7 +462,7 @@ int sz3g_predict_quantize(const sz3g_params* p, const void* d_in, uint16_t* d_co
   SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s));
   void* R[34];
   for (int k = 0; k <= pl.L; ++k) R[k] = (k == 0 && level_path_ok(pl)) ? nullptr : ws + L.R[k];
-  SZ3G_TRY(launch_quantize_levels(pl, d_in, d_codes, R, d_hist, st, xpyr_bytes(pl) ? ws + L.x1 : nullptr, s));
+  SZ3G_TRY(launch_quantize_levels(pl, d_in, d_codes, R, d_hist, st, xpyr_bytes(pl) ? ws + L.x1 : nullptr, false, s));
   PassMap map;
   make_pass_map(pl, &map);
   SZ3G_TRY(launch_compact_unpred(pl, d_codes, d_in, &map, ws + L.enc, (uint32_t*)(ws + L.table), d_unpred, st, s));

@@ -223,10 +223,12 @@ __device__ __forceinline__ double bits_to<double>(unsigned long long b) {
 // ---------------------------------------------------------------------------
 // k_interp.cu
 size_t range_scratch_bytes(const Plan& pl);
+// REL with X1 (the first level of the decimated pyramid): the range pass
+// also writes X_1 when the field's rows allow it (*wrote_x1).
 int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratch, size_t scratch_bytes,
-                    int eb_mode, double eb, cudaStream_t s);
+                    int eb_mode, double eb, cudaStream_t s, void* X1 = nullptr, bool* wrote_x1 = nullptr);
 int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R,
-                           uint32_t* hist, DevState* st, void* X1, cudaStream_t s);
+                           uint32_t* hist, DevState* st, void* X1, bool x1_ready, cudaStream_t s);
 int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred,
                           unsigned long long n_unpred, const unsigned long long* zunit,
                           void* const* R, void* d_out, DevState* st, unsigned long long ebT_bits,
@@ -239,7 +241,7 @@ int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unp
 extern int g_level_cta_cap;
 bool level_path_ok(const Plan& pl);
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                          DevState* st, void* X1, cudaStream_t s);
+                          DevState* st, void* X1, bool x1_ready, cudaStream_t s);
 // Decimated copies of the field X_k = x[::2^k, ::2^k, ::2^k] over G_k, k >= 1
 // (rows pitched to 16 bytes, one after another): the inputs of the coarser
 // levels; xpyr_bytes is 0 when the level path does not use them.

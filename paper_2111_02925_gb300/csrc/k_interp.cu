@@ -95,13 +95,26 @@ __device__ __forceinline__ void block_minmax(T& mn, T& mx, T* smn, T* smx) {
   }
 }
 
+// Where the range pass also writes the decimated copy X_1 = x[::2, ::2, ::2]
+// (rows of the padded 3-D view, each a whole number of 16-byte vectors).
+template <typename T>
+struct RangeRows {
+  T* X1;                      // null: flat pass, no copy
+  unsigned long long a1, a2;  // extents of axes 1 and 2 (rows: a0 x a1, row length a2)
+  unsigned long long rows;    // a0 * a1
+  unsigned long long p0, p1;  // X_1 strides (elements) along axes 0 and 1
+};
+
 // Min / max / finiteness of the field with 16-byte loads (the field is 16-byte
 // aligned), four in flight per thread; each block writes its partial result
-// and the last block to finish reduces them and sets the bound.
+// and the last block to finish reduces them and sets the bound.  With
+// rows.X1 the field is walked row by row (a warp per row), and the rows with
+// even coordinates on axes 0 and 1 also write their even elements to X_1.
 template <typename T>
 __global__ void __launch_bounds__(kRangeThreads) range_partial_kernel(const T* __restrict__ x,
                                                                        unsigned long long n, T* part,
-                                                                       DevState* st, int eb_mode, double eb) {
+                                                                       DevState* st, int eb_mode, double eb,
+                                                                       const RangeRows<T> rows) {
   using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   constexpr int kPer = 16 / sizeof(T);
   T mn = x[0], mx = x[0];
@@ -119,17 +132,49 @@ __global__ void __launch_bounds__(kRangeThreads) range_partial_kernel(const T* _
     }
   };
   const V* xv = reinterpret_cast<const V*>(x);
-  const unsigned long long nv = n / kPer;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + 3 * stride < nv; i += 4 * stride) {
-    const V v0 = __ldcs(xv + i), v1 = __ldcs(xv + i + stride), v2 = __ldcs(xv + i + 2 * stride),
-            v3 = __ldcs(xv + i + 3 * stride);
-    take_v(v0); take_v(v1); take_v(v2); take_v(v3);
+  if (rows.X1) {
+    const unsigned long long vpr = rows.a2 / kPer;  // vectors per row
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long r = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+         r < rows.rows; r += nw) {
+      const unsigned long long i = r / rows.a1, j = r - i * rows.a1;
+      const V* rp = xv + r * vpr;
+      T* dp = ((i | j) & 1) ? nullptr : rows.X1 + (i >> 1) * rows.p0 + (j >> 1) * rows.p1;
+      for (unsigned long long v0 = lane; v0 < vpr; v0 += 128) {
+        V q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (v0 + 32 * u < vpr) q[u] = __ldcs(rp + v0 + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned long long v = v0 + 32 * u;
+          if (v >= vpr) continue;
+          take_v(q[u]);
+          if (dp) {
+            if constexpr (sizeof(T) == 4) {
+              *reinterpret_cast<float2*>(dp + 2 * v) = make_float2(q[u].x, q[u].z);
+            } else {
+              dp[v] = q[u].x;
+            }
+          }
+        }
+      }
+    }
+  } else {
+    const unsigned long long nv = n / kPer;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < nv; i += 4 * stride) {
+      const V v0 = __ldcs(xv + i), v1 = __ldcs(xv + i + stride), v2 = __ldcs(xv + i + 2 * stride),
+              v3 = __ldcs(xv + i + 3 * stride);
+      take_v(v0); take_v(v1); take_v(v2); take_v(v3);
+    }
+    for (; i < nv; i += stride) take_v(__ldcs(xv + i));
+    for (unsigned long long t = nv * kPer + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += stride)
+      take(x[t]);
   }
-  for (; i < nv; i += stride) take_v(__ldcs(xv + i));
-  for (unsigned long long t = nv * kPer + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride)
-    take(x[t]);
   __shared__ T smn[kRangeThreads / 32], smx[kRangeThreads / 32];
   __shared__ bool s_last;
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->flags, kFlagNonFinite);
@@ -164,21 +209,44 @@ __global__ void eb_kernel(int eb_mode, double eb, DevState* st) {
 size_t range_scratch_bytes(const Plan&) { return (size_t)kRangeBlocks * 2 * 8; }
 
 int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratch, size_t scratch_bytes,
-                    int eb_mode, double eb, cudaStream_t s) {
+                    int eb_mode, double eb, cudaStream_t s, void* X1, bool* wrote_x1) {
   if (scratch_bytes < range_scratch_bytes(pl)) return SZ3G_E_CAPACITY;
+  if (wrote_x1) *wrote_x1 = false;
   int nparts = 1;
   if (eb_mode == SZ3G_EB_REL) {
     const int per = 16 / pl.esz;
     unsigned long long want = (pl.N / per + kRangeThreads * 4 - 1) / (kRangeThreads * 4);
     nparts = (int)(want < kRangeBlocks ? (want ? want : 1) : kRangeBlocks);
-    if (pl.dtype == SZ3G_F32)
+    // the decimated copy comes with the pass when rows are whole vectors
+    const bool rows_ok = X1 && pl.n[0] == 1 && pl.L >= 1 && pl.n[3] % (unsigned long long)per == 0;
+    if (pl.dtype == SZ3G_F32) {
+      RangeRows<float> r{};
+      if (rows_ok) {
+        r.X1 = (float*)X1;
+        r.a1 = pl.n[2];
+        r.a2 = pl.n[3];
+        r.rows = pl.n[1] * pl.n[2];
+        r.p1 = xk_pitch(pl, 1);
+        r.p0 = r.p1 * pl.gm[1][2];
+      }
       SZ3G_LAUNCH(kKRange, s,
                   range_partial_kernel<float><<<nparts, kRangeThreads, 0, s>>>((const float*)d_in, pl.N,
-                                                                                (float*)scratch, st, eb_mode, eb));
-    else
+                                                                                (float*)scratch, st, eb_mode, eb, r));
+    } else {
+      RangeRows<double> r{};
+      if (rows_ok) {
+        r.X1 = (double*)X1;
+        r.a1 = pl.n[2];
+        r.a2 = pl.n[3];
+        r.rows = pl.n[1] * pl.n[2];
+        r.p1 = xk_pitch(pl, 1);
+        r.p0 = r.p1 * pl.gm[1][2];
+      }
       SZ3G_LAUNCH(kKRange, s,
                   range_partial_kernel<double><<<nparts, kRangeThreads, 0, s>>>((const double*)d_in, pl.N,
-                                                                                 (double*)scratch, st, eb_mode, eb));
+                                                                                 (double*)scratch, st, eb_mode, eb, r));
+    }
+    if (wrote_x1) *wrote_x1 = rows_ok;
   } else if (pl.dtype == SZ3G_F32) {
     SZ3G_LAUNCH(kKEb, s, eb_kernel<float><<<1, 32, 0, s>>>(eb_mode, eb, st));
   } else {
@@ -408,8 +476,8 @@ static int quantize_levels_t(const Plan& pl, const T* x, uint16_t* codes, void* 
 }
 
 int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                           DevState* st, void* X1, cudaStream_t s) {
-  if (level_path_ok(pl)) return launch_quantize_fused(pl, d_in, codes, R, hist, st, X1, s);
+                           DevState* st, void* X1, bool x1_ready, cudaStream_t s) {
+  if (level_path_ok(pl)) return launch_quantize_fused(pl, d_in, codes, R, hist, st, X1, x1_ready, s);
   if (pl.dtype == SZ3G_F32) return quantize_levels_t<float>(pl, (const float*)d_in, codes, R, hist, st, s);
   return quantize_levels_t<double>(pl, (const double*)d_in, codes, R, hist, st, s);
 }

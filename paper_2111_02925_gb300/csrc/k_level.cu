@@ -1089,41 +1089,70 @@ __global__ void decimate_kernel(const T* __restrict__ src, unsigned long long s0
   for (int c = lane; c < m2; c += 32) dp[c] = __ldcs(sp + 2 * c);
 }
 
-// X_k for k = 1..kmax into the pyramid at X (byte offsets xpyr_offset).
-static int launch_decimate(const Plan& pl, const void* x, unsigned char* X, int kmax, cudaStream_t s) {
-  for (int k = 1; k <= kmax; ++k) {
-    const unsigned long long* m = pl.gm[k];
-    const unsigned long long p1 = xk_pitch(pl, k), p0 = p1 * m[2];
-    unsigned long long s0, s1;
-    const void* src;
-    if (k == 1) {
-      src = x;
-      s0 = pl.fstride[1];
-      s1 = pl.fstride[2];
-    } else {
-      src = X + xpyr_offset(pl, k - 1);
-      s1 = xk_pitch(pl, k - 1);
-      s0 = s1 * pl.gm[k - 1][2];
+// X_2 .. X_kmax from X_1 in one pass: one warp per row of X_2; a point of X_2
+// whose coordinates are multiples of 2^(k-2) is also the point of X_k.
+struct PyrDesc {
+  int kmax;
+  int m[32][3];                    // extents of G_k
+  unsigned long long off[32];      // element offset of X_k
+  unsigned long long p0[32], p1[32];
+};
+
+template <typename T>
+__global__ void pyramid_kernel(T* __restrict__ X, const __grid_constant__ PyrDesc d) {
+  const unsigned long long row = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= (unsigned long long)d.m[2][0] * d.m[2][1]) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long i = row / (unsigned)d.m[2][1], j = row % (unsigned)d.m[2][1];
+  const T* src = X + d.off[1] + 2 * i * d.p0[1] + 2 * j * d.p1[1];
+  for (int c = lane; c < d.m[2][2]; c += 32) {
+    const T v = src[2 * c];
+    X[d.off[2] + i * d.p0[2] + j * d.p1[2] + c] = v;
+    for (int k = 3; k <= d.kmax; ++k) {
+      const int sh = k - 2;
+      if (((i | j | (unsigned long long)c) & ((1ull << sh) - 1)) != 0) break;
+      X[d.off[k] + (i >> sh) * d.p0[k] + (j >> sh) * d.p1[k] + (c >> sh)] = v;
     }
-    void* dst = X + xpyr_offset(pl, k);
-    const unsigned long long rows = m[1] * m[2];
-    const unsigned blocks = (unsigned)((rows + 7) / 8);
+  }
+}
+
+// X_1 (unless the range pass wrote it) and X_2 .. X_kmax into the pyramid.
+static int launch_decimate(const Plan& pl, const void* x, unsigned char* X, int kmax, bool x1_ready, cudaStream_t s) {
+  if (!x1_ready) {
+    const unsigned long long* m = pl.gm[1];
+    const unsigned long long p1 = xk_pitch(pl, 1), p0 = p1 * m[2];
+    const unsigned blocks = (unsigned)((m[1] * m[2] + 7) / 8);
     if (pl.dtype == SZ3G_F32)
       SZ3G_LAUNCH(kKDecimate, s,
-                  decimate_kernel<float><<<blocks, 256, 0, s>>>((const float*)src, s0, s1, (float*)dst, (int)m[1],
-                                                                (int)m[2], (int)m[3], p0, p1));
+                  decimate_kernel<float><<<blocks, 256, 0, s>>>((const float*)x, pl.fstride[1], pl.fstride[2],
+                                                                (float*)X, (int)m[1], (int)m[2], (int)m[3], p0, p1));
     else
       SZ3G_LAUNCH(kKDecimate, s,
-                  decimate_kernel<double><<<blocks, 256, 0, s>>>((const double*)src, s0, s1, (double*)dst, (int)m[1],
-                                                                 (int)m[2], (int)m[3], p0, p1));
+                  decimate_kernel<double><<<blocks, 256, 0, s>>>((const double*)x, pl.fstride[1], pl.fstride[2],
+                                                                 (double*)X, (int)m[1], (int)m[2], (int)m[3], p0, p1));
     if (cudaGetLastError() != cudaSuccess) return SZ3G_E_CUDA;
   }
-  return SZ3G_OK;
+  if (kmax < 2) return SZ3G_OK;
+  PyrDesc d;
+  memset(&d, 0, sizeof(d));
+  d.kmax = kmax;
+  for (int k = 1; k <= kmax && k < 32; ++k) {
+    for (int q = 0; q < 3; ++q) d.m[k][q] = (int)pl.gm[k][q + 1];
+    d.off[k] = xpyr_offset(pl, k) / pl.esz;
+    d.p1[k] = xk_pitch(pl, k);
+    d.p0[k] = d.p1[k] * pl.gm[k][2];
+  }
+  const unsigned blocks = (unsigned)(((unsigned long long)d.m[2][0] * d.m[2][1] + 7) / 8);
+  if (pl.dtype == SZ3G_F32)
+    SZ3G_LAUNCH(kKDecimate, s, pyramid_kernel<float><<<blocks, 256, 0, s>>>((float*)X, d));
+  else
+    SZ3G_LAUNCH(kKDecimate, s, pyramid_kernel<double><<<blocks, 256, 0, s>>>((double*)X, d));
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
 template <typename T>
 static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* const* R, uint32_t* hist, DevState* st,
-                          void* X, cudaStream_t s) {
+                          void* X, bool x1_ready, cudaStream_t s) {
   const int kc = coarse_grid(pl);
   LevelArgs<T> a{};
   a.x = x;
@@ -1138,7 +1167,7 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
   // levels on G_1 and coarser read the decimated pyramid
   const bool dec = X && kc >= 2;
   if (dec) {
-    rc = launch_decimate(pl, x, (unsigned char*)X, kc - 1, s);
+    rc = launch_decimate(pl, x, (unsigned char*)X, kc - 1, x1_ready, s);
     if (rc) return rc;
   }
   for (int k = kc - 1; k >= 0; --k) {
@@ -1186,9 +1215,9 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
 }
 
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                          DevState* st, void* X, cudaStream_t s) {
-  if (pl.dtype == SZ3G_F32) return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, X, s);
-  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, X, s);
+                          DevState* st, void* X, bool x1_ready, cudaStream_t s) {
+  if (pl.dtype == SZ3G_F32) return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, X, x1_ready, s);
+  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, X, x1_ready, s);
 }
 
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,

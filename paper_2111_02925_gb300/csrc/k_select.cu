@@ -296,8 +296,7 @@ __global__ void sel_features_kernel(const SelAcc* acc, const SelLevel* gls, int 
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
-int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratch, size_t scratch_bytes, int eb_mode,
-                    double eb, cudaStream_t s);
+
 size_t range_scratch_bytes(const Plan& pl);
 
 struct SelScratch {
