@@ -37,6 +37,10 @@ namespace sz3g {
 // current tile is computed).  Measured on 512^3: many small single-stage CTAs
 // (other CTAs of the SM compute while one waits for its copies) beat fewer,
 // double-buffered ones -- compress 0.62 vs 0.73 ms, recover 0.48 vs 0.53 ms.
+// Recover stages the tile's code rows with 16-byte cp.async pieces spread
+// over the threads (true) or one bulk copy per row (false).
+constexpr bool kCodeCpAsync = true;
+
 template <bool COMP>
 struct FineThreads {
   static constexpr int kN = COMP ? 256 : 128, kMinBlocks = COMP ? 4 : 8, kStages = 1;
@@ -255,13 +259,40 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
     tile_origin(tile, A0, A1, A2);
     if (tid == 0) {
       fence_proxy_async_smem();
-      if (COMP) {
+      if (COMP || kCodeCpAsync) {
         mbar_expect_tx(&bar[b], d.tensor_bytes);
+      }
+      if (COMP) {
         tma_load_3d(Xs + b * XB, &tmx, A2 - 4, A1 - 2, A0, &bar[b]);
       }
       tma_load_3d(Cs + b * CB, &tmc, A2 / 2 - 4, A1 / 2 - 1, S::kHas0 ? A0 / 2 - 1 : 0, &bar[b]);
     }
-    if (!COMP && tid < S::kR2 + S::kR1 + S::kR0) {
+    if (!COMP && kCodeCpAsync) {
+      // every 16-byte piece of every staged row, spread over the threads
+      constexpr int kItems = S::kR2 * (S::kL2 / 8) + (S::kR1 + S::kR0) * (S::kL01 / 8);
+      for (int it = tid; it < kItems; it += kFineThreads) {
+        int r, q;
+        if (it < S::kR2 * (S::kL2 / 8)) {
+          r = it / (S::kL2 / 8);
+          q = it % (S::kL2 / 8);
+        } else {
+          const int u = it - S::kR2 * (S::kL2 / 8);
+          r = S::kR2 + u / (S::kL01 / 8);
+          q = u % (S::kL01 / 8);
+        }
+        int which, slot;
+        bool valid;
+        const long long c0 = row_c0(A0, A1, A2, r, which, slot, valid);
+        if (valid) {
+          long long al;
+          int o;
+          code_row(c0, &al, &o);
+          const uint32_t d16 = (uint32_t)__cvta_generic_to_shared(Ks + b * KB + slot + 8 * q);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d16), "l"(a.codes + al + 8 * q) : "memory");
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    } else if (!COMP && tid < S::kR2 + S::kR1 + S::kR0) {
       int which, slot;
       bool valid;
       const long long c0 = row_c0(A0, A1, A2, tid, which, slot, valid);
@@ -277,7 +308,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
     }
   };
   auto finish_issue = [&](int b) {  // after a barrier that follows issue(b)
-    if (!COMP && tid == 0) {
+    if (!COMP && tid == 0 && !kCodeCpAsync) {
       mbar_expect_tx(&bar[b], d.tensor_bytes + s_bytes[b]);
       s_bytes[b] = 0;
     }
@@ -297,7 +328,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
     const bool has_next = ST == 2 && next < d.ntiles;
     if (ST == 1) {  // the buffer is free: the previous tile ended with a barrier
       issue(tile, 0);
-      if (!COMP) {
+      if (!COMP && !kCodeCpAsync) {
         __syncthreads();
         finish_issue(0);
       }
@@ -315,6 +346,10 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
         }
       }
       if (done) phase[b] ^= 1u;
+      if (!COMP && kCodeCpAsync) {
+        if (ST == 2 && has_next) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
     }
     __syncthreads();
     if (s_timeout) {
