@@ -14,7 +14,7 @@ namespace sz3g {
 
 constexpr int kMaxPasses = 1 + 4 * 31;  // anchor + up to 4 passes on each of 31 levels
 constexpr int kSyms = 65536;            // alphabet of uint16 codes
-constexpr int kLutBits = 12;            // direct decode table: first 12 bits of a codeword
+constexpr int kLutBits = 13;            // direct decode table: first 13 bits of a codeword
 #define SZ3G_SUBBLOCK 512               // codes per decode sub-block inside a chunk
 
 // Status bits raised on the device and read back once per call.

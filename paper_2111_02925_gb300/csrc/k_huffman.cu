@@ -1016,11 +1016,14 @@ int launch_finalize(const Plan& pl, const sz3g_params* p, DevState* st, unsigned
 // Decoder.
 // ---------------------------------------------------------------------------
 struct DecTables {
-  uint32_t lut[1 << kLutBits];  // len << 16 | sym, 0 = longer than 12 bits / no codeword
-  uint32_t fc[SZ3G_LMAX + 2], cnt[SZ3G_LMAX + 2], start[SZ3G_LMAX + 2];
+  uint32_t lut[1 << kLutBits];   // window of kLutBits bits -> len << 16 | sym; 0 = a longer codeword
+  uint32_t lim[SZ3G_LMAX + 2];   // (fc[L] + cnt[L]) << (LMAX - L): an LMAX-bit window below it
+                                 // starts with a codeword of at most L bits
+  uint32_t base[SZ3G_LMAX + 2];  // start[L] - fc[L] (mod 2^32): codeword c of length L is symbol
+                                 // sorted[c + base[L]]
   uint32_t n_used;
   uint32_t pad;
-  unsigned long long keys[kSyms];  // sort scratch
+  unsigned long long keys[kSyms];  // used symbols (length << 16 | symbol) in symbol order
   uint16_t sorted[kSyms];          // symbols by (length, symbol)
 };
 
@@ -1040,7 +1043,6 @@ __global__ void __launch_bounds__(kCbThreads) decode_tables_kernel(const unsigne
     s_kraft = 0;
   }
   if (tid <= SZ3G_LMAX + 1) s_cnt[tid] = 0;
-  for (int i = tid; i < (1 << kLutBits); i += kCbThreads) T->lut[i] = 0;
   __syncthreads();
   unsigned long long* keys;
   int K;
@@ -1084,39 +1086,69 @@ __global__ void __launch_bounds__(kCbThreads) decode_tables_kernel(const unsigne
     if (L >= 1 && L <= SZ3G_LMAX) atomicAdd(&s_kraft, 1ull << (SZ3G_LMAX - L));
     if (L >= 1 && L <= SZ3G_LMAX) atomicAdd(&s_cnt[L], 1u);
   }
-  const int P = pow2_at_least(K);
-  for (int i = K + tid; i < P; i += kCbThreads) keys[i] = ~0ull;
   __syncthreads();
   const bool kraft_ok = K == 1 ? s_kraft == (1ull << (SZ3G_LMAX - 1)) : s_kraft == (1ull << SZ3G_LMAX);
   if (s_bad || !kraft_ok) {
     if (tid == 0) atomicOr(&st->flags, kFlagCorrupt);
     return;
   }
-  block_bitonic_sort(keys, P);
+  __shared__ uint32_t s_start[SZ3G_LMAX + 2], s_base[SZ3G_LMAX + 2], s_lim[SZ3G_LMAX + 2], s_cb[SZ3G_LMAX + 2];
+  __shared__ uint32_t s_wc[32][SZ3G_LMAX + 2];  // per-warp counts, then offsets, of each length in a tile
   if (tid == 0) {
     uint32_t start = 0, fc = 0;
     for (int L = 1; L <= SZ3G_LMAX; ++L) {
       if (L > 1) fc = (fc + s_cnt[L - 1]) << 1;
-      T->fc[L] = fc;
-      T->cnt[L] = s_cnt[L];
-      T->start[L] = start;
+      s_start[L] = start;
+      T->base[L] = s_cb[L] = start - fc;
+      T->lim[L] = s_lim[L] = (fc + s_cnt[L]) << (SZ3G_LMAX - L);
       start += s_cnt[L];
     }
     T->n_used = (uint32_t)K;
   }
-  __syncthreads();
-  for (int i = tid; i < K; i += kCbThreads) {
-    const uint32_t L = (uint32_t)(keys[i] >> 16), s = (uint32_t)(keys[i] & 0xffffu);
-    T->sorted[i] = (uint16_t)s;
-    if (L <= kLutBits) {
-      uint32_t fc = 0, start = 0, c = 0;
-      // recompute this length's first code and start (tables written by thread 0)
-      fc = T->fc[L];
-      start = T->start[L];
-      c = fc + ((uint32_t)i - start);
-      const uint32_t lo = c << (kLutBits - L), nfill = 1u << (kLutBits - L);
-      for (uint32_t k = 0; k < nfill; ++k) T->lut[lo + k] = (L << 16) | s;
+  if (tid <= SZ3G_LMAX + 1) s_base[tid] = 0;
+  // Symbols ordered by (length, symbol): the keys are in symbol order, so a
+  // stable counting sort on the length gives the order.  Tiles of one key
+  // per thread: a key's rank is its length's start, plus the keys of that
+  // length in earlier tiles (s_base), earlier warps of the tile and earlier
+  // lanes of its warp.
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int t0 = 0; t0 < K; t0 += kCbThreads) {
+    for (int i = tid; i < 32 * (SZ3G_LMAX + 2); i += kCbThreads) (&s_wc[0][0])[i] = 0;
+    __syncthreads();
+    const int i = t0 + tid;
+    const unsigned long long key = i < K ? keys[i] : 0ull;
+    const uint32_t L = (uint32_t)(key >> 16), sym = (uint32_t)(key & 0xffffu);  // L = 0: no key
+    const unsigned peers = __match_any_sync(0xffffffffu, L);
+    if (lane == __ffs(peers) - 1) s_wc[warp][L] = (uint32_t)__popc(peers);
+    __syncthreads();
+    if (warp >= 1 && warp <= SZ3G_LMAX) {  // warp w scans the warps' counts of length w
+      const uint32_t c = s_wc[lane][warp], base = s_base[warp];
+      uint32_t x = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      s_wc[lane][warp] = base + x - c;
+      __syncwarp();
+      if (lane == 31) s_base[warp] = base + x;
     }
+    __syncthreads();
+    if (L) {
+      const uint32_t r = s_start[L] + s_wc[warp][L] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+      T->sorted[r] = (uint16_t)sym;
+    }
+    __syncthreads();
+  }
+  // Direct table.  The windows that start with a codeword of length L are
+  // the range [lim[L-1], lim[L]) (left-justified), so a window finds its
+  // length by a short walk and its symbol through the (length, symbol) order.
+  for (int w = tid; w < (1 << kLutBits); w += kCbThreads) {
+    const uint32_t v = (uint32_t)w << (SZ3G_LMAX - kLutBits);
+    uint32_t L = 1;
+    while (L <= (uint32_t)kLutBits && v >= s_lim[L]) ++L;
+    uint32_t e = 0;
+    if (L <= (uint32_t)kLutBits) e = (L << 16) | T->sorted[((uint32_t)w >> (kLutBits - L)) + s_cb[L]];
+    T->lut[w] = e;
   }
 }
 
@@ -1135,23 +1167,54 @@ struct DecArgs {
 };
 
 // One thread decodes one unit: a 512-code sub-block when the stream carries
-// sub-block lengths (its start bit is their sum), else a whole chunk.
-// Large CTAs: the shared-memory lookup table is then held once per many warps,
-// leaving L1 for the per-thread payload streams.
+// sub-block lengths (its start bit is their sum), else a whole chunk.  The
+// length of the next codeword comes from a 16-bit direct table in shared
+// memory (longer codewords: comparisons with the left-justified limits), its
+// symbol from the (length, symbol) order, so only the table read and the
+// shift are on the thread's serial path.  Payload words reach a per-thread
+// ring in shared memory by cp.async kDecAhead words before they are used.
+// Large CTAs: the 64 KiB table is held once per sixteen warps.
 constexpr int kDecThreads = 512;
+constexpr bool kDecRingFetch = true;  // payload words by cp.async into a shared ring (else registers)
+constexpr int kDecRing = 8, kDecAhead = 6;
+constexpr int kDecSortedSmem = 16384;  // symbols kept in shared memory (more: read from global)
+constexpr size_t kDecOffRing = (size_t)4 << kLutBits;
+constexpr size_t kDecOffSorted = kDecOffRing + (kDecRingFetch ? (size_t)kDecThreads * kDecRing * 4 : 0);
+constexpr size_t kDecodeSmem = kDecOffSorted + (size_t)kDecSortedSmem * 2;
+
+__device__ __forceinline__ void dec_fetch(uint32_t* slot, const uint32_t* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(slot);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n\tcp.async.commit_group;" ::"r"(d), "l"(src) : "memory");
+}
 
 __global__ void __launch_bounds__(kDecThreads) decode_kernel(const DecArgs a) {
-  if (a.st->flags & kFlagCorrupt) return;  // tables or chunk table rejected
-  __shared__ uint32_t lut[1 << kLutBits];
-  __shared__ uint32_t fc[SZ3G_LMAX + 2], cnt[SZ3G_LMAX + 2], start[SZ3G_LMAX + 2];
-  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) lut[i] = a.T->lut[i];
-  if (threadIdx.x <= SZ3G_LMAX + 1) {
-    fc[threadIdx.x] = a.T->fc[threadIdx.x];
-    cnt[threadIdx.x] = a.T->cnt[threadIdx.x];
-    start[threadIdx.x] = a.T->start[threadIdx.x];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ uint32_t s_lim[SZ3G_LMAX + 2], s_base[SZ3G_LMAX + 2];
+  __shared__ int s_skip;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_skip = (a.st->flags & kFlagCorrupt) != 0;  // tables or chunk table rejected
+  __syncthreads();
+  if (s_skip) return;
+  const uint32_t n_used = a.T->n_used;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.T->lut);
+    uint4* dst = reinterpret_cast<uint4*>(dsm);
+    for (int i = tid; i < (1 << kLutBits) / 4; i += kDecThreads) dst[i] = src[i];
+    if (n_used <= (uint32_t)kDecSortedSmem) {
+      uint16_t* ds = reinterpret_cast<uint16_t*>(dsm + kDecOffSorted);
+      for (uint32_t i = tid; i < n_used; i += kDecThreads) ds[i] = a.T->sorted[i];
+    }
+    if (tid <= SZ3G_LMAX + 1) {
+      s_lim[tid] = a.T->lim[tid];
+      s_base[tid] = a.T->base[tid];
+    }
   }
   __syncthreads();
-  const unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t* lut = reinterpret_cast<const uint32_t*>(dsm);
+  const bool sorted_smem = n_used <= (uint32_t)kDecSortedSmem;
+  const uint16_t* s_sorted = reinterpret_cast<const uint16_t*>(dsm + kDecOffSorted);
+  uint32_t* ring = reinterpret_cast<uint32_t*>(dsm + kDecOffRing) + tid;  // slot k at ring[k * kDecThreads]
+  const unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + tid;
   if (u >= a.n_chunks * a.upc) return;
   const unsigned long long j = u / a.upc;
   const uint32_t b = (uint32_t)(u - j * a.upc);
@@ -1175,25 +1238,42 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(const DecArgs a) {
     return;
   }
   const uint32_t* wp = a.words + a.woff[j];
-  // bit buffer: `buf` holds nb valid bits at the top.  The next three payload
-  // words are held in w1..w3; a refill shifts w1 in and loads the word after
-  // w3 into a register that is only read three refills later, so a load is
-  // consumed some fifteen codes after it was issued.  Loads past the chunk
-  // read its last word again: a correct code never depends on bits after its
-  // own (canonical codes are prefix-free), and a decode that runs past the
-  // chunk is caught by the bit count at the end.
-  const uint32_t last = nw ? nw - 1 : 0;
-  uint32_t wi = (uint32_t)(bit0 >> 5);  // index of the word held in w1
-  uint32_t w1 = __ldg(wp + min(wi, last)), w2 = __ldg(wp + min(wi + 1, last)), w3 = __ldg(wp + min(wi + 2, last));
-  unsigned long long buf = (unsigned long long)w1 << (32 + (int)(bit0 & 31));
+  // Bit buffer: `buf` holds nb valid bits at the top.  Word k of the chunk
+  // is fetched into ring slot k % kDecRing when word k - kDecAhead is taken
+  // (one commit group per word, so the oldest group is the word taken next).
+  // Fetches past the chunk read its last word again: a correct code never
+  // depends on bits after its own (canonical codes are prefix-free), and a
+  // decode that runs past the chunk is caught by the bit count at the end.
+  const uint32_t last = nw - 1;
+  uint32_t wi = (uint32_t)(bit0 >> 5);  // next word to take
+  uint32_t q1 = 0, q2 = 0, q3 = 0;      // register queue (kDecRingFetch false)
+  if constexpr (kDecRingFetch) {
+#pragma unroll
+    for (int k = 0; k < kDecAhead; ++k) dec_fetch(ring + ((wi + k) % kDecRing) * kDecThreads, wp + min(wi + k, last));
+  } else {
+    q1 = __ldg(wp + min(wi, last));
+    q2 = __ldg(wp + min(wi + 1, last));
+    q3 = __ldg(wp + min(wi + 2, last));
+  }
+  auto take = [&]() -> uint32_t {
+    uint32_t w;
+    if constexpr (kDecRingFetch) {
+      asm volatile("cp.async.wait_group %0;" ::"n"(kDecAhead - 1) : "memory");
+      w = ring[(wi % kDecRing) * kDecThreads];
+      dec_fetch(ring + ((wi + kDecAhead) % kDecRing) * kDecThreads, wp + min(wi + kDecAhead, last));
+    } else {
+      w = q1;
+      q1 = q2;
+      q2 = q3;
+      q3 = __ldg(wp + min(wi + 3, last));
+    }
+    ++wi;
+    return w;
+  };
+  unsigned long long buf = (unsigned long long)take() << (32 + (int)(bit0 & 31));
   int nb = 32 - (int)(bit0 & 31);
-  ++wi;
-  w1 = w2;
-  w2 = w3;
-  w3 = __ldg(wp + min(wi + 2, last));
   uint32_t zeros = 0;
   uint16_t* out = a.codes + j * a.chunk;
-  const uint32_t n_used = a.T->n_used;
   for (uint32_t i = c0; i < c1; i += 8) {  // c0 is a multiple of 8
     if (i != c0 && (i & (SZ3G_SUBBLOCK - 1)) == 0) {  // whole-chunk units count per sub-block
       a.zcnt[j * a.nsb + ((i >> 9) - 1)] = zeros;
@@ -1205,31 +1285,22 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(const DecArgs a) {
     for (uint32_t q = 0; q < 8; ++q) {
       if (q < m) {
         if (nb <= 32) {
-          buf |= (unsigned long long)w1 << (32 - nb);
+          buf |= (unsigned long long)take() << (32 - nb);
           nb += 32;
-          ++wi;
-          w1 = w2;
-          w2 = w3;
-          w3 = __ldg(wp + min(wi + 2, last));
         }
         const uint32_t e = lut[(uint32_t)(buf >> (64 - kLutBits))];
         uint32_t L = e >> 16, sym = e & 0xffffu;
-        if (L == 0) {  // longer than kLutBits: canonical first-code comparison
-          for (uint32_t l = kLutBits + 1; l <= SZ3G_LMAX; ++l) {
-            const uint32_t v = (uint32_t)(buf >> (64 - l));
-            if (v - fc[l] < cnt[l]) {
-              const uint32_t k = start[l] + (v - fc[l]);
-              if (k < n_used) {
-                L = l;
-                sym = a.T->sorted[k];
-              }
-              break;
-            }
+        if (L == 0) {  // a codeword longer than kLutBits: the limits give its length
+          const uint32_t v = (uint32_t)(buf >> (64 - SZ3G_LMAX));
+          L = kLutBits + 1;
+#pragma unroll
+          for (int l = kLutBits + 1; l < SZ3G_LMAX; ++l) L += v >= s_lim[l];
+          const uint32_t k = (uint32_t)(buf >> (64 - L)) + s_base[L];
+          if (v >= s_lim[SZ3G_LMAX] || k >= n_used) {
+            bad = true;
+            break;
           }
-        }
-        if (L == 0) {
-          bad = true;
-          break;
+          sym = sorted_smem ? s_sorted[k] : __ldg(a.T->sorted + k);
         }
         buf <<= L;
         nb -= (int)L;
@@ -1244,8 +1315,11 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(const DecArgs a) {
       for (uint32_t q = 0; q < m; ++q) out[i + q] = (uint16_t)(pk[q >> 1] >> (16 * (q & 1)));
     }
   }
+  // no copy may land in shared memory after the thread has left
+  if constexpr (kDecRingFetch) asm volatile("cp.async.wait_all;" ::: "memory");
   if (!bad) {
-    const unsigned long long used = 32ull * wi - (unsigned long long)nb;  // bits consumed from the chunk start
+    // bits consumed from the chunk start: words taken, less the bits still buffered
+    const unsigned long long used = 32ull * wi - (unsigned long long)nb;
     a.zcnt[j * a.nsb + ((c1 - 1) >> 9)] = zeros;
     // the recorded sub-block boundary must be exactly where decoding ended
     if (sb && a.unit == SZ3G_SUBBLOCK && b + 1 < a.nsb && used != bit0 + sb[b]) bad = true;
@@ -1292,7 +1366,11 @@ int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, cons
   a.zcnt = zcnt;
   a.st = st;
   const unsigned long long threads = n_chunks * a.upc;
-  SZ3G_LAUNCH(kKDecode, s, decode_kernel<<<(unsigned)((threads + kDecThreads - 1) / kDecThreads), kDecThreads, 0, s>>>(a));
+  if (cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecodeSmem) !=
+      cudaSuccess)
+    return SZ3G_E_CUDA;
+  SZ3G_LAUNCH(kKDecode, s,
+              decode_kernel<<<(unsigned)((threads + kDecThreads - 1) / kDecThreads), kDecThreads, kDecodeSmem, s>>>(a));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 

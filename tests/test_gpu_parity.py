@@ -135,7 +135,7 @@ def test_stream_matches_oracle_bytes(case):
 
 
 @pytest.mark.parametrize("seed,nsym,spread", [(0, 65536, 3.0), (1, 65536, 300.0), (2, 1024, 20.0), (3, 8, 0.3),
-                                             (4, 65536, 20000.0)])
+                                             (4, 65536, 20000.0), (5, 65536, 1100.0), (6, 65536, 2600.0)])
 def test_huffman_build_encode_decode(seed, nsym, spread):
     rng = np.random.default_rng(seed)
     n = 200_003
