@@ -51,32 +51,6 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long
   return before;
 }
 
-// Ascending bitonic sort of P (a power of two) keys, whole block.
-__device__ void block_bitonic_sort(unsigned long long* a, int P) {
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const bool up = (i & k) == 0;
-          const unsigned long long x = a[i], y = a[ixj];
-          if ((x > y) == up) {
-            a[i] = y;
-            a[ixj] = x;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-__device__ __forceinline__ int pow2_at_least(int k) {
-  int p = 1;
-  while (p < k) p <<= 1;
-  return p;
-}
-
 // Two-queue Huffman merge over K leaves sorted by (weight, symbol); node ids:
 // leaves 0..K-1, internal K..2K-2 in creation order.  Each step takes the two
 // lightest fronts, the leaf first on equal weight, and appends their parent
@@ -134,6 +108,143 @@ __device__ void block_rank_sort(const unsigned long long* in, unsigned long long
   }
 }
 
+// One stable counting pass over K items on the whole block (32 warps): item
+// i has digit dig(i) in [0, NB) and emit(i, r) receives its rank r in the
+// order (digit, input position).  Tiles of one item per thread: the rank is
+// the digit's start, plus the items of that digit in earlier tiles, earlier
+// warps of the tile and earlier lanes of the warp.
+template <int NB, typename DigFn, typename EmitFn>
+__device__ __forceinline__ void block_counting_pass(int K, DigFn dig, EmitFn emit) {
+  static_assert(NB <= 32, "one warp per digit");
+  __shared__ uint32_t s_first[NB], s_run[NB], s_wc[32][NB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < NB) {
+    s_first[tid] = 0;
+    s_run[tid] = 0;
+  }
+  __syncthreads();
+  for (int i = tid; i < K; i += kCbThreads) atomicAdd(&s_first[dig(i)], 1u);
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t acc = 0;
+    for (int d = 0; d < NB; ++d) {
+      const uint32_t c = s_first[d];
+      s_first[d] = acc;
+      acc += c;
+    }
+  }
+  for (int t0 = 0; t0 < K; t0 += kCbThreads) {
+    for (int i = tid; i < 32 * NB; i += kCbThreads) (&s_wc[0][0])[i] = 0;
+    __syncthreads();
+    const int i = t0 + tid;
+    const uint32_t d = i < K ? dig(i) : (uint32_t)NB;  // NB: no item
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (d < (uint32_t)NB && lane == __ffs(peers) - 1) s_wc[warp][d] = (uint32_t)__popc(peers);
+    __syncthreads();
+    if (warp < NB) {  // warp w: offsets of digit w in the tile's warps
+      const uint32_t c = s_wc[lane][warp], base = s_run[warp];
+      uint32_t x = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      s_wc[lane][warp] = base + x - c;
+      __syncwarp();
+      if (lane == 31) s_run[warp] = base + x;
+    }
+    __syncthreads();
+    if (d < (uint32_t)NB) emit(i, s_first[d] + s_wc[warp][d] + (uint32_t)__popc(peers & ((1u << lane) - 1u)));
+    __syncthreads();
+  }
+}
+
+// Keys (weight << 16 | position in symbol order) sorted by weight, ties in
+// input order: least-significant-digit radix passes of 4 bits over the
+// weight, as many as its largest value needs.  a and b alternate; returns
+// the array holding the result.
+__device__ unsigned long long* block_radix_sort_w(unsigned long long* a, unsigned long long* b, int K) {
+  __shared__ uint32_t s_max;
+  if (threadIdx.x == 0) s_max = 1;
+  __syncthreads();
+  uint32_t m = 1;
+  for (int i = threadIdx.x; i < K; i += kCbThreads) m = max(m, (uint32_t)(a[i] >> 16));
+  atomicMax(&s_max, m);
+  __syncthreads();
+  const int passes = (32 - __clz((int)s_max) + 3) / 4;
+  for (int p = 0; p < passes; ++p) {
+    const int sh = 16 + 4 * p;
+    block_counting_pass<16>(
+        K, [&](int i) { return (uint32_t)(a[i] >> sh) & 15u; }, [&](int i, uint32_t r) { b[r] = a[i]; });
+    __syncthreads();
+    unsigned long long* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// The two-queue merge (leaf first on equal weight) built in batches, giving
+// the same tree node by node.  The merged consumption order lists leaves and
+// internal nodes by weight, a leaf before an internal node of equal weight,
+// internal nodes in creation order; internal node j has the items at
+// positions 2j and 2j + 1 as children.  Once the weight of node j0 is known,
+// so is its own position P (j0 + the leaves not heavier than it), and every
+// item before P is a leaf or an internal node below j0: nodes j0 .. (P-2)/2
+// are then built at once, each child found by a merge-path search.  Writes
+// W[j] (internal weights) and parent[] of every node but the root.
+template <typename PT>
+__device__ void batched_merge(const uint32_t* lw, int K, uint32_t* W, PT* parent) {
+  __shared__ uint32_t s_j1;
+  const uint32_t Ku = (uint32_t)K;
+  // item at position q when internal nodes [0, jk) are known: weight, id in *id
+  auto item = [&](uint32_t q, uint32_t jk, uint32_t* id) -> uint32_t {
+    uint32_t lo = q > jk ? q - jk : 0u, hi = min(q, Ku);
+    while (lo < hi) {  // leaves among the first q items
+      const uint32_t a = (lo + hi) >> 1;
+      if (lw[a] <= W[q - a - 1]) lo = a + 1;
+      else hi = a;
+    }
+    const uint32_t m = q - lo;
+    if (lo < Ku && (m >= jk || lw[lo] <= W[m])) {
+      *id = lo;
+      return lw[lo];
+    }
+    *id = Ku + m;
+    return W[m];
+  };
+  uint32_t j0 = 0;
+  while (j0 + 1 < Ku) {
+    if (threadIdx.x == 0) {
+      uint32_t ia, ib;
+      const uint32_t w = item(2 * j0, j0, &ia) + item(2 * j0 + 1, j0, &ib);
+      W[j0] = w;
+      parent[ia] = (PT)(Ku + j0);
+      parent[ib] = (PT)(Ku + j0);
+      uint32_t P = 2 * Ku - 2;  // the root is never consumed
+      if (j0 + 2 < Ku) {
+        uint32_t lo = 0, hi = Ku;  // leaves not heavier than w
+        while (lo < hi) {
+          const uint32_t a = (lo + hi) >> 1;
+          if (lw[a] <= w) lo = a + 1;
+          else hi = a;
+        }
+        P = j0 + lo;
+      }
+      s_j1 = min(Ku - 2, (P - 2) >> 1);
+    }
+    __syncthreads();
+    const uint32_t j1 = s_j1;
+    for (uint32_t j = j0 + 1 + threadIdx.x; j <= j1; j += kCbThreads) {
+      uint32_t ia, ib;
+      W[j] = item(2 * j, j0, &ia) + item(2 * j + 1, j0, &ib);
+      parent[ia] = (PT)(Ku + j);
+      parent[ib] = (PT)(Ku + j);
+    }
+    __syncthreads();
+    j0 = j1 + 1;
+  }
+}
+
 struct CbGlobal {  // global scratch of the codebook kernel (more than kSmemLeaves used symbols)
   unsigned long long keys[kSyms];
   unsigned long long keys2[kSyms];
@@ -150,6 +261,9 @@ constexpr size_t kCbOffNf = (size_t)kSmemLeaves * 16;
 constexpr size_t kCbOffPar = kCbOffNf + (size_t)(kSmemLeaves + 16) * 4;
 constexpr size_t kCbOffSym = kCbOffPar + (size_t)kSmemLeaves * 4;
 constexpr size_t kCbSmem = kCbOffSym + (size_t)kSmemLeaves * 2;
+// leaf + internal weights of up to this many leaves fit the dynamic shared
+// memory when the key arrays are in global memory
+constexpr int kCbSmemWeights = (int)(kCbSmem / 8);
 
 // Depth of every leaf by walking its parents (stops past SZ3G_LMAX); returns,
 // block-wide, whether some code is longer than SZ3G_LMAX.
@@ -169,15 +283,16 @@ __device__ bool leaf_depths(const PT* parent, int K, uint32_t* len) {
   return __syncthreads_or(deep) != 0;
 }
 
-// Code lengths of K leaves whose keys (weight << 16 | symbol) are in `cur`,
-// halving the weights while some code is longer than SZ3G_LMAX.  `other` is
-// a second key array; on return `srt` holds the leaves sorted by the
-// (weight, symbol) of the last round and len[i] the length of leaf srt[i].
+// Code lengths of K leaves whose keys (weight << 16 | position in symbol
+// order) are in `cur`, halving the weights while some code is longer than
+// SZ3G_LMAX.  `other` is a second key array; leaf weights and internal
+// weights go to lw_s / w_s when given (shared memory), else to the free key
+// array and nf.  On return `srt` holds the leaves sorted by the (weight,
+// position) of the last round and nf[i] the length of leaf srt[i].
 template <typename PT>
 __device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* cur, unsigned long long* other,
-                                                            uint32_t* nf, PT* parent, int K) {
-  const bool rank = K <= kRankSortMax;
-  const int P = pow2_at_least(K);
+                                                            uint32_t* nf, PT* parent, int K, uint32_t* lw_s,
+                                                            uint32_t* w_s) {
   const int tid = threadIdx.x;
   unsigned long long* srt = cur;
   if (K == 1) {
@@ -186,23 +301,19 @@ __device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* 
     return srt;
   }
   for (int iter = 0; iter < 40; ++iter) {
-    if (rank) {
-      block_rank_sort(cur, other, K);  // out of place
+    if (K <= kRankSortMax) {
+      block_rank_sort(cur, other, K);
       srt = other;
     } else {
-      srt = cur;  // in place, padded to a power of two
-      for (int i = K + tid; i < P; i += kCbThreads) srt[i] = ~0ull;
-      __syncthreads();
-      block_bitonic_sort(srt, P);
+      srt = block_radix_sort_w(cur, other, K);
     }
     __syncthreads();
-    // leaf weights (in the free key array) and the empty internal queue
-    uint32_t* lw = reinterpret_cast<uint32_t*>(srt == cur ? other : cur);
-    for (int i = tid; i < K + 2; i += kCbThreads) lw[i] = i < K ? (uint32_t)(srt[i] >> 16) : 0xffffffffu;
-    for (int i = tid; i < K + 4; i += kCbThreads) nf[i] = 0xffffffffu;
+    unsigned long long* spare = srt == cur ? other : cur;
+    uint32_t* lw = lw_s ? lw_s : reinterpret_cast<uint32_t*>(spare);
+    uint32_t* W = w_s ? w_s : nf;
+    for (int i = tid; i < K; i += kCbThreads) lw[i] = (uint32_t)(srt[i] >> 16);
     __syncthreads();
-    if (tid == 0) two_queue_merge_fast(lw, K, nf, parent);
-    __syncthreads();
+    batched_merge(lw, K, W, parent);
     if (!leaf_depths(parent, K, nf)) break;
     for (int i = tid; i < K; i += kCbThreads) {
       const unsigned long long k = srt[i];
@@ -210,13 +321,9 @@ __device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* 
       srt[i] = ((unsigned long long)(f ? f : 1u) << 16) | (k & 0xffffu);
     }
     __syncthreads();
-    // the halved keys are the input of the next sort; the other array is
-    // free again
-    if (rank) {
-      unsigned long long* t = cur;
-      cur = srt;
-      other = t;
-    }
+    // the halved keys are the next round's input
+    cur = srt;
+    other = spare;
   }
   return srt;
 }
@@ -373,7 +480,7 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
         for (int e = 0; e < 4; ++e) {
           const int b = 32 * h + 4 * r + e;
           if ((used >> b) & 1ull) {
-            ka[pos] = ((unsigned long long)comp(v[r], e) << 16) | (uint32_t)(s0 + b);
+            ka[pos] = ((unsigned long long)comp(v[r], e) << 16) | pos;  // position in symbol order
             symord[pos] = (uint16_t)(s0 + b);
             ++pos;
           }
@@ -389,8 +496,6 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
 
   // 2. lengths (shared-memory arrays are addressed through pointers derived
   //    from the shared array itself in their own branch)
-  const bool rank = K <= kRankSortMax;
-  const int P = pow2_at_least(K);
   unsigned long long* srt;
   if (in_smem) {
     // the rounds' scratch spans the second key array and the nf / parent
@@ -401,29 +506,25 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
       srt = (unsigned long long*)smem;
     } else {
       srt = code_lengths((unsigned long long*)smem, (unsigned long long*)(smem + kSmemLeaves * 8),
-                         (uint32_t*)(smem + kCbOffNf), (uint16_t*)(smem + kCbOffPar), K);
+                         (uint32_t*)(smem + kCbOffNf), (uint16_t*)(smem + kCbOffPar), K, (uint32_t*)nullptr,
+                         (uint32_t*)nullptr);
     }
+  } else if (K <= kCbSmemWeights) {  // leaf and internal weights in the (otherwise unused) shared memory
+    srt = code_lengths(g->keys, g->keys2, g->nf, g->parent, K, (uint32_t*)smem, (uint32_t*)smem + K);
   } else {
-    srt = code_lengths(g->keys, g->keys2, g->nf, g->parent, K);
+    srt = code_lengths(g->keys, g->keys2, g->nf, g->parent, K, (uint32_t*)nullptr, (uint32_t*)nullptr);
   }
-  // 3. canonical codewords: leaves ordered by (length, symbol)
+  // 3. canonical codewords: leaves ordered by (length, symbol), by a stable
+  //    counting pass over the lengths in symbol order
+  uint8_t* lenpos = reinterpret_cast<uint8_t*>(srt == ka ? kb : ka);  // the free key array
   if (tid <= SZ3G_LMAX + 1) s_cnt[tid] = 0;
   __syncthreads();
-  unsigned long long* c_in = srt;
-  unsigned long long* c_out = rank ? (srt == ka ? kb : ka) : srt;
   for (int i = tid; i < K; i += kCbThreads) {
     const uint32_t L = nf[i];
     atomicAdd(&s_cnt[L], 1u);
-    c_in[i] = ((unsigned long long)L << 16) | (c_in[i] & 0xffffu);
+    lenpos[(uint32_t)(srt[i] & 0xffffu)] = (uint8_t)L;
   }
   __syncthreads();
-  if (rank) {
-    block_rank_sort(c_in, c_out, K);
-  } else {
-    for (int i = K + tid; i < P; i += kCbThreads) c_out[i] = ~0ull;
-    __syncthreads();
-    block_bitonic_sort(c_out, P);
-  }
   if (tid == 0) {
     uint32_t start = 0, fc = 0;
     for (int L = 1; L <= SZ3G_LMAX; ++L) {
@@ -434,14 +535,14 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
     }
     st->n_used = (uint32_t)K;
   }
-  __syncthreads();
-  for (int i = tid; i < K; i += kCbThreads) {
-    const uint32_t L = (uint32_t)(c_out[i] >> 16), s = (uint32_t)(c_out[i] & 0xffffu);
-    const uint32_t code = s_fc[L] + ((uint32_t)i - s_start[L]);
-    table[s] = (L << 24) | code;
-    if (len_out) len_out[s] = (uint8_t)L;
-    if (code_out) code_out[s] = code;
-  }
+  block_counting_pass<32>(
+      K, [&](int i) { return (uint32_t)lenpos[i]; },
+      [&](int i, uint32_t r) {
+        const uint32_t L = lenpos[i], sy = symord[i], code = s_fc[L] + (r - s_start[L]);
+        table[sy] = (L << 24) | code;
+        if (len_out) len_out[sy] = (uint8_t)L;
+        if (code_out) code_out[sy] = code;
+      });
   __syncthreads();
   // 4. code-length section of the stream: (u16 symbol, u8 length) by symbol
   if (d_out) {
