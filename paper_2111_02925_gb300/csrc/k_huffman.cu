@@ -51,6 +51,13 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long
   return before;
 }
 
+// cnt[d] += 1 for every lane with `valid`, one atomic per distinct d in the
+// warp (all 32 lanes call it).
+__device__ __forceinline__ void warp_count(uint32_t* cnt, uint32_t d, bool valid) {
+  const unsigned m = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu);
+  if (valid && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&cnt[d], (uint32_t)__popc(m));
+}
+
 // Two-queue Huffman merge over K leaves sorted by (weight, symbol); node ids:
 // leaves 0..K-1, internal K..2K-2 in creation order.  Each step takes the two
 // lightest fronts, the leaf first on equal weight, and appends their parent
@@ -123,7 +130,10 @@ __device__ __forceinline__ void block_counting_pass(int K, DigFn dig, EmitFn emi
     s_run[tid] = 0;
   }
   __syncthreads();
-  for (int i = tid; i < K; i += kCbThreads) atomicAdd(&s_first[dig(i)], 1u);
+  for (int i0 = 0; i0 < K; i0 += kCbThreads) {
+    const int i = i0 + tid;
+    warp_count(s_first, i < K ? dig(i) : 0u, i < K);
+  }
   __syncthreads();
   if (tid == 0) {
     uint32_t acc = 0;
@@ -192,55 +202,84 @@ __device__ unsigned long long* block_radix_sort_w(unsigned long long* a, unsigne
 // item before P is a leaf or an internal node below j0: nodes j0 .. (P-2)/2
 // are then built at once, each child found by a merge-path search.  Writes
 // W[j] (internal weights) and parent[] of every node but the root.
-template <typename PT>
+// Items at positions q and q + 1 of the merged order when internal nodes
+// [0, jk) are known (q + 1 is before the consumption of node jk): one
+// merge-path search for the leaves among the first q items, then the two
+// queue fronts.  Weights returned, ids (leaf i, internal K + m) in ia / ib.
+__device__ __forceinline__ uint32_t merge_pair(const uint32_t* lw, const uint32_t* W, uint32_t Ku, uint32_t q,
+                                               uint32_t jk, uint32_t* ia, uint32_t* ib) {
+  uint32_t lo = q > jk ? q - jk : 0u, hi = min(q, Ku);
+  while (lo < hi) {
+    const uint32_t a = (lo + hi) >> 1;
+    if (lw[a] <= W[q - a - 1]) lo = a + 1;
+    else hi = a;
+  }
+  uint32_t a = lo, m = q - lo, w = 0;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const bool leaf = a < Ku && (m >= jk || lw[a] <= W[m]);
+    const uint32_t wt = leaf ? lw[a] : W[m];
+    *(t ? ib : ia) = leaf ? a : Ku + m;
+    w += wt;
+    a += leaf;
+    m += !leaf;
+  }
+  return w;
+}
+
+// Consumption position of internal node j of weight w (not the root): j
+// plus the leaves not heavier than w.
+__device__ __forceinline__ uint32_t merge_position(const uint32_t* lw, uint32_t Ku, uint32_t j, uint32_t w) {
+  uint32_t lo = 0, hi = Ku;
+  while (lo < hi) {
+    const uint32_t a = (lo + hi) >> 1;
+    if (lw[a] <= w) lo = a + 1;
+    else hi = a;
+  }
+  return j + lo;
+}
+
+// The two-queue merge (leaf first on equal weight) built in batches, giving
+// the same tree node by node.  The merged consumption order lists leaves and
+// internal nodes by weight, a leaf before an internal node of equal weight,
+// internal nodes in creation order; internal node j has the items at
+// positions 2j and 2j + 1 as children.  Once the weight of node j0 is known,
+// so is its own position P, and every item before P is a leaf or an
+// internal node below j0: nodes j0 .. (P-2)/2 are then built at once.
+// Writes W[j] (internal weights) and parent[] of every node but the root.
+// GROUP: the threads doing it, the whole block (1024) or one warp (32).
+template <int GROUP, typename PT>
 __device__ void batched_merge(const uint32_t* lw, int K, uint32_t* W, PT* parent) {
   __shared__ uint32_t s_j1;
-  const uint32_t Ku = (uint32_t)K;
-  // item at position q when internal nodes [0, jk) are known: weight, id in *id
-  auto item = [&](uint32_t q, uint32_t jk, uint32_t* id) -> uint32_t {
-    uint32_t lo = q > jk ? q - jk : 0u, hi = min(q, Ku);
-    while (lo < hi) {  // leaves among the first q items
-      const uint32_t a = (lo + hi) >> 1;
-      if (lw[a] <= W[q - a - 1]) lo = a + 1;
-      else hi = a;
-    }
-    const uint32_t m = q - lo;
-    if (lo < Ku && (m >= jk || lw[lo] <= W[m])) {
-      *id = lo;
-      return lw[lo];
-    }
-    *id = Ku + m;
-    return W[m];
-  };
+  const uint32_t Ku = (uint32_t)K, r = threadIdx.x & (GROUP - 1);
   uint32_t j0 = 0;
   while (j0 + 1 < Ku) {
-    if (threadIdx.x == 0) {
+    uint32_t j1 = 0;
+    if (r == 0) {
       uint32_t ia, ib;
-      const uint32_t w = item(2 * j0, j0, &ia) + item(2 * j0 + 1, j0, &ib);
+      const uint32_t w = merge_pair(lw, W, Ku, 2 * j0, j0, &ia, &ib);
       W[j0] = w;
       parent[ia] = (PT)(Ku + j0);
       parent[ib] = (PT)(Ku + j0);
-      uint32_t P = 2 * Ku - 2;  // the root is never consumed
-      if (j0 + 2 < Ku) {
-        uint32_t lo = 0, hi = Ku;  // leaves not heavier than w
-        while (lo < hi) {
-          const uint32_t a = (lo + hi) >> 1;
-          if (lw[a] <= w) lo = a + 1;
-          else hi = a;
-        }
-        P = j0 + lo;
-      }
-      s_j1 = min(Ku - 2, (P - 2) >> 1);
+      const uint32_t P = j0 + 2 < Ku ? merge_position(lw, Ku, j0, w) : 2 * Ku - 2;  // the root: never consumed
+      j1 = min(Ku - 2, (P - 2) >> 1);
+      if (GROUP > 32) s_j1 = j1;
     }
-    __syncthreads();
-    const uint32_t j1 = s_j1;
-    for (uint32_t j = j0 + 1 + threadIdx.x; j <= j1; j += kCbThreads) {
+    if (GROUP > 32) {
+      __syncthreads();
+      j1 = s_j1;
+    } else {
+      j1 = __shfl_sync(0xffffffffu, j1, 0);
+      __syncwarp();
+    }
+    for (uint32_t j = j0 + 1 + r; j <= j1; j += GROUP) {
       uint32_t ia, ib;
-      W[j] = item(2 * j, j0, &ia) + item(2 * j + 1, j0, &ib);
+      W[j] = merge_pair(lw, W, Ku, 2 * j, j0, &ia, &ib);
       parent[ia] = (PT)(Ku + j);
       parent[ib] = (PT)(Ku + j);
     }
-    __syncthreads();
+    if (GROUP > 32) __syncthreads();
+    else __syncwarp();
     j0 = j1 + 1;
   }
 }
@@ -313,7 +352,7 @@ __device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* 
     uint32_t* W = w_s ? w_s : nf;
     for (int i = tid; i < K; i += kCbThreads) lw[i] = (uint32_t)(srt[i] >> 16);
     __syncthreads();
-    batched_merge(lw, K, W, parent);
+    batched_merge<kCbThreads>(lw, K, W, parent);
     if (!leaf_depths(parent, K, nf)) break;
     for (int i = tid; i < K; i += kCbThreads) {
       const unsigned long long k = srt[i];
@@ -331,16 +370,18 @@ __device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* 
 // Speculative halving rounds for small alphabets.  Round i of the length
 // limit uses the weights max(1, f >> i) (halving max(1, f >> 1) i times), so
 // rounds 0..3 are independent: each is sorted (block-wide), the four merges
-// run at once on four threads of different warps, and the first round whose
+// run at once on four warps (batched as in code_lengths; one thread each for
+// small alphabets), and the first round whose
 // codes fit SZ3G_LMAX is the answer, as if the rounds had run one after
 // another.  `ka` holds the leaves in symbol order on entry.  On success the
 // chosen round's leaves sorted by (weight, symbol) are left in ka and their
 // lengths in nf; otherwise ka holds the weights of round 4 for the
 // sequential rounds.  Round scratch lives in [region, region + 4 * kSpecRound).
 constexpr int kSpecMax = 512, kSpecRounds = 4;
+constexpr int kSpecSerialMax = 128;  // smaller alphabets: each round's merge on one thread
 constexpr int kSpecRound = 2 * kSpecMax * 8 + (kSpecMax + 4) * 4 * 2 + 2 * kSpecMax * 2;
 __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsigned char* region, int K) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
   __shared__ int s_deep[kSpecRounds];
   auto uk = [&](int i) { return reinterpret_cast<unsigned long long*>(region + i * kSpecRound); };
   auto sk = [&](int i) { return reinterpret_cast<unsigned long long*>(region + i * kSpecRound + kSpecMax * 8); };
@@ -372,9 +413,10 @@ __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsign
   }
   __syncthreads();
   // 2. the merges at once (warps 0, 8, 16, 24: one per scheduler quarter)
-  if (lane == 0 && (warp & 7) == 0 && warp / 8 < kSpecRounds) {
+  if ((warp & 7) == 0 && warp / 8 < kSpecRounds) {
     const int i = warp / 8;
-    two_queue_merge_fast(lw(i), K, nfi(i), par(i));
+    if (K > kSpecSerialMax) batched_merge<32>(lw(i), K, nfi(i), par(i));
+    else if ((tid & 31) == 0) two_queue_merge_fast(lw(i), K, nfi(i), par(i));
   }
   __syncthreads();
   // 3. depths (into nf of the round), deep rounds flagged
@@ -410,9 +452,7 @@ __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsign
   return pick >= 0;
 }
 
-// table[sym] = len << 24 | code for every used symbol.  VEC: the histogram is
-// 16-byte aligned and read with vector loads.
-template <bool VEC>
+// table[sym] = len << 24 | code for every used symbol.
 __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __restrict__ hist, uint32_t nsym,
                                                               uint32_t* table, uint8_t* len_out, uint32_t* code_out,
                                                               DevState* st, CbGlobal* g, unsigned char* d_out,
@@ -423,42 +463,34 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   const int tid = threadIdx.x;
   static_assert(kSyms == kCbThreads * 64, "64 symbols per thread");
 
-  // 1. used symbols in symbol order: thread t owns symbols [64 t, 64 t + 64),
-  //    read in two halves of 32 with every load of a half in flight at once
-  const int s0 = tid * 64;
-  auto load8 = [&](int h, uint4* v) {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int sy = s0 + 32 * h + 4 * r;
-      if (VEC) {
-        v[r] = __ldcg(reinterpret_cast<const uint4*>(hist + sy));
-      } else {
-        v[r] = make_uint4(hist[sy], hist[sy + 1], hist[sy + 2], hist[sy + 3]);
-      }
-    }
-  };
-  auto comp = [](const uint4& v, int e) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); };
-  unsigned long long used = 0;
+  // 1. used symbols in symbol order.  Warp w reads bins 1024 k + 32 w + lane
+  //    (k = 0..63, coalesced); the ballot of each 32-bin segment marks its
+  //    used symbols, and segments in (k, w) order are symbol order.  Lane l
+  //    keeps the masks of its warp's segments k = l and k = l + 32.
+  const int lane = tid & 31, warp = tid >> 5;
+  uint32_t* s_seg = reinterpret_cast<uint32_t*>(smem + kCbOffPar);  // 2048 segment counts (free until step 2)
+  uint32_t mk0 = 0, mk1 = 0;
   bool bad = false;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    uint4 v[8];
-    load8(h, v);
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int b = 32 * h + 4 * r + e;
-        if (comp(v[r], e)) {
-          if (s0 + b < (int)nsym) used |= 1ull << b;
-          else bad = true;
-        }
-      }
+#pragma unroll 8
+  for (int k = 0; k < 64; ++k) {
+    const int sy = 1024 * k + 32 * warp + lane;
+    const uint32_t v = __ldcg(hist + sy);
+    bad |= v != 0 && sy >= (int)nsym;
+    const unsigned m = __ballot_sync(0xffffffffu, v != 0 && sy < (int)nsym);
+    if (lane == (k & 31)) {
+      if (k < 32) mk0 = m;
+      else mk1 = m;
+    }
+    if (lane == 0) s_seg[32 * k + warp] = (uint32_t)__popc(m);
   }
   if (bad) atomicOr(&st->flags, kFlagCorrupt);
   if (tid == 0) st->n_unpred = hist[0];  // code 0 marks an unpredictable value
+  __syncthreads();
+  const uint32_t c0 = s_seg[2 * tid], c1 = s_seg[2 * tid + 1];
   unsigned long long tot;
-  uint32_t pos = (uint32_t)block_exclusive_scan((unsigned long long)__popcll(used), s_warp, &tot);
+  const uint32_t off = (uint32_t)block_exclusive_scan((unsigned long long)(c0 + c1), s_warp, &tot);
+  s_seg[2 * tid] = off;
+  s_seg[2 * tid + 1] = off + c0;
   const int K = (int)tot;
   if (K == 0) {
     if (tid == 0) atomicOr(&st->flags, kFlagCorrupt);
@@ -469,22 +501,14 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   unsigned long long* kb = in_smem ? (unsigned long long*)(smem + kSmemLeaves * 8) : g->keys2;
   uint32_t* nf = in_smem ? (uint32_t*)(smem + kCbOffNf) : g->nf;
   uint16_t* symord = in_smem ? (uint16_t*)(smem + kCbOffSym) : g->symord;
-  if (used) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      uint4 v[8];
-      load8(h, v);
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int b = 32 * h + 4 * r + e;
-          if ((used >> b) & 1ull) {
-            ka[pos] = ((unsigned long long)comp(v[r], e) << 16) | pos;  // position in symbol order
-            symord[pos] = (uint16_t)(s0 + b);
-            ++pos;
-          }
-        }
+  __syncthreads();
+  for (int k = 0; k < 64; ++k) {
+    const unsigned m = __shfl_sync(0xffffffffu, k < 32 ? mk0 : mk1, k & 31);
+    if ((m >> lane) & 1u) {
+      const int sy = 1024 * k + 32 * warp + lane;
+      const uint32_t pos = s_seg[32 * k + warp] + (uint32_t)__popc(m & ((1u << lane) - 1u));
+      ka[pos] = ((unsigned long long)__ldcg(hist + sy) << 16) | pos;  // position in symbol order
+      symord[pos] = (uint16_t)sy;
     }
   }
   if (len_out || code_out)
@@ -519,10 +543,11 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   uint8_t* lenpos = reinterpret_cast<uint8_t*>(srt == ka ? kb : ka);  // the free key array
   if (tid <= SZ3G_LMAX + 1) s_cnt[tid] = 0;
   __syncthreads();
-  for (int i = tid; i < K; i += kCbThreads) {
-    const uint32_t L = nf[i];
-    atomicAdd(&s_cnt[L], 1u);
-    lenpos[(uint32_t)(srt[i] & 0xffffu)] = (uint8_t)L;
+  for (int i0 = 0; i0 < K; i0 += kCbThreads) {
+    const int i = i0 + tid;
+    const uint32_t L = i < K ? nf[i] : 0u;
+    warp_count(s_cnt, L, i < K);
+    if (i < K) lenpos[(uint32_t)(srt[i] & 0xffffu)] = (uint8_t)L;
   }
   __syncthreads();
   if (tid == 0) {
@@ -566,8 +591,7 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
 int launch_codebook(const uint32_t* hist, uint32_t nsym, uint32_t* table, uint8_t* len_out, uint32_t* code_out,
                     DevState* st, void* scratch, unsigned char* d_out, unsigned long long out_capacity, int esz,
                     cudaStream_t s) {
-  const bool vec = ((uintptr_t)hist % 16) == 0;
-  auto kern = vec ? codebook_kernel<true> : codebook_kernel<false>;
+  auto kern = codebook_kernel;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) != cudaSuccess)
     return SZ3G_E_CUDA;
   SZ3G_LAUNCH(kKCodebook, s,
@@ -1182,10 +1206,14 @@ __global__ void __launch_bounds__(kCbThreads) decode_tables_kernel(const unsigne
     return;
   }
   // Kraft sum in units of 2^-LMAX
-  for (int i = tid; i < K; i += kCbThreads) {
-    const uint32_t L = (uint32_t)(keys[i] >> 16);
-    if (L >= 1 && L <= SZ3G_LMAX) atomicAdd(&s_kraft, 1ull << (SZ3G_LMAX - L));
-    if (L >= 1 && L <= SZ3G_LMAX) atomicAdd(&s_cnt[L], 1u);
+  for (int i0 = 0; i0 < K; i0 += kCbThreads) {
+    const int i = i0 + tid;
+    const uint32_t L = i < K ? (uint32_t)(keys[i] >> 16) : 0u;
+    const bool ok = L >= 1 && L <= SZ3G_LMAX;
+    // a warp's sum is below 32 * 2^(LMAX-1) < 2^32
+    const uint32_t kr = __reduce_add_sync(0xffffffffu, ok ? 1u << (SZ3G_LMAX - L) : 0u);
+    if ((tid & 31) == 0 && kr) atomicAdd(&s_kraft, (unsigned long long)kr);
+    warp_count(s_cnt, L, ok);
   }
   __syncthreads();
   const bool kraft_ok = K == 1 ? s_kraft == (1ull << (SZ3G_LMAX - 1)) : s_kraft == (1ull << SZ3G_LMAX);
