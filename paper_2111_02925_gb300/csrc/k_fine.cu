@@ -12,12 +12,15 @@
 // around them with two 16-byte loads.
 //
 // Tile: T0 x T1 x 64 points (i, j, k); 4 x 16 x 64 in 3-D, 1 x 64 x 64 in 2-D.
-// Staged per tile, double-buffered, on one mbarrier per buffer:
+// Staged per tile on one mbarrier per buffer (kStages buffers):
 //   x box   (compress) input rows i in [A0, A0+T0), j in [A1-2, A1+T1+3),
 //           k in [A2-4, A2+68)                      -- tensor copy
 //   C box   R_{k+1} points (i/2, j/2, k/2) around the tile    -- tensor copy
-//   codes   (recover) every row of codes the tile's passes read -- bulk copies
-// The next tile's copies are issued before the current tile is computed.
+//   codes   (recover) every row of codes the tile's passes read -- 16-byte
+//           cp.async pieces (or one bulk copy per row)
+// With two stages the next tile's copies are issued before the current tile
+// is computed; with one (the configuration in use) they are issued when the
+// tile starts and other CTAs of the SM cover the wait.
 // Halo points (pass-0/1 points just outside the tile that pass 1/2 read) are
 // evaluated redundantly and never written; points outside the grid are
 // skipped.  Tiles on a face of the grid take the one-sided predictors through
