@@ -286,9 +286,25 @@ int sz3g_batch_results(sz3g_batch* batch, uint64_t* h_bytes, int* h_status);
 int sz3g_batch_configure(sz3g_batch* batch, int branches, int cta_cap);
 
 /*
+ * Level-queue mode (on = 1): every field gets its own workspace; the branches
+ * run each field's steps up to its grid levels, then one persistent kernel
+ * launch per element type runs the levels of all fields from a cross-field
+ * work queue -- tiles of every (field, level) in coarse-to-fine order, each
+ * level waiting (bounded) on a completion counter of its field's next
+ * coarser level -- then the branches run the encoders.  Rebuilds the graph;
+ * results stay bit-identical.  on = 0: every field's levels are launched in
+ * its own branch (the default).
+ */
+int sz3g_batch_set_queue(sz3g_batch* batch, int on);
+
+/* Whether the level queue is used, and the grid levels it holds. */
+int sz3g_batch_queue_info(const sz3g_batch* batch, int* on, int* levels);
+
+/*
  * Autotuner: runs the batch (twice after a warm-up) under every combination
- * of 1..256 branches and CTA caps of none, 1, 1/2 and 1/4 of the SMs, keeps
- * the fastest and reports it.  Overwrites the batch's outputs; synchronises.
+ * of 1..256 branches and CTA caps of none, 1, 1/2 and 1/4 of the SMs, and
+ * in level-queue mode under every branch count, keeps the fastest and
+ * reports it.  Overwrites the batch's outputs; synchronises.
  */
 int sz3g_batch_tune(sz3g_batch* batch, void* stream, int* h_branches, int* h_cta_cap);
 

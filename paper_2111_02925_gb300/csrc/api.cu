@@ -252,8 +252,8 @@ int parse_stream_header(const unsigned char* hb, size_t bytes, Header* h) { retu
 
 // The compress pipeline on stream s, without synchronising: on completion the
 // status block *st holds the flags and the stream length.
-int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
-                     unsigned char* ws, cudaStream_t s, DevState** st_out) {
+int compress_enqueue_pre(const sz3g_params* p, const Plan& pl, const void* d_in, unsigned char* ws, cudaStream_t s,
+                         DevState** st_out, LevelQueue* lq, int field) {
   const CompressWs L = compress_layout(pl);
   DevState* st = (DevState*)(ws + L.st);
   *st_out = st;
@@ -266,8 +266,17 @@ int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, voi
   for (int k = 0; k <= pl.L; ++k) R[k] = (k == 0 && level_path_ok(pl)) ? nullptr : ws + L.R[k];
   uint16_t* codes = (uint16_t*)(ws + L.codes);
   uint32_t* hist = (uint32_t*)(ws + L.hist);
+  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, X, x1_ready, s, lq, field));
+  return SZ3G_OK;
+}
+
+int compress_enqueue_post(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
+                          unsigned char* ws, cudaStream_t s) {
+  const CompressWs L = compress_layout(pl);
+  DevState* st = (DevState*)(ws + L.st);
+  uint16_t* codes = (uint16_t*)(ws + L.codes);
+  uint32_t* hist = (uint32_t*)(ws + L.hist);
   uint32_t* table = (uint32_t*)(ws + L.table);
-  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, X, x1_ready, s));
   SZ3G_TRY(launch_codebook(hist, 2 * pl.radius, table, nullptr, nullptr, st, ws + L.cb, (unsigned char*)d_out,
                            out_capacity, pl.esz, s));
   PassMap map;  // kernel parameter, copied at launch
@@ -278,9 +287,16 @@ int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, voi
   return SZ3G_OK;
 }
 
+// The compress pipeline on s, without synchronising.
+int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
+                     unsigned char* ws, cudaStream_t s, DevState** st_out) {
+  SZ3G_TRY(compress_enqueue_pre(p, pl, d_in, ws, s, st_out, nullptr, 0));
+  return compress_enqueue_post(p, pl, d_in, d_out, out_capacity, ws, s);
+}
+
 // The decompress pipeline of a parsed stream on s, without synchronising.
 int decompress_enqueue(const Header& h, const void* d_stream, void* d_out, unsigned char* ws, cudaStream_t s,
-                       DevState** st_out) {
+                       DevState** st_out, LevelQueue* lq, int field) {
   const Plan& pl = h.plan;
   const DecompressWs L = decompress_layout(pl);
   DevState* st = (DevState*)(ws + L.st);
@@ -299,7 +315,7 @@ int decompress_enqueue(const Header& h, const void* d_stream, void* d_out, unsig
   void* R[34];
   for (int k = 0; k <= pl.L; ++k) R[k] = k == 0 ? d_out : ws + L.R[k];
   SZ3G_TRY(launch_recover_levels(pl, codes, base + SZ3G_HEADER_BYTES, h.n_unpred, (unsigned long long*)(ws + L.zunit),
-                                 R, d_out, st, h.ebT_bits, true, s));
+                                 R, d_out, st, h.ebT_bits, true, s, lq, field));
   return SZ3G_OK;
 }
 

@@ -11,6 +11,13 @@
 // result array.  The number of branches and the CTA cap of the level kernels
 // (so that concurrent fields share the SMs) are chosen by sz3g_batch_tune,
 // which times every candidate on the batch itself.
+//
+// Level-queue mode: every field has its own workspace; the branches run each
+// field's steps up to its levels, then one persistent launch per type runs
+// the grid levels of all fields from a cross-field work queue (tiles of
+// every (field, level), each level waiting on its field's next coarser level
+// through a completion counter), then the branches run the encoders (or, for
+// decompression, only the status copies).
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -43,7 +50,10 @@ struct sz3g_batch {
   std::vector<size_t> out_cap;
   std::vector<size_t> ws_need;          // per field
   int branches = 0, cta_cap = 0;
-  std::vector<void*> ws;                // per branch
+  int queue = 0;                        // level-queue mode
+  std::vector<void*> ws;                // per branch (queue mode: one block holding every field's)
+  std::vector<size_t> ws_off;           // queue mode: offset of each field's workspace
+  LevelQueue* lq = nullptr;
   unsigned long long* d_res = nullptr;  // 2 per field
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -60,6 +70,8 @@ void release_graph(sz3g_batch* b) {
   for (void* p : b->ws)
     if (p) cudaFree(p);
   b->ws.clear();
+  level_queue_free(b->lq);
+  b->lq = nullptr;
 }
 
 // Captures the batch with the given number of branches and CTA cap.
@@ -79,18 +91,40 @@ int build_graph(sz3g_batch* b, int branches, int cta_cap) {
     lists[br].push_back(f);
     need[br] = std::max(need[br], b->ws_need[f]);
   }
-  b->ws.assign(branches, nullptr);
-  for (int br = 0; br < branches; ++br) {
-    if (lists[br].empty()) continue;
-    if (cudaMalloc(&b->ws[br], need[br] ? need[br] : 256) != cudaSuccess) {
+  if (!b->queue) {
+    b->ws.assign(branches, nullptr);
+    for (int br = 0; br < branches; ++br) {
+      if (lists[br].empty()) continue;
+      if (cudaMalloc(&b->ws[br], need[br] ? need[br] : 256) != cudaSuccess) {
+        cudaGetLastError();
+        release_graph(b);
+        return SZ3G_E_NOMEM;
+      }
+    }
+  } else {
+    b->ws_off.assign(b->n, 0);
+    size_t tot = 0, max_levels = 0;
+    for (int f = 0; f < b->n; ++f) {
+      b->ws_off[f] = tot;
+      tot += (b->ws_need[f] + 255) & ~(size_t)255;
+      max_levels += (size_t)b->plans[f].L + 1;
+    }
+    b->ws.assign(1, nullptr);
+    b->lq = level_queue_new(!b->decompress);
+    if (cudaMalloc(&b->ws[0], tot ? tot : 256) != cudaSuccess) {
       cudaGetLastError();
       release_graph(b);
       return SZ3G_E_NOMEM;
     }
+    const int r = level_queue_reserve(b->lq, max_levels);
+    if (r != SZ3G_OK) {
+      release_graph(b);
+      return r;
+    }
   }
   cudaStream_t cs = nullptr;
   std::vector<cudaStream_t> bs(branches, nullptr);
-  std::vector<cudaEvent_t> ev(branches + 1, nullptr);
+  std::vector<cudaEvent_t> ev(2 * branches + 2, nullptr);
   int rc = SZ3G_OK;
   auto fail = [&](int code) {
     if (rc == SZ3G_OK) rc = code;
@@ -98,40 +132,65 @@ int build_graph(sz3g_batch* b, int branches, int cta_cap) {
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) fail(SZ3G_E_CUDA);
   for (int i = 0; i < branches && rc == SZ3G_OK; ++i)
     if (cudaStreamCreateWithFlags(&bs[i], cudaStreamNonBlocking) != cudaSuccess) fail(SZ3G_E_CUDA);
-  for (int i = 0; i <= branches && rc == SZ3G_OK; ++i)
+  for (size_t i = 0; i < ev.size() && rc == SZ3G_OK; ++i)
     if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) fail(SZ3G_E_CUDA);
   const int saved_cap = g_level_cta_cap;
   if (rc == SZ3G_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) fail(SZ3G_E_CUDA);
   bool capturing = rc == SZ3G_OK;
   if (capturing) {
     g_level_cta_cap = cta_cap;
-    if (cudaEventRecord(ev[branches], cs) != cudaSuccess) fail(SZ3G_E_CUDA);
-    for (int br = 0; br < branches && rc == SZ3G_OK; ++br) {
-      if (lists[br].empty()) continue;
-      if (cudaStreamWaitEvent(bs[br], ev[branches], 0) != cudaSuccess) {
-        fail(SZ3G_E_CUDA);
-        break;
-      }
-      for (int f : lists[br]) {
-        DevState* st = nullptr;
-        int r;
-        if (b->decompress)
-          r = decompress_enqueue(b->headers[f], b->in[f], b->out[f], (unsigned char*)b->ws[br], bs[br], &st);
-        else
-          r = compress_enqueue(&b->params[f], b->plans[f], b->in[f], b->out[f], b->out_cap[f],
-                               (unsigned char*)b->ws[br], bs[br], &st);
-        if (r != SZ3G_OK) {
-          fail(r);
-          break;
-        }
-        SZ3G_LAUNCH(kKPublish, bs[br], publish_kernel<<<1, 32, 0, bs[br]>>>(st, b->d_res + 2 * f));
-        if (cudaGetLastError() != cudaSuccess) {
+    std::vector<DevState*> sts(b->n, nullptr);
+    // one fan-out of the branches from cs and back: step(br, f) for the
+    // fields of every branch, in order
+    auto fan = [&](cudaEvent_t root, cudaEvent_t* done, auto&& step) {
+      if (rc == SZ3G_OK && cudaEventRecord(root, cs) != cudaSuccess) fail(SZ3G_E_CUDA);
+      for (int br = 0; br < branches && rc == SZ3G_OK; ++br) {
+        if (lists[br].empty()) continue;
+        if (cudaStreamWaitEvent(bs[br], root, 0) != cudaSuccess) {
           fail(SZ3G_E_CUDA);
           break;
         }
+        for (int f : lists[br]) {
+          const int r = step(br, f);
+          if (r != SZ3G_OK) {
+            fail(r);
+            break;
+          }
+        }
+        if (rc == SZ3G_OK && cudaEventRecord(done[br], bs[br]) != cudaSuccess) fail(SZ3G_E_CUDA);
+        if (rc == SZ3G_OK && cudaStreamWaitEvent(cs, done[br], 0) != cudaSuccess) fail(SZ3G_E_CUDA);
       }
-      if (rc == SZ3G_OK && cudaEventRecord(ev[br], bs[br]) != cudaSuccess) fail(SZ3G_E_CUDA);
-      if (rc == SZ3G_OK && cudaStreamWaitEvent(cs, ev[br], 0) != cudaSuccess) fail(SZ3G_E_CUDA);
+    };
+    auto publish = [&](int br, int f) -> int {
+      SZ3G_LAUNCH(kKPublish, bs[br], publish_kernel<<<1, 32, 0, bs[br]>>>(sts[f], b->d_res + 2 * f));
+      return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+    };
+    if (!b->queue) {
+      fan(ev[2 * branches], ev.data(), [&](int br, int f) -> int {
+        int r;
+        if (b->decompress)
+          r = decompress_enqueue(b->headers[f], b->in[f], b->out[f], (unsigned char*)b->ws[br], bs[br], &sts[f]);
+        else
+          r = compress_enqueue(&b->params[f], b->plans[f], b->in[f], b->out[f], b->out_cap[f],
+                               (unsigned char*)b->ws[br], bs[br], &sts[f]);
+        return r != SZ3G_OK ? r : publish(br, f);
+      });
+    } else {
+      auto wsf = [&](int f) { return (unsigned char*)b->ws[0] + b->ws_off[f]; };
+      fan(ev[2 * branches], ev.data(), [&](int br, int f) -> int {
+        if (b->decompress)
+          return decompress_enqueue(b->headers[f], b->in[f], b->out[f], wsf(f), bs[br], &sts[f], b->lq, f);
+        return compress_enqueue_pre(&b->params[f], b->plans[f], b->in[f], wsf(f), bs[br], &sts[f], b->lq, f);
+      });
+      if (rc == SZ3G_OK) fail(level_queue_launch(b->lq, cs));
+      fan(ev[2 * branches + 1], ev.data() + branches, [&](int br, int f) -> int {
+        if (!b->decompress) {
+          const int r = compress_enqueue_post(&b->params[f], b->plans[f], b->in[f], b->out[f], b->out_cap[f],
+                                              wsf(f), bs[br]);
+          if (r != SZ3G_OK) return r;
+        }
+        return publish(br, f);
+      });
     }
     g_level_cta_cap = saved_cap;
     cudaGraph_t g = nullptr;
@@ -149,6 +208,7 @@ int build_graph(sz3g_batch* b, int branches, int cta_cap) {
       }
       size_t nn = 0;
       if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess) b->nodes = nn;
+      if (rc == SZ3G_OK && b->queue) fail(level_queue_upload(b->lq));
     }
   }
   for (cudaEvent_t e : ev)
@@ -225,6 +285,19 @@ int sz3g_batch_configure(sz3g_batch* b, int branches, int cta_cap) {
   return build_graph(b, branches, cta_cap);
 }
 
+int sz3g_batch_set_queue(sz3g_batch* b, int on) {
+  if (!b) return SZ3G_E_INVAL;
+  b->queue = on != 0;
+  return build_graph(b, b->branches ? b->branches : std::min(b->n, 8), b->cta_cap);
+}
+
+int sz3g_batch_queue_info(const sz3g_batch* b, int* on, int* levels) {
+  if (!b) return SZ3G_E_INVAL;
+  if (on) *on = b->queue;
+  if (levels) *levels = b->lq ? level_queue_count(b->lq) : 0;
+  return SZ3G_OK;
+}
+
 int sz3g_batch_run(sz3g_batch* b, void* stream) {
   if (!b || !b->exec) return SZ3G_E_INVAL;
   if (cudaGraphLaunch(b->exec, (cudaStream_t)stream) != cudaSuccess) {
@@ -275,11 +348,14 @@ int sz3g_batch_tune(sz3g_batch* b, void* stream, int* h_branches, int* h_cta_cap
     return SZ3G_E_CUDA;
   }
   float best = -1.0f;
-  int best_br = b->branches, best_cap = b->cta_cap;
+  int best_br = b->branches, best_cap = b->cta_cap, best_q = b->queue;
   int rc = SZ3G_OK;
+  for (int qm = 0; qm < 2 && rc == SZ3G_OK; ++qm)
   for (int br : br_cand) {
     if (br > b->n && br != 1) continue;
     for (int cap : cap_cand) {
+      if (qm && cap != 0) continue;  // the queue's launch takes the whole GPU
+      b->queue = qm;
       rc = build_graph(b, br, cap);
       if (rc != SZ3G_OK) break;
       float t = 0.0f, ms = 0.0f;
@@ -299,6 +375,7 @@ int sz3g_batch_tune(sz3g_batch* b, void* stream, int* h_branches, int* h_cta_cap
         best = t;
         best_br = br;
         best_cap = cap;
+        best_q = qm;
       }
     }
     if (rc != SZ3G_OK) break;
@@ -307,6 +384,7 @@ int sz3g_batch_tune(sz3g_batch* b, void* stream, int* h_branches, int* h_cta_cap
   cudaEventDestroy(e1);
   cudaGetLastError();
   if (rc != SZ3G_OK) return rc;
+  b->queue = best_q;
   rc = build_graph(b, best_br, best_cap);
   if (h_branches) *h_branches = b->branches;
   if (h_cta_cap) *h_cta_cap = b->cta_cap;

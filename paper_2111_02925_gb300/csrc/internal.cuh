@@ -227,12 +227,26 @@ size_t range_scratch_bytes(const Plan& pl);
 // also writes X_1 when the field's rows allow it (*wrote_x1).
 int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratch, size_t scratch_bytes,
                     int eb_mode, double eb, cudaStream_t s, void* X1 = nullptr, bool* wrote_x1 = nullptr);
+// Cross-field work queue of grid levels (k_level.cu): with a queue, the
+// level paths below launch the coarse group (and the decimated pyramid) and
+// collect the finer levels of the field into the queue instead of launching
+// them; level_queue_launch then runs every collected level in one
+// persistent launch per type.
+struct LevelQueue;
+LevelQueue* level_queue_new(bool comp);
+void level_queue_free(LevelQueue* q);
+int level_queue_reserve(LevelQueue* q, size_t max_levels);  // device descriptors; before graph capture
+int level_queue_count(const LevelQueue* q);
+int level_queue_launch(LevelQueue* q, cudaStream_t s);       // descriptors built on the host, kernels on s
+int level_queue_upload(LevelQueue* q);                        // descriptors to the device, before a run
+
 int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R,
-                           uint32_t* hist, DevState* st, void* X1, bool x1_ready, cudaStream_t s);
+                           uint32_t* hist, DevState* st, void* X1, bool x1_ready, cudaStream_t s,
+                           LevelQueue* lq = nullptr, int field = 0);
 int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred,
                           unsigned long long n_unpred, const unsigned long long* zunit,
                           void* const* R, void* d_out, DevState* st, unsigned long long ebT_bits,
-                          bool codes_padded, cudaStream_t s);
+                          bool codes_padded, cudaStream_t s, LevelQueue* lq = nullptr, int field = 0);
 
 // k_level.cu (fields of rank <= 3)
 // Upper bound on the CTAs of one level-kernel launch (0: one wave of the whole
@@ -241,7 +255,8 @@ int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unp
 extern int g_level_cta_cap;
 bool level_path_ok(const Plan& pl);
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                          DevState* st, void* X1, bool x1_ready, cudaStream_t s);
+                          DevState* st, void* X1, bool x1_ready, cudaStream_t s, LevelQueue* lq = nullptr,
+                          int field = 0);
 // Decimated copies of the field X_k = x[::2^k, ::2^k, ::2^k] over G_k, k >= 1
 // (rows pitched to 16 bytes, one after another): the inputs of the coarser
 // levels; xpyr_bytes is 0 when the level path does not use them.
@@ -263,7 +278,8 @@ inline unsigned long long xpyr_bytes(const Plan& pl) {
 }
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
                          const unsigned long long* zunit, void* const* R, void* d_out,
-                         DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s);
+                         DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s,
+                         LevelQueue* lq = nullptr, int field = 0);
 
 // api.cu: the pipelines without synchronisation (also used by the batch).
 struct Header {  // a parsed stream header
@@ -279,8 +295,15 @@ int stream_status(uint32_t flags);
 int parse_stream_header(const unsigned char* hb, size_t bytes, Header* h);
 int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
                      unsigned char* ws, cudaStream_t s, DevState** st);
+// compress_enqueue in two parts: up to the levels (collected into lq when
+// given), then the encoder.
+int compress_enqueue_pre(const sz3g_params* p, const Plan& pl, const void* d_in, unsigned char* ws, cudaStream_t s,
+                         DevState** st, LevelQueue* lq, int field);
+int compress_enqueue_post(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
+                          unsigned char* ws, cudaStream_t s);
+// with lq: everything but the levels collected into lq
 int decompress_enqueue(const Header& h, const void* d_stream, void* d_out, unsigned char* ws, cudaStream_t s,
-                       DevState** st);
+                       DevState** st, LevelQueue* lq = nullptr, int field = 0);
 
 // k_huffman.cu
 size_t codebook_scratch_bytes();

@@ -476,8 +476,8 @@ static int quantize_levels_t(const Plan& pl, const T* x, uint16_t* codes, void* 
 }
 
 int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                           DevState* st, void* X1, bool x1_ready, cudaStream_t s) {
-  if (level_path_ok(pl)) return launch_quantize_fused(pl, d_in, codes, R, hist, st, X1, x1_ready, s);
+                           DevState* st, void* X1, bool x1_ready, cudaStream_t s, LevelQueue* lq, int field) {
+  if (level_path_ok(pl)) return launch_quantize_fused(pl, d_in, codes, R, hist, st, X1, x1_ready, s, lq, field);
   if (pl.dtype == SZ3G_F32) return quantize_levels_t<float>(pl, (const float*)d_in, codes, R, hist, st, s);
   return quantize_levels_t<double>(pl, (const double*)d_in, codes, R, hist, st, s);
 }
@@ -505,9 +505,11 @@ static int recover_levels_t(const Plan& pl, const uint16_t* codes, const T* unpr
 
 int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
                           const unsigned long long* zunit, void* const* R, void* d_out,
-                          DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s) {
+                          DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s,
+                          LevelQueue* lq, int field) {
   if (level_path_ok(pl))
-    return launch_recover_fused(pl, codes, unpred, n_unpred, zunit, R, d_out, st, ebT_bits, codes_padded, s);
+    return launch_recover_fused(pl, codes, unpred, n_unpred, zunit, R, d_out, st, ebT_bits, codes_padded, s, lq,
+                                field);
   if (pl.dtype == SZ3G_F32) {
     float e;
     uint32_t b = (uint32_t)ebT_bits;

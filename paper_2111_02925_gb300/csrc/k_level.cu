@@ -25,6 +25,11 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <numeric>
+#include <unordered_map>
+#include <vector>
+
 #include "internal.cuh"
 #include "level_common.cuh"
 
@@ -490,12 +495,196 @@ __device__ __forceinline__ void write012(const LevelDesc& d, const LevelArgs<T>&
 // handles kUnroll items per warp at a time: all their loads are issued before
 // any result is stored (the points a pass writes are never its own inputs).
 
+// Per-CTA state of the level kernels across the tiles a CTA processes.
+template <typename T>
+struct LevelCtx {
+  T* V;
+  T* C;
+  uint32_t* hwin;
+  uint64_t* bar;
+  PassRegion* reg;
+  int* s_timeout;
+  uint32_t phase;
+  unsigned int my_nz;
+  bool my_bad;
+  T ebT, ebr;
+  int hlo;
+};
+
+// One tile of a grid level: stage its box, run the level's passes, write the
+// output tile.  Returns false when a bounded wait gave up.
+template <typename T, bool COMP, bool TMA, int INTERP>
+__device__ __forceinline__ bool level_tile(const LevelDesc& d, const LevelArgs<T>& a, const CUtensorMap* tmx,
+                                           const CUtensorMap* tmc, uint32_t tile, LevelCtx<T>& c) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kLevelThreads / 32;
+  T* V = c.V;
+  T* C = c.C;
+  uint32_t* hwin = c.hwin;
+  uint64_t* bar = c.bar;
+  const T ebT = c.ebT, ebr = c.ebr;
+  const int hlo = c.hlo;
+  const int ve1 = d.vext[1], ve2 = d.vext[2];
+  const int vs0 = ve1 * ve2;
+  const int m0 = d.m[0], m1 = d.m[1], m2 = d.m[2];
+  const int pos0 = d.pos[0], pos1 = d.pos[1], pos2 = d.pos[2];
+  (void)tid;
+  (void)C;
+  (void)bar;
+  const int t2 = (int)(tile % (uint32_t)d.nt[2]);
+  const int t1 = (int)((tile / (uint32_t)d.nt[2]) % (uint32_t)d.nt[1]);
+  const int t0 = (int)(tile / ((uint32_t)d.nt[2] * (uint32_t)d.nt[1]));
+  const int A0 = t0 * d.B[0], A1 = t1 * d.B[1], A2 = t2 * d.B[2];
+  const int E0 = min(A0 + d.B[0], m0), E1 = min(A1 + d.B[1], m1), E2 = min(A2 + d.B[2], m2);
+  const int lo0 = A0 - d.vlo[0], lo1 = A1 - d.vlo[1], lo2 = A2 - d.vlo[2];
+
+  if (TMA) {
+    // ---- stage with two tensor copies: the input box (compress) and the
+    //      coarse box of R_{k+1}; then spread the coarse values over V
+    const int cs0 = lo0 >> 1, cs1 = lo1 >> 1, cs2 = floor_to(lo2 >> 1, d.calign);
+    if (tid == 0) {
+      fence_proxy_async_smem();  // earlier generic writes to V / C precede the copies
+      const uint32_t cbytes = (uint32_t)(d.cw[0] * d.cw[1] * d.cw[2] * (int)sizeof(T));
+      const int xb0 = d.xb0_tile ? d.B[0] : d.vext[0];
+      const uint32_t xbytes = COMP ? (uint32_t)(xb0 * vs0 * (int)sizeof(T)) : 0u;
+      mbar_expect_tx(bar, cbytes + xbytes);
+      if (COMP) tma_load_3d(V + (d.xb0_tile ? d.vlo[0] * vs0 : 0), tmx, lo2, lo1, d.xb0_tile ? A0 : lo0, bar);
+      tma_load_3d(C, tmc, cs2, cs1, cs0, bar);
+    }
+    int spins = 0;
+    while (!mbar_try_wait(bar, c.phase)) {
+      if (++spins > kWaitLimit) {
+        *c.s_timeout = 1;
+        break;
+      }
+    }
+    c.phase ^= 1u;
+    __syncthreads();
+    if (*c.s_timeout) return false;
+    const bool fast = d.fast012 && (A0 >= 6 && A0 + kT0 + 6 <= m0) && (A1 >= 6 && A1 + kT1 + 6 <= m1);
+    if (fast) {
+      scatter012<T>(d, V, C, (lo2 >> 1) - cs2);
+      __syncthreads();
+    } else {
+    // coarse values to the all-even positions of V
+    const int i0a = (max(lo0, 0) + 1) >> 1, i0b = min(lo0 + d.vext[0] - 1, m0 - 1) >> 1;
+    const int i1a = (max(lo1, 0) + 1) >> 1, i1b = min(lo1 + ve1 - 1, m1 - 1) >> 1;
+    const int i2a = (max(lo2, 0) + 1) >> 1, i2b = min(lo2 + ve2 - 1, m2 - 1) >> 1;
+    const int n2 = i2b - i2a + 1, n1 = i1b - i1a + 1, n0 = i0b - i0a + 1;
+    const int cst1 = d.cw[2], cst0 = d.cw[1] * d.cw[2];
+    if (n0 > 0 && n1 > 0 && n2 > 0) {
+      const int nseg = (n2 + 31) >> 5;
+      const int items = n0 * n1 * nseg;
+      for (int it = warp; it < items; it += kWarps) {
+        const int r = it / nseg, seg = it - r * nseg;
+        const int q0 = r / n1, q1 = r - q0 * n1;
+        const int q2 = seg * 32 + lane;
+        if (q2 >= n2) continue;
+        const int i0 = i0a + q0, i1 = i1a + q1, i2 = i2a + q2;
+        V[(2 * i0 - lo0) * vs0 + (2 * i1 - lo1) * ve2 + (2 * i2 - lo2)] =
+            C[(i0 - cs0) * cst0 + (i1 - cs1) * cst1 + (i2 - cs2)];
+      }
+    }
+    __syncthreads();
+    }
+  } else {
+    // ---- stage with element copies, only the points some pass reads
+    const int nseg = (ve2 + 31) >> 5;
+    const int items = d.vext[0] * ve1 * nseg;
+    for (int it = warp; it < items; it += kWarps) {
+      const int r = it / nseg, seg = it - r * nseg;
+      const int b0 = r / ve1, b1 = r - b0 * ve1;
+      const int c0 = lo0 + b0, c1 = lo1 + b1;
+      if (c0 < 0 || c1 < 0 || c0 >= m0 || c1 >= m1) continue;
+      const int b2 = seg * 32 + lane;
+      const int c2 = lo2 + b2;
+      if (b2 >= ve2 || c2 < 0 || c2 >= m2) continue;
+      T* vp = V + r * ve2 + b2;
+      const bool odd01 = ((c0 | c1) & 1) != 0;
+      if (!odd01 && !(c2 & 1)) {
+        cp_async_elem(vp, a.Rc + ((uint32_t)(c0 >> 1) * d.rcs[0] + (uint32_t)(c1 >> 1) * d.rcs[1] +
+                                  (uint32_t)(c2 >> 1)));
+      } else if (COMP) {
+        // evaluated by pass p = the latest axis (in order) with an odd
+        // coordinate, on the tile range of the axes up to p
+        int p = -1;
+        if ((c0 & 1) && pos0 > p) p = pos0;
+        if ((c1 & 1) && pos1 > p) p = pos1;
+        if ((c2 & 1) && pos2 > p) p = pos2;
+        bool need = true;
+        if (pos0 >= 0 && pos0 <= p && (c0 < A0 || c0 >= E0)) need = false;
+        if (pos1 >= 0 && pos1 <= p && (c1 < A1 || c1 >= E1)) need = false;
+        if (pos2 >= 0 && pos2 <= p && (c2 < A2 || c2 >= E2)) need = false;
+        if (need) cp_async_elem(vp, a.x + ((uint32_t)c0 * d.xs[0] + (uint32_t)c1 * d.xs[1] + (uint32_t)c2 * d.xs[2]));
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+
+  // ---- the passes of the level (tiles away from every grid face take the
+  //      branch-free interior form)
+  const bool interior = (pos0 < 0 || (A0 >= 6 && A0 + d.B[0] + 6 <= m0)) &&
+                        (pos1 < 0 || (A1 >= 6 && A1 + d.B[1] + 6 <= m1)) &&
+                        (pos2 < 0 || (A2 >= 6 && A2 + d.B[2] + 6 <= m2));
+  // the specialised tile: interior along axes 0 and 1; a face along axis 2
+  // only changes the columns and the axis-2 pass
+  const bool fast = d.fast012 && (A0 >= 6 && A0 + kT0 + 6 <= m0) && (A1 >= 6 && A1 + kT1 + 6 <= m1);
+  const bool edge2 = !(A2 >= 6 && A2 + kT2 + 6 <= m2);
+  if (fast && !edge2) {
+    pass012<T, COMP, INTERP, 0, false>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, c.my_nz, c.my_bad);
+    __syncthreads();
+    pass012<T, COMP, INTERP, 1, false>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, c.my_nz, c.my_bad);
+    __syncthreads();
+    pass012<T, COMP, INTERP, 2, false>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, c.my_nz, c.my_bad);
+    __syncthreads();
+  } else if (fast) {
+    pass012<T, COMP, INTERP, 0, true>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, c.my_nz, c.my_bad);
+    __syncthreads();
+    pass012<T, COMP, INTERP, 1, true>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, c.my_nz, c.my_bad);
+    __syncthreads();
+    pass012<T, COMP, INTERP, 2, true>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, c.my_nz, c.my_bad);
+    __syncthreads();
+  } else {
+    for (int p = 0; p < d.P; ++p) {
+      const TileGeo g{A0, A1, A2, E0, E1, E2, lo0, lo1, lo2};
+      if (interior)
+        level_pass_interior<T, COMP, INTERP>(d, a, V, hwin, c.reg[p], A0, A1, A2, ebT, ebr, hlo, c.my_nz, c.my_bad);
+      else
+        level_pass<T, COMP, INTERP, false>(d, a, V, hwin, g, p, ebT, ebr, hlo, c.my_nz, c.my_bad);
+      __syncthreads();
+    }
+  }
+
+  // ---- write the tile of the output grid
+  if (d.write_out && fast) {
+    write012<T>(d, a, V, A0, A1, A2, E2);
+  } else if (d.write_out) {
+    const int w1 = E1 - A1, w2 = E2 - A2;
+    const int rows = (E0 - A0) * w1;
+    int q0 = warp / w1, q1 = warp - (warp / w1) * w1;
+    for (int r = warp; r < rows; r += kWarps) {
+      const int c0 = A0 + q0, c1 = A1 + q1;
+      T* dst = a.Rout + ((uint32_t)c0 * d.rs[0] + (uint32_t)c1 * d.rs[1] + (uint32_t)A2 * d.rs[2]);
+      const T* src = V + ((c0 - lo0) * vs0 + (c1 - lo1) * ve2 + (A2 - lo2));
+      for (int q2 = lane; q2 < w2; q2 += 32) dst[(uint32_t)q2 * d.rs[2]] = src[q2];
+      q1 += kWarps;
+      while (q1 >= w1) {
+        q1 -= w1;
+        ++q0;
+      }
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 template <typename T, bool COMP, bool TMA, int INTERP>
 __global__ void __launch_bounds__(kLevelThreads, 3) level_kernel(const LevelDesc d, const LevelArgs<T> a,
                                                               const __grid_constant__ CUtensorMap tmx,
                                                               const __grid_constant__ CUtensorMap tmc) {
   extern __shared__ __align__(128) unsigned char sm[];
-  const int vsize = d.vext[0] * d.vext[1] * d.vext[2];
   T* V = reinterpret_cast<T*>(sm);
   T* C = reinterpret_cast<T*>(sm + d.smem_c);
   uint32_t* hwin = reinterpret_cast<uint32_t*>(sm + d.smem_h);
@@ -503,8 +692,6 @@ __global__ void __launch_bounds__(kLevelThreads, 3) level_kernel(const LevelDesc
   __shared__ unsigned long long s_nz;
   __shared__ int s_bad, s_timeout;
   const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  constexpr int kWarps = kLevelThreads / 32;
   DevState* st = a.st;
   if (COMP && (st->flags & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound))) return;
   if (!COMP && (st->flags & kFlagCorrupt)) return;
@@ -523,165 +710,16 @@ __global__ void __launch_bounds__(kLevelThreads, 3) level_kernel(const LevelDesc
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
   }
-  unsigned int my_nz = 0;
-  bool my_bad = false;
-  const int ve1 = d.vext[1], ve2 = d.vext[2];
-  const int vs0 = ve1 * ve2;
-  const int m0 = d.m[0], m1 = d.m[1], m2 = d.m[2];
-  const int pos0 = d.pos[0], pos1 = d.pos[1], pos2 = d.pos[2];
-  uint32_t phase = 0;
-  (void)vsize;
   __shared__ PassRegion s_reg[3];
   if (tid == 0) make_regions(d, s_reg);
   __syncthreads();
 
-  for (uint32_t tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x) {
-    const int t2 = (int)(tile % (uint32_t)d.nt[2]);
-    const int t1 = (int)((tile / (uint32_t)d.nt[2]) % (uint32_t)d.nt[1]);
-    const int t0 = (int)(tile / ((uint32_t)d.nt[2] * (uint32_t)d.nt[1]));
-    const int A0 = t0 * d.B[0], A1 = t1 * d.B[1], A2 = t2 * d.B[2];
-    const int E0 = min(A0 + d.B[0], m0), E1 = min(A1 + d.B[1], m1), E2 = min(A2 + d.B[2], m2);
-    const int lo0 = A0 - d.vlo[0], lo1 = A1 - d.vlo[1], lo2 = A2 - d.vlo[2];
-
-    if (TMA) {
-      // ---- stage with two tensor copies: the input box (compress) and the
-      //      coarse box of R_{k+1}; then spread the coarse values over V
-      const int cs0 = lo0 >> 1, cs1 = lo1 >> 1, cs2 = floor_to(lo2 >> 1, d.calign);
-      if (tid == 0) {
-        fence_proxy_async_smem();  // earlier generic writes to V / C precede the copies
-        const uint32_t cbytes = (uint32_t)(d.cw[0] * d.cw[1] * d.cw[2] * (int)sizeof(T));
-        const int xb0 = d.xb0_tile ? d.B[0] : d.vext[0];
-        const uint32_t xbytes = COMP ? (uint32_t)(xb0 * vs0 * (int)sizeof(T)) : 0u;
-        mbar_expect_tx(bar, cbytes + xbytes);
-        if (COMP) tma_load_3d(V + (d.xb0_tile ? d.vlo[0] * vs0 : 0), &tmx, lo2, lo1, d.xb0_tile ? A0 : lo0, bar);
-        tma_load_3d(C, &tmc, cs2, cs1, cs0, bar);
-      }
-      int spins = 0;
-      while (!mbar_try_wait(bar, phase)) {
-        if (++spins > kWaitLimit) {
-          s_timeout = 1;
-          break;
-        }
-      }
-      phase ^= 1u;
-      __syncthreads();
-      if (s_timeout) break;
-      const bool fast = d.fast012 && (A0 >= 6 && A0 + kT0 + 6 <= m0) && (A1 >= 6 && A1 + kT1 + 6 <= m1);
-      if (fast) {
-        scatter012<T>(d, V, C, (lo2 >> 1) - cs2);
-        __syncthreads();
-      } else {
-      // coarse values to the all-even positions of V
-      const int i0a = (max(lo0, 0) + 1) >> 1, i0b = min(lo0 + d.vext[0] - 1, m0 - 1) >> 1;
-      const int i1a = (max(lo1, 0) + 1) >> 1, i1b = min(lo1 + ve1 - 1, m1 - 1) >> 1;
-      const int i2a = (max(lo2, 0) + 1) >> 1, i2b = min(lo2 + ve2 - 1, m2 - 1) >> 1;
-      const int n2 = i2b - i2a + 1, n1 = i1b - i1a + 1, n0 = i0b - i0a + 1;
-      const int cst1 = d.cw[2], cst0 = d.cw[1] * d.cw[2];
-      if (n0 > 0 && n1 > 0 && n2 > 0) {
-        const int nseg = (n2 + 31) >> 5;
-        const int items = n0 * n1 * nseg;
-        for (int it = warp; it < items; it += kWarps) {
-          const int r = it / nseg, seg = it - r * nseg;
-          const int q0 = r / n1, q1 = r - q0 * n1;
-          const int q2 = seg * 32 + lane;
-          if (q2 >= n2) continue;
-          const int i0 = i0a + q0, i1 = i1a + q1, i2 = i2a + q2;
-          V[(2 * i0 - lo0) * vs0 + (2 * i1 - lo1) * ve2 + (2 * i2 - lo2)] =
-              C[(i0 - cs0) * cst0 + (i1 - cs1) * cst1 + (i2 - cs2)];
-        }
-      }
-      __syncthreads();
-      }
-    } else {
-      // ---- stage with element copies, only the points some pass reads
-      const int nseg = (ve2 + 31) >> 5;
-      const int items = d.vext[0] * ve1 * nseg;
-      for (int it = warp; it < items; it += kWarps) {
-        const int r = it / nseg, seg = it - r * nseg;
-        const int b0 = r / ve1, b1 = r - b0 * ve1;
-        const int c0 = lo0 + b0, c1 = lo1 + b1;
-        if (c0 < 0 || c1 < 0 || c0 >= m0 || c1 >= m1) continue;
-        const int b2 = seg * 32 + lane;
-        const int c2 = lo2 + b2;
-        if (b2 >= ve2 || c2 < 0 || c2 >= m2) continue;
-        T* vp = V + r * ve2 + b2;
-        const bool odd01 = ((c0 | c1) & 1) != 0;
-        if (!odd01 && !(c2 & 1)) {
-          cp_async_elem(vp, a.Rc + ((uint32_t)(c0 >> 1) * d.rcs[0] + (uint32_t)(c1 >> 1) * d.rcs[1] +
-                                    (uint32_t)(c2 >> 1)));
-        } else if (COMP) {
-          // evaluated by pass p = the latest axis (in order) with an odd
-          // coordinate, on the tile range of the axes up to p
-          int p = -1;
-          if ((c0 & 1) && pos0 > p) p = pos0;
-          if ((c1 & 1) && pos1 > p) p = pos1;
-          if ((c2 & 1) && pos2 > p) p = pos2;
-          bool need = true;
-          if (pos0 >= 0 && pos0 <= p && (c0 < A0 || c0 >= E0)) need = false;
-          if (pos1 >= 0 && pos1 <= p && (c1 < A1 || c1 >= E1)) need = false;
-          if (pos2 >= 0 && pos2 <= p && (c2 < A2 || c2 >= E2)) need = false;
-          if (need) cp_async_elem(vp, a.x + ((uint32_t)c0 * d.xs[0] + (uint32_t)c1 * d.xs[1] + (uint32_t)c2 * d.xs[2]));
-        }
-      }
-      cp_async_wait_all();
-      __syncthreads();
-    }
-
-    // ---- the passes of the level (tiles away from every grid face take the
-    //      branch-free interior form)
-    const bool interior = (pos0 < 0 || (A0 >= 6 && A0 + d.B[0] + 6 <= m0)) &&
-                          (pos1 < 0 || (A1 >= 6 && A1 + d.B[1] + 6 <= m1)) &&
-                          (pos2 < 0 || (A2 >= 6 && A2 + d.B[2] + 6 <= m2));
-    // the specialised tile: interior along axes 0 and 1; a face along axis 2
-    // only changes the columns and the axis-2 pass
-    const bool fast = d.fast012 && (A0 >= 6 && A0 + kT0 + 6 <= m0) && (A1 >= 6 && A1 + kT1 + 6 <= m1);
-    const bool edge2 = !(A2 >= 6 && A2 + kT2 + 6 <= m2);
-    if (fast && !edge2) {
-      pass012<T, COMP, INTERP, 0, false>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
-      __syncthreads();
-      pass012<T, COMP, INTERP, 1, false>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
-      __syncthreads();
-      pass012<T, COMP, INTERP, 2, false>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
-      __syncthreads();
-    } else if (fast) {
-      pass012<T, COMP, INTERP, 0, true>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
-      __syncthreads();
-      pass012<T, COMP, INTERP, 1, true>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
-      __syncthreads();
-      pass012<T, COMP, INTERP, 2, true>(d, a, V, hwin, A0, A1, A2, E2, ebT, ebr, hlo, my_nz, my_bad);
-      __syncthreads();
-    } else {
-      for (int p = 0; p < d.P; ++p) {
-        const TileGeo g{A0, A1, A2, E0, E1, E2, lo0, lo1, lo2};
-        if (interior)
-          level_pass_interior<T, COMP, INTERP>(d, a, V, hwin, s_reg[p], A0, A1, A2, ebT, ebr, hlo, my_nz, my_bad);
-        else
-          level_pass<T, COMP, INTERP, false>(d, a, V, hwin, g, p, ebT, ebr, hlo, my_nz, my_bad);
-        __syncthreads();
-      }
-    }
-
-    // ---- write the tile of the output grid
-    if (d.write_out && fast) {
-      write012<T>(d, a, V, A0, A1, A2, E2);
-    } else if (d.write_out) {
-      const int w1 = E1 - A1, w2 = E2 - A2;
-      const int rows = (E0 - A0) * w1;
-      int q0 = warp / w1, q1 = warp - (warp / w1) * w1;
-      for (int r = warp; r < rows; r += kWarps) {
-        const int c0 = A0 + q0, c1 = A1 + q1;
-        T* dst = a.Rout + ((uint32_t)c0 * d.rs[0] + (uint32_t)c1 * d.rs[1] + (uint32_t)A2 * d.rs[2]);
-        const T* src = V + ((c0 - lo0) * vs0 + (c1 - lo1) * ve2 + (A2 - lo2));
-        for (int q2 = lane; q2 < w2; q2 += 32) dst[(uint32_t)q2 * d.rs[2]] = src[q2];
-        q1 += kWarps;
-        while (q1 >= w1) {
-          q1 -= w1;
-          ++q0;
-        }
-      }
-    }
-    __syncthreads();
-  }
+  LevelCtx<T> c{V, C, hwin, bar, s_reg, &s_timeout, 0u, 0u, false, ebT, ebr, hlo};
+  for (uint32_t tile = blockIdx.x; tile < d.ntiles; tile += gridDim.x)
+    if (!level_tile<T, COMP, TMA, INTERP>(d, a, &tmx, &tmc, tile, c)) break;
+  const uint32_t phase = c.phase;
+  const unsigned int my_nz = c.my_nz;
+  const bool my_bad = c.my_bad;
 
   // ---- flush the per-CTA counters
   if (my_nz) atomicAdd(&s_nz, (unsigned long long)my_nz);
@@ -919,11 +957,13 @@ static bool encode_map(CUtensorMap* map, const T* base, int m0, int m1, int m2, 
 
 static size_t up128(size_t x) { return (x + 127) & ~(size_t)127; }
 
+// Descriptor, shared-memory bytes and (when tensor copies are allowed and
+// possible) tensor maps of one grid level on the generic kernel.  d->P == 0:
+// the grid has no passes.
 template <typename T, bool COMP>
-static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t s) {
-  if ((COMP || a.codes_padded) && fine_eligible(pl, k, COMP, a.x, a.xs, a.Rc, a.Rout, !COMP && k == 0))
-    return launch_fine<T, COMP>(pl, k, a, !COMP && k == 0, s);
-  LevelDesc d;
+static int level_desc(const Plan& pl, int k, const LevelArgs<T>& a, bool allow_tma, LevelDesc* dp, size_t* smem,
+                      CUtensorMap* tmxp, CUtensorMap* tmcp, bool* tma_out) {
+  LevelDesc& d = *dp;
   memset(&d, 0, sizeof(d));
   d.k = k;
   d.write_out = a.Rout != nullptr;
@@ -943,7 +983,7 @@ static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t 
     ++P;
   }
   d.P = P;
-  if (P == 0) return SZ3G_OK;
+  if (P == 0) return SZ3G_OK;  // d.P == 0: nothing to launch
   tile_shape(pl, k, d.pos, d.B);
   const unsigned long long* mc = pl.gm[k + 1];
   const int mc0 = (int)mc[1], mc1 = (int)mc[2], mc2 = (int)mc[3];
@@ -951,7 +991,7 @@ static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t 
   // tensor copies: the coarse grid rows (and, on compress, the input rows of a
   // finest-level grid) must be 16-byte multiples, the box start along axis 2
   // a 16-byte boundary (tile starts are multiples of `al`)
-  bool tma = (size_t)mc2 * esz % 16 == 0 && (size_t)mc1 * mc2 * esz % 16 == 0 && d.B[2] % al == 0 &&
+  bool tma = allow_tma && (size_t)mc2 * esz % 16 == 0 && (size_t)mc1 * mc2 * esz % 16 == 0 && d.B[2] % al == 0 &&
              ((uintptr_t)a.Rc % 16) == 0 && tensor_map_encoder() != nullptr;
   if (COMP)
     tma = tma && k == 0 && (size_t)d.m[2] * esz % 16 == 0 && (size_t)d.m[1] * d.m[2] * esz % 16 == 0 &&
@@ -988,7 +1028,8 @@ static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t 
               d.B[2] == kT2 && d.vext[0] == kX0 && d.vext[1] == kX1 && d.vext[2] == kX2 && d.vlo[0] == kH0 &&
               d.vlo[1] == kH1 && d.vlo[2] == kH2 && d.rs[2] == 1;
   const size_t vbytes = (size_t)d.vext[0] * d.vext[1] * d.vext[2] * esz;
-  CUtensorMap tmx, tmc;
+  CUtensorMap& tmx = *tmxp;
+  CUtensorMap& tmc = *tmcp;
   memset(&tmx, 0, sizeof(tmx));
   memset(&tmc, 0, sizeof(tmc));
   size_t cbytes = 0;
@@ -1007,7 +1048,21 @@ static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t 
   d.smem_c = (uint32_t)up128(vbytes);
   d.smem_h = (uint32_t)up128(d.smem_c + cbytes);
   d.smem_bar = (uint32_t)(d.smem_h + (COMP ? kHistWin * 4 : 0));
-  const size_t smem = d.smem_bar + 16;
+  *smem = d.smem_bar + 16;
+  *tma_out = tma;
+  return SZ3G_OK;
+}
+
+template <typename T, bool COMP>
+static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t s) {
+  if ((COMP || a.codes_padded) && fine_eligible(pl, k, COMP, a.x, a.xs, a.Rc, a.Rout, !COMP && k == 0))
+    return launch_fine<T, COMP>(pl, k, a, !COMP && k == 0, s);
+  LevelDesc d;
+  size_t smem = 0;
+  CUtensorMap tmx, tmc;
+  bool tma = false;
+  const int rc = level_desc<T, COMP>(pl, k, a, true, &d, &smem, &tmx, &tmc, &tma);
+  if (rc != SZ3G_OK || d.P == 0) return rc;
   auto kern = tma ? (d.interp == SZ3G_CUBIC ? level_kernel<T, COMP, true, SZ3G_CUBIC>
                                             : level_kernel<T, COMP, true, SZ3G_LINEAR>)
                   : (d.interp == SZ3G_CUBIC ? level_kernel<T, COMP, false, SZ3G_CUBIC>
@@ -1025,6 +1080,311 @@ static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t 
   SZ3G_LAUNCH(COMP ? kKLevelQuantize : kKLevelRecover, s,
               kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(d, a, tmx, tmc));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Cross-field work queue (batches).  The levels below the coarse group of
+// every field of a batch are collected instead of launched, and one
+// persistent kernel per direction and type walks their tiles: a CTA takes the
+// next chunk of tiles by a ticket, loads its level's descriptor and arguments into
+// shared memory when the level changes (flushing the previous level's
+// histogram window and counters to its field), waits until its field's next
+// coarser level has counted all its tiles done, runs the tile and counts it
+// done.  The queue lists every field's levels coarse to fine (k descending),
+// so a tile waits only on tiles taken before it; a CTA takes a tile only
+// once it runs, so every awaited tile is held by a running CTA.  counters:
+// [0] the ticket, [1 + i] chunks of level i done, [1 + nlev] set when a wait
+// gave up (every later wait then gives up at once).  Counts are of chunks.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct QLevel {
+  LevelDesc d;
+  LevelArgs<T> a;
+  int dep;          // index of the level whose reconstruction this one reads (-1: none in the queue)
+  uint32_t first;   // queue index of the level's first chunk
+  uint32_t chunks;  // chunks of up to kQueueChunk consecutive tiles
+};
+
+constexpr uint32_t kQueueChunk = 8;  // tiles per ticket (one level's, consecutive)
+
+constexpr int kQueueSpinLimit = 1 << 24;  // x ~100 ns: the bound on one dependency wait
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename T, bool COMP>
+__global__ void __launch_bounds__(kLevelThreads, 3) level_queue_kernel(const QLevel<T>* __restrict__ q, int nlev,
+                                                                    uint32_t total, uint32_t* counters) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ LevelDesc s_d;
+  __shared__ LevelArgs<T> s_a;
+  __shared__ PassRegion s_reg[3];
+  __shared__ unsigned long long s_nz;
+  __shared__ int s_bad, s_timeout, s_skip, s_late, s_lev;
+  __shared__ uint32_t s_item;
+  const int tid = threadIdx.x;
+  int cur = -1;
+  LevelCtx<T> c{};
+  c.reg = s_reg;
+  c.s_timeout = &s_timeout;
+  if (tid == 0) {
+    s_nz = 0;
+    s_bad = 0;
+    s_timeout = 0;
+  }
+  // the per-CTA counters and histogram window of the current level to its field
+  auto flush = [&]() {
+    if (c.my_nz) atomicAdd(&s_nz, (unsigned long long)c.my_nz);
+    if (c.my_bad) s_bad = 1;
+    __syncthreads();
+    DevState* st = s_a.st;
+    if (COMP) {
+      for (int i = tid; i < kHistWin; i += kLevelThreads)
+        if (c.hwin[i]) atomicAdd(&s_a.hist[c.hlo + i], c.hwin[i]);
+      if (tid == 0) {
+        if (s_nz) atomicAdd(&st->n_unpred, s_nz);
+        if (s_bad) atomicOr(&st->flags, kFlagNonFinite);
+      }
+    } else if (tid == 0 && s_bad) {
+      atomicOr(&st->flags, kFlagCorrupt);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_nz = 0;
+      s_bad = 0;
+    }
+    c.my_nz = 0;
+    c.my_bad = false;
+  };
+  for (;;) {
+    if (tid == 0) {
+      const uint32_t it = atomicAdd(&counters[0], 1u);
+      int li = -1;
+      if (it < total) {  // the last level whose first tile is not after it
+        int lo = 0, hi = nlev - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (q[mid].first <= it) lo = mid;
+          else hi = mid - 1;
+        }
+        li = lo;
+      }
+      s_item = it;
+      s_lev = li;
+    }
+    __syncthreads();
+    const uint32_t it = s_item;
+    const int li = s_lev;
+    if (it >= total) break;
+    if (li != cur) {
+      if (cur >= 0) flush();
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&q[li].d);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_d);
+      for (int i = tid; i < (int)(sizeof(LevelDesc) / 4); i += kLevelThreads) dst[i] = src[i];
+      const uint32_t* sa = reinterpret_cast<const uint32_t*>(&q[li].a);
+      uint32_t* da = reinterpret_cast<uint32_t*>(&s_a);
+      for (int i = tid; i < (int)(sizeof(LevelArgs<T>) / 4); i += kLevelThreads) da[i] = sa[i];
+      __syncthreads();
+      if (tid == 0) {
+        make_regions(s_d, s_reg);
+        const uint32_t f = s_a.st->flags;
+        s_skip = COMP ? (f & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound)) != 0 : (f & kFlagCorrupt) != 0;
+      }
+      c.V = reinterpret_cast<T*>(sm);
+      c.C = reinterpret_cast<T*>(sm + s_d.smem_c);
+      c.hwin = reinterpret_cast<uint32_t*>(sm + s_d.smem_h);
+      c.bar = nullptr;
+      c.ebT = COMP ? bits_to<T>(s_a.st->ebT_bits) : s_a.ebT;
+      c.ebr = COMP ? bits_to<T>(s_a.st->ebr_bits) : T(0);
+      c.hlo = s_a.radius - kHistWin / 2;
+      if (COMP)
+        for (int i = tid; i < kHistWin; i += kLevelThreads) c.hwin[i] = 0;
+      __syncthreads();
+      cur = li;
+    }
+    // the next coarser level of the field must be complete
+    if (tid == 0) {
+      s_late = 0;
+      const int dep = q[li].dep;
+      if (dep >= 0) {
+        const uint32_t need = q[dep].chunks;
+        volatile uint32_t* abort_flag = counters + 1 + nlev;  // set by the first wait that gave up
+        int spins = 0;
+        while (ld_acquire_u32(&counters[1 + dep]) < need) {
+          if (++spins > kQueueSpinLimit || *abort_flag) {
+            s_late = 1;
+            atomicOr(&s_a.st->flags, kFlagTimeout);
+            atomicExch(counters + 1 + nlev, 1u);
+            break;
+          }
+          __nanosleep(100);
+        }
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (!s_skip && !s_late) {
+      const uint32_t t0 = (it - q[li].first) * kQueueChunk, t1 = min(t0 + kQueueChunk, s_d.ntiles);
+      for (uint32_t tile = t0; tile < t1; ++tile) {
+        if (s_d.interp == SZ3G_CUBIC)
+          level_tile<T, COMP, false, SZ3G_CUBIC>(s_d, s_a, nullptr, nullptr, tile, c);
+        else
+          level_tile<T, COMP, false, SZ3G_LINEAR>(s_d, s_a, nullptr, nullptr, tile, c);
+      }
+    }
+    // every thread's writes of the tile, then the tile counted done
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(&counters[1 + li], 1u);
+  }
+  if (cur >= 0) flush();
+}
+
+template <typename T>
+struct QItem {
+  const Plan* pl;
+  int k, field;
+  LevelArgs<T> a;
+};
+
+struct LevelQueue {
+  bool comp = false;
+  std::vector<QItem<float>> f32;
+  std::vector<QItem<double>> f64;
+  std::vector<unsigned char> h32, h64;  // QLevel arrays built at launch time
+  int n32 = 0, n64 = 0;
+  void* dev = nullptr;                  // counters of both types, then the QLevel arrays
+  size_t cap = 0, off32 = 0, off64 = 0, cnt64 = 0;
+};
+
+LevelQueue* level_queue_new(bool comp) {
+  LevelQueue* q = new LevelQueue;
+  q->comp = comp;
+  return q;
+}
+
+void level_queue_free(LevelQueue* q) {
+  if (!q) return;
+  if (q->dev) cudaFree(q->dev);
+  delete q;
+}
+
+int level_queue_reserve(LevelQueue* q, size_t max_levels) {
+  const size_t cnt = (max_levels + 2) * 4 * 2 + 512;
+  const size_t need = cnt + (max_levels + 1) * (sizeof(QLevel<double>) + 256);
+  if (q->dev && q->cap >= need) return SZ3G_OK;
+  if (q->dev) cudaFree(q->dev);
+  q->dev = nullptr;
+  if (cudaMalloc(&q->dev, need) != cudaSuccess) {
+    cudaGetLastError();
+    return SZ3G_E_NOMEM;
+  }
+  q->cap = need;
+  q->cnt64 = ((max_levels + 2) * 4 + 255) & ~(size_t)255;
+  q->off32 = (2 * q->cnt64 + 255) & ~(size_t)255;
+  q->off64 = q->off32;  // set once the f32 array size is known
+  return SZ3G_OK;
+}
+
+int level_queue_count(const LevelQueue* q) { return (int)(q->f32.size() + q->f64.size()); }
+
+template <typename T>
+static std::vector<QItem<T>>& queue_items(LevelQueue* q);
+template <>
+std::vector<QItem<float>>& queue_items<float>(LevelQueue* q) { return q->f32; }
+template <>
+std::vector<QItem<double>>& queue_items<double>(LevelQueue* q) { return q->f64; }
+
+template <typename T>
+static void queue_add(LevelQueue* q, const Plan& pl, int k, int field, const LevelArgs<T>& a) {
+  queue_items<T>(q).push_back(QItem<T>{&pl, k, field, a});
+}
+
+// Descriptors of one type's levels in queue order (into `host`), then the
+// counters cleared and the kernel launched on s.
+template <typename T, bool COMP>
+static int queue_launch_t(LevelQueue* q, std::vector<unsigned char>& host, size_t dev_off, uint32_t* counters,
+                          size_t counter_bytes, cudaStream_t s) {
+  const std::vector<QItem<T>>& items = queue_items<T>(q);
+  host.clear();
+  if (items.empty()) return SZ3G_OK;
+  std::vector<int> order(items.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (items[x].k != items[y].k) return items[x].k > items[y].k;
+    return items[x].field < items[y].field;
+  });
+  std::vector<QLevel<T>> lv;
+  lv.reserve(items.size());
+  std::unordered_map<int, int> last;  // field -> its latest queued (so nearest coarser) level
+  size_t smem = 0;
+  uint32_t total = 0;
+  for (int i : order) {
+    const QItem<T>& it = items[i];
+    QLevel<T> e;
+    memset(&e, 0, sizeof(e));
+    CUtensorMap tmx, tmc;
+    bool tma = false;
+    size_t sm = 0;
+    const int rc = level_desc<T, COMP>(*it.pl, it.k, it.a, false, &e.d, &sm, &tmx, &tmc, &tma);
+    if (rc != SZ3G_OK) return rc;
+    if (e.d.P == 0) continue;
+    e.a = it.a;
+    const auto f = last.find(it.field);
+    e.dep = f == last.end() ? -1 : f->second;
+    e.first = total;
+    e.chunks = (e.d.ntiles + kQueueChunk - 1) / kQueueChunk;
+    total += e.chunks;
+    smem = std::max(smem, sm);
+    last[it.field] = (int)lv.size();
+    lv.push_back(e);
+  }
+  if ((lv.size() + 2) * 4 > counter_bytes || dev_off + lv.size() * sizeof(QLevel<T>) > q->cap) return SZ3G_E_INVAL;
+  host.resize(lv.size() * sizeof(QLevel<T>));
+  if (!lv.empty()) memcpy(host.data(), lv.data(), host.size());
+  if (total == 0) return SZ3G_OK;
+  auto kern = level_queue_kernel<T, COMP>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return SZ3G_E_CUDA;
+  int dev = 0, nsm = 152, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kLevelThreads, smem);
+  if (per < 1) per = 1;
+  unsigned long long grid = (unsigned long long)nsm * per;
+  if (grid > total) grid = total;
+  if (cudaMemsetAsync(counters, 0, (lv.size() + 2) * 4, s) != cudaSuccess) return SZ3G_E_CUDA;
+  SZ3G_LAUNCH(COMP ? kKLevelQuantize : kKLevelRecover, s,
+              kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(
+                  reinterpret_cast<const QLevel<T>*>((unsigned char*)q->dev + dev_off), (int)lv.size(), total,
+                  counters));
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+}
+
+int level_queue_launch(LevelQueue* q, cudaStream_t s) {
+  if (!q->dev || (size_t)level_queue_count(q) + 2 > q->cnt64 / 4) return SZ3G_E_INVAL;
+  uint32_t* c32 = (uint32_t*)q->dev;
+  uint32_t* c64 = (uint32_t*)((unsigned char*)q->dev + q->cnt64);
+  int rc = q->comp ? queue_launch_t<float, true>(q, q->h32, q->off32, c32, q->cnt64, s)
+                   : queue_launch_t<float, false>(q, q->h32, q->off32, c32, q->cnt64, s);
+  if (rc != SZ3G_OK) return rc;
+  q->off64 = (q->off32 + q->h32.size() + 255) & ~(size_t)255;
+  rc = q->comp ? queue_launch_t<double, true>(q, q->h64, q->off64, c64, q->cnt64, s)
+               : queue_launch_t<double, false>(q, q->h64, q->off64, c64, q->cnt64, s);
+  return rc;
+}
+
+int level_queue_upload(LevelQueue* q) {
+  if (!q->h32.empty() && cudaMemcpy((unsigned char*)q->dev + q->off32, q->h32.data(), q->h32.size(),
+                                    cudaMemcpyHostToDevice) != cudaSuccess)
+    return SZ3G_E_CUDA;
+  if (!q->h64.empty() && cudaMemcpy((unsigned char*)q->dev + q->off64, q->h64.data(), q->h64.size(),
+                                    cudaMemcpyHostToDevice) != cudaSuccess)
+    return SZ3G_E_CUDA;
+  return SZ3G_OK;
 }
 
 template <typename T, bool COMP>
@@ -1152,7 +1512,7 @@ static int launch_decimate(const Plan& pl, const void* x, unsigned char* X, int 
 
 template <typename T>
 static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* const* R, uint32_t* hist, DevState* st,
-                          void* X, bool x1_ready, cudaStream_t s) {
+                          void* X, bool x1_ready, cudaStream_t s, LevelQueue* lq, int field) {
   const int kc = coarse_grid(pl);
   LevelArgs<T> a{};
   a.x = x;
@@ -1182,6 +1542,10 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
       a.x = x;
       for (int q = 0; q < 3; ++q) a.xs[q] = pl.fstride[q + 1] << k;
     }
+    if (lq) {
+      queue_add<T>(lq, pl, k, field, a);
+      continue;
+    }
     rc = run_level<T, true>(pl, k, a, s);
     if (rc) return rc;
   }
@@ -1191,7 +1555,7 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
 template <typename T>
 static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred, unsigned long long n_unpred,
                          const unsigned long long* zunit, void* const* R, T* out, DevState* st,
-                         T ebT, bool codes_padded, cudaStream_t s) {
+                         T ebT, bool codes_padded, cudaStream_t s, LevelQueue* lq, int field) {
   const int kc = coarse_grid(pl);
   LevelArgs<T> a{};
   a.codes = const_cast<uint16_t*>(codes);
@@ -1208,6 +1572,10 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
   for (int k = kc - 1; k >= 0; --k) {
     a.Rc = (const T*)R[k + 1];
     a.Rout = k == 0 ? out : (T*)R[k];
+    if (lq) {
+      queue_add<T>(lq, pl, k, field, a);
+      continue;
+    }
     rc = run_level<T, false>(pl, k, a, s);
     if (rc) return rc;
   }
@@ -1215,25 +1583,27 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
 }
 
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                          DevState* st, void* X, bool x1_ready, cudaStream_t s) {
-  if (pl.dtype == SZ3G_F32) return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, X, x1_ready, s);
-  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, X, x1_ready, s);
+                          DevState* st, void* X, bool x1_ready, cudaStream_t s, LevelQueue* lq, int field) {
+  if (pl.dtype == SZ3G_F32)
+    return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, X, x1_ready, s, lq, field);
+  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, X, x1_ready, s, lq, field);
 }
 
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
                          const unsigned long long* zunit, void* const* R, void* d_out,
-                         DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s) {
+                         DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s,
+                         LevelQueue* lq, int field) {
   if (pl.dtype == SZ3G_F32) {
     float e;
     uint32_t b = (uint32_t)ebT_bits;
     memcpy(&e, &b, 4);
     return recover_fused<float>(pl, codes, (const float*)unpred, n_unpred, zunit, R, (float*)d_out, st, e,
-                                codes_padded, s);
+                                codes_padded, s, lq, field);
   }
   double e;
   memcpy(&e, &ebT_bits, 8);
   return recover_fused<double>(pl, codes, (const double*)unpred, n_unpred, zunit, R, (double*)d_out, st, e,
-                               codes_padded, s);
+                               codes_padded, s, lq, field);
 }
 
 }  // namespace sz3g

@@ -87,6 +87,8 @@ _SIGS = {
     "sz3g_batch_configure": [_vp, C.c_int, C.c_int],
     "sz3g_batch_tune": [_vp, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "sz3g_batch_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(_u64)],
+    "sz3g_batch_set_queue": [_vp, C.c_int],
+    "sz3g_batch_queue_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "sz3g_batch_destroy": [_vp],
     "sz3g_select_costs": [_P, _vp, _u32, _u64, _vp, _vp],
     "sz3g_select_features": [_P, _vp, _u32, _u64, _vp, _vp],
@@ -279,6 +281,17 @@ class Batch:
 
     def configure(self, branches: int, cta_cap: int = 0) -> None:
         _chk(load().sz3g_batch_configure(self.h, branches, cta_cap), "sz3g_batch_configure")
+
+    def set_queue(self, on: bool) -> None:
+        """Level-queue mode: the grid levels of all fields in one persistent
+        launch per type from a cross-field work queue."""
+        _chk(load().sz3g_batch_set_queue(self.h, int(on)), "sz3g_batch_set_queue")
+
+    def queue_info(self):
+        """(level-queue mode on, grid levels in the queue)."""
+        on, lv = C.c_int(), C.c_int()
+        _chk(load().sz3g_batch_queue_info(self.h, C.byref(on), C.byref(lv)), "sz3g_batch_queue_info")
+        return bool(on.value), lv.value
 
     def tune(self, stream: int = 0):
         br, cap = C.c_int(), C.c_int()

@@ -59,7 +59,13 @@ def _batch_compress(params, xs, configs):
             if cfg == "tune":
                 br, cap = b.tune(G._stream_handle())
                 assert br >= 1 and cap >= 0
+            elif isinstance(cfg, str) and cfg.startswith("queue"):
+                b.set_queue(True)
+                b.configure(int(cfg[5:]), 0)
+                on, levels = b.queue_info()
+                assert on and levels > 0
             elif cfg is not None:
+                b.set_queue(False)
                 b.configure(*cfg)
             for o in outs:
                 o.zero_()
@@ -79,7 +85,7 @@ def test_batch_compress_matches_single_calls_and_oracle():
     xs = _fields(mix, 400)
     params = [G.make_params(x.shape, eb, eb_mode=G.REL, interp=it) for x, (_, eb, it) in zip(xs, mix)]
     ref = _single(params, xs)
-    runs = _batch_compress(params, xs, [None, (1, 0), (3, 0), (12, 16), (5, 1), "tune"])
+    runs = _batch_compress(params, xs, [None, (1, 0), (3, 0), (12, 16), (5, 1), "queue1", "queue5", "tune"])
     for r in runs:
         assert r == ref
     # two of the fields also against the oracle
@@ -98,8 +104,12 @@ def test_batch_decompress_matches_single_calls():
     b = G.Batch(None, [t.data_ptr() for t in sd], [t.data_ptr() for t in outs], [x.size * 4 for x in xs],
                 in_bytes=[len(s) for s in streams], decompress=True)
     try:
-        for cfg in (None, (2, 0), (10, 8)):
-            if cfg is not None:
+        for cfg in (None, (2, 0), (10, 8), "queue3", "queue1"):
+            if isinstance(cfg, str):
+                b.set_queue(True)
+                b.configure(int(cfg[5:]), 0)
+                assert b.queue_info()[0]
+            elif cfg is not None:
                 b.configure(*cfg)
             b.run(G._stream_handle())
             rc, _, st = b.results()
@@ -125,3 +135,54 @@ def test_batch_reports_per_field_errors():
         assert st[0] == 0 and st[1] == G.E_ZERO_RANGE_REL and rc == G.E_ZERO_RANGE_REL
     finally:
         b.close()
+
+
+def test_level_queue_mixed_types_and_ranks():
+    """The cross-field level queue over fields of both element types, ranks 1
+    to 4 (rank 4 keeps its own launches), both interpolations and uneven
+    bounds: streams byte-identical to one call per field, and back."""
+    rng = np.random.default_rng(9)
+    shapes = [(37, 29, 41), (64, 48, 40), (90, 70), (257,), (5, 6, 7, 8), (33, 17, 65), (128, 3, 50), (19, 160)]
+    xs, params = [], []
+    for i, sh in enumerate(shapes):
+        x = S.grf(sh, 900 + i)
+        dt = O.F64 if i % 3 == 1 else O.F32
+        xs.append(x.astype(np.float64 if dt == O.F64 else np.float32))
+        params.append(G.make_params(sh, float(np.exp(rng.uniform(np.log(1e-5), np.log(1e-2)))),
+                                    dtype=G.F64 if dt == O.F64 else G.F32, eb_mode=G.REL, interp=i % 2))
+    ref = _single(params, xs)
+    ins = [torch.from_numpy(x.reshape(-1)).to(DEV) for x in xs]
+    caps = [G.sz3g_compress_bound(p) for p in params]
+    outs = [torch.zeros(c, dtype=torch.uint8, device=DEV) for c in caps]
+    b = G.Batch(params, [t.data_ptr() for t in ins], [t.data_ptr() for t in outs], caps)
+    try:
+        for br in (1, 3, 8):
+            b.set_queue(True)
+            b.configure(br, 0)
+            on, levels = b.queue_info()
+            assert on and levels > 0
+            for o in outs:
+                o.zero_()
+            b.run(G._stream_handle())
+            rc, nbytes, st = b.results()
+            assert rc == 0 and all(v == 0 for v in st)
+            assert [o[:n].cpu().numpy().tobytes() for o, n in zip(outs, nbytes)] == ref
+    finally:
+        b.close()
+    sd = [torch.from_numpy(np.frombuffer(r, np.uint8).copy()).to(DEV) for r in ref]
+    back = [torch.full((x.size,), float("nan"), dtype=torch.float64 if x.dtype == np.float64 else torch.float32,
+                       device=DEV) for x in xs]
+    bd = G.Batch(None, [t.data_ptr() for t in sd], [t.data_ptr() for t in back], [x.nbytes for x in xs],
+                 in_bytes=[len(r) for r in ref], decompress=True)
+    try:
+        bd.set_queue(True)
+        bd.configure(4, 0)
+        bd.run(G._stream_handle())
+        rc, _, st = bd.results()
+        assert rc == 0 and all(v == 0 for v in st)
+        for r, o, x in zip(ref, back, xs):
+            want = O.decompress(r).reshape(-1)
+            got = o.cpu().numpy()
+            assert got.dtype == want.dtype and np.array_equal(got.view(np.uint8), want.view(np.uint8))
+    finally:
+        bd.close()
