@@ -21,11 +21,12 @@ int launch_decode_tables(const unsigned char* tab, uint32_t n_used, const uint8_
 int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, const uint32_t* chunk_words,
                          const uint16_t* sub_bits, unsigned long long n_chunks, uint32_t chunk, unsigned long long n,
                          const void* tables, unsigned long long* woff, uint16_t* codes, uint32_t* zcnt,
-                         void* scan_state, DevState* st, cudaStream_t s);
+                         void* scan_state, DevState* st, cudaStream_t s, bool state_zeroed = false);
 int launch_zero_counts(const uint16_t* codes, unsigned long long n, uint32_t chunk, unsigned long long n_chunks,
                        uint32_t* zcnt, cudaStream_t s);
 int launch_scan(const uint32_t* in, unsigned long long n, unsigned long long* out, uint32_t limit,
-                unsigned long long expect, int check_expect, void* state, DevState* st, cudaStream_t s);
+                unsigned long long expect, int check_expect, void* state, DevState* st, cudaStream_t s,
+                bool state_zeroed = false);
 size_t scan_state_bytes(unsigned long long n);
 int launch_pack_table(const uint8_t* len, const uint32_t* code, uint32_t nsym, uint32_t* table, cudaStream_t s);
 size_t dec_tables_bytes();
@@ -75,12 +76,13 @@ DecompressWs decompress_layout(const Plan& pl) {
   DecompressWs w{};
   Layout l;
   w.st = l.take(sizeof(DevState));
+  // the scans' look-back states next to the status block: one clear covers all three
+  w.scan1 = l.take(scan_state_bytes(pl.n_chunks));
+  w.scan2 = l.take(scan_state_bytes(pl.n_chunks * pl.nsub));
   w.tables = l.take(dec_tables_bytes());
   w.woff = l.take(pl.n_chunks * 8);
   w.zcnt = l.take(pl.n_chunks * pl.nsub * 4);
   w.zunit = l.take(pl.n_chunks * pl.nsub * 8);
-  w.scan1 = l.take(scan_state_bytes(pl.n_chunks));
-  w.scan2 = l.take(scan_state_bytes(pl.n_chunks * pl.nsub));
   w.codes = l.take(pl.N * 2 + 256);  // the level kernels copy whole 16-byte blocks of codes
   for (int k = 1; k <= pl.L; ++k) w.R[k] = l.take(pl.gsize[k] * pl.esz);
   w.R[0] = 0;
@@ -301,7 +303,7 @@ int decompress_enqueue(const Header& h, const void* d_stream, void* d_out, unsig
   const DecompressWs L = decompress_layout(pl);
   DevState* st = (DevState*)(ws + L.st);
   *st_out = st;
-  SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+  SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.tables, s));  // status block and the scans' look-back states
   const unsigned char* base = (const unsigned char*)d_stream;
   SZ3G_TRY(launch_decode_tables(base + h.off_table, h.n_used, nullptr, 2 * pl.radius, ws + L.tables, st, s));
   uint16_t* codes = (uint16_t*)(ws + L.codes);
@@ -309,9 +311,9 @@ int decompress_enqueue(const Header& h, const void* d_stream, void* d_out, unsig
                                 (const uint32_t*)(base + h.off_chunks),
                                 pl.nsub > 1 ? (const uint16_t*)(base + h.off_sub) : nullptr, pl.n_chunks, pl.chunk,
                                 pl.N, ws + L.tables, (unsigned long long*)(ws + L.woff), codes,
-                                (uint32_t*)(ws + L.zcnt), ws + L.scan1, st, s));
+                                (uint32_t*)(ws + L.zcnt), ws + L.scan1, st, s, true));
   SZ3G_TRY(launch_scan((uint32_t*)(ws + L.zcnt), pl.n_chunks * pl.nsub, (unsigned long long*)(ws + L.zunit), 0,
-                       h.n_unpred, 1, ws + L.scan2, st, s));
+                       h.n_unpred, 1, ws + L.scan2, st, s, true));
   void* R[34];
   for (int k = 0; k <= pl.L; ++k) R[k] = k == 0 ? d_out : ws + L.R[k];
   SZ3G_TRY(launch_recover_levels(pl, codes, base + SZ3G_HEADER_BYTES, h.n_unpred, (unsigned long long*)(ws + L.zunit),

@@ -729,9 +729,14 @@ __global__ void __launch_bounds__(kEncWarps * 32) count_kernel(const uint16_t* _
 
 // Pass 2: one warp per chunk writes the chunk's bits (MSB first, through a
 // shared-memory word ring), its table entries, and gathers its unpredictable
-// values from the input.
-template <typename U>
-__global__ void __launch_bounds__(kEncWarps * 32) emit_kernel(const EncArgs a, const __grid_constant__ PassMap map) {
+// values from the input.  ONEPASS (stream mode): the warp takes its chunk by
+// a ticket, counts the chunk's bits and zero codes itself and finds their
+// prefixes over the earlier chunks by decoupled look-back (wstat / zstat,
+// cleared with the workspace), so no count pass or scans run before it.
+template <typename U, bool ONEPASS>
+__global__ void __launch_bounds__(kEncWarps * 32) emit_kernel(const EncArgs a, const __grid_constant__ PassMap map,
+                                                              uint32_t* ticket, unsigned long long* wstat,
+                                                              unsigned long long* zstat) {
   __shared__ uint32_t ring[kEncWarps][kRingWords];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t* buf = ring[w];
@@ -739,12 +744,58 @@ __global__ void __launch_bounds__(kEncWarps * 32) emit_kernel(const EncArgs a, c
   __syncwarp();
   DevState* st = a.st;
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kEncWarps;
-  for (unsigned long long j = (unsigned long long)blockIdx.x * kEncWarps + w; j < a.n_chunks; j += nwarps) {
+  unsigned long long j = (unsigned long long)blockIdx.x * kEncWarps + w;
+  for (;; j += nwarps) {
+    if (ONEPASS) {
+      uint32_t t = 0;
+      if (lane == 0) t = atomicAdd(ticket, 1u);
+      j = __shfl_sync(0xffffffffu, t, 0);
+    }
+    if (j >= a.n_chunks) break;
     const unsigned long long i0 = j * a.chunk;
     const uint32_t cnt = (uint32_t)min((unsigned long long)a.chunk, a.n - i0);
     const uint16_t* cp = a.codes + i0;
-    const unsigned long long words = a.cwords[j];
-    const unsigned long long wexcl = a.wexcl[j], zexcl = a.zexcl[j];
+    unsigned long long words, wexcl, zexcl;
+    if (ONEPASS) {
+      uint32_t bits = 0, zeros = 0;
+      for (uint32_t t = lane * 8; t < cnt; t += 256) {
+        if (t + 8 <= cnt) {
+          const uint4 v = *reinterpret_cast<const uint4*>(cp + t);
+          const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t c0 = wv[q] & 0xffffu, c1 = wv[q] >> 16;
+            bits += (a.table[c0] >> 24) + (a.table[c1] >> 24);
+            zeros += (c0 == 0) + (c1 == 0);
+          }
+        } else {
+          for (uint32_t u = t; u < cnt; ++u) {
+            const uint32_t c = cp[u];
+            bits += a.table[c] >> 24;
+            zeros += c == 0;
+          }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        bits += __shfl_xor_sync(0xffffffffu, bits, o);
+        zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
+      }
+      words = (bits + 31) >> 5;
+      if (lane == 0) {
+        st_release(wstat + j, (j == 0 ? kFlagInc : kFlagAgg) | words);
+        st_release(zstat + j, (j == 0 ? kFlagInc : kFlagAgg) | zeros);
+      }
+      wexcl = lookback(wstat, (long long)j, st);
+      zexcl = lookback(zstat, (long long)j, st);
+      if (lane == 0 && j > 0) {
+        st_release(wstat + j, kFlagInc | (wexcl + words));
+        st_release(zstat + j, kFlagInc | (zexcl + zeros));
+      }
+    } else {
+      words = a.cwords[j];
+      wexcl = a.wexcl[j];
+      zexcl = a.zexcl[j];
+    }
     if (lane == 0 && j == a.n_chunks - 1) st->n_words = wexcl + words;
     // destinations
     uint32_t* pay;
@@ -958,9 +1009,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* in, 
   if (bad) atomicOr(&st->flags, kFlagCorrupt);
 }
 
+// state_zeroed: the caller cleared `state` already (with its workspace).
 int launch_scan(const uint32_t* in, unsigned long long n, unsigned long long* out, uint32_t limit,
-                unsigned long long expect, int check_expect, void* state, DevState* st, cudaStream_t s) {
-  if (cudaMemsetAsync(state, 0, scan_state_bytes(n), s) != cudaSuccess) return SZ3G_E_CUDA;
+                unsigned long long expect, int check_expect, void* state, DevState* st, cudaStream_t s,
+                bool state_zeroed = false) {
+  if (!state_zeroed && cudaMemsetAsync(state, 0, scan_state_bytes(n), s) != cudaSuccess) return SZ3G_E_CUDA;
   const unsigned long long ntiles = (n + kScanTile - 1) / kScanTile;
   SZ3G_LAUNCH(kKScan, s,
               scan_kernel<<<(unsigned)(ntiles ? ntiles : 1), kScanThreads, 0, s>>>(
@@ -973,7 +1026,9 @@ size_t encode_scratch_bytes(unsigned long long n_chunks) {
          2 * ((scan_state_bytes(n_chunks) + 255) & ~255ull);
 }
 
-// count -> two scans -> emit.  scratch: encode_scratch_bytes(n_chunks).
+// count -> two scans -> emit (or, stream mode on at most kOnePassMaxChunks
+// chunks, emit alone).  scratch: encode_scratch_bytes(n_chunks).
+constexpr unsigned long long kOnePassMaxChunks = 1024;
 static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch, cudaStream_t s) {
   const unsigned long long nch = a.n_chunks;
   const size_t a4 = (nch * 4 + 255) & ~255ull, a8 = (nch * 8 + 255) & ~255ull,
@@ -987,18 +1042,34 @@ static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch
   int nb = (int)((nch + kEncWarps - 1) / kEncWarps);
   if (nb > 152 * 8) nb = 152 * 8;
   if (nb < 1) nb = 1;
+  if (a.mode == kEncodeStream && a.emit_payload && nch <= kOnePassMaxChunks) {
+    // one pass: the compressor's workspace (this scratch included) was
+    // cleared when it started -- cw[0] is the ticket, we / ze the look-back states.
+    // Only for fields of few chunks: with thousands of chunks in flight the
+    // look-back frontier (about 32 chunks per round) becomes a serial chain.
+    if (a.esz == 4)
+      SZ3G_LAUNCH(kKEncode, s, emit_kernel<uint32_t, true><<<nb, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze));
+    else
+      SZ3G_LAUNCH(kKEncode, s, emit_kernel<unsigned long long, true><<<nb, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze));
+    return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+  }
   SZ3G_LAUNCH(kKEncode, s, count_kernel<<<nb, kEncWarps * 32, 0, s>>>(a.codes, a.table, a.n, nch, a.chunk, cw, cz));
-  int rc = launch_scan(cw, nch, we, 0, 0, 0, s1, a.st, s);
+  // stream mode: the compressor's workspace (this scratch included) was cleared when it started
+  const bool zeroed = a.mode == kEncodeStream;
+  int rc = launch_scan(cw, nch, we, 0, 0, 0, s1, a.st, s, zeroed);
   if (rc) return rc;
-  rc = launch_scan(cz, nch, ze, 0, 0, 0, s2, a.st, s);
+  rc = launch_scan(cz, nch, ze, 0, 0, 0, s2, a.st, s, zeroed);
   if (rc) return rc;
   a.cwords = cw;
   a.wexcl = we;
   a.zexcl = ze;
   if (a.esz == 4)
-    SZ3G_LAUNCH(kKEncode, s, emit_kernel<uint32_t><<<nb, kEncWarps * 32, 0, s>>>(a, *map));
+    SZ3G_LAUNCH(kKEncode, s,
+                emit_kernel<uint32_t, false><<<nb, kEncWarps * 32, 0, s>>>(a, *map, nullptr, nullptr, nullptr));
   else
-    SZ3G_LAUNCH(kKEncode, s, emit_kernel<unsigned long long><<<nb, kEncWarps * 32, 0, s>>>(a, *map));
+    SZ3G_LAUNCH(kKEncode, s,
+                emit_kernel<unsigned long long, false><<<nb, kEncWarps * 32, 0, s>>>(a, *map, nullptr, nullptr,
+                                                                                    nullptr));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
@@ -1475,9 +1546,9 @@ int launch_decode_tables(const unsigned char* tab, uint32_t n_used, const uint8_
 int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, const uint32_t* chunk_words,
                          const uint16_t* sub_bits, unsigned long long n_chunks, uint32_t chunk, unsigned long long n,
                          const void* tables, unsigned long long* woff, uint16_t* codes, uint32_t* zcnt,
-                         void* scan_state, DevState* st, cudaStream_t s) {
+                         void* scan_state, DevState* st, cudaStream_t s, bool state_zeroed) {
   const uint32_t maxw = (uint32_t)(((unsigned long long)chunk * SZ3G_LMAX + 31) / 32);
-  const int rc = launch_scan(chunk_words, n_chunks, woff, maxw, n_words, 1, scan_state, st, s);
+  const int rc = launch_scan(chunk_words, n_chunks, woff, maxw, n_words, 1, scan_state, st, s, state_zeroed);
   if (rc) return rc;
   DecArgs a{};
   a.words = words;

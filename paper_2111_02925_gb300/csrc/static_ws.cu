@@ -26,7 +26,7 @@ int launch_decode_tables(const unsigned char* tab, uint32_t n_used, const uint8_
 int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, const uint32_t* chunk_words,
                          const uint16_t* sub_bits, unsigned long long n_chunks, uint32_t chunk, unsigned long long n,
                          const void* tables, unsigned long long* woff, uint16_t* codes, uint32_t* zcnt,
-                         void* scan_state, DevState* st, cudaStream_t s);
+                         void* scan_state, DevState* st, cudaStream_t s, bool state_zeroed = false);
 
 constexpr size_t kStaticScratchBytes = 4u << 20;  // 4 MiB
 
