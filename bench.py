@@ -317,6 +317,26 @@ def run_batch(args):
     assert rc == 0 and list(nb2) == list(nbs)
     rc, _, st = bd.results()
     assert rc == 0
+    qc, qd = bc.queue_info()[0], bd.queue_info()[0]
+    tuned = {"compress": {"branches": tc[0], "cta_cap": tc[1], "level_queue": qc, "graph_nodes": bc.info()[2],
+                          "ms": timeit(lambda: bc.run(sh), 3)},
+             "decompress": {"branches": td[0], "cta_cap": td[1], "level_queue": qd, "graph_nodes": bd.info()[2],
+                            "ms": timeit(lambda: bd.run(sh), 3)}}
+    # the cross-field level queue at its best branch count, each direction (after the tuned run)
+    queue = {}
+    for b, lab in ((bc, "compress"), (bd, "decompress")):
+        br0, cap0 = b.info()[:2]
+        on0 = b.queue_info()[0]
+        b.set_queue(True)
+        best = None
+        for br in (16, 64, 128):
+            b.configure(min(br, len(xs)), 0)
+            t = timeit(lambda: b.run(sh), 3)
+            if best is None or t < best[0]:
+                best = (t, br)
+        queue[lab] = {"ms": best[0], "branches": best[1], "levels": b.queue_info()[1]}
+        b.set_queue(on0)
+        b.configure(br0, cap0)
     t_single = timeit(per_field, max(1, min(k, 3)))
     line = {
         "metric": "batch compress+decompress GB/s (input bytes), uneven fields, 1 GB300",
@@ -329,8 +349,8 @@ def run_batch(args):
                    "fields": args.fields, "input_bytes": in_bytes, "stream_bytes": int(sum(nbs))},
         "per_field_calls": {"ms_per_step": t_single, "GB/s": in_bytes / (t_single * 1e-3) / 1e9},
         "speedup_vs_per_field_calls": t_single / t_batch,
-        "tuned": {"compress": {"branches": tc[0], "cta_cap": tc[1], "graph_nodes": bc.info()[2]},
-                  "decompress": {"branches": td[0], "cta_cap": td[1], "graph_nodes": bd.info()[2]}},
+        "tuned": tuned,
+        "level_queue_ms": queue,
     }
     print(json.dumps(line), flush=True)
     bc.close()

@@ -301,7 +301,8 @@ int sz3g_batch_set_queue(sz3g_batch* batch, int on);
 int sz3g_batch_queue_info(const sz3g_batch* batch, int* on, int* levels);
 
 /*
- * Autotuner: runs the batch (twice after a warm-up) under every combination
+ * Autotuner: runs the batch (three times after two warm-ups, keeping the
+ * fastest of the three) under every combination
  * of 1..256 branches and CTA caps of none, 1, 1/2 and 1/4 of the SMs, and
  * in level-queue mode under every branch count, keeps the fastest and
  * reports it.  Overwrites the batch's outputs; synchronises.
