@@ -120,6 +120,17 @@ int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t ou
  * copied to the host with a synchronous cudaMemcpy).  Fills *p and the point
  * count.  Errors: SZ3G_E_CORRUPT, SZ3G_E_INVAL (NULL pointers), SZ3G_E_CUDA.
  */
+/*
+ * Graph cache (on by default): sz3g_compress / sz3g_decompress calls given a
+ * caller-owned workspace replay, as one CUDA graph launch, the pipeline
+ * captured by an earlier call with the same parameters (stream header) and
+ * the same buffers and workspace -- the per-kernel host work between the
+ * kernels is then skipped.  Up to 8 pipelines are kept (least recently used
+ * replaced); not used while profiling is on.  on = 0 turns it off and frees
+ * the cached graphs.
+ */
+int sz3g_graph_cache(int on);
+
 int sz3g_read_header(const void* stream, size_t bytes, int stream_on_device, sz3g_params* p,
                      uint64_t* n_points);
 

@@ -3,6 +3,7 @@
 // the stage entry points, and the mapping of device status bits to statuses.
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -321,6 +322,97 @@ int decompress_enqueue(const Header& h, const void* d_stream, void* d_out, unsig
   return SZ3G_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Graph cache: a compress or decompress call whose workspace is the
+// caller's replays the pipeline captured by an earlier call with the same
+// parameters (or stream header) and buffers -- everything the host-side
+// enqueue reads -- as one graph launch, without the per-kernel host work
+// (tensor maps, launch configuration) between the kernels.  Not used while
+// per-launch profiling is on.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GraphEntry {
+  std::vector<unsigned char> key;
+  cudaGraphExec_t exec = nullptr;
+  DevState* st = nullptr;
+  unsigned long long launches = 0, tick = 0;
+};
+
+constexpr int kGraphCacheEntries = 8;
+std::mutex g_gmu;
+GraphEntry g_graphs[kGraphCacheEntries];
+unsigned long long g_gtick = 0;
+bool g_gcache_on = true;
+
+template <typename T>
+void key_add(std::vector<unsigned char>& k, const T& v) {
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+  k.insert(k.end(), b, b + sizeof(T));
+}
+
+// Runs `enqueue(stream, &st)` on s through the cache.
+template <typename F>
+int run_cached(const std::vector<unsigned char>& key, cudaStream_t s, F enqueue, DevState** st_out) {
+  std::lock_guard<std::mutex> lk(g_gmu);
+  for (GraphEntry& e : g_graphs)
+    if (e.exec && e.key == key) {
+      e.tick = ++g_gtick;
+      if (cudaGraphLaunch(e.exec, s) != cudaSuccess) {
+        cudaGetLastError();
+        return SZ3G_E_CUDA;
+      }
+      count_launches(e.launches);
+      *st_out = e.st;
+      return SZ3G_OK;
+    }
+  // capture on a private stream (nothing runs), then replay on s
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return enqueue(s, st_out);
+  }
+  const unsigned long long l0 = launch_total();
+  DevState* st = nullptr;
+  int rc = SZ3G_OK;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    rc = SZ3G_E_CUDA;
+  } else {
+    rc = enqueue(cs, &st);
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess) rc = rc == SZ3G_OK ? SZ3G_E_CUDA : rc;
+  }
+  cudaStreamDestroy(cs);
+  const unsigned long long launches = launch_total() - l0;
+  cudaGraphExec_t exec = nullptr;
+  if (rc == SZ3G_OK && g && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  if (rc != SZ3G_OK || !exec) {  // not capturable: launch directly
+    if (exec) cudaGraphExecDestroy(exec);
+    return rc != SZ3G_OK ? rc : enqueue(s, st_out);
+  }
+  GraphEntry* slot = &g_graphs[0];
+  for (GraphEntry& e : g_graphs)
+    if (!e.exec || e.tick < slot->tick) slot = &e;
+  if (slot->exec) cudaGraphExecDestroy(slot->exec);
+  slot->key = key;
+  slot->exec = exec;
+  slot->st = st;
+  slot->launches = launches;
+  slot->tick = ++g_gtick;
+  if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+    cudaGetLastError();
+    return SZ3G_E_CUDA;
+  }
+  *st_out = st;
+  return SZ3G_OK;
+}
+
+bool use_graph_cache(const void* user_ws) { return user_ws && g_gcache_on && !profiling_on(); }
+
+}  // namespace
+
 }  // namespace sz3g
 
 using namespace sz3g;
@@ -371,11 +463,40 @@ int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t ou
   unsigned char* ws;
   SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
   DevState* st = nullptr;
-  SZ3G_TRY(compress_enqueue(p, pl, d_in, d_out, out_capacity, ws, s, &st));
+  if (use_graph_cache(d_workspace)) {
+    std::vector<unsigned char> key;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    key_add(key, 'C');
+    key_add(key, dev);
+    key_add(key, *p);
+    key_add(key, d_in);
+    key_add(key, d_out);
+    key_add(key, out_capacity);
+    key_add(key, d_workspace);
+    key_add(key, ws_bytes);
+    SZ3G_TRY(run_cached(
+        key, s,
+        [&](cudaStream_t es, DevState** sto) { return compress_enqueue(p, pl, d_in, d_out, out_capacity, ws, es, sto); },
+        &st));
+  } else {
+    SZ3G_TRY(compress_enqueue(p, pl, d_in, d_out, out_capacity, ws, s, &st));
+  }
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
   SZ3G_TRY(status_of(h.flags));
   *out_bytes = (size_t)h.out_bytes;
+  return SZ3G_OK;
+}
+
+int sz3g_graph_cache(int on) {
+  std::lock_guard<std::mutex> lk(g_gmu);
+  g_gcache_on = on != 0;
+  if (!g_gcache_on)
+    for (GraphEntry& e : g_graphs) {
+      if (e.exec) cudaGraphExecDestroy(e.exec);
+      e = GraphEntry{};
+    }
   return SZ3G_OK;
 }
 
@@ -412,7 +533,25 @@ int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_
   unsigned char* ws;
   SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
   DevState* st = nullptr;
-  SZ3G_TRY(decompress_enqueue(h, d_stream, d_out, ws, s, &st));
+  if (use_graph_cache(d_workspace)) {
+    std::vector<unsigned char> key;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    key_add(key, 'D');
+    key_add(key, dev);
+    key.insert(key.end(), hb, hb + SZ3G_HEADER_BYTES);
+    key_add(key, bytes);
+    key_add(key, d_stream);
+    key_add(key, d_out);
+    key_add(key, out_capacity);
+    key_add(key, d_workspace);
+    key_add(key, ws_bytes);
+    SZ3G_TRY(run_cached(
+        key, s, [&](cudaStream_t es, DevState** sto) { return decompress_enqueue(h, d_stream, d_out, ws, es, sto); },
+        &st));
+  } else {
+    SZ3G_TRY(decompress_enqueue(h, d_stream, d_out, ws, s, &st));
+  }
   DevState hs;
   SZ3G_TRY(read_state(st, &hs, s));
   return status_of(hs.flags);

@@ -102,6 +102,12 @@ enum KernelId {
   kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKPublish, kKSelect, kKMlp, kKernelCount
 };
 
+// prof.cu: whether per-launch timing is on; launches replayed inside a graph
+// are added to the launch count by the replaying code.
+bool profiling_on();
+void count_launches(unsigned long long n);
+unsigned long long launch_total();
+
 // Counts a launch and, while profiling is on, brackets it with CUDA events.
 class LaunchScope {
  public:

@@ -44,6 +44,15 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+bool profiling_on() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_on;
+}
+
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+unsigned long long launch_total() { return g_launches.load(); }
+
 LaunchScope::LaunchScope(int kid, cudaStream_t s) : kid_(kid), s_(s), a_(nullptr) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   std::lock_guard<std::mutex> lk(g_mu);

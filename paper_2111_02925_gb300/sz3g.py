@@ -90,6 +90,7 @@ _SIGS = {
     "sz3g_batch_set_queue": [_vp, C.c_int],
     "sz3g_batch_queue_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "sz3g_batch_destroy": [_vp],
+    "sz3g_graph_cache": [C.c_int],
     "sz3g_select_costs": [_P, _vp, _u32, _u64, _vp, _vp],
     "sz3g_select_features": [_P, _vp, _u32, _u64, _vp, _vp],
     "sz3g_select_sampled": [_P, _vp, _u32, _u64, _vp, _vp],
@@ -470,3 +471,8 @@ def workspace(p: Params, for_decompress: bool, device="cuda"):
     torch = _torch()
     n = sz3g_workspace_size(p, int(for_decompress))
     return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def sz3g_graph_cache(on: bool) -> None:
+    """Turn the compress / decompress graph cache on or off (on by default)."""
+    _chk(load().sz3g_graph_cache(int(on)), "sz3g_graph_cache")
