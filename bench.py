@@ -76,6 +76,25 @@ def dist_env():
     return ws, rank, local
 
 
+def shard_units(n: int, ws: int, rank: int):
+    """Global indices of the units rank `rank` of `ws` processes when every
+    rank takes n units of its own (weak scaling): a contiguous block."""
+    return list(range(rank * n, (rank + 1) * n))
+
+
+def reduce_over_ranks(values, op: str = "max", device=None):
+    """Element-wise max or sum of a list of floats over the process group
+    (the values themselves without one)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -262,10 +281,18 @@ def run_batch(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local if ws > 1 else 0)
     dev = torch.device("cuda", torch.cuda.current_device())
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
     B.build()
     G.load()
-    mix = S.batch_shapes(args.fields, 4)
-    xs = [grf_gpu(d, 4000 + i, dev).reshape(-1) for i, (d, _, _) in enumerate(mix)]
+    # every rank its own `fields` fields (weak scaling); field g of the whole
+    # job has the g-th shape of the mix and seed 4000 + g
+    own = shard_units(args.fields, ws, rank)
+    full = S.batch_shapes(args.fields * ws, 4)
+    mix = [full[g] for g in own]
+    xs = [grf_gpu(d, 4000 + g, dev).reshape(-1) for g, (d, _, _) in zip(own, mix)]
     params = [G.make_params(d, eb, eb_mode=G.REL, interp=it) for d, eb, it in mix]
     caps = [G.sz3g_compress_bound(p) for p in params]
     streams = [torch.empty(c, dtype=torch.uint8, device=dev) for c in caps]
@@ -303,6 +330,8 @@ def run_batch(args):
         for _ in range(max(args.warmup, 3)):
             fn()
         torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(k):
@@ -338,15 +367,23 @@ def run_batch(args):
         b.set_queue(on0)
         b.configure(br0, cap0)
     t_single = timeit(per_field, max(1, min(k, 3)))
+    t_batch, t_single = reduce_over_ranks([t_batch, t_single], "max", dev)
+    in_bytes, stream_total = reduce_over_ranks([in_bytes, sum(nbs)], "sum", dev)
+    if rank != 0:
+        bc.close()
+        bd.close()
+        dist.destroy_process_group()
+        return 0
     line = {
         "metric": "batch compress+decompress GB/s (input bytes), uneven fields, 1 GB300",
-        "value": in_bytes / (t_batch * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": k,
+        "value": in_bytes / (t_batch * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": ws, "steps": k,
         "warmup": max(args.warmup, 3), "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.fields} FP32 3-D k^-3 random fields, axes log-uniform in [32, 256], "
                                "REL eb log-uniform in [1e-5, 1e-2], linear/cubic at random (seed 4); "
                                "step = compress all + decompress all",
-                   "fields": args.fields, "input_bytes": in_bytes, "stream_bytes": int(sum(nbs))},
+                   "fields": args.fields * ws, "fields_per_gpu": args.fields, "input_bytes": int(in_bytes),
+                   "stream_bytes": int(stream_total)},
         "per_field_calls": {"ms_per_step": t_single, "GB/s": in_bytes / (t_single * 1e-3) / 1e9},
         "speedup_vs_per_field_calls": t_single / t_batch,
         "tuned": tuned,
@@ -355,6 +392,8 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
     bc.close()
     bd.close()
+    if ws > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -595,10 +634,7 @@ def main():
         if c:
             kern[name] = (t / nprof, c / nprof)
     G.sz3g_profile_enable(False)
-    if ws > 1:
-        t = torch.tensor([step_ms, comp_ms, dec_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms, comp_ms, dec_ms = [float(v) for v in t.tolist()]
+    step_ms, comp_ms, dec_ms = reduce_over_ranks([step_ms, comp_ms, dec_ms], "max", dev)
     in_bytes = x.nbytes
     value = ws * in_bytes / (step_ms * 1e-3) / 1e9
     # roofline of the dominant kernel
