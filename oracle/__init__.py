@@ -25,7 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libsz3o.so")
-_SOURCES = ("sz3o.c", "sz3o_typed.inc", "sz3o.h")
+_SOURCES = ("sz3o.c", "sz3o_typed.inc", "sz3o.h", "szlz.c")
 _CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
 _lock = threading.Lock()
 _lib = None
@@ -80,7 +80,7 @@ def build(force: bool = False) -> str:
             if all(os.path.getmtime(s) <= t for s in srcs):
                 return _LIB_PATH
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", *_CFLAGS, "-o", tmp, os.path.join(_HERE, "sz3o.c"), "-lm"]
+        cmd = ["gcc", *_CFLAGS, "-o", tmp, os.path.join(_HERE, "sz3o.c"), os.path.join(_HERE, "szlz.c"), "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
@@ -111,11 +111,15 @@ def lib():
             "sz3o_decompress": [vp, C.c_uint64, vp, C.c_uint64],
             "sz3o_select_costs": [P, vp, C.c_uint32, C.c_uint32, C.c_uint64, vp],
             "sz3o_select_features": [P, vp, C.c_uint32, C.c_uint32, C.c_uint64, vp],
+            "sz3o_lz_compress": [vp, C.c_uint64, vp, C.c_uint64, u64p],
+            "sz3o_lz_decompress": [vp, C.c_uint64, vp, C.c_uint64, u64p],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = C.c_int
+        L.sz3o_lz_bound.argtypes = [C.c_uint64]
+        L.sz3o_lz_bound.restype = C.c_uint64
         _lib = L
     return _lib
 
@@ -370,3 +374,35 @@ def params_for_choices(p: Params, dims, choices) -> Params:
                     order=[p.dim_order[i] for i in range(nd)], radius=p.radius, chunk=p.chunk_codes,
                     level_interp=li, level_order=lo)
     return q
+
+
+LZ_BLOCK = 32768
+
+
+def lz_compress(data: bytes) -> bytes:
+    """The lossless stage (szlz.c): byte-level LZ77 over 32 KiB blocks."""
+    n = len(data)
+    src = np.frombuffer(data, np.uint8) if n else np.zeros(1, np.uint8)
+    cap = int(lib().sz3o_lz_bound(n))
+    out = np.zeros(cap, np.uint8)
+    nb = C.c_uint64(0)
+    _check(lib().sz3o_lz_compress(_ptr(src), n, _ptr(out), cap, C.byref(nb)), "sz3o_lz_compress")
+    return out[: nb.value].tobytes()
+
+
+def lz_decompress_status(stream: bytes, cap: int):
+    """(status, bytes) of decoding an SZLZ stream into at most cap bytes."""
+    src = np.frombuffer(stream, np.uint8) if len(stream) else np.zeros(1, np.uint8)
+    out = np.zeros(max(cap, 1), np.uint8)
+    n = C.c_uint64(0)
+    rc = lib().sz3o_lz_decompress(_ptr(src), len(stream), _ptr(out), cap, C.byref(n))
+    return rc, (out[: n.value].tobytes() if rc == OK else b"")
+
+
+def lz_decompress(stream: bytes) -> bytes:
+    if len(stream) < 16:
+        raise OracleError(E_CORRUPT, "sz3o_lz_decompress")
+    n = int(np.frombuffer(stream[8:16], np.uint64)[0])
+    rc, out = lz_decompress_status(stream, n)
+    _check(rc, "sz3o_lz_decompress")
+    return out

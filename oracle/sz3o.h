@@ -146,6 +146,24 @@ int sz3o_select_costs(const sz3o_params* p, const void* x, uint32_t level, uint3
 int sz3o_select_features(const sz3o_params* p, const void* x, uint32_t level, uint32_t nblocks, uint64_t seed,
                          double* feat);
 
+/* Optional lossless stage after the Huffman coder (szlz.c): byte-level LZ77
+ * of our own definition over independent blocks of SZLZ_BLOCK bytes.
+ * Stream (little-endian): "SZLZ", u32 block size, u64 n (input bytes),
+ * u32 n_blocks = ceil(n / block), u32 0; then u32 size[n_blocks] (payload
+ * bytes of block b; bit 31 set: stored raw); then, from the next 8-byte
+ * boundary, the payloads in block order, each padded with zeros to 4 bytes.
+ * A coded payload is a run of sequences: token (literal count, max 15) << 4 |
+ * (match length - 4, max 15); when the literal nibble is 15, the rest of the
+ * count as 255-bytes and a last byte < 255; the literals; then, unless the
+ * payload ends there (the last sequence: literals only, match nibble 0), a
+ * u16 distance back (1..65535) and, when the match nibble is 15, the rest of
+ * the length the same way.  Matches may overlap their own output. */
+#define SZLZ_BLOCK 32768
+#define SZLZ_HEADER 24
+uint64_t sz3o_lz_bound(uint64_t n);
+int sz3o_lz_compress(const void* in, uint64_t n, void* out, uint64_t capacity, uint64_t* out_bytes);
+int sz3o_lz_decompress(const void* in, uint64_t bytes, void* out, uint64_t capacity, uint64_t* out_n);
+
 #ifdef __cplusplus
 }
 #endif
