@@ -13,6 +13,7 @@ steps.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sz3g|reference]
   python bench.py --workload batch   # the uneven 256-field batch, batched vs one call per field
   python bench.py --workload selector  # per-level selection on a 1024^3 field with fronts
+  python bench.py --workload lossless  # the optional lossless stage on two workloads' streams
 
 --impl reference times the serial CPU oracle on the host cores, on a bounded
 sample (a 128^3 corner of the same field) per step.  N > 1 (torchrun) runs
@@ -48,7 +49,7 @@ def parse():
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="field", choices=["field", "batch", "selector"])
+    ap.add_argument("--workload", default="field", choices=["field", "batch", "selector", "lossless"])
     ap.add_argument("--train-fields", type=int, default=400)
     ap.add_argument("--fields", type=int, default=256)
     return ap.parse_args()
@@ -543,8 +544,83 @@ def run_selector(args):
     return 0
 
 
+def run_lossless(args):
+    """The optional lossless stage after the Huffman coder on the streams of
+    two workloads: the 512^3 k^-3 field (REL 1e-3, cubic) and the 1800 x 3600
+    FP64 lat-lon field with 30% exact zeros (ABS 1e-6 of the range, cubic).
+    Reports stream GB/s of the stage each way and the extra ratio."""
+    import numpy as np
+    import torch
+
+    from paper_2111_02925_gb300 import build as B
+    from paper_2111_02925_gb300 import synthetic as S
+    from paper_2111_02925_gb300 import sz3g as G
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    B.build()
+    G.load()
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    res = {}
+    for name, x, p in (
+        ("grf512_rel1e-3", S.grf((args.size,) * 3, SEED), None),
+        ("latlon1800x3600_f64_abs1e-6", S.latlon(1800, 3600, seed=3), None),
+    ):
+        if p is None:
+            if x.dtype == np.float64:
+                p = G.make_params(x.shape, 1e-6 * (float(x.max()) - float(x.min())), dtype=G.F64, eb_mode=G.ABS,
+                                  interp=G.CUBIC)
+            else:
+                p = G.make_params(x.shape, EB, eb_mode=G.REL, interp=G.CUBIC)
+        xd = torch.from_numpy(np.ascontiguousarray(x).reshape(-1)).to(dev)
+        cap = G.sz3g_compress_bound(p)
+        st = torch.empty(cap, dtype=torch.uint8, device=dev)
+        rc, nb = G.sz3g_compress(p, xd.data_ptr(), st.data_ptr(), cap, stream=sh)
+        assert rc == 0
+        lcap = G.sz3g_lossless_bound(nb)
+        lz = torch.empty(lcap, dtype=torch.uint8, device=dev)
+        back = torch.empty(nb + 16, dtype=torch.uint8, device=dev)
+
+        def comp():
+            rc, m = G.sz3g_lossless_compress(st.data_ptr(), nb, lz.data_ptr(), lcap, sh)
+            assert rc == 0
+            return m
+
+        def dec(m):
+            rc, n2 = G.sz3g_lossless_decompress(lz.data_ptr(), m, back.data_ptr(), nb, sh)
+            assert rc == 0 and n2 == nb
+
+        m = comp()
+        dec(m)
+        assert bool(torch.equal(back[:nb], st[:nb]))
+        k = max(3, min(args.steps, 20))
+        tc, td = [], []
+        for _ in range(k):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            comp()
+            e[1].record()
+            dec(m)
+            e[2].record()
+            torch.cuda.synchronize()
+            tc.append(e[0].elapsed_time(e[1]))
+            td.append(e[1].elapsed_time(e[2]))
+        res[name] = {"input_bytes": int(x.nbytes), "stream_bytes": int(nb), "lossless_bytes": int(m),
+                     "ratio_before": x.nbytes / nb, "ratio_after": x.nbytes / m, "gain": nb / m,
+                     "compress_ms": statistics.median(tc), "decompress_ms": statistics.median(td),
+                     "compress_GB/s": nb / (statistics.median(tc) * 1e-3) / 1e9,
+                     "decompress_GB/s": nb / (statistics.median(td) * 1e-3) / 1e9}
+    line = {"metric": "lossless stage GB/s (stream bytes) and ratio gain, 1 GB300", "unit": "GB/s",
+            "value": res["grf512_rel1e-3"]["compress_GB/s"], "n_gpus": 1, "higher_is_better": True,
+            "dtype": "u8", "data": "synthetic", "config": {"workload": "streams of sz3g_compress", "fields": res}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "lossless":
+        return run_lossless(args)
     if args.workload == "selector":
         return run_selector(args)
     if args.impl == "reference":

@@ -51,6 +51,8 @@ enum { SZ3G_LINEAR = 0, SZ3G_CUBIC = 1 };
 #define SZ3G_MAX_LEVELS 32
 #define SZ3G_LMAX 24        /* longest Huffman code in a stream            */
 #define SZ3G_HEADER_BYTES 288
+#define SZ3G_LZ_BLOCK 32768   /* bytes per block of the lossless stage */
+#define SZ3G_LZ_HEADER 24     /* its header, before the block size table */
 
 /*
  * Compression parameters (the paper's Config<T,N>, Appendix A.1 / Alg. 1
@@ -130,6 +132,34 @@ int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t ou
  * the cached graphs.
  */
 int sz3g_graph_cache(int on);
+
+/* ---------------------------------------------------------------------------
+ * Optional lossless stage after the Huffman coder (SZ3 ends its pipelines in
+ * a dictionary coder): byte-level LZ77 over independent SZ3G_LZ_BLOCK-byte
+ * blocks, for any byte buffer (e.g. a stream of sz3g_compress).  Format
+ * (little-endian): "SZLZ", u32 block size, u64 n, u32 n_blocks =
+ * ceil(n / block), u32 0; u32 size[n_blocks] (payload bytes of block b; bit
+ * 31: stored raw); from the next 8-byte boundary the payloads in block order,
+ * each padded with zeros to 4 bytes.  A coded payload is a run of sequences:
+ * token = (literal count, max 15) << 4 | (match length - 4, max 15); the rest
+ * of a count of 15 or more as 255-bytes ending in a byte < 255; the literals;
+ * unless the payload ends there (the last sequence: literals only, match
+ * nibble 0), a u16 distance back (1..65535) and the rest of a match nibble
+ * 15 the same way.  Matches may overlap their output.  The encoder's parse:
+ * h(i) = (u32 at i) * 2654435761 >> 20 (mod 2^32); the candidate of position
+ * i is the last earlier position of the block with the same hash (over every
+ * position, not only the ones the parse visits); from `pos` the first
+ * position whose candidate matches in four bytes starts a match, extended
+ * while the next byte equals; a block whose coded form is not shorter is
+ * stored raw.  Device pointers 16-byte aligned; the workspace comes from the
+ * library's pool; synchronise `stream`.
+ * ------------------------------------------------------------------------- */
+int sz3g_lossless_bound(uint64_t n, uint64_t* max_bytes);
+int sz3g_lossless_compress(const void* d_in, uint64_t n, void* d_out, size_t out_capacity, size_t* out_bytes,
+                           void* stream);
+/* *n_out: decoded bytes (the header's n); out_capacity >= n, else SZ3G_E_CAPACITY */
+int sz3g_lossless_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_capacity, uint64_t* n_out,
+                             void* stream);
 
 int sz3g_read_header(const void* stream, size_t bytes, int stream_on_device, sz3g_params* p,
                      uint64_t* n_points);

@@ -25,10 +25,7 @@ int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, cons
                          void* scan_state, DevState* st, cudaStream_t s, bool state_zeroed = false);
 int launch_zero_counts(const uint16_t* codes, unsigned long long n, uint32_t chunk, unsigned long long n_chunks,
                        uint32_t* zcnt, cudaStream_t s);
-int launch_scan(const uint32_t* in, unsigned long long n, unsigned long long* out, uint32_t limit,
-                unsigned long long expect, int check_expect, void* state, DevState* st, cudaStream_t s,
-                bool state_zeroed = false);
-size_t scan_state_bytes(unsigned long long n);
+
 int launch_pack_table(const uint8_t* len, const uint32_t* code, uint32_t nsym, uint32_t* table, cudaStream_t s);
 size_t dec_tables_bytes();
 
@@ -489,6 +486,63 @@ int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t ou
   return SZ3G_OK;
 }
 
+int sz3g_lossless_bound(uint64_t n, uint64_t* max_bytes) {
+  if (!max_bytes) return SZ3G_E_INVAL;
+  const uint64_t nb = (n + SZ3G_LZ_BLOCK - 1) / SZ3G_LZ_BLOCK;
+  *max_bytes = SZ3G_LZ_HEADER + 8 * nb + 8 + n;
+  return SZ3G_OK;
+}
+
+int sz3g_lossless_compress(const void* d_in, uint64_t n, void* d_out, size_t out_capacity, size_t* out_bytes,
+                           void* stream) {
+  if (!d_out || !out_bytes || (n && !d_in) || !aligned(d_out, 16) || (n && !aligned(d_in, 16)) ||
+      (n + SZ3G_LZ_BLOCK - 1) / SZ3G_LZ_BLOCK > 0x7fffffffull)
+    return SZ3G_E_INVAL;
+  uint64_t bound = 0;
+  sz3g_lossless_bound(n, &bound);
+  if (out_capacity < bound) return SZ3G_E_CAPACITY;
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(nullptr, 0, lz_workspace_bytes(n), s, own, &ws));
+  DevState* st = nullptr;
+  SZ3G_TRY(launch_lz_compress(d_in, n, d_out, ws, s, &st));
+  DevState h;
+  SZ3G_TRY(read_state(st, &h, s));
+  SZ3G_TRY(status_of(h.flags));
+  *out_bytes = (size_t)h.out_bytes;
+  return SZ3G_OK;
+}
+
+int sz3g_lossless_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_capacity, uint64_t* n_out,
+                             void* stream) {
+  if (!d_stream || !d_out || !aligned(d_stream, 16) || !aligned(d_out, 16)) return SZ3G_E_INVAL;
+  if (bytes < SZ3G_LZ_HEADER) return SZ3G_E_CORRUPT;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char hb[SZ3G_LZ_HEADER];
+  SZ3G_CUDA(cudaMemcpyAsync(hb, d_stream, SZ3G_LZ_HEADER, cudaMemcpyDeviceToHost, s));
+  SZ3G_CUDA(cudaStreamSynchronize(s));
+  uint32_t bs = 0, nblk = 0;
+  uint64_t n = 0;
+  std::memcpy(&bs, hb + 4, 4);
+  std::memcpy(&n, hb + 8, 8);
+  std::memcpy(&nblk, hb + 16, 4);
+  if (std::memcmp(hb, "SZLZ", 4) != 0 || bs != SZ3G_LZ_BLOCK || nblk != (n + SZ3G_LZ_BLOCK - 1) / SZ3G_LZ_BLOCK ||
+      ((SZ3G_LZ_HEADER + 4ull * nblk + 7) & ~7ull) > bytes)
+    return SZ3G_E_CORRUPT;
+  if (n > out_capacity) return SZ3G_E_CAPACITY;
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(nullptr, 0, lz_workspace_bytes(n), s, own, &ws));
+  DevState* st = nullptr;
+  SZ3G_TRY(launch_lz_decompress(d_stream, bytes, n, d_out, ws, s, &st));
+  DevState h;
+  SZ3G_TRY(read_state(st, &h, s));
+  SZ3G_TRY(status_of(h.flags));
+  if (n_out) *n_out = n;
+  return SZ3G_OK;
+}
+
 int sz3g_graph_cache(int on) {
   std::lock_guard<std::mutex> lk(g_gmu);
   g_gcache_on = on != 0;
@@ -645,7 +699,7 @@ int sz3g_recover(const sz3g_params* p, const void* h_ebT, const uint16_t* d_code
   SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
   SZ3G_TRY(launch_zero_counts(d_codes, pl.N, pl.chunk, pl.n_chunks, (uint32_t*)(ws + L.zcnt), s));
   SZ3G_TRY(launch_scan((uint32_t*)(ws + L.zcnt), pl.n_chunks * pl.nsub, (unsigned long long*)(ws + L.zunit), 0,
-                       n_unpred, 1, ws + L.scan2, st, s));
+                       n_unpred, 1, ws + L.scan2, st, s, false));
   unsigned long long eb_bits = 0;
   std::memcpy(&eb_bits, h_ebT, pl.esz);
   void* R[34];

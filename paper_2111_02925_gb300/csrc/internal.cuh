@@ -99,7 +99,7 @@ struct Plan {
 enum KernelId {
   kKRange, kKEb, kKAnchor, kKLift, kKPassQuantize, kKPassRecover, kKCodebook, kKEncode, kKFinalize,
   kKDecodeTables, kKDecode, kKScan, kKZeroCount, kKPackTable, kKLevelQuantize, kKLevelRecover,
-  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKPublish, kKSelect, kKMlp, kKernelCount
+  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKPublish, kKSelect, kKMlp, kKLossless, kKernelCount
 };
 
 // prof.cu: whether per-launch timing is on; launches replayed inside a graph
@@ -286,6 +286,19 @@ int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpr
                          const unsigned long long* zunit, void* const* R, void* d_out,
                          DevState* st, unsigned long long ebT_bits, bool codes_padded, cudaStream_t s,
                          LevelQueue* lq = nullptr, int field = 0);
+
+// k_huffman.cu: device-wide exclusive prefix sum (u32 -> u64) by decoupled look-back
+size_t scan_state_bytes(unsigned long long n);
+int launch_scan(const uint32_t* in, unsigned long long n, unsigned long long* out, uint32_t limit,
+                unsigned long long expect, int check_expect, void* state, DevState* st, cudaStream_t s,
+                bool state_zeroed);
+
+// k_lz.cu: the optional lossless stage (byte-level LZ77 over 32 KiB blocks)
+size_t lz_workspace_bytes(unsigned long long n);
+int launch_lz_compress(const void* d_in, unsigned long long n, void* d_out, unsigned char* ws, cudaStream_t s,
+                       DevState** st);
+int launch_lz_decompress(const void* d_stream, unsigned long long bytes, unsigned long long n, void* d_out,
+                         unsigned char* ws, cudaStream_t s, DevState** st);
 
 // api.cu: the pipelines without synchronisation (also used by the batch).
 struct Header {  // a parsed stream header

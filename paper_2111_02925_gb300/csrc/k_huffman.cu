@@ -1012,7 +1012,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* in, 
 // state_zeroed: the caller cleared `state` already (with its workspace).
 int launch_scan(const uint32_t* in, unsigned long long n, unsigned long long* out, uint32_t limit,
                 unsigned long long expect, int check_expect, void* state, DevState* st, cudaStream_t s,
-                bool state_zeroed = false) {
+                bool state_zeroed) {
   if (!state_zeroed && cudaMemsetAsync(state, 0, scan_state_bytes(n), s) != cudaSuccess) return SZ3G_E_CUDA;
   const unsigned long long ntiles = (n + kScanTile - 1) / kScanTile;
   SZ3G_LAUNCH(kKScan, s,

@@ -91,6 +91,9 @@ _SIGS = {
     "sz3g_batch_queue_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "sz3g_batch_destroy": [_vp],
     "sz3g_graph_cache": [C.c_int],
+    "sz3g_lossless_bound": [_u64, C.POINTER(_u64)],
+    "sz3g_lossless_compress": [_vp, _u64, _vp, _sz, C.POINTER(_sz), _vp],
+    "sz3g_lossless_decompress": [_vp, _sz, _vp, _sz, C.POINTER(_u64), _vp],
     "sz3g_select_costs": [_P, _vp, _u32, _u64, _vp, _vp],
     "sz3g_select_features": [_P, _vp, _u32, _u64, _vp, _vp],
     "sz3g_select_sampled": [_P, _vp, _u32, _u64, _vp, _vp],
@@ -476,3 +479,23 @@ def workspace(p: Params, for_decompress: bool, device="cuda"):
 def sz3g_graph_cache(on: bool) -> None:
     """Turn the compress / decompress graph cache on or off (on by default)."""
     _chk(load().sz3g_graph_cache(int(on)), "sz3g_graph_cache")
+
+
+def sz3g_lossless_bound(n: int) -> int:
+    b = _u64(0)
+    _chk(load().sz3g_lossless_bound(n, C.byref(b)), "sz3g_lossless_bound")
+    return b.value
+
+
+def sz3g_lossless_compress(d_in: int, n: int, d_out: int, out_capacity: int, stream: int = 0):
+    """The lossless stage over n device bytes; returns (status, stream bytes)."""
+    nb = _sz(0)
+    rc = load().sz3g_lossless_compress(d_in or None, n, d_out, out_capacity, C.byref(nb), stream or None)
+    return rc, nb.value
+
+
+def sz3g_lossless_decompress(d_stream: int, nbytes: int, d_out: int, out_capacity: int, stream: int = 0):
+    """Returns (status, decoded bytes)."""
+    n = _u64(0)
+    rc = load().sz3g_lossless_decompress(d_stream, nbytes, d_out, out_capacity, C.byref(n), stream or None)
+    return rc, n.value
