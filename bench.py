@@ -184,7 +184,7 @@ def traffic_for(kernel: str):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             d = json.load(fh)
         e = d.get(kernel)
-        if e and e.get("source_stamp") == B._stamp():
+        if e and kernel in B.KERNEL_SOURCES and e.get("source_stamp") == B.kernel_stamp(kernel):
             return e.get("bytes_per_step")
     except Exception:
         pass

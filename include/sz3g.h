@@ -180,15 +180,27 @@ int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_
 
 /*
  * End-to-end forms on HOST buffers: copy h_in to the device, compress, copy
- * the stream back (and the reverse for decompress), all on `stream`, with
- * device memory from the library's stream-ordered pool (see Workspace).  h_* may be pageable or
- * pinned; pinned memory makes the copies asynchronous and faster.
- * Same errors as the device forms.
+ * the stream back (and the reverse for decompress), all on `stream`.  The
+ * device copies of input, output and workspace are one staging set per
+ * device, kept by the library between calls and grown on demand (so repeated
+ * calls on one field shape replay the cached graph of the pipeline, see
+ * sz3g_graph_cache); a call made while another thread holds the set stages
+ * through memory of the library's stream-ordered pool instead.  Both return
+ * after synchronising `stream`.  h_* may be pageable or pinned; pinned memory
+ * makes the copies asynchronous and faster.  Same errors as the device forms.
  */
 int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size_t out_capacity,
                        size_t* out_bytes, void* stream);
 int sz3g_decompress_host(const void* h_stream, size_t bytes, void* h_out, size_t out_capacity,
                          void* stream);
+
+/*
+ * Frees what the library keeps between calls: the cached graphs, the staging
+ * sets of the host-buffer forms, and the free memory of its pool on the
+ * devices that held a staging set.  Synchronises those devices.  Not to be
+ * called while another thread is inside a call of this library.
+ */
+int sz3g_trim(void);
 
 /* ---------------------------------------------------------------------------
  * Stage entry points: the steps of the hot path one at a time, with their

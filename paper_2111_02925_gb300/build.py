@@ -52,6 +52,26 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
+# The sources each measured kernel is compiled and launched from (its own
+# file, the headers it includes, the plan that sizes its work).
+KERNEL_SOURCES = {
+    "level_quantize": ["k_fine.cu", "level_common.cuh", "internal.cuh", "plan.cu"],
+    "level_recover": ["k_fine.cu", "level_common.cuh", "internal.cuh", "plan.cu"],
+}
+
+
+def kernel_stamp(kernel: str) -> str:
+    """Hash of the sources of one measured kernel, the public header and the
+    compile flags: a counter taken on a kernel stays valid while this holds."""
+    h = hashlib.sha256()
+    files = [os.path.join(CSRC, f) for f in KERNEL_SOURCES[kernel]] + [os.path.join(INCLUDE, "sz3g.h")]
+    for p in files:
+        with open(p, "rb") as fh:
+            h.update(os.path.relpath(p, os.path.dirname(HERE)).encode() + fh.read())
+    h.update(" ".join(f for f in NVCC_FLAGS if not f.startswith("-I")).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     stamp = _stamp()
     stamp_file = os.path.join(OBJ, "stamp")

@@ -408,6 +408,115 @@ int run_cached(const std::vector<unsigned char>& key, cudaStream_t s, F enqueue,
 
 bool use_graph_cache(const void* user_ws) { return user_ws && g_gcache_on && !profiling_on(); }
 
+void sz3g_graph_cache_clear() {
+  std::lock_guard<std::mutex> lk(g_gmu);
+  for (GraphEntry& e : g_graphs) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    e = GraphEntry{};
+  }
+}
+
+// Decompress with the header bytes `hb` already on the host (the device
+// stream holds the same bytes at its start).
+int decompress_parsed(const unsigned char* hb, const void* d_stream, size_t bytes, void* d_out, size_t out_capacity,
+                      void* d_workspace, size_t ws_bytes, cudaStream_t s) {
+  Header h;
+  SZ3G_TRY(parse_header(hb, bytes, &h));
+  const Plan& pl = h.plan;
+  if (out_capacity < pl.N * pl.esz) return SZ3G_E_CAPACITY;
+  const DecompressWs L = decompress_layout(pl);
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
+  DevState* st = nullptr;
+  if (use_graph_cache(d_workspace)) {
+    std::vector<unsigned char> key;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    key_add(key, 'D');
+    key_add(key, dev);
+    key.insert(key.end(), hb, hb + SZ3G_HEADER_BYTES);
+    key_add(key, bytes);
+    key_add(key, d_stream);
+    key_add(key, d_out);
+    key_add(key, out_capacity);
+    key_add(key, d_workspace);
+    key_add(key, ws_bytes);
+    SZ3G_TRY(run_cached(
+        key, s, [&](cudaStream_t es, DevState** sto) { return decompress_enqueue(h, d_stream, d_out, ws, es, sto); },
+        &st));
+  } else {
+    SZ3G_TRY(decompress_enqueue(h, d_stream, d_out, ws, s, &st));
+  }
+  DevState hs;
+  SZ3G_TRY(read_state(st, &hs, s));
+  return status_of(hs.flags);
+}
+
+// Device buffers the host-buffer entry points stage through: one set per
+// device, kept between calls and grown on demand, so that repeated calls on
+// fields of one shape reuse the same addresses and with them the cached graph
+// of the pipeline.  A call that finds the set in use by another thread stages
+// through pool memory of its own instead.
+struct Staging {
+  std::mutex mu;
+  void* buf[3] = {nullptr, nullptr, nullptr};
+  size_t cap[3] = {0, 0, 0};
+};
+constexpr int kStageDevices = 64;
+Staging g_stage[kStageDevices];
+
+Staging* staging_of_current() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStageDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return &g_stage[dev];
+}
+
+// Slot i of a held set with at least `bytes` (rounded up to 2 MiB); the old
+// buffer is released in stream order on s.
+int stage_reserve(Staging& g, int i, size_t bytes, cudaStream_t s, void** out) {
+  bytes = (bytes + (2u << 20) - 1) & ~(size_t)((2u << 20) - 1);
+  if (g.cap[i] < bytes) {
+    if (g.buf[i]) cudaFreeAsync(g.buf[i], s);
+    g.buf[i] = nullptr;
+    g.cap[i] = 0;
+    if (pool_alloc(&g.buf[i], bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      g.buf[i] = nullptr;
+      return SZ3G_E_NOMEM;
+    }
+    g.cap[i] = bytes;
+  }
+  *out = g.buf[i];
+  return SZ3G_OK;
+}
+
+// Releases every staging set and returns the pool's free memory of each
+// device that held one.
+void staging_release_all() {
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (int d = 0; d < kStageDevices; ++d) {
+    Staging& g = g_stage[d];
+    std::lock_guard<std::mutex> lk(g.mu);
+    if (!g.buf[0] && !g.buf[1] && !g.buf[2]) continue;
+    if (cudaSetDevice(d) != cudaSuccess) continue;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 3; ++i) {
+      if (g.buf[i]) cudaFreeAsync(g.buf[i], 0);
+      g.buf[i] = nullptr;
+      g.cap[i] = 0;
+    }
+    cudaDeviceSynchronize();
+    if (cudaMemPool_t pl = lib_pool()) cudaMemPoolTrimTo(pl, 0);
+  }
+  cudaSetDevice(cur);
+  cudaGetLastError();
+}
+
 }  // namespace
 
 }  // namespace sz3g
@@ -544,13 +653,11 @@ int sz3g_lossless_decompress(const void* d_stream, size_t bytes, void* d_out, si
 }
 
 int sz3g_graph_cache(int on) {
-  std::lock_guard<std::mutex> lk(g_gmu);
-  g_gcache_on = on != 0;
-  if (!g_gcache_on)
-    for (GraphEntry& e : g_graphs) {
-      if (e.exec) cudaGraphExecDestroy(e.exec);
-      e = GraphEntry{};
-    }
+  {
+    std::lock_guard<std::mutex> lk(g_gmu);
+    g_gcache_on = on != 0;
+  }
+  if (!on) sz3g_graph_cache_clear();
   return SZ3G_OK;
 }
 
@@ -578,38 +685,29 @@ int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_
   if (bytes < SZ3G_HEADER_BYTES) return SZ3G_E_CORRUPT;
   SZ3G_CUDA(cudaMemcpyAsync(hb, d_stream, SZ3G_HEADER_BYTES, cudaMemcpyDeviceToHost, s));
   SZ3G_CUDA(cudaStreamSynchronize(s));
-  Header h;
-  SZ3G_TRY(parse_header(hb, bytes, &h));
-  const Plan& pl = h.plan;
-  if (out_capacity < pl.N * pl.esz) return SZ3G_E_CAPACITY;
-  const DecompressWs L = decompress_layout(pl);
-  Scratch own;
-  unsigned char* ws;
-  SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
-  DevState* st = nullptr;
-  if (use_graph_cache(d_workspace)) {
-    std::vector<unsigned char> key;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    key_add(key, 'D');
-    key_add(key, dev);
-    key.insert(key.end(), hb, hb + SZ3G_HEADER_BYTES);
-    key_add(key, bytes);
-    key_add(key, d_stream);
-    key_add(key, d_out);
-    key_add(key, out_capacity);
-    key_add(key, d_workspace);
-    key_add(key, ws_bytes);
-    SZ3G_TRY(run_cached(
-        key, s, [&](cudaStream_t es, DevState** sto) { return decompress_enqueue(h, d_stream, d_out, ws, es, sto); },
-        &st));
-  } else {
-    SZ3G_TRY(decompress_enqueue(h, d_stream, d_out, ws, s, &st));
-  }
-  DevState hs;
-  SZ3G_TRY(read_state(st, &hs, s));
-  return status_of(hs.flags);
+  return decompress_parsed(hb, d_stream, bytes, d_out, out_capacity, d_workspace, ws_bytes, s);
 }
+
+namespace {
+
+// Holds the current device's staging set for one host-buffer call, if no
+// other thread has it; on release the stream is synchronised first, so that
+// no copy or kernel of an abandoned call still touches the buffers.
+struct StageHold {
+  Staging* g = nullptr;
+  cudaStream_t s = nullptr;
+  explicit StageHold(cudaStream_t st) : s(st) {
+    Staging* c = staging_of_current();
+    if (c && c->mu.try_lock()) g = c;
+  }
+  ~StageHold() {
+    if (!g) return;
+    cudaStreamSynchronize(s);
+    g->mu.unlock();
+  }
+};
+
+}  // namespace
 
 int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size_t out_capacity, size_t* out_bytes,
                        void* stream) {
@@ -619,17 +717,28 @@ int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size
   cudaStream_t s = (cudaStream_t)stream;
   size_t bound;
   SZ3G_TRY(sz3g_compress_bound(p, &bound));
+  const size_t in_bytes = pl.N * pl.esz, ws_bytes = compress_layout(pl).total;
+  StageHold hold(s);
   Scratch din, dout;
-  din.s = dout.s = s;
-  if (pool_alloc(&din.ptr, pl.N * pl.esz, s) != cudaSuccess || pool_alloc(&dout.ptr, bound, s) != cudaSuccess) {
-    cudaGetLastError();
-    return SZ3G_E_NOMEM;
+  void *d_in = nullptr, *d_out = nullptr, *d_ws = nullptr;
+  if (hold.g) {
+    SZ3G_TRY(stage_reserve(*hold.g, 0, in_bytes, s, &d_in));
+    SZ3G_TRY(stage_reserve(*hold.g, 1, bound, s, &d_out));
+    SZ3G_TRY(stage_reserve(*hold.g, 2, ws_bytes, s, &d_ws));
+  } else {
+    din.s = dout.s = s;
+    if (pool_alloc(&din.ptr, in_bytes, s) != cudaSuccess || pool_alloc(&dout.ptr, bound, s) != cudaSuccess) {
+      cudaGetLastError();
+      return SZ3G_E_NOMEM;
+    }
+    d_in = din.ptr;
+    d_out = dout.ptr;
   }
-  SZ3G_CUDA(cudaMemcpyAsync(din.ptr, h_in, pl.N * pl.esz, cudaMemcpyHostToDevice, s));
+  SZ3G_CUDA(cudaMemcpyAsync(d_in, h_in, in_bytes, cudaMemcpyHostToDevice, s));
   size_t nb = 0;
-  SZ3G_TRY(sz3g_compress(p, din.ptr, dout.ptr, bound, &nb, nullptr, 0, stream));
+  SZ3G_TRY(sz3g_compress(p, d_in, d_out, bound, &nb, d_ws, d_ws ? hold.g->cap[2] : 0, stream));
   if (nb > out_capacity) return SZ3G_E_CAPACITY;
-  SZ3G_CUDA(cudaMemcpyAsync(h_out, dout.ptr, nb, cudaMemcpyDeviceToHost, s));
+  SZ3G_CUDA(cudaMemcpyAsync(h_out, d_out, nb, cudaMemcpyDeviceToHost, s));
   SZ3G_CUDA(cudaStreamSynchronize(s));
   *out_bytes = nb;
   return SZ3G_OK;
@@ -637,22 +746,40 @@ int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size
 
 int sz3g_decompress_host(const void* h_stream, size_t bytes, void* h_out, size_t out_capacity, void* stream) {
   if (!h_stream || !h_out) return SZ3G_E_INVAL;
+  if (bytes < SZ3G_HEADER_BYTES) return SZ3G_E_CORRUPT;
   cudaStream_t s = (cudaStream_t)stream;
-  sz3g_params p;
-  uint64_t n;
-  SZ3G_TRY(sz3g_read_header(h_stream, bytes, 0, &p, &n));
-  const size_t esz = p.dtype == SZ3G_F32 ? 4 : 8;
-  if (out_capacity < n * esz) return SZ3G_E_CAPACITY;
+  unsigned char hb[SZ3G_HEADER_BYTES];
+  std::memcpy(hb, h_stream, SZ3G_HEADER_BYTES);
+  Header h;
+  SZ3G_TRY(parse_header(hb, bytes, &h));
+  const size_t out_bytes = h.plan.N * h.plan.esz, ws_bytes = decompress_layout(h.plan).total;
+  if (out_capacity < out_bytes) return SZ3G_E_CAPACITY;
+  StageHold hold(s);
   Scratch dst, dout;
-  dst.s = dout.s = s;
-  if (pool_alloc(&dst.ptr, bytes, s) != cudaSuccess || pool_alloc(&dout.ptr, n * esz, s) != cudaSuccess) {
-    cudaGetLastError();
-    return SZ3G_E_NOMEM;
+  void *d_st = nullptr, *d_out = nullptr, *d_ws = nullptr;
+  if (hold.g) {
+    SZ3G_TRY(stage_reserve(*hold.g, 0, out_bytes, s, &d_out));
+    SZ3G_TRY(stage_reserve(*hold.g, 1, bytes, s, &d_st));
+    SZ3G_TRY(stage_reserve(*hold.g, 2, ws_bytes, s, &d_ws));
+  } else {
+    dst.s = dout.s = s;
+    if (pool_alloc(&dst.ptr, bytes, s) != cudaSuccess || pool_alloc(&dout.ptr, out_bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      return SZ3G_E_NOMEM;
+    }
+    d_st = dst.ptr;
+    d_out = dout.ptr;
   }
-  SZ3G_CUDA(cudaMemcpyAsync(dst.ptr, h_stream, bytes, cudaMemcpyHostToDevice, s));
-  SZ3G_TRY(sz3g_decompress(dst.ptr, bytes, dout.ptr, n * esz, nullptr, 0, stream));
-  SZ3G_CUDA(cudaMemcpyAsync(h_out, dout.ptr, n * esz, cudaMemcpyDeviceToHost, s));
+  SZ3G_CUDA(cudaMemcpyAsync(d_st, h_stream, bytes, cudaMemcpyHostToDevice, s));
+  SZ3G_TRY(decompress_parsed(hb, d_st, bytes, d_out, out_bytes, d_ws, d_ws ? hold.g->cap[2] : 0, s));
+  SZ3G_CUDA(cudaMemcpyAsync(h_out, d_out, out_bytes, cudaMemcpyDeviceToHost, s));
   SZ3G_CUDA(cudaStreamSynchronize(s));
+  return SZ3G_OK;
+}
+
+int sz3g_trim(void) {
+  sz3g_graph_cache_clear();
+  staging_release_all();
   return SZ3G_OK;
 }
 

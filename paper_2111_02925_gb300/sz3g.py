@@ -91,6 +91,7 @@ _SIGS = {
     "sz3g_batch_queue_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "sz3g_batch_destroy": [_vp],
     "sz3g_graph_cache": [C.c_int],
+    "sz3g_trim": [],
     "sz3g_lossless_bound": [_u64, C.POINTER(_u64)],
     "sz3g_lossless_compress": [_vp, _u64, _vp, _sz, C.POINTER(_sz), _vp],
     "sz3g_lossless_decompress": [_vp, _sz, _vp, _sz, C.POINTER(_u64), _vp],
@@ -479,6 +480,11 @@ def workspace(p: Params, for_decompress: bool, device="cuda"):
 def sz3g_graph_cache(on: bool) -> None:
     """Turn the compress / decompress graph cache on or off (on by default)."""
     _chk(load().sz3g_graph_cache(int(on)), "sz3g_graph_cache")
+
+
+def sz3g_trim() -> None:
+    """Free the cached graphs, the host-buffer staging sets and the pool's free memory."""
+    _chk(load().sz3g_trim(), "sz3g_trim")
 
 
 def sz3g_lossless_bound(n: int) -> int:
