@@ -57,6 +57,8 @@ def test_host_forms_match_oracle_across_shapes(pinned):
         (S.grf((70, 66, 90), 6).astype(np.float32), 1e-4, G.LINEAR),   # staging grows
         (S.grf((21, 18, 30), 7).astype(np.float64), 1e-3, G.CUBIC),    # smaller again, another type
         (S.grf((33, 47, 70), 5).astype(np.float32), 1e-3, G.CUBIC),    # same shape as the first
+        (S.grf((48, 50, 64), 8).astype(np.float32), 1e-3, G.CUBIC),    # 16-byte rows
+        (S.grf((36, 44), 9).astype(np.float32), 1e-3, G.LINEAR),     # 2-D
     ]
     for x, eb, interp in cases:
         s, y = _host_roundtrip(x, eb, interp, pinned=pinned)
@@ -88,6 +90,19 @@ def test_host_forms_from_two_threads():
     for t in range(2):
         assert got[t][0] == want[t][0]
         assert _same_field(got[t][1], want[t][1])
+
+
+def test_host_decompress_into_pinned_output_at_any_offset():
+    # outputs that start at any 4-byte offset of a page-locked buffer
+    x = S.grf((40, 52, 64), 13).astype(np.float32)
+    so, yo = _oracle(x, 1e-3, G.CUBIC)
+    hs = torch.from_numpy(np.frombuffer(so, np.uint8).copy()).pin_memory()
+    big = torch.full((x.size + 16,), np.nan, dtype=torch.float32).pin_memory()
+    for off in (0, 1, 4, 3):
+        y = big[off:off + x.size]
+        rc = G.sz3g_decompress_host(hs.data_ptr(), hs.numel(), y.data_ptr(), x.size * 4, 0)
+        assert rc == G.OK
+        assert _same_field(y.numpy().copy(), yo)
 
 
 def test_host_forms_after_trim_and_after_errors():
