@@ -179,6 +179,31 @@ int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_
                     void* d_workspace, size_t ws_bytes, void* stream);
 
 /*
+ * Asynchronous forms for stream-ordered use and CUDA-graph capture: the
+ * pipeline is enqueued on `stream` and the call returns without
+ * synchronising; nothing is allocated and nothing is read back to the host.
+ * The result is written on the device when the pipeline ends:
+ *   *d_status      int32, SZ3G_OK or the error code the synchronous form
+ *                  would have returned for a run-time failure (non-finite
+ *                  input, zero range with REL, capacity, corrupt stream,
+ *                  timeout);
+ *   *d_out_bytes   (compress, may be NULL) u64 stream length, 0 on error.
+ * The workspace is required (sz3g_workspace_size bytes, 256-byte aligned) and
+ * must not be shared with a run still in flight.  Host-side checks (params,
+ * pointers, alignment, workspace size, header) are reported by the return
+ * value, as SZ3G_E_INVAL / SZ3G_E_CAPACITY / SZ3G_E_CORRUPT; SZ3G_OK means the
+ * work is enqueued.  A capture replays with the buffers, parameters (and, for
+ * decompress, the header) given at capture time.
+ *   h_header  (decompress) host copy of the stream's SZ3G_HEADER_BYTES bytes.
+ */
+int sz3g_compress_async(const sz3g_params* p, const void* d_in, void* d_out, size_t out_capacity,
+                        unsigned long long* d_out_bytes, int* d_status, void* d_workspace, size_t ws_bytes,
+                        void* stream);
+int sz3g_decompress_async(const void* h_header, const void* d_stream, size_t bytes, void* d_out,
+                          size_t out_capacity, int* d_status, void* d_workspace, size_t ws_bytes,
+                          void* stream);
+
+/*
  * End-to-end forms on HOST buffers: copy h_in to the device, compress, copy
  * the stream back (and the reverse for decompress), all on `stream`.  The
  * device copies of input, output and workspace are one staging set per

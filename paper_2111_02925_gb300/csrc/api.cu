@@ -150,7 +150,7 @@ int get_ws(void* user, size_t user_bytes, size_t need, cudaStream_t s, Scratch& 
   return SZ3G_OK;
 }
 
-int status_of(uint32_t f) {
+__host__ __device__ inline int flags_status(uint32_t f) {
   if (f & kFlagBadBound) return SZ3G_E_INVAL;
   if (f & kFlagNonFinite) return SZ3G_E_NONFINITE;
   if (f & kFlagZeroRange) return SZ3G_E_ZERO_RANGE_REL;
@@ -158,6 +158,22 @@ int status_of(uint32_t f) {
   if (f & kFlagTimeout) return SZ3G_E_TIMEOUT;
   if (f & kFlagCorrupt) return SZ3G_E_CORRUPT;
   return SZ3G_OK;
+}
+
+int status_of(uint32_t f) { return flags_status(f); }
+
+// The asynchronous forms' result on the device: the run's status and (a
+// compress) the stream length, 0 unless the status is SZ3G_OK.
+__global__ void report_kernel(const DevState* st, unsigned long long* out_bytes, int* status) {
+  if (threadIdx.x != 0) return;
+  const int r = flags_status(st->flags);
+  if (status) *status = r;
+  if (out_bytes) *out_bytes = r == SZ3G_OK ? st->out_bytes : 0ull;
+}
+
+int launch_report(const DevState* st, unsigned long long* out_bytes, int* status, cudaStream_t s) {
+  SZ3G_LAUNCH(kKReport, s, report_kernel<<<1, 32, 0, s>>>(st, out_bytes, status));
+  return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
 int read_state(const DevState* d, DevState* h, cudaStream_t s) {
@@ -708,6 +724,38 @@ struct StageHold {
 };
 
 }  // namespace
+
+int sz3g_compress_async(const sz3g_params* p, const void* d_in, void* d_out, size_t out_capacity,
+                        unsigned long long* d_out_bytes, int* d_status, void* d_workspace, size_t ws_bytes,
+                        void* stream) {
+  Plan pl;
+  SZ3G_TRY(make_plan(p, &pl));
+  if (!d_in || !d_out || !d_status || !d_workspace || !aligned(d_in, 16) || !aligned(d_out, 16) ||
+      !aligned(d_workspace, kAlign) || (d_out_bytes && !aligned(d_out_bytes, 8)) || !aligned(d_status, 4))
+    return SZ3G_E_INVAL;
+  const CompressWs L = compress_layout(pl);
+  if (ws_bytes < L.total) return SZ3G_E_CAPACITY;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevState* st = nullptr;
+  SZ3G_TRY(compress_enqueue(p, pl, d_in, d_out, out_capacity, (unsigned char*)d_workspace, s, &st));
+  return launch_report(st, d_out_bytes, d_status, s);
+}
+
+int sz3g_decompress_async(const void* h_header, const void* d_stream, size_t bytes, void* d_out,
+                          size_t out_capacity, int* d_status, void* d_workspace, size_t ws_bytes, void* stream) {
+  if (!h_header || !d_stream || !d_out || !d_status || !d_workspace || !aligned(d_stream, 16) ||
+      !aligned(d_out, 16) || !aligned(d_workspace, kAlign) || !aligned(d_status, 4))
+    return SZ3G_E_INVAL;
+  if (bytes < SZ3G_HEADER_BYTES) return SZ3G_E_CORRUPT;
+  Header h;
+  SZ3G_TRY(parse_header((const unsigned char*)h_header, bytes, &h));
+  if (out_capacity < h.plan.N * h.plan.esz) return SZ3G_E_CAPACITY;
+  if (ws_bytes < decompress_layout(h.plan).total) return SZ3G_E_CAPACITY;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevState* st = nullptr;
+  SZ3G_TRY(decompress_enqueue(h, d_stream, d_out, (unsigned char*)d_workspace, s, &st));
+  return launch_report(st, nullptr, d_status, s);
+}
 
 int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size_t out_capacity, size_t* out_bytes,
                        void* stream) {

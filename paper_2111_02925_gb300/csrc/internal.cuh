@@ -99,7 +99,7 @@ struct Plan {
 enum KernelId {
   kKRange, kKEb, kKAnchor, kKLift, kKPassQuantize, kKPassRecover, kKCodebook, kKEncode, kKFinalize,
   kKDecodeTables, kKDecode, kKScan, kKZeroCount, kKPackTable, kKLevelQuantize, kKLevelRecover,
-  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKPublish, kKSelect, kKMlp, kKLossless, kKernelCount
+  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKPublish, kKSelect, kKMlp, kKLossless, kKReport, kKernelCount
 };
 
 // prof.cu: whether per-launch timing is on; launches replayed inside a graph

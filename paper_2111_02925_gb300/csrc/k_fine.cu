@@ -43,6 +43,14 @@ namespace sz3g {
 // Recover stages the tile's code rows with 16-byte cp.async pieces spread
 // over the threads (true) or one bulk copy per row (false).
 constexpr bool kCodeCpAsync = true;
+// Pass 2 moves the four codes of a run as one 8-, two 4- or four 2-byte
+// accesses by the alignment of the run's first code (true), or one 2-byte
+// access per code (false).
+constexpr bool kPackCodes = true;
+// Histogram update without a branch: every code adds to the shared window
+// (codes outside it to a spare slot that is never flushed) and, when outside,
+// also to the global histogram (true); or window-or-global by a branch (false).
+constexpr bool kHistSpare = true;
 
 template <bool COMP>
 struct FineThreads {
@@ -86,7 +94,7 @@ struct FineLayout {
   static constexpr size_t kOffE = kOffC + kSt * (size_t)kCB * sizeof(T);
   static constexpr size_t kOffK = up(kOffE + (size_t)S::kT0 * S::kXJ * S::kEK * sizeof(T), 128);
   static constexpr size_t kOffH = kOffK + kSt * (size_t)kKB * 2;
-  static constexpr size_t kOffBar = up(kOffH + (COMP ? kHistWin * 4 : 0), 16);
+  static constexpr size_t kOffBar = up(kOffH + (COMP ? (kHistWin + 1) * 4 : 0), 16);
   static constexpr size_t kBytes = kOffBar + 16;
 };
 
@@ -138,6 +146,33 @@ __device__ __forceinline__ void st4(T* p, T a, T b, T c, T d) {  // 16-byte alig
   }
 }
 
+// Four consecutive codes as one 8-, two 4- or four 2-byte accesses, by the
+// alignment of the first.
+__device__ __forceinline__ void put_codes4(uint16_t* p, const uint32_t* c) {
+  const uint32_t lo = c[0] | (c[1] << 16), hi = c[2] | (c[3] << 16);
+  const uintptr_t ad = reinterpret_cast<uintptr_t>(p);
+  if ((ad & 7) == 0) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(lo, hi);
+  } else if ((ad & 3) == 0) {
+    reinterpret_cast<uint32_t*>(p)[0] = lo;
+    reinterpret_cast<uint32_t*>(p)[1] = hi;
+  } else {
+    p[0] = (uint16_t)c[0], p[1] = (uint16_t)c[1], p[2] = (uint16_t)c[2], p[3] = (uint16_t)c[3];
+  }
+}
+__device__ __forceinline__ void get_codes4(const uint16_t* p, uint32_t* c) {
+  const uintptr_t ad = reinterpret_cast<uintptr_t>(p);
+  if ((ad & 7) == 0) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    c[0] = v.x & 0xffffu, c[1] = v.x >> 16, c[2] = v.y & 0xffffu, c[3] = v.y >> 16;
+  } else if ((ad & 3) == 0) {
+    const uint32_t v0 = reinterpret_cast<const uint32_t*>(p)[0], v1 = reinterpret_cast<const uint32_t*>(p)[1];
+    c[0] = v0 & 0xffffu, c[1] = v0 >> 16, c[2] = v1 & 0xffffu, c[3] = v1 >> 16;
+  } else {
+    c[0] = p[0], c[1] = p[1], c[2] = p[2], c[3] = p[3];
+  }
+}
+
 // Per-thread results of the tile passes, flushed once per CTA.
 struct FineAcc {
   bool bad;  // recover: a code outside [0, 2r) or an unpredictable value past the list
@@ -147,7 +182,8 @@ struct FineAcc {
 // p; returns its reconstruction.  `code_in` is the stored code (recover).
 template <typename T, bool COMP>
 __device__ __forceinline__ T fine_point(const LevelArgs<T>& a, const FineDesc& d, uint32_t* hwin, int hlo, T x, T p,
-                                        T ebT, T ebr, bool own, uint32_t ci, uint32_t code_in, FineAcc& acc) {
+                                        T ebT, T ebr, bool own, uint32_t ci, uint32_t code_in, FineAcc& acc,
+                                        uint32_t* code_out = nullptr) {
   if (COMP) {
     T r;
     const uint32_t code = quantize_point<T>(x, p, ebT, ebr, a.radius, r);
@@ -155,10 +191,17 @@ __device__ __forceinline__ T fine_point(const LevelArgs<T>& a, const FineDesc& d
       // (unpredictable values -- also every non-finite input -- are counted by
       // histogram bin 0 and checked for finiteness where the encoder gathers
       // them)
-      a.codes[ci] = (uint16_t)code;
+      if (code_out) *code_out = code;
+      else a.codes[ci] = (uint16_t)code;
       const uint32_t bn = code - (uint32_t)hlo;
-      if (bn < (uint32_t)kHistWin) atomicAdd(&hwin[bn], 1u);
-      else atomicAdd(&a.hist[code], 1u);
+      if (kHistSpare) {
+        const bool far = bn >= (uint32_t)kHistWin;
+        atomicAdd(&hwin[far ? (uint32_t)kHistWin : bn], 1u);
+        if (far) atomicAdd(&a.hist[code], 1u);
+      } else {
+        if (bn < (uint32_t)kHistWin) atomicAdd(&hwin[bn], 1u);
+        else atomicAdd(&a.hist[code], 1u);
+      }
     }
     return r;
   } else {
@@ -211,7 +254,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
   const int hlo = a.radius - kHistWin / 2;
   const int m0 = d.m0, m1 = d.m1, m2 = d.m2;
   if (COMP)
-    for (int i = tid; i < kHistWin; i += kFineThreads) hwin[i] = 0;
+    for (int i = tid; i <= kHistWin; i += kFineThreads) hwin[i] = 0;
   if (tid == 0) {
     s_bad = 0;
     s_timeout = 0;
@@ -494,12 +537,22 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
         const int k0 = A2 + 8 * q4;  // first (even) k of the run's eight points
         T r[4];
         if (IN || !edgek) {
+          uint32_t kin[4] = {0u, 0u, 0u, 0u}, cq[4] = {0u, 0u, 0u, 0u};
+          if (!COMP) {
+            if (kPackCodes) {
+              get_codes4(kr, kin);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) kin[u] = kr[u];
+            }
+          }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const T p = interp_predict<T>(e[u + 2], e[u + 3], e[u + 1], e[u + 4], true, true, true, INTERP);
-            r[u] = fine_point<T, COMP>(a, d, hwin, hlo, xo[u], p, ebT, ebr, true, ci + u,
-                                       COMP ? 0u : (uint32_t)kr[u], acc);
+            r[u] = fine_point<T, COMP>(a, d, hwin, hlo, xo[u], p, ebT, ebr, true, ci + u, kin[u], acc,
+                                       COMP && kPackCodes ? &cq[u] : nullptr);
           }
+          if (COMP && kPackCodes) put_codes4(a.codes + ci, cq);
         } else {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {

@@ -92,6 +92,8 @@ _SIGS = {
     "sz3g_batch_destroy": [_vp],
     "sz3g_graph_cache": [C.c_int],
     "sz3g_trim": [],
+    "sz3g_compress_async": [_P, _vp, _vp, _sz, _vp, _vp, _vp, _sz, _vp],
+    "sz3g_decompress_async": [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp],
     "sz3g_lossless_bound": [_u64, C.POINTER(_u64)],
     "sz3g_lossless_compress": [_vp, _u64, _vp, _sz, C.POINTER(_sz), _vp],
     "sz3g_lossless_decompress": [_vp, _sz, _vp, _sz, C.POINTER(_u64), _vp],
@@ -208,6 +210,20 @@ def sz3g_compress_host(p: Params, h_in: int, h_out: int, out_capacity: int, stre
     nb = _sz(0)
     rc = load().sz3g_compress_host(C.byref(p), h_in, h_out, out_capacity, C.byref(nb), stream or None)
     return rc, nb.value
+
+
+def sz3g_compress_async(p: Params, d_in: int, d_out: int, out_capacity: int, d_out_bytes: int, d_status: int,
+                        d_ws: int, ws_bytes: int, stream: int = 0) -> int:
+    """Enqueue a compress; the stream length and status land in d_out_bytes (u64) and d_status (i32)."""
+    return load().sz3g_compress_async(C.byref(p), d_in, d_out, out_capacity, d_out_bytes or None, d_status,
+                                      d_ws or None, ws_bytes, stream or None)
+
+
+def sz3g_decompress_async(h_header: int, d_stream: int, nbytes: int, d_out: int, out_capacity: int, d_status: int,
+                          d_ws: int, ws_bytes: int, stream: int = 0) -> int:
+    """Enqueue a decompress of a stream whose header bytes are at host address h_header."""
+    return load().sz3g_decompress_async(h_header, d_stream, nbytes, d_out, out_capacity, d_status, d_ws or None,
+                                        ws_bytes, stream or None)
 
 
 def sz3g_decompress_host(h_stream: int, nbytes: int, h_out: int, out_capacity: int, stream: int = 0) -> int:
