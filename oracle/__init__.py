@@ -25,7 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libsz3o.so")
-_SOURCES = ("sz3o.c", "sz3o_typed.inc", "sz3o.h", "szlz.c")
+_SOURCES = ("sz3o.c", "sz3o_typed.inc", "sz3o.h", "szlz.c", "szpastri.c")
 _CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
 _lock = threading.Lock()
 _lib = None
@@ -80,7 +80,8 @@ def build(force: bool = False) -> str:
             if all(os.path.getmtime(s) <= t for s in srcs):
                 return _LIB_PATH
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", *_CFLAGS, "-o", tmp, os.path.join(_HERE, "sz3o.c"), os.path.join(_HERE, "szlz.c"), "-lm"]
+        cmd = ["gcc", *_CFLAGS, "-o", tmp, os.path.join(_HERE, "sz3o.c"), os.path.join(_HERE, "szlz.c"),
+               os.path.join(_HERE, "szpastri.c"), "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
@@ -113,6 +114,10 @@ def lib():
             "sz3o_select_features": [P, vp, C.c_uint32, C.c_uint32, C.c_uint64, vp],
             "sz3o_lz_compress": [vp, C.c_uint64, vp, C.c_uint64, u64p],
             "sz3o_lz_decompress": [vp, C.c_uint64, vp, C.c_uint64, u64p],
+            "sz3o_bitplane_exponent": [C.c_double, C.POINTER(C.c_int32)],
+            "sz3o_bitplane_encode": [C.c_uint32, vp, C.c_uint64, C.c_double, vp, C.c_uint64, u64p],
+            "sz3o_bitplane_decode": [vp, C.c_uint64, vp, C.c_uint64, u64p],
+            "sz3o_huffman_fixed_lengths": [C.c_uint32, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -120,6 +125,8 @@ def lib():
             f.restype = C.c_int
         L.sz3o_lz_bound.argtypes = [C.c_uint64]
         L.sz3o_lz_bound.restype = C.c_uint64
+        L.sz3o_bitplane_bound.argtypes = [C.c_uint64]
+        L.sz3o_bitplane_bound.restype = C.c_uint64
         _lib = L
     return _lib
 
@@ -405,4 +412,56 @@ def lz_decompress(stream: bytes) -> bytes:
     n = int(np.frombuffer(stream[8:16], np.uint64)[0])
     rc, out = lz_decompress_status(stream, n)
     _check(rc, "sz3o_lz_decompress")
+    return out
+
+
+# ---- SZ3-Pastri modules (szpastri.c) ----------------------------------------
+BP_HEADER = 32
+
+
+def bitplane_exponent(eb: float) -> int:
+    """e = floor(log2(eb)) of the unpred-aware quantizer (Sec. 4.2)."""
+    e = C.c_int32()
+    _check(lib().sz3o_bitplane_exponent(eb, C.byref(e)), "sz3o_bitplane_exponent")
+    return e.value
+
+
+def bitplane_encode_status(values: np.ndarray, eb: float):
+    """(status, stream bytes) of the unpred-aware quantizer on a float32 /
+    float64 array."""
+    v = np.ascontiguousarray(values).reshape(-1)
+    dt = {np.dtype(np.float32): F32, np.dtype(np.float64): F64}[v.dtype]
+    cap = int(lib().sz3o_bitplane_bound(v.size))
+    out = np.zeros(max(cap, 1), np.uint8)
+    nb = C.c_uint64()
+    rc = lib().sz3o_bitplane_encode(dt, _ptr(v), v.size, eb, _ptr(out), cap, C.byref(nb))
+    return rc, (out[:nb.value].tobytes() if rc == OK else b"")
+
+
+def bitplane_encode(values: np.ndarray, eb: float) -> bytes:
+    rc, s = bitplane_encode_status(values, eb)
+    _check(rc, "sz3o_bitplane_encode")
+    return s
+
+
+def bitplane_decode_status(stream: bytes, n: int, dtype):
+    out = np.zeros(max(n, 1), dtype)
+    buf = np.frombuffer(stream, np.uint8) if len(stream) else np.zeros(1, np.uint8)
+    nn = C.c_uint64()
+    rc = lib().sz3o_bitplane_decode(_ptr(buf), len(stream), _ptr(out), n * np.dtype(dtype).itemsize, C.byref(nn))
+    return rc, out[:nn.value] if rc == OK else None
+
+
+def bitplane_decode(stream: bytes) -> np.ndarray:
+    n = int(np.frombuffer(stream[8:16], np.uint64)[0])
+    dt = np.float32 if int(np.frombuffer(stream[4:8], np.uint32)[0]) == F32 else np.float64
+    rc, out = bitplane_decode_status(stream, n, dt)
+    _check(rc, "sz3o_bitplane_decode")
+    return out
+
+
+def huffman_fixed_lengths(radius: int) -> np.ndarray:
+    """Predefined code lengths over the 2 radius quantization codes."""
+    out = np.zeros(2 * radius, np.uint8)
+    _check(lib().sz3o_huffman_fixed_lengths(radius, _ptr(out)), "sz3o_huffman_fixed_lengths")
     return out

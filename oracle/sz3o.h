@@ -164,6 +164,28 @@ uint64_t sz3o_lz_bound(uint64_t n);
 int sz3o_lz_compress(const void* in, uint64_t n, void* out, uint64_t capacity, uint64_t* out_bytes);
 int sz3o_lz_decompress(const void* in, uint64_t bytes, void* out, uint64_t capacity, uint64_t* out_n);
 
+/* ---- SZ3-Pastri modules (szpastri.c) -------------------------------------
+ * Unpred-aware quantizer (Sec. 4.2): values of T (dtype 0 float, 1 double)
+ * aligned to the exponent e = floor(log2(eb)) of the bound, q = trunc(v /
+ * 2^e), stored as planes of bits.  Stream (little-endian): "SZBP", u32 dtype,
+ * u64 n, i32 e, u32 B (bit length of max |q|, <= 62), u64 W = ceil(n / 32);
+ * then W u32 words of signs (bit j of word w: q[32w + j] < 0), then B planes
+ * of W words, the plane of bit B-1 first and of bit 0 last (bit j of word w:
+ * that bit of |q[32w + j]|); bits past n are 0.  Decodes to q 2^e.
+ * Errors: SZ3O_E_INVAL (eb not finite and > 0, a |v / 2^e| >= 2^62),
+ * SZ3O_E_NONFINITE, SZ3O_E_CAPACITY; decode SZ3O_E_CORRUPT. */
+#define SZBP_HEADER 32
+int sz3o_bitplane_exponent(double eb, int32_t* e);
+uint64_t sz3o_bitplane_bound(uint64_t n);
+int sz3o_bitplane_encode(uint32_t dtype, const void* v, uint64_t n, double eb, void* out, uint64_t capacity,
+                         uint64_t* out_bytes);
+int sz3o_bitplane_decode(const void* in, uint64_t bytes, void* out, uint64_t capacity, uint64_t* n_out);
+/* Fixed Huffman code lengths over the 2 radius quantization codes (Sec. 3.2
+ * Encoder, the predefined tree of SZ-Pastri): len[r] = 1; a code at distance
+ * k >= 1 from r, with c the bit length of k, 2c + 2 bits when c <= 10, else
+ * 24; len[0] (unpredictable) = 24.  Codewords: sz3o_canonical_codes. */
+int sz3o_huffman_fixed_lengths(uint32_t radius, uint8_t* len);
+
 #ifdef __cplusplus
 }
 #endif
