@@ -161,6 +161,37 @@ int sz3g_lossless_compress(const void* d_in, uint64_t n, void* d_out, size_t out
 int sz3g_lossless_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_capacity, uint64_t* n_out,
                              void* stream);
 
+/* ---------------------------------------------------------------------------
+ * SZ3-Pastri modules on the quantize / encode path.
+ *
+ * Unpred-aware quantizer (Sec. 4.2): n values of T (dtype SZ3G_F32 / F64,
+ * device, aligned to T) are aligned to the exponent e = floor(log2(eb)) of
+ * the absolute bound eb, q = trunc(v / 2^e) (so |v - q 2^e| < 2^e <= eb), and
+ * stored by bitplane.  Stream (little-endian, d_out 16-byte aligned, at most
+ * sz3g_bitplane_bound bytes): "SZBP", u32 dtype, u64 n, i32 e, u32 B (bit
+ * length of max |q|, <= 62), u64 W = ceil(n / 32); then W u32 words of signs
+ * (bit j of word w: q[32w + j] < 0); then B planes of W words each, the plane
+ * of bit B-1 first and of bit 0 last (bit j of word w: that bit of
+ * |q[32w + j]|); bits past n are 0.  Decodes to q 2^e in T (exact).
+ * Encode errors: SZ3G_E_INVAL (eb not finite and > 0, some |v / 2^e| >= 2^62),
+ * SZ3G_E_NONFINITE, SZ3G_E_CAPACITY; decode: SZ3G_E_CORRUPT (header or
+ * length), SZ3G_E_CAPACITY.  Both synchronise `stream`.
+ *
+ * Fixed Huffman (Sec. 3.2 Encoder, the predefined tree of SZ-Pastri): the
+ * code lengths (d_len, 2 radius uint8) and canonical codewords (d_code, 2
+ * radius uint32) of a code fixed in advance, for sz3g_huffman_encode /
+ * sz3g_huffman_decode with nsym = 2 radius: code r 1 bit; a code at distance
+ * k >= 1 from r, c = bit length of k, 2c + 2 bits when c <= 10, else 24; code 0
+ * (unpredictable) 24 bits.  Asynchronous; radius in [2, 32768].
+ * ------------------------------------------------------------------------- */
+#define SZ3G_BP_HEADER 32
+int sz3g_bitplane_bound(uint64_t n, uint64_t* max_bytes);
+int sz3g_bitplane_encode(uint32_t dtype, const void* d_values, uint64_t n, double eb, void* d_out,
+                         size_t out_capacity, size_t* out_bytes, void* stream);
+int sz3g_bitplane_decode(const void* d_stream, size_t bytes, void* d_out, size_t out_capacity, uint64_t* n_out,
+                         void* stream);
+int sz3g_huffman_fixed(uint32_t radius, uint8_t* d_len, uint32_t* d_code, void* stream);
+
 int sz3g_read_header(const void* stream, size_t bytes, int stream_on_device, sz3g_params* p,
                      uint64_t* n_points);
 

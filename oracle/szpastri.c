@@ -50,18 +50,29 @@ int sz3o_bitplane_encode(uint32_t dtype, const void* v, uint64_t n, double eb, v
   uint64_t i, maxmag = 0, W = (n + 31) / 32, total;
   uint32_t B = 0, b;
   if (dtype > 1 || !out_bytes || (n && !v) || sz3o_bitplane_exponent(eb, &e) != SZ3O_OK) return SZ3O_E_INVAL;
-  /* pass 1: every value aligned, the widest magnitude */
-  for (i = 0; i < n; ++i) {
-    const double x = value_at(dtype, v, i);
-    double w;
-    if (!isfinite(x)) return SZ3O_E_NONFINITE;
-    w = ldexp(x, -e);
-    if (!(fabs(w) < 0x1p62)) return SZ3O_E_INVAL; /* aligned integer past 62 bits */
-    {
-      const double t = trunc(w);
-      const uint64_t mag = (uint64_t)fabs(t);
-      if (mag > maxmag) maxmag = mag;
+  /* pass 1: every value aligned, the widest magnitude; a non-finite value
+   * anywhere is reported before an aligned integer past 62 bits */
+  {
+    int bad = 0, wide = 0;
+    for (i = 0; i < n; ++i) {
+      const double x = value_at(dtype, v, i);
+      double w;
+      if (!isfinite(x)) {
+        bad = 1;
+        continue;
+      }
+      w = ldexp(x, -e);
+      if (!(fabs(w) < 0x1p62)) {
+        wide = 1;
+        continue;
+      }
+      {
+        const uint64_t mag = (uint64_t)fabs(trunc(w));
+        if (mag > maxmag) maxmag = mag;
+      }
     }
+    if (bad) return SZ3O_E_NONFINITE;
+    if (wide) return SZ3O_E_INVAL;
   }
   while (B < 64 && (maxmag >> B)) ++B;
   total = SZBP_HEADER + 4ull * W * (1ull + B);

@@ -668,6 +668,66 @@ int sz3g_lossless_decompress(const void* d_stream, size_t bytes, void* d_out, si
   return SZ3G_OK;
 }
 
+int sz3g_bitplane_bound(uint64_t n, uint64_t* max_bytes) {
+  if (!max_bytes) return SZ3G_E_INVAL;
+  *max_bytes = SZ3G_BP_HEADER + 4ull * ((n + 31) / 32) * 64ull;
+  return SZ3G_OK;
+}
+
+int sz3g_bitplane_encode(uint32_t dtype, const void* d_values, uint64_t n, double eb, void* d_out,
+                         size_t out_capacity, size_t* out_bytes, void* stream) {
+  int e = 0;
+  if (dtype > SZ3G_F64 || !d_out || !out_bytes || (n && !d_values) || !aligned(d_out, 16) ||
+      (n && !aligned(d_values, dtype == SZ3G_F32 ? 4 : 8)) || n > (1ull << 40))
+    return SZ3G_E_INVAL;
+  SZ3G_TRY(bitplane_exponent(eb, &e));
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch own;
+  unsigned char* ws;
+  SZ3G_TRY(get_ws(nullptr, 0, bp_state_bytes(), s, own, &ws));
+  SZ3G_TRY(launch_bitplane_encode(dtype, d_values, n, e, d_out, out_capacity, ws, s));
+  uint32_t flags = 0;
+  unsigned long long nb = 0;
+  SZ3G_TRY(read_bitplane_state(ws, &flags, &nb, s));
+  if (flags & kFlagNonFinite) return SZ3G_E_NONFINITE;  // before a too-wide value
+  SZ3G_TRY(status_of(flags));
+  *out_bytes = (size_t)nb;
+  return SZ3G_OK;
+}
+
+int sz3g_bitplane_decode(const void* d_stream, size_t bytes, void* d_out, size_t out_capacity, uint64_t* n_out,
+                         void* stream) {
+  if (!d_stream || !aligned(d_stream, 16)) return SZ3G_E_INVAL;
+  if (bytes < SZ3G_BP_HEADER) return SZ3G_E_CORRUPT;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char hb[SZ3G_BP_HEADER];
+  SZ3G_CUDA(cudaMemcpyAsync(hb, d_stream, SZ3G_BP_HEADER, cudaMemcpyDeviceToHost, s));
+  SZ3G_CUDA(cudaStreamSynchronize(s));
+  uint32_t dtype = 0, B = 0, eu = 0;
+  uint64_t n = 0, W = 0;
+  std::memcpy(&dtype, hb + 4, 4);
+  std::memcpy(&n, hb + 8, 8);
+  std::memcpy(&eu, hb + 16, 4);
+  std::memcpy(&B, hb + 20, 4);
+  std::memcpy(&W, hb + 24, 8);
+  if (std::memcmp(hb, "SZBP", 4) != 0 || dtype > SZ3G_F64 || B > 62 || n > (1ull << 40) || W != (n + 31) / 32 ||
+      bytes < SZ3G_BP_HEADER + 4ull * W * (1ull + B))
+    return SZ3G_E_CORRUPT;
+  const size_t esz = dtype == SZ3G_F32 ? 4 : 8;
+  if (n * esz > out_capacity || (n && !d_out)) return SZ3G_E_CAPACITY;
+  if (n && !aligned(d_out, esz)) return SZ3G_E_INVAL;
+  SZ3G_TRY(launch_bitplane_decode(dtype, d_stream, n, W, B, (int)(int32_t)eu, d_out, s));
+  SZ3G_CUDA(cudaStreamSynchronize(s));
+  if (n_out) *n_out = n;
+  return SZ3G_OK;
+}
+
+int sz3g_huffman_fixed(uint32_t radius, uint8_t* d_len, uint32_t* d_code, void* stream) {
+  if (radius < 2 || radius > 32768 || !d_len || !d_code) return SZ3G_E_INVAL;
+  SZ3G_TRY(launch_huffman_fixed(radius, d_len, d_code, (cudaStream_t)stream));
+  return SZ3G_OK;
+}
+
 int sz3g_graph_cache(int on) {
   {
     std::lock_guard<std::mutex> lk(g_gmu);

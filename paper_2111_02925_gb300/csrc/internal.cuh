@@ -99,7 +99,7 @@ struct Plan {
 enum KernelId {
   kKRange, kKEb, kKAnchor, kKLift, kKPassQuantize, kKPassRecover, kKCodebook, kKEncode, kKFinalize,
   kKDecodeTables, kKDecode, kKScan, kKZeroCount, kKPackTable, kKLevelQuantize, kKLevelRecover,
-  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKPublish, kKSelect, kKMlp, kKLossless, kKReport, kKernelCount
+  kKCoarseQuantize, kKCoarseRecover, kKDecimate, kKPublish, kKSelect, kKMlp, kKLossless, kKReport, kKBitplane, kKFixedTable, kKernelCount
 };
 
 // prof.cu: whether per-launch timing is on; launches replayed inside a graph
@@ -294,6 +294,15 @@ int launch_scan(const uint32_t* in, unsigned long long n, unsigned long long* ou
                 bool state_zeroed);
 
 // k_lz.cu: the optional lossless stage (byte-level LZ77 over 32 KiB blocks)
+// k_pastri.cu: unpred-aware quantizer (bitplanes) and the fixed Huffman table
+int bitplane_exponent(double eb, int* e);
+size_t bp_state_bytes();
+int launch_bitplane_encode(uint32_t dtype, const void* d_values, unsigned long long n, int e, void* d_out,
+                           unsigned long long cap, void* d_state, cudaStream_t s);
+int read_bitplane_state(const void* d_state, uint32_t* flags, unsigned long long* out_bytes, cudaStream_t s);
+int launch_bitplane_decode(uint32_t dtype, const void* d_stream, unsigned long long n, unsigned long long W,
+                           uint32_t B, int e, void* d_out, cudaStream_t s);
+int launch_huffman_fixed(uint32_t radius, uint8_t* d_len, uint32_t* d_code, cudaStream_t s);
 size_t lz_workspace_bytes(unsigned long long n);
 int launch_lz_compress(const void* d_in, unsigned long long n, void* d_out, unsigned char* ws, cudaStream_t s,
                        DevState** st);

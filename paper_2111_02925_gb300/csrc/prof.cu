@@ -15,7 +15,7 @@ namespace sz3g {
 static const char* kKernelNames[kKernelCount] = {
     "range", "eb", "anchor", "lift", "pass_quantize", "pass_recover", "codebook", "encode", "finalize",
     "decode_tables", "decode", "scan", "zero_count", "pack_table", "level_quantize", "level_recover",
-    "coarse_quantize", "coarse_recover", "decimate", "publish", "select", "mlp", "lossless", "report",
+    "coarse_quantize", "coarse_recover", "decimate", "publish", "select", "mlp", "lossless", "report", "bitplane", "fixed_table",
 };
 
 namespace {

@@ -92,6 +92,10 @@ _SIGS = {
     "sz3g_batch_destroy": [_vp],
     "sz3g_graph_cache": [C.c_int],
     "sz3g_trim": [],
+    "sz3g_bitplane_bound": [_u64, C.POINTER(_u64)],
+    "sz3g_bitplane_encode": [_u32, _vp, _u64, C.c_double, _vp, _sz, C.POINTER(_sz), _vp],
+    "sz3g_bitplane_decode": [_vp, _sz, _vp, _sz, C.POINTER(_u64), _vp],
+    "sz3g_huffman_fixed": [_u32, _vp, _vp, _vp],
     "sz3g_compress_async": [_P, _vp, _vp, _sz, _vp, _vp, _vp, _sz, _vp],
     "sz3g_decompress_async": [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp],
     "sz3g_lossless_bound": [_u64, C.POINTER(_u64)],
@@ -501,6 +505,36 @@ def sz3g_graph_cache(on: bool) -> None:
 def sz3g_trim() -> None:
     """Free the cached graphs, the host-buffer staging sets and the pool's free memory."""
     _chk(load().sz3g_trim(), "sz3g_trim")
+
+
+BP_HEADER = 32
+
+
+def sz3g_bitplane_bound(n: int) -> int:
+    b = _u64(0)
+    _chk(load().sz3g_bitplane_bound(n, C.byref(b)), "sz3g_bitplane_bound")
+    return b.value
+
+
+def sz3g_bitplane_encode(dtype: int, d_values: int, n: int, eb: float, d_out: int, out_capacity: int,
+                         stream: int = 0):
+    """Unpred-aware quantizer (bitplanes); returns (status, stream bytes)."""
+    nb = _sz(0)
+    rc = load().sz3g_bitplane_encode(dtype, d_values or None, n, eb, d_out, out_capacity, C.byref(nb),
+                                     stream or None)
+    return rc, nb.value
+
+
+def sz3g_bitplane_decode(d_stream: int, nbytes: int, d_out: int, out_capacity: int, stream: int = 0):
+    """Returns (status, n values)."""
+    n = _u64(0)
+    rc = load().sz3g_bitplane_decode(d_stream, nbytes, d_out or None, out_capacity, C.byref(n), stream or None)
+    return rc, n.value
+
+
+def sz3g_huffman_fixed(radius: int, d_len: int, d_code: int, stream: int = 0) -> int:
+    """Predefined Huffman lengths / canonical codewords over the 2 radius codes."""
+    return load().sz3g_huffman_fixed(radius, d_len, d_code, stream or None)
 
 
 def sz3g_lossless_bound(n: int) -> int:

@@ -102,6 +102,9 @@ def test_bitplane_errors():
     # an aligned integer of 62 bits or more
     rc, _ = O.bitplane_encode_status(np.array([2.0 ** 62], np.float64), 1.0)
     assert rc == O.E_INVAL
+    # a non-finite value anywhere is reported before a too-wide one
+    rc, _ = O.bitplane_encode_status(np.array([2.0 ** 63, 0.0, np.inf], np.float64), 1.0)
+    assert rc == O.E_NONFINITE
     rc, _ = O.bitplane_encode_status(np.array([2.0 ** 61], np.float64), 1.0)
     assert rc == O.OK
     for eb in (0.0, -1.0, float("nan"), float("inf")):
