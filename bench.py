@@ -14,6 +14,7 @@ steps.
   python bench.py --workload batch   # the uneven 256-field batch, batched vs one call per field
   python bench.py --workload selector  # per-level selection on a 1024^3 field with fronts
   python bench.py --workload lossless  # the optional lossless stage on two workloads' streams
+  python bench.py --workload pastri    # unpred-aware quantizer (bitplanes) and the fixed Huffman table
 
 --impl reference times the serial CPU oracle on the host cores, on a bounded
 sample (a 128^3 corner of the same field) per step.  N > 1 (torchrun) runs
@@ -49,7 +50,7 @@ def parse():
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="field", choices=["field", "batch", "selector", "lossless"])
+    ap.add_argument("--workload", default="field", choices=["field", "batch", "selector", "lossless", "pastri"])
     ap.add_argument("--train-fields", type=int, default=400)
     ap.add_argument("--fields", type=int, default=256)
     return ap.parse_args()
@@ -617,10 +618,147 @@ def run_lossless(args):
     return 0
 
 
+def _median_ms(fn, k):
+    """Median of k CUDA-event timings of fn() on the current stream."""
+    import torch
+
+    ts = []
+    for _ in range(k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def run_pastri(args):
+    """The SZ3-Pastri modules.  (1) The unpred-aware quantizer on 2^26 FP32
+    prediction differences of unpredictable points (Laplace, scale 200 eb,
+    5% of them 100x wider; eb 1e-3): encode / decode GB/s of input bytes and
+    the dominant kernel's roofline, and the lossless stage's size on the
+    bitplane stream against the same integers stored one int32 per value.
+    (2) The fixed Huffman table against the built codebook on the codes of
+    the 512^3 field (REL 1e-3, cubic): table time, encode GB/s, payload."""
+    import numpy as np
+    import torch
+
+    from paper_2111_02925_gb300 import build as B
+    from paper_2111_02925_gb300 import synthetic as S
+    from paper_2111_02925_gb300 import sz3g as G
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    B.build()
+    G.load()
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    peak, peak_kind = peaks()
+    k = max(3, min(args.steps, 20))
+    # (1) unpred-aware quantizer
+    rng = np.random.default_rng(SEED)
+    n, eb = 1 << 26, 1e-3
+    v = rng.laplace(0.0, 200 * eb, n)
+    wide = rng.random(n) < 0.05
+    v[wide] *= 100.0
+    vd = torch.from_numpy(v.astype(np.float32)).to(dev)
+    cap = G.sz3g_bitplane_bound(n)
+    bp = torch.empty(cap, dtype=torch.uint8, device=dev)
+    back = torch.empty(n, dtype=torch.float32, device=dev)
+    nb = [0]
+
+    def enc():
+        rc, nb[0] = G.sz3g_bitplane_encode(G.F32, vd.data_ptr(), n, eb, bp.data_ptr(), cap, sh)
+        assert rc == 0
+
+    def dec():
+        rc, m = G.sz3g_bitplane_decode(bp.data_ptr(), nb[0], back.data_ptr(), n * 4, sh)
+        assert rc == 0 and m == n
+
+    for _ in range(3):
+        enc()
+        dec()
+    e = int(np.floor(np.log2(eb)))
+    assert float((back - vd).abs().max()) < 2.0 ** e
+    t_enc, t_dec = _median_ms(enc, k), _median_ms(dec, k)
+    planes = int(np.frombuffer(bp[20:24].cpu().numpy().tobytes(), np.uint32)[0])
+    # the lossless stage on the bitplane stream and on one int32 per value
+    q32 = torch.trunc(vd.double() / 2.0 ** e).to(torch.int32).contiguous()
+    sizes = {}
+    for name, buf, nbytes in (("bitplane", bp, nb[0]), ("int32_per_value", q32, n * 4)):
+        lcap = G.sz3g_lossless_bound(nbytes)
+        lz = torch.empty(lcap, dtype=torch.uint8, device=dev)
+        rc, m = G.sz3g_lossless_compress(buf.data_ptr(), nbytes, lz.data_ptr(), lcap, sh)
+        assert rc == 0
+        sizes[name] = {"bytes": int(nbytes), "after_lossless": int(m)}
+    bp_res = {
+        "values": n, "input_bytes": n * 4, "stream_bytes": int(nb[0]), "planes": planes,
+        "encode_ms": t_enc, "decode_ms": t_dec,
+        "encode_GB/s": n * 4 / (t_enc * 1e-3) / 1e9, "decode_GB/s": n * 4 / (t_dec * 1e-3) / 1e9,
+        "encode_frac_of_hbm_algorithmic": (n * 4 + nb[0]) / (t_enc * 1e-3) / 1e9 / peak,
+        "decode_frac_of_hbm_algorithmic": (n * 4 + nb[0]) / (t_dec * 1e-3) / 1e9 / peak,
+        "lossless": sizes,
+    }
+    del q32, bp, back, vd
+    # (2) fixed Huffman table against the built codebook
+    x = S.grf((args.size,) * 3, SEED)
+    p = G.make_params(x.shape, EB, eb_mode=G.REL, interp=G.CUBIC)
+    xd = torch.from_numpy(x.reshape(-1)).to(dev)
+    N = x.size
+    codes = torch.empty(N + 128, dtype=torch.int16, device=dev)
+    unpred = torch.empty(N, dtype=torch.float32, device=dev)
+    hist = torch.zeros(65536, dtype=torch.int32, device=dev)
+    ws = G.workspace(p, False, dev)
+    rc, n_unpred, _ = G.sz3g_predict_quantize(p, xd.data_ptr(), codes.data_ptr(), unpred.data_ptr(), hist.data_ptr(),
+                                              ws.data_ptr(), ws.numel(), sh)
+    assert rc == 0
+    del ws, unpred
+    radius, chunk = 32768, 4096
+    nsym = 2 * radius
+    nch = (N + chunk - 1) // chunk
+    wcap = nch * ((chunk * 24 + 31) // 32)
+    words = torch.empty(wcap, dtype=torch.int32, device=dev)
+    cw = torch.empty(nch, dtype=torch.int32, device=dev)
+    tabs = {}
+    for name in ("built", "fixed"):
+        ln = torch.zeros(65536, dtype=torch.uint8, device=dev)
+        cd = torch.zeros(65536, dtype=torch.int32, device=dev)
+
+        def table():
+            if name == "built":
+                assert G.sz3g_huffman_build(hist.data_ptr(), nsym, ln.data_ptr(), cd.data_ptr(), sh) == 0
+            else:
+                assert G.sz3g_huffman_fixed(radius, ln.data_ptr(), cd.data_ptr(), sh) == 0
+
+        nw = [0]
+
+        def encode():
+            rc, nw[0] = G.sz3g_huffman_encode(codes.data_ptr(), N, ln.data_ptr(), cd.data_ptr(), nsym, chunk,
+                                              words.data_ptr(), wcap, cw.data_ptr(), 0, sh)
+            assert rc == 0
+
+        table()
+        encode()
+        t_tab, t_e = _median_ms(table, k), _median_ms(encode, k)
+        used = int((ln > 0).sum())
+        tabs[name] = {"table_ms": t_tab, "encode_ms": t_e, "encode_GB/s_codes": N * 2 / (t_e * 1e-3) / 1e9,
+                      "payload_bytes": nw[0] * 4, "stored_table_bytes": 3 * used if name == "built" else 0}
+    line = {"metric": "SZ3-Pastri modules on 1 GB300: unpred-aware quantizer GB/s (input bytes); fixed Huffman",
+            "unit": "GB/s", "value": bp_res["encode_GB/s"], "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic", "peak_gbs": peak, "peak_kind": peak_kind,
+            "config": {"workload": "2^26 FP32 Laplace prediction differences (scale 200 eb, 5% x100), eb 1e-3; "
+                                   f"codes of the {args.size}^3 k^-3 field (REL 1e-3, cubic)",
+                       "bitplane": bp_res, "huffman": tabs, "n_unpred": int(n_unpred)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "lossless":
         return run_lossless(args)
+    if args.workload == "pastri":
+        return run_pastri(args)
     if args.workload == "selector":
         return run_selector(args)
     if args.impl == "reference":

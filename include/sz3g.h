@@ -315,7 +315,8 @@ int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_le
 
 /*
  * Chunked Huffman decode of n codes (Sec. 3.2 Encoder decode()).  d_len are
- * the code lengths of nsym symbols.  With d_sub_bits (as written by
+ * the code lengths of nsym symbols: any prefix code with lengths <= LMAX
+ * (Kraft sum <= 1; an incomplete one such as sz3g_huffman_fixed's too).  With d_sub_bits (as written by
  * sz3g_huffman_encode) every 512-code sub-block decodes on its own thread and
  * must end exactly where the table says; with NULL one thread decodes a
  * chunk.  SZ3G_E_CORRUPT when a chunk runs out of bits, holds a bit pattern

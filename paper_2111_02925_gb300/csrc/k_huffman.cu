@@ -1287,7 +1287,11 @@ __global__ void __launch_bounds__(kCbThreads) decode_tables_kernel(const unsigne
     warp_count(s_cnt, L, ok);
   }
   __syncthreads();
-  const bool kraft_ok = K == 1 ? s_kraft == (1ull << (SZ3G_LMAX - 1)) : s_kraft == (1ull << SZ3G_LMAX);
+  // a stream's table is a complete code (one symbol: one 1-bit codeword); a
+  // caller's length array may be any prefix code (Kraft sum <= 1): windows
+  // past its last codeword are no codeword and stop the decoder
+  const unsigned long long full = 1ull << SZ3G_LMAX;
+  const bool kraft_ok = tab ? (K == 1 ? s_kraft == full / 2 : s_kraft == full) : s_kraft <= full;
   if (s_bad || !kraft_ok) {
     if (tid == 0) atomicOr(&st->flags, kFlagCorrupt);
     return;

@@ -5,11 +5,12 @@
 // stored as a sign plane and B magnitude planes, most significant first
 // (stream layout in include/sz3g.h).  Two kernels: a scan for B and the
 // finiteness / width checks, then the planes, a tile of 1024 values (32 plane
-// words) per CTA iteration -- each warp turns 32 values into one word of a
-// plane with a ballot, the words of a tile meet in shared memory and every
-// plane row of the tile leaves as one coalesced 128-byte store.  The decoder
-// stages a tile's plane words in shared memory and rebuilds each value from
-// its bit of every plane word (a broadcast read per plane).
+// words) per CTA iteration -- a warp turns its 32 magnitudes into the 32
+// plane words of their bits with one 32 x 32 bit-matrix transpose across the
+// lanes (five exchange rounds), the words of a tile meet in shared memory and
+// every plane row of the tile leaves as one coalesced 128-byte store.  The
+// decoder stages a tile's plane words in shared memory and runs the same
+// transpose backwards (it is its own inverse).
 //
 // Fixed Huffman (Sec. 3.2 Encoder, the predefined tree of SZ-Pastri): the
 // lengths and canonical codewords of the predefined code over the 2r
@@ -33,11 +34,43 @@ struct BpState {
   unsigned long long out_bytes;
 };
 
-// v / 2^e rounded toward zero (in double; exact while it fits 62 bits)
-template <typename T>
-__device__ __forceinline__ double bp_aligned(T v, int e) {
-  return trunc(scalbn((double)v, -e));
+// v / 2^e rounded toward zero, as its magnitude and sign; false when it is
+// 2^62 or wider.  In T: scaling by a power of two is exact unless the result
+// leaves T's range, and then it is either too wide (overflow) or below 1
+// (underflow, truncated to 0) either way -- so float data never needs FP64.
+__device__ __forceinline__ bool bp_align(float v, int e, unsigned long long* mag, bool* neg) {
+  const float w = scalbnf(v, -e);
+  if (!(fabsf(w) < 0x1p62f)) return false;
+  const float t = truncf(w);
+  *mag = (unsigned long long)fabsf(t);
+  *neg = t < 0.0f;
+  return true;
 }
+__device__ __forceinline__ bool bp_align(double v, int e, unsigned long long* mag, bool* neg) {
+  const double w = scalbn(v, -e);
+  if (!(fabs(w) < 0x1p62)) return false;
+  const double t = trunc(w);
+  *mag = (unsigned long long)fabs(t);
+  *neg = t < 0.0;
+  return true;
+}
+
+// 32 x 32 bit-matrix transpose across a warp: bit j of lane i's input is
+// bit i of lane j's output.  Five rounds; in round s a lane swaps, with the
+// lane s away, the bit columns whose index differs from its own in bit s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const int sft = 16 >> r;
+    const uint32_t m = masks[r];
+    const uint32_t t = __shfl_xor_sync(0xffffffffu, x, sft);
+    x = (lane & sft) ? ((x & ~m) | ((t & ~m) >> sft)) : ((x & m) | ((t & m) << sft));
+  }
+  return x;
+}
+
+constexpr int kBpRow = 33;  // shared-memory words per plane row of a tile (padded: no bank conflicts)
 
 template <typename T>
 __global__ void __launch_bounds__(kBpThreads) bp_scan_kernel(const T* __restrict__ v, unsigned long long n, int e,
@@ -45,21 +78,27 @@ __global__ void __launch_bounds__(kBpThreads) bp_scan_kernel(const T* __restrict
   uint32_t width = 0;
   bool bad = false, wide = false;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const double x = (double)v[i];
+  auto take = [&](T x) {
     if (!isfinite(x)) {
       bad = true;
-      continue;
+      return;
     }
-    const double w = scalbn(x, -e);
-    if (!(fabs(w) < 0x1p62)) {
+    unsigned long long mag;
+    bool neg;
+    if (!bp_align(x, e, &mag, &neg)) {
       wide = true;
-      continue;
+      return;
     }
-    const unsigned long long mag = (unsigned long long)fabs(trunc(w));
     const uint32_t bl = mag ? 64u - (uint32_t)__clzll((long long)mag) : 0u;
     width = bl > width ? bl : width;
+  };
+  unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {  // four loads in flight
+    const T x0 = __ldcs(v + i), x1 = __ldcs(v + i + stride), x2 = __ldcs(v + i + 2 * stride),
+            x3 = __ldcs(v + i + 3 * stride);
+    take(x0), take(x1), take(x2), take(x3);
   }
+  for (; i < n; i += stride) take(__ldcs(v + i));
   width = __reduce_max_sync(0xffffffffu, width);
   const bool any_bad = __any_sync(0xffffffffu, bad), any_wide = __any_sync(0xffffffffu, wide);
   if ((threadIdx.x & 31) == 0) {
@@ -73,7 +112,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBpThreads) bp_encode_kernel(const T* __restrict__ v, unsigned long long n, int e,
                                                               uint32_t dtype, unsigned long long W,
                                                               unsigned long long cap, uint8_t* out, BpState* st) {
-  __shared__ uint32_t sm[(kBpMaxB + 1) * 32];
+  __shared__ uint32_t sm[(kBpMaxB + 1) * kBpRow];
   if (st->flags) return;
   const uint32_t B = st->B;
   const unsigned long long total = SZ3G_BP_HEADER + 4ull * W * (1ull + B);
@@ -99,21 +138,24 @@ __global__ void __launch_bounds__(kBpThreads) bp_encode_kernel(const T* __restri
     for (int k = 0; k < kBpTile / 32 / (kBpThreads / 32); ++k) {
       const int g = warp + (kBpThreads / 32) * k;
       const unsigned long long i = t * kBpTile + (unsigned long long)g * 32 + lane;
-      const double q = i < n ? bp_aligned(v[i], e) : 0.0;
-      const unsigned long long mag = (unsigned long long)fabs(q);
-      const uint32_t sw = __ballot_sync(0xffffffffu, q < 0.0);
+      unsigned long long mag = 0;
+      bool neg = false;
+      if (i < n) bp_align(v[i], e, &mag, &neg);  // in range: the scan found no wider value
+      const uint32_t sw = __ballot_sync(0xffffffffu, neg);
       if (lane == 0) sm[g] = sw;
-      for (uint32_t b = 0; b < B; ++b) {
-        const uint32_t wd = __ballot_sync(0xffffffffu, (mag >> b) & 1ull);
-        const uint32_t p = 1 + (B - 1 - b);
-        if (lane == (int)(p & 31)) sm[p * 32 + g] = wd;
+      // lane b receives the plane word of bit b (plane B - b)
+      const uint32_t lo = warp_transpose32((uint32_t)mag, lane);
+      if ((uint32_t)lane < B) sm[(B - lane) * kBpRow + g] = lo;
+      if (B > 32) {
+        const uint32_t hi = warp_transpose32((uint32_t)(mag >> 32), lane);
+        if ((uint32_t)lane + 32 < B) sm[(B - 32 - lane) * kBpRow + g] = hi;
       }
     }
     __syncthreads();
     const unsigned long long w0 = t * 32;
     for (uint32_t idx = threadIdx.x; idx < (B + 1) * 32; idx += kBpThreads) {
       const uint32_t p = idx >> 5, g = idx & 31;
-      if (w0 + g < W) planes[(unsigned long long)p * W + w0 + g] = sm[idx];
+      if (w0 + g < W) planes[(unsigned long long)p * W + w0 + g] = sm[p * kBpRow + g];
     }
     __syncthreads();
   }
@@ -123,28 +165,35 @@ template <typename T>
 __global__ void __launch_bounds__(kBpThreads) bp_decode_kernel(const uint32_t* __restrict__ planes,
                                                               unsigned long long n, unsigned long long W, uint32_t B,
                                                               int e, T* __restrict__ out) {
-  __shared__ uint32_t sm[(kBpMaxB + 1) * 32];
+  __shared__ uint32_t sm[(kBpMaxB + 1) * kBpRow];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned long long ntiles = (n + kBpTile - 1) / kBpTile;
   for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const unsigned long long w0 = t * 32;
     for (uint32_t idx = threadIdx.x; idx < (B + 1) * 32; idx += kBpThreads) {
       const uint32_t p = idx >> 5, g = idx & 31;
-      sm[idx] = w0 + g < W ? planes[(unsigned long long)p * W + w0 + g] : 0u;
+      sm[p * kBpRow + g] = w0 + g < W ? planes[(unsigned long long)p * W + w0 + g] : 0u;
     }
     __syncthreads();
 #pragma unroll 1
     for (int k = 0; k < kBpTile / 32 / (kBpThreads / 32); ++k) {
       const int g = warp + (kBpThreads / 32) * k;
       const unsigned long long i = t * kBpTile + (unsigned long long)g * 32 + lane;
-      unsigned long long mag = 0;
-      for (uint32_t b = 0; b < B; ++b) {
-        const uint32_t p = 1 + (B - 1 - b);
-        mag |= (unsigned long long)((sm[p * 32 + g] >> lane) & 1u) << b;
+      // lane b holds the plane word of bit b; the transpose gives lane i its bits
+      const uint32_t wlo = (uint32_t)lane < B ? sm[(B - lane) * kBpRow + g] : 0u;
+      unsigned long long mag = warp_transpose32(wlo, lane);
+      if (B > 32) {
+        const uint32_t whi = (uint32_t)lane + 32 < B ? sm[(B - 32 - lane) * kBpRow + g] : 0u;
+        mag |= (unsigned long long)warp_transpose32(whi, lane) << 32;
       }
-      double r = scalbn((double)mag, e);
-      if ((sm[g] >> lane) & 1u) r = -r;
-      if (i < n) out[i] = (T)r;
+      T r;
+      if (sizeof(T) == 4 && B <= 24) {  // |q| < 2^24: exact in float, one rounding at most (underflow)
+        r = (T)scalbnf((float)mag, e);
+      } else {
+        r = (T)scalbn((double)mag, e);
+      }
+      if ((sm[g] >> lane) & 1u) r = -r;  // the sign plane is row 0
+      if (i < n) out[i] = r;
     }
     __syncthreads();
   }
@@ -222,12 +271,14 @@ int launch_bitplane_encode(uint32_t dtype, const void* d_values, unsigned long l
   const unsigned long long W = (n + 31) / 32;
   const int g1 = bp_grid(n, 8), g2 = bp_grid(n, 8);
   if (dtype == SZ3G_F32) {
-    if (n) SZ3G_LAUNCH(kKBitplane, s, bp_scan_kernel<float><<<g1, kBpThreads, 0, s>>>((const float*)d_values, n, e, st));
+    if (n)
+      SZ3G_LAUNCH(kKBitplane, s, bp_scan_kernel<float><<<g1, kBpThreads, 0, s>>>((const float*)d_values, n, e, st));
     SZ3G_LAUNCH(kKBitplane, s,
                 bp_encode_kernel<float><<<g2, kBpThreads, 0, s>>>((const float*)d_values, n, e, dtype, W, cap,
                                                                    (uint8_t*)d_out, st));
   } else {
-    if (n) SZ3G_LAUNCH(kKBitplane, s, bp_scan_kernel<double><<<g1, kBpThreads, 0, s>>>((const double*)d_values, n, e, st));
+    if (n)
+      SZ3G_LAUNCH(kKBitplane, s, bp_scan_kernel<double><<<g1, kBpThreads, 0, s>>>((const double*)d_values, n, e, st));
     SZ3G_LAUNCH(kKBitplane, s,
                 bp_encode_kernel<double><<<g2, kBpThreads, 0, s>>>((const double*)d_values, n, e, dtype, W, cap,
                                                                     (uint8_t*)d_out, st));
