@@ -243,7 +243,11 @@ int sz3g_decompress_async(const void* h_header, const void* d_stream, size_t byt
  * sz3g_graph_cache); a call made while another thread holds the set stages
  * through memory of the library's stream-ordered pool instead.  Both return
  * after synchronising `stream`.  h_* may be pageable or pinned; pinned memory
- * makes the copies asynchronous and faster.  Same errors as the device forms.
+ * makes the copies asynchronous and faster.  Decompressing into page-locked
+ * h_out a 3-D field whose finest level runs on the register-blocked kernel,
+ * that level runs in slabs of planes and each slab is copied out (on a
+ * library stream) while the next ones are computed.  Same errors as the
+ * device forms; on an error the contents of h_out are unspecified.
  */
 int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size_t out_capacity,
                        size_t* out_bytes, void* stream);

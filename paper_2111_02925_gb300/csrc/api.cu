@@ -458,6 +458,10 @@ int decompress_parsed(const unsigned char* hb, const void* d_stream, size_t byte
     key_add(key, out_capacity);
     key_add(key, d_workspace);
     key_add(key, ws_bytes);
+    if (g_slab_sink) {  // the graph holds the copies to this host buffer
+      key_add(key, g_slab_sink->h_out);
+      key_add(key, g_slab_sink->slabs);
+    }
     SZ3G_TRY(run_cached(
         key, s, [&](cudaStream_t es, DevState** sto) { return decompress_enqueue(h, d_stream, d_out, ws, es, sto); },
         &st));
@@ -480,6 +484,7 @@ struct Staging {
   size_t cap[3] = {0, 0, 0};
 };
 constexpr int kStageDevices = 64;
+constexpr int kOutputSlabs = 8;  // slabs of planes the host-buffer decompress copies out one by one
 Staging g_stage[kStageDevices];
 
 Staging* staging_of_current() {
@@ -766,6 +771,36 @@ int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_
 
 namespace {
 
+// The library's stream for copies that overlap a pipeline, one per device.
+cudaStream_t copy_stream_of_current() {
+  static std::mutex mu;
+  static cudaStream_t streams[kStageDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStageDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    streams[dev] = nullptr;
+  }
+  return streams[dev];
+}
+
+// Whether [h, h + n) is page-locked host memory (copies from the device into
+// it can run asynchronously and inside a graph).
+bool host_locked(const void* h, size_t n) {
+  if (!h || !n) return false;
+  cudaPointerAttributes a0, a1;
+  if (cudaPointerGetAttributes(&a0, h) != cudaSuccess ||
+      cudaPointerGetAttributes(&a1, (const unsigned char*)h + (n - 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a0.type == cudaMemoryTypeHost && a1.type == cudaMemoryTypeHost;
+}
+
 // Holds the current device's staging set for one host-buffer call, if no
 // other thread has it; on release the stream is synchronised first, so that
 // no copy or kernel of an abandoned call still touches the buffers.
@@ -879,8 +914,19 @@ int sz3g_decompress_host(const void* h_stream, size_t bytes, void* h_out, size_t
     d_out = dout.ptr;
   }
   SZ3G_CUDA(cudaMemcpyAsync(d_st, h_stream, bytes, cudaMemcpyHostToDevice, s));
-  SZ3G_TRY(decompress_parsed(hb, d_st, bytes, d_out, out_bytes, d_ws, d_ws ? hold.g->cap[2] : 0, s));
-  SZ3G_CUDA(cudaMemcpyAsync(h_out, d_out, out_bytes, cudaMemcpyDeviceToHost, s));
+  // A page-locked output of a field whose finest level runs on the
+  // register-blocked kernel leaves in slabs of planes, each copied while the
+  // later slabs are still computed.  Only the holder of the staging set uses
+  // the copy stream, so no two calls ever share it (one may be capturing).
+  cudaStream_t cs = nullptr;
+  const bool slabbed = hold.g && recover_writes_out_once(h.plan, d_out) && host_locked(h_out, out_bytes) &&
+                       (cs = copy_stream_of_current()) != nullptr;
+  SlabSink sink{h_out, cs, kOutputSlabs};
+  g_slab_sink = slabbed ? &sink : nullptr;
+  const int rc = decompress_parsed(hb, d_st, bytes, d_out, out_bytes, d_ws, d_ws ? hold.g->cap[2] : 0, s);
+  g_slab_sink = nullptr;
+  SZ3G_TRY(rc);
+  if (!slabbed) SZ3G_CUDA(cudaMemcpyAsync(h_out, d_out, out_bytes, cudaMemcpyDeviceToHost, s));
   SZ3G_CUDA(cudaStreamSynchronize(s));
   return SZ3G_OK;
 }

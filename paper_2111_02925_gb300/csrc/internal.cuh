@@ -260,6 +260,19 @@ int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unp
 // SMs; read on the host at launch time.
 extern int g_level_cta_cap;
 bool level_path_ok(const Plan& pl);
+// Whether decompressing writes the field only from the finest level's
+// register-blocked kernel, in plane-group order (3-D, rows of 16 bytes, a
+// 16-byte aligned output): the field can then leave for the host in slabs.
+bool recover_writes_out_once(const Plan& pl, const void* d_out);
+// Copies of the field to page-locked host memory, issued on `copy` as each
+// slab of the finest level's planes is done (set by the host-buffer
+// decompress around its enqueue; read on the same thread).
+struct SlabSink {
+  void* h_out;
+  cudaStream_t copy;
+  int slabs;
+};
+extern thread_local const SlabSink* g_slab_sink;
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
                           DevState* st, void* X1, bool x1_ready, cudaStream_t s, LevelQueue* lq = nullptr,
                           int field = 0);

@@ -28,6 +28,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <functional>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -101,7 +102,7 @@ struct FineLayout {
 struct FineDesc {
   int m0, m1, m2;              // extents of G_k (m0 = 1 in 2-D)
   int nt1, nt2;                // tiles along j, k
-  uint32_t ntiles;
+  uint32_t tile0, ntiles;       // tiles [tile0, ntiles) of this launch
   uint32_t off[3];             // first code of passes 0, 1, 2 (pass 0 unused in 2-D)
   uint32_t E1[3], E2[3];       // lattice extents of each pass along j and k
   uint32_t rs0, rs1;           // output row strides (elements) along i, j; contiguous along k
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
 
   constexpr int ST = FineThreads<COMP>::kStages;
   uint32_t phase[2] = {0u, 0u};
-  uint32_t tile = blockIdx.x;
+  uint32_t tile = d.tile0 + blockIdx.x;
   if (ST == 2) {
     if (tile < d.ntiles) issue(tile, 0);
     __syncthreads();
@@ -652,8 +653,10 @@ bool fine_eligible(const Plan& pl, int k, bool comp, const void* x, const unsign
   return m[2] >= 2 && m[3] >= 2 && pl.gsize[k] <= 0xffffffffull;
 }
 
+// Tiles of the plane groups [g0, g1) along axis 0 (T0 planes of G_k each).
 template <typename T, bool COMP, int T0>
-static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_field, cudaStream_t s) {
+static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_field, cudaStream_t s,
+                         uint32_t g0 = 0, uint32_t g1 = 0xffffffffu) {
   using S = FineShape<T0>;
   FineDesc d;
   memset(&d, 0, sizeof(d));
@@ -664,7 +667,10 @@ static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_f
   d.nt1 = (d.m1 + S::kT1 - 1) / S::kT1;
   d.nt2 = (d.m2 + S::kW - 1) / S::kW;
   const int nt0 = (d.m0 + S::kT0 - 1) / S::kT0;
-  d.ntiles = (uint32_t)nt0 * (uint32_t)d.nt1 * (uint32_t)d.nt2;
+  if (g1 > (uint32_t)nt0) g1 = (uint32_t)nt0;
+  if (g0 >= g1) return SZ3G_OK;
+  d.tile0 = g0 * (uint32_t)d.nt1 * (uint32_t)d.nt2;
+  d.ntiles = g1 * (uint32_t)d.nt1 * (uint32_t)d.nt2;
   int p = S::kHas0 ? 0 : 1;
   int interp = SZ3G_LINEAR;
   for (int i = 0; i < pl.n_pass; ++i) {
@@ -708,7 +714,7 @@ static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_f
   if (per < 1) per = 1;
   unsigned long long grid = (unsigned long long)nsm * per;
   if (g_level_cta_cap > 0 && grid > (unsigned long long)g_level_cta_cap) grid = (unsigned long long)g_level_cta_cap;
-  if (grid > d.ntiles) grid = d.ntiles;
+  if (grid > d.ntiles - d.tile0) grid = d.ntiles - d.tile0;
   SZ3G_LAUNCH(COMP ? kKLevelQuantize : kKLevelRecover, s,
               kern<<<(unsigned)grid, FineThreads<COMP>::kN, smem, s>>>(d, a, tmx, tmc));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
@@ -719,6 +725,31 @@ int launch_fine(const Plan& pl, int k, const LevelArgs<T>& a, bool to_field, cud
   return pl.gm[k][1] > 1 ? launch_fine_t<T, COMP, 4>(pl, k, a, to_field, s)
                          : launch_fine_t<T, COMP, 1>(pl, k, a, to_field, s);
 }
+
+// The finest level of a decompress (3-D, to the field) in `slabs` launches of
+// consecutive plane groups; after each, `done(first_plane, planes)` is called
+// on the host with the field planes that launch completed.
+template <typename T>
+int launch_fine_slabs(const Plan& pl, const LevelArgs<T>& a, cudaStream_t s, int slabs,
+                      const std::function<int(unsigned long long, unsigned long long)>& done) {
+  constexpr int T0 = 4;
+  const unsigned long long m0 = pl.gm[0][1];
+  const uint32_t ng = (uint32_t)((m0 + T0 - 1) / T0);
+  const uint32_t per = (ng + (uint32_t)slabs - 1) / (uint32_t)slabs;
+  for (uint32_t g0 = 0; g0 < ng; g0 += per) {
+    const uint32_t g1 = g0 + per < ng ? g0 + per : ng;
+    const int rc = launch_fine_t<T, false, T0>(pl, 0, a, true, s, g0, g1);
+    if (rc != SZ3G_OK) return rc;
+    const unsigned long long p0 = (unsigned long long)g0 * T0, p1 = (unsigned long long)g1 * T0 < m0 ? g1 * T0 : m0;
+    const int rd = done(p0, p1 - p0);
+    if (rd != SZ3G_OK) return rd;
+  }
+  return SZ3G_OK;
+}
+template int launch_fine_slabs<float>(const Plan&, const LevelArgs<float>&, cudaStream_t, int,
+                                      const std::function<int(unsigned long long, unsigned long long)>&);
+template int launch_fine_slabs<double>(const Plan&, const LevelArgs<double>&, cudaStream_t, int,
+                                       const std::function<int(unsigned long long, unsigned long long)>&);
 
 template int launch_fine<float, true>(const Plan&, int, const LevelArgs<float>&, bool, cudaStream_t);
 template int launch_fine<float, false>(const Plan&, int, const LevelArgs<float>&, bool, cudaStream_t);

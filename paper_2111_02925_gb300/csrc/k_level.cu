@@ -26,6 +26,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <functional>
 #include <numeric>
 #include <unordered_map>
 #include <vector>
@@ -891,11 +892,22 @@ bool fine_eligible(const Plan& pl, int k, bool comp, const void* x, const unsign
                    const void* Rout, bool to_field);
 template <typename T, bool COMP>
 int launch_fine(const Plan& pl, int k, const LevelArgs<T>& a, bool to_field, cudaStream_t s);
+template <typename T>
+int launch_fine_slabs(const Plan& pl, const LevelArgs<T>& a, cudaStream_t s, int slabs,
+                      const std::function<int(unsigned long long, unsigned long long)>& done);
 
 int coarse_grid(const Plan& pl) {
   int kc = pl.L;
   while (kc > 0 && pl.gsize[kc - 1] <= kCoarseMax) --kc;
   return kc;
+}
+
+thread_local const SlabSink* g_slab_sink = nullptr;
+
+bool recover_writes_out_once(const Plan& pl, const void* d_out) {
+  alignas(16) static const unsigned char kAlignedRc[16] = {};
+  return level_path_ok(pl) && coarse_grid(pl) > 0 && pl.gm[0][1] > 1 &&
+         fine_eligible(pl, 0, false, nullptr, nullptr, kAlignedRc, d_out, true);
 }
 
 static void tile_shape(const Plan& pl, int k, const int* pos, int* B) {
@@ -1552,6 +1564,29 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
   return SZ3G_OK;
 }
 
+// The finest level in slabs of planes, each slab copied to the host on the
+// sink's stream as soon as its launch is done; the copies join back into s.
+template <typename T>
+static int recover_finest_to_host(const Plan& pl, const LevelArgs<T>& a, cudaStream_t s, const SlabSink& sink) {
+  const unsigned long long plane = pl.fstride[1] * pl.esz;
+  auto done = [&](unsigned long long p0, unsigned long long np) -> int {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return SZ3G_E_CUDA;
+    const bool ok = cudaEventRecord(ev, s) == cudaSuccess && cudaStreamWaitEvent(sink.copy, ev, 0) == cudaSuccess &&
+                    cudaMemcpyAsync((unsigned char*)sink.h_out + p0 * plane, (const unsigned char*)a.Rout + p0 * plane,
+                                    np * plane, cudaMemcpyDeviceToHost, sink.copy) == cudaSuccess;
+    cudaEventDestroy(ev);
+    return ok ? SZ3G_OK : SZ3G_E_CUDA;
+  };
+  int rc = launch_fine_slabs<T>(pl, a, s, sink.slabs, done);
+  cudaEvent_t join;
+  if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) return SZ3G_E_CUDA;
+  const bool ok = cudaEventRecord(join, sink.copy) == cudaSuccess && cudaStreamWaitEvent(s, join, 0) == cudaSuccess;
+  cudaEventDestroy(join);
+  if (rc == SZ3G_OK && !ok) rc = SZ3G_E_CUDA;
+  return rc;
+}
+
 template <typename T>
 static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred, unsigned long long n_unpred,
                          const unsigned long long* zunit, void* const* R, T* out, DevState* st,
@@ -1574,6 +1609,11 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
     a.Rout = k == 0 ? out : (T*)R[k];
     if (lq) {
       queue_add<T>(lq, pl, k, field, a);
+      continue;
+    }
+    if (k == 0 && g_slab_sink && a.codes_padded && recover_writes_out_once(pl, out)) {
+      rc = recover_finest_to_host(pl, a, s, *g_slab_sink);
+      if (rc) return rc;
       continue;
     }
     rc = run_level<T, false>(pl, k, a, s);
