@@ -882,14 +882,15 @@ def main():
         hy = torch.empty(x.size, dtype=torch.float32).pin_memory()
         ke = min(args.steps, 5)
         nbh = 0
+        hst = int(torch.cuda.Stream().cuda_stream)  # a stream of the caller's own, as a user would
         for _ in range(2):
-            rc, nbh = G.sz3g_compress_host(p, hx.data_ptr(), hs.data_ptr(), hs.numel(), sh)
-            G.sz3g_decompress_host(hs.data_ptr(), nbh, hy.data_ptr(), hy.numel() * 4, sh)
+            rc, nbh = G.sz3g_compress_host(p, hx.data_ptr(), hs.data_ptr(), hs.numel(), hst)
+            G.sz3g_decompress_host(hs.data_ptr(), nbh, hy.data_ptr(), hy.numel() * 4, hst)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ke):
-            rc, nbh = G.sz3g_compress_host(p, hx.data_ptr(), hs.data_ptr(), hs.numel(), sh)
-            rc2 = G.sz3g_decompress_host(hs.data_ptr(), nbh, hy.data_ptr(), hy.numel() * 4, sh)
+            rc, nbh = G.sz3g_compress_host(p, hx.data_ptr(), hs.data_ptr(), hs.numel(), hst)
+            rc2 = G.sz3g_decompress_host(hs.data_ptr(), nbh, hy.data_ptr(), hy.numel() * 4, hst)
             if rc or rc2:
                 raise RuntimeError(f"host status {rc} {rc2}")
         torch.cuda.synchronize()
