@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the REL 1e-2 / 1e-4 timings of the field")
     ap.add_argument("--workload", default="field", choices=["field", "batch", "selector", "lossless", "pastri"])
     ap.add_argument("--train-fields", type=int, default=400)
     ap.add_argument("--fields", type=int, default=256)
@@ -897,6 +898,35 @@ def main():
         dt = (time.perf_counter() - t0) / ke
         e2e = {"value": ws * in_bytes / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": in_bytes + nbh,
                "d2h_bytes_per_step": nbh + in_bytes, "ms_per_step": dt * 1e3}
+    # the other bounds of the 512^3 configuration, outside the timed region
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = {}
+        for eb in (1e-2, 1e-4):
+            pe = G.make_params(x.shape, eb, eb_mode=G.REL, interp=G.CUBIC)
+            wse, wde = G.workspace(pe, False, dev), G.workspace(pe, True, dev)
+            oute = torch.empty(G.sz3g_compress_bound(pe), dtype=torch.uint8, device=dev)
+            nbe = [0]
+
+            def comp_e():
+                rc, nbe[0] = G.sz3g_compress(pe, xd.data_ptr(), oute.data_ptr(), oute.numel(), wse.data_ptr(),
+                                             wse.numel(), sh)
+                assert rc == 0
+
+            def dec_e():
+                rc = G.sz3g_decompress(oute.data_ptr(), nbe[0], y.data_ptr(), y.numel() * 4, wde.data_ptr(),
+                                       wde.numel(), sh)
+                assert rc == 0
+
+            for _ in range(3):
+                comp_e()
+                dec_e()
+            tc, td = _median_ms(comp_e, 20), _median_ms(dec_e, 20)
+            err = float((y - xd.reshape(-1)).abs().max())
+            sweep[f"rel{eb:g}"] = {"compress_ms": tc, "decompress_ms": td,
+                                   "GB/s": in_bytes / ((tc + td) * 1e-3) / 1e9,  # per compress + decompress step
+                                   "compression_ratio": in_bytes / nbe[0], "max_abs_error": err}
+            del wse, wde, oute
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(x)
@@ -911,7 +941,7 @@ def main():
                            "frac_of_hbm_algorithmic": (in_bytes + nb) / (dec_ms * 1e-3) / 1e9 / peak},
             "compression_ratio": in_bytes / nb, "max_abs_error": maxerr, "stream_bytes": nb,
             "roofline": roof, "kernels_ms_per_step": {k: v[0] for k, v in sorted(kern.items())},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "eb_sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
