@@ -46,10 +46,12 @@ struct Layout {
 };
 
 struct CompressWs {
-  size_t st, hist, table, range, cb, enc, codes, x1, R[34], total;
+  size_t st, hist, table, range, cb, enc, codes, x1, R[34], rounds, total;
 };
 
-CompressWs compress_layout(const Plan& pl) {
+// rounds: room for the codebook's parallel length-limit rounds at the end
+// (the single-field forms; a batch's per-field workspaces leave it out).
+CompressWs compress_layout(const Plan& pl, bool rounds = true) {
   CompressWs w{};
   Layout l;
   w.st = l.take(sizeof(DevState));
@@ -62,6 +64,9 @@ CompressWs compress_layout(const Plan& pl) {
   w.x1 = l.take(xpyr_bytes(pl));
   // the fused level path never stores the finest grid's reconstruction
   for (int k = level_path_ok(pl) ? 1 : 0; k <= pl.L; ++k) w.R[k] = l.take(pl.gsize[k] * pl.esz);
+  const unsigned long long max_sym = pl.N < 2ull * pl.radius ? pl.N : 2ull * pl.radius;
+  const size_t rb = rounds ? codebook_rounds_bytes(max_sym) : 0;
+  w.rounds = rb ? l.take(rb) : 0;
   w.total = l.off;
   return w;
 }
@@ -261,7 +266,7 @@ int parse_header(const unsigned char* s, size_t bytes, Header* h) {
 
 }  // namespace
 
-size_t compress_ws_bytes(const Plan& pl) { return compress_layout(pl).total; }
+size_t compress_ws_bytes(const Plan& pl) { return compress_layout(pl, false).total; }
 size_t decompress_ws_bytes(const Plan& pl) { return decompress_layout(pl).total; }
 int stream_status(uint32_t flags) { return status_of(flags); }
 int parse_stream_header(const unsigned char* hb, size_t bytes, Header* h) { return parse_header(hb, bytes, h); }
@@ -287,14 +292,14 @@ int compress_enqueue_pre(const sz3g_params* p, const Plan& pl, const void* d_in,
 }
 
 int compress_enqueue_post(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
-                          unsigned char* ws, cudaStream_t s) {
-  const CompressWs L = compress_layout(pl);
+                          unsigned char* ws, cudaStream_t s, bool rounds) {
+  const CompressWs L = compress_layout(pl, rounds);
   DevState* st = (DevState*)(ws + L.st);
   uint16_t* codes = (uint16_t*)(ws + L.codes);
   uint32_t* hist = (uint32_t*)(ws + L.hist);
   uint32_t* table = (uint32_t*)(ws + L.table);
   SZ3G_TRY(launch_codebook(hist, 2 * pl.radius, table, nullptr, nullptr, st, ws + L.cb, (unsigned char*)d_out,
-                           out_capacity, pl.esz, s));
+                           out_capacity, pl.esz, s, L.rounds ? ws + L.rounds : nullptr));
   PassMap map;  // kernel parameter, copied at launch
   make_pass_map(pl, &map);
   SZ3G_TRY(launch_encode(pl, codes, table, d_in, &map, ws + L.enc, st, (unsigned char*)d_out, out_capacity,
@@ -305,9 +310,9 @@ int compress_enqueue_post(const sz3g_params* p, const Plan& pl, const void* d_in
 
 // The compress pipeline on s, without synchronising.
 int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
-                     unsigned char* ws, cudaStream_t s, DevState** st_out) {
+                     unsigned char* ws, cudaStream_t s, DevState** st_out, bool rounds) {
   SZ3G_TRY(compress_enqueue_pre(p, pl, d_in, ws, s, st_out, nullptr, 0));
-  return compress_enqueue_post(p, pl, d_in, d_out, out_capacity, ws, s);
+  return compress_enqueue_post(p, pl, d_in, d_out, out_capacity, ws, s, rounds);
 }
 
 // The decompress pipeline of a parsed stream on s, without synchronising.
@@ -604,10 +609,12 @@ int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t ou
     key_add(key, ws_bytes);
     SZ3G_TRY(run_cached(
         key, s,
-        [&](cudaStream_t es, DevState** sto) { return compress_enqueue(p, pl, d_in, d_out, out_capacity, ws, es, sto); },
+        [&](cudaStream_t es, DevState** sto) {
+          return compress_enqueue(p, pl, d_in, d_out, out_capacity, ws, es, sto, true);
+        },
         &st));
   } else {
-    SZ3G_TRY(compress_enqueue(p, pl, d_in, d_out, out_capacity, ws, s, &st));
+    SZ3G_TRY(compress_enqueue(p, pl, d_in, d_out, out_capacity, ws, s, &st, true));
   }
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
@@ -832,7 +839,7 @@ int sz3g_compress_async(const sz3g_params* p, const void* d_in, void* d_out, siz
   if (ws_bytes < L.total) return SZ3G_E_CAPACITY;
   cudaStream_t s = (cudaStream_t)stream;
   DevState* st = nullptr;
-  SZ3G_TRY(compress_enqueue(p, pl, d_in, d_out, out_capacity, (unsigned char*)d_workspace, s, &st));
+  SZ3G_TRY(compress_enqueue(p, pl, d_in, d_out, out_capacity, (unsigned char*)d_workspace, s, &st, true));
   return launch_report(st, d_out_bytes, d_status, s);
 }
 
@@ -997,12 +1004,14 @@ int sz3g_huffman_build(const uint32_t* d_hist, uint32_t nsym, uint8_t* d_len, ui
   cudaStream_t s = (cudaStream_t)stream;
   Layout l;
   const size_t o_st = l.take(sizeof(DevState)), o_tab = l.take(kSyms * 4), o_cb = l.take(codebook_scratch_bytes());
+  const size_t rb = codebook_rounds_bytes(nsym), o_rounds = rb ? l.take(rb) : 0;
   Scratch own;
   unsigned char* ws;
   SZ3G_TRY(get_ws(nullptr, 0, l.off, s, own, &ws));
   DevState* st = (DevState*)(ws + o_st);
   SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
-  SZ3G_TRY(launch_codebook(d_hist, nsym, (uint32_t*)(ws + o_tab), d_len, d_code, st, ws + o_cb, nullptr, 0, 4, s));
+  SZ3G_TRY(launch_codebook(d_hist, nsym, (uint32_t*)(ws + o_tab), d_len, d_code, st, ws + o_cb, nullptr, 0, 4, s,
+                           rb ? ws + o_rounds : nullptr));
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
   return status_of(h.flags);

@@ -334,23 +334,28 @@ size_t compress_ws_bytes(const Plan& pl);
 size_t decompress_ws_bytes(const Plan& pl);
 int stream_status(uint32_t flags);
 int parse_stream_header(const unsigned char* hb, size_t bytes, Header* h);
+// rounds: the workspace holds the codebook's parallel-rounds scratch
+// (compress_layout(pl, true)); the batch's workspaces do not
 int compress_enqueue(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
-                     unsigned char* ws, cudaStream_t s, DevState** st);
+                     unsigned char* ws, cudaStream_t s, DevState** st, bool rounds = false);
 // compress_enqueue in two parts: up to the levels (collected into lq when
 // given), then the encoder.
 int compress_enqueue_pre(const sz3g_params* p, const Plan& pl, const void* d_in, unsigned char* ws, cudaStream_t s,
                          DevState** st, LevelQueue* lq, int field);
 int compress_enqueue_post(const sz3g_params* p, const Plan& pl, const void* d_in, void* d_out, size_t out_capacity,
-                          unsigned char* ws, cudaStream_t s);
+                          unsigned char* ws, cudaStream_t s, bool rounds = false);
 // with lq: everything but the levels collected into lq
 int decompress_enqueue(const Header& h, const void* d_stream, void* d_out, unsigned char* ws, cudaStream_t s,
                        DevState** st, LevelQueue* lq = nullptr, int field = 0);
 
 // k_huffman.cu
 size_t codebook_scratch_bytes();
+// rounds: scratch of the parallel length-limit rounds (codebook_rounds_bytes),
+// or null for the rounds one after another
 int launch_codebook(const uint32_t* hist, uint32_t nsym, uint32_t* table, uint8_t* len_out,
                     uint32_t* code_out, DevState* st, void* scratch, unsigned char* d_out,
-                    unsigned long long out_capacity, int esz, cudaStream_t s);
+                    unsigned long long out_capacity, int esz, cudaStream_t s, void* rounds = nullptr);
+size_t codebook_rounds_bytes(unsigned long long max_symbols);  // 0: never needed
 int launch_finalize(const Plan& pl, const sz3g_params* p, DevState* st, unsigned char* d_out,
                     unsigned long long out_capacity, cudaStream_t s);
 

@@ -367,6 +367,60 @@ __device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* 
   return srt;
 }
 
+// Alphabets up to kSpecMax symbols run their first kSpecRounds length-limit
+// rounds at once inside the codebook kernel (speculative_lengths below).
+constexpr int kSpecMax = 512, kSpecRounds = 4;
+
+// Length-limit rounds of larger alphabets on separate CTAs.  Round r of the
+// limit uses the weights max(1, f >> r) and does not depend on round r - 1,
+// so codebook_rounds_kernel computes rounds 0 .. kCbRounds-1 at once, CTA r
+// on its own scratch, and records which fit SZ3G_LMAX and their lengths; the
+// codebook kernel takes the first that fits -- the round at which the
+// sequential halving would have stopped -- and continues sequentially from
+// round kCbRounds only when none does.
+constexpr int kCbRounds = 8;
+struct CbRound {
+  unsigned long long keys[kSyms];
+  unsigned long long keys2[kSyms];
+  uint32_t nf[kSyms + 16];
+  uint32_t parent[2 * kSyms];
+  uint8_t lenpos[kSyms];  // code length by position in symbol order
+};
+struct CbRounds {
+  int fits[kCbRounds];
+  int pad[8];
+  CbRound r[kCbRounds];
+};
+
+size_t codebook_rounds_bytes(unsigned long long max_symbols) {
+  return max_symbols > (unsigned long long)kSpecMax ? sizeof(CbRounds) : 0;
+}
+
+// One round of code_lengths (no halving loop): sorts `cur` by (weight,
+// position), builds the tree, and returns whether some code is longer than
+// SZ3G_LMAX; *srt_out gets the sorted keys and nf[i] the length of srt[i].
+template <typename PT>
+__device__ bool one_round_lengths(unsigned long long* cur, unsigned long long* other, uint32_t* nf, PT* parent,
+                                  int K, uint32_t* lw_s, uint32_t* w_s, unsigned long long** srt_out) {
+  const int tid = threadIdx.x;
+  unsigned long long* srt;
+  if (K <= kRankSortMax) {
+    block_rank_sort(cur, other, K);
+    srt = other;
+  } else {
+    srt = block_radix_sort_w(cur, other, K);
+  }
+  __syncthreads();
+  unsigned long long* spare = srt == cur ? other : cur;
+  uint32_t* lw = lw_s ? lw_s : reinterpret_cast<uint32_t*>(spare);
+  uint32_t* W = w_s ? w_s : nf;
+  for (int i = tid; i < K; i += kCbThreads) lw[i] = (uint32_t)(srt[i] >> 16);
+  __syncthreads();
+  batched_merge<kCbThreads>(lw, K, W, parent);
+  *srt_out = srt;
+  return leaf_depths(parent, K, nf);
+}
+
 // Speculative halving rounds for small alphabets.  Round i of the length
 // limit uses the weights max(1, f >> i) (halving max(1, f >> 1) i times), so
 // rounds 0..3 are independent: each is sorted (block-wide), the four merges
@@ -377,7 +431,6 @@ __device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* 
 // chosen round's leaves sorted by (weight, symbol) are left in ka and their
 // lengths in nf; otherwise ka holds the weights of round 4 for the
 // sequential rounds.  Round scratch lives in [region, region + 4 * kSpecRound).
-constexpr int kSpecMax = 512, kSpecRounds = 4;
 constexpr int kSpecSerialMax = 128;  // smaller alphabets: each round's merge on one thread
 constexpr int kSpecRound = 2 * kSpecMax * 8 + (kSpecMax + 4) * 4 * 2 + 2 * kSpecMax * 2;
 __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsigned char* region, int K) {
@@ -456,7 +509,8 @@ __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsign
 __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __restrict__ hist, uint32_t nsym,
                                                               uint32_t* table, uint8_t* len_out, uint32_t* code_out,
                                                               DevState* st, CbGlobal* g, unsigned char* d_out,
-                                                              unsigned long long out_capacity, int esz) {
+                                                              unsigned long long out_capacity, int esz,
+                                                              const CbRounds* R) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_warp[32];
   __shared__ uint32_t s_cnt[SZ3G_LMAX + 2], s_start[SZ3G_LMAX + 2], s_fc[SZ3G_LMAX + 2];
@@ -521,7 +575,23 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   // 2. lengths (shared-memory arrays are addressed through pointers derived
   //    from the shared array itself in their own branch)
   unsigned long long* srt;
-  if (in_smem) {
+  // the first of the parallel rounds that fits, if they ran (larger alphabets)
+  int pick = -1;
+  if (R && K > kSpecMax)
+    for (int r = 0; r < kCbRounds && pick < 0; ++r)
+      if (R->fits[r]) pick = r;
+  if (R && K > kSpecMax && pick < 0) {
+    // none of them fits: continue the halving from round kCbRounds
+    for (int i = tid; i < K; i += kCbThreads) {
+      const unsigned long long k = ka[i];
+      const uint32_t f = (uint32_t)(k >> 16) >> kCbRounds;
+      ka[i] = ((unsigned long long)(f ? f : 1u) << 16) | (k & 0xffffu);
+    }
+    __syncthreads();
+  }
+  if (pick >= 0) {
+    srt = nullptr;
+  } else if (in_smem) {
     // the rounds' scratch spans the second key array and the nf / parent
     // areas, all free until the lengths are known
     static_assert(kSpecRounds * kSpecRound <= kCbOffSym - kSmemLeaves * 8, "speculative rounds fit");
@@ -545,9 +615,17 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   __syncthreads();
   for (int i0 = 0; i0 < K; i0 += kCbThreads) {
     const int i = i0 + tid;
-    const uint32_t L = i < K ? nf[i] : 0u;
+    uint32_t L = 0;
+    if (i < K) {
+      if (pick >= 0) {
+        L = R->r[pick].lenpos[i];
+        lenpos[i] = (uint8_t)L;
+      } else {
+        L = nf[i];
+        lenpos[(uint32_t)(srt[i] & 0xffffu)] = (uint8_t)L;
+      }
+    }
     warp_count(s_cnt, L, i < K);
-    if (i < K) lenpos[(uint32_t)(srt[i] & 0xffffu)] = (uint8_t)L;
   }
   __syncthreads();
   if (tid == 0) {
@@ -588,15 +666,85 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   }
 }
 
+__global__ void __launch_bounds__(kCbThreads) codebook_rounds_kernel(const uint32_t* __restrict__ hist,
+                                                                     uint32_t nsym, CbRounds* R) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_warp[32];
+  __shared__ uint32_t s_seg[2048];  // used symbols of each 32-bin segment, then their first position
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, r = blockIdx.x;
+  // used symbols in symbol order, as in the codebook kernel: warp w reads
+  // bins 1024 k + 32 w + lane (coalesced), a ballot marks each segment's
+  // used bins; lane l keeps the masks of its warp's segments l and l + 32
+  uint32_t mk0 = 0, mk1 = 0;
+#pragma unroll 8
+  for (int k = 0; k < 64; ++k) {
+    const int sy = 1024 * k + 32 * warp + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, sy < (int)nsym && __ldcg(hist + sy) != 0);
+    if (lane == (k & 31)) {
+      if (k < 32) mk0 = m;
+      else mk1 = m;
+    }
+    if (lane == 0) s_seg[32 * k + warp] = (uint32_t)__popc(m);
+  }
+  __syncthreads();
+  const uint32_t c0 = s_seg[2 * tid], c1 = s_seg[2 * tid + 1];
+  unsigned long long tot;
+  const uint32_t off = (uint32_t)block_exclusive_scan((unsigned long long)(c0 + c1), s_warp, &tot);
+  s_seg[2 * tid] = off;
+  s_seg[2 * tid + 1] = off + c0;
+  const int K = (int)tot;
+  if (K <= kSpecMax) {  // small alphabets: the codebook kernel's own speculative rounds
+    if (tid == 0) R->fits[r] = 0;
+    return;
+  }
+  CbRound& g = R->r[r];
+  const bool in_smem = K <= kSmemLeaves;
+  unsigned long long* ka = in_smem ? (unsigned long long*)smem : g.keys;
+  unsigned long long* kb = in_smem ? (unsigned long long*)(smem + kSmemLeaves * 8) : g.keys2;
+  __syncthreads();
+  for (int k = 0; k < 64; ++k) {
+    const unsigned m = __shfl_sync(0xffffffffu, k < 32 ? mk0 : mk1, k & 31);
+    if ((m >> lane) & 1u) {
+      const int sy = 1024 * k + 32 * warp + lane;
+      const uint32_t pos = s_seg[32 * k + warp] + (uint32_t)__popc(m & ((1u << lane) - 1u));
+      const uint32_t f = __ldcg(hist + sy) >> r;
+      ka[pos] = ((unsigned long long)(f ? f : 1u) << 16) | pos;
+    }
+  }
+  __syncthreads();
+  unsigned long long* srt = nullptr;
+  bool deep;
+  uint32_t* nf;
+  if (in_smem) {
+    nf = (uint32_t*)(smem + kCbOffNf);
+    deep = one_round_lengths(ka, kb, nf, (uint16_t*)(smem + kCbOffPar), K, (uint32_t*)nullptr, (uint32_t*)nullptr,
+                             &srt);
+  } else {
+    nf = g.nf;
+    uint32_t* lw_s = K <= kCbSmemWeights ? (uint32_t*)smem : nullptr;
+    deep = one_round_lengths(ka, kb, nf, g.parent, K, lw_s, lw_s ? lw_s + K : nullptr, &srt);
+  }
+  if (!deep)
+    for (int i = tid; i < K; i += kCbThreads) g.lenpos[(uint32_t)(srt[i] & 0xffffu)] = (uint8_t)nf[i];
+  if (tid == 0) R->fits[r] = deep ? 0 : 1;
+}
+
 int launch_codebook(const uint32_t* hist, uint32_t nsym, uint32_t* table, uint8_t* len_out, uint32_t* code_out,
                     DevState* st, void* scratch, unsigned char* d_out, unsigned long long out_capacity, int esz,
-                    cudaStream_t s) {
+                    cudaStream_t s, void* rounds) {
   auto kern = codebook_kernel;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) != cudaSuccess)
     return SZ3G_E_CUDA;
+  if (rounds) {
+    if (cudaFuncSetAttribute(codebook_rounds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) !=
+        cudaSuccess)
+      return SZ3G_E_CUDA;
+    SZ3G_LAUNCH(kKCodebook, s,
+                codebook_rounds_kernel<<<kCbRounds, kCbThreads, kCbSmem, s>>>(hist, nsym, (CbRounds*)rounds));
+  }
   SZ3G_LAUNCH(kKCodebook, s,
               kern<<<1, kCbThreads, kCbSmem, s>>>(hist, nsym, table, len_out, code_out, st, (CbGlobal*)scratch, d_out,
-                                                  out_capacity, esz));
+                                                  out_capacity, esz, (const CbRounds*)rounds));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 

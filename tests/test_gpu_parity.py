@@ -213,7 +213,7 @@ def test_length_limit_rounds_match_oracle(nfib):
     assert np.array_equal(gcode.cpu().numpy().view(np.uint32), O.canonical_codes(ln))
 
 
-@pytest.mark.parametrize("k", [2, 3, 511, 512, 513, 900])
+@pytest.mark.parametrize("k", [2, 3, 511, 512, 513, 900, 3000, 12000, 40000])
 def test_codebook_alphabet_sizes_match_oracle(k):
     # steeply falling weights over k symbols (deep trees, several rounds)
     rng = np.random.default_rng(k)
