@@ -317,6 +317,20 @@ def _grf512():
     return _GRF512["x"]
 
 
+@pytest.mark.parametrize("eb", [1e-4, 1e-5, 1e-6])
+def test_large_alphabets_whole_stream(eb):
+    # thousands to all 65536 codes used: the codebook's parallel length-limit
+    # rounds (shared-memory and global-scratch forms) inside the pipeline
+    x = S.grf((128, 128, 128), 6).astype(np.float32)
+    op, gp = both_params(x.shape, eb, eb_mode=O.REL, interp=O.CUBIC)
+    rc, s = gpu_compress(gp, x)
+    assert rc == G.OK
+    assert s == O.compress(op, x)
+    rc, y = gpu_decompress(s, x.size, O.F32)
+    assert rc == G.OK
+    assert np.array_equal(y.view(np.uint32), O.decompress(s).reshape(-1).view(np.uint32))
+
+
 @pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
 def test_full_512cube_rel_cubic(eb):
     x = _grf512()
