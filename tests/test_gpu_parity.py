@@ -213,6 +213,26 @@ def test_length_limit_rounds_match_oracle(nfib):
     assert np.array_equal(gcode.cpu().numpy().view(np.uint32), O.canonical_codes(ln))
 
 
+def test_codebook_rounds_beyond_the_parallel_ones():
+    # 500 heavy symbols above an 18-long Fibonacci chain scaled by 256: 518
+    # used symbols whose code fits 24 bits only at halving round 9 -- past the
+    # eight rounds computed at once, so the sequential rounds finish it
+    fib = [1, 1]
+    while len(fib) < 18:
+        fib.append(fib[-1] + fib[-2])
+    hist = np.zeros(65536, np.uint64)
+    hist[3000:3018] = [f * 256 for f in fib]
+    hist[20000:20500] = 2_900_000
+    assert int(hist.sum()) < 2 ** 31
+    ln = O.huffman_lengths(hist)
+    hd = dev(hist.astype(np.uint32).view(np.int32))
+    glen = torch.empty(65536, dtype=torch.uint8, device=DEV)
+    gcode = torch.empty(65536, dtype=torch.int32, device=DEV)
+    assert G.sz3g_huffman_build(hd.data_ptr(), 65536, glen.data_ptr(), gcode.data_ptr(), G._stream_handle()) == G.OK
+    assert np.array_equal(glen.cpu().numpy(), ln)
+    assert np.array_equal(gcode.cpu().numpy().view(np.uint32), O.canonical_codes(ln))
+
+
 @pytest.mark.parametrize("k", [2, 3, 511, 512, 513, 900, 3000, 12000, 40000])
 def test_codebook_alphabet_sizes_match_oracle(k):
     # steeply falling weights over k symbols (deep trees, several rounds)
