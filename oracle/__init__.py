@@ -3,9 +3,12 @@
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library never does.
 
-The arithmetic lives in ``sz3o.c`` / ``sz3o_typed.inc`` (plain C, serial,
-compiled with ``-O2 -ffp-contract=off -fno-fast-math``); this module only
-builds that library and marshals numpy arrays into it.  What each C function
+The arithmetic lives in ``sz3o.c`` / ``sz3o_typed.inc`` (the hot path),
+``szlz.c`` (the lossless stage after the Huffman coder) and ``szpastri.c``
+(the SZ3-Pastri modules: unpred-aware quantizer, fixed Huffman code) -- plain
+C, serial, compiled with ``-O2 -ffp-contract=off -fno-fast-math``; this
+module only builds that library and marshals numpy arrays into it (``mlp.py``
+is the selector network's numpy reference).  What each C function
 computes, and the passage of the SZ3 paper (arXiv 2111.02925) it follows, is
 documented in ``sz3o.h``.
 
