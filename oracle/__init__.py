@@ -126,6 +126,10 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = C.c_int
+        L.sz3o_splitmix64.argtypes = [C.c_uint64]
+        L.sz3o_splitmix64.restype = C.c_uint64
+        L.sz3o_select_blocks.argtypes = [P, C.c_uint32, C.c_uint32, C.c_uint64, u64p, u64p]
+        L.sz3o_select_blocks.restype = C.c_uint32
         L.sz3o_lz_bound.argtypes = [C.c_uint64]
         L.sz3o_lz_bound.restype = C.c_uint64
         L.sz3o_bitplane_bound.argtypes = [C.c_uint64]
@@ -366,6 +370,22 @@ def select_features(p: Params, x: np.ndarray, level: int, nblocks: int = 0, seed
     out = np.zeros(SEL_FEATURES, np.float64)
     _check(lib().sz3o_select_features(C.byref(p), _ptr(x), level, nblocks, seed, _ptr(out)), "select_features")
     return out
+
+
+def splitmix64(key: int) -> int:
+    """The SplitMix64 output function of the sample-block placement."""
+    return int(lib().sz3o_splitmix64(key & 0xFFFFFFFFFFFFFFFF))
+
+
+def select_blocks(p: Params, level: int, nblocks: int, seed: int):
+    """(lo, hi): int arrays [n, ndim] of the sample blocks of `level`."""
+    nd = int(p.ndim)
+    lo = np.zeros(4 * 1024, np.uint64)
+    hi = np.zeros(4 * 1024, np.uint64)
+    n = int(lib().sz3o_select_blocks(C.byref(p), level, nblocks, seed & 0xFFFFFFFFFFFFFFFF,
+                                     lo.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                     hi.ctypes.data_as(C.POINTER(C.c_uint64))))
+    return (lo.reshape(1024, 4)[:n, :nd].astype(np.int64), hi.reshape(1024, 4)[:n, :nd].astype(np.int64))
 
 
 def select_levels(p: Params, x: np.ndarray, nblocks: int = 0, seed: int = 0):

@@ -961,6 +961,27 @@ int sz3o_select_costs(const sz3o_params* p, const void* x, uint32_t level, uint3
                               : select_costs_f64(p, &g, (const double*)x, level, nblocks, seed, cost);
 }
 
+uint64_t sz3o_splitmix64(uint64_t key) { return splitmix64(key); }
+
+uint32_t sz3o_select_blocks(const sz3o_params* p, uint32_t level, uint32_t nblocks, uint64_t seed, uint64_t* lo,
+                            uint64_t* hi) {
+  walk_geom g;
+  sel_blocks* blk;
+  uint32_t b, d, n;
+  if (geom_of(p, &g) != SZ3O_OK || level < 1 || level > g.L) return 0;
+  blk = (sel_blocks*)malloc(sizeof(sel_blocks));
+  if (!blk) return 0;
+  sel_make_blocks(&g, level, nblocks, seed, blk);
+  for (b = 0; b < blk->n; ++b)
+    for (d = 0; d < g.ndim; ++d) {
+      lo[4 * b + d] = blk->lo[b][d];
+      hi[4 * b + d] = blk->hi[b][d];
+    }
+  n = blk->n;
+  free(blk);
+  return n;
+}
+
 int sz3o_select_features(const sz3o_params* p, const void* x, uint32_t level, uint32_t nblocks, uint64_t seed,
                          double* feat) {
   walk_geom g;

@@ -145,6 +145,14 @@ int sz3o_select_costs(const sz3o_params* p, const void* x, uint32_t level, uint3
                       double* cost);
 int sz3o_select_features(const sz3o_params* p, const void* x, uint32_t level, uint32_t nblocks, uint64_t seed,
                          double* feat);
+/* The SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014): the
+ * first output of the generator whose state is `key`. */
+uint64_t sz3o_splitmix64(uint64_t key);
+/* The sample blocks of level `level`: block b covers grid coordinates
+ * [lo[4b+d], hi[4b+d]) of G_{level-1} on axis d (d < ndim).  nblocks is
+ * capped at 1024; returns the number of blocks written. */
+uint32_t sz3o_select_blocks(const sz3o_params* p, uint32_t level, uint32_t nblocks, uint64_t seed, uint64_t* lo,
+                            uint64_t* hi);
 
 /* Optional lossless stage after the Huffman coder (szlz.c): byte-level LZ77
  * of our own definition over independent blocks of SZLZ_BLOCK bytes.

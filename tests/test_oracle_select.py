@@ -1,5 +1,9 @@
 """Oracle: the per-level selection estimate, its features and the network's
 reference, pinned independently of the oracle's own C code."""
+import json
+import math
+import os
+
 import numpy as np
 
 import oracle as O
@@ -8,9 +12,11 @@ from paper_2111_02925_gb300 import synthetic as S
 
 
 def _brute_costs(x, eb_rel, level):
-    """Independent restatement on a small field: every point of the level,
-    the pass axis by its odd coordinates, the predictor and quantizer written
-    out with numpy float32 scalars, Shannon bits of the code histogram."""
+    """A second transcription of the cost estimate (numpy float32 scalars,
+    pure-Python loops).  It guards the C code against transcription slips but
+    pins nothing of the reading itself: the pins of the estimate are the
+    behavioural tests below (constant field, one-axis field, blocks covering
+    the grid) and the closed-form feature and block tests."""
     x = np.asarray(x, np.float32)
     nd = x.ndim
     n = x.shape
@@ -124,3 +130,114 @@ def test_network_gradient_matches_finite_differences():
         num = (M.loss_and_grad(w + e, feat, mask, label)[0] - M.loss_and_grad(w - e, feat, mask, label)[0]) / 2e-6
         assert abs(num - g[k]) <= 1e-6 * max(1.0, abs(num))
     assert np.all(g[:M.OFF_W1] == 0.0)
+
+
+_GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_splitmix64_matches_published_outputs():
+    """The block placement hashes with SplitMix64; its first outputs from
+    state 1234567 are the published reference values."""
+    g = json.load(open(os.path.join(_GOLDEN, "splitmix64_1234567.json")))
+    gamma = int(g["gamma"], 16)
+    for i, want in enumerate(g["outputs"]):
+        assert O.splitmix64((g["seed"] + i * gamma) % (1 << 64)) == int(want)
+
+
+def test_sample_blocks_hand_worked():
+    g = json.load(open(os.path.join(_GOLDEN, "select_blocks.json")))
+    for c in g["cases"]:
+        p = O.make_params(tuple(c["dims"]), 1e-3)
+        lo, hi = O.select_blocks(p, c["level"], c["nblocks"], int(c["seed"]))
+        assert lo.shape == (c["nblocks"], 3)
+        b, d = c["block"], c["axis"]
+        assert c["modulus"] == c["m"] - c["span"] + 1
+        assert lo[b, d] == c["start"] and hi[b, d] - lo[b, d] == c["span"]
+        # every block lies in the grid of the level and spans min(16, m) points
+        s = 1 << (c["level"] - 1)
+        m = [(n + s - 1) // s for n in c["dims"]]
+        for e in range(3):
+            assert np.all(lo[:, e] >= 0) and np.all(hi[:, e] <= m[e])
+            assert np.all(hi[:, e] - lo[:, e] == min(16, m[e]))
+
+
+def _quartic(shape, axis):
+    """x = i_axis^4 (exact small integers in float32)."""
+    i = np.arange(shape[axis], dtype=np.float64) ** 4
+    sh = [1, 1, 1]
+    sh[axis] = shape[axis]
+    return np.broadcast_to(i.reshape(sh), shape).astype(np.float32).copy()
+
+
+def test_features_closed_forms_on_a_quartic():
+    """x = i^4 along one axis of 20 points, constant along the others, ABS
+    eb = 1.  At stride s = 1, for odd i with a +1 neighbour (i = 1..17):
+    linear error |((i-1)^4 + (i+1)^4)/2 - i^4| = 6 i^2 + 1 (mean 5823/9 =
+    647); cubic error |(9((i-1)^4 + (i+1)^4) - ((i-3)^4 + (i+3)^4))/16 - i^4|
+    = 9 where i >= 3 and i + 3 < 20, the linear error elsewhere (mean
+    (63 + 7 + 1735)/9).  The level's points whose pass axis (order (0,1,2))
+    is the quartic one: linear error above 64 at i = 5..17 and at i = 19
+    (extrapolation 1.5 x(18) - 0.5 x(16): error 5625), cubic above 64 only
+    at i = 17 ((6 x(16) + 3 x(18) - x(14))/8: error 195) and i = 19."""
+    others = (6, 8)
+    for a in range(3):
+        shape = list(others)
+        shape.insert(a, 20)
+        shape = tuple(shape)
+        x = _quartic(shape, a)
+        p = O.make_params(shape, 1.0)  # ABS eb = 1 (exact in float32)
+        f = O.select_features(p, x, 1)
+        for d in range(3):
+            if d == a:
+                assert f[3 * d] == math.log2(1.0 + 647.0)
+                assert abs(f[3 * d + 1] - math.log2(1.0 + 1805.0 / 9.0)) < 1e-12
+            else:
+                assert f[3 * d] == 0.0 and f[3 * d + 1] == 0.0
+        assert f[9] == 1.0 / 5 and f[10] == 0.0          # l / L with L = ceil(log2 20) = 5; l - 1
+        assert abs(f[11] - math.log10(1.0 / 130321.0)) < 1e-12  # range 19^4
+        # +1 differences all within eb: only where i = 0 on the quartic axis
+        assert abs(f[12] - 1.0 / 19.0) < 1e-15
+        # points whose pass axis is a: odd on a, any on earlier axes, even on later ones
+        m = list(shape)
+        n_pass_a = 10 * int(np.prod([m[b] for b in range(a)])) * int(np.prod([(m[b] + 1) // 2 for b in range(a + 1, 3)]))
+        n_lvl = int(np.prod(m)) - int(np.prod([(e + 1) // 2 for e in m]))
+        assert abs(f[13] - (8 / 10) * n_pass_a / n_lvl) < 1e-15
+        assert abs(f[14] - (2 / 10) * n_pass_a / n_lvl) < 1e-15
+        assert abs(f[15] - math.log2(shape[2] / shape[0])) < 1e-15
+
+
+def test_features_closed_forms_at_stride_two():
+    """Level 2 (stride 2) of the quartic along axis 0: the grid values are
+    16 g^4 (g = 0..9), so the errors are 16 times those of g^4 on a 10-point
+    axis: odd g with g + 1 < 10 (1, 3, 5, 7): linear 16 (6 g^2 + 1), mean
+    16 * 508 / 4 = 2032; cubic 16 * 9 at g = 3, 5, the linear error at
+    g = 1, 7: mean (112 + 144 + 144 + 4720) / 4 = 1280."""
+    shape = (20, 6, 8)
+    x = _quartic(shape, 0)
+    p = O.make_params(shape, 1.0)
+    f = O.select_features(p, x, 2)
+    assert f[0] == math.log2(1.0 + 2032.0)
+    assert f[1] == math.log2(1.0 + 1280.0)
+    assert f[3] == f[4] == f[6] == f[7] == 0.0
+    assert f[9] == 2.0 / 5 and f[10] == 1.0
+    assert abs(f[15] - math.log2(4 / 10)) < 1e-15
+
+
+def test_lag_ratio_on_ramps_along_each_axis():
+    """A ramp along axis d: lag-2 differences are twice the lag-1 ones, so
+    log2 of the ratio of their mean squares is 2; the other axes are flat
+    (ratio of zeros, 0 by the regularised form)."""
+    for a in range(3):
+        shape = [10, 12, 14]
+        i = np.arange(shape[a], dtype=np.float64) * 0.5
+        sh = [1, 1, 1]
+        sh[a] = shape[a]
+        x = np.broadcast_to(i.reshape(sh), shape).astype(np.float32).copy()
+        p = O.make_params(tuple(shape), 1e-3)
+        f = O.select_features(p, x, 1)
+        for d in range(3):
+            if d == a:
+                assert abs(f[3 * d + 2] - 2.0) < 1e-6
+                assert f[3 * d] < 1e-9  # linear prediction exact on a ramp
+            else:
+                assert f[3 * d + 2] == 0.0 and f[3 * d] == 0.0
