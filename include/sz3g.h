@@ -117,12 +117,6 @@ int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t ou
                   size_t* out_bytes, void* d_workspace, size_t ws_bytes, void* stream);
 
 /*
- * Parse and validate a stream header.  `stream` is a host pointer
- * (stream_on_device = 0) or a device pointer (1: the 288 header bytes are
- * copied to the host with a synchronous cudaMemcpy).  Fills *p and the point
- * count.  Errors: SZ3G_E_CORRUPT, SZ3G_E_INVAL (NULL pointers), SZ3G_E_CUDA.
- */
-/*
  * Graph cache (on by default): sz3g_compress / sz3g_decompress calls given a
  * caller-owned workspace replay, as one CUDA graph launch, the pipeline
  * captured by an earlier call with the same parameters (stream header) and
@@ -192,6 +186,12 @@ int sz3g_bitplane_decode(const void* d_stream, size_t bytes, void* d_out, size_t
                          void* stream);
 int sz3g_huffman_fixed(uint32_t radius, uint8_t* d_len, uint32_t* d_code, void* stream);
 
+/*
+ * Parse and validate a stream header.  `stream` is a host pointer
+ * (stream_on_device = 0) or a device pointer (1: the 288 header bytes are
+ * copied to the host with a synchronous cudaMemcpy).  Fills *p and the point
+ * count.  Errors: SZ3G_E_CORRUPT, SZ3G_E_INVAL (NULL pointers), SZ3G_E_CUDA.
+ */
 int sz3g_read_header(const void* stream, size_t bytes, int stream_on_device, sz3g_params* p,
                      uint64_t* n_points);
 
@@ -340,8 +340,9 @@ int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_
  * array built into the library (held on every GPU that loads the library
  * until the process exits).
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current.
+ *  - Synchronous: every call waits for its own GPU work (also on the error
+ *    paths), so it cannot be recorded into a CUDA graph.
  *  - All calls share the array and each call resets the parts that must start
  *    at zero; calls whose GPU work overlaps race on it, so do not run two at
  *    once.
@@ -349,7 +350,7 @@ int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_
  *    (about 40 bytes per 4096-code chunk plus 0.7 MiB of decode tables,
  *    i.e. n up to roughly 3.5e8 codes at 4096-code chunks); nothing is
  *    launched then.
- *  - Synchronises `stream` before returning.
+ *  - Statuses as sz3g_huffman_decode (the same mapping of device flags).
  */
 int sz3g_huffman_decode_static(const uint32_t* d_words, uint64_t n_words, const uint32_t* d_chunk_words,
                                const uint16_t* d_sub_bits, uint32_t chunk, const uint8_t* d_len,

@@ -76,6 +76,9 @@ extern "C" int sz3g_huffman_decode_static(const uint32_t* d_words, uint64_t n_wo
       chunk > 65536 || chunk % 8 || ((uintptr_t)d_codes % 16) != 0)
     return SZ3G_E_INVAL;
   const unsigned long long nch = (n + chunk - 1) / chunk;
+  // no stream with more chunks than 8-byte offsets fit in the array can fit;
+  // refusing it here also keeps the size sums below from wrapping
+  if (nch > kStaticScratchBytes / 8) return SZ3G_E_CAPACITY;
   const unsigned long long nsb = (chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
   // layout inside the fixed array; a stream too long for it is refused
   const size_t o_st = 0;
@@ -97,17 +100,23 @@ extern "C" int sz3g_huffman_decode_static(const uint32_t* d_words, uint64_t n_wo
     return SZ3G_E_CUDA;
   }
   int rc = launch_decode_tables(nullptr, 0, d_len, nsym, ws + o_tab, st, s);
-  if (rc != SZ3G_OK) return rc;
-  rc = launch_decode_chunks(d_words, n_words, d_chunk_words, d_sub_bits, nch, chunk, n, ws + o_tab,
-                            (unsigned long long*)(ws + o_woff), d_codes, (uint32_t*)(ws + o_zc), ws + o_scan, st, s);
-  if (rc != SZ3G_OK) return rc;
+  if (rc == SZ3G_OK)
+    rc = launch_decode_chunks(d_words, n_words, d_chunk_words, d_sub_bits, nch, chunk, n, ws + o_tab,
+                              (unsigned long long*)(ws + o_woff), d_codes, (uint32_t*)(ws + o_zc), ws + o_scan, st,
+                              s);
+  if (rc != SZ3G_OK) {
+    // work already queued may still use the array: let it finish before the
+    // caller can start another call
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    return rc;
+  }
   DevState h;
   if (cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return SZ3G_E_CUDA;
   }
-  if (h.flags & kFlagTimeout) return SZ3G_E_TIMEOUT;
-  if (h.flags & kFlagCorrupt) return SZ3G_E_CORRUPT;
-  return h.flags ? SZ3G_E_CORRUPT : SZ3G_OK;
+  // the same flag-to-status mapping as sz3g_huffman_decode
+  return stream_status(h.flags);
 }

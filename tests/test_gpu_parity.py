@@ -353,35 +353,18 @@ def test_large_alphabets_whole_stream(eb):
 
 @pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
 def test_full_512cube_rel_cubic(eb):
+    """The benchmark's field in the benchmark's launch configuration: the
+    whole compressed stream and every reconstructed value against the oracle,
+    at each bound of the sweep."""
     x = _grf512()
     op, gp = both_params(x.shape, eb, eb_mode=O.REL, interp=O.CUBIC)
     rc, s = gpu_compress(gp, x)
     assert rc == G.OK
-    if eb == 1e-3:  # the whole stream against the oracle
-        assert s == O.compress(op, x)
+    ref = O.compress(op, x)
+    assert s == ref
     rc, y = gpu_decompress(s, x.size, O.F32)
     assert rc == G.OK
+    want = O.decompress(ref).reshape(-1)
+    assert np.array_equal(y.view(np.uint32), want.view(np.uint32))
     eb_abs = eb * (float(x.max()) - float(x.min()))
     assert float(np.max(np.abs(y.astype(np.float64) - x.ravel()))) <= eb_abs
-    # sampled points: each code and reconstruction re-derived by the oracle's
-    # quantizer from the GPU's reconstruction of the point's neighbours
-    import struct
-    ebT = np.frombuffer(struct.pack("<Q", struct.unpack_from("<Q", s, 64)[0])[:4], np.float32)[0]
-    yr = y.reshape(x.shape)
-    rng = np.random.default_rng(int(eb * 1e6))
-    for _ in range(300):
-        i, j, k = (int(v) for v in rng.integers(0, 512, 3))
-        if k % 2 == 1:  # a last-pass point: neighbours along axis 2 at +-1, +-3
-            nb = [yr[i, j, k + dd] if 0 <= k + dd < 512 else None for dd in (-1, 1, -3, 3)]
-            a, b, c, d = [np.float32(v) if v is not None else np.float32(0) for v in nb]
-            hb, hc, hd = k + 1 < 512, k >= 3, k + 3 < 512
-            if hc and hd:
-                pred = np.float32(np.float32(np.float32(9) * np.float32(a + b)) - np.float32(c + d)) * np.float32(0.0625)
-            elif not hc and hd:
-                pred = np.float32(np.float32(np.float32(3) * a + np.float32(6) * b) - d) * np.float32(0.125)
-            elif hc and hb:
-                pred = np.float32(np.float32(np.float32(6) * a + np.float32(3) * b) - c) * np.float32(0.125)
-            else:
-                continue
-            code, recon = O.quantize1(x[i, j, k], np.float32(pred), ebT)
-            assert (recon == yr[i, j, k]) or code == 0

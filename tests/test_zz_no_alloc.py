@@ -60,3 +60,43 @@ def test_static_decode_refuses_streams_beyond_its_scratch():
     rc = G.sz3g_huffman_decode_static(w.data_ptr(), nw, cw.data_ptr(), 0, 8, ln.data_ptr(), 65536, out.data_ptr(),
                                       1 << 31, G._stream_handle())
     assert rc == G.E_CAPACITY
+
+
+def test_static_decode_reports_corrupt_then_recovers():
+    """A moved sub-block boundary is reported as SZ3G_E_CORRUPT (the same
+    status as the allocating decoder), and the next well-formed call, which
+    starts from a reset status block, succeeds and matches it."""
+    codes, w, nw, cw, sub, ln = _encoded(4, 50_000, 4096, 30.0)
+    sh = G._stream_handle()
+    bad = sub.clone()
+    bad[0] += 1
+    out = torch.empty(codes.size, dtype=torch.int16, device="cuda")
+    args = (w.data_ptr(), nw, cw.data_ptr())
+    tail = (4096, ln.data_ptr(), 65536, out.data_ptr(), codes.size, sh)
+    assert G.sz3g_huffman_decode(*args, bad.data_ptr(), *tail) == G.E_CORRUPT
+    assert G.sz3g_huffman_decode_static(*args, bad.data_ptr(), *tail) == G.E_CORRUPT
+    assert G.sz3g_huffman_decode_static(*args, sub.data_ptr(), *tail) == G.OK
+    assert np.array_equal(out.cpu().numpy().view(np.uint16), codes)
+
+
+def test_static_decode_small_alphabet():
+    rng = np.random.default_rng(5)
+    n, nsym = 20_001, 40
+    codes = rng.integers(0, nsym, n).astype(np.uint16)
+    ln = O.huffman_lengths(O.histogram(codes))[:nsym].copy()
+    full = np.zeros(65536, np.uint8)
+    full[:nsym] = ln
+    cc = O.canonical_codes(full)
+    words, cw, sub = O.huffman_encode(codes, full, cc, 1024, with_sub=True)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    w, c, sb, l = dev(words.view(np.int32)), dev(cw.view(np.int32)), dev(sub.view(np.int16)), dev(ln)
+    sh = G._stream_handle()
+    ref = torch.empty(n, dtype=torch.int16, device="cuda")
+    assert G.sz3g_huffman_decode(w.data_ptr(), words.size, c.data_ptr(), sb.data_ptr(), 1024, l.data_ptr(), nsym,
+                                 ref.data_ptr(), n, sh) == G.OK
+    for _ in range(2):
+        out = torch.full((n,), -1, dtype=torch.int16, device="cuda")
+        assert G.sz3g_huffman_decode_static(w.data_ptr(), words.size, c.data_ptr(), sb.data_ptr(), 1024, l.data_ptr(),
+                                            nsym, out.data_ptr(), n, sh) == G.OK
+        assert torch.equal(out, ref)
+    assert np.array_equal(ref.cpu().numpy().view(np.uint16), codes)
