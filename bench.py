@@ -157,23 +157,62 @@ class Clocks:
 
 
 def algorithmic_bytes(kernel: str, info: dict) -> float:
-    """Bytes a kernel must move per step, counting each input read and each
-    output written once (the figure the roofline fraction divides)."""
+    """A kernel's share of the algorithmic bytes of its direction: compress
+    (REL) must read the field twice (range, then the values) and write the
+    stream; decompress must read the stream and write the field.  The shares
+    partition those totals: range and the quantize levels one field read
+    each, the encoder the stream it writes; the decoder the stream it reads,
+    the recover levels the field they write.  Kernels with no share (the
+    codebook, the coarse grids' helpers) move only implementation bytes."""
     N, esz = info["N"], info["esz"]
-    coarse = info["coarse_points"]  # points of G_1 and coarser (recon pyramid)
-    payload = info["payload_bytes"]
-    unpred = info["n_unpred"] * esz
+    stream = info["stream_bytes"]
     return {
         "range": N * esz,
-        "pass_quantize": N * (esz + 2) + coarse * esz,
-        "level_quantize": info["level_quantize_bytes"],
-        "pass_recover": N * (2 + esz) + coarse * esz,
-        "level_recover": info["level_recover_bytes"],
-        "decode": payload + 2 * N,
-        "encode": 2 * N + payload + 2 * unpred,
-        "codebook": 65536 * 4 * 2,
-        "lift": 2 * coarse * esz,
-    }.get(kernel, float("nan"))
+        "level_quantize": N * esz,
+        "encode": stream,
+        "decode": stream,
+        "level_recover": N * esz,
+    }.get(kernel, 0.0)
+
+
+def implementation_bytes(kernel: str, info: dict) -> float:
+    """Bytes a kernel moves beyond its algorithmic share, counted once each:
+    the 2-byte code of every point (written by the quantize levels, read by
+    the encoder; written by the decoder, read by the recover levels) and the
+    reconstruction of the coarser grids (written once, read once by the
+    level above)."""
+    N, esz = info["N"], info["esz"]
+    coarse = info["coarse_points"]
+    return {
+        "level_quantize": 2 * N + 2 * coarse * esz,
+        "encode": 2 * N,
+        "decode": 2 * N,
+        "level_recover": 2 * N + 2 * coarse * esz,
+    }.get(kernel, 0.0)
+
+
+def host_cpu():
+    """The host CPU's model name and logical core count."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count()}
 
 
 def traffic_for(kernel: str):
@@ -204,7 +243,7 @@ def run_reference(args):
 
     O.build()
     x = S.grf((args.size,) * 3, SEED)
-    m = min(128, args.size)
+    m = min(256, args.size)
     sample = np.ascontiguousarray(x[:m, :m, :m])
     p = O.make_params(sample.shape, EB, eb_mode=O.REL, interp=O.CUBIC)
     for _ in range(args.warmup):
@@ -221,7 +260,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{m}^3 corner of the {args.size}^3 field, compress + decompress per step"},
+                         "sample": f"{m}^3 corner of the {args.size}^3 field ({sample.nbytes} bytes), compress + "
+                                   "decompress per step, one thread", **host_cpu()},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -246,7 +286,7 @@ def cpu_baseline(x):
             break
     dt = (time.perf_counter() - t0) / reps
     return {"value": sample.nbytes / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{m}^3 corner of the field, compress + decompress, {reps} run(s), one thread"}
+            "sample": f"{m}^3 corner of the field, compress + decompress, {reps} run(s), one thread", **host_cpu()}
 
 
 def grf_gpu(shape, seed, dev):
@@ -807,7 +847,12 @@ def main():
     for _ in range(max(args.warmup, 3)):
         nb = step()
     torch.cuda.synchronize()
-    maxerr = float((y - xd.reshape(-1)).abs().max().item())
+    diff = (y - xd.reshape(-1)).double()
+    maxerr = float(diff.abs().max().item())
+    mse = float((diff * diff).mean().item())
+    vrange = float(xd.max().item()) - float(xd.min().item())
+    psnr = 20.0 * np.log10(vrange) - 10.0 * np.log10(mse) if mse > 0 else float("inf")
+    del diff
     # timed region
     clocks = Clocks(torch.cuda.current_device())
     if ws > 1:
@@ -859,22 +904,26 @@ def main():
     n_unpred = struct.unpack_from("<Q", head, 88)[0]
     n_words = struct.unpack_from("<Q", head, 104)[0]
     coarse = sum(int(np.prod([-(-n // (1 << k))] * 3)) for k in range(1, 10))
-    g1 = int(np.prod([-(-n // 2)] * 3))
     info = {"N": x.size, "esz": 4, "coarse_points": coarse, "payload_bytes": n_words * 4, "n_unpred": n_unpred,
-            "level_quantize_bytes": x.size * (4 + 2) + coarse * 4,
-            "level_recover_bytes": x.size * (2 + 4) + coarse * 4}
-    del g1
+            "stream_bytes": nb}
     peak, peak_kind = peaks()
     dom = max(kern.items(), key=lambda kv: kv[1][0]) if kern else None
+    comp_frac = (in_bytes * 2 + nb) / (comp_ms * 1e-3) / 1e9 / peak
+    dec_frac = (in_bytes + nb) / (dec_ms * 1e-3) / 1e9 / peak
     roof = None
     if dom:
         name, (ms_per_step, l_per_step) = dom
         byts = algorithmic_bytes(name, info)
         ach = byts / (ms_per_step * 1e-3) / 1e9
+        launches_per_step = max(l_per_step, 1.0)
+        tr = traffic_for(name)
         roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "peak_kind": peak_kind, "traffic": traffic_for(name),
-                "launches_per_step": l_per_step, "ms_per_step": ms_per_step,
-                "algorithmic_bytes_per_step": byts}
+                "peak_kind": peak_kind, "traffic": (tr / launches_per_step) if tr else None,
+                "traffic_per_step": tr, "launches_per_step": l_per_step, "ms_per_step": ms_per_step,
+                "algorithmic_bytes_per_step": byts, "implementation_bytes_per_step": implementation_bytes(name, info),
+                "per_direction": {"compress": comp_frac, "decompress": dec_frac,
+                                  "compress_algorithmic_bytes": in_bytes * 2 + nb,
+                                  "decompress_algorithmic_bytes": in_bytes + nb}}
     # end to end through the host-buffer entry points (pinned host memory)
     e2e = None
     if not args.no_e2e:
@@ -936,10 +985,11 @@ def main():
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(n),
             "compress": {"ms": comp_ms, "GB/s": in_bytes / (comp_ms * 1e-3) / 1e9,
-                         "frac_of_hbm_algorithmic": (in_bytes * 2 + nb) / (comp_ms * 1e-3) / 1e9 / peak},
+                         "frac_of_hbm_algorithmic": comp_frac},
             "decompress": {"ms": dec_ms, "GB/s": in_bytes / (dec_ms * 1e-3) / 1e9,
-                           "frac_of_hbm_algorithmic": (in_bytes + nb) / (dec_ms * 1e-3) / 1e9 / peak},
-            "compression_ratio": in_bytes / nb, "max_abs_error": maxerr, "stream_bytes": nb,
+                           "frac_of_hbm_algorithmic": dec_frac},
+            "compression_ratio": in_bytes / nb, "bits_per_value": 8.0 * nb / x.size, "psnr_db": psnr,
+            "max_abs_error": maxerr, "stream_bytes": nb, "n_unpred": n_unpred,
             "roofline": roof, "kernels_ms_per_step": {k: v[0] for k, v in sorted(kern.items())},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "eb_sweep": sweep,
         }
