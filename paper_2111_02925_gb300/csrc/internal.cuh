@@ -175,10 +175,22 @@ __device__ __forceinline__ T interp_predict(T a, T b, T c, T d, bool has_b, bool
   return a;
 }
 
-// Truncation toward zero, saturating (NaN -> 0): only used where the result is
-// discarded unless the value is in range.
-__device__ __forceinline__ int to_int_rz(float v) { return __float2int_rz(v); }
+// Truncation toward zero of a value the caller only uses when 0 <= v < 2^22
+// (any other input gives an unspecified result that the caller discards).
+// FP32: the sum v + 2^23 rounded toward zero is 2^23 + trunc(v), whose bits
+// hold trunc(v) in the mantissa -- one full-rate add instead of a conversion.
+__device__ __forceinline__ int to_int_rz(float v) { return __float_as_int(__fadd_rz(v, 8388608.0f)) - 0x4B000000; }
 __device__ __forceinline__ int to_int_rz(double v) { return __double2int_rz(v); }
+
+// (T)v for an integer |v| < 2^22, exactly.  FP32: the float whose bits are
+// those of 1.5 * 2^23 plus v is 1.5 * 2^23 + v (v lands in the mantissa), so
+// subtracting 1.5 * 2^23 leaves v -- integer and float adds instead of a
+// conversion.
+template <typename T>
+__device__ __forceinline__ T small_int_to(int v) {
+  if constexpr (sizeof(T) == 4) return __int_as_float(0x4B400000 + v) - 12582912.0f;
+  else return T(v);
+}
 
 // Linear-scaling quantizer (Sec. 3.2): code radius + q with q the index of the
 // width-2*eb bin holding x - pred (half-up), or 0 when |q| would reach the
@@ -196,7 +208,7 @@ __device__ __forceinline__ uint32_t quantize_point(T x, T pred, T ebT, T ebr, in
   const int m = to_int_rz(t);
   const int h = (int)(((unsigned)m + 1u) >> 1);
   const int q = d < T(0) ? -h : h;
-  const T q2 = T((int)((unsigned)q << 1));
+  const T q2 = small_int_to<T>((int)((unsigned)q << 1));
   const T step = q2 * ebT;
   const T r = pred + step;
   const bool ok = in && fabs(r - x) <= ebT;
@@ -208,7 +220,7 @@ __device__ __forceinline__ uint32_t quantize_point(T x, T pred, T ebT, T ebr, in
 template <typename T>
 __device__ __forceinline__ T recover_point(T pred, uint32_t code, int radius, T ebT) {
   int q = (int)code - radius;
-  T q2 = T(2 * q);
+  T q2 = small_int_to<T>(2 * q);
   T step = q2 * ebT;
   return pred + step;
 }

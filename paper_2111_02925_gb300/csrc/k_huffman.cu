@@ -1366,7 +1366,7 @@ struct DecTables {
   uint32_t base[SZ3G_LMAX + 2];  // start[L] - fc[L] (mod 2^32): codeword c of length L is symbol
                                  // sorted[c + base[L]]
   uint32_t n_used;
-  uint32_t pad;
+  uint32_t has_zero;               // symbol 0 (the unpredictable code) has a codeword
   unsigned long long keys[kSyms];  // used symbols (length << 16 | symbol) in symbol order
   uint16_t sorted[kSyms];          // symbols by (length, symbol)
 };
@@ -1456,6 +1456,7 @@ __global__ void __launch_bounds__(kCbThreads) decode_tables_kernel(const unsigne
       start += s_cnt[L];
     }
     T->n_used = (uint32_t)K;
+    T->has_zero = (keys[0] & 0xffffull) == 0 ? 1u : 0u;  // keys are in symbol order
   }
   if (tid <= SZ3G_LMAX + 1) s_base[tid] = 0;
   // Symbols ordered by (length, symbol): the keys are in symbol order, so a
@@ -1510,6 +1511,7 @@ struct DecArgs {
   const uint32_t* chunk_words;
   const uint16_t* sub_bits;        // bit lengths of 512-code sub-blocks (nsb - 1 per chunk), or null
   unsigned long long n_chunks, n;
+  unsigned long long n_words;      // payload words (>= 1)
   uint32_t chunk, nsb;             // nsb = 512-code sub-blocks per chunk
   uint32_t unit, upc;              // codes per decoding thread, threads per chunk
   const DecTables* T;
@@ -1519,53 +1521,77 @@ struct DecArgs {
 };
 
 // One thread decodes one unit: a 512-code sub-block when the stream carries
-// sub-block lengths (its start bit is their sum), else a whole chunk.  The
-// length of the next codeword comes from a 16-bit direct table in shared
-// memory (longer codewords: comparisons with the left-justified limits), its
-// symbol from the (length, symbol) order, so only the table read and the
-// shift are on the thread's serial path.  Payload words reach a per-thread
-// ring in shared memory by cp.async kDecAhead words before they are used.
-// Large CTAs: the 64 KiB table is held once per sixteen warps.
-constexpr int kDecThreads = 512;
-constexpr bool kDecRingFetch = true;  // payload words by cp.async into a shared ring (else registers)
-constexpr int kDecRing = 8, kDecAhead = 6;
-constexpr int kDecSortedSmem = 16384;  // symbols kept in shared memory (more: read from global)
-constexpr size_t kDecOffRing = (size_t)4 << kLutBits;
-constexpr size_t kDecOffSorted = kDecOffRing + (kDecRingFetch ? (size_t)kDecThreads * kDecRing * 4 : 0);
-constexpr size_t kDecodeSmem = kDecOffSorted + (size_t)kDecSortedSmem * 2;
+// sub-block lengths (its start bit is their sum), else a whole chunk.
+//
+// The thread's payload words pass through a ring of kDecRingW words in shared
+// memory (slot q of thread t at word q * kDecThreads + t: the lanes of a warp
+// never share a bank).  They arrive as 16-byte blocks copied asynchronously
+// into a per-thread staging area kDecStage blocks ahead of their use.  The
+// two words under the read position are kept in registers; the next
+// codeword's length and symbol come from a 12-bit direct table in shared
+// memory (entry: symbol << 16 | length; 0 for a longer codeword) applied to
+// the 32-bit window at the read position (one funnel shift), so only the
+// table read is on a code's serial path.  One ring check per eight codes
+// (eight codes use at most 6 words), the word advance as a select, one byte
+// permute packing two symbols, zero codes counted on the packed words, and a
+// rarely taken branch for codewords longer than the table (their length by
+// comparisons with the left-justified limits).
+constexpr int kDecThreads = 256;
+constexpr int kDecLB = 12;                        // bits of the shared-memory direct table
+constexpr int kDecRingW = 16;                     // ring words per thread (a power of two)
+constexpr int kDecStage = 2;                      // 16-byte blocks in flight per thread
+constexpr size_t kDecOffRing = (size_t)4 << kDecLB;
+constexpr size_t kDecOffStage = kDecOffRing + (size_t)kDecRingW * kDecThreads * 4;
+constexpr size_t kDecodeSmem = kDecOffStage + (size_t)kDecStage * kDecThreads * 16;
 
-__device__ __forceinline__ void dec_fetch(uint32_t* slot, const uint32_t* src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(slot);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n\tcp.async.commit_group;" ::"r"(d), "l"(src) : "memory");
+__device__ __forceinline__ void dec_stage(uint4* dst, const uint4* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n\tcp.async.commit_group;" ::"r"(d), "l"(src) : "memory");
 }
 
-__global__ void __launch_bounds__(kDecThreads) decode_kernel(const DecArgs a) {
+// A codeword longer than the direct table: its length from the left-justified
+// limits, its symbol from the (length, symbol) order; symbol << 16 | length,
+// or 0 when the window starts no codeword.
+__device__ __forceinline__ uint32_t dec_long(uint32_t win, const uint32_t* s_lim, const uint32_t* s_base,
+                                             uint32_t n_used, const uint16_t* sorted) {
+  const uint32_t v = win >> (32 - SZ3G_LMAX);
+  uint32_t L = kDecLB + 1;
+#pragma unroll
+  for (int l = kDecLB + 1; l < SZ3G_LMAX; ++l) L += v >= s_lim[l];
+  const uint32_t k = (win >> (32 - L)) + s_base[L];
+  if (v >= s_lim[SZ3G_LMAX] || k >= n_used) return 0u;
+  return ((uint32_t)__ldg(sorted + k) << 16) | L;
+}
+
+// number of zero 16-bit halves of x
+__device__ __forceinline__ uint32_t zero_halves(uint32_t x) {
+  return (uint32_t)((x & 0xffffu) == 0) + (uint32_t)((x >> 16) == 0);
+}
+
+__global__ void __launch_bounds__(kDecThreads, 4) decode_kernel(const DecArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ uint32_t s_lim[SZ3G_LMAX + 2], s_base[SZ3G_LMAX + 2];
   __shared__ int s_skip;
   const int tid = threadIdx.x;
   if (tid == 0) s_skip = (a.st->flags & kFlagCorrupt) != 0;  // tables or chunk table rejected
+  uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
+  // the 12-bit table from the 13-bit one (len << 16 | sym): codewords of 13
+  // bits become "longer"; entries as sym << 16 | len
+  for (int w = tid; w < (1 << kDecLB); w += kDecThreads) {
+    const uint32_t e = a.T->lut[w << (kLutBits - kDecLB)];
+    const uint32_t L = e >> 16;
+    lut[w] = (L != 0 && L <= (uint32_t)kDecLB) ? ((e << 16) | L) : 0u;
+  }
+  if (tid <= SZ3G_LMAX + 1) {
+    s_lim[tid] = a.T->lim[tid];
+    s_base[tid] = a.T->base[tid];
+  }
   __syncthreads();
   if (s_skip) return;
   const uint32_t n_used = a.T->n_used;
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(a.T->lut);
-    uint4* dst = reinterpret_cast<uint4*>(dsm);
-    for (int i = tid; i < (1 << kLutBits) / 4; i += kDecThreads) dst[i] = src[i];
-    if (n_used <= (uint32_t)kDecSortedSmem) {
-      uint16_t* ds = reinterpret_cast<uint16_t*>(dsm + kDecOffSorted);
-      for (uint32_t i = tid; i < n_used; i += kDecThreads) ds[i] = a.T->sorted[i];
-    }
-    if (tid <= SZ3G_LMAX + 1) {
-      s_lim[tid] = a.T->lim[tid];
-      s_base[tid] = a.T->base[tid];
-    }
-  }
-  __syncthreads();
-  const uint32_t* lut = reinterpret_cast<const uint32_t*>(dsm);
-  const bool sorted_smem = n_used <= (uint32_t)kDecSortedSmem;
-  const uint16_t* s_sorted = reinterpret_cast<const uint16_t*>(dsm + kDecOffSorted);
-  uint32_t* ring = reinterpret_cast<uint32_t*>(dsm + kDecOffRing) + tid;  // slot k at ring[k * kDecThreads]
+  const bool count_zeros = a.T->has_zero != 0;
+  uint32_t* ring = reinterpret_cast<uint32_t*>(dsm + kDecOffRing) + tid;  // word slot q at ring[q * kDecThreads]
+  uint4* stg = reinterpret_cast<uint4*>(dsm + kDecOffStage) + tid;        // block slot s at stg[s * kDecThreads]
   const unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + tid;
   if (u >= a.n_chunks * a.upc) return;
   const unsigned long long j = u / a.upc;
@@ -1589,89 +1615,102 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(const DecArgs a) {
     atomicOr(&a.st->flags, kFlagCorrupt);
     return;
   }
-  const uint32_t* wp = a.words + a.woff[j];
-  // Bit buffer: `buf` holds nb valid bits at the top.  Word k of the chunk
-  // is fetched into ring slot k % kDecRing when word k - kDecAhead is taken
-  // (one commit group per word, so the oldest group is the word taken next).
-  // Fetches past the chunk read its last word again: a correct code never
-  // depends on bits after its own (canonical codes are prefix-free), and a
-  // decode that runs past the chunk is caught by the bit count at the end.
-  const uint32_t last = nw - 1;
-  uint32_t wi = (uint32_t)(bit0 >> 5);  // next word to take
-  uint32_t q1 = 0, q2 = 0, q3 = 0;      // register queue (kDecRingFetch false)
-  if constexpr (kDecRingFetch) {
-#pragma unroll
-    for (int k = 0; k < kDecAhead; ++k) dec_fetch(ring + ((wi + k) % kDecRing) * kDecThreads, wp + min(wi + k, last));
-  } else {
-    q1 = __ldg(wp + min(wi, last));
-    q2 = __ldg(wp + min(wi + 1, last));
-    q3 = __ldg(wp + min(wi + 2, last));
-  }
-  auto take = [&]() -> uint32_t {
-    uint32_t w;
-    if constexpr (kDecRingFetch) {
-      asm volatile("cp.async.wait_group %0;" ::"n"(kDecAhead - 1) : "memory");
-      w = ring[(wi % kDecRing) * kDecThreads];
-      dec_fetch(ring + ((wi + kDecAhead) % kDecRing) * kDecThreads, wp + min(wi + kDecAhead, last));
-    } else {
-      w = q1;
-      q1 = q2;
-      q2 = q3;
-      q3 = __ldg(wp + min(wi + 3, last));
-    }
-    ++wi;
-    return w;
+  // The unit's words as a sequence of 16-byte blocks starting at the aligned
+  // block that holds its first word; blocks past the payload's last one read
+  // that block again (a correct code never depends on bits after its own, and
+  // a decode that runs past its bits is caught by the bit count at the end).
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(a.words + a.woff[j] + (bit0 >> 5));
+  const uint4* blk = reinterpret_cast<const uint4*>(a0 & ~(uintptr_t)15);
+  const uintptr_t a_last = reinterpret_cast<uintptr_t>(a.words + a.n_words - 1) & ~(uintptr_t)15;
+  const uint32_t q_last = a_last >= (a0 & ~(uintptr_t)15) ? (uint32_t)((a_last - (a0 & ~(uintptr_t)15)) >> 4) : 0u;
+  constexpr uint32_t RM = kDecRingW - 1, SM_ = kDecStage - 1;
+  auto stage = [&](uint32_t q) { dec_stage(stg + (q & SM_) * kDecThreads, blk + min(q, q_last)); };
+  auto put = [&](uint32_t at, const uint4& v) {  // words at .. at + 3 of the sequence
+    ring[((at + 0) & RM) * kDecThreads] = v.x;
+    ring[((at + 1) & RM) * kDecThreads] = v.y;
+    ring[((at + 2) & RM) * kDecThreads] = v.z;
+    ring[((at + 3) & RM) * kDecThreads] = v.w;
   };
-  unsigned long long buf = (unsigned long long)take() << (32 + (int)(bit0 & 31));
-  int nb = 32 - (int)(bit0 & 31);
+  stage(0);
+  stage(1);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  put(0, stg[0]);
+  put(4, stg[1 * kDecThreads]);
+  stage(2);
+  stage(3);
+  uint32_t stored = 8, next_use = 2;  // words in the ring; next staged block to take
+  const uint32_t start_bit = (uint32_t)((a0 & 15) * 8) + (uint32_t)(bit0 & 31);
+  // window: words wk - 2 (wa) and wk - 1 (wb); read position bp in wa
+  uint32_t wk = (start_bit >> 5) + 2;
+  uint32_t wa = ring[((wk - 2) & RM) * kDecThreads];
+  uint32_t wb = ring[((wk - 1) & RM) * kDecThreads];
+  uint32_t bp = start_bit & 31;
   uint32_t zeros = 0;
-  uint16_t* out = a.codes + j * a.chunk;
-  for (uint32_t i = c0; i < c1; i += 8) {  // c0 is a multiple of 8
+  uint16_t* out = a.codes + j * a.chunk + c0;
+  // one codeword: its entry (symbol << 16 | length), or false for a window
+  // that starts no codeword
+  auto one = [&](uint32_t& e) -> bool {
+    const uint32_t win = __funnelshift_l(wb, wa, bp);
+    e = lut[win >> (32 - kDecLB)];
+    if ((e & 31u) == 0) {  // a codeword longer than the table
+      e = dec_long(win, s_lim, s_base, n_used, a.T->sorted);
+      if (e == 0) return false;
+    }
+    bp += e & 31u;
+    const bool adv = bp >= 32;
+    const uint32_t wn = ring[(wk & RM) * kDecThreads];
+    wa = adv ? wb : wa;
+    wb = adv ? wn : wb;
+    wk += adv ? 1u : 0u;
+    bp -= adv ? 32u : 0u;
+    return true;
+  };
+  for (uint32_t i = c0; i < c1; i += 8, out += 8) {  // c0 is a multiple of 8
     if (i != c0 && (i & (SZ3G_SUBBLOCK - 1)) == 0) {  // whole-chunk units count per sub-block
       a.zcnt[j * a.nsb + ((i >> 9) - 1)] = zeros;
       zeros = 0;
     }
-    const uint32_t m = min(8u, c1 - i);
-    uint32_t pk[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (uint32_t q = 0; q < 8; ++q) {
-      if (q < m) {
-        if (nb <= 32) {
-          buf |= (unsigned long long)take() << (32 - nb);
-          nb += 32;
-        }
-        const uint32_t e = lut[(uint32_t)(buf >> (64 - kLutBits))];
-        uint32_t L = e >> 16, sym = e & 0xffffu;
-        if (L == 0) {  // a codeword longer than kLutBits: the limits give its length
-          const uint32_t v = (uint32_t)(buf >> (64 - SZ3G_LMAX));
-          L = kLutBits + 1;
-#pragma unroll
-          for (int l = kLutBits + 1; l < SZ3G_LMAX; ++l) L += v >= s_lim[l];
-          const uint32_t k = (uint32_t)(buf >> (64 - L)) + s_base[L];
-          if (v >= s_lim[SZ3G_LMAX] || k >= n_used) {
-            bad = true;
-            break;
-          }
-          sym = sorted_smem ? s_sorted[k] : __ldg(a.T->sorted + k);
-        }
-        buf <<= L;
-        nb -= (int)L;
-        zeros += sym == 0;
-        pk[q >> 1] |= sym << (16 * (q & 1));
-      }
+    // eight codes advance the window by at most 6 words
+    while (stored < wk + 6) {
+      asm volatile("cp.async.wait_group %0;" ::"n"(kDecStage - 1) : "memory");
+      put(stored, stg[(next_use & SM_) * kDecThreads]);
+      stored += 4;
+      stage(next_use + kDecStage);  // into the slot just read
+      ++next_use;
     }
-    if (bad) break;
+    const uint32_t m = min(8u, c1 - i);
     if (m == 8) {
-      *reinterpret_cast<uint4*>(out + i) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t e0 = 0, e1 = 0;
+        if (!one(e0) || !one(e1)) {
+          bad = true;
+          break;
+        }
+        pk[q] = __byte_perm(e0, e1, 0x7632);  // symbol of e0 low, of e1 high
+      }
+      if (bad) break;
+      if (count_zeros) zeros += zero_halves(pk[0]) + zero_halves(pk[1]) + zero_halves(pk[2]) + zero_halves(pk[3]);
+      *reinterpret_cast<uint4*>(out) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     } else {
-      for (uint32_t q = 0; q < m; ++q) out[i + q] = (uint16_t)(pk[q >> 1] >> (16 * (q & 1)));
+      for (uint32_t q = 0; q < m; ++q) {
+        uint32_t e;
+        if (!one(e)) {
+          bad = true;
+          break;
+        }
+        out[q] = (uint16_t)(e >> 16);
+        if (count_zeros) zeros += (e >> 16) == 0;
+      }
+      if (bad) break;
     }
   }
   // no copy may land in shared memory after the thread has left
-  if constexpr (kDecRingFetch) asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("cp.async.wait_all;" ::: "memory");
   if (!bad) {
-    // bits consumed from the chunk start: words taken, less the bits still buffered
-    const unsigned long long used = 32ull * wi - (unsigned long long)nb;
+    // bits consumed from the chunk start
+    const unsigned long long used = bit0 + (unsigned long long)((wk - 2) * 32u + bp - start_bit);
     a.zcnt[j * a.nsb + ((c1 - 1) >> 9)] = zeros;
     // the recorded sub-block boundary must be exactly where decoding ended
     if (sb && a.unit == SZ3G_SUBBLOCK && b + 1 < a.nsb && used != bit0 + sb[b]) bad = true;
@@ -1709,6 +1748,7 @@ int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, cons
   a.sub_bits = sub_bits;
   a.n_chunks = n_chunks;
   a.n = n;
+  a.n_words = n_words > 0 ? n_words : 1;
   a.chunk = chunk;
   a.nsb = (chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
   a.unit = (sub_bits && a.nsb > 1) ? (uint32_t)SZ3G_SUBBLOCK : chunk;
