@@ -127,6 +127,39 @@ int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t ou
  */
 int sz3g_graph_cache(int on);
 
+/*
+ * Failure injection, for tests of the library's failure handling (the paper
+ * has no counterpart).  Process-wide settings read by the host when a call
+ * enqueues its kernels (a pipeline replayed from the graph cache, or a batch
+ * captured earlier, keeps the settings it was built with); not thread-safe.
+ * Nothing here makes a GPU fault: every injected failure ends a bounded wait
+ * or refuses an allocation, and the call returns its status.
+ *   SZ3G_DEBUG_RESET        all settings back to normal (value ignored)
+ *   SZ3G_DEBUG_WAIT_LIMIT   value = spin limit of the level queue's dependency
+ *                           waits and of the encoder's and scans' look-backs
+ *                           (0: the built-in limits)
+ *   SZ3G_DEBUG_QUEUE_STALL  value = v: the first level of a batch's level
+ *                           queue at or after index v that waits on another
+ *                           level waits for one chunk more than that level
+ *                           has (-1: none); the wait gives up and the run
+ *                           reports SZ3G_E_TIMEOUT
+ *   SZ3G_DEBUG_SILENT_CHUNK value = chunk that never publishes its look-back
+ *                           state in the one-pass encoder (fields of at most
+ *                           1024 chunks; -1: none); the chunks after it give
+ *                           up and the call reports SZ3G_E_TIMEOUT
+ *   SZ3G_DEBUG_ALLOC_FAIL   value = number of the library's following
+ *                           workspace allocations that fail (SZ3G_E_NOMEM)
+ * Returns SZ3G_OK, or SZ3G_E_INVAL for an unknown kind or a value out of range.
+ */
+enum {
+  SZ3G_DEBUG_RESET = 0,
+  SZ3G_DEBUG_WAIT_LIMIT = 1,
+  SZ3G_DEBUG_QUEUE_STALL = 2,
+  SZ3G_DEBUG_SILENT_CHUNK = 3,
+  SZ3G_DEBUG_ALLOC_FAIL = 4
+};
+int sz3g_debug_inject(int kind, long long value);
+
 /* ---------------------------------------------------------------------------
  * Optional lossless stage after the Huffman coder (SZ3 ends its pipelines in
  * a dictionary coder): byte-level LZ77 over independent SZ3G_LZ_BLOCK-byte

@@ -9,6 +9,8 @@
 
 namespace sz3g {
 
+DebugInject g_debug = {0u, -1, -1, 0};
+
 // Launchers defined in k_huffman.cu that are used only here.
 int launch_encode(const Plan& pl, const uint16_t* codes, const uint32_t* table, const void* d_in, const PassMap* map,
                   void* scratch, DevState* st, unsigned char* d_out, unsigned long long out_capacity, int mode,
@@ -125,6 +127,11 @@ cudaMemPool_t lib_pool() {
 }
 
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  if (g_debug.alloc_fail > 0) {  // injected failure (tests)
+    --g_debug.alloc_fail;
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   cudaMemPool_t pl = lib_pool();
   return pl ? cudaMallocFromPoolAsync(p, bytes, pl, s) : cudaMallocAsync(p, bytes, s);
 }
@@ -738,6 +745,30 @@ int sz3g_huffman_fixed(uint32_t radius, uint8_t* d_len, uint32_t* d_code, void* 
   if (radius < 2 || radius > 32768 || !d_len || !d_code) return SZ3G_E_INVAL;
   SZ3G_TRY(launch_huffman_fixed(radius, d_len, d_code, (cudaStream_t)stream));
   return SZ3G_OK;
+}
+
+int sz3g_debug_inject(int kind, long long value) {
+  switch (kind) {
+    case SZ3G_DEBUG_RESET:
+      g_debug = DebugInject{0u, -1, -1, 0};
+      return SZ3G_OK;
+    case SZ3G_DEBUG_WAIT_LIMIT:
+      if (value < 0 || value > 0x7fffffffll) return SZ3G_E_INVAL;
+      g_debug.wait_limit = (uint32_t)value;
+      return SZ3G_OK;
+    case SZ3G_DEBUG_QUEUE_STALL:
+      g_debug.queue_stall = value < 0 ? -1 : value;
+      return SZ3G_OK;
+    case SZ3G_DEBUG_SILENT_CHUNK:
+      g_debug.silent_chunk = value < 0 ? -1 : value;
+      return SZ3G_OK;
+    case SZ3G_DEBUG_ALLOC_FAIL:
+      if (value < 0 || value > 0x7fffffffll) return SZ3G_E_INVAL;
+      g_debug.alloc_fail = (int)value;
+      return SZ3G_OK;
+    default:
+      return SZ3G_E_INVAL;
+  }
 }
 
 int sz3g_graph_cache(int on) {

@@ -95,6 +95,16 @@ struct Plan {
   uint32_t nsub;             // 512-code sub-blocks per chunk
 };
 
+// Failure injection for tests (set by sz3g_debug_inject, read on the host by
+// the launchers, which pass the values to their kernels; process-wide).
+struct DebugInject {
+  uint32_t wait_limit;     // spin limit of the dependency waits and look-backs (0: the built-in limits)
+  long long queue_stall;   // level-queue entry whose dependency can never be met (-1: none)
+  long long silent_chunk;  // chunk that never publishes its look-back state in the one-pass encoder (-1: none)
+  int alloc_fail;          // library allocations still to fail
+};
+extern DebugInject g_debug;
+
 // Kernels known to the launch accounting (names in prof.cu).
 enum KernelId {
   kKRange, kKEb, kKAnchor, kKLift, kKPassQuantize, kKPassRecover, kKCodebook, kKEncode, kKFinalize,

@@ -220,6 +220,44 @@ __device__ __forceinline__ T fine_point(const LevelArgs<T>& a, const FineDesc& d
   }
 }
 
+// N points of one task with every point inside the grid: compress quantizes
+// them and counts the owned ones (codes away from the shared window reach the
+// global histogram on a path taken once per task); recover reconstructs them,
+// sending codes 0 (unpredictable) and codes past the alphabet through
+// fine_point on a path taken once per task.  cq receives the codes (compress).
+template <typename T, bool COMP, int N>
+__device__ __forceinline__ void fine_points(const LevelArgs<T>& a, const FineDesc& d, uint32_t* hwin, int hlo,
+                                            const T* x, const T* p, T ebT, T ebr, const bool* own, uint32_t ci0,
+                                            const uint32_t* kin, FineAcc& acc, T* r, uint32_t* cq) {
+  if (COMP) {
+    bool anyfar = false;
+#pragma unroll
+    for (int u = 0; u < N; ++u) cq[u] = quantize_point<T>(x[u], p[u], ebT, ebr, a.radius, r[u]);
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+      const uint32_t bn = cq[u] - (uint32_t)hlo;
+      const bool far = bn >= (uint32_t)kHistWin;
+      if (own[u]) atomicAdd(&hwin[far ? (uint32_t)kHistWin : bn], 1u);
+      anyfar |= far && own[u];
+    }
+    if (anyfar)
+      for (int u = 0; u < N; ++u)
+        if (own[u] && cq[u] - (uint32_t)hlo >= (uint32_t)kHistWin) atomicAdd(&a.hist[cq[u]], 1u);
+  } else {
+    const uint32_t lim = 2u * (uint32_t)a.radius - 1u;
+    bool rare = false;
+#pragma unroll
+    for (int u = 0; u < N; ++u) rare |= (kin[u] - 1u) >= lim;
+    if (!rare) {
+#pragma unroll
+      for (int u = 0; u < N; ++u) r[u] = recover_point<T>(p[u], kin[u], a.radius, ebT);
+    } else {
+      for (int u = 0; u < N; ++u)
+        r[u] = fine_point<T, false>(a, d, hwin, hlo, T(0), p[u], ebT, ebr, true, ci0 + u, kin[u], acc);
+    }
+  }
+}
+
 // First code of a staged row and where its aligned 16-byte copy starts
 // (codes before the array start, only at rows whose leading points lie
 // outside the grid, are never read).
@@ -452,15 +490,29 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
             kr = K + S::kR2 * S::kL2 + (S::kR1 + row) * S::kL01 + o + ke;
           }
           T r[2];
+          if (IN) {
+            const T p2[2] = {interp_predict<T>(va[0], vb[0], vc[0], vd[0], true, true, true, INTERP),
+                             interp_predict<T>(va[1], vb[1], vc[1], vd[1], true, true, true, INTERP)};
+            const bool own2[2] = {ownj && ke >= 2 && ke < 2 + S::kW / 2, ownj && ke + 1 >= 2 && ke + 1 < 2 + S::kW / 2};
+            const T x2[2] = {xv[0], xv[2]};
+            uint32_t k2[2] = {0u, 0u}, q2[2];
+            if (!COMP) k2[0] = kr[0], k2[1] = kr[1];
+            fine_points<T, COMP, 2>(a, d, hwin, hlo, x2, p2, ebT, ebr, own2, (uint32_t)(c0 + ke), k2, acc, r, q2);
+            if (COMP) {
+              if (own2[0]) a.codes[c0 + ke] = (uint16_t)q2[0];
+              if (own2[1]) a.codes[c0 + ke + 1] = (uint16_t)q2[1];
+            }
+          } else {
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int kq = k + 2 * q;
-            r[q] = T(0);
-            if (!IN && (kq < 0 || kq >= m2)) continue;
-            const T p = interp_predict<T>(va[q], vb[q], vc[q], vd[q], hb, hc, hd, INTERP);
-            const bool own = ownj && ke + q >= 2 && ke + q < 2 + S::kW / 2;
-            r[q] = fine_point<T, COMP>(a, d, hwin, hlo, xv[2 * q], p, ebT, ebr, own, (uint32_t)(c0 + ke + q),
-                                       COMP ? 0u : (uint32_t)kr[q], acc);
+            for (int q = 0; q < 2; ++q) {
+              const int kq = k + 2 * q;
+              r[q] = T(0);
+              if (kq < 0 || kq >= m2) continue;
+              const T p = interp_predict<T>(va[q], vb[q], vc[q], vd[q], hb, hc, hd, INTERP);
+              const bool own = ownj && ke + q >= 2 && ke + q < 2 + S::kW / 2;
+              r[q] = fine_point<T, COMP>(a, d, hwin, hlo, xv[2 * q], p, ebT, ebr, own, (uint32_t)(c0 + ke + q),
+                                         COMP ? 0u : (uint32_t)kr[q], acc);
+            }
           }
           st2(E + ((2 * eo + 1) * S::kXJ + 2 * cj) * S::kEK + ke, r[0], r[1]);
         }
@@ -493,15 +545,29 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
           kr = K + S::kR2 * S::kL2 + row * S::kL01 + o + ke;
         }
         T r[2];
+        if (IN) {
+          const T p2[2] = {interp_predict<T>(va[0], vb[0], vc[0], vd[0], true, true, true, INTERP),
+                           interp_predict<T>(va[1], vb[1], vc[1], vd[1], true, true, true, INTERP)};
+          const bool own2[2] = {ke >= 2 && ke < 2 + S::kW / 2, ke + 1 >= 2 && ke + 1 < 2 + S::kW / 2};
+          const T x2[2] = {xv[0], xv[2]};
+          uint32_t k2[2] = {0u, 0u}, q2[2];
+          if (!COMP) k2[0] = kr[0], k2[1] = kr[1];
+          fine_points<T, COMP, 2>(a, d, hwin, hlo, x2, p2, ebT, ebr, own2, (uint32_t)(c0 + ke), k2, acc, r, q2);
+          if (COMP) {
+            if (own2[0]) a.codes[c0 + ke] = (uint16_t)q2[0];
+            if (own2[1]) a.codes[c0 + ke + 1] = (uint16_t)q2[1];
+          }
+        } else {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int kq = k + 2 * q;
-          r[q] = T(0);
-          if (!IN && (kq < 0 || kq >= m2)) continue;
-          const T p = interp_predict<T>(va[q], vb[q], vc[q], vd[q], hb, hc, hd, INTERP);
-          const bool own = ke + q >= 2 && ke + q < 2 + S::kW / 2;
-          r[q] = fine_point<T, COMP>(a, d, hwin, hlo, xv[2 * q], p, ebT, ebr, own, (uint32_t)(c0 + ke + q),
-                                     COMP ? 0u : (uint32_t)kr[q], acc);
+          for (int q = 0; q < 2; ++q) {
+            const int kq = k + 2 * q;
+            r[q] = T(0);
+            if (kq < 0 || kq >= m2) continue;
+            const T p = interp_predict<T>(va[q], vb[q], vc[q], vd[q], hb, hc, hd, INTERP);
+            const bool own = ke + q >= 2 && ke + q < 2 + S::kW / 2;
+            r[q] = fine_point<T, COMP>(a, d, hwin, hlo, xv[2 * q], p, ebT, ebr, own, (uint32_t)(c0 + ke + q),
+                                       COMP ? 0u : (uint32_t)kr[q], acc);
+          }
         }
         st2(E + (i4 * S::kXJ + j21) * S::kEK + ke, r[0], r[1]);
       }
@@ -547,13 +613,13 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
               for (int u = 0; u < 4; ++u) kin[u] = kr[u];
             }
           }
+          T p4[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const T p = interp_predict<T>(e[u + 2], e[u + 3], e[u + 1], e[u + 4], true, true, true, INTERP);
-            r[u] = fine_point<T, COMP>(a, d, hwin, hlo, xo[u], p, ebT, ebr, true, ci + u, kin[u], acc,
-                                       COMP && kPackCodes ? &cq[u] : nullptr);
-          }
-          if (COMP && kPackCodes) put_codes4(a.codes + ci, cq);
+          for (int u = 0; u < 4; ++u)
+            p4[u] = interp_predict<T>(e[u + 2], e[u + 3], e[u + 1], e[u + 4], true, true, true, INTERP);
+          const bool own4[4] = {true, true, true, true};
+          fine_points<T, COMP, 4>(a, d, hwin, hlo, xo, p4, ebT, ebr, own4, ci, kin, acc, r, cq);
+          if (COMP) put_codes4(a.codes + ci, cq);
         } else {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {

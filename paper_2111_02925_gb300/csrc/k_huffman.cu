@@ -7,12 +7,14 @@
 //    two-queue merge (leaf first on equal weight), depths by a bounded walk to
 //    the root, frequency halving while a code is longer than 24 bits, then
 //    canonical codewords ordered by (length, symbol).
-//  * encode_kernel    one warp per chunk of the code stream: chunk bit count,
-//    decoupled look-back over the chunks for the payload word offset and the
-//    unpredictable-value offset, then packing through a shared-memory word
-//    ring (MSB first) and the gather of the chunk's unpredictable values.
-//  * decode_kernel    one thread per chunk: 12-bit direct table, canonical
-//    comparison for longer codes; counts zero codes for the recover step.
+//  * count_kernel / emit_kernel  one warp per chunk of the code stream: chunk
+//    bit counts and their prefix (a scan, or decoupled look-back over the
+//    chunks for the payload word offset and the unpredictable-value offset),
+//    then packing through a shared-memory word ring (MSB first) and the
+//    gather of the chunk's unpredictable values.
+//  * decode_kernel    one thread per 512-code sub-block: 12-bit direct table,
+//    canonical comparison for longer codes; counts zero codes for the
+//    recover step.
 #include "internal.cuh"
 
 namespace sz3g {
@@ -760,8 +762,10 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
   return v;
 }
 
-// Decoupled look-back: exclusive prefix of chunk j's value, whole warp.
-__device__ unsigned long long lookback(unsigned long long* stat, long long j, DevState* st) {
+// Decoupled look-back: exclusive prefix of chunk j's value, whole warp.  A
+// wait longer than `limit` polls gives up, raises the timeout flag and
+// returns the partial prefix (the caller's status then reports the timeout).
+__device__ unsigned long long lookback(unsigned long long* stat, long long j, DevState* st, uint32_t limit) {
   const int lane = threadIdx.x & 31;
   unsigned long long excl = 0;
   long long base = j - 1;
@@ -771,7 +775,7 @@ __device__ unsigned long long lookback(unsigned long long* stat, long long j, De
     unsigned long long v = idx >= 0 ? ld_acquire(stat + idx) : kFlagInc;
     const unsigned not_ready = __ballot_sync(0xffffffffu, (v >> 62) == 0);
     if (not_ready) {
-      if (++spins > kSpinLimit) {
+      if ((uint32_t)++spins > limit) {
         if (lane == 0) atomicOr(&st->flags, kFlagTimeout);
         return excl;
       }
@@ -810,6 +814,8 @@ struct EncArgs {
   void* unpred_out;             // raw mode: unpredictable values (or null)
   int mode;                     // kEncodeStream / kEncodeRaw
   int emit_payload;             // 0: only gather unpredictable values
+  uint32_t spin_limit;          // look-back wait limit
+  long long silent_chunk;       // injected failure: this chunk never publishes (-1: none)
 };
 
 constexpr int kEncWarps = 8;
@@ -834,6 +840,8 @@ __device__ __forceinline__ unsigned long long map_code_to_input(const PassMap& m
 }
 
 // Pass 1 of the encoder: bits (as 32-bit words) and zero codes of every chunk.
+// One warp per chunk; each lane takes 16-byte pieces of eight codes, four
+// pieces in flight before their table entries are looked up.
 __global__ void __launch_bounds__(kEncWarps * 32) count_kernel(const uint16_t* __restrict__ codes,
                                                                const uint32_t* __restrict__ table, unsigned long long n,
                                                                unsigned long long n_chunks, uint32_t chunk,
@@ -846,20 +854,30 @@ __global__ void __launch_bounds__(kEncWarps * 32) count_kernel(const uint16_t* _
     const uint32_t cnt = (uint32_t)min((unsigned long long)chunk, n - i0);
     const uint16_t* cp = codes + i0;
     uint32_t bits = 0, zeros = 0;
-    for (uint32_t t = lane * 8; t < cnt; t += 256) {
-      if (t + 8 <= cnt) {
-        const uint4 v = *reinterpret_cast<const uint4*>(cp + t);
-        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+    auto piece = [&](const uint4& v) {
+      const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t c0 = wv[q] & 0xffffu, c1 = wv[q] >> 16;
-          bits += (table[c0] >> 24) + (table[c1] >> 24);
-          zeros += (c0 == 0) + (c1 == 0);
-        }
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t c0 = wv[q] & 0xffffu, c1 = wv[q] >> 16;
+        bits += (__ldg(table + c0) >> 24) + (__ldg(table + c1) >> 24);
+        zeros += (c0 == 0) + (c1 == 0);
+      }
+    };
+    uint32_t t = lane * 8;
+    for (; t + 3 * 256 + 8 <= cnt; t += 4 * 256) {  // four whole pieces
+      uint4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const uint4*>(cp + t + u * 256));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) piece(v[u]);
+    }
+    for (; t < cnt; t += 256) {
+      if (t + 8 <= cnt) {
+        piece(__ldg(reinterpret_cast<const uint4*>(cp + t)));
       } else {
         for (uint32_t u = t; u < cnt; ++u) {
           const uint32_t c = cp[u];
-          bits += table[c] >> 24;
+          bits += __ldg(table + c) >> 24;
           zeros += c == 0;
         }
       }
@@ -929,13 +947,14 @@ __global__ void __launch_bounds__(kEncWarps * 32) emit_kernel(const EncArgs a, c
         zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
       }
       words = (bits + 31) >> 5;
-      if (lane == 0) {
+      const bool publish = (long long)j != a.silent_chunk;
+      if (lane == 0 && publish) {
         st_release(wstat + j, (j == 0 ? kFlagInc : kFlagAgg) | words);
         st_release(zstat + j, (j == 0 ? kFlagInc : kFlagAgg) | zeros);
       }
-      wexcl = lookback(wstat, (long long)j, st);
-      zexcl = lookback(zstat, (long long)j, st);
-      if (lane == 0 && j > 0) {
+      wexcl = lookback(wstat, (long long)j, st, a.spin_limit);
+      zexcl = lookback(zstat, (long long)j, st, a.spin_limit);
+      if (lane == 0 && j > 0 && publish) {
         st_release(wstat + j, kFlagInc | (wexcl + words));
         st_release(zstat + j, kFlagInc | (zexcl + zeros));
       }
@@ -1115,7 +1134,7 @@ size_t scan_state_bytes(unsigned long long n) { return 256 + 8 * ((n + kScanTile
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* in, unsigned long long n,
                                                             unsigned long long* out, uint32_t limit,
                                                             unsigned long long expect, int check_expect,
-                                                            unsigned char* state, DevState* st) {
+                                                            unsigned char* state, DevState* st, uint32_t spin_limit) {
   __shared__ unsigned long long s_warp[32];
   __shared__ unsigned long long s_excl;
   __shared__ unsigned long long s_tile;
@@ -1140,7 +1159,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const uint32_t* in, 
   unsigned long long run = block_exclusive_scan(sum, s_warp, &agg);
   if (threadIdx.x < 32) {
     if (threadIdx.x == 0) st_release(stat + t, (t == 0 ? kFlagInc : kFlagAgg) | agg);
-    const unsigned long long ex = lookback(stat, (long long)t, st);
+    const unsigned long long ex = lookback(stat, (long long)t, st, spin_limit);
     if (threadIdx.x == 0) {
       if (t > 0) st_release(stat + t, kFlagInc | (ex + agg));
       s_excl = ex;
@@ -1165,7 +1184,8 @@ int launch_scan(const uint32_t* in, unsigned long long n, unsigned long long* ou
   const unsigned long long ntiles = (n + kScanTile - 1) / kScanTile;
   SZ3G_LAUNCH(kKScan, s,
               scan_kernel<<<(unsigned)(ntiles ? ntiles : 1), kScanThreads, 0, s>>>(
-                  in, n, out, limit, expect, check_expect, (unsigned char*)state, st));
+                  in, n, out, limit, expect, check_expect, (unsigned char*)state, st,
+                  g_debug.wait_limit ? g_debug.wait_limit : (uint32_t)kSpinLimit));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
@@ -1174,10 +1194,198 @@ size_t encode_scratch_bytes(unsigned long long n_chunks) {
          2 * ((scan_state_bytes(n_chunks) + 255) & ~255ull);
 }
 
+// ---------------------------------------------------------------------------
+// Stream-mode packing for fields whose chunk word offsets and zero-code
+// prefixes are known (count pass, then chunk_prefix_kernel).  One warp per
+// chunk, rounds of 256 codes (eight per lane): each lane concatenates the
+// codewords of its codes 0-3 and of its codes 4-7 into two strings in 64-bit
+// registers (a string of four codewords over 64 bits, which needs codewords
+// averaging more than 16 bits, is placed as two strings of two), a warp scan
+// gives each lane's bit offset, the strings are OR-ed into a shared-memory
+// word ring and the round's full words leave as coalesced stores.  Zero codes (unpredictable values) are looked for once per round
+// (a 16-bit minimum over the lane's codes); only rounds that hold one scan
+// their positions and gather the values.
+// ---------------------------------------------------------------------------
+constexpr int kPackRing = 202;  // words: two guard words, one round (<= 256 x 24 bits) and the carried word
+
+// OR a string of n (1..64) bits, right-aligned in (hi, lo), into buf so that
+// it covers bits [e - n, e) (MSB first).  z zero bits follow it in its last
+// word; shifted left by z the string spans the words (e-1)/32 - 2 .. (e-1)/32
+// -- 32-bit funnel shifts only.
+// shared-memory OR of a nonzero word, predicated (no branch)
+__device__ __forceinline__ void red_or_nz(uint32_t* p, uint32_t v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q red.shared.or.b32 [%0], %1;\n\t}" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(p)),
+               "r"(v)
+               : "memory");
+}
+__device__ __forceinline__ void ring_or(uint32_t* buf, uint32_t hi, uint32_t lo, uint32_t e) {
+  const uint32_t we = (e - 1) >> 5, z = (0u - e) & 31u;
+  red_or_nz(&buf[we], lo << z);
+  red_or_nz(&buf[we - 1], __funnelshift_l(lo, hi, z));
+  red_or_nz(&buf[we - 2], __funnelshift_l(hi, 0u, z));
+}
+
+template <typename U>
+__global__ void __launch_bounds__(kEncWarps * 32, 4) pack_kernel(const EncArgs a, const __grid_constant__ PassMap map) {
+  __shared__ uint32_t ring[kEncWarps][kPackRing];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* buf = ring[w] + 2;  // buf[-2], buf[-1]: guards for strings that end in word 0 or 1
+  for (int k = lane; k < kPackRing; k += 32) ring[w][k] = 0;
+  __syncwarp();
+  DevState* st = a.st;
+  const unsigned long long nu = st->n_unpred;
+  const unsigned long long off_table = SZ3G_HEADER_BYTES + pad8(nu * a.esz);
+  const unsigned long long off_chunks = off_table + pad8(3ull * st->n_used);
+  const unsigned long long off_sub = off_chunks + pad8(a.n_chunks * 4);
+  const unsigned long long off_payload = off_sub + pad8(a.n_chunks * (a.nsb - 1) * 2);
+  U* unp = reinterpret_cast<U*>(a.d_out + SZ3G_HEADER_BYTES);
+  const uint32_t* table = a.table;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * kEncWarps;
+  for (unsigned long long j = (unsigned long long)blockIdx.x * kEncWarps + w; j < a.n_chunks; j += nwarps) {
+    const unsigned long long i0 = j * a.chunk;
+    const uint32_t cnt = (uint32_t)min((unsigned long long)a.chunk, a.n - i0);
+    const uint16_t* cp = a.codes + i0;
+    const uint32_t words = a.cwords[j];
+    const unsigned long long wexcl = a.wexcl[j];
+    unsigned long long zpos = a.zexcl[j];
+    if (lane == 0 && j == a.n_chunks - 1) st->n_words = wexcl + words;
+    if (off_payload + 4 * (wexcl + words) > a.out_capacity) {
+      if (lane == 0) atomicOr(&st->flags, kFlagCapacity);
+      continue;
+    }
+    if (lane == 0) *reinterpret_cast<uint32_t*>(a.d_out + off_chunks + 4 * j) = words;
+    uint32_t* pay = reinterpret_cast<uint32_t*>(a.d_out + off_payload) + wexcl;
+    uint16_t* sub = a.nsb > 1 ? reinterpret_cast<uint16_t*>(a.d_out + off_sub) + j * (a.nsb - 1) : nullptr;
+    if (sub && lane == 0)  // sub-blocks past the end of a short chunk are empty
+      for (uint32_t b = (cnt + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK; b + 1 < a.nsb; ++b) sub[b] = 0;
+    uint32_t wpos = 0, carry = 0, sbits = 0;
+    for (uint32_t r0 = 0; r0 < cnt; r0 += 256) {
+      const uint32_t t = r0 + lane * 8;
+      uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);  // 0xffff: no code
+      if (t + 8 <= cnt) {
+        v = *reinterpret_cast<const uint4*>(cp + t);
+      } else if (t < cnt) {
+        uint32_t h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) h[q] = t + q < cnt ? cp[t + q] : 0xffffu;
+        v = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+      }
+      const uint32_t cw[4] = {v.x, v.y, v.z, v.w};
+      // the codewords of the lane's two halves, right-aligned in (hi, lo)
+      // (codewords are at most 24 bits: 32-bit funnel shifts)
+      uint32_t ahi[2] = {0u, 0u}, alo[2] = {0u, 0u}, n2[2] = {0u, 0u};
+      auto append = [&](int q, uint32_t e) {  // e = len << 24 | codeword
+        const uint32_t L = e >> 24;
+        ahi[q >> 2] = __funnelshift_l(alo[q >> 2], ahi[q >> 2], L);
+        alo[q >> 2] = (alo[q >> 2] << L) | (e & 0xffffffu);
+        n2[q >> 2] += L;
+      };
+      if (r0 + 256 <= cnt) {  // every lane has eight codes
+        uint32_t e8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) e8[q] = __ldg(table + ((q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) append(q, e8[q]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t c = (q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu;
+          append(q, c != 0xffffu ? __ldg(table + c) : 0u);
+        }
+      }
+      const uint32_t nb = n2[0] + n2[1];
+      uint32_t incl = nb;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t round_bits = __shfl_sync(0xffffffffu, incl, 31);
+      uint32_t o = carry + incl - nb;  // bit offset of the lane's strings in the ring
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t n = n2[h];
+        o += n;  // the end of the half's string
+        if (n <= 64) {
+          if (n) ring_or(buf, ahi[h], alo[h], o);
+        } else {  // four codewords over 64 bits: the half as two strings of two
+          uint32_t op = o - n;
+          for (int p = 0; p < 2; ++p) {
+            uint32_t xh = 0u, xl = 0u, m = 0u;
+            for (int q = 4 * h + 2 * p; q < 4 * h + 2 * p + 2; ++q) {
+              const uint32_t c = (q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu;
+              const uint32_t e = c != 0xffffu ? __ldg(table + c) : 0u;
+              xh = __funnelshift_l(xl, xh, e >> 24);
+              xl = (xl << (e >> 24)) | (e & 0xffffffu);
+              m += e >> 24;
+            }
+            op += m;
+            if (m) ring_or(buf, xh, xl, op);
+          }
+        }
+      }
+      sbits += round_bits;
+      if ((r0 & 256) || r0 + 256 >= cnt) {  // a sub-block ends with this round
+        const uint32_t b = r0 >> 9;
+        if (sub && lane == 0 && b + 1 < a.nsb) sub[b] = (uint16_t)sbits;
+        sbits = 0;
+      }
+      __syncwarp();
+      const uint32_t total = carry + round_bits, full = total >> 5;
+      for (uint32_t k = lane; k < full; k += 32) pay[wpos + k] = buf[k];
+      wpos += full;
+      const uint32_t rest = buf[full];
+      __syncwarp();
+      for (uint32_t k = lane; k <= full; k += 32) buf[k] = 0;
+      __syncwarp();
+      carry = total & 31;
+      if (lane == 0) buf[0] = carry ? rest : 0u;
+      __syncwarp();
+      // unpredictable values of the round, in code order
+      if (nu) {
+        const uint32_t mn = __vminu2(__vminu2(v.x, v.y), __vminu2(v.z, v.w));
+        const bool has0 = (mn & 0xffffu) == 0 || (mn >> 16) == 0;
+        if (__any_sync(0xffffffffu, has0)) {
+          uint32_t nz = 0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) nz += ((q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu) == 0;
+          uint32_t zincl = nz;
+#pragma unroll
+          for (int s = 1; s < 32; s <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, zincl, s);
+            if (lane >= s) zincl += y;
+          }
+          unsigned long long zr = zpos + zincl - nz;
+          bool nonfinite = false;
+          for (int q = 0; q < 8 && nz; ++q) {
+            const uint32_t c = (q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu;
+            if (c == 0) {
+              const U x = reinterpret_cast<const U*>(a.x)[map_code_to_input(map, i0 + t + q)];
+              unp[zr++] = x;
+              // the quantizer sends every NaN / Inf to the unpredictable list
+              nonfinite |= sizeof(U) == 4 ? ((x & 0x7f800000u) == 0x7f800000u)
+                                          : ((x & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
+            }
+          }
+          if (nonfinite) atomicOr(&st->flags, kFlagNonFinite);
+          zpos += __shfl_sync(0xffffffffu, zincl, 31);
+        }
+      }
+    }
+    if (carry && lane == 0) pay[wpos] = buf[0];
+    __syncwarp();
+    if (lane == 0) buf[0] = 0;
+    __syncwarp();
+  }
+}
+
 // count -> two scans -> emit (or, stream mode on at most kOnePassMaxChunks
 // chunks, emit alone).  scratch: encode_scratch_bytes(n_chunks).
 constexpr unsigned long long kOnePassMaxChunks = 1024;
 static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch, cudaStream_t s) {
+  a.spin_limit = g_debug.wait_limit ? g_debug.wait_limit : (uint32_t)kSpinLimit;
+  a.silent_chunk = g_debug.silent_chunk;
   const unsigned long long nch = a.n_chunks;
   const size_t a4 = (nch * 4 + 255) & ~255ull, a8 = (nch * 8 + 255) & ~255ull,
                as = (scan_state_bytes(nch) + 255) & ~255ull;
@@ -1202,6 +1410,22 @@ static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch
     return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
   }
   SZ3G_LAUNCH(kKEncode, s, count_kernel<<<nb, kEncWarps * 32, 0, s>>>(a.codes, a.table, a.n, nch, a.chunk, cw, cz));
+  if (a.mode == kEncodeStream && a.emit_payload) {
+    // the prefixes (the compressor's workspace, this scratch included, was
+    // cleared when it started), then the packing kernel
+    int rc = launch_scan(cw, nch, we, 0, 0, 0, s1, a.st, s, true);
+    if (rc) return rc;
+    rc = launch_scan(cz, nch, ze, 0, 0, 0, s2, a.st, s, true);
+    if (rc) return rc;
+    a.cwords = cw;
+    a.wexcl = we;
+    a.zexcl = ze;
+    if (a.esz == 4)
+      SZ3G_LAUNCH(kKEncode, s, pack_kernel<uint32_t><<<nb, kEncWarps * 32, 0, s>>>(a, *map));
+    else
+      SZ3G_LAUNCH(kKEncode, s, pack_kernel<unsigned long long><<<nb, kEncWarps * 32, 0, s>>>(a, *map));
+    return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+  }
   // stream mode: the compressor's workspace (this scratch included) was cleared when it started
   const bool zeroed = a.mode == kEncodeStream;
   int rc = launch_scan(cw, nch, we, 0, 0, 0, s1, a.st, s, zeroed);

@@ -1131,6 +1131,7 @@ struct QLevel {
   int dep;          // index of the level whose reconstruction this one reads (-1: none in the queue)
   uint32_t first;   // queue index of the level's first chunk
   uint32_t chunks;  // chunks of up to kQueueChunk consecutive tiles
+  uint32_t extra;   // injected failure (tests): chunks awaited beyond the dependency's own (else 0)
 };
 
 constexpr uint32_t kQueueChunk = 8;  // tiles per ticket (one level's, consecutive)
@@ -1145,7 +1146,8 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 
 template <typename T, bool COMP>
 __global__ void __launch_bounds__(kLevelThreads, 3) level_queue_kernel(const QLevel<T>* __restrict__ q, int nlev,
-                                                                    uint32_t total, uint32_t* counters) {
+                                                                    uint32_t total, uint32_t* counters,
+                                                                    uint32_t spin_limit) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ LevelDesc s_d;
   __shared__ LevelArgs<T> s_a;
@@ -1238,11 +1240,11 @@ __global__ void __launch_bounds__(kLevelThreads, 3) level_queue_kernel(const QLe
       s_late = 0;
       const int dep = q[li].dep;
       if (dep >= 0) {
-        const uint32_t need = q[dep].chunks;
+        const uint32_t need = q[dep].chunks + q[li].extra;
         volatile uint32_t* abort_flag = counters + 1 + nlev;  // set by the first wait that gave up
-        int spins = 0;
+        uint32_t spins = 0;
         while (ld_acquire_u32(&counters[1 + dep]) < need) {
-          if (++spins > kQueueSpinLimit || *abort_flag) {
+          if (++spins > spin_limit || *abort_flag) {
             s_late = 1;
             atomicOr(&s_a.st->flags, kFlagTimeout);
             atomicExch(counters + 1 + nlev, 1u);
@@ -1350,6 +1352,7 @@ static int queue_launch_t(LevelQueue* q, std::vector<unsigned char>& host, size_
   std::unordered_map<int, int> last;  // field -> its latest queued (so nearest coarser) level
   size_t smem = 0;
   uint32_t total = 0;
+  bool stalled = false;
   for (int i : order) {
     const QItem<T>& it = items[i];
     QLevel<T> e;
@@ -1365,6 +1368,12 @@ static int queue_launch_t(LevelQueue* q, std::vector<unsigned char>& host, size_
     e.dep = f == last.end() ? -1 : f->second;
     e.first = total;
     e.chunks = (e.d.ntiles + kQueueChunk - 1) / kQueueChunk;
+    // injected stall: the first level at or after the given index that waits on another
+    e.extra = 0;
+    if (!stalled && g_debug.queue_stall >= 0 && (long long)lv.size() >= g_debug.queue_stall && e.dep >= 0) {
+      e.extra = 1;
+      stalled = true;
+    }
     total += e.chunks;
     smem = std::max(smem, sm);
     last[it.field] = (int)lv.size();
@@ -1388,7 +1397,7 @@ static int queue_launch_t(LevelQueue* q, std::vector<unsigned char>& host, size_
   SZ3G_LAUNCH(COMP ? kKLevelQuantize : kKLevelRecover, s,
               kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(
                   reinterpret_cast<const QLevel<T>*>((unsigned char*)q->dev + dev_off), (int)lv.size(), total,
-                  counters));
+                  counters, g_debug.wait_limit ? g_debug.wait_limit : (uint32_t)kQueueSpinLimit));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 

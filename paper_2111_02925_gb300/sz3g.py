@@ -91,6 +91,7 @@ _SIGS = {
     "sz3g_batch_queue_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "sz3g_batch_destroy": [_vp],
     "sz3g_graph_cache": [C.c_int],
+    "sz3g_debug_inject": [C.c_int, C.c_longlong],
     "sz3g_trim": [],
     "sz3g_bitplane_bound": [_u64, C.POINTER(_u64)],
     "sz3g_bitplane_encode": [_u32, _vp, _u64, C.c_double, _vp, _sz, C.POINTER(_sz), _vp],
@@ -495,6 +496,14 @@ def workspace(p: Params, for_decompress: bool, device="cuda"):
     torch = _torch()
     n = sz3g_workspace_size(p, int(for_decompress))
     return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+DEBUG_RESET, DEBUG_WAIT_LIMIT, DEBUG_QUEUE_STALL, DEBUG_SILENT_CHUNK, DEBUG_ALLOC_FAIL = 0, 1, 2, 3, 4
+
+
+def sz3g_debug_inject(kind: int, value: int = 0) -> int:
+    """Failure injection for tests (see include/sz3g.h); returns the status."""
+    return int(load().sz3g_debug_inject(kind, value))
 
 
 def sz3g_graph_cache(on: bool) -> None:
