@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--workload", default="field", choices=["field", "batch", "selector", "lossless", "pastri"])
     ap.add_argument("--train-fields", type=int, default=400)
     ap.add_argument("--fields", type=int, default=256)
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch / selector / lossless figures")
+    ap.add_argument("--extra-train-fields", type=int, default=160)
     return ap.parse_args()
 
 
@@ -483,18 +485,9 @@ def run_selector(args):
     exhaustive trial; reported: stream size / compression ratio under a fixed
     choice, the exhaustive, sampling and learned selections, and the time of
     each selection."""
-    import multiprocessing as mp
-
     import numpy as np
 
-    rng = np.random.default_rng(31)
-    jobs = []
-    for i in range(args.train_fields):
-        shape = tuple(int(v) for v in rng.integers(32, 65, 3))
-        eb = float(np.exp(rng.uniform(np.log(1e-5), np.log(1e-2))))
-        jobs.append((shape, 20000 + i, int(rng.integers(0, 17)), eb))
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:  # before any GPU call
-        labels = pool.map(_label_field, jobs)
+    jobs, labels = label_jobs(args.train_fields)  # before any GPU call
     import torch
 
     from oracle import mlp as M
@@ -794,6 +787,181 @@ def run_pastri(args):
     return 0
 
 
+def extras(args, dev, xd, out, nb, pool_labels):
+    """Figures of the extensions on the same box, outside the timed region,
+    each bounded and each wrapped so that a failure only records its error:
+    the uneven 256-field batch (batched graph vs one call per field), the
+    per-level selector on the 1024^3 fronts field at REL 1e-4 (fixed,
+    sampled, exhaustive and learned choices; network trained on the GPU on
+    oracle-labelled small fields) and the lossless stage on the headline
+    stream."""
+    import numpy as np
+    import torch
+
+    from paper_2111_02925_gb300 import synthetic as S
+    from paper_2111_02925_gb300 import sz3g as G
+
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    res = {}
+
+    def ev_ms(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    # (1) batch: 256 uneven fields, one step = compress all + decompress all
+    try:
+        t0 = time.perf_counter()
+        mix = S.batch_shapes(args.fields, 4)
+        xs = [grf_gpu(d, 4000 + g, dev).reshape(-1) for g, (d, _, _) in enumerate(mix)]
+        params = [G.make_params(d, eb, eb_mode=G.REL, interp=it) for d, eb, it in mix]
+        caps = [G.sz3g_compress_bound(p) for p in params]
+        streams = [torch.empty(c, dtype=torch.uint8, device=dev) for c in caps]
+        outs = [torch.empty_like(x) for x in xs]
+        wsc = [G.workspace(p, False, dev) for p in params]
+        wsd = [G.workspace(p, True, dev) for p in params]
+        nbs = [0] * len(xs)
+
+        def per_field():
+            for i, (p, x, s, w) in enumerate(zip(params, xs, streams, wsc)):
+                rc, nbs[i] = G.sz3g_compress(p, x.data_ptr(), s.data_ptr(), s.numel(), w.data_ptr(), w.numel(), sh)
+                assert rc == 0
+            for s, n, o, w in zip(streams, nbs, outs, wsd):
+                assert G.sz3g_decompress(s.data_ptr(), n, o.data_ptr(), o.numel() * 4, w.data_ptr(), w.numel(),
+                                         sh) == 0
+
+        t_single = ev_ms(per_field, 2)
+        del wsc, wsd
+        bc = G.Batch(params, [x.data_ptr() for x in xs], [s.data_ptr() for s in streams], caps)
+        bd = G.Batch(None, [s.data_ptr() for s in streams], [o.data_ptr() for o in outs],
+                     [o.numel() * 4 for o in outs], in_bytes=list(nbs), decompress=True)
+        try:
+            bc.configure(64, 0)  # branch counts the autotuner picks on this mix
+            bd.configure(256, 0)
+            t_batch = ev_ms(lambda: (bc.run(sh), bd.run(sh)), 3)
+            rc, nb2, _ = bc.results()
+            ok = rc == 0 and list(nb2) == list(nbs) and bd.results()[0] == 0
+        finally:
+            bc.close()
+            bd.close()
+        in_bytes = sum(x.numel() * 4 for x in xs)
+        res["batch"] = {"fields": len(xs), "input_bytes": int(in_bytes), "batched_ms": t_batch,
+                        "per_field_ms": t_single, "batched_GB/s": in_bytes / (t_batch * 1e-3) / 1e9,
+                        "per_field_GB/s": in_bytes / (t_single * 1e-3) / 1e9, "speedup": t_single / t_batch,
+                        "streams_identical": bool(ok), "branches": {"compress": 64, "decompress": 256},
+                        "seconds": time.perf_counter() - t0}
+        del xs, streams, outs
+    except Exception as exc:  # noqa: BLE001
+        res["batch"] = {"error": repr(exc)[:300]}
+    torch.cuda.empty_cache()
+
+    # (2) selector at the 1024^3 fronts field, REL 1e-4
+    try:
+        from oracle import mlp as M
+
+        t0 = time.perf_counter()
+        jobs, labels = pool_labels
+        feats, ys = [], []
+        for (shape, seed, fr, eb), lab in zip(jobs, labels):
+            x = torch.from_numpy(S.grf_fronts(shape, seed, fr).reshape(-1)).to(dev)
+            feats.extend(G.sz3g_select_features(G.make_params(shape, eb, eb_mode=G.REL), x.data_ptr(), 8, seed, sh))
+            ys.extend(lab)
+        feats = np.array(feats)
+        ys = np.array(ys, np.int32)
+        w = torch.from_numpy(M.init(feats, 5).astype(np.float32)).to(dev)
+        fd = torch.from_numpy(feats.astype(np.float32).reshape(-1)).to(dev)
+        yd = torch.from_numpy(ys).to(dev)
+        md = torch.ones(len(ys) * 8, dtype=torch.uint8, device=dev)
+        loss = G.sz3g_mlp_train(w.data_ptr(), fd.data_ptr(), md.data_ptr(), yd.data_ptr(), len(ys), 0.3, 3000, sh)
+        n = 1024
+        x = fronts_gpu((n, n, n), 5, 16, dev).reshape(-1)
+        p = G.make_params((n, n, n), 1e-4, eb_mode=G.REL, interp=G.LINEAR)
+        cap = G.sz3g_compress_bound(p)
+        o = torch.empty(cap, dtype=torch.uint8, device=dev)
+        wsx = G.workspace(p, False, dev)
+
+        def size(q):
+            rc, m = G.sz3g_compress(q, x.data_ptr(), o.data_ptr(), cap, wsx.data_ptr(), wsx.numel(), sh)
+            assert rc == 0
+            return m
+
+        def sel_ms(fn):
+            fn()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            return r, (time.perf_counter() - t) * 1e3
+
+        ch_s, ms_s = sel_ms(lambda: G.sz3g_select_sampled(p, x.data_ptr(), 64, 1, sh))
+        ch_l, ms_l = sel_ms(lambda: G.sz3g_select_learned(p, x.data_ptr(), w.data_ptr(), 16, 1, sh))
+        ch_e, ms_e = sel_ms(lambda: G.sz3g_select_sampled(p, x.data_ptr(), 0, 1, sh))
+        raw = x.numel() * 4
+        sizes = {"fixed_linear_012": size(p),
+                 "fixed_cubic_012": size(G.make_params((n, n, n), 1e-4, eb_mode=G.REL, interp=G.CUBIC)),
+                 "exhaustive": size(G.params_for_choices(p, ch_e)), "sampled": size(G.params_for_choices(p, ch_s)),
+                 "learned": size(G.params_for_choices(p, ch_l))}
+        res["selector"] = {"workload": "1024^3 FP32 k^-3 field + 16 tanh fronts (seed 5), REL 1e-4",
+                           "ratio": {k: raw / v for k, v in sizes.items()},
+                           "learned_vs_sampled": sizes["sampled"] / sizes["learned"],
+                           "learned_vs_fixed_linear": sizes["fixed_linear_012"] / sizes["learned"],
+                           "selection_ms": {"sampled": ms_s, "learned": ms_l, "exhaustive": ms_e},
+                           "training": {"fields": len(jobs), "examples": int(len(ys)), "final_loss": loss},
+                           "seconds": time.perf_counter() - t0}
+        del x, o, wsx
+    except Exception as exc:  # noqa: BLE001
+        res["selector"] = {"error": repr(exc)[:300]}
+    torch.cuda.empty_cache()
+
+    # (3) lossless stage on the headline stream
+    try:
+        lcap = G.sz3g_lossless_bound(nb)
+        lz = torch.empty(lcap, dtype=torch.uint8, device=dev)
+        back = torch.empty(nb + 16, dtype=torch.uint8, device=dev)
+        m = [0]
+
+        def comp():
+            rc, m[0] = G.sz3g_lossless_compress(out.data_ptr(), nb, lz.data_ptr(), lcap, sh)
+            assert rc == 0
+
+        def dec():
+            rc, n2 = G.sz3g_lossless_decompress(lz.data_ptr(), m[0], back.data_ptr(), nb, sh)
+            assert rc == 0 and n2 == nb
+
+        tc = ev_ms(comp, 3)
+        td = ev_ms(dec, 3)
+        res["lossless"] = {"stream_bytes": int(nb), "lossless_bytes": int(m[0]), "gain": nb / m[0],
+                           "compress_GB/s": nb / (tc * 1e-3) / 1e9, "decompress_GB/s": nb / (td * 1e-3) / 1e9,
+                           "identical": bool(torch.equal(back[:nb], out[:nb]))}
+    except Exception as exc:  # noqa: BLE001
+        res["lossless"] = {"error": repr(exc)[:300]}
+    return res
+
+
+def label_jobs(n_fields):
+    """Oracle labels (exhaustive trial) of n small training fields, in a spawned
+    process pool: (jobs, labels)."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    rng = np.random.default_rng(31)
+    jobs = []
+    for i in range(n_fields):
+        shape = tuple(int(v) for v in rng.integers(32, 65, 3))
+        eb = float(np.exp(rng.uniform(np.log(1e-5), np.log(1e-2))))
+        jobs.append((shape, 20000 + i, int(rng.integers(0, 17)), eb))
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        labels = pool.map(_label_field, jobs)
+    return jobs, labels
+
+
 def main():
     args = parse()
     if args.workload == "lossless":
@@ -814,6 +982,12 @@ def main():
     from paper_2111_02925_gb300 import sz3g as G
 
     ws, rank, local = dist_env()
+    pool_labels = None
+    if rank == 0 and ws == 1 and not args.no_extras:
+        try:  # the oracle's labels for the selector figure, before any GPU call
+            pool_labels = label_jobs(args.extra_train_fields)
+        except Exception:  # noqa: BLE001
+            pool_labels = None
     if ws > 1:
         import torch.distributed as dist
 
@@ -979,6 +1153,9 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(x)
+    ext = None
+    if rank == 0 and ws == 1 and not args.no_extras:
+        ext = extras(args, dev, xd, out, nb, pool_labels or ([], []))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
@@ -992,6 +1169,7 @@ def main():
             "max_abs_error": maxerr, "stream_bytes": nb, "n_unpred": n_unpred,
             "roofline": roof, "kernels_ms_per_step": {k: v[0] for k, v in sorted(kern.items())},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "eb_sweep": sweep,
+            "extras": ext,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -43,7 +43,12 @@ namespace sz3g {
 // double-buffered ones -- compress 0.62 vs 0.73 ms, recover 0.48 vs 0.53 ms.
 // Recover stages the tile's code rows with 16-byte cp.async pieces spread
 // over the threads (true) or one bulk copy per row (false).
-constexpr bool kCodeCpAsync = true;
+constexpr bool kCodeCpAsync = false;
+// Code rows by one bulk copy per row, each row's thread announcing its own
+// bytes with an arrival on the tile's mbarrier (which then expects one
+// arrival per staged row): no byte count through shared memory and no extra
+// barrier (true); or the two forms above (false).
+constexpr bool kCodeRowArrive = true;
 // Pass 2 moves the four codes of a run as one 8-, two 4- or four 2-byte
 // accesses by the alignment of the run's first code (true), or one 2-byte
 // access per code (false).
@@ -298,8 +303,10 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
     s_bad = 0;
     s_timeout = 0;
     s_bytes[0] = s_bytes[1] = 0;
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    // recover with per-row arrivals: one arrival per staged code row
+    const uint32_t arrivals = (!COMP && kCodeRowArrive) ? (uint32_t)(S::kR2 + S::kR1 + S::kR0) : 1u;
+    mbar_init(&bar[0], arrivals);
+    mbar_init(&bar[1], arrivals);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -342,6 +349,27 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
   auto issue = [&](uint32_t tile, int b) {
     int A0, A1, A2;
     tile_origin(tile, A0, A1, A2);
+    if (!COMP && kCodeRowArrive) {
+      // row r by thread r: its arrival announces its bytes (thread 0 also the
+      // coarse box's), then its copy
+      if (tid < S::kR2 + S::kR1 + S::kR0) {
+        int which, slot;
+        bool valid;
+        const long long c0 = row_c0(A0, A1, A2, tid, which, slot, valid);
+        const uint32_t bytes = valid ? (which == 2 ? S::kL2 * 2 : S::kL01 * 2) : 0u;
+        fence_proxy_async_smem();
+        mbar_expect_tx(&bar[b], bytes + (tid == 0 ? d.tensor_bytes : 0u));
+        if (tid == 0)
+          tma_load_3d(Cs + b * CB, &tmc, A2 / 2 - 4, A1 / 2 - 1, S::kHas0 ? A0 / 2 - 1 : 0, &bar[b]);
+        if (valid) {
+          long long al;
+          int o;
+          code_row(c0, &al, &o);
+          bulk_load(Ks + b * KB + slot, a.codes + al, bytes, &bar[b]);
+        }
+      }
+      return;
+    }
     if (tid == 0) {
       fence_proxy_async_smem();
       if (COMP || kCodeCpAsync) {
@@ -393,7 +421,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
     }
   };
   auto finish_issue = [&](int b) {  // after a barrier that follows issue(b)
-    if (!COMP && tid == 0 && !kCodeCpAsync) {
+    if (!COMP && tid == 0 && !kCodeCpAsync && !kCodeRowArrive) {
       mbar_expect_tx(&bar[b], d.tensor_bytes + s_bytes[b]);
       s_bytes[b] = 0;
     }
@@ -413,7 +441,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
     const bool has_next = ST == 2 && next < d.ntiles;
     if (ST == 1) {  // the buffer is free: the previous tile ended with a barrier
       issue(tile, 0);
-      if (!COMP && !kCodeCpAsync) {
+      if (!COMP && !kCodeCpAsync && !kCodeRowArrive) {
         __syncthreads();
         finish_issue(0);
       }

@@ -458,8 +458,20 @@ __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsign
     uk(i)[j] = key_of(i, j);
   }
   __syncthreads();
-  // 1. every round sorted by (weight, symbol)
-  for (int i = 0; i < kSpecRounds; ++i) block_rank_sort(uk(i), sk(i), K);
+  // 1. every round sorted by (weight, symbol): the ranks of all rounds' keys
+  //    at once (distinct keys: rank = keys below it)
+  for (int it = tid; it < kSpecRounds * K; it += blockDim.x) {
+    const int i = it / K, j = it - i * K;
+    const unsigned long long* in = uk(i);
+    const unsigned long long k = in[j];
+    int r = 0, q = 0;
+    for (; q + 1 < K; q += 2) {
+      const ulonglong2 pr = *reinterpret_cast<const ulonglong2*>(in + q);
+      r += (pr.x < k) + (pr.y < k);
+    }
+    if (q < K) r += in[q] < k;
+    sk(i)[r] = k;
+  }
   __syncthreads();
   for (int it = tid; it < kSpecRounds * (K + 4); it += blockDim.x) {
     const int i = it / (K + 4), t = it - i * (K + 4);
@@ -527,17 +539,21 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   uint32_t* s_seg = reinterpret_cast<uint32_t*>(smem + kCbOffPar);  // 2048 segment counts (free until step 2)
   uint32_t mk0 = 0, mk1 = 0;
   bool bad = false;
-#pragma unroll 8
-  for (int k = 0; k < 64; ++k) {
-    const int sy = 1024 * k + 32 * warp + lane;
-    const uint32_t v = __ldcg(hist + sy);
-    bad |= v != 0 && sy >= (int)nsym;
-    const unsigned m = __ballot_sync(0xffffffffu, v != 0 && sy < (int)nsym);
-    if (lane == (k & 31)) {
-      if (k < 32) mk0 = m;
-      else mk1 = m;
+  for (int k0 = 0; k0 < 64; k0 += 16) {  // sixteen loads in flight, then their ballots
+    uint32_t v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = __ldcg(hist + 1024 * (k0 + u) + 32 * warp + lane);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = k0 + u, sy = 1024 * k + 32 * warp + lane;
+      bad |= v[u] != 0 && sy >= (int)nsym;
+      const unsigned m = __ballot_sync(0xffffffffu, v[u] != 0 && sy < (int)nsym);
+      if (lane == (k & 31)) {
+        if (k < 32) mk0 = m;
+        else mk1 = m;
+      }
+      if (lane == 0) s_seg[32 * k + warp] = (uint32_t)__popc(m);
     }
-    if (lane == 0) s_seg[32 * k + warp] = (uint32_t)__popc(m);
   }
   if (bad) atomicOr(&st->flags, kFlagCorrupt);
   if (tid == 0) st->n_unpred = hist[0];  // code 0 marks an unpredictable value
@@ -558,13 +574,23 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   uint32_t* nf = in_smem ? (uint32_t*)(smem + kCbOffNf) : g->nf;
   uint16_t* symord = in_smem ? (uint16_t*)(smem + kCbOffSym) : g->symord;
   __syncthreads();
-  for (int k = 0; k < 64; ++k) {
-    const unsigned m = __shfl_sync(0xffffffffu, k < 32 ? mk0 : mk1, k & 31);
-    if ((m >> lane) & 1u) {
-      const int sy = 1024 * k + 32 * warp + lane;
-      const uint32_t pos = s_seg[32 * k + warp] + (uint32_t)__popc(m & ((1u << lane) - 1u));
-      ka[pos] = ((unsigned long long)__ldcg(hist + sy) << 16) | pos;  // position in symbol order
-      symord[pos] = (uint16_t)sy;
+  for (int k0 = 0; k0 < 64; k0 += 16) {  // the used bins' counts, sixteen loads in flight
+    unsigned m[16];
+    uint32_t v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = k0 + u;
+      m[u] = __shfl_sync(0xffffffffu, k < 32 ? mk0 : mk1, k & 31);
+      v[u] = ((m[u] >> lane) & 1u) ? __ldcg(hist + 1024 * k + 32 * warp + lane) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      if ((m[u] >> lane) & 1u) {
+        const int k = k0 + u, sy = 1024 * k + 32 * warp + lane;
+        const uint32_t pos = s_seg[32 * k + warp] + (uint32_t)__popc(m[u] & ((1u << lane) - 1u));
+        ka[pos] = ((unsigned long long)v[u] << 16) | pos;  // position in symbol order
+        symord[pos] = (uint16_t)sy;
+      }
     }
   }
   if (len_out || code_out)
@@ -678,15 +704,20 @@ __global__ void __launch_bounds__(kCbThreads) codebook_rounds_kernel(const uint3
   // bins 1024 k + 32 w + lane (coalesced), a ballot marks each segment's
   // used bins; lane l keeps the masks of its warp's segments l and l + 32
   uint32_t mk0 = 0, mk1 = 0;
-#pragma unroll 8
-  for (int k = 0; k < 64; ++k) {
-    const int sy = 1024 * k + 32 * warp + lane;
-    const unsigned m = __ballot_sync(0xffffffffu, sy < (int)nsym && __ldcg(hist + sy) != 0);
-    if (lane == (k & 31)) {
-      if (k < 32) mk0 = m;
-      else mk1 = m;
+  for (int k0 = 0; k0 < 64; k0 += 16) {  // sixteen loads in flight, then their ballots
+    uint32_t v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = __ldcg(hist + 1024 * (k0 + u) + 32 * warp + lane);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = k0 + u, sy = 1024 * k + 32 * warp + lane;
+      const unsigned m = __ballot_sync(0xffffffffu, sy < (int)nsym && v[u] != 0);
+      if (lane == (k & 31)) {
+        if (k < 32) mk0 = m;
+        else mk1 = m;
+      }
+      if (lane == 0) s_seg[32 * k + warp] = (uint32_t)__popc(m);
     }
-    if (lane == 0) s_seg[32 * k + warp] = (uint32_t)__popc(m);
   }
   __syncthreads();
   const uint32_t c0 = s_seg[2 * tid], c1 = s_seg[2 * tid + 1];
@@ -704,13 +735,23 @@ __global__ void __launch_bounds__(kCbThreads) codebook_rounds_kernel(const uint3
   unsigned long long* ka = in_smem ? (unsigned long long*)smem : g.keys;
   unsigned long long* kb = in_smem ? (unsigned long long*)(smem + kSmemLeaves * 8) : g.keys2;
   __syncthreads();
-  for (int k = 0; k < 64; ++k) {
-    const unsigned m = __shfl_sync(0xffffffffu, k < 32 ? mk0 : mk1, k & 31);
-    if ((m >> lane) & 1u) {
-      const int sy = 1024 * k + 32 * warp + lane;
-      const uint32_t pos = s_seg[32 * k + warp] + (uint32_t)__popc(m & ((1u << lane) - 1u));
-      const uint32_t f = __ldcg(hist + sy) >> r;
-      ka[pos] = ((unsigned long long)(f ? f : 1u) << 16) | pos;
+  for (int k0 = 0; k0 < 64; k0 += 16) {  // the used bins' counts, sixteen loads in flight
+    unsigned m[16];
+    uint32_t v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = k0 + u;
+      m[u] = __shfl_sync(0xffffffffu, k < 32 ? mk0 : mk1, k & 31);
+      v[u] = ((m[u] >> lane) & 1u) ? __ldcg(hist + 1024 * k + 32 * warp + lane) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      if ((m[u] >> lane) & 1u) {
+        const int k = k0 + u;
+        const uint32_t pos = s_seg[32 * k + warp] + (uint32_t)__popc(m[u] & ((1u << lane) - 1u));
+        const uint32_t f = v[u] >> r;
+        ka[pos] = ((unsigned long long)(f ? f : 1u) << 16) | pos;
+      }
     }
   }
   __syncthreads();
