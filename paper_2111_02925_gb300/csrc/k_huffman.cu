@@ -15,6 +15,8 @@
 //  * decode_kernel    one thread per 512-code sub-block: 12-bit direct table,
 //    canonical comparison for longer codes; counts zero codes for the
 //    recover step.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace sz3g {
@@ -1267,6 +1269,150 @@ __device__ __forceinline__ void ring_or(uint32_t* buf, uint32_t hi, uint32_t lo,
   red_or_nz(&buf[we - 2], __funnelshift_l(hi, 0u, z));
 }
 
+// Packs chunk j (words payload words at word offset wexcl, its zero codes
+// after zexcl earlier ones) with the calling warp; buf: the warp's ring.
+template <typename U>
+__device__ __forceinline__ void pack_chunk(const EncArgs& a, const PassMap& map, uint32_t* buf, int lane,
+                                           unsigned long long j, uint32_t words, unsigned long long wexcl,
+                                           unsigned long long zexcl, unsigned long long off_chunks,
+                                           unsigned long long off_sub, unsigned long long off_payload, U* unp,
+                                           unsigned long long nu) {
+  DevState* st = a.st;
+  const uint32_t* table = a.table;
+  const unsigned long long i0 = j * a.chunk;
+  const uint32_t cnt = (uint32_t)min((unsigned long long)a.chunk, a.n - i0);
+  const uint16_t* cp = a.codes + i0;
+  unsigned long long zpos = zexcl;
+  if (lane == 0 && j == a.n_chunks - 1) st->n_words = wexcl + words;
+  if (off_payload + 4 * (wexcl + words) > a.out_capacity) {
+    if (lane == 0) atomicOr(&st->flags, kFlagCapacity);
+    return;
+  }
+  if (lane == 0) *reinterpret_cast<uint32_t*>(a.d_out + off_chunks + 4 * j) = words;
+  uint32_t* pay = reinterpret_cast<uint32_t*>(a.d_out + off_payload) + wexcl;
+  uint16_t* sub = a.nsb > 1 ? reinterpret_cast<uint16_t*>(a.d_out + off_sub) + j * (a.nsb - 1) : nullptr;
+  if (sub && lane == 0)  // sub-blocks past the end of a short chunk are empty
+    for (uint32_t b = (cnt + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK; b + 1 < a.nsb; ++b) sub[b] = 0;
+  uint32_t wpos = 0, carry = 0, sbits = 0;
+  for (uint32_t r0 = 0; r0 < cnt; r0 += 256) {
+    const uint32_t t = r0 + lane * 8;
+    uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);  // 0xffff: no code
+    if (t + 8 <= cnt) {
+      v = *reinterpret_cast<const uint4*>(cp + t);
+    } else if (t < cnt) {
+      uint32_t h[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) h[q] = t + q < cnt ? cp[t + q] : 0xffffu;
+      v = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+    }
+    const uint32_t cw[4] = {v.x, v.y, v.z, v.w};
+    // the codewords of the lane's two halves, right-aligned in (hi, lo)
+    // (codewords are at most 24 bits: 32-bit funnel shifts)
+    uint32_t ahi[2] = {0u, 0u}, alo[2] = {0u, 0u}, n2[2] = {0u, 0u};
+    auto append = [&](int q, uint32_t e) {  // e = len << 24 | codeword
+      const uint32_t L = e >> 24;
+      ahi[q >> 2] = __funnelshift_l(alo[q >> 2], ahi[q >> 2], L);
+      alo[q >> 2] = (alo[q >> 2] << L) | (e & 0xffffffu);
+      n2[q >> 2] += L;
+    };
+    if (r0 + 256 <= cnt) {  // every lane has eight codes
+      uint32_t e8[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) e8[q] = __ldg(table + ((q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu));
+#pragma unroll
+      for (int q = 0; q < 8; ++q) append(q, e8[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t c = (q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu;
+        append(q, c != 0xffffu ? __ldg(table + c) : 0u);
+      }
+    }
+    const uint32_t nb = n2[0] + n2[1];
+    uint32_t incl = nb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t round_bits = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t o = carry + incl - nb;  // bit offset of the lane's strings in the ring
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t n = n2[h];
+      o += n;  // the end of the half's string
+      if (n <= 64) {
+        if (n) ring_or(buf, ahi[h], alo[h], o);
+      } else {  // four codewords over 64 bits: the half as two strings of two
+        uint32_t op = o - n;
+        for (int p = 0; p < 2; ++p) {
+          uint32_t xh = 0u, xl = 0u, m = 0u;
+          for (int q = 4 * h + 2 * p; q < 4 * h + 2 * p + 2; ++q) {
+            const uint32_t c = (q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu;
+            const uint32_t e = c != 0xffffu ? __ldg(table + c) : 0u;
+            xh = __funnelshift_l(xl, xh, e >> 24);
+            xl = (xl << (e >> 24)) | (e & 0xffffffu);
+            m += e >> 24;
+          }
+          op += m;
+          if (m) ring_or(buf, xh, xl, op);
+        }
+      }
+    }
+    sbits += round_bits;
+    if ((r0 & 256) || r0 + 256 >= cnt) {  // a sub-block ends with this round
+      const uint32_t b = r0 >> 9;
+      if (sub && lane == 0 && b + 1 < a.nsb) sub[b] = (uint16_t)sbits;
+      sbits = 0;
+    }
+    __syncwarp();
+    const uint32_t total = carry + round_bits, full = total >> 5;
+    for (uint32_t k = lane; k < full; k += 32) pay[wpos + k] = buf[k];
+    wpos += full;
+    const uint32_t rest = buf[full];
+    __syncwarp();
+    for (uint32_t k = lane; k <= full; k += 32) buf[k] = 0;
+    __syncwarp();
+    carry = total & 31;
+    if (lane == 0) buf[0] = carry ? rest : 0u;
+    __syncwarp();
+    // unpredictable values of the round, in code order
+    if (nu) {
+      const uint32_t mn = __vminu2(__vminu2(v.x, v.y), __vminu2(v.z, v.w));
+      const bool has0 = (mn & 0xffffu) == 0 || (mn >> 16) == 0;
+      if (__any_sync(0xffffffffu, has0)) {
+        uint32_t nz = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) nz += ((q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu) == 0;
+        uint32_t zincl = nz;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, zincl, s);
+          if (lane >= s) zincl += y;
+        }
+        unsigned long long zr = zpos + zincl - nz;
+        bool nonfinite = false;
+        for (int q = 0; q < 8 && nz; ++q) {
+          const uint32_t c = (q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu;
+          if (c == 0) {
+            const U x = reinterpret_cast<const U*>(a.x)[map_code_to_input(map, i0 + t + q)];
+            unp[zr++] = x;
+            // the quantizer sends every NaN / Inf to the unpredictable list
+            nonfinite |= sizeof(U) == 4 ? ((x & 0x7f800000u) == 0x7f800000u)
+                                        : ((x & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
+          }
+        }
+        if (nonfinite) atomicOr(&st->flags, kFlagNonFinite);
+        zpos += __shfl_sync(0xffffffffu, zincl, 31);
+      }
+    }
+  }
+  if (carry && lane == 0) pay[wpos] = buf[0];
+  __syncwarp();
+  if (lane == 0) buf[0] = 0;
+  __syncwarp();
+}
+
 template <typename U>
 __global__ void __launch_bounds__(kEncWarps * 32, 4) pack_kernel(const EncArgs a, const __grid_constant__ PassMap map) {
   __shared__ uint32_t ring[kEncWarps][kPackRing];
@@ -1281,143 +1427,128 @@ __global__ void __launch_bounds__(kEncWarps * 32, 4) pack_kernel(const EncArgs a
   const unsigned long long off_sub = off_chunks + pad8(a.n_chunks * 4);
   const unsigned long long off_payload = off_sub + pad8(a.n_chunks * (a.nsb - 1) * 2);
   U* unp = reinterpret_cast<U*>(a.d_out + SZ3G_HEADER_BYTES);
-  const uint32_t* table = a.table;
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kEncWarps;
-  for (unsigned long long j = (unsigned long long)blockIdx.x * kEncWarps + w; j < a.n_chunks; j += nwarps) {
-    const unsigned long long i0 = j * a.chunk;
-    const uint32_t cnt = (uint32_t)min((unsigned long long)a.chunk, a.n - i0);
-    const uint16_t* cp = a.codes + i0;
-    const uint32_t words = a.cwords[j];
-    const unsigned long long wexcl = a.wexcl[j];
-    unsigned long long zpos = a.zexcl[j];
-    if (lane == 0 && j == a.n_chunks - 1) st->n_words = wexcl + words;
-    if (off_payload + 4 * (wexcl + words) > a.out_capacity) {
-      if (lane == 0) atomicOr(&st->flags, kFlagCapacity);
-      continue;
+  for (unsigned long long j = (unsigned long long)blockIdx.x * kEncWarps + w; j < a.n_chunks; j += nwarps)
+    pack_chunk<U>(a, map, buf, lane, j, a.cwords[j], a.wexcl[j], a.zexcl[j], off_chunks, off_sub, off_payload, unp,
+                  nu);
+}
+
+
+// Bits (as 32-bit words) and zero codes of chunk j, counted by the calling
+// warp: four 16-byte pieces of eight codes in flight per lane.
+__device__ __forceinline__ void chunk_counts(const uint16_t* __restrict__ codes, const uint32_t* __restrict__ table,
+                                             unsigned long long n, uint32_t chunk, unsigned long long j, int lane,
+                                             uint32_t* words, uint32_t* zeros) {
+  const unsigned long long i0 = j * chunk;
+  const uint32_t cnt = (uint32_t)min((unsigned long long)chunk, n - i0);
+  const uint16_t* cp = codes + i0;
+  uint32_t bits = 0, zc = 0;
+  auto piece = [&](const uint4& v) {
+    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t c0 = wv[q] & 0xffffu, c1 = wv[q] >> 16;
+      bits += (__ldg(table + c0) >> 24) + (__ldg(table + c1) >> 24);
+      zc += (c0 == 0) + (c1 == 0);
     }
-    if (lane == 0) *reinterpret_cast<uint32_t*>(a.d_out + off_chunks + 4 * j) = words;
-    uint32_t* pay = reinterpret_cast<uint32_t*>(a.d_out + off_payload) + wexcl;
-    uint16_t* sub = a.nsb > 1 ? reinterpret_cast<uint16_t*>(a.d_out + off_sub) + j * (a.nsb - 1) : nullptr;
-    if (sub && lane == 0)  // sub-blocks past the end of a short chunk are empty
-      for (uint32_t b = (cnt + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK; b + 1 < a.nsb; ++b) sub[b] = 0;
-    uint32_t wpos = 0, carry = 0, sbits = 0;
-    for (uint32_t r0 = 0; r0 < cnt; r0 += 256) {
-      const uint32_t t = r0 + lane * 8;
-      uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);  // 0xffff: no code
-      if (t + 8 <= cnt) {
-        v = *reinterpret_cast<const uint4*>(cp + t);
-      } else if (t < cnt) {
-        uint32_t h[8];
+  };
+  uint32_t t = lane * 8;
+  for (; t + 3 * 256 + 8 <= cnt; t += 4 * 256) {  // four whole pieces
+    uint4 v[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) h[q] = t + q < cnt ? cp[t + q] : 0xffffu;
-        v = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
-      }
-      const uint32_t cw[4] = {v.x, v.y, v.z, v.w};
-      // the codewords of the lane's two halves, right-aligned in (hi, lo)
-      // (codewords are at most 24 bits: 32-bit funnel shifts)
-      uint32_t ahi[2] = {0u, 0u}, alo[2] = {0u, 0u}, n2[2] = {0u, 0u};
-      auto append = [&](int q, uint32_t e) {  // e = len << 24 | codeword
-        const uint32_t L = e >> 24;
-        ahi[q >> 2] = __funnelshift_l(alo[q >> 2], ahi[q >> 2], L);
-        alo[q >> 2] = (alo[q >> 2] << L) | (e & 0xffffffu);
-        n2[q >> 2] += L;
-      };
-      if (r0 + 256 <= cnt) {  // every lane has eight codes
-        uint32_t e8[8];
+    for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const uint4*>(cp + t + u * 256));
 #pragma unroll
-        for (int q = 0; q < 8; ++q) e8[q] = __ldg(table + ((q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu));
-#pragma unroll
-        for (int q = 0; q < 8; ++q) append(q, e8[q]);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const uint32_t c = (q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu;
-          append(q, c != 0xffffu ? __ldg(table + c) : 0u);
-        }
-      }
-      const uint32_t nb = n2[0] + n2[1];
-      uint32_t incl = nb;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const uint32_t round_bits = __shfl_sync(0xffffffffu, incl, 31);
-      uint32_t o = carry + incl - nb;  // bit offset of the lane's strings in the ring
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t n = n2[h];
-        o += n;  // the end of the half's string
-        if (n <= 64) {
-          if (n) ring_or(buf, ahi[h], alo[h], o);
-        } else {  // four codewords over 64 bits: the half as two strings of two
-          uint32_t op = o - n;
-          for (int p = 0; p < 2; ++p) {
-            uint32_t xh = 0u, xl = 0u, m = 0u;
-            for (int q = 4 * h + 2 * p; q < 4 * h + 2 * p + 2; ++q) {
-              const uint32_t c = (q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu;
-              const uint32_t e = c != 0xffffu ? __ldg(table + c) : 0u;
-              xh = __funnelshift_l(xl, xh, e >> 24);
-              xl = (xl << (e >> 24)) | (e & 0xffffffu);
-              m += e >> 24;
-            }
-            op += m;
-            if (m) ring_or(buf, xh, xl, op);
-          }
-        }
-      }
-      sbits += round_bits;
-      if ((r0 & 256) || r0 + 256 >= cnt) {  // a sub-block ends with this round
-        const uint32_t b = r0 >> 9;
-        if (sub && lane == 0 && b + 1 < a.nsb) sub[b] = (uint16_t)sbits;
-        sbits = 0;
-      }
-      __syncwarp();
-      const uint32_t total = carry + round_bits, full = total >> 5;
-      for (uint32_t k = lane; k < full; k += 32) pay[wpos + k] = buf[k];
-      wpos += full;
-      const uint32_t rest = buf[full];
-      __syncwarp();
-      for (uint32_t k = lane; k <= full; k += 32) buf[k] = 0;
-      __syncwarp();
-      carry = total & 31;
-      if (lane == 0) buf[0] = carry ? rest : 0u;
-      __syncwarp();
-      // unpredictable values of the round, in code order
-      if (nu) {
-        const uint32_t mn = __vminu2(__vminu2(v.x, v.y), __vminu2(v.z, v.w));
-        const bool has0 = (mn & 0xffffu) == 0 || (mn >> 16) == 0;
-        if (__any_sync(0xffffffffu, has0)) {
-          uint32_t nz = 0;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) nz += ((q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu) == 0;
-          uint32_t zincl = nz;
-#pragma unroll
-          for (int s = 1; s < 32; s <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, zincl, s);
-            if (lane >= s) zincl += y;
-          }
-          unsigned long long zr = zpos + zincl - nz;
-          bool nonfinite = false;
-          for (int q = 0; q < 8 && nz; ++q) {
-            const uint32_t c = (q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu;
-            if (c == 0) {
-              const U x = reinterpret_cast<const U*>(a.x)[map_code_to_input(map, i0 + t + q)];
-              unp[zr++] = x;
-              // the quantizer sends every NaN / Inf to the unpredictable list
-              nonfinite |= sizeof(U) == 4 ? ((x & 0x7f800000u) == 0x7f800000u)
-                                          : ((x & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
-            }
-          }
-          if (nonfinite) atomicOr(&st->flags, kFlagNonFinite);
-          zpos += __shfl_sync(0xffffffffu, zincl, 31);
-        }
+    for (int u = 0; u < 4; ++u) piece(v[u]);
+  }
+  for (; t < cnt; t += 256) {
+    if (t + 8 <= cnt) {
+      piece(__ldg(reinterpret_cast<const uint4*>(cp + t)));
+    } else {
+      for (uint32_t u = t; u < cnt; ++u) {
+        const uint32_t c = cp[u];
+        bits += __ldg(table + c) >> 24;
+        zc += c == 0;
       }
     }
-    if (carry && lane == 0) pay[wpos] = buf[0];
-    __syncwarp();
-    if (lane == 0) buf[0] = 0;
-    __syncwarp();
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    bits += __shfl_xor_sync(0xffffffffu, bits, o);
+    zc += __shfl_xor_sync(0xffffffffu, zc, o);
+  }
+  *words = (bits + 31) >> 5;
+  *zeros = zc;
+}
+
+// Stream-mode encoder in one pass for any number of chunks: tiles of
+// kEncWarps consecutive chunks taken in ticket order; each warp counts its
+// chunk, the tile's totals are published and the words and zero codes before
+// the tile found by one decoupled look-back over the tiles (warp 0), then
+// each warp packs its chunk (its codes read again, from the cache).  ticket,
+// wstat and zstat start at zero (the compressor's workspace is cleared when
+// it starts).
+template <typename U>
+__global__ void __launch_bounds__(kEncWarps * 32, 4) tile_pack_kernel(const EncArgs a,
+                                                                       const __grid_constant__ PassMap map,
+                                                                       uint32_t* ticket, unsigned long long* wstat,
+                                                                       unsigned long long* zstat) {
+  __shared__ uint32_t ring[kEncWarps][kPackRing];
+  __shared__ uint32_t s_words[kEncWarps], s_zeros[kEncWarps], s_tile;
+  __shared__ unsigned long long s_we, s_ze;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* buf = ring[w] + 2;  // buf[-2], buf[-1]: guards for strings that end in word 0 or 1
+  for (int k = lane; k < kPackRing; k += 32) ring[w][k] = 0;
+  __syncwarp();
+  DevState* st = a.st;
+  const unsigned long long nu = st->n_unpred;
+  const unsigned long long off_table = SZ3G_HEADER_BYTES + pad8(nu * a.esz);
+  const unsigned long long off_chunks = off_table + pad8(3ull * st->n_used);
+  const unsigned long long off_sub = off_chunks + pad8(a.n_chunks * 4);
+  const unsigned long long off_payload = off_sub + pad8(a.n_chunks * (a.nsb - 1) * 2);
+  U* unp = reinterpret_cast<U*>(a.d_out + SZ3G_HEADER_BYTES);
+  const unsigned long long ntiles = (a.n_chunks + kEncWarps - 1) / kEncWarps;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const unsigned long long tile = s_tile;
+    if (tile >= ntiles) break;
+    const unsigned long long j = tile * kEncWarps + w;
+    uint32_t words = 0, zeros = 0;
+    if (j < a.n_chunks) chunk_counts(a.codes, a.table, a.n, a.chunk, j, lane, &words, &zeros);
+    if (lane == 0) {
+      s_words[w] = words;
+      s_zeros[w] = zeros;
+    }
+    __syncthreads();
+    if (w == 0) {
+      uint32_t aw = lane < kEncWarps ? s_words[lane] : 0u, az = lane < kEncWarps ? s_zeros[lane] : 0u;
+      for (int o = 16; o > 0; o >>= 1) {
+        aw += __shfl_xor_sync(0xffffffffu, aw, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+      }
+      if (lane == 0) {
+        st_release(wstat + tile, (tile == 0 ? kFlagInc : kFlagAgg) | aw);
+        st_release(zstat + tile, (tile == 0 ? kFlagInc : kFlagAgg) | az);
+      }
+      const unsigned long long ew = lookback(wstat, (long long)tile, st, a.spin_limit);
+      const unsigned long long ez = lookback(zstat, (long long)tile, st, a.spin_limit);
+      if (lane == 0) {
+        if (tile > 0) {
+          st_release(wstat + tile, kFlagInc | (ew + aw));
+          st_release(zstat + tile, kFlagInc | (ez + az));
+        }
+        s_we = ew;
+        s_ze = ez;
+      }
+    }
+    __syncthreads();
+    unsigned long long wexcl = s_we, zexcl = s_ze;
+    for (int q = 0; q < w; ++q) {
+      wexcl += s_words[q];
+      zexcl += s_zeros[q];
+    }
+    if (j < a.n_chunks)
+      pack_chunk<U>(a, map, buf, lane, j, words, wexcl, zexcl, off_chunks, off_sub, off_payload, unp, nu);
+    __syncthreads();  // the tile's shared counts are read before the next ticket overwrites them
   }
 }
 
@@ -1448,6 +1579,19 @@ static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch
       SZ3G_LAUNCH(kKEncode, s, emit_kernel<uint32_t, true><<<nb, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze));
     else
       SZ3G_LAUNCH(kKEncode, s, emit_kernel<unsigned long long, true><<<nb, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze));
+    return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+  }
+  if (a.mode == kEncodeStream && a.emit_payload) {
+    // counts, prefixes and packing in one pass over tiles of chunks (cw[0]
+    // is the ticket, we / ze the tiles' look-back states, all cleared with
+    // the compressor's workspace)
+    const unsigned long long ntiles = (nch + kEncWarps - 1) / kEncWarps;
+    const unsigned ng = (unsigned)std::min<unsigned long long>(ntiles, 152ull * 4);
+    if (a.esz == 4)
+      SZ3G_LAUNCH(kKEncode, s, tile_pack_kernel<uint32_t><<<ng, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze));
+    else
+      SZ3G_LAUNCH(kKEncode, s,
+                  tile_pack_kernel<unsigned long long><<<ng, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze));
     return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
   }
   SZ3G_LAUNCH(kKEncode, s, count_kernel<<<nb, kEncWarps * 32, 0, s>>>(a.codes, a.table, a.n, nch, a.chunk, cw, cz));

@@ -31,8 +31,6 @@
 #include <unordered_map>
 #include <vector>
 
-#include <cstdlib>
-
 #include "internal.cuh"
 #include "level_common.cuh"
 
@@ -894,19 +892,6 @@ bool fine_eligible(const Plan& pl, int k, bool comp, const void* x, const unsign
                    const void* Rout, bool to_field);
 template <typename T, bool COMP>
 int launch_fine(const Plan& pl, int k, const LevelArgs<T>& a, bool to_field, cudaStream_t s);
-// k_sweep.cu: the plane-pair sweep form of the same levels
-template <typename T, bool COMP>
-int launch_sweep(const Plan& pl, int k, const LevelArgs<T>& a, bool to_field, cudaStream_t s);
-// The sweep kernel takes the grids of the register-blocked kernel when the
-// environment sets SZ3G_SWEEP=1 (read once); the register-blocked kernel
-// measured faster on the benchmark field, so it stays the default.
-static bool sweep_enabled() {
-  static const bool on = [] {
-    const char* e = getenv("SZ3G_SWEEP");
-    return e && e[0] == '1';
-  }();
-  return on;
-}
 template <typename T>
 int launch_fine_slabs(const Plan& pl, const LevelArgs<T>& a, cudaStream_t s, int slabs,
                       const std::function<int(unsigned long long, unsigned long long)>& done);
@@ -1083,8 +1068,7 @@ static int level_desc(const Plan& pl, int k, const LevelArgs<T>& a, bool allow_t
 template <typename T, bool COMP>
 static int run_level(const Plan& pl, int k, const LevelArgs<T>& a, cudaStream_t s) {
   if ((COMP || a.codes_padded) && fine_eligible(pl, k, COMP, a.x, a.xs, a.Rc, a.Rout, !COMP && k == 0))
-    return sweep_enabled() && pl.N < (1ull << 31) ? launch_sweep<T, COMP>(pl, k, a, !COMP && k == 0, s)
-                                                  : launch_fine<T, COMP>(pl, k, a, !COMP && k == 0, s);
+    return launch_fine<T, COMP>(pl, k, a, !COMP && k == 0, s);
   LevelDesc d;
   size_t smem = 0;
   CUtensorMap tmx, tmc;
