@@ -60,8 +60,10 @@ CompressWs compress_layout(const Plan& pl, bool rounds = true) {
   w.hist = l.take(kSyms * 4);
   w.table = l.take(kSyms * 4);
   w.range = l.take(range_scratch_bytes(pl));
-  w.cb = l.take(codebook_scratch_bytes());
   w.enc = l.take(encode_scratch_bytes(pl.n_chunks));
+  // cleared at the start of every call up to here; the codebook scratch
+  // needs no clearing
+  w.cb = l.take(codebook_scratch_bytes());
   w.codes = l.take(pl.N * 2);
   w.x1 = l.take(xpyr_bytes(pl));
   // the fused level path never stores the finest grid's reconstruction
@@ -285,7 +287,7 @@ int compress_enqueue_pre(const sz3g_params* p, const Plan& pl, const void* d_in,
   const CompressWs L = compress_layout(pl);
   DevState* st = (DevState*)(ws + L.st);
   *st_out = st;
-  SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.codes, s));  // state, histogram, tables, look-back status
+  SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.cb, s));  // state, histogram, tables, look-back status
   void* X = xpyr_bytes(pl) ? ws + L.x1 : nullptr;
   bool x1_ready = false;
   SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s, X,
@@ -987,7 +989,7 @@ int sz3g_predict_quantize(const sz3g_params* p, const void* d_in, uint16_t* d_co
   unsigned char* ws;
   SZ3G_TRY(get_ws(d_workspace, ws_bytes, L.total, s, own, &ws));
   DevState* st = (DevState*)(ws + L.st);
-  SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.codes, s));
+  SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.cb, s));
   SZ3G_CUDA(cudaMemsetAsync(d_hist, 0, kSyms * 4, s));
   SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s));
   void* R[34];

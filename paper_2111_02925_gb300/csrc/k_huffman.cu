@@ -62,63 +62,6 @@ __device__ __forceinline__ void warp_count(uint32_t* cnt, uint32_t d, bool valid
   if (valid && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&cnt[d], (uint32_t)__popc(m));
 }
 
-// Two-queue Huffman merge over K leaves sorted by (weight, symbol); node ids:
-// leaves 0..K-1, internal K..2K-2 in creation order.  Each step takes the two
-// lightest fronts, the leaf first on equal weight, and appends their parent
-// to the internal queue.  Single thread, branch-free: lw = sorted leaf
-// weights followed by two kInf sentinels, nf = internal weights pre-filled
-// with kInf up to K + 2 (so loads past the created nodes read kInf).  Three
-// weights of each queue are held in registers; every load is used two picks
-// after it was issued.
-template <typename PT>
-__device__ __forceinline__ void two_queue_merge_fast(const uint32_t* lw, int K, uint32_t* nf, PT* parent) {
-  constexpr uint32_t kInf = 0xffffffffu;
-  uint32_t li = 0, ni = 0;
-  uint32_t L0 = lw[0], L1 = lw[1], L2 = lw[2];
-  uint32_t I0 = kInf, I1 = kInf, I2 = kInf;
-  for (uint32_t nn = 0; nn + 1 < (uint32_t)K; ++nn) {
-    uint32_t id[2], w[2];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const bool tl = L0 <= I0;  // the leaf first on equal weight
-      id[t] = tl ? li : (uint32_t)K + ni;
-      w[t] = tl ? L0 : I0;
-      const uint32_t nl = lw[min(li + 3, (uint32_t)K + 1)], ninl = nf[ni + 3];
-      li += tl;
-      ni += !tl;
-      L0 = tl ? L1 : L0;
-      L1 = tl ? L2 : L1;
-      L2 = tl ? nl : L2;
-      I0 = tl ? I0 : I1;
-      I1 = tl ? I1 : I2;
-      I2 = tl ? I2 : ninl;
-    }
-    const uint32_t wn = w[0] + w[1];
-    nf[nn] = wn;
-    // a node created while the queue is short is one of its three fronts
-    I0 = nn == ni ? wn : I0;
-    I1 = nn == ni + 1 ? wn : I1;
-    I2 = nn == ni + 2 ? wn : I2;
-    parent[id[0]] = (PT)(K + nn);
-    parent[id[1]] = (PT)(K + nn);
-  }
-}
-
-// Rank sort of K distinct keys (K <= kRankSortMax): out[rank(k)] = k.
-constexpr int kRankSortMax = 2048;
-__device__ void block_rank_sort(const unsigned long long* in, unsigned long long* out, int K) {
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    const unsigned long long k = in[i];
-    int r = 0, j = 0;
-    for (; j + 1 < K; j += 2) {
-      const ulonglong2 p = *reinterpret_cast<const ulonglong2*>(in + j);
-      r += (p.x < k) + (p.y < k);
-    }
-    if (j < K) r += in[j] < k;
-    out[r] = k;
-  }
-}
-
 // One stable counting pass over K items on the whole block (32 warps): item
 // i has digit dig(i) in [0, NB) and emit(i, r) receives its rank r in the
 // order (digit, input position).  Tiles of one item per thread: the rank is
@@ -197,99 +140,263 @@ __device__ unsigned long long* block_radix_sort_w(unsigned long long* a, unsigne
   return a;
 }
 
-// The two-queue merge (leaf first on equal weight) built in batches, giving
-// the same tree node by node.  The merged consumption order lists leaves and
-// internal nodes by weight, a leaf before an internal node of equal weight,
-// internal nodes in creation order; internal node j has the items at
-// positions 2j and 2j + 1 as children.  Once the weight of node j0 is known,
-// so is its own position P (j0 + the leaves not heavier than it), and every
-// item before P is a leaf or an internal node below j0: nodes j0 .. (P-2)/2
-// are then built at once, each child found by a merge-path search.  Writes
-// W[j] (internal weights) and parent[] of every node but the root.
-// Items at positions q and q + 1 of the merged order when internal nodes
-// [0, jk) are known (q + 1 is before the consumption of node jk): one
-// merge-path search for the leaves among the first q items, then the two
-// queue fronts.  Weights returned, ids (leaf i, internal K + m) in ia / ib.
-__device__ __forceinline__ uint32_t merge_pair(const uint32_t* lw, const uint32_t* W, uint32_t Ku, uint32_t q,
-                                               uint32_t jk, uint32_t* ia, uint32_t* ib) {
-  uint32_t lo = q > jk ? q - jk : 0u, hi = min(q, Ku);
-  while (lo < hi) {
-    const uint32_t a = (lo + hi) >> 1;
-    if (lw[a] <= W[q - a - 1]) lo = a + 1;
-    else hi = a;
+// Sorts nseg arrays seg(0) .. seg(nseg - 1) of n distinct keys each,
+// ascending and in place, by a bitonic network on the whole block.  Each
+// array must hold the next power of two >= n keys: the tail is padded with
+// ~0, above every key.
+template <typename SegFn>
+__device__ void block_bitonic_sort(SegFn seg, int nseg, int n) {
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;
+  const int npad = 1 << lg, tail = npad - n;
+  for (int it = threadIdx.x; it < nseg * tail; it += blockDim.x) {
+    const int s = it / tail;
+    seg(s)[n + it - s * tail] = ~0ull;
   }
-  uint32_t a = lo, m = q - lo, w = 0;
+  __syncthreads();
+  if (lg == 0) return;
+  const int lh = lg - 1, half = 1 << lh;
+  for (int k = 2; k <= npad; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int it = threadIdx.x; it < nseg * half; it += blockDim.x) {
+        const int s = it >> lh, u = it & (half - 1);
+        const int i = ((u & ~(j - 1)) << 1) | (u & (j - 1));  // pair (i, i + j)
+        unsigned long long* A = seg(s);
+        const unsigned long long x = A[i], y = A[i + j];
+        if ((x > y) == ((i & k) == 0)) {
+          A[i] = y;
+          A[i + j] = x;
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// First index in [lo, hi) of the ascending array a whose value exceeds w
+// (hi if none), the same in every lane: a 32-way search by the whole warp,
+// two probe rounds for up to 1024 values.  Lane l probes the last value of
+// block l; the blocks whose last value is not above w form a prefix.
+__device__ __forceinline__ uint32_t warp_upper_bound(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t w) {
+  const uint32_t lane = threadIdx.x & 31;
+  while (lo < hi) {
+    const uint32_t s = (hi - lo + 31) >> 5, b = lo + s * lane;
+    const bool le = b < hi && a[min(b + s, hi) - 1] <= w;
+    const uint32_t nlo = lo + s * (uint32_t)__popc(__ballot_sync(0xffffffffu, le));
+    if (nlo >= hi) return hi;
+    hi = min(nlo + s, hi) - 1;  // the last value of the first such block exceeds w
+    lo = nlo;
+  }
+  return lo;
+}
+
+// The items at positions d and d + 1 of the merge of leaves [a, cL) and
+// internal nodes [m, je) (a leaf before an internal node of equal weight);
+// both exist.  Returns the sum of their weights and their ids (leaf x,
+// internal node Ku + y) in ia / ib.  One merge-path search inside the
+// segment, then the two fronts.
+__device__ __forceinline__ uint32_t seg_pair(const uint32_t* lw, const uint32_t* W, uint32_t Ku, uint32_t a,
+                                             uint32_t cL, uint32_t m, uint32_t je, uint32_t d, uint32_t* ia,
+                                             uint32_t* ib) {
+  const uint32_t nI = je - m;
+  uint32_t lo = d > nI ? d - nI : 0u, hi = min(d, cL - a);  // leaves among the first d items
+  while (lo < hi) {
+    const uint32_t i = (lo + hi) >> 1;
+    if (lw[a + i] <= W[m + d - i - 1]) lo = i + 1;
+    else hi = i;
+  }
+  uint32_t x = a + lo, y = m + d - lo, w = 0;
 #pragma unroll
   for (int t = 0; t < 2; ++t) {
-    const bool leaf = a < Ku && (m >= jk || lw[a] <= W[m]);
-    const uint32_t wt = leaf ? lw[a] : W[m];
-    *(t ? ib : ia) = leaf ? a : Ku + m;
-    w += wt;
-    a += leaf;
-    m += !leaf;
+    const bool leaf = x < cL && (y >= je || lw[x] <= W[y]);
+    w += leaf ? lw[x] : W[y];
+    *(t ? ib : ia) = leaf ? x : Ku + y;
+    x += leaf;
+    y += !leaf;
   }
   return w;
 }
 
-// Consumption position of internal node j of weight w (not the root): j
-// plus the leaves not heavier than w.
-__device__ __forceinline__ uint32_t merge_position(const uint32_t* lw, uint32_t Ku, uint32_t j, uint32_t w) {
-  uint32_t lo = 0, hi = Ku;
-  while (lo < hi) {
-    const uint32_t a = (lo + hi) >> 1;
-    if (lw[a] <= w) lo = a + 1;
-    else hi = a;
-  }
-  return j + lo;
-}
-
-// The two-queue merge (leaf first on equal weight) built in batches, giving
-// the same tree node by node.  The merged consumption order lists leaves and
-// internal nodes by weight, a leaf before an internal node of equal weight,
-// internal nodes in creation order; internal node j has the items at
-// positions 2j and 2j + 1 as children.  Once the weight of node j0 is known,
-// so is its own position P, and every item before P is a leaf or an
-// internal node below j0: nodes j0 .. (P-2)/2 are then built at once.
-// Writes W[j] (internal weights) and parent[] of every node but the root.
-// GROUP: the threads doing it, the whole block (1024) or one warp (32).
+// The two-queue Huffman merge (the two lightest fronts, a leaf first on
+// equal weight) built batch by batch, giving the same tree node by node.
+// S is the merged consumption order: leaves and internal nodes by weight, a
+// leaf before an internal node of equal weight, internal nodes in creation
+// order.  Internal node j has the items S[2j], S[2j+1] as children and sits
+// at position P(j) = j + (leaves not heavier than it) of S.  Once node j0
+// exists, the items of S before P(j0) are those leaves and the internal
+// nodes below j0, so nodes j0+1 .. (P-2)/2, whose children all lie there,
+// are built at once: node j0+1+t from the items 2t, 2t+1 of the segment
+// that merges the leaves and internal nodes not yet consumed.  The next
+// node takes node j0 itself and its neighbour in S (the segment's last item
+// when P is odd, the item after node j0 when it is even).  Quantization-code
+// histograms need about one batch per tree level.  lw: the K >= 2 leaf
+// weights in order; writes W[j] (internal weights) and parent[] of every
+// node but the root (node ids: leaves 0..K-1, internal K + j).  GROUP: the
+// threads doing it, one warp (32) or the whole block; warp 0 of the group
+// runs the searches for P.
 template <int GROUP, typename PT>
 __device__ void batched_merge(const uint32_t* lw, int K, uint32_t* W, PT* parent) {
-  __shared__ uint32_t s_j1;
+  __shared__ uint32_t s_P;
   const uint32_t Ku = (uint32_t)K, r = threadIdx.x & (GROUP - 1);
-  uint32_t j0 = 0;
-  while (j0 + 1 < Ku) {
-    uint32_t j1 = 0;
-    if (r == 0) {
-      uint32_t ia, ib;
-      const uint32_t w = merge_pair(lw, W, Ku, 2 * j0, j0, &ia, &ib);
-      W[j0] = w;
-      parent[ia] = (PT)(Ku + j0);
-      parent[ib] = (PT)(Ku + j0);
-      const uint32_t P = j0 + 2 < Ku ? merge_position(lw, Ku, j0, w) : 2 * Ku - 2;  // the root: never consumed
-      j1 = min(Ku - 2, (P - 2) >> 1);
-      if (GROUP > 32) s_j1 = j1;
-    }
-    if (GROUP > 32) {
-      __syncthreads();
-      j1 = s_j1;
+  // (a, m): leaves and internal nodes consumed by nodes 0 .. j0
+  uint32_t j0 = 0, a = 2, m = 0, w0 = lw[0] + lw[1];
+  if (r == 0) {
+    W[0] = w0;
+    parent[0] = (PT)Ku;
+    parent[1] = (PT)Ku;
+  }
+  while (j0 + 2 < Ku) {  // node Ku - 2 is the root
+    uint32_t P;
+    if (GROUP == 32) {
+      P = j0 + warp_upper_bound(lw, a, Ku, w0);
     } else {
-      j1 = __shfl_sync(0xffffffffu, j1, 0);
-      __syncwarp();
+      if (r < 32) {
+        P = j0 + warp_upper_bound(lw, a, Ku, w0);
+        if (r == 0) s_P = P;
+      }
+      __syncthreads();
+      P = s_P;
     }
-    for (uint32_t j = j0 + 1 + r; j <= j1; j += GROUP) {
+    const uint32_t cL = P - j0, j1 = (P - 2) >> 1;
+    for (uint32_t t = r; j0 + 1 + t <= j1; t += GROUP) {
       uint32_t ia, ib;
-      W[j] = merge_pair(lw, W, Ku, 2 * j, j0, &ia, &ib);
-      parent[ia] = (PT)(Ku + j);
-      parent[ib] = (PT)(Ku + j);
+      const uint32_t w = seg_pair(lw, W, Ku, a, cL, m, j0, 2 * t, &ia, &ib);
+      W[j0 + 1 + t] = w;
+      parent[ia] = (PT)(Ku + j0 + 1 + t);
+      parent[ib] = (PT)(Ku + j0 + 1 + t);
     }
-    if (GROUP > 32) __syncthreads();
-    else __syncwarp();
-    j0 = j1 + 1;
+    if (GROUP == 32) __syncwarp();
+    else __syncthreads();
+    const uint32_t jn = j1 + 1;
+    uint32_t i0, i1;
+    if (P & 1u) {  // the segment's last item, then node j0
+      const bool last_leaf = j0 == m || (cL > a && lw[cL - 1] > W[j0 - 1]);
+      i0 = last_leaf ? cL - 1 : Ku + j0 - 1;
+      i1 = Ku + j0;
+      a = cL;
+      m = j0 + 1;
+    } else {  // node j0, then the next front (internal nodes j0+1 .. j1 exist)
+      const bool leaf = cL < Ku && (j1 == j0 || lw[cL] <= W[j0 + 1]);
+      i0 = Ku + j0;
+      i1 = leaf ? cL : Ku + j0 + 1;
+      a = cL + leaf;
+      m = j0 + 1 + !leaf;
+    }
+    const uint32_t wn = (i0 < Ku ? lw[i0] : W[i0 - Ku]) + (i1 < Ku ? lw[i1] : W[i1 - Ku]);
+    if (r == 0) {
+      W[jn] = wn;
+      parent[i0] = (PT)(Ku + jn);
+      parent[i1] = (PT)(Ku + jn);
+    }
+    if (GROUP == 32) __syncwarp();
+    j0 = jn;
+    w0 = wn;
+  }
+  if (GROUP == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// The compacted histogram: the used symbols of each 1024-bin segment in
+// symbol order, written by hist_compact_kernel for the codebook kernels.
+constexpr int kHcSeg = 1024, kHcNseg = kSyms / kHcSeg, kHcThreads = 256;
+struct HistList {
+  uint32_t n[kHcNseg];  // used symbols of segment b
+  uint2 e[kSyms];       // segment b's at [b kHcSeg, b kHcSeg + n[b]): (count, symbol)
+};
+
+// One CTA per segment: thread t reads bins 256 k + t (k = 0..3, coalesced);
+// the ballot of each 32-bin run marks its used bins, runs in (k, warp) order
+// are symbol order.  Also flags counts outside the alphabet and records the
+// unpredictable count (code 0).
+__global__ void __launch_bounds__(kHcThreads) hist_compact_kernel(const uint32_t* __restrict__ hist, uint32_t nsym,
+                                                                  HistList* H, DevState* st) {
+  __shared__ uint32_t s_run[4 * kHcThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t b0 = blockIdx.x * kHcSeg;
+  uint32_t v[4];
+  unsigned msk[4];
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = __ldcg(hist + b0 + k * kHcThreads + tid);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t sy = b0 + k * kHcThreads + tid;
+    bad |= v[k] != 0 && sy >= nsym;
+    msk[k] = __ballot_sync(0xffffffffu, v[k] != 0 && sy < nsym);
+    if (lane == 0) s_run[k * (kHcThreads / 32) + warp] = (uint32_t)__popc(msk[k]);
+  }
+  __syncthreads();
+  if (warp == 0) {  // exclusive prefix over the 32 runs
+    const uint32_t c = s_run[lane];
+    uint32_t x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    s_run[lane] = x - c;
+    if (lane == 31) H->n[blockIdx.x] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if ((msk[k] >> lane) & 1u) {
+      const uint32_t pos = s_run[k * (kHcThreads / 32) + warp] + (uint32_t)__popc(msk[k] & ((1u << lane) - 1u));
+      H->e[b0 + pos] = make_uint2(v[k], b0 + k * kHcThreads + tid);
+    }
+  if (bad) atomicOr(&st->flags, kFlagCorrupt);
+  if (blockIdx.x == 0 && tid == 0) st->n_unpred = v[0];  // code 0 marks an unpredictable value
+}
+
+// The number K of used symbols (every thread), with s_base[b] the position
+// of segment b's first used symbol.  s_base: kHcNseg + 1 shared words.
+__device__ int used_count(const HistList* H, uint32_t* s_base) {
+  const int lane = threadIdx.x & 31;
+  static_assert(kHcNseg == 64, "two segments per lane");
+  if (threadIdx.x < 32) {
+    const uint32_t c0 = __ldcg(&H->n[2 * lane]), c1 = __ldcg(&H->n[2 * lane + 1]);
+    uint32_t x = c0 + c1;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    s_base[2 * lane] = x - c0 - c1;
+    s_base[2 * lane + 1] = x - c1;
+    if (lane == 31) s_base[kHcNseg] = x;
+  }
+  __syncthreads();
+  return (int)s_base[kHcNseg];
+}
+
+// emit(p, count, symbol) for the used symbol at every position p < K in
+// symbol order, eight entries in flight per thread.
+template <typename EmitFn>
+__device__ __forceinline__ void used_entries(const HistList* H, const uint32_t* s_base, int K, EmitFn emit) {
+  for (int p0 = 0; p0 < K; p0 += 8 * (int)blockDim.x) {
+    uint2 e[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int p = p0 + u * (int)blockDim.x + (int)threadIdx.x;
+      e[u] = make_uint2(0u, 0u);
+      if (p < K) {
+        int lo = 0, hi = kHcNseg - 1;  // the last segment starting at or before p
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_base[mid] <= (uint32_t)p) lo = mid;
+          else hi = mid - 1;
+        }
+        e[u] = __ldcg(&H->e[lo * kHcSeg + (p - (int)s_base[lo])]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int p = p0 + u * (int)blockDim.x + (int)threadIdx.x;
+      if (p < K) emit(p, e[u].x, e[u].y);
+    }
   }
 }
 
-struct CbGlobal {  // global scratch of the codebook kernel (more than kSmemLeaves used symbols)
-  unsigned long long keys[kSyms];
+struct CbGlobal {  // global scratch of the codebook kernels
+  HistList hl;      // the compacted histogram
+  unsigned long long keys[kSyms];  // the key arrays below: more than kSmemLeaves used symbols
   unsigned long long keys2[kSyms];
   uint32_t nf[kSyms + 16];
   uint32_t parent[2 * kSyms];
@@ -344,9 +451,9 @@ __device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* 
     return srt;
   }
   for (int iter = 0; iter < 40; ++iter) {
-    if (K <= kRankSortMax) {
-      block_rank_sort(cur, other, K);
-      srt = other;
+    if (K <= kSmemLeaves) {  // keys in shared memory, room for the padded sort
+      block_bitonic_sort([&](int) { return cur; }, 1, K);
+      srt = cur;
     } else {
       srt = block_radix_sort_w(cur, other, K);
     }
@@ -408,9 +515,9 @@ __device__ bool one_round_lengths(unsigned long long* cur, unsigned long long* o
                                   int K, uint32_t* lw_s, uint32_t* w_s, unsigned long long** srt_out) {
   const int tid = threadIdx.x;
   unsigned long long* srt;
-  if (K <= kRankSortMax) {
-    block_rank_sort(cur, other, K);
-    srt = other;
+  if (K <= kSmemLeaves) {  // keys in shared memory, room for the padded sort
+    block_bitonic_sort([&](int) { return cur; }, 1, K);
+    srt = cur;
   } else {
     srt = block_radix_sort_w(cur, other, K);
   }
@@ -427,27 +534,26 @@ __device__ bool one_round_lengths(unsigned long long* cur, unsigned long long* o
 
 // Speculative halving rounds for small alphabets.  Round i of the length
 // limit uses the weights max(1, f >> i) (halving max(1, f >> 1) i times), so
-// rounds 0..3 are independent: each is sorted (block-wide), the four merges
-// run at once on four warps (batched as in code_lengths; one thread each for
-// small alphabets), and the first round whose
-// codes fit SZ3G_LMAX is the answer, as if the rounds had run one after
-// another.  `ka` holds the leaves in symbol order on entry.  On success the
-// chosen round's leaves sorted by (weight, symbol) are left in ka and their
-// lengths in nf; otherwise ka holds the weights of round 4 for the
-// sequential rounds.  Round scratch lives in [region, region + 4 * kSpecRound).
-constexpr int kSpecSerialMax = 128;  // smaller alphabets: each round's merge on one thread
-constexpr int kSpecRound = 2 * kSpecMax * 8 + (kSpecMax + 4) * 4 * 2 + 2 * kSpecMax * 2;
+// rounds 0..3 are independent: all four are sorted at once (block-wide), the
+// four merges run at once on four warps (one per scheduler quarter), and the
+// first round whose codes fit SZ3G_LMAX is the answer, as if the rounds had
+// run one after another.  `ka` holds the leaves in symbol order on entry.
+// On success the chosen round's leaves sorted by (weight, symbol) are left
+// in ka and their lengths in nf; otherwise ka holds the weights of round 4
+// for the sequential rounds.  Round scratch lives in
+// [region, region + 4 * kSpecRound): keys, leaf weights, internal weights
+// (then lengths), parents.
+constexpr int kSpecRound = kSpecMax * 8 + (kSpecMax + 4) * 4 * 2 + 2 * kSpecMax * 2;
 __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsigned char* region, int K) {
   const int tid = threadIdx.x, warp = tid >> 5;
   __shared__ int s_deep[kSpecRounds];
   auto uk = [&](int i) { return reinterpret_cast<unsigned long long*>(region + i * kSpecRound); };
-  auto sk = [&](int i) { return reinterpret_cast<unsigned long long*>(region + i * kSpecRound + kSpecMax * 8); };
-  auto lw = [&](int i) { return reinterpret_cast<uint32_t*>(region + i * kSpecRound + 2 * kSpecMax * 8); };
+  auto lw = [&](int i) { return reinterpret_cast<uint32_t*>(region + i * kSpecRound + kSpecMax * 8); };
   auto nfi = [&](int i) {
-    return reinterpret_cast<uint32_t*>(region + i * kSpecRound + 2 * kSpecMax * 8 + (kSpecMax + 4) * 4);
+    return reinterpret_cast<uint32_t*>(region + i * kSpecRound + kSpecMax * 8 + (kSpecMax + 4) * 4);
   };
   auto par = [&](int i) {
-    return reinterpret_cast<uint16_t*>(region + i * kSpecRound + 2 * kSpecMax * 8 + (kSpecMax + 4) * 8);
+    return reinterpret_cast<uint16_t*>(region + i * kSpecRound + kSpecMax * 8 + (kSpecMax + 4) * 8);
   };
   auto key_of = [&](int i, int j) {
     const unsigned long long k = ka[j];
@@ -459,34 +565,16 @@ __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsign
     const int i = it / K, j = it - i * K;
     uk(i)[j] = key_of(i, j);
   }
-  __syncthreads();
-  // 1. every round sorted by (weight, symbol): the ranks of all rounds' keys
-  //    at once (distinct keys: rank = keys below it)
+  // 1. every round sorted by (weight, symbol) (the sort's first barrier
+  //    orders the writes above)
+  block_bitonic_sort(uk, kSpecRounds, K);
   for (int it = tid; it < kSpecRounds * K; it += blockDim.x) {
     const int i = it / K, j = it - i * K;
-    const unsigned long long* in = uk(i);
-    const unsigned long long k = in[j];
-    int r = 0, q = 0;
-    for (; q + 1 < K; q += 2) {
-      const ulonglong2 pr = *reinterpret_cast<const ulonglong2*>(in + q);
-      r += (pr.x < k) + (pr.y < k);
-    }
-    if (q < K) r += in[q] < k;
-    sk(i)[r] = k;
+    lw(i)[j] = (uint32_t)(uk(i)[j] >> 16);
   }
   __syncthreads();
-  for (int it = tid; it < kSpecRounds * (K + 4); it += blockDim.x) {
-    const int i = it / (K + 4), t = it - i * (K + 4);
-    if (t < K + 2) lw(i)[t] = t < K ? (uint32_t)(sk(i)[t] >> 16) : 0xffffffffu;
-    nfi(i)[t] = 0xffffffffu;
-  }
-  __syncthreads();
-  // 2. the merges at once (warps 0, 8, 16, 24: one per scheduler quarter)
-  if ((warp & 7) == 0 && warp / 8 < kSpecRounds) {
-    const int i = warp / 8;
-    if (K > kSpecSerialMax) batched_merge<32>(lw(i), K, nfi(i), par(i));
-    else if ((tid & 31) == 0) two_queue_merge_fast(lw(i), K, nfi(i), par(i));
-  }
+  // 2. the merges at once (warps 0, 8, 16, 24)
+  if ((warp & 7) == 0 && warp / 8 < kSpecRounds) batched_merge<32>(lw(warp / 8), K, nfi(warp / 8), par(warp / 8));
   __syncthreads();
   // 3. depths (into nf of the round), deep rounds flagged
   const uint32_t root = (uint32_t)(2 * K - 2);
@@ -509,7 +597,7 @@ __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsign
   unsigned long long kk = 0;
   uint32_t ll = 0;
   if (tid < K) {
-    kk = pick >= 0 ? sk(pick)[tid] : key_of(kSpecRounds, tid);
+    kk = pick >= 0 ? uk(pick)[tid] : key_of(kSpecRounds, tid);
     ll = pick >= 0 ? nfi(pick)[tid] : 0u;
   }
   __syncthreads();
@@ -522,50 +610,17 @@ __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsign
 }
 
 // table[sym] = len << 24 | code for every used symbol.
-__global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __restrict__ hist, uint32_t nsym,
-                                                              uint32_t* table, uint8_t* len_out, uint32_t* code_out,
-                                                              DevState* st, CbGlobal* g, unsigned char* d_out,
-                                                              unsigned long long out_capacity, int esz,
-                                                              const CbRounds* R) {
+__global__ void __launch_bounds__(kCbThreads) codebook_kernel(uint32_t nsym, uint32_t* table, uint8_t* len_out,
+                                                              uint32_t* code_out, DevState* st, CbGlobal* g,
+                                                              unsigned char* d_out, unsigned long long out_capacity,
+                                                              int esz, const CbRounds* R) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long s_warp[32];
   __shared__ uint32_t s_cnt[SZ3G_LMAX + 2], s_start[SZ3G_LMAX + 2], s_fc[SZ3G_LMAX + 2];
+  __shared__ uint32_t s_base[kHcNseg + 1];
   const int tid = threadIdx.x;
-  static_assert(kSyms == kCbThreads * 64, "64 symbols per thread");
 
-  // 1. used symbols in symbol order.  Warp w reads bins 1024 k + 32 w + lane
-  //    (k = 0..63, coalesced); the ballot of each 32-bin segment marks its
-  //    used symbols, and segments in (k, w) order are symbol order.  Lane l
-  //    keeps the masks of its warp's segments k = l and k = l + 32.
-  const int lane = tid & 31, warp = tid >> 5;
-  uint32_t* s_seg = reinterpret_cast<uint32_t*>(smem + kCbOffPar);  // 2048 segment counts (free until step 2)
-  uint32_t mk0 = 0, mk1 = 0;
-  bool bad = false;
-  for (int k0 = 0; k0 < 64; k0 += 16) {  // sixteen loads in flight, then their ballots
-    uint32_t v[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) v[u] = __ldcg(hist + 1024 * (k0 + u) + 32 * warp + lane);
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int k = k0 + u, sy = 1024 * k + 32 * warp + lane;
-      bad |= v[u] != 0 && sy >= (int)nsym;
-      const unsigned m = __ballot_sync(0xffffffffu, v[u] != 0 && sy < (int)nsym);
-      if (lane == (k & 31)) {
-        if (k < 32) mk0 = m;
-        else mk1 = m;
-      }
-      if (lane == 0) s_seg[32 * k + warp] = (uint32_t)__popc(m);
-    }
-  }
-  if (bad) atomicOr(&st->flags, kFlagCorrupt);
-  if (tid == 0) st->n_unpred = hist[0];  // code 0 marks an unpredictable value
-  __syncthreads();
-  const uint32_t c0 = s_seg[2 * tid], c1 = s_seg[2 * tid + 1];
-  unsigned long long tot;
-  const uint32_t off = (uint32_t)block_exclusive_scan((unsigned long long)(c0 + c1), s_warp, &tot);
-  s_seg[2 * tid] = off;
-  s_seg[2 * tid + 1] = off + c0;
-  const int K = (int)tot;
+  // 1. used symbols in symbol order, from the compacted histogram
+  const int K = used_count(&g->hl, s_base);
   if (K == 0) {
     if (tid == 0) atomicOr(&st->flags, kFlagCorrupt);
     return;
@@ -575,26 +630,10 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   unsigned long long* kb = in_smem ? (unsigned long long*)(smem + kSmemLeaves * 8) : g->keys2;
   uint32_t* nf = in_smem ? (uint32_t*)(smem + kCbOffNf) : g->nf;
   uint16_t* symord = in_smem ? (uint16_t*)(smem + kCbOffSym) : g->symord;
-  __syncthreads();
-  for (int k0 = 0; k0 < 64; k0 += 16) {  // the used bins' counts, sixteen loads in flight
-    unsigned m[16];
-    uint32_t v[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int k = k0 + u;
-      m[u] = __shfl_sync(0xffffffffu, k < 32 ? mk0 : mk1, k & 31);
-      v[u] = ((m[u] >> lane) & 1u) ? __ldcg(hist + 1024 * k + 32 * warp + lane) : 0u;
-    }
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      if ((m[u] >> lane) & 1u) {
-        const int k = k0 + u, sy = 1024 * k + 32 * warp + lane;
-        const uint32_t pos = s_seg[32 * k + warp] + (uint32_t)__popc(m[u] & ((1u << lane) - 1u));
-        ka[pos] = ((unsigned long long)v[u] << 16) | pos;  // position in symbol order
-        symord[pos] = (uint16_t)sy;
-      }
-    }
-  }
+  used_entries(&g->hl, s_base, K, [&](int p, uint32_t c, uint32_t sy) {
+    ka[p] = ((unsigned long long)c << 16) | (uint32_t)p;  // position in symbol order
+    symord[p] = (uint16_t)sy;
+  });
   if (len_out || code_out)
     for (int sy = tid; sy < (int)nsym; sy += kCbThreads) {
       if (len_out) len_out[sy] = 0;
@@ -696,38 +735,11 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(const uint32_t* __
   }
 }
 
-__global__ void __launch_bounds__(kCbThreads) codebook_rounds_kernel(const uint32_t* __restrict__ hist,
-                                                                     uint32_t nsym, CbRounds* R) {
+__global__ void __launch_bounds__(kCbThreads) codebook_rounds_kernel(const HistList* H, CbRounds* R) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long s_warp[32];
-  __shared__ uint32_t s_seg[2048];  // used symbols of each 32-bin segment, then their first position
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, r = blockIdx.x;
-  // used symbols in symbol order, as in the codebook kernel: warp w reads
-  // bins 1024 k + 32 w + lane (coalesced), a ballot marks each segment's
-  // used bins; lane l keeps the masks of its warp's segments l and l + 32
-  uint32_t mk0 = 0, mk1 = 0;
-  for (int k0 = 0; k0 < 64; k0 += 16) {  // sixteen loads in flight, then their ballots
-    uint32_t v[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) v[u] = __ldcg(hist + 1024 * (k0 + u) + 32 * warp + lane);
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int k = k0 + u, sy = 1024 * k + 32 * warp + lane;
-      const unsigned m = __ballot_sync(0xffffffffu, sy < (int)nsym && v[u] != 0);
-      if (lane == (k & 31)) {
-        if (k < 32) mk0 = m;
-        else mk1 = m;
-      }
-      if (lane == 0) s_seg[32 * k + warp] = (uint32_t)__popc(m);
-    }
-  }
-  __syncthreads();
-  const uint32_t c0 = s_seg[2 * tid], c1 = s_seg[2 * tid + 1];
-  unsigned long long tot;
-  const uint32_t off = (uint32_t)block_exclusive_scan((unsigned long long)(c0 + c1), s_warp, &tot);
-  s_seg[2 * tid] = off;
-  s_seg[2 * tid + 1] = off + c0;
-  const int K = (int)tot;
+  __shared__ uint32_t s_base[kHcNseg + 1];
+  const int tid = threadIdx.x, r = blockIdx.x;
+  const int K = used_count(H, s_base);
   if (K <= kSpecMax) {  // small alphabets: the codebook kernel's own speculative rounds
     if (tid == 0) R->fits[r] = 0;
     return;
@@ -736,26 +748,10 @@ __global__ void __launch_bounds__(kCbThreads) codebook_rounds_kernel(const uint3
   const bool in_smem = K <= kSmemLeaves;
   unsigned long long* ka = in_smem ? (unsigned long long*)smem : g.keys;
   unsigned long long* kb = in_smem ? (unsigned long long*)(smem + kSmemLeaves * 8) : g.keys2;
-  __syncthreads();
-  for (int k0 = 0; k0 < 64; k0 += 16) {  // the used bins' counts, sixteen loads in flight
-    unsigned m[16];
-    uint32_t v[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int k = k0 + u;
-      m[u] = __shfl_sync(0xffffffffu, k < 32 ? mk0 : mk1, k & 31);
-      v[u] = ((m[u] >> lane) & 1u) ? __ldcg(hist + 1024 * k + 32 * warp + lane) : 0u;
-    }
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      if ((m[u] >> lane) & 1u) {
-        const int k = k0 + u;
-        const uint32_t pos = s_seg[32 * k + warp] + (uint32_t)__popc(m[u] & ((1u << lane) - 1u));
-        const uint32_t f = v[u] >> r;
-        ka[pos] = ((unsigned long long)(f ? f : 1u) << 16) | pos;
-      }
-    }
-  }
+  used_entries(H, s_base, K, [&](int p, uint32_t c, uint32_t) {
+    const uint32_t f = c >> r;
+    ka[p] = ((unsigned long long)(f ? f : 1u) << 16) | (uint32_t)p;
+  });
   __syncthreads();
   unsigned long long* srt = nullptr;
   bool deep;
@@ -780,16 +776,18 @@ int launch_codebook(const uint32_t* hist, uint32_t nsym, uint32_t* table, uint8_
   auto kern = codebook_kernel;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) != cudaSuccess)
     return SZ3G_E_CUDA;
+  CbGlobal* g = (CbGlobal*)scratch;
+  SZ3G_LAUNCH(kKCodebook, s, hist_compact_kernel<<<kHcNseg, kHcThreads, 0, s>>>(hist, nsym, &g->hl, st));
   if (rounds) {
     if (cudaFuncSetAttribute(codebook_rounds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem) !=
         cudaSuccess)
       return SZ3G_E_CUDA;
     SZ3G_LAUNCH(kKCodebook, s,
-                codebook_rounds_kernel<<<kCbRounds, kCbThreads, kCbSmem, s>>>(hist, nsym, (CbRounds*)rounds));
+                codebook_rounds_kernel<<<kCbRounds, kCbThreads, kCbSmem, s>>>(&g->hl, (CbRounds*)rounds));
   }
   SZ3G_LAUNCH(kKCodebook, s,
-              kern<<<1, kCbThreads, kCbSmem, s>>>(hist, nsym, table, len_out, code_out, st, (CbGlobal*)scratch, d_out,
-                                                  out_capacity, esz, (const CbRounds*)rounds));
+              kern<<<1, kCbThreads, kCbSmem, s>>>(nsym, table, len_out, code_out, st, g, d_out, out_capacity, esz,
+                                                  (const CbRounds*)rounds));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
