@@ -142,34 +142,75 @@ __device__ unsigned long long* block_radix_sort_w(unsigned long long* a, unsigne
 
 // Sorts nseg arrays seg(0) .. seg(nseg - 1) of n distinct keys each,
 // ascending and in place, by a bitonic network on the whole block.  Each
-// array must hold the next power of two >= n keys: the tail is padded with
-// ~0, above every key.
-template <typename SegFn>
+// array must hold the next power of two >= n keys (npad): the tail is padded
+// with ~0, above every key.  Element e of the concatenated arrays lives in
+// slot e / blockDim of thread e % blockDim, so the compare-exchanges at
+// distances below 32 stay inside a warp and run on registers by shuffles;
+// only the longer distances go through shared memory, with a barrier each.
+// Requires nseg * npad <= SLOTS * blockDim.
+template <int SLOTS, typename SegFn>
 __device__ void block_bitonic_sort(SegFn seg, int nseg, int n) {
   int lg = 0;
   while ((1 << lg) < n) ++lg;
-  const int npad = 1 << lg, tail = npad - n;
-  for (int it = threadIdx.x; it < nseg * tail; it += blockDim.x) {
-    const int s = it / tail;
-    seg(s)[n + it - s * tail] = ~0ull;
+  const int npad = 1 << lg, total = nseg * npad, NT = (int)blockDim.x, tid = (int)threadIdx.x;
+  __syncthreads();  // the keys are written
+  unsigned long long x[SLOTS];
+#pragma unroll
+  for (int q = 0; q < SLOTS; ++q) {
+    const int e = q * NT + tid, i = e & (npad - 1);
+    x[q] = (e < total && i < n) ? seg(e >> lg)[i] : ~0ull;
   }
-  __syncthreads();
-  if (lg == 0) return;
-  const int lh = lg - 1, half = 1 << lh;
-  for (int k = 2; k <= npad; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int it = threadIdx.x; it < nseg * half; it += blockDim.x) {
-        const int s = it >> lh, u = it & (half - 1);
-        const int i = ((u & ~(j - 1)) << 1) | (u & (j - 1));  // pair (i, i + j)
-        unsigned long long* A = seg(s);
-        const unsigned long long x = A[i], y = A[i + j];
-        if ((x > y) == ((i & k) == 0)) {
-          A[i] = y;
-          A[i + j] = x;
-        }
+  // compare-exchange at distance j < 32 on registers (every lane of a warp
+  // with any element takes part)
+  auto warp_stages = [&](int k, int j0) {
+    for (int j = j0; j > 0; j >>= 1)
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) {
+        if (q * NT >= total) break;
+        const int e = q * NT + tid, i = e & (npad - 1);
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, x[q], j);
+        const bool lower = (i & j) == 0, asc = (i & k) == 0;
+        x[q] = (lower == asc) ? (x[q] < y ? x[q] : y) : (x[q] < y ? y : x[q]);
+      }
+  };
+  for (int k = 2; k <= npad; k <<= 1) {
+    if (k > 32) {  // distances k/2 .. 32 in shared memory
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) {
+        const int e = q * NT + tid;
+        if (e < total) seg(e >> lg)[e & (npad - 1)] = x[q];
       }
       __syncthreads();
+      for (int j = k >> 1; j >= 32; j >>= 1) {
+        for (int it = tid; it < total >> 1; it += NT) {
+          const int s = it >> (lg - 1), u = it & ((npad >> 1) - 1);
+          const int i = ((u & ~(j - 1)) << 1) | (u & (j - 1));  // pair (i, i + j)
+          unsigned long long* A = seg(s);
+          const unsigned long long a0 = A[i], a1 = A[i + j];
+          if ((a0 > a1) == ((i & k) == 0)) {
+            A[i] = a1;
+            A[i + j] = a0;
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) {
+        const int e = q * NT + tid;
+        if (e < total) x[q] = seg(e >> lg)[e & (npad - 1)];
+      }
+      warp_stages(k, 16);
+    } else {
+      warp_stages(k, k >> 1);
     }
+  }
+  __syncthreads();  // every read of the arrays above is done
+#pragma unroll
+  for (int q = 0; q < SLOTS; ++q) {
+    const int e = q * NT + tid;
+    if (e < total) seg(e >> lg)[e & (npad - 1)] = x[q];
+  }
+  __syncthreads();
 }
 
 // First index in [lo, hi) of the ascending array a whose value exceeds w
@@ -204,16 +245,17 @@ __device__ __forceinline__ uint32_t seg_pair(const uint32_t* lw, const uint32_t*
     if (lw[a + i] <= W[m + d - i - 1]) lo = i + 1;
     else hi = i;
   }
-  uint32_t x = a + lo, y = m + d - lo, w = 0;
-#pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    const bool leaf = x < cL && (y >= je || lw[x] <= W[y]);
-    w += leaf ? lw[x] : W[y];
-    *(t ? ib : ia) = leaf ? x : Ku + y;
-    x += leaf;
-    y += !leaf;
-  }
-  return w;
+  // the two fronts of each run (a front past its run's end never wins)
+  const uint32_t x = a + lo, y = m + d - lo;
+  const uint32_t L0 = x < cL ? lw[x] : 0xffffffffu, L1 = x + 1 < cL ? lw[x + 1] : 0xffffffffu;
+  const uint32_t I0 = y < je ? W[y] : 0xffffffffu, I1 = y + 1 < je ? W[y + 1] : 0xffffffffu;
+  const bool f0 = x < cL && (y >= je || L0 <= I0);  // first item a leaf
+  const uint32_t L = f0 ? L1 : L0, I = f0 ? I0 : I1;
+  const uint32_t xs = x + f0, ys = y + !f0;
+  const bool f1 = xs < cL && (ys >= je || L <= I);  // second item a leaf
+  *ia = f0 ? x : Ku + y;
+  *ib = f1 ? xs : Ku + ys;
+  return (f0 ? L0 : I0) + (f1 ? L : I);
 }
 
 // The two-queue Huffman merge (the two lightest fronts, a leaf first on
@@ -267,21 +309,24 @@ __device__ void batched_merge(const uint32_t* lw, int K, uint32_t* W, PT* parent
     if (GROUP == 32) __syncwarp();
     else __syncthreads();
     const uint32_t jn = j1 + 1;
-    uint32_t i0, i1;
+    uint32_t i0, i1, wn;
     if (P & 1u) {  // the segment's last item, then node j0
-      const bool last_leaf = j0 == m || (cL > a && lw[cL - 1] > W[j0 - 1]);
+      const uint32_t lL = cL > a ? lw[cL - 1] : 0u, lI = j0 > m ? W[j0 - 1] : 0u;
+      const bool last_leaf = j0 == m || (cL > a && lL > lI);
       i0 = last_leaf ? cL - 1 : Ku + j0 - 1;
       i1 = Ku + j0;
+      wn = (last_leaf ? lL : lI) + w0;
       a = cL;
       m = j0 + 1;
     } else {  // node j0, then the next front (internal nodes j0+1 .. j1 exist)
-      const bool leaf = cL < Ku && (j1 == j0 || lw[cL] <= W[j0 + 1]);
+      const uint32_t nL = cL < Ku ? lw[cL] : 0u, nI = j1 > j0 ? W[j0 + 1] : 0u;
+      const bool leaf = cL < Ku && (j1 == j0 || nL <= nI);
       i0 = Ku + j0;
       i1 = leaf ? cL : Ku + j0 + 1;
+      wn = w0 + (leaf ? nL : nI);
       a = cL + leaf;
       m = j0 + 1 + !leaf;
     }
-    const uint32_t wn = (i0 < Ku ? lw[i0] : W[i0 - Ku]) + (i1 < Ku ? lw[i1] : W[i1 - Ku]);
     if (r == 0) {
       W[jn] = wn;
       parent[i0] = (PT)(Ku + jn);
@@ -452,7 +497,7 @@ __device__ __forceinline__ unsigned long long* code_lengths(unsigned long long* 
   }
   for (int iter = 0; iter < 40; ++iter) {
     if (K <= kSmemLeaves) {  // keys in shared memory, room for the padded sort
-      block_bitonic_sort([&](int) { return cur; }, 1, K);
+      block_bitonic_sort<kSmemLeaves / kCbThreads>([&](int) { return cur; }, 1, K);
       srt = cur;
     } else {
       srt = block_radix_sort_w(cur, other, K);
@@ -516,7 +561,7 @@ __device__ bool one_round_lengths(unsigned long long* cur, unsigned long long* o
   const int tid = threadIdx.x;
   unsigned long long* srt;
   if (K <= kSmemLeaves) {  // keys in shared memory, room for the padded sort
-    block_bitonic_sort([&](int) { return cur; }, 1, K);
+    block_bitonic_sort<kSmemLeaves / kCbThreads>([&](int) { return cur; }, 1, K);
     srt = cur;
   } else {
     srt = block_radix_sort_w(cur, other, K);
@@ -535,7 +580,7 @@ __device__ bool one_round_lengths(unsigned long long* cur, unsigned long long* o
 // Speculative halving rounds for small alphabets.  Round i of the length
 // limit uses the weights max(1, f >> i) (halving max(1, f >> 1) i times), so
 // rounds 0..3 are independent: all four are sorted at once (block-wide), the
-// four merges run at once on four warps (one per scheduler quarter), and the
+// four merges run at once on four warps (one per scheduler), and the
 // first round whose codes fit SZ3G_LMAX is the answer, as if the rounds had
 // run one after another.  `ka` holds the leaves in symbol order on entry.
 // On success the chosen round's leaves sorted by (weight, symbol) are left
@@ -567,14 +612,14 @@ __device__ bool speculative_lengths(unsigned long long* ka, uint32_t* nf, unsign
   }
   // 1. every round sorted by (weight, symbol) (the sort's first barrier
   //    orders the writes above)
-  block_bitonic_sort(uk, kSpecRounds, K);
+  block_bitonic_sort<kSpecRounds * kSpecMax / kCbThreads>(uk, kSpecRounds, K);
   for (int it = tid; it < kSpecRounds * K; it += blockDim.x) {
     const int i = it / K, j = it - i * K;
     lw(i)[j] = (uint32_t)(uk(i)[j] >> 16);
   }
   __syncthreads();
-  // 2. the merges at once (warps 0, 8, 16, 24)
-  if ((warp & 7) == 0 && warp / 8 < kSpecRounds) batched_merge<32>(lw(warp / 8), K, nfi(warp / 8), par(warp / 8));
+  // 2. the merges at once (warps 0..3: one per scheduler)
+  if (warp < kSpecRounds) batched_merge<32>(lw(warp), K, nfi(warp), par(warp));
   __syncthreads();
   // 3. depths (into nf of the round), deep rounds flagged
   const uint32_t root = (uint32_t)(2 * K - 2);
