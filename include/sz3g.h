@@ -380,8 +380,8 @@ int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_
  *    at zero; calls whose GPU work overlaps race on it, so do not run two at
  *    once.
  *  - SZ3G_E_CAPACITY when the stream needs more scratch than the array holds
- *    (about 40 bytes per 4096-code chunk plus 0.7 MiB of decode tables,
- *    i.e. n up to roughly 3.5e8 codes at 4096-code chunks); nothing is
+ *    (about 32 bytes per 4096-code chunk plus 0.7 MiB of decode tables,
+ *    i.e. n up to roughly 4.3e8 codes at 4096-code chunks); nothing is
  *    launched then.
  *  - Statuses as sz3g_huffman_decode (the same mapping of device flags).
  */

@@ -23,8 +23,9 @@ int launch_decode_tables(const unsigned char* tab, uint32_t n_used, const uint8_
                          void* tables, DevState* st, cudaStream_t s);
 int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, const uint32_t* chunk_words,
                          const uint16_t* sub_bits, unsigned long long n_chunks, uint32_t chunk, unsigned long long n,
-                         const void* tables, unsigned long long* woff, uint16_t* codes, uint32_t* zcnt,
-                         void* scan_state, DevState* st, cudaStream_t s, bool state_zeroed = false);
+                         const void* tables, uint16_t* codes, uint32_t* zcnt, void* state, DevState* st,
+                         cudaStream_t s, bool state_zeroed = false);
+size_t decode_state_bytes(unsigned long long n_chunks, uint32_t chunk);
 int launch_zero_counts(const uint16_t* codes, unsigned long long n, uint32_t chunk, unsigned long long n_chunks,
                        uint32_t* zcnt, cudaStream_t s);
 
@@ -76,7 +77,7 @@ CompressWs compress_layout(const Plan& pl, bool rounds = true) {
 }
 
 struct DecompressWs {
-  size_t st, tables, woff, zcnt, zunit, scan1, scan2, codes, R[34], total;
+  size_t st, dstate, scan2, tables, zcnt, zunit, codes, R[34], total;
 };
 
 DecompressWs decompress_layout(const Plan& pl) {
@@ -84,10 +85,9 @@ DecompressWs decompress_layout(const Plan& pl) {
   Layout l;
   w.st = l.take(sizeof(DevState));
   // the scans' look-back states next to the status block: one clear covers all three
-  w.scan1 = l.take(scan_state_bytes(pl.n_chunks));
+  w.dstate = l.take(decode_state_bytes(pl.n_chunks, pl.chunk));
   w.scan2 = l.take(scan_state_bytes(pl.n_chunks * pl.nsub));
   w.tables = l.take(dec_tables_bytes());
-  w.woff = l.take(pl.n_chunks * 8);
   w.zcnt = l.take(pl.n_chunks * pl.nsub * 4);
   w.zunit = l.take(pl.n_chunks * pl.nsub * 8);
   w.codes = l.take(pl.N * 2 + 256);  // the level kernels copy whole 16-byte blocks of codes
@@ -338,8 +338,7 @@ int decompress_enqueue(const Header& h, const void* d_stream, void* d_out, unsig
   SZ3G_TRY(launch_decode_chunks((const uint32_t*)(base + h.off_payload), h.n_words,
                                 (const uint32_t*)(base + h.off_chunks),
                                 pl.nsub > 1 ? (const uint16_t*)(base + h.off_sub) : nullptr, pl.n_chunks, pl.chunk,
-                                pl.N, ws + L.tables, (unsigned long long*)(ws + L.woff), codes,
-                                (uint32_t*)(ws + L.zcnt), ws + L.scan1, st, s, true));
+                                pl.N, ws + L.tables, codes, (uint32_t*)(ws + L.zcnt), ws + L.dstate, st, s, true));
   SZ3G_TRY(launch_scan((uint32_t*)(ws + L.zcnt), pl.n_chunks * pl.nsub, (unsigned long long*)(ws + L.zunit), 0,
                        h.n_unpred, 1, ws + L.scan2, st, s, true));
   void* R[34];
@@ -1095,16 +1094,16 @@ int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_
   cudaStream_t s = (cudaStream_t)stream;
   const unsigned long long nch = (n + chunk - 1) / chunk, nsb = (chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
   Layout l;
-  const size_t o_st = l.take(sizeof(DevState)), o_t = l.take(dec_tables_bytes()), o_wo = l.take(nch * 8),
-               o_zc = l.take(nch * nsb * 4), o_sc = l.take(scan_state_bytes(nch));
+  const size_t o_st = l.take(sizeof(DevState)), o_t = l.take(dec_tables_bytes()), o_zc = l.take(nch * nsb * 4),
+               o_sc = l.take(decode_state_bytes(nch, chunk));
   Scratch own;
   unsigned char* ws;
   SZ3G_TRY(get_ws(nullptr, 0, l.off, s, own, &ws));
   DevState* st = (DevState*)(ws + o_st);
   SZ3G_CUDA(cudaMemsetAsync(st, 0, sizeof(DevState), s));
   SZ3G_TRY(launch_decode_tables(nullptr, 0, d_len, nsym, ws + o_t, st, s));
-  SZ3G_TRY(launch_decode_chunks(d_words, n_words, d_chunk_words, d_sub_bits, nch, chunk, n, ws + o_t,
-                                (unsigned long long*)(ws + o_wo), d_codes, (uint32_t*)(ws + o_zc), ws + o_sc, st, s));
+  SZ3G_TRY(launch_decode_chunks(d_words, n_words, d_chunk_words, d_sub_bits, nch, chunk, n, ws + o_t, d_codes,
+                                (uint32_t*)(ws + o_zc), ws + o_sc, st, s));
   DevState h;
   SZ3G_TRY(read_state(st, &h, s));
   return status_of(h.flags);

@@ -20,13 +20,13 @@
 namespace sz3g {
 
 size_t dec_tables_bytes();
-size_t scan_state_bytes(unsigned long long n);
+size_t decode_state_bytes(unsigned long long n_chunks, uint32_t chunk);
 int launch_decode_tables(const unsigned char* tab, uint32_t n_used, const uint8_t* len, uint32_t nsym, void* tables,
                          DevState* st, cudaStream_t s);
 int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, const uint32_t* chunk_words,
                          const uint16_t* sub_bits, unsigned long long n_chunks, uint32_t chunk, unsigned long long n,
-                         const void* tables, unsigned long long* woff, uint16_t* codes, uint32_t* zcnt,
-                         void* scan_state, DevState* st, cudaStream_t s, bool state_zeroed = false);
+                         const void* tables, uint16_t* codes, uint32_t* zcnt, void* state, DevState* st,
+                         cudaStream_t s, bool state_zeroed = false);
 
 constexpr size_t kStaticScratchBytes = 4u << 20;  // 4 MiB
 
@@ -76,17 +76,16 @@ extern "C" int sz3g_huffman_decode_static(const uint32_t* d_words, uint64_t n_wo
       chunk > 65536 || chunk % 8 || ((uintptr_t)d_codes % 16) != 0)
     return SZ3G_E_INVAL;
   const unsigned long long nch = (n + chunk - 1) / chunk;
-  // no stream with more chunks than 8-byte offsets fit in the array can fit;
+  // no stream with more chunks than 4-byte counts fit in the array can fit;
   // refusing it here also keeps the size sums below from wrapping
-  if (nch > kStaticScratchBytes / 8) return SZ3G_E_CAPACITY;
+  if (nch > kStaticScratchBytes / 4) return SZ3G_E_CAPACITY;
   const unsigned long long nsb = (chunk + SZ3G_SUBBLOCK - 1) / SZ3G_SUBBLOCK;
   // layout inside the fixed array; a stream too long for it is refused
   const size_t o_st = 0;
   const size_t o_tab = o_st + up256(sizeof(DevState));
-  const size_t o_woff = o_tab + up256(dec_tables_bytes());
-  const size_t o_zc = o_woff + up256(nch * 8);
+  const size_t o_zc = o_tab + up256(dec_tables_bytes());
   const size_t o_scan = o_zc + up256(nch * nsb * 4);
-  const size_t need = o_scan + up256(scan_state_bytes(nch));
+  const size_t need = o_scan + up256(decode_state_bytes(nch, chunk));
   if (need > kStaticScratchBytes) return SZ3G_E_CAPACITY;
   void* base = nullptr;
   const int rc0 = scratch_address(&base);
@@ -101,9 +100,8 @@ extern "C" int sz3g_huffman_decode_static(const uint32_t* d_words, uint64_t n_wo
   }
   int rc = launch_decode_tables(nullptr, 0, d_len, nsym, ws + o_tab, st, s);
   if (rc == SZ3G_OK)
-    rc = launch_decode_chunks(d_words, n_words, d_chunk_words, d_sub_bits, nch, chunk, n, ws + o_tab,
-                              (unsigned long long*)(ws + o_woff), d_codes, (uint32_t*)(ws + o_zc), ws + o_scan, st,
-                              s);
+    rc = launch_decode_chunks(d_words, n_words, d_chunk_words, d_sub_bits, nch, chunk, n, ws + o_tab, d_codes,
+                              (uint32_t*)(ws + o_zc), ws + o_scan, st, s);
   if (rc != SZ3G_OK) {
     // work already queued may still use the array: let it finish before the
     // caller can start another call
