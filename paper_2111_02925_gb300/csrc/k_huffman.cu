@@ -1541,7 +1541,7 @@ __device__ __forceinline__ void chunk_counts(const uint16_t* __restrict__ codes,
 // wstat and zstat start at zero (the compressor's workspace is cleared when
 // it starts).
 template <typename U>
-__global__ void __launch_bounds__(kEncWarps * 32, 4) tile_pack_kernel(const EncArgs a,
+__global__ void __launch_bounds__(kEncWarps * 32, 5) tile_pack_kernel(const EncArgs a,
                                                                        const __grid_constant__ PassMap map,
                                                                        uint32_t* ticket, unsigned long long* wstat,
                                                                        unsigned long long* zstat) {
@@ -1640,7 +1640,15 @@ static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch
     // is the ticket, we / ze the tiles' look-back states, all cleared with
     // the compressor's workspace)
     const unsigned long long ntiles = (nch + kEncWarps - 1) / kEncWarps;
-    const unsigned ng = (unsigned)std::min<unsigned long long>(ntiles, 152ull * 4);
+    int dev = 0, nsm = 152, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (a.esz == 4)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_pack_kernel<uint32_t>, kEncWarps * 32, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_pack_kernel<unsigned long long>, kEncWarps * 32, 0);
+    if (per < 1) per = 1;
+    const unsigned ng = (unsigned)std::min<unsigned long long>(ntiles, (unsigned long long)nsm * per);
     if (a.esz == 4)
       SZ3G_LAUNCH(kKEncode, s, tile_pack_kernel<uint32_t><<<ng, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze));
     else
