@@ -614,11 +614,18 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
         ld4(Er + 4, e + 4);
         T xo[4] = {T(0), T(0), T(0), T(0)};
         if (COMP) {
-          T xv[8];
+          // the run's eight x values as two 16-byte loads; the upper four
+          // lanes of each group of eight load the second half first, so that
+          // the eight lanes of one load touch distinct banks
+          const bool sw = (q4 & 4) != 0;
+          T xa[4], xb[4];
           const T* xr = X + (i4 * S::kXJ + j21) * S::kXK + 8 * q4 + 4;
-          ld4(xr, xv);
-          ld4(xr + 4, xv + 4);
-          xo[0] = xv[1], xo[1] = xv[3], xo[2] = xv[5], xo[3] = xv[7];
+          ld4(xr + (sw ? 4 : 0), xa);
+          ld4(xr + (sw ? 0 : 4), xb);
+          xo[0] = sw ? xb[1] : xa[1];
+          xo[1] = sw ? xb[3] : xa[3];
+          xo[2] = sw ? xa[1] : xb[1];
+          xo[3] = sw ? xa[3] : xb[3];
         }
         const int c0 = (int)d.off[2] + (i * (int)d.E1[2] + j) * (int)d.E2[2] + A2 / 2;
         const uint32_t ci = (uint32_t)(c0 + 4 * q4);

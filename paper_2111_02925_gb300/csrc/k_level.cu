@@ -770,10 +770,18 @@ struct CoarseDesc {
   uint32_t chunk, nsub;
 };
 
+// Shared memory of the coarse kernel: the reconstruction of G_kc, then
+// (recover) the group's codes in traversal order.
+__host__ __device__ constexpr size_t coarse_off_codes(size_t npts, size_t esz) {
+  return (npts * esz + 15) & ~(size_t)15;
+}
+
 template <typename T, bool COMP>
 __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc d, const LevelArgs<T> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   T* R = reinterpret_cast<T*>(sm);
+  const uint32_t npts = d.mk[0] * d.mk[1] * d.mk[2];
+  uint16_t* Kc = reinterpret_cast<uint16_t*>(sm + coarse_off_codes(npts, sizeof(T)));  // recover
   const int tid = threadIdx.x;
   DevState* st = a.st;
   if (COMP && (st->flags & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound))) return;
@@ -783,6 +791,12 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
   const int radius = a.radius;
   __shared__ unsigned int s_nz;
   __shared__ int s_bad;
+  // recover: the group's codes (the first npts codes of the traversal) in one
+  // round of coalesced loads, so that no pass waits for global memory
+  if (!COMP) {
+    for (uint32_t i = tid; i < npts; i += kCoarseThreads) Kc[i] = a.codes[i];
+    __syncthreads();
+  }
   if (tid == 0) {
     s_nz = 0;
     s_bad = 0;
@@ -796,7 +810,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
       if (code == 0) s_nz = 1;
       if (!isfinite(xv)) s_bad = 1;
     } else {
-      const uint32_t code = a.codes[0];
+      const uint32_t code = Kc[0];
       if (code == 0) {
         if (a.n_unpred) {
           r = a.unpred[0];
@@ -841,7 +855,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
         if (code == 0) atomicAdd(&s_nz, 1u);
         if (!isfinite(xv)) s_bad = 1;
       } else {
-        const uint32_t code = a.codes[ci];
+        const uint32_t code = Kc[ci];
         if (code == 0) {
           const unsigned long long rk = rank_of_zero(a.codes, ci, d.chunk, d.nsub, a.zunit);
           if (rk < a.n_unpred) {
@@ -1440,11 +1454,15 @@ static int run_coarse(const Plan& pl, int kc, const LevelArgs<T>& a, cudaStream_
     c.m_ax = pd.m[pd.axis];
     c.interp = pd.interp;
     c.scale_log = pd.grid - kc;
+    // the group's codes are the first codes of the traversal: recover
+    // stages them by code index
+    if (c.off + c.count > pl.gsize[kc]) return SZ3G_E_INVAL;
   }
   d.n_pass = n;
   d.chunk = pl.chunk;
   d.nsub = pl.nsub;
-  const size_t smem = (size_t)pl.gsize[kc] * sizeof(T);
+  const size_t smem = COMP ? (size_t)pl.gsize[kc] * sizeof(T)
+                           : coarse_off_codes((size_t)pl.gsize[kc], sizeof(T)) + (size_t)pl.gsize[kc] * 2;
   if (cudaFuncSetAttribute(coarse_kernel<T, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return SZ3G_E_CUDA;
