@@ -179,6 +179,22 @@ __device__ __forceinline__ void get_codes4(const uint16_t* p, uint32_t* c) {
   }
 }
 
+// Task t of a sweep over nrows rows of kPairs = 18 pairs: the first 16 pairs
+// of every row, then the last two of every row, so that the 16 lanes of a
+// half-warp take 16 pairs of one row (8-byte shared accesses without bank
+// conflicts) instead of straddling two rows.
+__device__ __forceinline__ void pair_task(int t, int nrows, int& row, int& pr) {
+  const int n16 = nrows * 16;
+  if (t < n16) {
+    row = t >> 4;
+    pr = t & 15;
+  } else {
+    const int u = t - n16;
+    row = u >> 1;
+    pr = 16 + (u & 1);
+  }
+}
+
 // Per-thread results of the tile passes, flushed once per CTA.
 struct FineAcc {
   bool bad;  // recover: a code outside [0, 2r) or an unpredictable value past the list
@@ -485,7 +501,9 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
       // ---- coarse points into E, and pass 0 (odd i, even j) ----------------
       for (int t = tid; t < S::kCopyTasks + S::kP0Tasks; t += kFineThreads) {
         if (t < S::kCopyTasks) {
-          const int pr = t % S::kPairs, row = t / S::kPairs;
+          static_assert(S::kPairs == 18, "pair_task takes rows of 18 pairs");
+          int pr, row;
+          pair_task(t, S::kCopyTasks / S::kPairs, row, pr);
           const int e = row / S::kCJ, cj = row % S::kCJ;
           T v[2];
           ld2(C + ((e + (S::kHas0 ? 1 : 0)) * S::kCJ + cj) * S::kCK + 2 * pr + 2, v);
@@ -494,7 +512,8 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
         }
         if constexpr (S::kHas0) {
           const int u = t - S::kCopyTasks;
-          const int pr = u % S::kPairs, row = u / S::kPairs;
+          int pr, row;
+          pair_task(u, S::kP0Tasks / S::kPairs, row, pr);
           const int eo = row / S::kCJ, cj = row % S::kCJ;
           const int i = A0 + 2 * eo + 1, j = A1 - 2 + 2 * cj;
           if (!IN && (i >= m0 || j < 0 || j >= m1)) continue;
@@ -549,7 +568,8 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
 
       // ---- pass 1 (any i, odd j) --------------------------------------------
       for (int t = tid; t < S::kP1Tasks; t += kFineThreads) {
-        const int pr = t % S::kPairs, row = t / S::kPairs;
+        int pr, row;
+        pair_task(t, S::kP1Tasks / S::kPairs, row, pr);
         const int i4 = row / (S::kT1 / 2), jo = row % (S::kT1 / 2);
         const int i = A0 + i4, j = A1 + 2 * jo + 1;
         if (!IN && (i >= m0 || j >= m1)) continue;
