@@ -1573,25 +1573,17 @@ __global__ void __launch_bounds__(kEncWarps * 32, 5) tile_pack_kernel(const EncA
       s_zeros[w] = zeros;
     }
     __syncthreads();
-    if (w == 0) {
-      uint32_t aw = lane < kEncWarps ? s_words[lane] : 0u, az = lane < kEncWarps ? s_zeros[lane] : 0u;
-      for (int o = 16; o > 0; o >>= 1) {
-        aw += __shfl_xor_sync(0xffffffffu, aw, o);
-        az += __shfl_xor_sync(0xffffffffu, az, o);
-      }
+    if (w < 2) {  // warp 0: the words before the tile, warp 1: the zero codes (at once)
+      const uint32_t* cnt = w == 0 ? s_words : s_zeros;
+      unsigned long long* stat = w == 0 ? wstat : zstat;
+      uint32_t agg = lane < kEncWarps ? cnt[lane] : 0u;
+      for (int o = 16; o > 0; o >>= 1) agg += __shfl_xor_sync(0xffffffffu, agg, o);
+      if (lane == 0) st_release(stat + tile, (tile == 0 ? kFlagInc : kFlagAgg) | agg);
+      const unsigned long long ex = lookback(stat, (long long)tile, st, a.spin_limit);
       if (lane == 0) {
-        st_release(wstat + tile, (tile == 0 ? kFlagInc : kFlagAgg) | aw);
-        st_release(zstat + tile, (tile == 0 ? kFlagInc : kFlagAgg) | az);
-      }
-      const unsigned long long ew = lookback(wstat, (long long)tile, st, a.spin_limit);
-      const unsigned long long ez = lookback(zstat, (long long)tile, st, a.spin_limit);
-      if (lane == 0) {
-        if (tile > 0) {
-          st_release(wstat + tile, kFlagInc | (ew + aw));
-          st_release(zstat + tile, kFlagInc | (ez + az));
-        }
-        s_we = ew;
-        s_ze = ez;
+        if (tile > 0) st_release(stat + tile, kFlagInc | (ex + agg));
+        if (w == 0) s_we = ex;
+        else s_ze = ex;
       }
     }
     __syncthreads();
