@@ -41,7 +41,8 @@ enum {
   SZ3G_E_CORRUPT = -5,        /* stream fails a magic/version/length/decode check */
   SZ3G_E_CUDA = -6,           /* a CUDA runtime call failed                    */
   SZ3G_E_NOMEM = -7,          /* device allocation failed                      */
-  SZ3G_E_TIMEOUT = -8         /* a bounded wait inside a kernel gave up        */
+  SZ3G_E_TIMEOUT = -8,        /* a bounded wait inside a kernel gave up        */
+  SZ3G_E_CHECK = -9           /* checking build only: an index check inside a kernel failed */
 };
 
 enum { SZ3G_F32 = 0, SZ3G_F64 = 1 };

@@ -165,6 +165,7 @@ int get_ws(void* user, size_t user_bytes, size_t need, cudaStream_t s, Scratch& 
 }
 
 __host__ __device__ inline int flags_status(uint32_t f) {
+  if (f & kFlagCheck) return SZ3G_E_CHECK;  // checking build: an index went out of range
   if (f & kFlagBadBound) return SZ3G_E_INVAL;
   if (f & kFlagNonFinite) return SZ3G_E_NONFINITE;
   if (f & kFlagZeroRange) return SZ3G_E_ZERO_RANGE_REL;
@@ -570,6 +571,7 @@ const char* sz3g_strerror(int status) {
     case SZ3G_E_CUDA: return "a CUDA runtime call failed";
     case SZ3G_E_NOMEM: return "device allocation failed";
     case SZ3G_E_TIMEOUT: return "a bounded wait inside a kernel gave up";
+    case SZ3G_E_CHECK: return "an index check inside a kernel failed (checking build)";
     default: return "unknown status";
   }
 }
@@ -594,6 +596,7 @@ int sz3g_workspace_size(const sz3g_params* p, int for_decompress, size_t* bytes)
 
 int sz3g_compress(const sz3g_params* p, const void* d_in, void* d_out, size_t out_capacity, size_t* out_bytes,
                   void* d_workspace, size_t ws_bytes, void* stream) {
+  SZ3G_TRACE("sz3g_compress");
   Plan pl;
   SZ3G_TRY(make_plan(p, &pl));
   if (!d_in || !d_out || !out_bytes || !aligned(d_in, 16) || !aligned(d_out, 16)) return SZ3G_E_INVAL;
@@ -799,6 +802,7 @@ int sz3g_read_header(const void* stream, size_t bytes, int stream_on_device, sz3
 
 int sz3g_decompress(const void* d_stream, size_t bytes, void* d_out, size_t out_capacity, void* d_workspace,
                     size_t ws_bytes, void* stream) {
+  SZ3G_TRACE("sz3g_decompress");
   if (!d_stream || !d_out || !aligned(d_stream, 16) || !aligned(d_out, 16)) return SZ3G_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char hb[SZ3G_HEADER_BYTES];
@@ -862,6 +866,7 @@ struct StageHold {
 int sz3g_compress_async(const sz3g_params* p, const void* d_in, void* d_out, size_t out_capacity,
                         unsigned long long* d_out_bytes, int* d_status, void* d_workspace, size_t ws_bytes,
                         void* stream) {
+  SZ3G_TRACE("sz3g_compress_async");
   Plan pl;
   SZ3G_TRY(make_plan(p, &pl));
   if (!d_in || !d_out || !d_status || !d_workspace || !aligned(d_in, 16) || !aligned(d_out, 16) ||
@@ -877,6 +882,7 @@ int sz3g_compress_async(const sz3g_params* p, const void* d_in, void* d_out, siz
 
 int sz3g_decompress_async(const void* h_header, const void* d_stream, size_t bytes, void* d_out,
                           size_t out_capacity, int* d_status, void* d_workspace, size_t ws_bytes, void* stream) {
+  SZ3G_TRACE("sz3g_decompress_async");
   if (!h_header || !d_stream || !d_out || !d_status || !d_workspace || !aligned(d_stream, 16) ||
       !aligned(d_out, 16) || !aligned(d_workspace, kAlign) || !aligned(d_status, 4))
     return SZ3G_E_INVAL;
@@ -893,6 +899,7 @@ int sz3g_decompress_async(const void* h_header, const void* d_stream, size_t byt
 
 int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size_t out_capacity, size_t* out_bytes,
                        void* stream) {
+  SZ3G_TRACE("sz3g_compress_host");
   Plan pl;
   SZ3G_TRY(make_plan(p, &pl));
   if (!h_in || !h_out || !out_bytes) return SZ3G_E_INVAL;
@@ -927,6 +934,7 @@ int sz3g_compress_host(const sz3g_params* p, const void* h_in, void* h_out, size
 }
 
 int sz3g_decompress_host(const void* h_stream, size_t bytes, void* h_out, size_t out_capacity, void* stream) {
+  SZ3G_TRACE("sz3g_decompress_host");
   if (!h_stream || !h_out) return SZ3G_E_INVAL;
   if (bytes < SZ3G_HEADER_BYTES) return SZ3G_E_CORRUPT;
   cudaStream_t s = (cudaStream_t)stream;
@@ -979,6 +987,7 @@ int sz3g_trim(void) {
 int sz3g_predict_quantize(const sz3g_params* p, const void* d_in, uint16_t* d_codes, void* d_unpred,
                           uint32_t* d_hist, uint64_t* h_n_unpred, void* h_ebT, void* d_workspace, size_t ws_bytes,
                           void* stream) {
+  SZ3G_TRACE("sz3g_predict_quantize");
   Plan pl;
   SZ3G_TRY(make_plan(p, &pl));
   if (!d_in || !d_codes || !d_unpred || !d_hist || !aligned(d_in, 16) || !aligned(d_codes, 16)) return SZ3G_E_INVAL;
@@ -1007,6 +1016,7 @@ int sz3g_predict_quantize(const sz3g_params* p, const void* d_in, uint16_t* d_co
 
 int sz3g_recover(const sz3g_params* p, const void* h_ebT, const uint16_t* d_codes, const void* d_unpred,
                  uint64_t n_unpred, void* d_out, void* d_workspace, size_t ws_bytes, void* stream) {
+  SZ3G_TRACE("sz3g_recover");
   Plan pl;
   SZ3G_TRY(make_plan(p, &pl));
   if (!h_ebT || !d_codes || !d_out || (n_unpred && !d_unpred) || !aligned(d_codes, 16)) return SZ3G_E_INVAL;
@@ -1032,6 +1042,7 @@ int sz3g_recover(const sz3g_params* p, const void* h_ebT, const uint16_t* d_code
 }
 
 int sz3g_huffman_build(const uint32_t* d_hist, uint32_t nsym, uint8_t* d_len, uint32_t* d_code, void* stream) {
+  SZ3G_TRACE("sz3g_huffman_build");
   if (!d_hist || !d_len || !d_code || nsym < 1 || nsym > (uint32_t)kSyms) return SZ3G_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
   Layout l;
@@ -1052,6 +1063,7 @@ int sz3g_huffman_build(const uint32_t* d_hist, uint32_t nsym, uint8_t* d_len, ui
 int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_len, const uint32_t* d_code,
                         uint32_t nsym, uint32_t chunk, uint32_t* d_words, uint64_t cap_words,
                         uint32_t* d_chunk_words, uint16_t* d_sub_bits, uint64_t* h_n_words, void* stream) {
+  SZ3G_TRACE("sz3g_huffman_encode");
   if (!d_codes || !d_len || !d_code || !d_words || !d_chunk_words || n < 1 || nsym < 1 || nsym > (uint32_t)kSyms ||
       chunk < 8 || chunk > 65536 || chunk % 8 || !aligned(d_codes, 16))
     return SZ3G_E_INVAL;
@@ -1088,6 +1100,7 @@ int sz3g_huffman_encode(const uint16_t* d_codes, uint64_t n, const uint8_t* d_le
 int sz3g_huffman_decode(const uint32_t* d_words, uint64_t n_words, const uint32_t* d_chunk_words,
                         const uint16_t* d_sub_bits, uint32_t chunk, const uint8_t* d_len, uint32_t nsym,
                         uint16_t* d_codes, uint64_t n, void* stream) {
+  SZ3G_TRACE("sz3g_huffman_decode");
   if (!d_words || !d_chunk_words || !d_len || !d_codes || n < 1 || nsym < 1 || nsym > (uint32_t)kSyms || chunk < 8 ||
       chunk > 65536 || chunk % 8 || !aligned(d_codes, 16))
     return SZ3G_E_INVAL;

@@ -299,6 +299,7 @@ int sz3g_batch_queue_info(const sz3g_batch* b, int* on, int* levels) {
 }
 
 int sz3g_batch_run(sz3g_batch* b, void* stream) {
+  SZ3G_TRACE("sz3g_batch_run");
   if (!b || !b->exec) return SZ3G_E_INVAL;
   if (cudaGraphLaunch(b->exec, (cudaStream_t)stream) != cudaSuccess) {
     cudaGetLastError();

@@ -25,6 +25,7 @@ enum : uint32_t {
   kFlagCapacity = 1u << 3,
   kFlagCorrupt = 1u << 4,
   kFlagTimeout = 1u << 5,
+  kFlagCheck = 1u << 6,  // checking build: an index check failed
 };
 
 // Small block of device state at the start of every workspace.
@@ -117,6 +118,31 @@ enum KernelId {
 bool profiling_on();
 void count_launches(unsigned long long n);
 unsigned long long launch_total();
+
+// Named ranges on the host timeline (NVTX, header-only; free unless a
+// profiler attached its collector): every C-ABI entry point opens one.
+class TraceRange {
+ public:
+  explicit TraceRange(const char* name);
+  ~TraceRange();
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+#define SZ3G_TRACE(name) ::sz3g::TraceRange sz3g_trace_range_(name)
+
+// Index checks of the checking build (compiled with -DSZ3G_CHECK): a failed
+// check raises kFlagCheck (the call then reports SZ3G_E_CHECK) and the
+// access it guards is skipped.  In the ordinary build every check is the
+// constant true and compiles away.
+#ifdef SZ3G_CHECK
+__device__ __forceinline__ bool index_ok(bool ok, DevState* st) {
+  if (!ok) atomicOr(&st->flags, kFlagCheck);
+  return ok;
+}
+#define SZ3G_IN(cond, st) ::sz3g::index_ok((cond), (st))
+#else
+#define SZ3G_IN(cond, st) true
+#endif
 
 // Counts a launch and, while profiling is on, brackets it with CUDA events.
 class LaunchScope {

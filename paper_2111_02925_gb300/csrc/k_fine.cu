@@ -214,7 +214,7 @@ __device__ __forceinline__ T fine_point(const LevelArgs<T>& a, const FineDesc& d
       // histogram bin 0 and checked for finiteness where the encoder gathers
       // them)
       if (code_out) *code_out = code;
-      else a.codes[ci] = (uint16_t)code;
+      else if (SZ3G_IN(ci < a.n_codes, a.st)) a.codes[ci] = (uint16_t)code;
       const uint32_t bn = code - (uint32_t)hlo;
       if (kHistSpare) {
         const bool far = bn >= (uint32_t)kHistWin;
@@ -307,6 +307,10 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
   __shared__ uint32_t s_bytes[2];
   const int tid = threadIdx.x;
   DevState* st = a.st;
+  // two values into the even-k plane at element offset off
+  auto est2 = [&](int off, T v0, T v1) {
+    if (SZ3G_IN(off >= 0 && off + 2 <= S::kT0 * S::kXJ * S::kEK, st)) st2(E + off, v0, v1);
+  };
   if (COMP && (st->flags & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound))) return;
   if (!COMP && (st->flags & kFlagCorrupt)) return;
   const T ebT = COMP ? bits_to<T>(st->ebT_bits) : a.ebT;
@@ -372,17 +376,19 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
         int which, slot;
         bool valid;
         const long long c0 = row_c0(A0, A1, A2, tid, which, slot, valid);
-        const uint32_t bytes = valid ? (which == 2 ? S::kL2 * 2 : S::kL01 * 2) : 0u;
+        long long al = 0;
+        int o = 0;
+        if (valid) code_row(c0, &al, &o);
+        const uint32_t want = which == 2 ? S::kL2 * 2 : S::kL01 * 2;
+        // the row's copy stays inside the codes and the padding after them
+        const bool inb = !valid || SZ3G_IN((unsigned long long)al + want / 2 <=
+                                               a.n_codes + (a.codes_padded ? 128ull : 0ull), st);
+        const uint32_t bytes = valid && inb ? want : 0u;
         fence_proxy_async_smem();
         mbar_expect_tx(&bar[b], bytes + (tid == 0 ? d.tensor_bytes : 0u));
         if (tid == 0)
           tma_load_3d(Cs + b * CB, &tmc, A2 / 2 - 4, A1 / 2 - 1, S::kHas0 ? A0 / 2 - 1 : 0, &bar[b]);
-        if (valid) {
-          long long al;
-          int o;
-          code_row(c0, &al, &o);
-          bulk_load(Ks + b * KB + slot, a.codes + al, bytes, &bar[b]);
-        }
+        if (bytes) bulk_load(Ks + b * KB + slot, a.codes + al, bytes, &bar[b]);
       }
       return;
     }
@@ -507,7 +513,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
           const int e = row / S::kCJ, cj = row % S::kCJ;
           T v[2];
           ld2(C + ((e + (S::kHas0 ? 1 : 0)) * S::kCJ + cj) * S::kCK + 2 * pr + 2, v);
-          st2(E + ((2 * e) * S::kXJ + 2 * cj) * S::kEK + 2 * pr, v[0], v[1]);
+          est2(((2 * e) * S::kXJ + 2 * cj) * S::kEK + 2 * pr, v[0], v[1]);
           continue;
         }
         if constexpr (S::kHas0) {
@@ -546,8 +552,10 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
             if (!COMP) k2[0] = kr[0], k2[1] = kr[1];
             fine_points<T, COMP, 2>(a, d, hwin, hlo, x2, p2, ebT, ebr, own2, (uint32_t)(c0 + ke), k2, acc, r, q2);
             if (COMP) {
-              if (own2[0]) a.codes[c0 + ke] = (uint16_t)q2[0];
-              if (own2[1]) a.codes[c0 + ke + 1] = (uint16_t)q2[1];
+              if (own2[0] && SZ3G_IN((unsigned long long)(long long)(c0 + ke) < a.n_codes, st))
+                a.codes[c0 + ke] = (uint16_t)q2[0];
+              if (own2[1] && SZ3G_IN((unsigned long long)(long long)(c0 + ke + 1) < a.n_codes, st))
+                a.codes[c0 + ke + 1] = (uint16_t)q2[1];
             }
           } else {
 #pragma unroll
@@ -561,7 +569,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
                                          COMP ? 0u : (uint32_t)kr[q], acc);
             }
           }
-          st2(E + ((2 * eo + 1) * S::kXJ + 2 * cj) * S::kEK + ke, r[0], r[1]);
+          est2(((2 * eo + 1) * S::kXJ + 2 * cj) * S::kEK + ke, r[0], r[1]);
         }
       }
       __syncthreads();
@@ -602,8 +610,10 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
           if (!COMP) k2[0] = kr[0], k2[1] = kr[1];
           fine_points<T, COMP, 2>(a, d, hwin, hlo, x2, p2, ebT, ebr, own2, (uint32_t)(c0 + ke), k2, acc, r, q2);
           if (COMP) {
-            if (own2[0]) a.codes[c0 + ke] = (uint16_t)q2[0];
-            if (own2[1]) a.codes[c0 + ke + 1] = (uint16_t)q2[1];
+            if (own2[0] && SZ3G_IN((unsigned long long)(long long)(c0 + ke) < a.n_codes, st))
+              a.codes[c0 + ke] = (uint16_t)q2[0];
+            if (own2[1] && SZ3G_IN((unsigned long long)(long long)(c0 + ke + 1) < a.n_codes, st))
+              a.codes[c0 + ke + 1] = (uint16_t)q2[1];
           }
         } else {
 #pragma unroll
@@ -617,7 +627,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
                                        COMP ? 0u : (uint32_t)kr[q], acc);
           }
         }
-        st2(E + (i4 * S::kXJ + j21) * S::kEK + ke, r[0], r[1]);
+        est2((i4 * S::kXJ + j21) * S::kEK + ke, r[0], r[1]);
       }
       __syncthreads();
 
@@ -674,7 +684,7 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
             p4[u] = interp_predict<T>(e[u + 2], e[u + 3], e[u + 1], e[u + 4], true, true, true, INTERP);
           const bool own4[4] = {true, true, true, true};
           fine_points<T, COMP, 4>(a, d, hwin, hlo, xo, p4, ebT, ebr, own4, ci, kin, acc, r, cq);
-          if (COMP) put_codes4(a.codes + ci, cq);
+          if (COMP && SZ3G_IN((unsigned long long)ci + 4 <= a.n_codes, st)) put_codes4(a.codes + ci, cq);
         } else {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -689,15 +699,19 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
           }
         }
         if (d.write_out) {
-          T* dst = a.Rout + ((unsigned long long)i * d.rs0 + (unsigned long long)j * d.rs1 + (unsigned long long)k0);
+          const unsigned long long od =
+              (unsigned long long)i * d.rs0 + (unsigned long long)j * d.rs1 + (unsigned long long)k0;
+          T* dst = a.Rout + od;
           if (IN || k0 + 8 <= m2) {
-            st4(dst, e[2], r[0], e[3], r[1]);
-            st4(dst + 4, e[4], r[2], e[5], r[3]);
+            if (SZ3G_IN(od + 8 <= a.n_out, st)) {
+              st4(dst, e[2], r[0], e[3], r[1]);
+              st4(dst + 4, e[4], r[2], e[5], r[3]);
+            }
           } else {
             const T v8[8] = {e[2], r[0], e[3], r[1], e[4], r[2], e[5], r[3]};
 #pragma unroll
             for (int s8 = 0; s8 < 8; ++s8)
-              if (k0 + s8 < m2) dst[s8] = v8[s8];
+              if (k0 + s8 < m2 && SZ3G_IN(od + s8 < a.n_out, st)) dst[s8] = v8[s8];
           }
         }
       }

@@ -1179,7 +1179,8 @@ __global__ void __launch_bounds__(kEncWarps * 32) emit_kernel(const EncArgs a, c
         __syncwarp();
         const uint32_t total = carry + round_bits;
         const uint32_t full = total >> 5;
-        for (uint32_t k = lane; k < full; k += 32) pay[wpos + k] = buf[k];
+        for (uint32_t k = lane; k < full; k += 32)
+          if (SZ3G_IN(wpos + k < wexcl + words, st)) pay[wpos + k] = buf[k];
         wpos += full;
         const uint32_t rest = buf[full];
         __syncwarp();
@@ -1196,7 +1197,8 @@ __global__ void __launch_bounds__(kEncWarps * 32) emit_kernel(const EncArgs a, c
           if (c8[q] == 0) {
             const unsigned long long xi = map_code_to_input(map, i0 + t + q);
             const U v = reinterpret_cast<const U*>(a.x)[xi];
-            unp[zr++] = v;
+            if (SZ3G_IN(a.mode != kEncodeStream || zr < st->n_unpred, st)) unp[zr] = v;
+            ++zr;
             // the quantizer sends every NaN / Inf to the unpredictable list
             nonfinite |= sizeof(U) == 4 ? ((v & 0x7f800000u) == 0x7f800000u)
                                         : ((v & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
@@ -1209,7 +1211,7 @@ __global__ void __launch_bounds__(kEncWarps * 32) emit_kernel(const EncArgs a, c
     // raw mode: the number of unpredictable values is known at the last chunk
     if (a.mode == kEncodeRaw && lane == 0 && j == a.n_chunks - 1) st->n_unpred = zpos;
     if (emit) {
-      if (carry && lane == 0) pay[wpos] = buf[0];
+      if (carry && lane == 0 && SZ3G_IN(wpos < wexcl + words, st)) pay[wpos] = buf[0];
       __syncwarp();
       if (lane == 0) buf[0] = 0;
       __syncwarp();
@@ -1316,8 +1318,9 @@ __device__ __forceinline__ void red_or_nz(uint32_t* p, uint32_t v) {
                "r"(v)
                : "memory");
 }
-__device__ __forceinline__ void ring_or(uint32_t* buf, uint32_t hi, uint32_t lo, uint32_t e) {
+__device__ __forceinline__ void ring_or(uint32_t* buf, uint32_t hi, uint32_t lo, uint32_t e, DevState* st) {
   const uint32_t we = (e - 1) >> 5, z = (0u - e) & 31u;
+  if (!SZ3G_IN(e >= 1 && we < (uint32_t)kPackRing - 2, st)) return;
   red_or_nz(&buf[we], lo << z);
   red_or_nz(&buf[we - 1], __funnelshift_l(lo, hi, z));
   red_or_nz(&buf[we - 2], __funnelshift_l(hi, 0u, z));
@@ -1396,7 +1399,7 @@ __device__ __forceinline__ void pack_chunk(const EncArgs& a, const PassMap& map,
       const uint32_t n = n2[h];
       o += n;  // the end of the half's string
       if (n <= 64) {
-        if (n) ring_or(buf, ahi[h], alo[h], o);
+        if (n) ring_or(buf, ahi[h], alo[h], o, st);
       } else {  // four codewords over 64 bits: the half as two strings of two
         uint32_t op = o - n;
         for (int p = 0; p < 2; ++p) {
@@ -1409,7 +1412,7 @@ __device__ __forceinline__ void pack_chunk(const EncArgs& a, const PassMap& map,
             m += e >> 24;
           }
           op += m;
-          if (m) ring_or(buf, xh, xl, op);
+          if (m) ring_or(buf, xh, xl, op, st);
         }
       }
     }
@@ -1421,7 +1424,8 @@ __device__ __forceinline__ void pack_chunk(const EncArgs& a, const PassMap& map,
     }
     __syncwarp();
     const uint32_t total = carry + round_bits, full = total >> 5;
-    for (uint32_t k = lane; k < full; k += 32) pay[wpos + k] = buf[k];
+    for (uint32_t k = lane; k < full; k += 32)
+      if (SZ3G_IN(wpos + k < words, st)) pay[wpos + k] = buf[k];
     wpos += full;
     const uint32_t rest = buf[full];
     __syncwarp();
@@ -1450,7 +1454,8 @@ __device__ __forceinline__ void pack_chunk(const EncArgs& a, const PassMap& map,
           const uint32_t c = (q & 1) ? cw[q >> 1] >> 16 : cw[q >> 1] & 0xffffu;
           if (c == 0) {
             const U x = reinterpret_cast<const U*>(a.x)[map_code_to_input(map, i0 + t + q)];
-            unp[zr++] = x;
+            if (SZ3G_IN(zr < nu, st)) unp[zr] = x;
+            ++zr;
             // the quantizer sends every NaN / Inf to the unpredictable list
             nonfinite |= sizeof(U) == 4 ? ((x & 0x7f800000u) == 0x7f800000u)
                                         : ((x & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
@@ -1461,7 +1466,7 @@ __device__ __forceinline__ void pack_chunk(const EncArgs& a, const PassMap& map,
       }
     }
   }
-  if (carry && lane == 0) pay[wpos] = buf[0];
+  if (carry && lane == 0 && SZ3G_IN(wpos < words, st)) pay[wpos] = buf[0];
   __syncwarp();
   if (lane == 0) buf[0] = 0;
   __syncwarp();
@@ -2098,11 +2103,14 @@ __global__ void __launch_bounds__(kDecThreads, 4) decode_kernel(const DecArgs a)
     const uint32_t nw = a.chunk_words[j];
     const uint16_t* sb = a.sub_bits ? a.sub_bits + j * (a.nsb - 1) : nullptr;
     uint32_t* zc = a.zcnt + j * a.nsb;
+    auto zset = [&](uint32_t q, uint32_t v) {  // zero codes of the chunk's sub-block q
+      if (SZ3G_IN(j * a.nsb + q < a.n_chunks * a.nsb, a.st)) zc[q] = v;
+    };
     unsigned long long bit0 = 0;  // start bit of the unit inside the chunk
     if (sb)
       for (uint32_t q = 0; q < b; ++q) bit0 += sb[q];
     if (c0 >= n_chunk) {  // past the end of a short last chunk
-      if (a.unit == SZ3G_SUBBLOCK) zc[b] = 0;
+      if (a.unit == SZ3G_SUBBLOCK) zset(b, 0u);
       return sb && b + 1 < a.nsb && sb[b] != 0;
     }
     const uint32_t c1 = min(c0 + a.unit, n_chunk);
@@ -2171,7 +2179,7 @@ __global__ void __launch_bounds__(kDecThreads, 4) decode_kernel(const DecArgs a)
     };
     for (uint32_t i = c0; i < c1; i += 8, out += 8) {  // c0 is a multiple of 8
       if (i != c0 && (i & (SZ3G_SUBBLOCK - 1)) == 0) {  // whole-chunk units count per sub-block
-        zc[(i >> 9) - 1] = zeros;
+        zset((i >> 9) - 1, zeros);
         zeros = 0;
       }
       // eight codes advance the window by at most 6 words
@@ -2196,7 +2204,8 @@ __global__ void __launch_bounds__(kDecThreads, 4) decode_kernel(const DecArgs a)
         }
         if (fail) break;
         if (count_zeros) zeros += zero_halves(pk[0]) + zero_halves(pk[1]) + zero_halves(pk[2]) + zero_halves(pk[3]);
-        *reinterpret_cast<uint4*>(out) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        if (SZ3G_IN(j * a.chunk + i + 8 <= a.n, a.st))
+          *reinterpret_cast<uint4*>(out) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
       } else {
         for (uint32_t q = 0; q < m; ++q) {
           uint32_t e;
@@ -2204,7 +2213,7 @@ __global__ void __launch_bounds__(kDecThreads, 4) decode_kernel(const DecArgs a)
             fail = true;
             break;
           }
-          out[q] = (uint16_t)(e >> 16);
+          if (SZ3G_IN(j * a.chunk + i + q < a.n, a.st)) out[q] = (uint16_t)(e >> 16);
           if (count_zeros) zeros += (e >> 16) == 0;
         }
         if (fail) break;
@@ -2213,9 +2222,9 @@ __global__ void __launch_bounds__(kDecThreads, 4) decode_kernel(const DecArgs a)
     // no copy may land in shared memory after the thread has left
     asm volatile("cp.async.wait_all;" ::: "memory");
     if (fail) return true;
-    zc[(c1 - 1) >> 9] = zeros;
+    zset((c1 - 1) >> 9, zeros);
     if (a.unit != SZ3G_SUBBLOCK)  // sub-blocks past the end of a short chunk
-      for (uint32_t q = ((c1 - 1) >> 9) + 1; q < a.nsb; ++q) zc[q] = 0;
+      for (uint32_t q = ((c1 - 1) >> 9) + 1; q < a.nsb; ++q) zset(q, 0u);
     // bits consumed from the chunk start; the recorded sub-block boundary
     // must be exactly where decoding ended
     const unsigned long long used = bit0 + (unsigned long long)((wk - 2) * 32u + bp - start_bit);

@@ -850,12 +850,12 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
         const T xv = a.x[(unsigned long long)g0 * P.xs[0] + (unsigned long long)g1 * P.xs[1] +
                          (unsigned long long)g2 * P.xs[2]];
         const uint32_t code = quantize_point<T>(xv, pred, ebT, ebr, radius, r);
-        a.codes[ci] = (uint16_t)code;
+        if (SZ3G_IN(ci < a.n_codes && ci < npts, st)) a.codes[ci] = (uint16_t)code;
         atomicAdd(&a.hist[code], 1u);
         if (code == 0) atomicAdd(&s_nz, 1u);
         if (!isfinite(xv)) s_bad = 1;
       } else {
-        const uint32_t code = Kc[ci];
+        const uint32_t code = SZ3G_IN(ci < npts, st) ? Kc[ci] : 0u;
         if (code == 0) {
           const unsigned long long rk = rank_of_zero(a.codes, ci, d.chunk, d.nsub, a.zunit);
           if (rk < a.n_unpred) {
@@ -871,7 +871,9 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
           r = recover_point<T>(pred, code, radius, ebT);
         }
       }
-      R[v] = r;
+      if (SZ3G_IN(v < npts && v >= vst && (!hb || v + vst < npts) && (!hc || v >= 3 * vst) &&
+                      (!hd || v + 3 * vst < npts), st))
+        R[v] = r;
     }
     __syncthreads();
   }
@@ -879,8 +881,9 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
   const uint32_t tot = a.Rout ? d.mk[0] * d.mk[1] * d.mk[2] : 0u;
   for (uint32_t f = tid; f < tot; f += kCoarseThreads) {
     const uint32_t c2 = f % d.mk[2], c1 = (f / d.mk[2]) % d.mk[1], c0 = f / (d.mk[2] * d.mk[1]);
-    a.Rout[(unsigned long long)c0 * d.rs[0] + (unsigned long long)c1 * d.rs[1] + (unsigned long long)c2 * d.rs[2]] =
-        R[c0 * d.gs[0] + c1 * d.gs[1] + c2 * d.gs[2]];
+    const unsigned long long od =
+        (unsigned long long)c0 * d.rs[0] + (unsigned long long)c1 * d.rs[1] + (unsigned long long)c2 * d.rs[2];
+    if (SZ3G_IN(od < a.n_out, st)) a.Rout[od] = R[c0 * d.gs[0] + c1 * d.gs[1] + c2 * d.gs[2]];
   }
   if (tid == 0) {
     if (COMP) {
@@ -1557,10 +1560,16 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
   a.x = x;
   for (int q = 0; q < 3; ++q) a.xs[q] = pl.fstride[q + 1];
   a.codes = codes;
+#ifdef SZ3G_CHECK
+  a.n_codes = pl.N;
+#endif
   a.hist = hist;
   a.st = st;
   a.radius = (int)pl.radius;
   a.Rout = kc == 0 ? nullptr : (T*)R[kc];  // the finest grid's reconstruction is not kept
+#ifdef SZ3G_CHECK
+  a.n_out = kc == 0 ? 0 : pl.gsize[kc];
+#endif
   int rc = run_coarse<T, true>(pl, kc, a, s);
   if (rc) return rc;
   // levels on G_1 and coarser read the decimated pyramid
@@ -1572,6 +1581,9 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
   for (int k = kc - 1; k >= 0; --k) {
     a.Rc = (const T*)R[k + 1];
     a.Rout = k == 0 ? nullptr : (T*)R[k];
+#ifdef SZ3G_CHECK
+    a.n_out = k == 0 ? 0 : pl.gsize[k];
+#endif
     if (dec && k >= 1) {
       a.x = (const T*)((unsigned char*)X + xpyr_offset(pl, k));
       a.xs[1] = xk_pitch(pl, k);
@@ -1621,6 +1633,9 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
   const int kc = coarse_grid(pl);
   LevelArgs<T> a{};
   a.codes = const_cast<uint16_t*>(codes);
+#ifdef SZ3G_CHECK
+  a.n_codes = pl.N;
+#endif
   a.st = st;
   a.radius = (int)pl.radius;
   a.unpred = unpred;
@@ -1629,11 +1644,17 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
   a.ebT = ebT;
   a.codes_padded = codes_padded;
   a.Rout = kc == 0 ? out : (T*)R[kc];
+#ifdef SZ3G_CHECK
+  a.n_out = kc == 0 ? pl.N : pl.gsize[kc];
+#endif
   int rc = run_coarse<T, false>(pl, kc, a, s);
   if (rc) return rc;
   for (int k = kc - 1; k >= 0; --k) {
     a.Rc = (const T*)R[k + 1];
     a.Rout = k == 0 ? out : (T*)R[k];
+#ifdef SZ3G_CHECK
+    a.n_out = k == 0 ? pl.N : pl.gsize[k];
+#endif
     if (lq) {
       queue_add<T>(lq, pl, k, field, a);
       continue;

@@ -27,6 +27,10 @@ struct LevelArgs {
   int radius;
   T ebT;               // decompress (compress reads the device state)
   int codes_padded;    // decompress: at least 256 readable bytes follow the codes
+#ifdef SZ3G_CHECK
+  unsigned long long n_codes;  // codes in the array (index checks)
+  unsigned long long n_out;    // elements of Rout (index checks)
+#endif
 };
 
 // Asynchronous 4- or 8-byte global -> shared copy.

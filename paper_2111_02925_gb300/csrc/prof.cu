@@ -1,4 +1,5 @@
-// prof.cu -- launch accounting and optional per-kernel CUDA-event timing.
+// prof.cu -- launch accounting, optional per-kernel CUDA-event timing and the
+// NVTX ranges of the entry points.
 //
 // Every kernel launch of the library goes through a LaunchScope, which counts
 // it and, while profiling is on, records a CUDA event before and after it on
@@ -8,9 +9,14 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 namespace sz3g {
+
+TraceRange::TraceRange(const char* name) { nvtxRangePushA(name); }
+TraceRange::~TraceRange() { nvtxRangePop(); }
 
 static const char* kKernelNames[kKernelCount] = {
     "range", "eb", "anchor", "lift", "pass_quantize", "pass_recover", "codebook", "encode", "finalize",

@@ -31,6 +31,7 @@ E_CORRUPT = -5
 E_CUDA = -6
 E_NOMEM = -7
 E_TIMEOUT = -8
+E_CHECK = -9  # checking build only
 
 
 class SZ3GError(RuntimeError):
@@ -119,10 +120,11 @@ def lib_path() -> str:
     return _build.LIB
 
 
-def load(path: str | None = None):
-    """Load the built library (raises if it is missing)."""
+def load(path: str | None = None, reload: bool = False):
+    """Load the built library (raises if it is missing).  reload: drop the
+    library loaded so far and load `path` (the checking build, or back)."""
     global _lib
-    if _lib is not None:
+    if _lib is not None and not reload:
         return _lib
     path = path or _build.LIB
     if not os.path.exists(path):
