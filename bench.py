@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the REL 1e-2 / 1e-4 timings of the field")
     ap.add_argument("--workload", default="field", choices=["field", "batch", "selector", "lossless", "pastri"])
-    ap.add_argument("--train-fields", type=int, default=400)
+    ap.add_argument("--train-fields", type=int, default=2000)
+    ap.add_argument("--train-size", type=int, default=128,
+                    help="points per axis of the selector workload's training fields (0: 32..64 at random)")
     ap.add_argument("--fields", type=int, default=256)
     ap.add_argument("--no-extras", action="store_true", help="skip the batch / selector / lossless figures")
     ap.add_argument("--extra-train-fields", type=int, default=160)
@@ -443,7 +445,10 @@ def run_batch(args):
 
 
 def _label_field(job):
-    """Oracle labels of one training field (runs in a spawned worker)."""
+    """Oracle labels (exhaustive trial) and input features (8 sampled blocks
+    per level) of one training field, per level; runs in a spawned worker.
+    The GPU's features equal the oracle's to 1e-10 (tests/test_gpu_select.py),
+    so the network trained on these is applied to the GPU's."""
     import numpy as np
 
     import oracle as O
@@ -453,7 +458,9 @@ def _label_field(job):
     x = S.grf_fronts(shape, seed, fronts)
     op = O.make_params(shape, eb, eb_mode=O.REL)
     _, L = O.shape(op)
-    return [int(np.argmin(O.select_costs(op, x, l))) for l in range(1, L + 1)]
+    labels = [int(np.argmin(O.select_costs(op, x, l))) for l in range(1, L + 1)]
+    feats = [O.select_features(op, x, l, 8, seed).tolist() for l in range(1, L + 1)]
+    return labels, feats
 
 
 def fronts_gpu(shape, seed, n_fronts, dev):
@@ -487,7 +494,7 @@ def run_selector(args):
     each selection."""
     import numpy as np
 
-    jobs, labels = label_jobs(args.train_fields)  # before any GPU call
+    jobs, labels, tfeats = label_jobs(args.train_fields, args.train_size)  # before any GPU call
     import torch
 
     from oracle import mlp as M
@@ -501,9 +508,7 @@ def run_selector(args):
     G.load()
     sh = int(torch.cuda.current_stream().cuda_stream)
     feats, ys = [], []
-    for (shape, seed, fr, eb), lab in zip(jobs, labels):
-        x = torch.from_numpy(S.grf_fronts(shape, seed, fr).reshape(-1)).to(dev)
-        f = G.sz3g_select_features(G.make_params(shape, eb, eb_mode=G.REL), x.data_ptr(), 8, seed, sh)
+    for f, lab in zip(tfeats, labels):
         feats.extend(f)
         ys.extend(lab)
     feats = np.array(feats)
@@ -565,7 +570,8 @@ def run_selector(args):
         "value": raw / res["learned"], "unit": "ratio", "n_gpus": 1, "higher_is_better": True,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "1024^3 FP32 k^-3 random field + 16 tanh fronts (seed 5), REL eb 1e-4; network "
-                               f"trained on {args.train_fields} oracle-labelled fields of 32..64 per axis",
+                               f"trained on {args.train_fields} oracle-labelled fields of "
+                               + (f"{args.train_size}^3 points" if args.train_size > 0 else "32..64 points per axis"),
                    "sample_blocks": {"sampled": 64, "learned_features": 16}},
         "ratio": {k: raw / v for k, v in res.items()},
         "learned_vs_sampled": res["sampled"] / res["learned"],
@@ -866,11 +872,10 @@ def extras(args, dev, xd, out, nb, pool_labels):
         from oracle import mlp as M
 
         t0 = time.perf_counter()
-        jobs, labels = pool_labels
+        jobs, labels, tfeats = pool_labels
         feats, ys = [], []
-        for (shape, seed, fr, eb), lab in zip(jobs, labels):
-            x = torch.from_numpy(S.grf_fronts(shape, seed, fr).reshape(-1)).to(dev)
-            feats.extend(G.sz3g_select_features(G.make_params(shape, eb, eb_mode=G.REL), x.data_ptr(), 8, seed, sh))
+        for f, lab in zip(tfeats, labels):
+            feats.extend(f)
             ys.extend(lab)
         feats = np.array(feats)
         ys = np.array(ys, np.int32)
@@ -944,9 +949,10 @@ def extras(args, dev, xd, out, nb, pool_labels):
     return res
 
 
-def label_jobs(n_fields):
-    """Oracle labels (exhaustive trial) of n small training fields, in a spawned
-    process pool: (jobs, labels)."""
+def label_jobs(n_fields, size=0):
+    """Oracle labels (exhaustive trial) and features of n training fields (size^3
+    points, or 32..64 per axis at random for size 0), in a spawned process
+    pool: (jobs, labels, features)."""
     import multiprocessing as mp
 
     import numpy as np
@@ -954,12 +960,12 @@ def label_jobs(n_fields):
     rng = np.random.default_rng(31)
     jobs = []
     for i in range(n_fields):
-        shape = tuple(int(v) for v in rng.integers(32, 65, 3))
+        shape = (size, size, size) if size > 0 else tuple(int(v) for v in rng.integers(32, 65, 3))
         eb = float(np.exp(rng.uniform(np.log(1e-5), np.log(1e-2))))
         jobs.append((shape, 20000 + i, int(rng.integers(0, 17)), eb))
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        labels = pool.map(_label_field, jobs)
-    return jobs, labels
+        out = pool.map(_label_field, jobs, chunksize=4)
+    return jobs, [o[0] for o in out], [o[1] for o in out]
 
 
 def main():
@@ -1155,7 +1161,7 @@ def main():
         cpu = cpu_baseline(x)
     ext = None
     if rank == 0 and ws == 1 and not args.no_extras:
-        ext = extras(args, dev, xd, out, nb, pool_labels or ([], []))
+        ext = extras(args, dev, xd, out, nb, pool_labels or ([], [], []))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
