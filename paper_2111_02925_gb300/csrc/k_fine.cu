@@ -505,7 +505,10 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
     auto passes = [&](auto interior_tag) {
       constexpr bool IN = decltype(interior_tag)::value;
       // ---- coarse points into E, and pass 0 (odd i, even j) ----------------
-      for (int t = tid; t < S::kCopyTasks + S::kP0Tasks; t += kFineThreads) {
+      // pass-0 tasks start on a warp boundary (kCopyPad), so that their
+      // half-warps take whole rows as well
+      constexpr int kCopyPad = (S::kCopyTasks + 31) & ~31;
+      for (int t = tid; t < kCopyPad + S::kP0Tasks; t += kFineThreads) {
         if (t < S::kCopyTasks) {
           static_assert(S::kPairs == 18, "pair_task takes rows of 18 pairs");
           int pr, row;
@@ -516,8 +519,9 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
           est2(((2 * e) * S::kXJ + 2 * cj) * S::kEK + 2 * pr, v[0], v[1]);
           continue;
         }
+        if (t < kCopyPad) continue;
         if constexpr (S::kHas0) {
-          const int u = t - S::kCopyTasks;
+          const int u = t - kCopyPad;
           int pr, row;
           pair_task(u, S::kP0Tasks / S::kPairs, row, pr);
           const int eo = row / S::kCJ, cj = row % S::kCJ;
