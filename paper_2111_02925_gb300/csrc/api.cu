@@ -290,14 +290,14 @@ int compress_enqueue_pre(const sz3g_params* p, const Plan& pl, const void* d_in,
   *st_out = st;
   SZ3G_CUDA(cudaMemsetAsync(ws, 0, L.cb, s));  // state, histogram, tables, look-back status
   void* X = xpyr_bytes(pl) ? ws + L.x1 : nullptr;
-  bool x1_ready = false;
+  bool pyr_ready = false;
   SZ3G_TRY(launch_range_eb(pl, d_in, st, ws + L.range, range_scratch_bytes(pl), (int)p->eb_mode, p->eb, s, X,
-                           &x1_ready));
+                           &pyr_ready));
   void* R[34];
   for (int k = 0; k <= pl.L; ++k) R[k] = (k == 0 && level_path_ok(pl)) ? nullptr : ws + L.R[k];
   uint16_t* codes = (uint16_t*)(ws + L.codes);
   uint32_t* hist = (uint32_t*)(ws + L.hist);
-  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, X, x1_ready, s, lq, field));
+  SZ3G_TRY(launch_quantize_levels(pl, d_in, codes, R, hist, st, X, pyr_ready, s, lq, field));
   return SZ3G_OK;
 }
 

@@ -277,10 +277,13 @@ __device__ __forceinline__ double bits_to<double>(unsigned long long b) {
 // ---------------------------------------------------------------------------
 // k_interp.cu
 size_t range_scratch_bytes(const Plan& pl);
-// REL with X1 (the first level of the decimated pyramid): the range pass
-// also writes X_1 when the field's rows allow it (*wrote_x1).
+// REL with X1 (the decimated pyramid): the range pass also writes X_1 ..
+// X_{kc-1}, every copy the levels read, when the field's rows allow it
+// (*wrote_pyr).
 int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratch, size_t scratch_bytes,
-                    int eb_mode, double eb, cudaStream_t s, void* X1 = nullptr, bool* wrote_x1 = nullptr);
+                    int eb_mode, double eb, cudaStream_t s, void* X1 = nullptr, bool* wrote_pyr = nullptr);
+// The grid of the coarse group (levels on it and coarser run in one CTA).
+int coarse_grid(const Plan& pl);
 // Cross-field work queue of grid levels (k_level.cu): with a queue, the
 // level paths below launch the coarse group (and the decimated pyramid) and
 // collect the finer levels of the field into the queue instead of launching
@@ -295,7 +298,7 @@ int level_queue_launch(LevelQueue* q, cudaStream_t s);       // descriptors buil
 int level_queue_upload(LevelQueue* q);                        // descriptors to the device, before a run
 
 int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R,
-                           uint32_t* hist, DevState* st, void* X1, bool x1_ready, cudaStream_t s,
+                           uint32_t* hist, DevState* st, void* X1, bool pyr_ready, cudaStream_t s,
                            LevelQueue* lq = nullptr, int field = 0);
 int launch_recover_levels(const Plan& pl, const uint16_t* codes, const void* unpred,
                           unsigned long long n_unpred, const unsigned long long* zunit,
@@ -322,7 +325,7 @@ struct SlabSink {
 };
 extern thread_local const SlabSink* g_slab_sink;
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                          DevState* st, void* X1, bool x1_ready, cudaStream_t s, LevelQueue* lq = nullptr,
+                          DevState* st, void* X1, bool pyr_ready, cudaStream_t s, LevelQueue* lq = nullptr,
                           int field = 0);
 // Decimated copies of the field X_k = x[::2^k, ::2^k, ::2^k] over G_k, k >= 1
 // (rows pitched to 16 bytes, one after another): the inputs of the coarser

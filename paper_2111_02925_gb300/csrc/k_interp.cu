@@ -95,14 +95,19 @@ __device__ __forceinline__ void block_minmax(T& mn, T& mx, T* smn, T* smx) {
   }
 }
 
-// Where the range pass also writes the decimated copy X_1 = x[::2, ::2, ::2]
-// (rows of the padded 3-D view, each a whole number of 16-byte vectors).
+// Where the range pass also writes the decimated copies X_k = x[::2^k, ::2^k,
+// ::2^k], k = 1 .. kmax (rows of the padded 3-D view, each a whole number of
+// 16-byte vectors): the inputs of the coarser levels, written from the rows
+// it reads anyway.
+constexpr int kRangePyr = 16;  // most levels written by the range pass
 template <typename T>
 struct RangeRows {
   T* X1;                      // null: flat pass, no copy
   unsigned long long a1, a2;  // extents of axes 1 and 2 (rows: a0 x a1, row length a2)
   unsigned long long rows;    // a0 * a1
   unsigned long long p0, p1;  // X_1 strides (elements) along axes 0 and 1
+  int kmax;                   // X_2 .. X_kmax too (kmax <= 1: X_1 only)
+  unsigned long long off[kRangePyr + 1], q0[kRangePyr + 1], q1[kRangePyr + 1];  // X_k: offset from X_1, strides
 };
 
 // Min / max / finiteness of the field with 16-byte loads (the field is 16-byte
@@ -157,6 +162,14 @@ __global__ void __launch_bounds__(kRangeThreads) range_partial_kernel(const T* _
             } else {
               dp[v] = q[u].x;
             }
+            // X_k, k >= 2: element c = e >> k of rows with i, j multiples of
+            // 2^k, for the vector's first element e = kPer v a multiple of 2^k
+            for (int k = 2; k <= rows.kmax; ++k) {
+              const unsigned long long mk = (1ull << k) - 1;
+              const int sv = k - (sizeof(T) == 4 ? 2 : 1);  // e multiple of 2^k <=> v multiple of 2^sv
+              if (((i | j) & mk) != 0 || (v & ((1ull << sv) - 1)) != 0) break;
+              rows.X1[rows.off[k] + (i >> k) * rows.q0[k] + (j >> k) * rows.q1[k] + (v >> sv)] = q[u].x;
+            }
           }
         }
       }
@@ -209,44 +222,47 @@ __global__ void eb_kernel(int eb_mode, double eb, DevState* st) {
 size_t range_scratch_bytes(const Plan&) { return (size_t)kRangeBlocks * 2 * 8; }
 
 int launch_range_eb(const Plan& pl, const void* d_in, DevState* st, void* scratch, size_t scratch_bytes,
-                    int eb_mode, double eb, cudaStream_t s, void* X1, bool* wrote_x1) {
+                    int eb_mode, double eb, cudaStream_t s, void* X1, bool* wrote_pyr) {
   if (scratch_bytes < range_scratch_bytes(pl)) return SZ3G_E_CAPACITY;
-  if (wrote_x1) *wrote_x1 = false;
+  if (wrote_pyr) *wrote_pyr = false;
   int nparts = 1;
   if (eb_mode == SZ3G_EB_REL) {
     const int per = 16 / pl.esz;
     unsigned long long want = (pl.N / per + kRangeThreads * 4 - 1) / (kRangeThreads * 4);
     nparts = (int)(want < kRangeBlocks ? (want ? want : 1) : kRangeBlocks);
-    // the decimated copy comes with the pass when rows are whole vectors
-    const bool rows_ok = X1 && pl.n[0] == 1 && pl.L >= 1 && pl.n[3] % (unsigned long long)per == 0;
+    // the decimated copies the levels read (X_1 .. X_{kc-1}, kc the coarse
+    // group's grid) come with the pass when rows are whole vectors
+    const int kmax = coarse_grid(pl) - 1;
+    const bool rows_ok = X1 && pl.n[0] == 1 && pl.L >= 1 && pl.n[3] % (unsigned long long)per == 0 &&
+                         kmax <= kRangePyr;
+    auto fill = [&](auto& r, auto* base) {
+      r.X1 = base;
+      r.a1 = pl.n[2];
+      r.a2 = pl.n[3];
+      r.rows = pl.n[1] * pl.n[2];
+      r.p1 = xk_pitch(pl, 1);
+      r.p0 = r.p1 * pl.gm[1][2];
+      r.kmax = kmax;
+      for (int k = 2; k <= kmax; ++k) {
+        r.off[k] = xpyr_offset(pl, k) / pl.esz;
+        r.q1[k] = xk_pitch(pl, k);
+        r.q0[k] = r.q1[k] * pl.gm[k][2];
+      }
+    };
     if (pl.dtype == SZ3G_F32) {
       RangeRows<float> r{};
-      if (rows_ok) {
-        r.X1 = (float*)X1;
-        r.a1 = pl.n[2];
-        r.a2 = pl.n[3];
-        r.rows = pl.n[1] * pl.n[2];
-        r.p1 = xk_pitch(pl, 1);
-        r.p0 = r.p1 * pl.gm[1][2];
-      }
+      if (rows_ok) fill(r, (float*)X1);
       SZ3G_LAUNCH(kKRange, s,
                   range_partial_kernel<float><<<nparts, kRangeThreads, 0, s>>>((const float*)d_in, pl.N,
                                                                                 (float*)scratch, st, eb_mode, eb, r));
     } else {
       RangeRows<double> r{};
-      if (rows_ok) {
-        r.X1 = (double*)X1;
-        r.a1 = pl.n[2];
-        r.a2 = pl.n[3];
-        r.rows = pl.n[1] * pl.n[2];
-        r.p1 = xk_pitch(pl, 1);
-        r.p0 = r.p1 * pl.gm[1][2];
-      }
+      if (rows_ok) fill(r, (double*)X1);
       SZ3G_LAUNCH(kKRange, s,
                   range_partial_kernel<double><<<nparts, kRangeThreads, 0, s>>>((const double*)d_in, pl.N,
                                                                                  (double*)scratch, st, eb_mode, eb, r));
     }
-    if (wrote_x1) *wrote_x1 = rows_ok;
+    if (wrote_pyr) *wrote_pyr = rows_ok;
   } else if (pl.dtype == SZ3G_F32) {
     SZ3G_LAUNCH(kKEb, s, eb_kernel<float><<<1, 32, 0, s>>>(eb_mode, eb, st));
   } else {
@@ -476,8 +492,8 @@ static int quantize_levels_t(const Plan& pl, const T* x, uint16_t* codes, void* 
 }
 
 int launch_quantize_levels(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                           DevState* st, void* X1, bool x1_ready, cudaStream_t s, LevelQueue* lq, int field) {
-  if (level_path_ok(pl)) return launch_quantize_fused(pl, d_in, codes, R, hist, st, X1, x1_ready, s, lq, field);
+                           DevState* st, void* X1, bool pyr_ready, cudaStream_t s, LevelQueue* lq, int field) {
+  if (level_path_ok(pl)) return launch_quantize_fused(pl, d_in, codes, R, hist, st, X1, pyr_ready, s, lq, field);
   if (pl.dtype == SZ3G_F32) return quantize_levels_t<float>(pl, (const float*)d_in, codes, R, hist, st, s);
   return quantize_levels_t<double>(pl, (const double*)d_in, codes, R, hist, st, s);
 }

@@ -1518,9 +1518,10 @@ __global__ void pyramid_kernel(T* __restrict__ X, const __grid_constant__ PyrDes
   }
 }
 
-// X_1 (unless the range pass wrote it) and X_2 .. X_kmax into the pyramid.
-static int launch_decimate(const Plan& pl, const void* x, unsigned char* X, int kmax, bool x1_ready, cudaStream_t s) {
-  if (!x1_ready) {
+// X_1 .. X_kmax into the pyramid, unless the range pass wrote them.
+static int launch_decimate(const Plan& pl, const void* x, unsigned char* X, int kmax, bool pyr_ready, cudaStream_t s) {
+  if (pyr_ready) return SZ3G_OK;  // the range pass wrote X_1 .. X_kmax
+  {
     const unsigned long long* m = pl.gm[1];
     const unsigned long long p1 = xk_pitch(pl, 1), p0 = p1 * m[2];
     const unsigned blocks = (unsigned)((m[1] * m[2] + 7) / 8);
@@ -1554,7 +1555,7 @@ static int launch_decimate(const Plan& pl, const void* x, unsigned char* X, int 
 
 template <typename T>
 static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* const* R, uint32_t* hist, DevState* st,
-                          void* X, bool x1_ready, cudaStream_t s, LevelQueue* lq, int field) {
+                          void* X, bool pyr_ready, cudaStream_t s, LevelQueue* lq, int field) {
   const int kc = coarse_grid(pl);
   LevelArgs<T> a{};
   a.x = x;
@@ -1575,7 +1576,7 @@ static int quantize_fused(const Plan& pl, const T* x, uint16_t* codes, void* con
   // levels on G_1 and coarser read the decimated pyramid
   const bool dec = X && kc >= 2;
   if (dec) {
-    rc = launch_decimate(pl, x, (unsigned char*)X, kc - 1, x1_ready, s);
+    rc = launch_decimate(pl, x, (unsigned char*)X, kc - 1, pyr_ready, s);
     if (rc) return rc;
   }
   for (int k = kc - 1; k >= 0; --k) {
@@ -1671,10 +1672,10 @@ static int recover_fused(const Plan& pl, const uint16_t* codes, const T* unpred,
 }
 
 int launch_quantize_fused(const Plan& pl, const void* d_in, uint16_t* codes, void* const* R, uint32_t* hist,
-                          DevState* st, void* X, bool x1_ready, cudaStream_t s, LevelQueue* lq, int field) {
+                          DevState* st, void* X, bool pyr_ready, cudaStream_t s, LevelQueue* lq, int field) {
   if (pl.dtype == SZ3G_F32)
-    return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, X, x1_ready, s, lq, field);
-  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, X, x1_ready, s, lq, field);
+    return quantize_fused<float>(pl, (const float*)d_in, codes, R, hist, st, X, pyr_ready, s, lq, field);
+  return quantize_fused<double>(pl, (const double*)d_in, codes, R, hist, st, X, pyr_ready, s, lq, field);
 }
 
 int launch_recover_fused(const Plan& pl, const uint16_t* codes, const void* unpred, unsigned long long n_unpred,
