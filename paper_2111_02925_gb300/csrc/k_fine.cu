@@ -16,8 +16,10 @@
 //   x box   (compress) input rows i in [A0, A0+T0), j in [A1-2, A1+T1+3),
 //           k in [A2-4, A2+68)                      -- tensor copy
 //   C box   R_{k+1} points (i/2, j/2, k/2) around the tile    -- tensor copy
-//   codes   (recover) every row of codes the tile's passes read -- 16-byte
-//           cp.async pieces (or one bulk copy per row)
+//   codes   (recover) every row of codes the tile's passes read -- one
+//           tensor copy per pass when each pass's codes form 16-byte
+//           aligned rows (the pass's lattice as a 3-D array of 2-byte codes),
+//           else one bulk copy per row (or 16-byte cp.async pieces)
 // With two stages the next tile's copies are issued before the current tile
 // is computed; with one (the configuration in use) they are issued when the
 // tile starts and other CTAs of the SM cover the wait.
@@ -114,6 +116,7 @@ struct FineDesc {
   uint32_t chunk, nsub;
   int write_out;
   uint32_t tensor_bytes;       // bytes of the x and coarse boxes of one tile
+  int code_tma;                // recover: code rows by one tensor copy per pass
 };
 
 // ---- vector helpers -----------------------------------------------------------
@@ -291,7 +294,8 @@ __device__ __forceinline__ void code_row(long long c0, long long* a16, int* o) {
 template <typename T, bool COMP, int INTERP, int T0>
 __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMinBlocks)
     fine_kernel(const FineDesc d, const LevelArgs<T> a, const __grid_constant__ CUtensorMap tmx,
-                const __grid_constant__ CUtensorMap tmc) {
+                const __grid_constant__ CUtensorMap tmc, const __grid_constant__ CUtensorMap tmk0,
+                const __grid_constant__ CUtensorMap tmk1, const __grid_constant__ CUtensorMap tmk2) {
   using S = FineShape<T0>;
   using L = FineLayout<T, COMP, T0>;
   constexpr int kFineThreads = FineThreads<COMP>::kN;
@@ -324,7 +328,8 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
     s_timeout = 0;
     s_bytes[0] = s_bytes[1] = 0;
     // recover with per-row arrivals: one arrival per staged code row
-    const uint32_t arrivals = (!COMP && kCodeRowArrive) ? (uint32_t)(S::kR2 + S::kR1 + S::kR0) : 1u;
+    const uint32_t arrivals =
+        (!COMP && kCodeRowArrive && !d.code_tma) ? (uint32_t)(S::kR2 + S::kR1 + S::kR0) : 1u;
     mbar_init(&bar[0], arrivals);
     mbar_init(&bar[1], arrivals);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -369,6 +374,22 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
   auto issue = [&](uint32_t tile, int b) {
     int A0, A1, A2;
     tile_origin(tile, A0, A1, A2);
+    if (!COMP && d.code_tma) {
+      // the code rows of each pass as one box of the pass's code lattice, laid
+      // out as the per-row copies place them: pass-2 rows of 40 codes from
+      // k/2 = A2/2, pass-1 and pass-0 rows of 48 from A2/2 - 8 (rows and
+      // codes outside the lattice read as 0 and are never used)
+      if (tid == 0) {
+        uint16_t* Kb = Ks + b * KB;
+        fence_proxy_async_smem();
+        mbar_expect_tx(&bar[b], d.tensor_bytes + (uint32_t)S::kCodeSlots * 2u);
+        tma_load_3d(Cs + b * CB, &tmc, A2 / 2 - 4, A1 / 2 - 1, S::kHas0 ? A0 / 2 - 1 : 0, &bar[b]);
+        tma_load_3d(Kb, &tmk2, A2 / 2, A1, A0, &bar[b]);
+        tma_load_3d(Kb + S::kR2 * S::kL2, &tmk1, A2 / 2 - 8, A1 / 2, A0, &bar[b]);
+        if (S::kHas0) tma_load_3d(Kb + S::kR2 * S::kL2 + S::kR1 * S::kL01, &tmk0, A2 / 2 - 8, A1 / 2 - 1, A0 / 2, &bar[b]);
+      }
+      return;
+    }
     if (!COMP && kCodeRowArrive) {
       // row r by thread r: its arrival announces its bytes (thread 0 also the
       // coarse box's), then its copy
@@ -751,7 +772,8 @@ __global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMin
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 // 3-D tensor map over rows of m2 elements (row stride s1, plane stride s0
-// elements) with a box of b0 x b1 x b2 elements.
+// elements) with a box of b0 x b1 x b2 elements (T: float, double or the
+// 2-byte codes).
 template <typename T>
 static bool fine_map(CUtensorMap* map, const T* base, int m0, int m1, int m2, unsigned long long s0,
                      unsigned long long s1, int b0, int b1, int b2) {
@@ -761,7 +783,9 @@ static bool fine_map(CUtensorMap* map, const T* base, int m0, int m1, int m2, un
   const cuuint64_t strides[2] = {(cuuint64_t)s1 * sizeof(T), (cuuint64_t)s0 * sizeof(T)};
   const cuuint32_t box[3] = {(cuuint32_t)b2, (cuuint32_t)b1, (cuuint32_t)b0};
   const cuuint32_t es[3] = {1, 1, 1};
-  const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const CUtensorMapDataType dt = sizeof(T) == 2   ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                : sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
   return enc(map, dt, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -812,10 +836,12 @@ static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_f
   d.ntiles = g1 * (uint32_t)d.nt1 * (uint32_t)d.nt2;
   int p = S::kHas0 ? 0 : 1;
   int interp = SZ3G_LINEAR;
+  uint32_t E0[3] = {0u, 0u, 0u};  // lattice extent of each pass along axis 0
   for (int i = 0; i < pl.n_pass; ++i) {
     const PassDesc& pd = pl.pass[i];
     if (pd.grid != k) continue;
     d.off[p] = (uint32_t)pd.off;
+    E0[p] = pd.E[1];
     d.E1[p] = pd.E[2];
     d.E2[p] = pd.E[3];
     interp = pd.interp;
@@ -841,6 +867,24 @@ static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_f
     ok = ok && fine_map<T>(&tmx, a.x, d.m0, d.m1, d.m2, a.xs[0], a.xs[1], S::kT0, S::kXJ, S::kXK);
     d.tensor_bytes += (uint32_t)(S::kT0 * S::kXJ * S::kXK * sizeof(T));
   }
+  CUtensorMap tmk[3];
+  memset(tmk, 0, sizeof(tmk));
+  if (!COMP) {
+    // code rows by tensor copies when every pass's codes start on a 16-byte
+    // boundary and its rows are a multiple of 16 bytes long
+    bool tma = ((uintptr_t)a.codes % 16) == 0;
+    for (int q = S::kHas0 ? 0 : 1; q < 3; ++q) tma = tma && d.E2[q] % 8 == 0 && d.off[q] % 8 == 0;
+    if (tma) {
+      for (int q = S::kHas0 ? 0 : 1; q < 3 && ok; ++q) {
+        const int rows = q == 2 ? S::kT1 : (q == 1 ? S::kT1 / 2 : S::kCJ);
+        const int planes = q == 0 ? 2 : S::kT0;
+        ok = fine_map<uint16_t>(&tmk[q], a.codes + d.off[q], (int)E0[q], (int)d.E1[q], (int)d.E2[q],
+                                (unsigned long long)d.E1[q] * d.E2[q], d.E2[q], planes, rows,
+                                q == 2 ? S::kL2 : S::kL01);
+      }
+      d.code_tma = 1;
+    }
+  }
   if (!ok) return SZ3G_E_CUDA;
   const size_t smem = FineLayout<T, COMP, T0>::kBytes;
   auto kern = interp == SZ3G_CUBIC ? fine_kernel<T, COMP, SZ3G_CUBIC, T0> : fine_kernel<T, COMP, SZ3G_LINEAR, T0>;
@@ -855,7 +899,7 @@ static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_f
   if (g_level_cta_cap > 0 && grid > (unsigned long long)g_level_cta_cap) grid = (unsigned long long)g_level_cta_cap;
   if (grid > d.ntiles - d.tile0) grid = d.ntiles - d.tile0;
   SZ3G_LAUNCH(COMP ? kKLevelQuantize : kKLevelRecover, s,
-              kern<<<(unsigned)grid, FineThreads<COMP>::kN, smem, s>>>(d, a, tmx, tmc));
+              kern<<<(unsigned)grid, FineThreads<COMP>::kN, smem, s>>>(d, a, tmx, tmc, tmk[0], tmk[1], tmk[2]));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
