@@ -1423,16 +1423,24 @@ __device__ __forceinline__ void pack_chunk(const EncArgs& a, const PassMap& map,
       sbits = 0;
     }
     __syncwarp();
+    // the round's full words leave (and are cleared); the partial word moves
+    // to the front of the ring
     const uint32_t total = carry + round_bits, full = total >> 5;
-    for (uint32_t k = lane; k < full; k += 32)
-      if (SZ3G_IN(wpos + k < words, st)) pay[wpos + k] = buf[k];
-    wpos += full;
     const uint32_t rest = buf[full];
-    __syncwarp();
-    for (uint32_t k = lane; k <= full; k += 32) buf[k] = 0;
-    __syncwarp();
+    for (uint32_t k0 = 0; k0 < full; k0 += 32) {  // warp-uniform trip count
+      const uint32_t k = k0 + lane;
+      if (k < full) {
+        if (SZ3G_IN(wpos + k < words, st)) pay[wpos + k] = buf[k];
+        buf[k] = 0;
+      }
+    }
+    wpos += full;
     carry = total & 31;
-    if (lane == 0) buf[0] = carry ? rest : 0u;
+    __syncwarp();
+    if (lane == 0) {
+      buf[full] = 0;
+      buf[0] = carry ? rest : 0u;
+    }
     __syncwarp();
     // unpredictable values of the round, in code order
     if (nu) {
@@ -1505,11 +1513,13 @@ __device__ __forceinline__ void chunk_counts(const uint16_t* __restrict__ codes,
   auto piece = [&](const uint4& v) {
     const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t c0 = wv[q] & 0xffffu, c1 = wv[q] >> 16;
-      bits += (__ldg(table + c0) >> 24) + (__ldg(table + c1) >> 24);
-      zc += (c0 == 0) + (c1 == 0);
-    }
+    for (int q = 0; q < 4; ++q) bits += (__ldg(table + (wv[q] & 0xffffu)) >> 24) + (__ldg(table + (wv[q] >> 16)) >> 24);
+    // zero codes (unpredictable values) are rare: a 16-bit minimum over the
+    // eight codes finds the pieces that hold one
+    const uint32_t mn = __vminu2(__vminu2(v.x, v.y), __vminu2(v.z, v.w));
+    if ((mn & 0xffffu) == 0 || (mn >> 16) == 0)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) zc += ((wv[q] & 0xffffu) == 0) + ((wv[q] >> 16) == 0);
   };
   uint32_t t = lane * 8;
   for (; t + 3 * 256 + 8 <= cnt; t += 4 * 256) {  // four whole pieces
