@@ -60,10 +60,14 @@ constexpr bool kPackCodes = true;
 // also to the global histogram (true); or window-or-global by a branch (false).
 constexpr bool kHistSpare = true;
 
-template <bool COMP>
+// Recover runs levels of many tiles with 128 threads per CTA (more CTAs per
+// SM cover the staging waits) and levels of at most kWideTiles tiles per SM,
+// where a tile's own latency is the time, with 256 (WIDE).
+template <bool COMP, bool WIDE = false>
 struct FineThreads {
-  static constexpr int kN = COMP ? 256 : 128, kMinBlocks = COMP ? 4 : 8, kStages = 1;
+  static constexpr int kN = (COMP || WIDE) ? 256 : 128, kMinBlocks = (COMP || WIDE) ? 4 : 8, kStages = 1;
 };
+constexpr int kWideTiles = 4;
 
 template <int T0>
 struct FineShape {
@@ -291,14 +295,14 @@ __device__ __forceinline__ void code_row(long long c0, long long* a16, int* o) {
   *o = (int)(c0 - al);
 }
 
-template <typename T, bool COMP, int INTERP, int T0>
-__global__ void __launch_bounds__(FineThreads<COMP>::kN, FineThreads<COMP>::kMinBlocks)
+template <typename T, bool COMP, int INTERP, int T0, bool WIDE>
+__global__ void __launch_bounds__(FineThreads<COMP, WIDE>::kN, FineThreads<COMP, WIDE>::kMinBlocks)
     fine_kernel(const FineDesc d, const LevelArgs<T> a, const __grid_constant__ CUtensorMap tmx,
                 const __grid_constant__ CUtensorMap tmc, const __grid_constant__ CUtensorMap tmk0,
                 const __grid_constant__ CUtensorMap tmk1, const __grid_constant__ CUtensorMap tmk2) {
   using S = FineShape<T0>;
   using L = FineLayout<T, COMP, T0>;
-  constexpr int kFineThreads = FineThreads<COMP>::kN;
+  constexpr int kFineThreads = FineThreads<COMP, WIDE>::kN;
   constexpr int XB = L::kXB, CB = L::kCB, KB = L::kKB;  // elements per buffer
   extern __shared__ __align__(128) unsigned char sm[];
   T* Xs = reinterpret_cast<T*>(sm + L::kOffX);              // [2][XB] (compress)
@@ -887,19 +891,27 @@ static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_f
   }
   if (!ok) return SZ3G_E_CUDA;
   const size_t smem = FineLayout<T, COMP, T0>::kBytes;
-  auto kern = interp == SZ3G_CUBIC ? fine_kernel<T, COMP, SZ3G_CUBIC, T0> : fine_kernel<T, COMP, SZ3G_LINEAR, T0>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return SZ3G_E_CUDA;
   int dev = 0, nsm = 152, per = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, FineThreads<COMP>::kN, smem);
+  const bool wide = !COMP && d.ntiles - d.tile0 <= (uint32_t)(kWideTiles * nsm);
+  decltype(&fine_kernel<T, COMP, SZ3G_CUBIC, T0, false>) kern;
+  if constexpr (COMP)
+    kern = interp == SZ3G_CUBIC ? fine_kernel<T, COMP, SZ3G_CUBIC, T0, false> : fine_kernel<T, COMP, SZ3G_LINEAR, T0, false>;
+  else if (wide)
+    kern = interp == SZ3G_CUBIC ? fine_kernel<T, COMP, SZ3G_CUBIC, T0, true> : fine_kernel<T, COMP, SZ3G_LINEAR, T0, true>;
+  else
+    kern = interp == SZ3G_CUBIC ? fine_kernel<T, COMP, SZ3G_CUBIC, T0, false> : fine_kernel<T, COMP, SZ3G_LINEAR, T0, false>;
+  const int nthr = wide ? FineThreads<COMP, true>::kN : FineThreads<COMP, false>::kN;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return SZ3G_E_CUDA;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, nthr, smem);
   if (per < 1) per = 1;
   unsigned long long grid = (unsigned long long)nsm * per;
   if (g_level_cta_cap > 0 && grid > (unsigned long long)g_level_cta_cap) grid = (unsigned long long)g_level_cta_cap;
   if (grid > d.ntiles - d.tile0) grid = d.ntiles - d.tile0;
   SZ3G_LAUNCH(COMP ? kKLevelQuantize : kKLevelRecover, s,
-              kern<<<(unsigned)grid, FineThreads<COMP>::kN, smem, s>>>(d, a, tmx, tmc, tmk[0], tmk[1], tmk[2]));
+              kern<<<(unsigned)grid, nthr, smem, s>>>(d, a, tmx, tmc, tmk[0], tmk[1], tmk[2]));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
