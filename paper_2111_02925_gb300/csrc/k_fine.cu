@@ -121,6 +121,8 @@ struct FineDesc {
   int write_out;
   uint32_t tensor_bytes;       // bytes of the x and coarse boxes of one tile
   int code_tma;                // recover: code rows by one tensor copy per pass
+  int code_al;                 // bit p: pass p's code pairs (p < 2) or runs of four (p = 2) are
+                               // 4- or 8-byte aligned, in global and in the staged rows
 };
 
 // ---- vector helpers -----------------------------------------------------------
@@ -578,13 +580,26 @@ __global__ void __launch_bounds__(FineThreads<COMP, WIDE>::kN, FineThreads<COMP,
             const bool own2[2] = {ownj && ke >= 2 && ke < 2 + S::kW / 2, ownj && ke + 1 >= 2 && ke + 1 < 2 + S::kW / 2};
             const T x2[2] = {xv[0], xv[2]};
             uint32_t k2[2] = {0u, 0u}, q2[2];
-            if (!COMP) k2[0] = kr[0], k2[1] = kr[1];
+            if (!COMP) {
+              if (d.code_al & 1) {
+                const uint32_t v = *reinterpret_cast<const uint32_t*>(kr);
+                k2[0] = v & 0xffffu, k2[1] = v >> 16;
+              } else {
+                k2[0] = kr[0], k2[1] = kr[1];
+              }
+            }
             fine_points<T, COMP, 2>(a, d, hwin, hlo, x2, p2, ebT, ebr, own2, (uint32_t)(c0 + ke), k2, acc, r, q2);
             if (COMP) {
-              if (own2[0] && SZ3G_IN((unsigned long long)(long long)(c0 + ke) < a.n_codes, st))
-                a.codes[c0 + ke] = (uint16_t)q2[0];
-              if (own2[1] && SZ3G_IN((unsigned long long)(long long)(c0 + ke + 1) < a.n_codes, st))
-                a.codes[c0 + ke + 1] = (uint16_t)q2[1];
+              // (ke is even: both points of the pair are owned or neither)
+              if ((d.code_al & 1) && own2[0]) {
+                if (SZ3G_IN((unsigned long long)(long long)(c0 + ke) + 2 <= a.n_codes, st))
+                  *reinterpret_cast<uint32_t*>(a.codes + c0 + ke) = q2[0] | (q2[1] << 16);
+              } else {
+                if (own2[0] && SZ3G_IN((unsigned long long)(long long)(c0 + ke) < a.n_codes, st))
+                  a.codes[c0 + ke] = (uint16_t)q2[0];
+                if (own2[1] && SZ3G_IN((unsigned long long)(long long)(c0 + ke + 1) < a.n_codes, st))
+                  a.codes[c0 + ke + 1] = (uint16_t)q2[1];
+              }
             }
           } else {
 #pragma unroll
@@ -636,13 +651,25 @@ __global__ void __launch_bounds__(FineThreads<COMP, WIDE>::kN, FineThreads<COMP,
           const bool own2[2] = {ke >= 2 && ke < 2 + S::kW / 2, ke + 1 >= 2 && ke + 1 < 2 + S::kW / 2};
           const T x2[2] = {xv[0], xv[2]};
           uint32_t k2[2] = {0u, 0u}, q2[2];
-          if (!COMP) k2[0] = kr[0], k2[1] = kr[1];
+          if (!COMP) {
+            if (d.code_al & 2) {
+              const uint32_t v = *reinterpret_cast<const uint32_t*>(kr);
+              k2[0] = v & 0xffffu, k2[1] = v >> 16;
+            } else {
+              k2[0] = kr[0], k2[1] = kr[1];
+            }
+          }
           fine_points<T, COMP, 2>(a, d, hwin, hlo, x2, p2, ebT, ebr, own2, (uint32_t)(c0 + ke), k2, acc, r, q2);
           if (COMP) {
-            if (own2[0] && SZ3G_IN((unsigned long long)(long long)(c0 + ke) < a.n_codes, st))
-              a.codes[c0 + ke] = (uint16_t)q2[0];
-            if (own2[1] && SZ3G_IN((unsigned long long)(long long)(c0 + ke + 1) < a.n_codes, st))
-              a.codes[c0 + ke + 1] = (uint16_t)q2[1];
+            if ((d.code_al & 2) && own2[0]) {
+              if (SZ3G_IN((unsigned long long)(long long)(c0 + ke) + 2 <= a.n_codes, st))
+                *reinterpret_cast<uint32_t*>(a.codes + c0 + ke) = q2[0] | (q2[1] << 16);
+            } else {
+              if (own2[0] && SZ3G_IN((unsigned long long)(long long)(c0 + ke) < a.n_codes, st))
+                a.codes[c0 + ke] = (uint16_t)q2[0];
+              if (own2[1] && SZ3G_IN((unsigned long long)(long long)(c0 + ke + 1) < a.n_codes, st))
+                a.codes[c0 + ke + 1] = (uint16_t)q2[1];
+            }
           }
         } else {
 #pragma unroll
@@ -701,7 +728,12 @@ __global__ void __launch_bounds__(FineThreads<COMP, WIDE>::kN, FineThreads<COMP,
           uint32_t kin[4] = {0u, 0u, 0u, 0u}, cq[4] = {0u, 0u, 0u, 0u};
           if (!COMP) {
             if (kPackCodes) {
-              get_codes4(kr, kin);
+              if (d.code_al & 4) {
+                const uint2 v = *reinterpret_cast<const uint2*>(kr);
+                kin[0] = v.x & 0xffffu, kin[1] = v.x >> 16, kin[2] = v.y & 0xffffu, kin[3] = v.y >> 16;
+              } else {
+                get_codes4(kr, kin);
+              }
             } else {
 #pragma unroll
               for (int u = 0; u < 4; ++u) kin[u] = kr[u];
@@ -713,7 +745,12 @@ __global__ void __launch_bounds__(FineThreads<COMP, WIDE>::kN, FineThreads<COMP,
             p4[u] = interp_predict<T>(e[u + 2], e[u + 3], e[u + 1], e[u + 4], true, true, true, INTERP);
           const bool own4[4] = {true, true, true, true};
           fine_points<T, COMP, 4>(a, d, hwin, hlo, xo, p4, ebT, ebr, own4, ci, kin, acc, r, cq);
-          if (COMP && SZ3G_IN((unsigned long long)ci + 4 <= a.n_codes, st)) put_codes4(a.codes + ci, cq);
+          if (COMP && SZ3G_IN((unsigned long long)ci + 4 <= a.n_codes, st)) {
+            if (d.code_al & 4)
+              *reinterpret_cast<uint2*>(a.codes + ci) = make_uint2(cq[0] | (cq[1] << 16), cq[2] | (cq[3] << 16));
+            else
+              put_codes4(a.codes + ci, cq);
+          }
         } else {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -870,6 +907,14 @@ static int launch_fine_t(const Plan& pl, int k, const LevelArgs<T>& a, bool to_f
   if (COMP) {
     ok = ok && fine_map<T>(&tmx, a.x, d.m0, d.m1, d.m2, a.xs[0], a.xs[1], S::kT0, S::kXJ, S::kXK);
     d.tensor_bytes += (uint32_t)(S::kT0 * S::kXJ * S::kXK * sizeof(T));
+  }
+  // pairs of codes (passes 0, 1: the pair starts at an even lattice index)
+  // and runs of four (pass 2: at a multiple of four) start on 4- and 8-byte
+  // boundaries when the pass's first code and row length allow it
+  if ((uintptr_t)a.codes % 8 == 0) {
+    for (int q = S::kHas0 ? 0 : 1; q < 2; ++q)
+      if (d.off[q] % 2 == 0 && d.E2[q] % 2 == 0) d.code_al |= 1 << q;
+    if (d.off[2] % 4 == 0 && d.E2[2] % 4 == 0) d.code_al |= 4;
   }
   CUtensorMap tmk[3];
   memset(tmk, 0, sizeof(tmk));
