@@ -2056,10 +2056,7 @@ __global__ void __launch_bounds__(kDecThreads, 4) decode_kernel(const DecArgs a)
   __shared__ unsigned long long s_tk, s_ex, s_warp[32], s_cwx[kDecThreads];
   const int tid = threadIdx.x;
   unsigned long long* stat_w = reinterpret_cast<unsigned long long*>(a.lb + 256);
-  if (tid == 0) {
-    s_skip = (a.st->flags & kFlagCorrupt) != 0;  // tables rejected
-    s_tk = atomicAdd(reinterpret_cast<unsigned int*>(a.lb), 1u);  // CTAs take their units in ticket order
-  }
+  if (tid == 0) s_skip = (a.st->flags & kFlagCorrupt) != 0;  // tables rejected
   uint32_t* lut = reinterpret_cast<uint32_t*>(dsm);
   // the 12-bit table from the 13-bit one (len << 16 | sym): codewords of 13
   // bits become "longer"; entries as sym << 16 | len
@@ -2072,177 +2069,185 @@ __global__ void __launch_bounds__(kDecThreads, 4) decode_kernel(const DecArgs a)
     s_lim[tid] = a.T->lim[tid];
     s_base[tid] = a.T->base[tid];
   }
-  __syncthreads();
-  const unsigned long long c = s_tk, units = a.n_chunks * a.upc;
-  // 1. Word offsets.  The chunks whose first unit falls in this CTA are its
-  //    own (one per thread at most); their exclusive prefix inside the CTA,
-  //    plus the words of every chunk before them (a decoupled look-back over
-  //    the CTAs before it in ticket order), gives each chunk's first word.
-  //    The chunk this CTA shares with the one before starts that chunk's
-  //    words before the CTA's own.  The last CTA checks the total.
-  const unsigned long long jo0 = (c * kDecThreads + a.upc - 1) / a.upc;
-  const unsigned long long jo1 = min(((c + 1) * kDecThreads + a.upc - 1) / a.upc, a.n_chunks);
-  bool bad = false;
-  uint32_t cwo = 0;
-  if (jo0 + tid < jo1) {
-    cwo = a.chunk_words[jo0 + tid];
-    bad = cwo > a.maxw;
-  }
-  unsigned long long agg;
-  s_cwx[tid] = block_exclusive_scan(cwo, s_warp, &agg);
-  if (tid < 32) {
-    const unsigned long long ex = cta_prefix(stat_w, c, agg, a.st, a.spin_limit);
-    if (tid == 0) {
-      s_ex = ex;
-      if (c + 1 == a.n_ctas && ex + agg != a.n_words) atomicOr(&a.st->flags, kFlagCorrupt);
+  // The CTA (one of about as many as fit on the GPU at once) takes groups of
+  // kDecThreads units in ticket order until none are left: no second, partly
+  // filled round of CTAs.
+  for (;;) {
+    __syncthreads();  // the previous group's shared state is no longer read
+    if (tid == 0) s_tk = atomicAdd(reinterpret_cast<unsigned int*>(a.lb), 1u);
+    __syncthreads();
+    const unsigned long long c = s_tk, units = a.n_chunks * a.upc;
+    if (c >= a.n_ctas) break;
+    // 1. Word offsets.  The chunks whose first unit falls in this CTA are its
+    //    own (one per thread at most); their exclusive prefix inside the CTA,
+    //    plus the words of every chunk before them (a decoupled look-back over
+    //    the CTAs before it in ticket order), gives each chunk's first word.
+    //    The chunk this CTA shares with the one before starts that chunk's
+    //    words before the CTA's own.  The last CTA checks the total.
+    const unsigned long long jo0 = (c * kDecThreads + a.upc - 1) / a.upc;
+    const unsigned long long jo1 = min(((c + 1) * kDecThreads + a.upc - 1) / a.upc, a.n_chunks);
+    bool bad = false;
+    uint32_t cwo = 0;
+    if (jo0 + tid < jo1) {
+      cwo = a.chunk_words[jo0 + tid];
+      bad = cwo > a.maxw;
     }
-  }
-  __syncthreads();
-  const unsigned long long ew = s_ex;
-  // 2. The unit.  Returns true when it is corrupt.
-  const unsigned long long u = c * kDecThreads + tid;
-  auto decode_unit = [&]() -> bool {
-    const uint32_t n_used = a.T->n_used;
-    const bool count_zeros = a.T->has_zero != 0;
-    uint32_t* ring = reinterpret_cast<uint32_t*>(dsm + kDecOffRing) + tid;  // word slot q at ring[q * kDecThreads]
-    uint4* stg = reinterpret_cast<uint4*>(dsm + kDecOffStage) + tid;        // block slot s at stg[s * kDecThreads]
-    const unsigned long long j = u / a.upc;
-    const uint32_t b = (uint32_t)(u - j * a.upc);
-    const uint32_t n_chunk = (uint32_t)min((unsigned long long)a.chunk, a.n - j * a.chunk);
-    const uint32_t c0 = b * a.unit;
-    const uint32_t nw = a.chunk_words[j];
-    const uint16_t* sb = a.sub_bits ? a.sub_bits + j * (a.nsb - 1) : nullptr;
-    uint32_t* zc = a.zcnt + j * a.nsb;
-    auto zset = [&](uint32_t q, uint32_t v) {  // zero codes of the chunk's sub-block q
-      if (SZ3G_IN(j * a.nsb + q < a.n_chunks * a.nsb, a.st)) zc[q] = v;
-    };
-    unsigned long long bit0 = 0;  // start bit of the unit inside the chunk
-    if (sb)
-      for (uint32_t q = 0; q < b; ++q) bit0 += sb[q];
-    if (c0 >= n_chunk) {  // past the end of a short last chunk
-      if (a.unit == SZ3G_SUBBLOCK) zset(b, 0u);
-      return sb && b + 1 < a.nsb && sb[b] != 0;
+    unsigned long long agg;
+    s_cwx[tid] = block_exclusive_scan(cwo, s_warp, &agg);
+    if (tid < 32) {
+      const unsigned long long ex = cta_prefix(stat_w, c, agg, a.st, a.spin_limit);
+      if (tid == 0) {
+        s_ex = ex;
+        if (c + 1 == a.n_ctas && ex + agg != a.n_words) atomicOr(&a.st->flags, kFlagCorrupt);
+      }
     }
-    const uint32_t c1 = min(c0 + a.unit, n_chunk);
-    // a chunk with codes has at least one word, the unit's start bit inside
-    // it, and all of its words inside the payload
-    if (nw == 0 || bit0 >= 32ull * nw) return true;
-    unsigned long long wj;  // the chunk's first word
-    if (j >= jo0) {
-      wj = ew + s_cwx[j - jo0];
-    } else {
-      if (ew < nw) return true;
-      wj = ew - nw;
-    }
-    if (wj > a.n_words || nw > a.n_words - wj) return true;
-    // The unit's words as a sequence of 16-byte blocks starting at the aligned
-    // block that holds its first word; blocks past the payload's last one read
-    // that block again (a correct code never depends on bits after its own,
-    // and a decode that runs past its bits is caught by the bit count at the
-    // end).
-    const uintptr_t a0 = reinterpret_cast<uintptr_t>(a.words + wj + (bit0 >> 5));
-    const uint4* blk = reinterpret_cast<const uint4*>(a0 & ~(uintptr_t)15);
-    const uintptr_t a_last = reinterpret_cast<uintptr_t>(a.words + a.n_words - 1) & ~(uintptr_t)15;
-    const uint32_t q_last = a_last >= (a0 & ~(uintptr_t)15) ? (uint32_t)((a_last - (a0 & ~(uintptr_t)15)) >> 4) : 0u;
-    constexpr uint32_t RM = kDecRingW - 1, SM_ = kDecStage - 1;
-    auto stage = [&](uint32_t q) { dec_stage(stg + (q & SM_) * kDecThreads, blk + min(q, q_last)); };
-    auto put = [&](uint32_t at, const uint4& v) {  // words at .. at + 3 of the sequence
-      ring[((at + 0) & RM) * kDecThreads] = v.x;
-      ring[((at + 1) & RM) * kDecThreads] = v.y;
-      ring[((at + 2) & RM) * kDecThreads] = v.z;
-      ring[((at + 3) & RM) * kDecThreads] = v.w;
-    };
-    stage(0);
-    stage(1);
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    put(0, stg[0]);
-    put(4, stg[1 * kDecThreads]);
-    stage(2);
-    stage(3);
-    uint32_t stored = 8, next_use = 2;  // words in the ring; next staged block to take
-    const uint32_t start_bit = (uint32_t)((a0 & 15) * 8) + (uint32_t)(bit0 & 31);
-    // window: words wk - 2 (wa) and wk - 1 (wb); read position bp in wa
-    uint32_t wk = (start_bit >> 5) + 2;
-    uint32_t wa = ring[((wk - 2) & RM) * kDecThreads];
-    uint32_t wb = ring[((wk - 1) & RM) * kDecThreads];
-    uint32_t bp = start_bit & 31;
-    uint32_t zeros = 0;
-    bool fail = false;
-    uint16_t* out = a.codes + j * a.chunk + c0;
-    // one codeword: its entry (symbol << 16 | length), or false for a window
-    // that starts no codeword
-    auto one = [&](uint32_t& e) -> bool {
-      const uint32_t win = __funnelshift_l(wb, wa, bp);
-      e = lut[win >> (32 - kDecLB)];
-      if ((e & 31u) == 0) {  // a codeword longer than the table
-        e = dec_long(win, s_lim, s_base, n_used, a.T->sorted);
-        if (e == 0) return false;
+    __syncthreads();
+    const unsigned long long ew = s_ex;
+    // 2. The unit.  Returns true when it is corrupt.
+    const unsigned long long u = c * kDecThreads + tid;
+    auto decode_unit = [&]() -> bool {
+      const uint32_t n_used = a.T->n_used;
+      const bool count_zeros = a.T->has_zero != 0;
+      uint32_t* ring = reinterpret_cast<uint32_t*>(dsm + kDecOffRing) + tid;  // word slot q at ring[q * kDecThreads]
+      uint4* stg = reinterpret_cast<uint4*>(dsm + kDecOffStage) + tid;        // block slot s at stg[s * kDecThreads]
+      const unsigned long long j = u / a.upc;
+      const uint32_t b = (uint32_t)(u - j * a.upc);
+      const uint32_t n_chunk = (uint32_t)min((unsigned long long)a.chunk, a.n - j * a.chunk);
+      const uint32_t c0 = b * a.unit;
+      const uint32_t nw = a.chunk_words[j];
+      const uint16_t* sb = a.sub_bits ? a.sub_bits + j * (a.nsb - 1) : nullptr;
+      uint32_t* zc = a.zcnt + j * a.nsb;
+      auto zset = [&](uint32_t q, uint32_t v) {  // zero codes of the chunk's sub-block q
+        if (SZ3G_IN(j * a.nsb + q < a.n_chunks * a.nsb, a.st)) zc[q] = v;
+      };
+      unsigned long long bit0 = 0;  // start bit of the unit inside the chunk
+      if (sb)
+        for (uint32_t q = 0; q < b; ++q) bit0 += sb[q];
+      if (c0 >= n_chunk) {  // past the end of a short last chunk
+        if (a.unit == SZ3G_SUBBLOCK) zset(b, 0u);
+        return sb && b + 1 < a.nsb && sb[b] != 0;
       }
-      bp += e & 31u;
-      const bool adv = bp >= 32;
-      const uint32_t wn = ring[(wk & RM) * kDecThreads];
-      wa = adv ? wb : wa;
-      wb = adv ? wn : wb;
-      wk += adv ? 1u : 0u;
-      bp -= adv ? 32u : 0u;
-      return true;
-    };
-    for (uint32_t i = c0; i < c1; i += 8, out += 8) {  // c0 is a multiple of 8
-      if (i != c0 && (i & (SZ3G_SUBBLOCK - 1)) == 0) {  // whole-chunk units count per sub-block
-        zset((i >> 9) - 1, zeros);
-        zeros = 0;
-      }
-      // eight codes advance the window by at most 6 words
-      while (stored < wk + 6) {
-        asm volatile("cp.async.wait_group %0;" ::"n"(kDecStage - 1) : "memory");
-        put(stored, stg[(next_use & SM_) * kDecThreads]);
-        stored += 4;
-        stage(next_use + kDecStage);  // into the slot just read
-        ++next_use;
-      }
-      const uint32_t m = min(8u, c1 - i);
-      if (m == 8) {
-        uint32_t pk[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          uint32_t e0 = 0, e1 = 0;
-          if (!one(e0) || !one(e1)) {
-            fail = true;
-            break;
-          }
-          pk[q] = __byte_perm(e0, e1, 0x7632);  // symbol of e0 low, of e1 high
-        }
-        if (fail) break;
-        if (count_zeros) zeros += zero_halves(pk[0]) + zero_halves(pk[1]) + zero_halves(pk[2]) + zero_halves(pk[3]);
-        if (SZ3G_IN(j * a.chunk + i + 8 <= a.n, a.st))
-          *reinterpret_cast<uint4*>(out) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      const uint32_t c1 = min(c0 + a.unit, n_chunk);
+      // a chunk with codes has at least one word, the unit's start bit inside
+      // it, and all of its words inside the payload
+      if (nw == 0 || bit0 >= 32ull * nw) return true;
+      unsigned long long wj;  // the chunk's first word
+      if (j >= jo0) {
+        wj = ew + s_cwx[j - jo0];
       } else {
-        for (uint32_t q = 0; q < m; ++q) {
-          uint32_t e;
-          if (!one(e)) {
-            fail = true;
-            break;
-          }
-          if (SZ3G_IN(j * a.chunk + i + q < a.n, a.st)) out[q] = (uint16_t)(e >> 16);
-          if (count_zeros) zeros += (e >> 16) == 0;
-        }
-        if (fail) break;
+        if (ew < nw) return true;
+        wj = ew - nw;
       }
-    }
-    // no copy may land in shared memory after the thread has left
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    if (fail) return true;
-    zset((c1 - 1) >> 9, zeros);
-    if (a.unit != SZ3G_SUBBLOCK)  // sub-blocks past the end of a short chunk
-      for (uint32_t q = ((c1 - 1) >> 9) + 1; q < a.nsb; ++q) zset(q, 0u);
-    // bits consumed from the chunk start; the recorded sub-block boundary
-    // must be exactly where decoding ended
-    const unsigned long long used = bit0 + (unsigned long long)((wk - 2) * 32u + bp - start_bit);
-    if (sb && a.unit == SZ3G_SUBBLOCK && b + 1 < a.nsb && used != bit0 + sb[b]) return true;
-    return used > 32ull * nw;
-  };
-  if (!s_skip && u < units && decode_unit()) bad = true;
-  if (bad) atomicOr(&a.st->flags, kFlagCorrupt);
+      if (wj > a.n_words || nw > a.n_words - wj) return true;
+      // The unit's words as a sequence of 16-byte blocks starting at the aligned
+      // block that holds its first word; blocks past the payload's last one read
+      // that block again (a correct code never depends on bits after its own,
+      // and a decode that runs past its bits is caught by the bit count at the
+      // end).
+      const uintptr_t a0 = reinterpret_cast<uintptr_t>(a.words + wj + (bit0 >> 5));
+      const uint4* blk = reinterpret_cast<const uint4*>(a0 & ~(uintptr_t)15);
+      const uintptr_t a_last = reinterpret_cast<uintptr_t>(a.words + a.n_words - 1) & ~(uintptr_t)15;
+      const uint32_t q_last = a_last >= (a0 & ~(uintptr_t)15) ? (uint32_t)((a_last - (a0 & ~(uintptr_t)15)) >> 4) : 0u;
+      constexpr uint32_t RM = kDecRingW - 1, SM_ = kDecStage - 1;
+      auto stage = [&](uint32_t q) { dec_stage(stg + (q & SM_) * kDecThreads, blk + min(q, q_last)); };
+      auto put = [&](uint32_t at, const uint4& v) {  // words at .. at + 3 of the sequence
+        ring[((at + 0) & RM) * kDecThreads] = v.x;
+        ring[((at + 1) & RM) * kDecThreads] = v.y;
+        ring[((at + 2) & RM) * kDecThreads] = v.z;
+        ring[((at + 3) & RM) * kDecThreads] = v.w;
+      };
+      stage(0);
+      stage(1);
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      put(0, stg[0]);
+      put(4, stg[1 * kDecThreads]);
+      stage(2);
+      stage(3);
+      uint32_t stored = 8, next_use = 2;  // words in the ring; next staged block to take
+      const uint32_t start_bit = (uint32_t)((a0 & 15) * 8) + (uint32_t)(bit0 & 31);
+      // window: words wk - 2 (wa) and wk - 1 (wb); read position bp in wa
+      uint32_t wk = (start_bit >> 5) + 2;
+      uint32_t wa = ring[((wk - 2) & RM) * kDecThreads];
+      uint32_t wb = ring[((wk - 1) & RM) * kDecThreads];
+      uint32_t bp = start_bit & 31;
+      uint32_t zeros = 0;
+      bool fail = false;
+      uint16_t* out = a.codes + j * a.chunk + c0;
+      // one codeword: its entry (symbol << 16 | length), or false for a window
+      // that starts no codeword
+      auto one = [&](uint32_t& e) -> bool {
+        const uint32_t win = __funnelshift_l(wb, wa, bp);
+        e = lut[win >> (32 - kDecLB)];
+        if ((e & 31u) == 0) {  // a codeword longer than the table
+          e = dec_long(win, s_lim, s_base, n_used, a.T->sorted);
+          if (e == 0) return false;
+        }
+        bp += e & 31u;
+        const bool adv = bp >= 32;
+        const uint32_t wn = ring[(wk & RM) * kDecThreads];
+        wa = adv ? wb : wa;
+        wb = adv ? wn : wb;
+        wk += adv ? 1u : 0u;
+        bp -= adv ? 32u : 0u;
+        return true;
+      };
+      for (uint32_t i = c0; i < c1; i += 8, out += 8) {  // c0 is a multiple of 8
+        if (i != c0 && (i & (SZ3G_SUBBLOCK - 1)) == 0) {  // whole-chunk units count per sub-block
+          zset((i >> 9) - 1, zeros);
+          zeros = 0;
+        }
+        // eight codes advance the window by at most 6 words
+        while (stored < wk + 6) {
+          asm volatile("cp.async.wait_group %0;" ::"n"(kDecStage - 1) : "memory");
+          put(stored, stg[(next_use & SM_) * kDecThreads]);
+          stored += 4;
+          stage(next_use + kDecStage);  // into the slot just read
+          ++next_use;
+        }
+        const uint32_t m = min(8u, c1 - i);
+        if (m == 8) {
+          uint32_t pk[4];
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            uint32_t e0 = 0, e1 = 0;
+            if (!one(e0) || !one(e1)) {
+              fail = true;
+              break;
+            }
+            pk[q] = __byte_perm(e0, e1, 0x7632);  // symbol of e0 low, of e1 high
+          }
+          if (fail) break;
+          if (count_zeros) zeros += zero_halves(pk[0]) + zero_halves(pk[1]) + zero_halves(pk[2]) + zero_halves(pk[3]);
+          if (SZ3G_IN(j * a.chunk + i + 8 <= a.n, a.st))
+            *reinterpret_cast<uint4*>(out) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        } else {
+          for (uint32_t q = 0; q < m; ++q) {
+            uint32_t e;
+            if (!one(e)) {
+              fail = true;
+              break;
+            }
+            if (SZ3G_IN(j * a.chunk + i + q < a.n, a.st)) out[q] = (uint16_t)(e >> 16);
+            if (count_zeros) zeros += (e >> 16) == 0;
+          }
+          if (fail) break;
+        }
+      }
+      // no copy may land in shared memory after the thread has left
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      if (fail) return true;
+      zset((c1 - 1) >> 9, zeros);
+      if (a.unit != SZ3G_SUBBLOCK)  // sub-blocks past the end of a short chunk
+        for (uint32_t q = ((c1 - 1) >> 9) + 1; q < a.nsb; ++q) zset(q, 0u);
+      // bits consumed from the chunk start; the recorded sub-block boundary
+      // must be exactly where decoding ended
+      const unsigned long long used = bit0 + (unsigned long long)((wk - 2) * 32u + bp - start_bit);
+      if (sb && a.unit == SZ3G_SUBBLOCK && b + 1 < a.nsb && used != bit0 + sb[b]) return true;
+      return used > 32ull * nw;
+    };
+    if (!s_skip && u < units && decode_unit()) bad = true;
+    if (bad) atomicOr(&a.st->flags, kFlagCorrupt);
+  }
 }
 
 size_t dec_tables_bytes() { return sizeof(DecTables); }
@@ -2292,11 +2297,16 @@ int launch_decode_chunks(const uint32_t* words, unsigned long long n_words, cons
   a.lb = (unsigned char*)state;
   a.st = st;
   const unsigned long long threads = n_chunks * a.upc;
-  a.n_ctas = threads ? (threads + kDecThreads - 1) / kDecThreads : 1;
+  a.n_ctas = threads ? (threads + kDecThreads - 1) / kDecThreads : 1;  // groups of kDecThreads units
   if (cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecodeSmem) !=
       cudaSuccess)
     return SZ3G_E_CUDA;
-  SZ3G_LAUNCH(kKDecode, s, decode_kernel<<<(unsigned)a.n_ctas, kDecThreads, kDecodeSmem, s>>>(a));
+  int dev = 0, nsm = 152, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, decode_kernel, kDecThreads, kDecodeSmem);
+  const unsigned long long grid = min(a.n_ctas, (unsigned long long)nsm * (unsigned long long)(per > 0 ? per : 1));
+  SZ3G_LAUNCH(kKDecode, s, decode_kernel<<<(unsigned)grid, kDecThreads, kDecodeSmem, s>>>(a));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
 
