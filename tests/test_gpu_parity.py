@@ -72,6 +72,10 @@ CASES = [
     ("latlon_cubic", lambda: S.latlon(181, 363, 5), O.F64, O.ABS, 1e-5, O.CUBIC, (1, 0), 32768, 4096),
     ("grf1d", lambda: S.grf((5000,), 6), O.F32, O.REL, 1e-3, O.CUBIC, (0,), 32768, 1024),
     ("grf4d", lambda: S.grf((7, 9, 6, 10), 7), O.F32, O.REL, 1e-3, O.LINEAR, (3, 1, 0, 2), 32768, 256),
+    # 3-D FP64 on the register-blocked level kernel: G_0 stages its code rows
+    # by tensor copies (rows of 40 odd-k codes), G_1 by per-row copies (20)
+    ("grf3d_f64_cubic", lambda: S.grf((40, 48, 80), 12).astype(np.float64), O.F64, O.REL, 1e-4, O.CUBIC,
+     (0, 1, 2), 32768, 4096),
     ("grf4d_f64", lambda: S.grf((5, 8, 9, 6), 8).astype(np.float64), O.F64, O.REL, 1e-4, O.CUBIC, (0, 1, 2, 3), 512,
      64),
     ("tiny_1", lambda: np.array([3.5], np.float32), O.F32, O.ABS, 0.1, O.LINEAR, (0,), 32768, 4096),
