@@ -76,6 +76,10 @@ CASES = [
     # by tensor copies (rows of 40 odd-k codes), G_1 by per-row copies (20)
     ("grf3d_f64_cubic", lambda: S.grf((40, 48, 80), 12).astype(np.float64), O.F64, O.REL, 1e-4, O.CUBIC,
      (0, 1, 2), 32768, 4096),
+    # 2-D FP32: code rows by per-row copies (rows of 100 odd-k codes) and,
+    # on the power-of-two grid, by tensor copies
+    ("grf2d_f32_cubic", lambda: S.grf((136, 200), 13), O.F32, O.REL, 1e-3, O.CUBIC, (0, 1), 32768, 4096),
+    ("grf2d_f32_pow2_lin", lambda: S.grf((128, 256), 14), O.F32, O.REL, 1e-3, O.LINEAR, (0, 1), 32768, 4096),
     ("grf4d_f64", lambda: S.grf((5, 8, 9, 6), 8).astype(np.float64), O.F64, O.REL, 1e-4, O.CUBIC, (0, 1, 2, 3), 512,
      64),
     ("tiny_1", lambda: np.array([3.5], np.float32), O.F32, O.ABS, 0.1, O.LINEAR, (0,), 32768, 4096),

@@ -39,6 +39,10 @@ CASES = [
     ("grf4d", lambda: S.grf((7, 9, 6, 10), 7), O.F32, O.REL, 1e-3, O.LINEAR, (3, 1, 0, 2), 32768, 256),
     ("grf3d_f64_cubic", lambda: S.grf((40, 48, 80), 12).astype(np.float64), O.F64, O.REL, 1e-4, O.CUBIC,
      (0, 1, 2), 32768, 4096),
+    # 2-D FP32: code rows by per-row copies (rows of 100 odd-k codes) and,
+    # on the power-of-two grid, by tensor copies
+    ("grf2d_f32_cubic", lambda: S.grf((136, 200), 13), O.F32, O.REL, 1e-3, O.CUBIC, (0, 1), 32768, 4096),
+    ("grf2d_f32_pow2_lin", lambda: S.grf((128, 256), 14), O.F32, O.REL, 1e-3, O.LINEAR, (0, 1), 32768, 4096),
     ("tiny_2x1x3", lambda: np.arange(6, dtype=np.float32).reshape(2, 1, 3), O.F32, O.ABS, 0.1, O.CUBIC,
      (0, 1, 2), 32768, 8),
     ("all_unpred", lambda: S.grf((12, 13, 14), 9), O.F32, O.REL, 1e-7, O.LINEAR, (0, 1, 2), 2, 8),
