@@ -751,10 +751,30 @@ __global__ void __launch_bounds__(kLevelThreads, 3) level_kernel(const LevelDesc
 constexpr int kCoarseThreads = 1024;
 constexpr int kCoarseMaxPasses = 96;
 
+// Division of a 32-bit n by an invariant d >= 1 by one multiply-high, after
+// Granlund and Montgomery ("Division by invariant integers using
+// multiplication", 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n) and
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) for every n < 2^32.
+struct DivU32 {
+  uint32_t m, s1, s2;
+};
+static DivU32 divu32(uint32_t d) {
+  uint32_t l = 0;
+  while (l < 32 && (1ull << l) < d) ++l;
+  const unsigned long long m = (((1ull << l) - d) << 32) / d + 1;
+  return DivU32{(uint32_t)m, l < 1 ? l : 1u, l > 1 ? l - 1 : 0u};
+}
+__device__ __forceinline__ uint32_t div_by(uint32_t n, const DivU32& v) {
+  const uint32_t t = __umulhi(v.m, n);
+  return (t + ((n - t) >> v.s1)) >> v.s2;
+}
+
 struct CoarsePass {
   unsigned long long off;
   uint32_t count;
   uint32_t E[3];
+  DivU32 dE2, dE1;      // division by E[2] and by E[1]
   uint32_t start[3], step[3];
   uint32_t m_ax;        // extent of the pass axis in G_grid
   int ax, interp, scale_log;  // scale_log = grid - kc
@@ -777,7 +797,8 @@ __host__ __device__ constexpr size_t coarse_off_codes(size_t npts, size_t esz) {
 }
 
 template <typename T, bool COMP>
-__global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc d, const LevelArgs<T> a) {
+__global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const __grid_constant__ CoarseDesc d,
+                                                                const LevelArgs<T> a) {
   extern __shared__ __align__(128) unsigned char sm[];
   T* R = reinterpret_cast<T*>(sm);
   const uint32_t npts = d.mk[0] * d.mk[1] * d.mk[2];
@@ -791,6 +812,16 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
   const int radius = a.radius;
   __shared__ unsigned int s_nz;
   __shared__ int s_bad;
+  // the pass descriptors, copied once (indexed reads of the parameter space
+  // would wait for the constant cache on every pass)
+  __shared__ CoarsePass s_pass[kCoarseMaxPasses];
+  static_assert(sizeof(CoarsePass) % 4 == 0, "pass descriptors copy as words");
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(d.pass);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_pass);
+    const int nw = d.n_pass * (int)(sizeof(CoarsePass) / 4);
+    for (int i = tid; i < nw; i += kCoarseThreads) dst[i] = src[i];
+  }
   // recover: the group's codes (the first npts codes of the traversal) in one
   // round of coalesced loads, so that no pass waits for global memory
   if (!COMP) {
@@ -829,11 +860,12 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
   }
   __syncthreads();
   for (int q = 0; q < d.n_pass; ++q) {
-    const CoarsePass& P = d.pass[q];
+    const CoarsePass& P = s_pass[q];
     const uint32_t sc = 1u << P.scale_log;
     const uint32_t vst = sc * d.gs[P.ax];
     for (uint32_t j = tid; j < P.count; j += kCoarseThreads) {
-      const uint32_t j2 = j % P.E[2], j1 = (j / P.E[2]) % P.E[1], j0 = j / (P.E[2] * P.E[1]);
+      const uint32_t q1 = div_by(j, P.dE2), j0 = div_by(q1, P.dE1);
+      const uint32_t j2 = j - q1 * P.E[2], j1 = q1 - j0 * P.E[1];
       const uint32_t g0 = P.start[0] + P.step[0] * j0, g1 = P.start[1] + P.step[1] * j1,
                      g2 = P.start[2] + P.step[2] * j2;
       const uint32_t v = sc * (g0 * d.gs[0] + g1 * d.gs[1] + g2 * d.gs[2]);
@@ -875,7 +907,11 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const CoarseDesc
                       (!hd || v + 3 * vst < npts), st))
         R[v] = r;
     }
-    __syncthreads();
+    // a pass of at most 32 points followed by another runs on warp 0 alone:
+    // a warp barrier suffices between them (the condition is the same for
+    // every thread)
+    if (P.count <= 32 && q + 1 < d.n_pass && s_pass[q + 1].count <= 32) __syncwarp();
+    else __syncthreads();
   }
   // write G_kc
   const uint32_t tot = a.Rout ? d.mk[0] * d.mk[1] * d.mk[2] : 0u;
@@ -1453,6 +1489,9 @@ static int run_coarse(const Plan& pl, int kc, const LevelArgs<T>& a, cudaStream_
       c.step[q] = pd.step[q + 1];
       c.xs[q] = pd.xstride[q + 1];
     }
+    if (c.E[1] == 0 || c.E[2] == 0) return SZ3G_E_INVAL;
+    c.dE2 = divu32(c.E[2]);
+    c.dE1 = divu32(c.E[1]);
     c.ax = pd.axis - 1;
     c.m_ax = pd.m[pd.axis];
     c.interp = pd.interp;
