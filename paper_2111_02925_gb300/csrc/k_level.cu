@@ -749,6 +749,7 @@ __global__ void __launch_bounds__(kLevelThreads, 3) level_kernel(const LevelDesc
 // Coarse group: every level whose grid is small, one CTA.
 // ---------------------------------------------------------------------------
 constexpr int kCoarseThreads = 1024;
+constexpr unsigned long long kCoarseMax = 4096;  // points of the largest coarse-group grid
 constexpr int kCoarseMaxPasses = 96;
 
 // Division of a 32-bit n by an invariant d >= 1 by one multiply-high, after
@@ -786,6 +787,7 @@ struct CoarseDesc {
   uint32_t mk[3];              // extents of G_kc
   uint32_t gs[3];              // strides of G_kc (compact)
   unsigned long long rs[3];    // strides of the output grid (R_kc or the field)
+  unsigned long long xk[3];    // compress: input strides of one G_kc step
   CoarsePass pass[kCoarseMaxPasses];
   uint32_t chunk, nsub;
 };
@@ -803,6 +805,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const __grid_con
   T* R = reinterpret_cast<T*>(sm);
   const uint32_t npts = d.mk[0] * d.mk[1] * d.mk[2];
   uint16_t* Kc = reinterpret_cast<uint16_t*>(sm + coarse_off_codes(npts, sizeof(T)));  // recover
+  T* Xs = reinterpret_cast<T*>(sm + coarse_off_codes(npts, sizeof(T)));  // compress: input at every point of G_kc
   const int tid = threadIdx.x;
   DevState* st = a.st;
   if (COMP && (st->flags & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound))) return;
@@ -827,6 +830,23 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const __grid_con
   if (!COMP) {
     for (uint32_t i = tid; i < npts; i += kCoarseThreads) Kc[i] = a.codes[i];
     __syncthreads();
+  } else {
+    // compress: the input at every point of G_kc (at most 4 per thread), all
+    // loads in flight at once, indexed like the reconstruction
+    static_assert(kCoarseMax <= 4 * kCoarseThreads, "four points per thread");
+    T xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t v = tid + u * kCoarseThreads;
+      if (v < npts) {
+        const uint32_t c2 = v % d.mk[2], c1 = (v / d.mk[2]) % d.mk[1], c0 = v / (d.mk[2] * d.mk[1]);
+        xv[u] = a.x[c0 * d.xk[0] + c1 * d.xk[1] + c2 * d.xk[2]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (tid + u * kCoarseThreads < npts) Xs[tid + u * kCoarseThreads] = xv[u];
+    __syncthreads();
   }
   if (tid == 0) {
     s_nz = 0;
@@ -834,7 +854,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const __grid_con
     // anchor: point 0, prediction 0
     T r;
     if (COMP) {
-      const T xv = a.x[0];
+      const T xv = Xs[0];
       const uint32_t code = quantize_point<T>(xv, T(0), ebT, ebr, radius, r);
       a.codes[0] = (uint16_t)code;
       atomicAdd(&a.hist[code], 1u);
@@ -879,8 +899,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const __grid_con
       const unsigned long long ci = P.off + j;
       T r;
       if (COMP) {
-        const T xv = a.x[(unsigned long long)g0 * P.xs[0] + (unsigned long long)g1 * P.xs[1] +
-                         (unsigned long long)g2 * P.xs[2]];
+        const T xv = Xs[v];
         const uint32_t code = quantize_point<T>(xv, pred, ebT, ebr, radius, r);
         if (SZ3G_IN(ci < a.n_codes && ci < npts, st)) a.codes[ci] = (uint16_t)code;
         atomicAdd(&a.hist[code], 1u);
@@ -934,7 +953,6 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(const __grid_con
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
-constexpr unsigned long long kCoarseMax = 4096;  // points of the largest coarse-group grid
 
 int g_level_cta_cap = 0;
 
@@ -1492,6 +1510,8 @@ static int run_coarse(const Plan& pl, int kc, const LevelArgs<T>& a, cudaStream_
     if (c.E[1] == 0 || c.E[2] == 0) return SZ3G_E_INVAL;
     c.dE2 = divu32(c.E[2]);
     c.dE1 = divu32(c.E[1]);
+    if (pd.grid == kc)
+      for (int q = 0; q < 3; ++q) d.xk[q] = pd.xstride[q + 1];
     c.ax = pd.axis - 1;
     c.m_ax = pd.m[pd.axis];
     c.interp = pd.interp;
@@ -1500,11 +1520,11 @@ static int run_coarse(const Plan& pl, int kc, const LevelArgs<T>& a, cudaStream_
     // stages them by code index
     if (c.off + c.count > pl.gsize[kc]) return SZ3G_E_INVAL;
   }
+  if (pl.gsize[kc] > kCoarseMax) return SZ3G_E_INVAL;  // one CTA holds the group (four points per thread)
   d.n_pass = n;
   d.chunk = pl.chunk;
   d.nsub = pl.nsub;
-  const size_t smem = COMP ? (size_t)pl.gsize[kc] * sizeof(T)
-                           : coarse_off_codes((size_t)pl.gsize[kc], sizeof(T)) + (size_t)pl.gsize[kc] * 2;
+  const size_t smem = coarse_off_codes((size_t)pl.gsize[kc], sizeof(T)) + (size_t)pl.gsize[kc] * (COMP ? sizeof(T) : 2);
   if (cudaFuncSetAttribute(coarse_kernel<T, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return SZ3G_E_CUDA;
