@@ -15,7 +15,7 @@ DebugInject g_debug = {0u, -1, -1, 0};
 int launch_encode(const Plan& pl, const uint16_t* codes, const uint32_t* table, const void* d_in, const PassMap* map,
                   void* scratch, DevState* st, unsigned char* d_out, unsigned long long out_capacity, int mode,
                   uint32_t* words_out, uint32_t* chunk_words_out, uint16_t* sub_out, unsigned long long cap_words,
-                  cudaStream_t s);
+                  cudaStream_t s, const sz3g_params* header_p = nullptr, bool* header_written = nullptr);
 int launch_compact_unpred(const Plan& pl, const uint16_t* codes, const void* d_in, const PassMap* map, void* scratch,
                           const uint32_t* table, void* d_unpred, DevState* st, cudaStream_t s);
 size_t encode_scratch_bytes(unsigned long long n_chunks);
@@ -312,9 +312,12 @@ int compress_enqueue_post(const sz3g_params* p, const Plan& pl, const void* d_in
                            out_capacity, pl.esz, s, L.rounds ? ws + L.rounds : nullptr));
   PassMap map;  // kernel parameter, copied at launch
   make_pass_map(pl, &map);
+  // the one-pass encoder writes the header from its last tile; otherwise a
+  // finalize launch does
+  bool header_written = false;
   SZ3G_TRY(launch_encode(pl, codes, table, d_in, &map, ws + L.enc, st, (unsigned char*)d_out, out_capacity,
-                         kEncodeStream, nullptr, nullptr, nullptr, 0, s));
-  SZ3G_TRY(launch_finalize(pl, p, st, (unsigned char*)d_out, out_capacity, s));
+                         kEncodeStream, nullptr, nullptr, nullptr, 0, s, p, &header_written));
+  if (!header_written) SZ3G_TRY(launch_finalize(pl, p, st, (unsigned char*)d_out, out_capacity, s));
   return SZ3G_OK;
 }
 

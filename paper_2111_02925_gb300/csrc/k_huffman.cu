@@ -1548,6 +1548,102 @@ __device__ __forceinline__ void chunk_counts(const uint16_t* __restrict__ codes,
   *zeros = zc;
 }
 
+// ---------------------------------------------------------------------------
+// Stream header (written last, once every count is known): by the encoder's
+// last tile when the one-pass encoder runs, else by finalize_kernel.
+// ---------------------------------------------------------------------------
+struct HeaderArgs {
+  unsigned char bytes[SZ3G_HEADER_BYTES];  // static fields, counts filled on device
+  unsigned long long n_chunks;
+  int esz;
+  uint32_t nsb;  // 512-code sub-blocks per chunk
+};
+
+// The header, the padding after each section and the stream length, by
+// threads tid of nthr; nw: payload words.
+__device__ void write_stream_header(const HeaderArgs& h, DevState* st, unsigned char* d_out,
+                                    unsigned long long out_capacity, unsigned long long nw, int tid, int nthr) {
+  if (st->flags & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound | kFlagCapacity | kFlagTimeout)) return;
+  const unsigned long long nu = st->n_unpred;
+  const uint32_t nused = st->n_used;
+  const unsigned long long off_table = SZ3G_HEADER_BYTES + pad8(nu * h.esz);
+  const unsigned long long off_chunks = off_table + pad8(3ull * nused);
+  const unsigned long long off_sub = off_chunks + pad8(h.n_chunks * 4);
+  const unsigned long long n_sub = h.n_chunks * (h.nsb - 1);
+  const unsigned long long off_payload = off_sub + pad8(n_sub * 2);
+  const unsigned long long end = off_payload + pad8(nw * 4);
+  if (end > out_capacity) {
+    if (tid == 0) atomicOr(&st->flags, kFlagCapacity);
+    return;
+  }
+  for (int b = tid; b < SZ3G_HEADER_BYTES; b += nthr) {
+    unsigned char v = h.bytes[b];
+    if (b >= 56 && b < 64) v = (unsigned char)(__double_as_longlong(st->eb_abs) >> (8 * (b - 56)));
+    if (b >= 64 && b < 72) v = (unsigned char)(st->ebT_bits >> (8 * (b - 64)));
+    if (b >= 76 && b < 80) v = (unsigned char)(nused >> (8 * (b - 76)));
+    if (b >= 88 && b < 96) v = (unsigned char)(nu >> (8 * (b - 88)));
+    if (b >= 104 && b < 112) v = (unsigned char)(nw >> (8 * (b - 104)));
+    d_out[b] = v;
+  }
+  // zero padding after the unpredictable values, the chunk table and the payload
+  if (tid < 8) {
+    const unsigned long long u_end = SZ3G_HEADER_BYTES + nu * h.esz;
+    if (u_end + tid < off_table) d_out[u_end + tid] = 0;
+    const unsigned long long c_end = off_chunks + h.n_chunks * 4;
+    if (c_end + tid < off_sub) d_out[c_end + tid] = 0;
+    const unsigned long long s_end = off_sub + n_sub * 2;
+    if (s_end + tid < off_payload) d_out[s_end + tid] = 0;
+    const unsigned long long p_end = off_payload + nw * 4;
+    if (p_end + tid < end) d_out[p_end + tid] = 0;
+  }
+  if (tid == 0) st->out_bytes = end;
+}
+
+__global__ void finalize_kernel(const HeaderArgs h, DevState* st, unsigned char* d_out,
+                                unsigned long long out_capacity) {
+  write_stream_header(h, st, d_out, out_capacity, st->n_words, threadIdx.x, blockDim.x);
+}
+
+// The header's static fields and the sizes the device needs to finish it.
+static HeaderArgs header_args(const Plan& pl, const sz3g_params* p) {
+  HeaderArgs h;
+  memset(&h, 0, sizeof(h));
+  unsigned char* b = h.bytes;
+  auto put = [&](int off, unsigned long long v, int n) {
+    for (int i = 0; i < n; ++i) b[off + i] = (unsigned char)(v >> (8 * i));
+  };
+  b[0] = 'S';
+  b[1] = 'Z';
+  b[2] = '3';
+  b[3] = 'G';
+  put(4, 1, 2);
+  b[6] = (unsigned char)p->dtype;
+  b[7] = (unsigned char)p->ndim;
+  for (int i = 0; i < 4; ++i) put(8 + 8 * i, i < (int)p->ndim ? p->dims[i] : 1, 8);
+  b[40] = (unsigned char)p->eb_mode;
+  b[41] = (unsigned char)p->interp;
+  b[42] = p->per_level;
+  b[43] = (unsigned char)pl.L;
+  put(44, p->radius, 4);
+  unsigned long long ebb;
+  memcpy(&ebb, &p->eb, 8);
+  put(48, ebb, 8);
+  put(72, p->chunk_codes, 4);
+  put(80, pl.N, 8);
+  put(96, pl.n_chunks, 8);
+  if (p->per_level) {
+    for (int l = 1; l <= pl.L; ++l) {
+      b[112 + l] = p->level_interp[l];
+      for (int i = 0; i < 4; ++i) b[144 + 4 * l + i] = i < (int)p->ndim ? p->level_order[l][i] : 0;
+    }
+  }
+  for (int i = 0; i < 4; ++i) b[272 + i] = i < (int)p->ndim ? p->dim_order[i] : 0;
+  h.n_chunks = pl.n_chunks;
+  h.esz = pl.esz;
+  h.nsb = pl.nsub;
+  return h;
+}
+
 // Stream-mode encoder in one pass for any number of chunks: tiles of
 // kEncWarps consecutive chunks taken in ticket order; each warp counts its
 // chunk, the tile's totals are published and the words and zero codes before
@@ -1559,7 +1655,9 @@ template <typename U>
 __global__ void __launch_bounds__(kEncWarps * 32, 5) tile_pack_kernel(const EncArgs a,
                                                                        const __grid_constant__ PassMap map,
                                                                        uint32_t* ticket, unsigned long long* wstat,
-                                                                       unsigned long long* zstat) {
+                                                                       unsigned long long* zstat,
+                                                                       const __grid_constant__ HeaderArgs hdr,
+                                                                       int with_header) {
   __shared__ uint32_t ring[kEncWarps][kPackRing];
   __shared__ uint32_t s_words[kEncWarps], s_zeros[kEncWarps], s_tile;
   __shared__ unsigned long long s_we, s_ze;
@@ -1607,6 +1705,11 @@ __global__ void __launch_bounds__(kEncWarps * 32, 5) tile_pack_kernel(const EncA
       wexcl += s_words[q];
       zexcl += s_zeros[q];
     }
+    if (with_header && tile + 1 == ntiles) {  // every total is known once the last tile's prefix is
+      unsigned long long nw = s_we;
+      for (int q = 0; q < kEncWarps; ++q) nw += s_words[q];
+      write_stream_header(hdr, st, a.d_out, a.out_capacity, nw, threadIdx.x, blockDim.x);
+    }
     if (j < a.n_chunks)
       pack_chunk<U>(a, map, buf, lane, j, words, wexcl, zexcl, off_chunks, off_sub, off_payload, unp, nu);
     __syncthreads();  // the tile's shared counts are read before the next ticket overwrites them
@@ -1616,7 +1719,9 @@ __global__ void __launch_bounds__(kEncWarps * 32, 5) tile_pack_kernel(const EncA
 // count -> two scans -> emit (or, stream mode on at most kOnePassMaxChunks
 // chunks, emit alone).  scratch: encode_scratch_bytes(n_chunks).
 constexpr unsigned long long kOnePassMaxChunks = 1024;
-static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch, cudaStream_t s) {
+static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch, cudaStream_t s,
+                           const HeaderArgs* hdr = nullptr, bool* header_written = nullptr) {
+  if (header_written) *header_written = false;
   a.spin_limit = g_debug.wait_limit ? g_debug.wait_limit : (uint32_t)kSpinLimit;
   a.silent_chunk = g_debug.silent_chunk;
   const unsigned long long nch = a.n_chunks;
@@ -1656,12 +1761,17 @@ static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_pack_kernel<unsigned long long>, kEncWarps * 32, 0);
     if (per < 1) per = 1;
     const unsigned ng = (unsigned)std::min<unsigned long long>(ntiles, (unsigned long long)nsm * per);
+    HeaderArgs h{};
+    if (hdr) h = *hdr;
+    const int wh = hdr ? 1 : 0;
     if (a.esz == 4)
-      SZ3G_LAUNCH(kKEncode, s, tile_pack_kernel<uint32_t><<<ng, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze));
+      SZ3G_LAUNCH(kKEncode, s, tile_pack_kernel<uint32_t><<<ng, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze, h, wh));
     else
       SZ3G_LAUNCH(kKEncode, s,
-                  tile_pack_kernel<unsigned long long><<<ng, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze));
-    return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
+                  tile_pack_kernel<unsigned long long><<<ng, kEncWarps * 32, 0, s>>>(a, *map, cw, we, ze, h, wh));
+    if (cudaGetLastError() != cudaSuccess) return SZ3G_E_CUDA;
+    if (header_written) *header_written = hdr != nullptr;
+    return SZ3G_OK;
   }
   SZ3G_LAUNCH(kKEncode, s, count_kernel<<<nb, kEncWarps * 32, 0, s>>>(a.codes, a.table, a.n, nch, a.chunk, cw, cz));
   if (a.mode == kEncodeStream && a.emit_payload) {
@@ -1702,7 +1812,7 @@ static int encode_pipeline(EncArgs a, const PassMap* map, unsigned char* scratch
 int launch_encode(const Plan& pl, const uint16_t* codes, const uint32_t* table, const void* d_in, const PassMap* map,
                   void* scratch, DevState* st, unsigned char* d_out, unsigned long long out_capacity, int mode,
                   uint32_t* words_out, uint32_t* chunk_words_out, uint16_t* sub_out, unsigned long long cap_words,
-                  cudaStream_t s) {
+                  cudaStream_t s, const sz3g_params* header_p, bool* header_written) {
   EncArgs a{};
   a.codes = codes;
   a.table = table;
@@ -1722,6 +1832,11 @@ int launch_encode(const Plan& pl, const uint16_t* codes, const uint32_t* table, 
   a.unpred_out = nullptr;
   a.mode = mode;
   a.emit_payload = 1;
+  if (header_p && mode == kEncodeStream) {
+    const HeaderArgs h = header_args(pl, header_p);
+    return encode_pipeline(a, map, (unsigned char*)scratch, s, &h, header_written);
+  }
+  if (header_written) *header_written = false;
   return encode_pipeline(a, map, (unsigned char*)scratch, s);
 }
 
@@ -1744,92 +1859,9 @@ int launch_compact_unpred(const Plan& pl, const uint16_t* codes, const void* d_i
   return encode_pipeline(a, map, (unsigned char*)scratch, s);
 }
 
-// ---------------------------------------------------------------------------
-// Stream header (written last, once every count is known).
-// ---------------------------------------------------------------------------
-struct HeaderArgs {
-  unsigned char bytes[SZ3G_HEADER_BYTES];  // static fields, counts filled on device
-  unsigned long long n_chunks;
-  int esz;
-  uint32_t nsb;  // 512-code sub-blocks per chunk
-};
-
-__global__ void finalize_kernel(const HeaderArgs h, DevState* st, unsigned char* d_out,
-                                unsigned long long out_capacity) {
-  const int tid = threadIdx.x;
-  if (st->flags & (kFlagNonFinite | kFlagZeroRange | kFlagBadBound | kFlagCapacity | kFlagTimeout)) return;
-  const unsigned long long nu = st->n_unpred, nw = st->n_words;
-  const uint32_t nused = st->n_used;
-  const unsigned long long off_table = SZ3G_HEADER_BYTES + pad8(nu * h.esz);
-  const unsigned long long off_chunks = off_table + pad8(3ull * nused);
-  const unsigned long long off_sub = off_chunks + pad8(h.n_chunks * 4);
-  const unsigned long long n_sub = h.n_chunks * (h.nsb - 1);
-  const unsigned long long off_payload = off_sub + pad8(n_sub * 2);
-  const unsigned long long end = off_payload + pad8(nw * 4);
-  if (end > out_capacity) {
-    if (tid == 0) atomicOr(&st->flags, kFlagCapacity);
-    return;
-  }
-  for (int b = tid; b < SZ3G_HEADER_BYTES; b += blockDim.x) {
-    unsigned char v = h.bytes[b];
-    if (b >= 56 && b < 64) v = (unsigned char)(__double_as_longlong(st->eb_abs) >> (8 * (b - 56)));
-    if (b >= 64 && b < 72) v = (unsigned char)(st->ebT_bits >> (8 * (b - 64)));
-    if (b >= 76 && b < 80) v = (unsigned char)(nused >> (8 * (b - 76)));
-    if (b >= 88 && b < 96) v = (unsigned char)(nu >> (8 * (b - 88)));
-    if (b >= 104 && b < 112) v = (unsigned char)(nw >> (8 * (b - 104)));
-    d_out[b] = v;
-  }
-  // zero padding after the unpredictable values, the chunk table and the payload
-  if (tid < 8) {
-    const unsigned long long u_end = SZ3G_HEADER_BYTES + nu * h.esz;
-    if (u_end + tid < off_table) d_out[u_end + tid] = 0;
-    const unsigned long long c_end = off_chunks + h.n_chunks * 4;
-    if (c_end + tid < off_sub) d_out[c_end + tid] = 0;
-    const unsigned long long s_end = off_sub + n_sub * 2;
-    if (s_end + tid < off_payload) d_out[s_end + tid] = 0;
-    const unsigned long long p_end = off_payload + nw * 4;
-    if (p_end + tid < end) d_out[p_end + tid] = 0;
-  }
-  if (tid == 0) st->out_bytes = end;
-}
-
 int launch_finalize(const Plan& pl, const sz3g_params* p, DevState* st, unsigned char* d_out,
                     unsigned long long out_capacity, cudaStream_t s) {
-  HeaderArgs h;
-  memset(&h, 0, sizeof(h));
-  unsigned char* b = h.bytes;
-  auto put = [&](int off, unsigned long long v, int n) {
-    for (int i = 0; i < n; ++i) b[off + i] = (unsigned char)(v >> (8 * i));
-  };
-  b[0] = 'S';
-  b[1] = 'Z';
-  b[2] = '3';
-  b[3] = 'G';
-  put(4, 1, 2);
-  b[6] = (unsigned char)p->dtype;
-  b[7] = (unsigned char)p->ndim;
-  for (int i = 0; i < 4; ++i) put(8 + 8 * i, i < (int)p->ndim ? p->dims[i] : 1, 8);
-  b[40] = (unsigned char)p->eb_mode;
-  b[41] = (unsigned char)p->interp;
-  b[42] = p->per_level;
-  b[43] = (unsigned char)pl.L;
-  put(44, p->radius, 4);
-  unsigned long long ebb;
-  memcpy(&ebb, &p->eb, 8);
-  put(48, ebb, 8);
-  put(72, p->chunk_codes, 4);
-  put(80, pl.N, 8);
-  put(96, pl.n_chunks, 8);
-  if (p->per_level) {
-    for (int l = 1; l <= pl.L; ++l) {
-      b[112 + l] = p->level_interp[l];
-      for (int i = 0; i < 4; ++i) b[144 + 4 * l + i] = i < (int)p->ndim ? p->level_order[l][i] : 0;
-    }
-  }
-  for (int i = 0; i < 4; ++i) b[272 + i] = i < (int)p->ndim ? p->dim_order[i] : 0;
-  h.n_chunks = pl.n_chunks;
-  h.esz = pl.esz;
-  h.nsb = pl.nsub;
+  const HeaderArgs h = header_args(pl, p);
   SZ3G_LAUNCH(kKFinalize, s, finalize_kernel<<<1, 64, 0, s>>>(h, st, d_out, out_capacity));
   return cudaGetLastError() == cudaSuccess ? SZ3G_OK : SZ3G_E_CUDA;
 }
